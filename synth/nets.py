@@ -1,0 +1,92 @@
+"""Seeded multilayer perceptrons shaped like the paper's networks (Eq. 3, Table 1).
+
+Weights are drawn N(0, 1/fan_in) and biases are zero.  The trained MNIST and SCOPF
+networks of the paper are not available, so these random networks stand in for them
+with the same widths, depths and activations.
+"""
+from dataclasses import dataclass, field
+from typing import List, Optional
+import numpy as np
+
+from .rng import derive_key, normal
+
+ACTIVATIONS = ("identity", "tanh", "sigmoid", "softplus", "gelu")
+
+
+@dataclass
+class MLPSpec:
+    """Widths d_0 = n_in, d_1, ..., d_L = n_out and one activation name per layer."""
+    widths: List[int]
+    acts: List[str]
+    name: str = "mlp"
+
+    def __post_init__(self):
+        assert len(self.acts) == len(self.widths) - 1
+        for a in self.acts:
+            assert a in ACTIVATIONS, a
+
+    @property
+    def n_layers(self) -> int:
+        return len(self.widths) - 1
+
+    @property
+    def n_in(self) -> int:
+        return self.widths[0]
+
+    @property
+    def n_out(self) -> int:
+        return self.widths[-1]
+
+    @property
+    def n_weights(self) -> int:
+        return sum(self.widths[l] * self.widths[l + 1] for l in range(self.n_layers))
+
+    @property
+    def n_params(self) -> int:
+        return self.n_weights + sum(self.widths[1:])
+
+
+@dataclass
+class MLP:
+    spec: MLPSpec
+    W: List[np.ndarray]            # W[l] has shape (d_{l+1}, d_l), row-major, float64
+    b: List[np.ndarray]            # b[l] has shape (d_{l+1},)
+    seed: int = 0
+    extra: dict = field(default_factory=dict)
+
+
+def make_mlp(spec: MLPSpec, seed: int = 0, tag: str = "mlp", bias_std: float = 0.0) -> MLP:
+    W, b = [], []
+    for l in range(spec.n_layers):
+        m, k = spec.widths[l + 1], spec.widths[l]
+        key = derive_key(seed, tag, "W", l)
+        W.append(normal(key, m * k).reshape(m, k) / np.sqrt(k))
+        if bias_std > 0.0:
+            b.append(bias_std * normal(derive_key(seed, tag, "b", l), m))
+        else:
+            b.append(np.zeros(m))
+    return MLP(spec, W, b, seed)
+
+
+def mnist_like_spec(hidden: int, n_hidden_layers: int, act: str = "tanh",
+                    out_act: str = "identity", n_in: int = 784, n_out: int = 10) -> MLPSpec:
+    """784 -> hidden x n_hidden_layers -> 10.  The output layer is linear (logits) by default."""
+    widths = [n_in] + [hidden] * n_hidden_layers + [n_out]
+    acts = [act] * n_hidden_layers + [out_act]
+    return MLPSpec(widths, acts, name=f"mnist_{n_in}_{hidden}x{n_hidden_layers}_{n_out}_{act}")
+
+
+def surrogate_spec(n_in: int, hidden: int = 1024, depth: int = 5, act: str = "sigmoid") -> MLPSpec:
+    """A stability-margin surrogate: n_in setpoints -> hidden x depth -> 1 margin."""
+    return MLPSpec([n_in] + [hidden] * depth + [1], [act] * depth + ["identity"],
+                   name=f"surrogate_{n_in}_{hidden}x{depth}")
+
+
+# Named workloads (synthetic stand-ins for the paper's MNIST classifiers).
+TINY = mnist_like_spec(128, 2)                 # 784 -> 128 -> 128 -> 10, 118,016 weights
+PAPER_104M = mnist_like_spec(4096, 7)          # 784 -> 4096 x 7 -> 10, 103,944,202 params
+PAPER_87M = mnist_like_spec(4096, 6)           # literal "6 hidden layers" reading, 87,162,890 params
+
+
+def spec_by_name(name: str) -> Optional[MLPSpec]:
+    return {"tiny": TINY, "104m": PAPER_104M, "87m": PAPER_87M}.get(name)
