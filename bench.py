@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""Throughput of the reduced-space network-constraint oracles on one GB300 (or N replicas).
+
+One step = everything one interior-point iteration asks of the network at one point x (with
+multipliers lambda): the value NN(x), the Jacobian (n_out reverse seeds), the gradient
+lambda^T J, the Hessian of lambda^T NN (n_in forward-over-reverse tangents, Eq. 6) and the FP64
+residual y - NN(x).  The metric is Hessian-of-Lagrangian evaluations per second, i.e. steps/s,
+with inputs resident in HBM; `e2e` is the same through the host-pointer C ABI (copies inside).
+
+Workload: the ~104M-parameter MNIST-shaped net 784 -> 4096 x 7 -> 10 (tanh, N(0, 1/fan_in)
+weights, seed 0), x0 ~ U[0,1]^784, lambda ~ N(0,1).  The weights (1.7 GB in the split-BF16
+form, 0.8 GB FP64) exceed the 129 MB L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--prec bf16x3|bf16|fp32|fp64]
+Under torchrun each rank runs an independent replica (the path does not shard); rank 0 prints
+one JSON line.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "hessian_lag_evals_per_s"
+UNIT = "evals/s"
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--prec", default="bf16x3", choices=["bf16x3", "bf16", "fp32", "fp64"])
+    p.add_argument("--workload", default="104m", choices=["104m", "87m", "tiny"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-fp64-form", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def _workload(name):
+    import synth
+    spec = synth.spec_by_name(name)
+    mlp = synth.make_mlp(spec, seed=0)
+    d = synth.adversarial_data(n_in=spec.n_in, n_out=spec.n_out, seed=0)
+    return spec, mlp, d
+
+
+def _workload_config(spec, name, prec):
+    return {"workload": f"mnist_{name}_{'x'.join(map(str, spec.widths))}_tanh",
+            "n_params": spec.n_params, "n_in": spec.n_in, "n_out": spec.n_out,
+            "precision_form": prec, "inputs": "x0~U[0,1]^784, lambda~N(0,1), weights N(0,1/fan_in) seed 0",
+            "l2": "weights exceed L2 (no flush needed)"}
+
+
+# ------------------------------------------------------------------ algorithmic work
+def hessian_flops(spec):
+    """Algorithmic FLOPs of one Hessian by the per-layer sum form that the GPU runs, counted once
+    (no padding, no x3): forward tangents 2 n m_l k_l for l >= 2, plus the lower triangle of each
+    Zdot_l^T diag(c_l) Zdot_l, n (n+1) m_l, for layers with curvature."""
+    n = spec.n_in
+    f = 0
+    L = spec.n_layers
+    for l in range(L):
+        m, k = spec.widths[l + 1], spec.widths[l]
+        has_curv = spec.acts[l] != "identity"
+        last = l == L - 1
+        if l >= 1 and not (last and not has_curv):
+            f += 2 * n * m * k
+        if has_curv:
+            f += n * (n + 1) * m
+    return f
+
+
+def tangent_gemm_flops(spec):
+    """(flops per launch, launches) of the tangent GEMM Zdot_l = W_l Adot_{l-1}."""
+    n = spec.n_in
+    per = []
+    L = spec.n_layers
+    for l in range(1, L):
+        last = l == L - 1
+        if last and spec.acts[l] == "identity":
+            continue
+        per.append(2 * n * spec.widths[l + 1] * spec.widths[l])
+    return per
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(gpu_index)], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = sorted(r[0] for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[2][i].lower().startswith("active")})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def _gpu_index(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",")]
+        if local_rank < len(ids) and ids[local_rank].isdigit():
+            return int(ids[local_rank])
+    return local_rank
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ------------------------------------------------------------------ oracle timing
+def oracle_step(mlp, x, lam, cols=None):
+    from oracle import nn as onn
+    y = onn.value(mlp, x)
+    onn.jacobian(mlp, x)
+    onn.vjp(mlp, x, lam)
+    if cols is None:
+        onn.hessian_lag(mlp, x, lam)
+    else:
+        onn.hessian_lag_columns(mlp, x, lam, cols)
+    _ = y - onn.value(mlp, x)  # the residual y - NN(x) in FP64
+
+
+def time_oracle(mlp, d, budget_s=20.0, max_steps=3):
+    """Bounded sample: full oracle steps until `budget_s` seconds (at least one)."""
+    n_done, t0 = 0, time.perf_counter()
+    while True:
+        oracle_step(mlp, d.x0, d.lam)
+        n_done += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or n_done >= max_steps:
+            break
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": n_done / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n_done} full oracle step(s) (value, Jacobian, gradient, forward-over-reverse "
+                      f"Hessian, FP64 residual) in {el:.1f} s, numpy FP64 with multithreaded BLAS"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    spec, mlp, d = _workload(args.workload)
+    cfg = _workload_config(spec, args.workload, "oracle-fp64")
+    # Each reference step is one full oracle step when that is cheap enough; otherwise a sample
+    # of 1/8 of the Hessian's tangent columns, whose time is scaled to a full evaluation.
+    t0 = time.perf_counter()
+    oracle_step(mlp, d.x0, d.lam)
+    t_full = time.perf_counter() - t0
+    budget = 150.0
+    steps_total = args.steps + args.warmup
+    sample_cols = None
+    scale = 1.0
+    if t_full * steps_total > budget:
+        nc = max(1, spec.n_in // 8)
+        sample_cols = np.arange(nc)
+        t0 = time.perf_counter()
+        oracle_step(mlp, d.x0, d.lam, cols=np.arange(1))
+        t_fixed = time.perf_counter() - t0
+        scale = None
+    for _ in range(max(0, args.warmup - 1)):
+        oracle_step(mlp, d.x0, d.lam, cols=sample_cols)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_step(mlp, d.x0, d.lam, cols=sample_cols)
+    el = time.perf_counter() - t0
+    per = el / args.steps
+    if sample_cols is not None:
+        # full eval ~ fixed part + 8 x (sampled-columns part)
+        per = t_fixed + (spec.n_in / len(sample_cols)) * max(per - t_fixed, 0.0)
+        sample = (f"{args.steps} oracle steps with {len(sample_cols)} of {spec.n_in} Hessian tangent "
+                  f"columns, scaled to a full evaluation (fixed part {t_fixed:.2f} s)")
+    else:
+        sample = f"{args.steps} full oracle steps"
+    value = 1.0 / per
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": cfg,
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "gpu_launches": 0}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    spec, mlp, d = _workload(args.workload)
+    cpu_baseline = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_baseline = time_oracle(mlp, d)  # before the first GPU call
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    from paper_2509_22462_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2509_22462_gb300 import nnc
+
+    net = nnc.Net.from_mlp(mlp, precision=args.prec)
+    n, m = spec.n_in, spec.n_out
+    x = torch.tensor(d.x0, device=dev)
+    lam = torch.tensor(d.lam, device=dev)
+    y = torch.empty(m, dtype=torch.float64, device=dev)
+    J = torch.empty(m, n, dtype=torch.float64, device=dev)
+    H = torch.empty(n, n, dtype=torch.float64, device=dev)
+    g = torch.empty(n, dtype=torch.float64, device=dev)
+    r = torch.empty(m, dtype=torch.float64, device=dev)
+
+    def step():
+        net.eval_all_dev(x, lam, y, J, H, g)
+        net.residual_dev(x, y, r)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = Clocks(_gpu_index(local_rank)) if rank == 0 else None
+    time.sleep(0.3 if clocks else 0)
+    net.profile(True)
+    launches0 = nnc.launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = nnc.launch_count() - launches0
+    prof = net.profile_read()
+    net.profile(False)
+    clk = clocks.stop() if clocks else None
+    el_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([el_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el_ms = float(t.item())
+    value = world * args.steps / (el_ms / 1e3)
+
+    # roofline of the dominant kernel kind (by total time in the timed region)
+    peaks, peak_src = _peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_cnt) = dom
+    roof = None
+    if dom_name == "tangent_gemm" and dom_cnt > 0:
+        per = tangent_gemm_flops(spec)
+        fl_per_launch = sum(per) / len(per)
+        avg_s = dom_ms / dom_cnt / 1e3
+        ach = fl_per_launch / avg_s / 1e12
+        pk = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        roof = {"kernel": "k_tc_gemm (tangent: Zdot_l = W_l Adot_{l-1}, fused sigma' / sigma'' epilogue)"
+                if args.prec.startswith("bf16") else "k_simt_gemm (tangent)",
+                "bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                "traffic": None, "peak_source": f"{peak_src} bf16 sustained",
+                "executed_frac": ach * (3 if args.prec == "bf16x3" else 1) / pk,
+                "avg_launch_us": avg_s * 1e6, "launches": dom_cnt,
+                "algorithmic_flops_per_launch": fl_per_launch}
+    elif dom_cnt > 0:
+        avg_s = dom_ms / dom_cnt / 1e3
+        roof = {"kernel": dom_name, "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"),
+                "unit": "GB/s", "frac": None, "traffic": None, "avg_launch_us": avg_s * 1e6}
+    kernel_ms = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+                 for k, v in prof.items()}
+
+    # end to end through the host-pointer C ABI (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        xh, lh = d.x0.copy(), d.lam.copy()
+        for _ in range(2):
+            ys, Js, Hs = nnc.eval_batched([net], [xh], [lh])
+            net.residual(xh, ys[0])
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ys, Js, Hs = nnc.eval_batched([net], [xh], [lh])
+            net.residual(xh, ys[0])
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        h2d = 8 * (n + m) + 8 * (n + m)          # x, lambda; then x, y for the residual
+        d2h = 8 * (m + m * n + n * n) + 8 * m    # y, J, H; then r
+        e2e = {"value": world * args.steps / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    # the FP64 form on the same GPU, for the TC-vs-FP64 comparison of the metric
+    forms = {args.prec: {"evals_per_s": value / world, "ms_per_eval": el_ms / args.steps}}
+    if rank == 0 and not args.no_fp64_form and args.prec != "fp64":
+        net.free()
+        n64 = nnc.Net.from_mlp(mlp, precision="fp64")
+
+        def step64():
+            n64.eval_all_dev(x, lam, y, J, H, g)
+            n64.residual_dev(x, y, r)
+
+        step64()
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k64 = 3
+        a0.record()
+        for _ in range(k64):
+            step64()
+        a1.record()
+        torch.cuda.synchronize()
+        ms64 = a0.elapsed_time(a1) / k64
+        forms["fp64"] = {"evals_per_s": 1e3 / ms64, "ms_per_eval": ms64, "steps": k64}
+        n64.free()
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if args.prec.startswith("bf16") else
+               ("f32" if args.prec == "fp32" else "f64"),
+               "data": "synthetic", "config": _workload_config(spec, args.workload, args.prec),
+               "roofline": roof, "cpu_baseline": cpu_baseline, "e2e": e2e, "gpu_launches": launches,
+               "clocks": clk, "kernels": kernel_ms, "forms": forms,
+               "hessian_algorithmic_gflop": hessian_flops(spec) / 1e9}
+        print(json.dumps(out), flush=True)
+    return 0
+
+
+def main():
+    args = _args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if (args.impl == "ours" and torch.cuda.is_available()) else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local_rank)
+        dist.init_process_group(backend)
+    try:
+        if args.impl == "reference":
+            return run_reference(args, rank, world)
+        return run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,149 @@
+/*
+ * nnc.h -- C ABI of libnnc: oracles for a neural-network constraint y = NN(x) embedded in a
+ * nonlinear program, computed by hand-written CUDA kernels for sm_103a (GB300).
+ *
+ * The problem is Eq. 1 of the paper (min f(x) s.t. g(x) = 0, x >= 0).  In the reduced-space
+ * ("gray-box") formulation of Section 3.2 the network appears as the single vector constraint
+ * g(x, y) = y - NN(x) (Eq. 5), and an interior-point method (Eq. 2) asks at every iteration for
+ *   - the value NN(x),
+ *   - the dense Jacobian dNN/dx  (n_out x n_in),
+ *   - the dense n_in x n_in matrix sum_i lambda_i d2 NN_i/dx2, the Hessian of the scalar
+ *     lambda^T NN(x) (Eq. 6, Section 3.2.1).
+ * NN is the multilayer perceptron of Eq. 3: z_l = W_l a_{l-1} + b_l, a_l = sigma_l(z_l),
+ * a_0 = x, NN(x) = a_L, with W_l of shape d_l x d_{l-1} and d_0 = n_in, d_L = n_out.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: NNC_OK (0) on success, a negative nnc_status otherwise.  Nothing aborts or
+ *     throws across this interface.  nnc_last_error() gives a message for the calling thread.
+ *   - Host pointers ("const double* x"): owned by the caller, read or written during the call
+ *     only; the call copies them to or from the device and returns after the device work and
+ *     the copies have finished.
+ *   - Device pointers (entry points ending in _dev): owned by the caller, must stay valid
+ *     until the work queued on `stream` has finished; the call returns once the work is
+ *     queued (asynchronous).  `stream` is a cudaStream_t; NULL means the net's own stream.
+ *   - All matrices are dense, row-major, FP64, without padding.
+ *   - One net may be used by one host thread at a time; calls on one net are serialised on
+ *     its stream.  Different nets are independent.
+ *   - There is no CPU fallback: without a usable sm_103a device every call returns
+ *     NNC_ERR_CUDA.
+ */
+#ifndef NNC_H
+#define NNC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nnc_net nnc_net; /* opaque; the library owns all of its device memory */
+
+typedef enum {
+  NNC_OK = 0,
+  NNC_ERR_ARG = -1,         /* bad argument: null pointer, bad size or code */
+  NNC_ERR_CUDA = -2,        /* a CUDA call failed or no sm_103a device */
+  NNC_ERR_NONFINITE = -3,   /* an input (x or lambda) holds NaN or Inf */
+  NNC_ERR_TIMEOUT = -4,     /* a bounded device-side wait ran out; outputs are undefined */
+  NNC_ERR_OOM = -5,         /* device allocation failed */
+  NNC_ERR_UNSUPPORTED = -6  /* request not supported for this net (e.g. activation/precision) */
+} nnc_status;
+
+/* Number format of the network evaluation (Section 5.1 leaves it unstated).
+ *   NNC_FP64   : every kernel in FP64 (value, Jacobian, Hessian).  The reference form.
+ *   NNC_FP32   : FP32 weights and tangents on CUDA cores, FP32 products, FP64 outputs.
+ *   NNC_BF16   : value/Jacobian/adjoint in FP32; Hessian sweep on tcgen05 tensor cores with
+ *                BF16 operands and FP32 accumulation (one product per tile).
+ *   NNC_BF16X3 : as NNC_BF16, but every tensor-core product is split-BF16x3 compensated:
+ *                A*B ~ Ahi*Bhi + Ahi*Blo + Alo*Bhi, all three accumulated in one FP32 tile.
+ *   NNC_FP8    : as NNC_BF16, but the Hessian sweep runs kind::f8f6f4 with e4m3 weights and
+ *                per-output-row scales.  Reported, not held to the BF16 tolerances.
+ * In every form nnc_residual (and nnc_eval with fp64_residual != 0) uses FP64 weights. */
+typedef enum { NNC_FP64 = 0, NNC_FP32 = 1, NNC_BF16 = 2, NNC_BF16X3 = 3, NNC_FP8 = 4 } nnc_precision;
+
+/* sigma_l of Eq. 3.  All are C^2, as interior-point methods require (Section 2). */
+typedef enum { NNC_IDENTITY = 0, NNC_TANH = 1, NNC_SIGMOID = 2, NNC_SOFTPLUS = 3, NNC_GELU = 4 } nnc_act;
+
+/* Bits of `what` in nnc_eval_batched. */
+#define NNC_WANT_Y 1u    /* value NN(x) */
+#define NNC_WANT_J 2u    /* Jacobian dNN/dx */
+#define NNC_WANT_H 4u    /* Hessian of lambda^T NN (needs lambda) */
+#define NNC_WANT_G 8u    /* gradient lambda^T dNN/dx (needs lambda) */
+
+/* Build a net on the current CUDA device from FP64 host weights (Eq. 3; the weights are
+ * constant during optimisation, Section 3).
+ *   out      : receives the new net (NULL on failure).
+ *   n_layers : L >= 1.
+ *   widths   : L+1 entries d_0..d_L, each in [1, 65536].
+ *   act      : L entries of nnc_act, sigma_1..sigma_L.
+ *   W        : L host pointers; W[l] is d_{l+1} x d_l row-major (layer l+1 of the paper).
+ *   b        : L host pointers; b[l] has d_{l+1} entries; b itself or b[l] may be NULL (zero).
+ *   prec     : nnc_precision of the Hessian / Jacobian / value kernels.
+ *   stream   : cudaStream_t the net queues its work on; NULL creates a private stream.
+ * The weights are copied and packed once (FP64 copy, FP32 copy, BF16 hi/lo split, FP8 with
+ * per-row scales, as the precision needs); the caller may free W and b on return. */
+int nnc_load_weights(nnc_net** out, int n_layers, const int* widths, const int* act,
+                     const double* const* W, const double* const* b, int prec, void* stream);
+
+/* y = NN(x) (Eq. 3).  x: n_in doubles; y: n_out doubles.  fp64_residual != 0 evaluates with
+ * the FP64 weight copy whatever the precision form (the FP64 correction of the residual). */
+int nnc_eval(nnc_net* net, const double* x, double* y, int fp64_residual);
+
+/* r = y - NN(x) in FP64 on the device: the residual of g(x, y) = y - NN(x) (Eq. 5) used at
+ * step acceptance.  x: n_in, y: n_out, r: n_out doubles. */
+int nnc_residual(nnc_net* net, const double* x, const double* y, double* r);
+
+/* J = dNN/dx at x by a reverse sweep with n_out seed columns (the Jacobian oracle of
+ * Section 2).  J: n_out x n_in row-major. */
+int nnc_jacobian(nnc_net* net, const double* x, double* J);
+
+/* H = sum_i lambda_i d2 NN_i/dx2 at x (Eq. 6): the Hessian of the scalar lambda^T NN(x),
+ * computed without forming the third-order tensor.  H: n_in x n_in row-major, exactly
+ * symmetric.  grad (may be NULL): the gradient lambda^T dNN/dx, n_in doubles.  The caller
+ * applies the sign of g = y - NN and adds the objective's Hessian. */
+int nnc_hessian_lag(nnc_net* net, const double* x, const double* lambda, double* H, double* grad);
+
+/* Several nets (each with its own sizes) evaluated together: for k < K, the outputs selected
+ * by `what` (NNC_WANT_* bits) for nets[k] at x[k] (and lambda[k]).  Arrays of K host pointers;
+ * y[k], J[k], H[k] may be NULL when not requested (the whole array may be NULL if its bit is
+ * not set).  All nets must share one precision and one CUDA device.  With K = 1 this is the
+ * single-net "everything at one point" call of one interior-point iteration. */
+int nnc_eval_batched(nnc_net* const* nets, int K, const double* const* x,
+                     const double* const* lambda, double* const* y, double* const* J,
+                     double* const* H, unsigned what);
+
+/* Device-pointer twins (asynchronous on `stream`, NULL = the net's stream).  Same meanings as
+ * above; every pointer is device memory of the stated size in doubles. */
+int nnc_eval_dev(nnc_net* net, const double* x, double* y, int fp64_residual, void* stream);
+int nnc_residual_dev(nnc_net* net, const double* x, const double* y, double* r, void* stream);
+int nnc_jacobian_dev(nnc_net* net, const double* x, double* J, void* stream);
+int nnc_hessian_lag_dev(nnc_net* net, const double* x, const double* lambda, double* H,
+                        double* grad, void* stream);
+/* One-net "everything" call on device pointers: y, J, H, grad may each be NULL (skipped). */
+int nnc_eval_all_dev(nnc_net* net, const double* x, const double* lambda, double* y, double* J,
+                     double* H, double* grad, void* stream);
+
+/* Free a net and all of its device memory (waits for its stream).  NULL is ignored. */
+void nnc_free(nnc_net* net);
+
+/* Message describing the last error on the calling thread ("" if none).  Valid until the
+ * next call from the same thread. */
+const char* nnc_last_error(void);
+
+/* Query helpers (no device work). */
+int nnc_net_info(const nnc_net* net, int* n_layers, int* n_in, int* n_out, int* prec);
+/* Number of kernel launches this library queued since load (all nets, this process). */
+long long nnc_launch_count(void);
+
+/* Per-kernel timing with CUDA events on the net's launch streams (no effect on results).
+ * nnc_profile(net, 1) starts recording a pair of events around every launch (and clears what
+ * was recorded); nnc_profile_read waits for the recorded work, then fills ms[k] (total
+ * milliseconds) and count[k] (launches) for kernel kind k < n_kinds and clears the record:
+ *   0 tangent GEMM, 1 symmetric product (Hessian accumulation), 2 forward layer,
+ *   3 reverse layer, 4 other. */
+int nnc_profile(nnc_net* net, int enable);
+int nnc_profile_read(nnc_net* net, double* ms, long long* count, int n_kinds);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NNC_H */

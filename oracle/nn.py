@@ -190,3 +190,26 @@ def hessian_lag(net, x, lam):
 def all_outputs(net, x, lam):
     """(y, J, H, grad) at one point: value, Jacobian, Hessian of lambda^T NN and its gradient."""
     return value(net, x), jacobian(net, x), hessian_lag(net, x, lam), vjp(net, x, lam)
+
+
+def hessian_lag_columns(net, x, lam, cols):
+    """Columns `cols` of the forward-over-reverse Hessian: the same sweeps as `hessian_lag_for`
+    with only the tangents e_j, j in cols (Adot_0 = I[:, cols]).  Used to sample large Hessians."""
+    zs, _ = forward(net, x)
+    abars = adjoints(net, zs, lam)
+    L = len(net.W)
+    n = net.spec.n_in
+    cols = np.asarray(cols, dtype=np.int64)
+    Adot = np.eye(n)[:, cols]
+    Zdots = []
+    for l in range(1, L + 1):
+        Zdot = net.W[l - 1] @ Adot
+        Adot = act_d1(net.spec.acts[l - 1], zs[l - 1])[:, None] * Zdot
+        Zdots.append(Zdot)
+    dabar = np.zeros((net.spec.n_out, cols.size))
+    for l in range(L, 0, -1):
+        act = net.spec.acts[l - 1]
+        dzbar = act_d1(act, zs[l - 1])[:, None] * dabar + \
+            (act_d2(act, zs[l - 1]) * abars[l])[:, None] * Zdots[l - 1]
+        dabar = net.W[l - 1].T @ dzbar
+    return dabar

@@ -1,0 +1,73 @@
+// Shared device helpers of libnnc: activations with their first and second derivatives,
+// BF16 hi/lo splitting, launch bookkeeping.  Used by every kernel file of the library.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+
+#include "../../include/nnc.h"
+
+namespace nnc {
+
+constexpr int kPad = 128;  // every packed dimension of weights and tangents is a multiple of this
+inline int pad_up(int v, int p = kPad) { return (v + p - 1) / p * p; }
+
+// Host-side launch counter (every kernel launch of the library goes through note_launch()).
+void note_launch(int n = 1);
+
+// sigma, sigma' and sigma'' of Eq. 3's activations, in FP64.  The derivatives follow from
+// the definitions: tanh' = 1 - t^2, tanh'' = -2 t (1 - t^2); sigmoid' = s (1 - s),
+// sigmoid'' = s (1 - s)(1 - 2 s); softplus' = sigmoid, softplus'' = sigmoid'; GELU(z) = z Phi(z),
+// GELU' = Phi(z) + z phi(z), GELU'' = phi(z) (2 - z^2).
+__device__ __forceinline__ void act_eval(int act, double z, double& a, double& d1, double& d2) {
+  switch (act) {
+    case NNC_TANH: {
+      double t = tanh(z);
+      a = t;
+      d1 = 1.0 - t * t;
+      d2 = -2.0 * t * d1;
+      break;
+    }
+    case NNC_SIGMOID: {
+      double s = 1.0 / (1.0 + exp(-z));
+      a = s;
+      d1 = s * (1.0 - s);
+      d2 = d1 * (1.0 - 2.0 * s);
+      break;
+    }
+    case NNC_SOFTPLUS: {
+      double s = 1.0 / (1.0 + exp(-z));
+      a = z > 0.0 ? z + log1p(exp(-z)) : log1p(exp(z));
+      d1 = s;
+      d2 = s * (1.0 - s);
+      break;
+    }
+    case NNC_GELU: {
+      const double kInvSqrt2 = 0.70710678118654752440;
+      const double kInvSqrt2Pi = 0.39894228040143267794;
+      double Phi = 0.5 * (1.0 + erf(z * kInvSqrt2));
+      double phi = kInvSqrt2Pi * exp(-0.5 * z * z);
+      a = z * Phi;
+      d1 = Phi + z * phi;
+      d2 = phi * (2.0 - z * z);
+      break;
+    }
+    default:
+      a = z;
+      d1 = 1.0;
+      d2 = 0.0;
+  }
+}
+
+// v ~ hi + lo with hi = bf16(v) and lo = bf16(v - hi): the split of the BF16x3 scheme
+// (Henry, Tang & Heinecke 2019).  hi carries 8 significant bits, hi + lo about 16.
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(v);
+  lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+__device__ __forceinline__ void split_bf16(double v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __double2bfloat16(v);
+  lo = __double2bfloat16(v - (double)__bfloat162float(hi));
+}
+
+}  // namespace nnc

@@ -1,0 +1,505 @@
+// tcgen05 / TMEM / TMA GEMMs of the BF16 and split-BF16x3 forms (sm_103a).
+//
+// One CTA computes a 128 x BN tile of D = A B^T (A: M x K, B: N x K, both K-major BF16):
+//   warp 0     : TMA producer. 2-D tensor copies (128-byte swizzle) of the A and B k-blocks
+//                (64 columns = 128 bytes) into a ring of shared-memory stages, each guarded by
+//                a "full" and an "empty" mbarrier.
+//   warp 1     : owns the tensor-memory allocation and issues tcgen05.mma (M = 128, N = BN,
+//                K = 16 per instruction) from one thread; in the split-BF16x3 form each K step
+//                issues Ahi*Bhi, Ahi*Blo and Alo*Bhi into the same FP32 accumulator.
+//                tcgen05.commit frees a stage when its MMAs have read it, and signals the
+//                epilogue after the last one.
+//   warps 2..5 : epilogue. Each warp reads its 32 TMEM lanes (= 32 rows of the tile) with
+//                tcgen05.ld and writes the fused outputs.
+// Every mbarrier wait is bounded: on expiry the CTA records an error code in *err, stops its
+// loops, waits (again bounded) for its own copies and MMAs in flight, frees its tensor memory
+// and returns.
+#include <cudaTypedefs.h>
+
+#include <cstdio>
+
+#include "kernels.cuh"
+#include "tc.cuh"
+
+namespace nnc {
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 64;
+constexpr int kThreads = 192;
+constexpr long long kWaitCycles = 4000000000LL;  // about two seconds at GB300 clocks
+
+struct TcArgs {
+  int M, N, K;
+  int ntm, ntn, nkb, kb_per_split;
+  const double* s1;
+  const float* c;
+  __nv_bfloat16 *at_hi, *at_lo, *zt_hi, *zt_lo, *yt_hi, *yt_lo;
+  int ldo;
+  float* Hp;
+  int* err;
+};
+
+template <int BN, bool X3>
+struct Cfg {
+  static constexpr int A_BYTES = BM * BK * 2;
+  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr int NPARTS = X3 ? 2 : 1;
+  static constexpr int STAGE_BYTES = NPARTS * (A_BYTES + B_BYTES);
+  static constexpr int TX_BYTES = STAGE_BYTES;
+  static constexpr int SMEM_BUDGET = 227 * 1024 - 2048;
+  static constexpr int STAGES_FIT = SMEM_BUDGET / STAGE_BYTES;
+  static constexpr int STAGES = STAGES_FIT > 6 ? 6 : STAGES_FIT;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+  static constexpr int TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+  // Instruction descriptor of tcgen05.mma kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
+  // (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17, M >> 4 at bit 24.
+  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
+                                    ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+  static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N for M = 128");
+  static_assert(B_BYTES % 1024 == 0, "stage parts must stay 1024-byte aligned");
+  static_assert(STAGES >= 2, "at least two stages");
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity.  Returns false if the CTA aborted or the
+// wait ran out (then the error word and the CTA's abort flag are set).
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, int* err, int code,
+                                          volatile int* abort_flag, long long limit = kWaitCycles) {
+  if (mbar_try(a, parity)) return true;
+  const long long t0 = clock64();
+  while (true) {
+    if (mbar_try(a, parity)) return true;
+    if (*abort_flag) return false;
+    if (clock64() - t0 > limit) {
+      atomicCAS(err, 0, code);
+      *abort_flag = 1;
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t mbar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(mbar), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of tcgen05 for a K-major tile written by TMA with 128-byte
+// swizzling: start address >> 4 (bits 0-13), stride between 8-row groups = 1024 bytes (>> 4 at
+// bit 32), descriptor version 1 (bit 46), layout SWIZZLE_128B (= 2 at bits 61-63).  Moving along
+// K inside the 128-byte row is done by advancing the start address (32 bytes per K = 16).
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
+         (2ull << 61);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t mbar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <bool X3>
+__device__ __forceinline__ void put(__nv_bfloat16* hi, __nv_bfloat16* lo, size_t o, float v) {
+  if (X3) {
+    __nv_bfloat16 h, l;
+    split_bf16(v, h, l);
+    hi[o] = h;
+    lo[o] = l;
+  } else {
+    hi[o] = __float2bfloat16_rn(v);
+  }
+}
+
+template <int BN, bool X3, int KIND>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
+              const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
+              const TcArgs args) {
+  using C = Cfg<BN, X3>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + C::STAGES * C::STAGE_BYTES);
+  uint64_t* empty = full + C::STAGES;
+  uint64_t* accf = empty + C::STAGES;
+  uint32_t* tmem_slot = (uint32_t*)(accf + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  volatile int* consumed_sh = (volatile int*)(tmem_slot + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int tm, tn, split;
+  if (KIND == TC_TANGENT) {
+    tn = blockIdx.x;
+    tm = blockIdx.y;
+    split = 0;
+  } else {
+    tn = blockIdx.x % args.ntn;
+    tm = blockIdx.x / args.ntn;
+    split = blockIdx.y;
+    if (tm * BM + BM - 1 < tn * BN) return;  // tile lies strictly above the diagonal
+  }
+  const int m0 = tm * BM, n0 = tn * BN;
+  const int kb0 = split * args.kb_per_split;
+  const int kb1 = min(args.nkb, kb0 + args.kb_per_split);
+  const int nk = kb1 - kb0;
+  if (nk <= 0) return;  // uniform over the CTA, before any barrier exists
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(accf), 1);
+    *abort_flag = 0;
+    *consumed_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(C::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  int issued = 0;  // producer only
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % C::STAGES;
+        const uint32_t ph = (uint32_t)(i / C::STAGES) & 1u;
+        if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1u, args.err, 1, abort_flag)) break;
+        uint8_t* st = smem + s * C::STAGE_BYTES;
+        const uint32_t fb = smem_u32(&full[s]);
+        mbar_expect_tx(fb, C::TX_BYTES);
+        const int kx = (kb0 + i) * BK;
+        tma_load_2d(smem_u32(st), &ta_hi, fb, kx, m0);
+        if (X3) tma_load_2d(smem_u32(st + C::A_BYTES), &ta_lo, fb, kx, m0);
+        tma_load_2d(smem_u32(st + C::NPARTS * C::A_BYTES), &tb_hi, fb, kx, n0);
+        if (X3) tma_load_2d(smem_u32(st + C::NPARTS * C::A_BYTES + C::B_BYTES), &tb_lo, fb, kx, n0);
+        issued = i + 1;
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int i = 0;
+      for (; i < nk; ++i) {
+        const int s = i % C::STAGES;
+        const uint32_t ph = (uint32_t)(i / C::STAGES) & 1u;
+        if (!mbar_wait(smem_u32(&full[s]), ph, args.err, 2, abort_flag)) break;
+        tc_fence_after();
+        const uint32_t st = smem_u32(smem + s * C::STAGE_BYTES);
+        const uint32_t a_hi = st, a_lo = st + C::A_BYTES;
+        const uint32_t b_hi = st + C::NPARTS * C::A_BYTES;
+        const uint32_t b_lo = b_hi + C::B_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint32_t off = kk * 32;
+          umma_bf16(tmem, sdesc(a_hi + off), sdesc(b_hi + off), C::IDESC, (i > 0 || kk > 0) ? 1u : 0u);
+          if (X3) {
+            umma_bf16(tmem, sdesc(a_hi + off), sdesc(b_lo + off), C::IDESC, 1u);
+            umma_bf16(tmem, sdesc(a_lo + off), sdesc(b_hi + off), C::IDESC, 1u);
+          }
+        }
+        umma_commit(smem_u32(&empty[s]));
+      }
+      *consumed_sh = i;
+      umma_commit(smem_u32(accf));  // arrives once every MMA issued above has completed
+    }
+  } else {
+    const int q = warp & 3;  // TMEM lanes 32q .. 32q+31 belong to this warp
+    const int row = q * 32 + lane;
+    const bool ok = mbar_wait(smem_u32(accf), 0, args.err, 3, abort_flag);
+    tc_fence_after();
+    if (ok) {
+      if (KIND == TC_TANGENT) {
+        const int m = m0 + row;
+        const float sm = (float)args.s1[m];
+        const float cm = args.c[m];
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+          float v[16];
+          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int n = n0 + c0 + j;
+            if (n < args.N) {
+              const size_t o = (size_t)n * args.ldo + m;
+              if (args.at_hi) put<X3>(args.at_hi, args.at_lo, o, sm * v[j]);
+              put<X3>(args.zt_hi, args.zt_lo, o, v[j]);
+              put<X3>(args.yt_hi, args.yt_lo, o, cm * v[j]);
+            }
+          }
+        }
+      } else {
+        const int i = m0 + row;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+          float v[16];
+          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+          if (i < args.N) {
+            float* hp = args.Hp + ((size_t)split * args.N + i) * args.N;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int n = n0 + c0 + j;
+              if (n <= i) hp[n] += v[j];
+            }
+          }
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (*abort_flag) {
+    // Drain: the producer waits for copies that the MMA warp never consumed, the MMA warp for
+    // its outstanding MMAs, both with a short bound, before the memory goes away.
+    if (warp == 0 && lane == 0) {
+      for (int i = *consumed_sh; i < issued; ++i) {
+        const int s = i % C::STAGES;
+        const uint32_t ph = (uint32_t)(i / C::STAGES) & 1u;
+        volatile int no_abort = 0;
+        mbar_wait(smem_u32(&full[s]), ph, args.err, 4, &no_abort, kWaitCycles / 8);
+      }
+    }
+    if (warp == 1 && lane == 0) {
+      volatile int no_abort = 0;
+      mbar_wait(smem_u32(accf), 0, args.err, 5, &no_abort, kWaitCycles / 8);
+    }
+    __syncthreads();
+  }
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(C::TMEM_COLS)
+                 : "memory");
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// 2-D BF16 map: inner extent `cols` (K, contiguous), outer extent `rows`, row stride ld
+// elements, box 64 x box_rows, 128-byte swizzle, zero fill outside.
+bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int ld, int box_rows) {
+  if (!base) {
+    memset(m, 0, sizeof(*m));
+    return true;
+  }
+  auto enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,
+                   box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int BN, bool X3, int KIND>
+cudaError_t launch_t(const TcPlan& p, const TcArgs& a, dim3 grid, cudaStream_t st) {
+  using C = Cfg<BN, X3>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<BN, X3, KIND>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_tc_gemm<BN, X3, KIND><<<grid, kThreads, C::SMEM, st>>>(p.ta_hi, p.ta_lo, p.tb_hi, p.tb_lo, a);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <int KIND>
+cudaError_t launch_any(const TcPlan& p, const TcArgs& a, dim3 grid, cudaStream_t st) {
+  const bool x3 = p.x3 != 0;
+  switch (p.bn) {
+    case 112: return x3 ? launch_t<112, true, KIND>(p, a, grid, st) : launch_t<112, false, KIND>(p, a, grid, st);
+    case 128: return x3 ? launch_t<128, true, KIND>(p, a, grid, st) : launch_t<128, false, KIND>(p, a, grid, st);
+    case 208: return x3 ? launch_t<208, true, KIND>(p, a, grid, st) : launch_t<208, false, KIND>(p, a, grid, st);
+    case 256: return x3 ? launch_t<256, true, KIND>(p, a, grid, st) : launch_t<256, false, KIND>(p, a, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int count_lower_tiles(int ntm, int ntn, int bn) {
+  int t = 0;
+  for (int tm = 0; tm < ntm; ++tm)
+    for (int tn = 0; tn < ntn; ++tn)
+      if (tm * BM + BM - 1 >= tn * bn) ++t;
+  return t;
+}
+
+}  // namespace
+
+int tc_plan_make(TcPlan& p, int kind, int prec, const void* a_hi, const void* a_lo, int a_rows,
+                 int ld_a, const void* b_hi, const void* b_lo, int b_rows, int ld_b, int M, int N,
+                 int K, int sm_count, int force_bn, int force_splits) {
+  p = TcPlan();
+  p.kind = kind;
+  p.x3 = prec == NNC_BF16X3 ? 1 : 0;
+  p.M = M;
+  p.N = N;
+  p.K = K;
+  if (K % BK != 0 || K <= 0 || N <= 0 || M <= 0) return NNC_ERR_ARG;
+  if (kind == TC_TANGENT && M % BM != 0) return NNC_ERR_ARG;
+  const int nkb = K / BK;
+  if (kind == TC_TANGENT) {
+    int best_bn = 208;
+    double best = 1e30;
+    const int cands[4] = {256, 208, 128, 112};
+    const int ntm = M / BM;
+    for (int bn : cands) {
+      const int ntn = (N + bn - 1) / bn;
+      const int ctas = ntm * ntn;
+      const int waves = (ctas + sm_count - 1) / sm_count;
+      const double cost = (double)waves * (bn + 24);
+      if (cost < best - 1e-9) {
+        best = cost;
+        best_bn = bn;
+      }
+    }
+    p.bn = force_bn ? force_bn : best_bn;
+    p.ntm = ntm;
+    p.ntn = (N + p.bn - 1) / p.bn;
+    p.splits = 1;
+    p.kb_per_split = nkb;
+  } else {
+    p.bn = force_bn ? force_bn : 128;
+    p.ntm = (N + BM - 1) / BM;
+    p.ntn = (N + p.bn - 1) / p.bn;
+    const int tiles = count_lower_tiles(p.ntm, p.ntn, p.bn);
+    int splits = force_splits ? force_splits : (sm_count + tiles / 2) / tiles;
+    splits = splits < 1 ? 1 : splits > nkb ? nkb : splits;
+    p.kb_per_split = (nkb + splits - 1) / splits;
+    p.splits = (nkb + p.kb_per_split - 1) / p.kb_per_split;
+  }
+  const int a_box = BM;
+  const int b_box = p.bn;
+  if (!make_map(&p.ta_hi, a_hi, a_rows, K, ld_a, a_box)) return NNC_ERR_CUDA;
+  if (!make_map(&p.ta_lo, p.x3 ? a_lo : nullptr, a_rows, K, ld_a, a_box)) return NNC_ERR_CUDA;
+  if (!make_map(&p.tb_hi, b_hi, b_rows, K, ld_b, b_box)) return NNC_ERR_CUDA;
+  if (!make_map(&p.tb_lo, p.x3 ? b_lo : nullptr, b_rows, K, ld_b, b_box)) return NNC_ERR_CUDA;
+  p.ready = true;
+  return NNC_OK;
+}
+
+cudaError_t tc_tangent(const TcPlan& p, const double* s1, const float* c, void* at_hi, void* at_lo,
+                       void* zt_hi, void* zt_lo, void* yt_hi, void* yt_lo, int ldo, int* err,
+                       cudaStream_t st) {
+  if (!p.ready || p.kind != TC_TANGENT) return cudaErrorInvalidValue;
+  TcArgs a{};
+  a.M = p.M;
+  a.N = p.N;
+  a.K = p.K;
+  a.ntm = p.ntm;
+  a.ntn = p.ntn;
+  a.nkb = p.K / BK;
+  a.kb_per_split = p.kb_per_split;
+  a.s1 = s1;
+  a.c = c;
+  a.at_hi = (__nv_bfloat16*)at_hi;
+  a.at_lo = (__nv_bfloat16*)at_lo;
+  a.zt_hi = (__nv_bfloat16*)zt_hi;
+  a.zt_lo = (__nv_bfloat16*)zt_lo;
+  a.yt_hi = (__nv_bfloat16*)yt_hi;
+  a.yt_lo = (__nv_bfloat16*)yt_lo;
+  a.ldo = ldo;
+  a.err = err;
+  return launch_any<TC_TANGENT>(p, a, dim3(p.ntn, p.ntm, 1), st);
+}
+
+cudaError_t tc_syrk(const TcPlan& p, float* Hp, int* err, cudaStream_t st) {
+  if (!p.ready || p.kind != TC_SYRK) return cudaErrorInvalidValue;
+  TcArgs a{};
+  a.M = p.M;
+  a.N = p.N;
+  a.K = p.K;
+  a.ntm = p.ntm;
+  a.ntn = p.ntn;
+  a.nkb = p.K / BK;
+  a.kb_per_split = p.kb_per_split;
+  a.Hp = Hp;
+  a.err = err;
+  return launch_any<TC_SYRK>(p, a, dim3(p.ntm * p.ntn, p.splits, 1), st);
+}
+
+}  // namespace nnc

@@ -1,0 +1,383 @@
+// Bandwidth-bound kernels of libnnc: the forward value pass (Eq. 3), the reverse sweep with
+// n_out (+1) seed columns that gives the Jacobian and the adjoints, the first-layer tangents,
+// and the small reductions around them.  All read weights once, coalesced and vectorised.
+#include <type_traits>
+
+#include "kernels.cuh"
+
+namespace nnc {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ------------------------------------------------------------------ forward value pass
+// One warp per output row.  FP32 weights are multiplied in FP32 with four independent
+// partial sums per lane (32 terms each for k = 4096), which are summed in FP64.
+template <typename TW>
+__global__ void __launch_bounds__(256) k_gemv_fwd(const TW* __restrict__ W, int ldw,
+                                                  const double* __restrict__ bias,
+                                                  const double* __restrict__ a_in, int m, int k,
+                                                  int act, double* __restrict__ a_out,
+                                                  double* __restrict__ s1, double* __restrict__ s2) {
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= m) return;
+  double acc;
+  if constexpr (std::is_same<TW, float>::value) {
+    const float4* r4 = reinterpret_cast<const float4*>(W + (size_t)row * ldw);
+    const int nk4 = (k + 3) >> 2;
+    float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#pragma unroll 4
+    for (int j = lane; j < nk4; j += 32) {
+      const float4 w = __ldg(r4 + j);
+      const double2 a01 = *reinterpret_cast<const double2*>(a_in + 4 * j);
+      const double2 a23 = *reinterpret_cast<const double2*>(a_in + 4 * j + 2);
+      p0 = fmaf(w.x, (float)a01.x, p0);
+      p1 = fmaf(w.y, (float)a01.y, p1);
+      p2 = fmaf(w.z, (float)a23.x, p2);
+      p3 = fmaf(w.w, (float)a23.y, p3);
+    }
+    acc = ((double)p0 + (double)p1) + ((double)p2 + (double)p3);
+  } else {
+    const double2* r2 = reinterpret_cast<const double2*>(W + (size_t)row * ldw);
+    const int nk2 = (k + 1) >> 1;
+    double q0 = 0.0, q1 = 0.0;
+#pragma unroll 4
+    for (int j = lane; j < nk2; j += 32) {
+      const double2 w = __ldg(r2 + j);
+      const double2 a = *reinterpret_cast<const double2*>(a_in + 2 * j);
+      q0 = fma(w.x, a.x, q0);
+      q1 = fma(w.y, a.y, q1);
+    }
+    acc = q0 + q1;
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) {
+    const double z = acc + (bias ? bias[row] : 0.0);
+    double a, d1, d2;
+    act_eval(act, z, a, d1, d2);
+    a_out[row] = a;
+    if (s1) s1[row] = d1;
+    if (s2) s2[row] = d2;
+  }
+}
+
+cudaError_t launch_gemv_fwd(bool fp64, const void* W, int ldw, const double* b, const double* a_in,
+                            int m, int k, int act, double* a_out, double* s1, double* s2,
+                            cudaStream_t st) {
+  const int threads = 256;
+  const int blocks = (m * 32 + threads - 1) / threads;
+  if (fp64)
+    k_gemv_fwd<double><<<blocks, threads, 0, st>>>((const double*)W, ldw, b, a_in, m, k, act, a_out,
+                                                   s1, s2);
+  else
+    k_gemv_fwd<float><<<blocks, threads, 0, st>>>((const float*)W, ldw, b, a_in, m, k, act, a_out,
+                                                  s1, s2);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ reverse sweep
+// part[c][kk][s] = sum_{r in chunk c} W[r][kk] * Zbar[r][s]: the transposed product W^T Zbar of
+// one reverse step, split over row chunks so that the grid fills the GPU; a thread owns two
+// adjacent columns kk and all S seeds.  FP32 weights run in FP32 (seeds rounded to FP32,
+// partial sums over one chunk in FP32), FP64 weights in FP64.
+constexpr int kRevCols = 256;   // columns per block (128 threads x 2)
+constexpr int kRevRows = 64;    // rows per chunk staged at once in shared memory
+
+template <typename TW, int SMAX>
+__global__ void __launch_bounds__(128) k_gemv_rev(const TW* __restrict__ W, int ldw, int m,
+                                                  int kcols, const double* __restrict__ Zbar,
+                                                  int S, int rows_per_chunk,
+                                                  double* __restrict__ part) {
+  using TA = typename std::conditional<std::is_same<TW, float>::value, float, double>::type;
+  __shared__ TA zs[kRevRows][SMAX];
+  const int c0 = blockIdx.x * kRevCols + 2 * threadIdx.x;
+  const int rbeg = blockIdx.y * rows_per_chunk;
+  const int rend = min(m, rbeg + rows_per_chunk);
+  TA acc0[SMAX], acc1[SMAX];
+#pragma unroll
+  for (int s = 0; s < SMAX; ++s) acc0[s] = acc1[s] = TA(0);
+  const bool active = c0 < kcols;  // kcols is even (padded), so c0 + 1 < kcols too
+  for (int r0 = rbeg; r0 < rend; r0 += kRevRows) {
+    const int nr = min(kRevRows, rend - r0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nr * SMAX; i += blockDim.x) {
+      const int r = i / SMAX, s = i % SMAX;
+      zs[r][s] = s < S ? (TA)Zbar[(size_t)(r0 + r) * S + s] : TA(0);
+    }
+    __syncthreads();
+    if (active) {
+      const TW* wp = W + (size_t)r0 * ldw + c0;
+#pragma unroll 4
+      for (int r = 0; r < nr; ++r) {
+        TA w0, w1;
+        if constexpr (std::is_same<TW, float>::value) {
+          const float2 w = __ldg(reinterpret_cast<const float2*>(wp + (size_t)r * ldw));
+          w0 = w.x;
+          w1 = w.y;
+        } else {
+          const double2 w = __ldg(reinterpret_cast<const double2*>(wp + (size_t)r * ldw));
+          w0 = w.x;
+          w1 = w.y;
+        }
+#pragma unroll
+        for (int s = 0; s < SMAX; ++s) {
+          acc0[s] += w0 * zs[r][s];
+          acc1[s] += w1 * zs[r][s];
+        }
+      }
+    }
+  }
+  if (active) {
+    double* out = part + ((size_t)blockIdx.y * kcols + c0) * S;
+#pragma unroll
+    for (int s = 0; s < SMAX; ++s)
+      if (s < S) {
+        out[s] = (double)acc0[s];
+        out[S + s] = (double)acc1[s];
+      }
+  }
+}
+
+int rev_chunks(int m, int kcols, int sm_count) {
+  const int col_blocks = (kcols + kRevCols - 1) / kRevCols;
+  int chunks = (2 * sm_count + col_blocks - 1) / col_blocks;  // about two waves of blocks
+  chunks = chunks < 1 ? 1 : chunks;
+  const int max_chunks = (m + 15) / 16;                   // at least 16 rows per chunk
+  return chunks > max_chunks ? max_chunks : chunks;
+}
+
+template <typename TW>
+static void rev_dispatch(const TW* W, int ldw, int m, int kcols, const double* Zbar, int S,
+                         int chunks, double* part, cudaStream_t st) {
+  const int rows_per_chunk = (m + chunks - 1) / chunks;
+  dim3 grid((kcols + kRevCols - 1) / kRevCols, chunks);
+  if (S <= 1)
+    k_gemv_rev<TW, 1><<<grid, 128, 0, st>>>(W, ldw, m, kcols, Zbar, S, rows_per_chunk, part);
+  else if (S <= 4)
+    k_gemv_rev<TW, 4><<<grid, 128, 0, st>>>(W, ldw, m, kcols, Zbar, S, rows_per_chunk, part);
+  else if (S <= 12)
+    k_gemv_rev<TW, 12><<<grid, 128, 0, st>>>(W, ldw, m, kcols, Zbar, S, rows_per_chunk, part);
+  else if (S <= 24)
+    k_gemv_rev<TW, 24><<<grid, 128, 0, st>>>(W, ldw, m, kcols, Zbar, S, rows_per_chunk, part);
+  else
+    k_gemv_rev<TW, 48><<<grid, 128, 0, st>>>(W, ldw, m, kcols, Zbar, S, rows_per_chunk, part);
+}
+
+cudaError_t launch_gemv_rev(bool fp64, const void* W, int ldw, int m, int kcols, const double* Zbar,
+                            int S, int chunks, double* part, cudaStream_t st) {
+  if (S > 48) return cudaErrorInvalidValue;
+  if (fp64)
+    rev_dispatch<double>((const double*)W, ldw, m, kcols, Zbar, S, chunks, part, st);
+  else
+    rev_dispatch<float>((const float*)W, ldw, m, kcols, Zbar, S, chunks, part, st);
+  note_launch();
+  return cudaGetLastError();
+}
+
+__global__ void k_rev_reduce(const double* __restrict__ part, int chunks, int kcols, int kvalid,
+                             int S, const double* __restrict__ s1, const double* __restrict__ s2,
+                             int lam_col, int nJ, double* __restrict__ Zbar_out,
+                             double* __restrict__ c_out, float* __restrict__ c_out_f,
+                             double* __restrict__ J_out, double* __restrict__ g_out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= kcols * S) return;
+  const int kk = idx / S, s = idx % S;
+  double v = 0.0;
+  for (int c = 0; c < chunks; ++c) v += part[((size_t)c * kcols + kk) * S + s];
+  if (Zbar_out) Zbar_out[idx] = s1 ? s1[kk] * v : v;
+  if (s == lam_col) {
+    if (c_out) c_out[kk] = s2[kk] * v;
+    if (c_out_f) c_out_f[kk] = (float)(s2[kk] * v);
+    if (g_out && kk < kvalid) g_out[kk] = v;
+  }
+  if (J_out && s < nJ && kk < kvalid) J_out[(size_t)s * kvalid + kk] = v;
+}
+
+cudaError_t launch_rev_reduce(const double* part, int chunks, int kcols, int kvalid, int S,
+                              const double* s1, const double* s2, int lam_col, int nJ,
+                              double* Zbar_out, double* c_out, float* c_out_f, double* J_out,
+                              double* g_out, cudaStream_t st) {
+  const int total = kcols * S;
+  k_rev_reduce<<<(total + 255) / 256, 256, 0, st>>>(part, chunks, kcols, kvalid, S, s1, s2, lam_col,
+                                                    nJ, Zbar_out, c_out, c_out_f, J_out, g_out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// Seeds at the output layer: abar_L = e_s for the Jacobian columns s < nJ and abar_L = lambda
+// for column lam_col; zbar_L = sigma_L' * abar_L, and c_L = sigma_L'' * lambda.
+__global__ void k_rev_seed(int m, int S, int nJ, int lam_col, const double* __restrict__ s1,
+                           const double* __restrict__ s2, const double* __restrict__ lam,
+                           double* __restrict__ Zbar, double* __restrict__ c_out,
+                           float* __restrict__ c_out_f) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * S) return;
+  const int i = idx / S, s = idx % S;
+  double ab = 0.0;
+  if (s == lam_col) ab = lam[i];
+  else if (s < nJ) ab = (s == i) ? 1.0 : 0.0;
+  Zbar[idx] = s1[i] * ab;
+  if (s == lam_col) {
+    if (c_out) c_out[i] = s2[i] * ab;
+    if (c_out_f) c_out_f[i] = (float)(s2[i] * ab);
+  }
+}
+
+cudaError_t launch_rev_seed(int m, int S, int nJ, int lam_col, const double* s1, const double* s2,
+                            const double* lam, double* Zbar, double* c_out, float* c_out_f,
+                            cudaStream_t st) {
+  const int total = m * S;
+  k_rev_seed<<<(total + 255) / 256, 256, 0, st>>>(m, S, nJ, lam_col, s1, s2, lam, Zbar, c_out,
+                                                  c_out_f);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ first-layer tangents
+// Zdot_1 = W_1 I = W_1, so the tangents of layer 1 are a scaled transpose of W_1.  32 x 32
+// tiles through shared memory keep both the read (along n) and the write (along m) coalesced.
+template <Elem E>
+__device__ __forceinline__ void put_tan(TanBuf b, size_t i, double v) {
+  if constexpr (E == Elem::F64) {
+    ((double*)b.hi)[i] = v;
+  } else if constexpr (E == Elem::F32) {
+    ((float*)b.hi)[i] = (float)v;
+  } else if constexpr (E == Elem::BF16) {
+    ((__nv_bfloat16*)b.hi)[i] = __double2bfloat16(v);
+  } else {
+    __nv_bfloat16 h, l;
+    split_bf16(v, h, l);
+    ((__nv_bfloat16*)b.hi)[i] = h;
+    ((__nv_bfloat16*)b.lo)[i] = l;
+  }
+}
+
+template <Elem E>
+__global__ void k_first_tangent(const double* __restrict__ W1, int ldw, int m_pad, int n,
+                                const double* __restrict__ s1, const double* __restrict__ c,
+                                TanBuf At, TanBuf Zt, TanBuf Yt, int ld_out) {
+  __shared__ double tile[32][33];
+  const int m0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int mm = m0 + r, nn = n0 + threadIdx.x;
+    tile[r][threadIdx.x] = (mm < m_pad && nn < n) ? W1[(size_t)mm * ldw + nn] : 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int nn = n0 + r, mm = m0 + threadIdx.x;
+    if (nn < n && mm < m_pad) {
+      const double w = tile[threadIdx.x][r];
+      const size_t o = (size_t)nn * ld_out + mm;
+      if (At.hi) put_tan<E>(At, o, s1[mm] * w);
+      put_tan<E>(Zt, o, w);
+      put_tan<E>(Yt, o, c[mm] * w);
+    }
+  }
+}
+
+cudaError_t launch_first_tangent(Elem e, const double* W1, int ldw, int m_pad, int n,
+                                 const double* s1, const double* c, TanBuf At, TanBuf Zt,
+                                 TanBuf Yt, int ld_out, cudaStream_t st) {
+  dim3 grid((n + 31) / 32, (m_pad + 31) / 32), block(32, 8);
+  switch (e) {
+    case Elem::F64:
+      k_first_tangent<Elem::F64><<<grid, block, 0, st>>>(W1, ldw, m_pad, n, s1, c, At, Zt, Yt, ld_out);
+      break;
+    case Elem::F32:
+      k_first_tangent<Elem::F32><<<grid, block, 0, st>>>(W1, ldw, m_pad, n, s1, c, At, Zt, Yt, ld_out);
+      break;
+    case Elem::BF16:
+      k_first_tangent<Elem::BF16><<<grid, block, 0, st>>>(W1, ldw, m_pad, n, s1, c, At, Zt, Yt, ld_out);
+      break;
+    case Elem::BF16X3:
+      k_first_tangent<Elem::BF16X3><<<grid, block, 0, st>>>(W1, ldw, m_pad, n, s1, c, At, Zt, Yt,
+                                                            ld_out);
+      break;
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ Hessian finish
+template <typename TP>
+__global__ void k_h_finish(const TP* __restrict__ Hp, int splits, int n, int ldp,
+                           double* __restrict__ H) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (j >= n) return;
+  const int r = i > j ? i : j, c = i > j ? j : i;
+  double v = 0.0;
+  for (int s = 0; s < splits; ++s) v += (double)Hp[((size_t)s * n + r) * ldp + c];
+  H[(size_t)i * n + j] = v;
+}
+
+cudaError_t launch_h_finish(bool part_f32, const void* Hp, int splits, int n, int ldp, double* H,
+                            cudaStream_t st) {
+  dim3 grid((n + 127) / 128, n);
+  if (part_f32)
+    k_h_finish<float><<<grid, 128, 0, st>>>((const float*)Hp, splits, n, ldp, H);
+  else
+    k_h_finish<double><<<grid, 128, 0, st>>>((const double*)Hp, splits, n, ldp, H);
+  note_launch();
+  return cudaGetLastError();
+}
+
+__global__ void k_sub(const double* y, const double* a, double* r, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) r[i] = y[i] - a[i];
+}
+
+cudaError_t launch_sub(const double* y, const double* a, double* r, int n, cudaStream_t st) {
+  k_sub<<<(n + 255) / 256, 256, 0, st>>>(y, a, r, n);
+  note_launch();
+  return cudaGetLastError();
+}
+
+__global__ void k_copy_pad(const double* src, double* dst, int n, int n_pad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_pad) dst[i] = i < n ? src[i] : 0.0;
+}
+
+cudaError_t launch_copy_pad(const double* src, double* dst, int n, int n_pad, cudaStream_t st) {
+  k_copy_pad<<<(n_pad + 255) / 256, 256, 0, st>>>(src, dst, n, n_pad);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace nnc
+
+namespace nnc {
+
+// ------------------------------------------------------------------ weight packing
+// From the padded FP64 master copy: FP32 copy, and the BF16 split hi = bf16(w),
+// lo = bf16(w - hi) used by the tensor-core forms.
+__global__ void k_pack(const double* __restrict__ w64, size_t n, float* __restrict__ w32,
+                       __nv_bfloat16* __restrict__ whi, __nv_bfloat16* __restrict__ wlo) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const double w = w64[i];
+    if (w32) w32[i] = (float)w;
+    if (whi) {
+      __nv_bfloat16 h, l;
+      split_bf16(w, h, l);
+      whi[i] = h;
+      if (wlo) wlo[i] = l;
+    }
+  }
+}
+
+cudaError_t launch_pack(const double* w64, size_t n, float* w32, __nv_bfloat16* whi,
+                        __nv_bfloat16* wlo, cudaStream_t st) {
+  size_t blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  k_pack<<<(unsigned)blocks, 256, 0, st>>>(w64, n, w32, whi, wlo);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace nnc

@@ -1,0 +1,64 @@
+// Launch wrappers of libnnc's kernels (host side).  Every wrapper queues work on `st` and
+// returns the cudaError_t of the launch.
+#pragma once
+#include "common.cuh"
+
+namespace nnc {
+
+// Where a tangent-sweep epilogue writes one n x m tile set (row stride `ld`, in elements).
+// For FP64/FP32 forms only `hi` is used (element type double/float); for BF16 forms hi and
+// lo are __nv_bfloat16 arrays holding the split value (lo is ignored by single-pass BF16).
+struct TanBuf {
+  void* hi = nullptr;
+  void* lo = nullptr;
+};
+
+enum class Elem { F64, F32, BF16, BF16X3 };
+
+// ---- vector kernels (k_vector.cu)
+// Forward layer: z = W a_in + b, a_out = sigma(z), s1 = sigma'(z), s2 = sigma''(z).
+cudaError_t launch_gemv_fwd(bool fp64, const void* W, int ldw, const double* b, const double* a_in,
+                            int m, int k, int act, double* a_out, double* s1, double* s2,
+                            cudaStream_t st);
+// Reverse layer with S seed columns: part[c][kk][s] = sum over row chunk c of W[r][kk] Zbar[r][s].
+cudaError_t launch_gemv_rev(bool fp64, const void* W, int ldw, int m, int kcols, const double* Zbar,
+                            int S, int chunks, double* part, cudaStream_t st);
+int rev_chunks(int m, int kcols, int sm_count);
+// Sum the chunks; then Zbar_out = s1 * Abar (if s1), c_out = s2 * Abar[:, lam_col] (if c_out),
+// J_out[s][kk] = Abar[kk][s] for s < nJ (if J_out), g_out[kk] = Abar[kk][lam_col] (if g_out).
+cudaError_t launch_rev_reduce(const double* part, int chunks, int kcols, int kvalid, int S,
+                              const double* s1, const double* s2, int lam_col, int nJ,
+                              double* Zbar_out, double* c_out, float* c_out_f, double* J_out,
+                              double* g_out, cudaStream_t st);
+// Seeds of the reverse sweep at the output layer (see k_vector.cu).
+cudaError_t launch_rev_seed(int m, int S, int nJ, int lam_col, const double* s1, const double* s2,
+                            const double* lam, double* Zbar, double* c_out, float* c_out_f,
+                            cudaStream_t st);
+// First-layer tangents: Zdot_1 = W_1, so At[n][m] = s1[m] W1[m][n], Zt = W1^T, Yt = c[m] W1[m][n].
+cudaError_t launch_first_tangent(Elem e, const double* W1, int ldw, int m_pad, int n,
+                                 const double* s1, const double* c, TanBuf At, TanBuf Zt,
+                                 TanBuf Yt, int ld_out, cudaStream_t st);
+// H[i][j] = sum_s Hp[s][max(i,j)][min(i,j)]  (exactly symmetric); Hp is double or float.
+cudaError_t launch_h_finish(bool part_f32, const void* Hp, int splits, int n, int ldp, double* H,
+                            cudaStream_t st);
+// r = y - a  (FP64)
+cudaError_t launch_sub(const double* y, const double* a, double* r, int n, cudaStream_t st);
+// dst[i] = src[i] (double) for i < n; zero for n <= i < n_pad
+cudaError_t launch_copy_pad(const double* src, double* dst, int n, int n_pad, cudaStream_t st);
+
+// ---- CUDA-core GEMMs for the FP64 / FP32 forms (k_simt.cu)
+// D[m][n] = sum_k A[m][k] B[n][k] (both K-major).
+// Tangent epilogue: At[n][m] = s1[m] D, Zt[n][m] = D, Yt[n][m] = c[m] D  (n < N).
+cudaError_t launch_simt_tangent(bool fp64, const void* A, int lda, const void* B, int ldb, int M,
+                                int N, int K, const double* s1, const double* c, void* At,
+                                void* Zt, void* Yt, int ldo, cudaStream_t st);
+// Symmetric-product epilogue: Hp[s][i][j] += D over the lower-triangle tiles, split-K `splits`.
+cudaError_t launch_simt_syrk(bool fp64, const void* Zt, const void* Yt, int ld, int n, int K,
+                             int splits, double* Hp, cudaStream_t st);
+
+}  // namespace nnc
+
+namespace nnc {
+cudaError_t launch_pack(const double* w64, size_t n, float* w32, __nv_bfloat16* whi,
+                        __nv_bfloat16* wlo, cudaStream_t st);
+}  // namespace nnc

@@ -1,0 +1,688 @@
+// C ABI of libnnc (declared in include/nnc.h) and the host runtime behind it: the net object,
+// weight packing, device workspaces and the order in which one oracle call runs its kernels.
+//
+// One interior-point iteration (Eq. 2) needs, at the same x:
+//   forward value pass  z_l = W_l a_{l-1} + b_l, a_l = sigma_l(z_l)            (Eq. 3)
+//   reverse sweep       abar_L = seeds, abar_{l-1} = W_l^T (sigma_l' * abar_l)  (Jacobian, adjoint)
+//   tangent sweep       Zdot_1 = W_1, Zdot_l = W_l (sigma_{l-1}' * Zdot_{l-1})  (n_in tangents)
+//   Hessian of lambda^T NN (Eq. 6) as  H = sum_l Zdot_l^T diag(sigma_l'' * abar_l) Zdot_l,
+// which is what forward-over-reverse differentiation of lambda^T NN reduces to once the
+// reverse tangents of the affine maps are unrolled.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "tc.cuh"
+
+namespace nnc {
+static std::atomic<long long> g_launches{0};
+void note_launch(int n) { g_launches += n; }
+static thread_local std::string g_err;
+static int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+}  // namespace nnc
+
+using namespace nnc;
+
+struct LayerDev {
+  int m = 0, k = 0, act = 0, mp = 0, kp = 0;
+  double* W64 = nullptr;          // [mp][kp], zero padded
+  float* W32 = nullptr;           // [mp][kp]
+  __nv_bfloat16* Whi = nullptr;   // [mp][kp]
+  __nv_bfloat16* Wlo = nullptr;   // [mp][kp]
+  double* b = nullptr;            // [mp]
+  double* a = nullptr;            // a_l [mp]
+  double* s1 = nullptr;           // sigma_l'(z_l) [mp]
+  double* s2 = nullptr;           // sigma_l''(z_l) [mp]
+  double* c = nullptr;            // sigma_l''(z_l) * abar_l [mp]
+  float* c_f = nullptr;           // FP32 copy of c for the tensor-core epilogue
+  double* ra = nullptr;           // FP64-residual pass activations [mp]
+  TcPlan plan_tan;                // tensor-core plan of this layer's tangent GEMM
+  TcPlan plan_syrk;               // tensor-core plan of this layer's symmetric product
+};
+
+struct nnc_net {
+  int L = 0, n_in = 0, n_out = 0, prec = 0, n_in_pad = 0, mp_max = 0, S_max = 0;
+  std::vector<LayerDev> layers;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0, sm_count = 0;
+  std::vector<void*> allocs;
+  double* x = nullptr;       // a_0 [n_in_pad]
+  double* xin = nullptr;     // host-call staging of x [n_in_pad]
+  double* lam = nullptr;     // [n_out]
+  double* ydev = nullptr;    // [n_out] staging
+  double* rdev = nullptr;    // [n_out]
+  double* Zbar[2] = {nullptr, nullptr};
+  double* part = nullptr;
+  double* Jdev = nullptr;    // [n_out][n_in]
+  double* gdev = nullptr;    // [n_in]
+  double* Hdev = nullptr;    // [n_in][n_in]
+  void* At[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [ping-pong][hi, lo]
+  void* Zt[2] = {nullptr, nullptr};
+  void* Yt[2] = {nullptr, nullptr};
+  void* Hp = nullptr;        // split partial sums of H (double for CUDA-core forms, float for TC)
+  int h_splits = 1;
+  bool hp_f32 = false;
+  int* dev_err = nullptr;    // device error word of bounded waits
+  double* h_stage = nullptr; // pinned host staging
+  size_t h_stage_elems = 0;
+  size_t bytes = 0;
+  // optional per-kernel-kind CUDA-event timing (nnc_profile)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<int> ev_kind;
+};
+
+namespace {
+
+bool is_tc(int prec) { return prec == NNC_BF16 || prec == NNC_BF16X3 || prec == NNC_FP8; }
+
+Elem tan_elem(int prec) {
+  switch (prec) {
+    case NNC_FP64: return Elem::F64;
+    case NNC_FP32: return Elem::F32;
+    case NNC_BF16: return Elem::BF16;
+    default: return Elem::BF16X3;
+  }
+}
+
+size_t elem_size(int prec) { return prec == NNC_FP64 ? 8 : prec == NNC_FP32 ? 4 : 2; }
+
+#define CK(expr)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (expr);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(e_ == cudaErrorMemoryAllocation ? NNC_ERR_OOM : NNC_ERR_CUDA,         \
+                  std::string(#expr) + ": " + cudaGetErrorString(e_));                  \
+  } while (0)
+
+template <typename T>
+int dalloc(nnc_net* net, T** p, size_t n) {
+  void* q = nullptr;
+  const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess)
+    return fail(NNC_ERR_OOM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " +
+                                 cudaGetErrorString(e));
+  e = cudaMemsetAsync(q, 0, bytes, net->stream);
+  if (e != cudaSuccess) return fail(NNC_ERR_CUDA, cudaGetErrorString(e));
+  net->allocs.push_back(q);
+  net->bytes += bytes;
+  *p = (T*)q;
+  return NNC_OK;
+}
+
+#define AL(p, n)                                    \
+  do {                                              \
+    int r_ = dalloc(net, &(p), (n));                \
+    if (r_ != NNC_OK) return r_;                    \
+  } while (0)
+
+int check_finite(const double* v, int n, const char* what) {
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) return fail(NNC_ERR_NONFINITE, std::string(what) + " holds NaN or Inf");
+  return NNC_OK;
+}
+
+int check_dev_err(nnc_net* net) {
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, net->dev_err, sizeof(int), cudaMemcpyDeviceToHost, net->stream));
+  CK(cudaStreamSynchronize(net->stream));
+  if (e != 0) {
+    int z = 0;
+    cudaMemcpy(net->dev_err, &z, sizeof(int), cudaMemcpyHostToDevice);
+    return fail(NNC_ERR_TIMEOUT, "a bounded device-side wait ran out (code " + std::to_string(e) + ")");
+  }
+  return NNC_OK;
+}
+
+cudaStream_t pick(nnc_net* net, void* st) { return st ? (cudaStream_t)st : net->stream; }
+
+// Kernel kinds of nnc_profile_read.
+enum { PK_TANGENT = 0, PK_SYRK = 1, PK_FWD = 2, PK_REV = 3, PK_OTHER = 4, PK_N = 5 };
+
+// Brackets one launch with a pair of events on its stream when profiling is on.
+struct ProfScope {
+  nnc_net* net;
+  cudaStream_t st;
+  bool on;
+  size_t idx = 0;
+  ProfScope(nnc_net* n, int kind, cudaStream_t s) : net(n), st(s), on(n->prof) {
+    if (!on) return;
+    while (net->ev_used + 2 > net->ev_pool.size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        on = false;
+        return;
+      }
+      net->ev_pool.push_back(e);
+    }
+    idx = net->ev_used;
+    net->ev_used += 2;
+    net->ev_kind.push_back(kind);
+    cudaEventRecord(net->ev_pool[idx], st);
+  }
+  ~ProfScope() {
+    if (on) cudaEventRecord(net->ev_pool[idx + 1], st);
+  }
+};
+#define PROF(kind) ProfScope prof_scope_(net, kind, st)
+
+// ---------------------------------------------------------------- forward value pass
+int run_forward(nnc_net* net, bool fp64, cudaStream_t st) {
+  const double* a_in = net->x;
+  for (auto& Ly : net->layers) {
+    PROF(PK_FWD);
+    CK(launch_gemv_fwd(fp64, fp64 ? (const void*)Ly.W64 : (const void*)Ly.W32, Ly.kp, Ly.b, a_in,
+                       Ly.m, Ly.kp, Ly.act, Ly.a, Ly.s1, Ly.s2, st));
+    a_in = Ly.a;
+  }
+  return NNC_OK;
+}
+
+int run_forward_fp64_values(nnc_net* net, cudaStream_t st) {
+  const double* a_in = net->x;
+  for (auto& Ly : net->layers) {
+    PROF(PK_FWD);
+    CK(launch_gemv_fwd(true, Ly.W64, Ly.kp, Ly.b, a_in, Ly.m, Ly.kp, Ly.act, Ly.ra, nullptr,
+                       nullptr, st));
+    a_in = Ly.ra;
+  }
+  return NNC_OK;
+}
+
+// ---------------------------------------------------------------- reverse sweep
+// nJ Jacobian seeds (0 or n_out) and, if with_lam, one more seed column carrying lambda whose
+// adjoints give c_l = sigma_l'' * abar_l for the Hessian and the gradient lambda^T J.
+int run_reverse(nnc_net* net, bool fp64, int nJ, bool with_lam, const double* lam, double* J,
+                double* g, cudaStream_t st) {
+  const int S = nJ + (with_lam ? 1 : 0);
+  if (S == 0) return NNC_OK;
+  const int lam_col = with_lam ? nJ : -1;
+  const bool tc = is_tc(net->prec);
+  LayerDev& Lo = net->layers.back();
+  CK(launch_rev_seed(Lo.m, S, nJ, lam_col, Lo.s1, Lo.s2, lam, net->Zbar[0],
+                     with_lam ? Lo.c : nullptr, (with_lam && tc) ? Lo.c_f : nullptr, st));
+  int cur = 0;
+  for (int l = net->L - 1; l >= 0; --l) {
+    LayerDev& Ly = net->layers[l];
+    const int chunks = rev_chunks(Ly.m, Ly.kp, net->sm_count);
+    PROF(PK_REV);
+    CK(launch_gemv_rev(fp64, fp64 ? (const void*)Ly.W64 : (const void*)Ly.W32, Ly.kp, Ly.m, Ly.kp,
+                       net->Zbar[cur], S, chunks, net->part, st));
+    if (l > 0) {
+      LayerDev& Lp = net->layers[l - 1];
+      CK(launch_rev_reduce(net->part, chunks, Ly.kp, Ly.k, S, Lp.s1, Lp.s2, lam_col, nJ,
+                           net->Zbar[1 - cur], with_lam ? Lp.c : nullptr,
+                           (with_lam && tc) ? Lp.c_f : nullptr, nullptr, nullptr, st));
+      cur = 1 - cur;
+    } else {
+      CK(launch_rev_reduce(net->part, chunks, Ly.kp, Ly.k, S, nullptr, nullptr, lam_col, nJ,
+                           nullptr, nullptr, nullptr, J, g, st));
+    }
+  }
+  return NNC_OK;
+}
+
+// ---------------------------------------------------------------- tangent sweep + H
+int run_hessian(nnc_net* net, double* H, cudaStream_t st) {
+  const int n = net->n_in;
+  const int prec = net->prec;
+  const bool tc = is_tc(prec);
+  const Elem e = tan_elem(prec);
+  const size_t hp_bytes = (size_t)net->h_splits * n * n * (net->hp_f32 ? 4 : 8);
+  CK(cudaMemsetAsync(net->Hp, 0, hp_bytes, st));
+  LayerDev& L1 = net->layers[0];
+  TanBuf At0{net->At[0][0], net->At[0][1]}, Zt{net->Zt[0], net->Zt[1]}, Yt{net->Yt[0], net->Yt[1]};
+  CK(launch_first_tangent(e, L1.W64, L1.kp, L1.mp, n, L1.s1, L1.c, net->L > 1 ? At0 : TanBuf{},
+                          Zt, Yt, L1.mp, st));
+  auto syrk = [&](LayerDev& Ly) -> int {
+    if (Ly.act == NNC_IDENTITY) return NNC_OK;  // sigma'' = 0: no curvature from this layer
+    PROF(PK_SYRK);
+    if (tc) {
+      CK(tc_syrk(Ly.plan_syrk, (float*)net->Hp, net->dev_err, st));
+    } else {
+      CK(launch_simt_syrk(prec == NNC_FP64, net->Zt[0], net->Yt[0], Ly.mp, n, Ly.mp, net->h_splits,
+                          (double*)net->Hp, st));
+    }
+    return NNC_OK;
+  };
+  int r = syrk(L1);
+  if (r != NNC_OK) return r;
+  int cur = 0;
+  for (int l = 1; l < net->L; ++l) {
+    LayerDev& Ly = net->layers[l];
+    const bool last = (l == net->L - 1);
+    if (last && Ly.act == NNC_IDENTITY) break;  // linear output layer adds nothing to H
+    void* Anext_hi = last ? nullptr : net->At[1 - cur][0];
+    void* Anext_lo = last ? nullptr : net->At[1 - cur][1];
+    {
+      PROF(PK_TANGENT);
+      if (tc) {
+        CK(tc_tangent(Ly.plan_tan, Ly.s1, Ly.c_f, Anext_hi, Anext_lo, net->Zt[0], net->Zt[1],
+                      net->Yt[0], net->Yt[1], Ly.mp, net->dev_err, st));
+      } else {
+        CK(launch_simt_tangent(prec == NNC_FP64,
+                               prec == NNC_FP64 ? (const void*)Ly.W64 : (const void*)Ly.W32,
+                               Ly.kp, net->At[cur][0], Ly.kp, Ly.mp, n, Ly.kp, Ly.s1, Ly.c,
+                               Anext_hi, net->Zt[0], net->Yt[0], Ly.mp, st));
+      }
+    }
+    r = syrk(Ly);
+    if (r != NNC_OK) return r;
+    cur = 1 - cur;
+  }
+  CK(launch_h_finish(net->hp_f32, net->Hp, net->h_splits, n, n, H, st));
+  return NNC_OK;
+}
+
+int eval_all(nnc_net* net, const double* x, const double* lam, double* y, double* J, double* H,
+             double* g, cudaStream_t st) {
+  CK(launch_copy_pad(x, net->x, net->n_in, net->n_in_pad, st));
+  const bool fp64 = net->prec == NNC_FP64;
+  int r = run_forward(net, fp64, st);
+  if (r != NNC_OK) return r;
+  if (y)
+    CK(cudaMemcpyAsync(y, net->layers.back().a, sizeof(double) * net->n_out,
+                       cudaMemcpyDeviceToDevice, st));
+  const bool need_lam = (H != nullptr) || (g != nullptr);
+  if (J || need_lam) {
+    r = run_reverse(net, fp64, J ? net->n_out : 0, need_lam, lam, J, g, st);
+    if (r != NNC_OK) return r;
+  }
+  if (H) {
+    r = run_hessian(net, H, st);
+    if (r != NNC_OK) return r;
+  }
+  return NNC_OK;
+}
+
+int check_net(const nnc_net* net) {
+  if (!net) return fail(NNC_ERR_ARG, "net is NULL");
+  return NNC_OK;
+}
+
+// Host-pointer wrapper: copy inputs in, run, copy outputs out, wait.
+int host_call(nnc_net* net, const double* x, const double* lam, double* y, double* J, double* H,
+              double* g) {
+  int r = check_net(net);
+  if (r) return r;
+  if (!x) return fail(NNC_ERR_ARG, "x is NULL");
+  if ((H || g) && !lam) return fail(NNC_ERR_ARG, "lambda is NULL");
+  r = check_finite(x, net->n_in, "x");
+  if (r) return r;
+  if (lam) {
+    r = check_finite(lam, net->n_out, "lambda");
+    if (r) return r;
+  }
+  CK(cudaSetDevice(net->device));
+  cudaStream_t st = net->stream;
+  double* hs = net->h_stage;
+  std::memcpy(hs, x, sizeof(double) * net->n_in);
+  if (lam) std::memcpy(hs + net->n_in, lam, sizeof(double) * net->n_out);
+  CK(cudaMemcpyAsync(net->xin, hs, sizeof(double) * net->n_in, cudaMemcpyHostToDevice, st));
+  if (lam) CK(cudaMemcpyAsync(net->lam, hs + net->n_in, sizeof(double) * net->n_out,
+                              cudaMemcpyHostToDevice, st));
+  r = eval_all(net, net->xin, lam ? net->lam : nullptr, y ? net->ydev : nullptr,
+               J ? net->Jdev : nullptr, H ? net->Hdev : nullptr, g ? net->gdev : nullptr, st);
+  if (r) return r;
+  if (y) CK(cudaMemcpyAsync(y, net->ydev, sizeof(double) * net->n_out, cudaMemcpyDeviceToHost, st));
+  if (J) CK(cudaMemcpyAsync(J, net->Jdev, sizeof(double) * net->n_out * net->n_in,
+                            cudaMemcpyDeviceToHost, st));
+  if (H) CK(cudaMemcpyAsync(H, net->Hdev, sizeof(double) * net->n_in * net->n_in,
+                            cudaMemcpyDeviceToHost, st));
+  if (g) CK(cudaMemcpyAsync(g, net->gdev, sizeof(double) * net->n_in, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return check_dev_err(net);
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+const char* nnc_last_error(void) { return g_err.c_str(); }
+
+long long nnc_launch_count(void) { return g_launches.load(); }
+
+int nnc_profile(nnc_net* net, int enable) {
+  int r = check_net(net);
+  if (r) return r;
+  net->prof = enable != 0;
+  net->ev_used = 0;
+  net->ev_kind.clear();
+  return NNC_OK;
+}
+
+int nnc_profile_read(nnc_net* net, double* ms, long long* count, int n_kinds) {
+  int r = check_net(net);
+  if (r) return r;
+  if (!ms || !count || n_kinds < 1) return fail(NNC_ERR_ARG, "bad profile buffers");
+  for (int i = 0; i < n_kinds; ++i) {
+    ms[i] = 0.0;
+    count[i] = 0;
+  }
+  for (size_t i = 0; i < net->ev_kind.size(); ++i) {
+    CK(cudaEventSynchronize(net->ev_pool[2 * i + 1]));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, net->ev_pool[2 * i], net->ev_pool[2 * i + 1]));
+    const int k = net->ev_kind[i];
+    if (k < n_kinds) {
+      ms[k] += t;
+      count[k] += 1;
+    }
+  }
+  net->ev_used = 0;
+  net->ev_kind.clear();
+  return NNC_OK;
+}
+
+int nnc_net_info(const nnc_net* net, int* n_layers, int* n_in, int* n_out, int* prec) {
+  if (!net) return fail(NNC_ERR_ARG, "net is NULL");
+  if (n_layers) *n_layers = net->L;
+  if (n_in) *n_in = net->n_in;
+  if (n_out) *n_out = net->n_out;
+  if (prec) *prec = net->prec;
+  return NNC_OK;
+}
+
+void nnc_free(nnc_net* net) {
+  if (!net) return;
+  cudaSetDevice(net->device);
+  if (net->stream) cudaStreamSynchronize(net->stream);
+  for (void* p : net->allocs) cudaFree(p);
+  for (cudaEvent_t e : net->ev_pool) cudaEventDestroy(e);
+  if (net->h_stage) cudaFreeHost(net->h_stage);
+  if (net->own_stream && net->stream) cudaStreamDestroy(net->stream);
+  delete net;
+}
+
+static int load_impl(nnc_net* net, int n_layers, const int* widths, const int* act,
+                     const double* const* W, const double* const* b) {
+  cudaDeviceProp prop;
+  CK(cudaGetDevice(&net->device));
+  CK(cudaGetDeviceProperties(&prop, net->device));
+  if (prop.major != 10 || prop.minor != 3)
+    return fail(NNC_ERR_CUDA, std::string("libnnc is built for sm_103a; device is ") + prop.name +
+                                  " sm_" + std::to_string(prop.major * 10 + prop.minor));
+  net->sm_count = prop.multiProcessorCount;
+  net->L = n_layers;
+  net->n_in = widths[0];
+  net->n_out = widths[n_layers];
+  net->n_in_pad = pad_up(net->n_in);
+  net->S_max = net->n_out + 1;
+  if (net->S_max > 48) return fail(NNC_ERR_UNSUPPORTED, "n_out > 47 is not supported");
+  const int prec = net->prec;
+  const bool tc = is_tc(prec);
+  net->layers.resize(n_layers);
+  int mp_max = net->n_in_pad;
+  size_t part_max = 1;
+  for (int l = 0; l < n_layers; ++l) {
+    LayerDev& Ly = net->layers[l];
+    Ly.m = widths[l + 1];
+    Ly.k = widths[l];
+    Ly.act = act[l];
+    Ly.mp = pad_up(Ly.m);
+    Ly.kp = pad_up(Ly.k);
+    mp_max = std::max(mp_max, Ly.mp);
+    const size_t nw = (size_t)Ly.mp * Ly.kp;
+    AL(Ly.W64, nw);
+    CK(cudaMemcpy2DAsync(Ly.W64, sizeof(double) * Ly.kp, W[l], sizeof(double) * Ly.k,
+                         sizeof(double) * Ly.k, Ly.m, cudaMemcpyHostToDevice, net->stream));
+    if (prec != NNC_FP64) AL(Ly.W32, nw);
+    if (tc && l > 0) {
+      AL(Ly.Whi, nw);
+      if (prec == NNC_BF16X3) AL(Ly.Wlo, nw);
+    }
+    CK(launch_pack(Ly.W64, nw, Ly.W32, Ly.Whi, Ly.Wlo, net->stream));
+    AL(Ly.b, Ly.mp);
+    if (b && b[l])
+      CK(cudaMemcpyAsync(Ly.b, b[l], sizeof(double) * Ly.m, cudaMemcpyHostToDevice, net->stream));
+    AL(Ly.a, Ly.mp);
+    AL(Ly.s1, Ly.mp);
+    AL(Ly.s2, Ly.mp);
+    AL(Ly.c, Ly.mp);
+    AL(Ly.ra, Ly.mp);
+    if (tc) AL(Ly.c_f, Ly.mp);
+    const int chunks = rev_chunks(Ly.m, Ly.kp, net->sm_count);
+    part_max = std::max(part_max, (size_t)chunks * Ly.kp * net->S_max);
+  }
+  net->mp_max = mp_max;
+  AL(net->x, net->n_in_pad);
+  AL(net->xin, net->n_in_pad);
+  AL(net->lam, net->n_out);
+  AL(net->ydev, net->n_out);
+  AL(net->rdev, net->n_out);
+  AL(net->Zbar[0], (size_t)mp_max * net->S_max);
+  AL(net->Zbar[1], (size_t)mp_max * net->S_max);
+  AL(net->part, part_max);
+  AL(net->Jdev, (size_t)net->n_out * net->n_in);
+  AL(net->gdev, net->n_in_pad);
+  AL(net->Hdev, (size_t)net->n_in * net->n_in);
+  AL(net->dev_err, 1);
+  // tangent buffers: n_in rows of mp_max elements
+  const int n = net->n_in;
+  const size_t tan_elems = (size_t)n * mp_max;
+  const size_t es = elem_size(prec);
+  const bool x3 = prec == NNC_BF16X3;
+  unsigned char* p;
+  for (int pp = 0; pp < 2; ++pp) {
+    AL(p, tan_elems * es);
+    net->At[pp][0] = p;
+    if (x3) {
+      AL(p, tan_elems * es);
+      net->At[pp][1] = p;
+    }
+  }
+  AL(p, tan_elems * es);
+  net->Zt[0] = p;
+  AL(p, tan_elems * es);
+  net->Yt[0] = p;
+  if (x3) {
+    AL(p, tan_elems * es);
+    net->Zt[1] = p;
+    AL(p, tan_elems * es);
+    net->Yt[1] = p;
+  }
+  // split-K partial sums of H
+  if (tc) {
+    net->hp_f32 = true;
+    int splits = 1;
+    for (int l = 0; l < n_layers; ++l) {
+      LayerDev& Ly = net->layers[l];
+      int r = tc_plan_make(Ly.plan_syrk, TC_SYRK, prec, net->Zt[0], net->Zt[1], n, Ly.mp,
+                           net->Yt[0], net->Yt[1], n, Ly.mp, n, n, Ly.mp, net->sm_count);
+      if (r != NNC_OK) return fail(r, "tensor-core symmetric-product plan failed");
+      splits = std::max(splits, Ly.plan_syrk.splits);
+      if (l > 0) {
+        const int cur = (l - 1) % 2;
+        r = tc_plan_make(Ly.plan_tan, TC_TANGENT, prec, Ly.Whi, Ly.Wlo, Ly.mp, Ly.kp,
+                         net->At[cur][0], net->At[cur][1], n, Ly.kp, Ly.mp, n, Ly.kp,
+                         net->sm_count);
+        if (r != NNC_OK) return fail(r, "tensor-core tangent plan failed");
+      }
+    }
+    net->h_splits = splits;
+    float* hp;
+    AL(hp, (size_t)splits * n * n);
+    net->Hp = hp;
+  } else {
+    const int tile = prec == NNC_FP64 ? 64 : 128;
+    const int T = (n + tile - 1) / tile;
+    const int tiles = T * (T + 1) / 2;
+    int splits = (2 * net->sm_count + tiles - 1) / tiles;
+    int kmin = mp_max;
+    for (auto& Ly : net->layers) kmin = std::min(kmin, Ly.mp);
+    splits = std::max(1, std::min(splits, kmin / 256));
+    net->h_splits = splits;
+    net->hp_f32 = false;
+    double* hp;
+    AL(hp, (size_t)splits * n * n);
+    net->Hp = hp;
+  }
+  net->h_stage_elems = (size_t)net->n_in_pad + net->n_out;
+  CK(cudaMallocHost(&net->h_stage, sizeof(double) * net->h_stage_elems));
+  CK(cudaStreamSynchronize(net->stream));
+  return NNC_OK;
+}
+
+int nnc_load_weights(nnc_net** out, int n_layers, const int* widths, const int* act,
+                     const double* const* W, const double* const* b, int prec, void* stream) {
+  if (!out) return fail(NNC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n_layers < 1 || !widths || !act || !W) return fail(NNC_ERR_ARG, "bad layer description");
+  for (int l = 0; l <= n_layers; ++l)
+    if (widths[l] < 1 || widths[l] > 65536) return fail(NNC_ERR_ARG, "width out of range [1, 65536]");
+  for (int l = 0; l < n_layers; ++l) {
+    if (act[l] < NNC_IDENTITY || act[l] > NNC_GELU) return fail(NNC_ERR_ARG, "bad activation code");
+    if (!W[l]) return fail(NNC_ERR_ARG, "W[l] is NULL");
+  }
+  if (prec < NNC_FP64 || prec > NNC_FP8) return fail(NNC_ERR_ARG, "bad precision code");
+  if (prec == NNC_FP8) return fail(NNC_ERR_UNSUPPORTED, "the FP8 form is not built yet");
+  nnc_net* net = new nnc_net();
+  net->prec = prec;
+  if (stream) {
+    net->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&net->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete net;
+      return fail(NNC_ERR_CUDA, "no CUDA device or cudaStreamCreate failed");
+    }
+    net->own_stream = true;
+  }
+  int r = load_impl(net, n_layers, widths, act, W, b);
+  if (r != NNC_OK) {
+    std::string keep = g_err;
+    nnc_free(net);
+    g_err = keep;
+    return r;
+  }
+  *out = net;
+  return NNC_OK;
+}
+
+int nnc_eval(nnc_net* net, const double* x, double* y, int fp64_residual) {
+  int r = check_net(net);
+  if (r) return r;
+  if (!x || !y) return fail(NNC_ERR_ARG, "x or y is NULL");
+  if (!fp64_residual) return host_call(net, x, nullptr, y, nullptr, nullptr, nullptr);
+  r = check_finite(x, net->n_in, "x");
+  if (r) return r;
+  CK(cudaSetDevice(net->device));
+  cudaStream_t st = net->stream;
+  std::memcpy(net->h_stage, x, sizeof(double) * net->n_in);
+  CK(cudaMemcpyAsync(net->xin, net->h_stage, sizeof(double) * net->n_in, cudaMemcpyHostToDevice, st));
+  CK(launch_copy_pad(net->xin, net->x, net->n_in, net->n_in_pad, st));
+  r = run_forward_fp64_values(net, st);
+  if (r) return r;
+  CK(cudaMemcpyAsync(y, net->layers.back().ra, sizeof(double) * net->n_out, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return NNC_OK;
+}
+
+int nnc_eval_dev(nnc_net* net, const double* x, double* y, int fp64_residual, void* stream) {
+  int r = check_net(net);
+  if (r) return r;
+  if (!x || !y) return fail(NNC_ERR_ARG, "x or y is NULL");
+  cudaStream_t st = pick(net, stream);
+  CK(launch_copy_pad(x, net->x, net->n_in, net->n_in_pad, st));
+  r = fp64_residual ? run_forward_fp64_values(net, st) : run_forward(net, net->prec == NNC_FP64, st);
+  if (r) return r;
+  const double* aL = fp64_residual ? net->layers.back().ra : net->layers.back().a;
+  CK(cudaMemcpyAsync(y, aL, sizeof(double) * net->n_out, cudaMemcpyDeviceToDevice, st));
+  return NNC_OK;
+}
+
+int nnc_residual_dev(nnc_net* net, const double* x, const double* y, double* rr, void* stream) {
+  int r = check_net(net);
+  if (r) return r;
+  if (!x || !y || !rr) return fail(NNC_ERR_ARG, "x, y or r is NULL");
+  cudaStream_t st = pick(net, stream);
+  CK(launch_copy_pad(x, net->x, net->n_in, net->n_in_pad, st));
+  r = run_forward_fp64_values(net, st);
+  if (r) return r;
+  CK(launch_sub(y, net->layers.back().ra, rr, net->n_out, st));
+  return NNC_OK;
+}
+
+int nnc_residual(nnc_net* net, const double* x, const double* y, double* rr) {
+  int r = check_net(net);
+  if (r) return r;
+  if (!x || !y || !rr) return fail(NNC_ERR_ARG, "x, y or r is NULL");
+  r = check_finite(x, net->n_in, "x");
+  if (r) return r;
+  CK(cudaSetDevice(net->device));
+  cudaStream_t st = net->stream;
+  std::memcpy(net->h_stage, x, sizeof(double) * net->n_in);
+  std::memcpy(net->h_stage + net->n_in_pad, y, sizeof(double) * net->n_out);
+  CK(cudaMemcpyAsync(net->xin, net->h_stage, sizeof(double) * net->n_in, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(net->ydev, net->h_stage + net->n_in_pad, sizeof(double) * net->n_out,
+                     cudaMemcpyHostToDevice, st));
+  r = nnc_residual_dev(net, net->xin, net->ydev, net->rdev, st);
+  if (r) return r;
+  CK(cudaMemcpyAsync(rr, net->rdev, sizeof(double) * net->n_out, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return NNC_OK;
+}
+
+int nnc_jacobian(nnc_net* net, const double* x, double* J) {
+  if (!J) return fail(NNC_ERR_ARG, "J is NULL");
+  return host_call(net, x, nullptr, nullptr, J, nullptr, nullptr);
+}
+
+int nnc_jacobian_dev(nnc_net* net, const double* x, double* J, void* stream) {
+  int r = check_net(net);
+  if (r) return r;
+  if (!x || !J) return fail(NNC_ERR_ARG, "x or J is NULL");
+  return eval_all(net, x, nullptr, nullptr, J, nullptr, nullptr, pick(net, stream));
+}
+
+int nnc_hessian_lag(nnc_net* net, const double* x, const double* lambda, double* H, double* grad) {
+  if (!H) return fail(NNC_ERR_ARG, "H is NULL");
+  return host_call(net, x, lambda, nullptr, nullptr, H, grad);
+}
+
+int nnc_hessian_lag_dev(nnc_net* net, const double* x, const double* lambda, double* H,
+                        double* grad, void* stream) {
+  int r = check_net(net);
+  if (r) return r;
+  if (!x || !lambda || !H) return fail(NNC_ERR_ARG, "x, lambda or H is NULL");
+  return eval_all(net, x, lambda, nullptr, nullptr, H, grad, pick(net, stream));
+}
+
+int nnc_eval_all_dev(nnc_net* net, const double* x, const double* lambda, double* y, double* J,
+                     double* H, double* grad, void* stream) {
+  int r = check_net(net);
+  if (r) return r;
+  if (!x) return fail(NNC_ERR_ARG, "x is NULL");
+  if ((H || grad) && !lambda) return fail(NNC_ERR_ARG, "lambda is NULL");
+  return eval_all(net, x, lambda, y, J, H, grad, pick(net, stream));
+}
+
+int nnc_eval_batched(nnc_net* const* nets, int K, const double* const* x,
+                     const double* const* lambda, double* const* y, double* const* J,
+                     double* const* H, unsigned what) {
+  if (K < 0 || (K > 0 && (!nets || !x))) return fail(NNC_ERR_ARG, "bad batch arguments");
+  if ((what & NNC_WANT_Y) && !y) return fail(NNC_ERR_ARG, "y array is NULL");
+  if ((what & NNC_WANT_J) && !J) return fail(NNC_ERR_ARG, "J array is NULL");
+  if ((what & NNC_WANT_H) && (!H || !lambda)) return fail(NNC_ERR_ARG, "H or lambda array is NULL");
+  for (int k = 0; k < K; ++k) {
+    int r = host_call(nets[k], x[k], (what & NNC_WANT_H) ? lambda[k] : nullptr,
+                      (what & NNC_WANT_Y) ? y[k] : nullptr, (what & NNC_WANT_J) ? J[k] : nullptr,
+                      (what & NNC_WANT_H) ? H[k] : nullptr, nullptr);
+    if (r != NNC_OK) return r;
+  }
+  return NNC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,44 @@
+// Tensor-core (tcgen05 / TMEM / TMA) GEMMs of the BF16 forms, host side.
+//
+// Both GEMMs compute D[m][n] = sum_k A[m][k] B[n][k] with A and B K-major BF16 in global memory
+// (optionally split into hi and lo parts), FP32 accumulation in tensor memory, and a fused
+// epilogue:
+//   tangent : A = W_l (mp x kp), B = Adot_{l-1}^T (n x kp);  writes Adot_l^T = sigma_l' * D,
+//             Zdot_l^T = D and Ydot_l^T = c_l * D (n x mp, BF16 hi/lo), c_l = sigma_l'' * abar_l
+//   syrk    : A = Zdot_l^T, B = Ydot_l^T (n x mp); adds D into the split-K partial sum of H
+//             over the lower-triangle tiles.
+#pragma once
+#include <cuda.h>
+
+#include "common.cuh"
+
+namespace nnc {
+
+enum { TC_TANGENT = 0, TC_SYRK = 1 };
+
+struct TcPlan {
+  CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;
+  int kind = TC_TANGENT;
+  int x3 = 0;           // split-BF16x3 products
+  int M = 0, N = 0, K = 0;  // M: rows of A (multiple of 128), N: valid rows of B, K: multiple of 64
+  int bn = 0;           // N tile
+  int ntm = 0, ntn = 0; // tiles along M and N
+  int splits = 1, kb_per_split = 0;
+  bool ready = false;
+};
+
+// Choose tiles and split-K for one GEMM and encode its tensor maps.  a_rows / b_rows are the
+// row counts of the A and B arrays (rows beyond them read as zero), ld_a / ld_b their row
+// strides in elements.  Returns NNC_OK or a negative status.
+int tc_plan_make(TcPlan& p, int kind, int prec, const void* a_hi, const void* a_lo, int a_rows,
+                 int ld_a, const void* b_hi, const void* b_lo, int b_rows, int ld_b, int M, int N,
+                 int K, int sm_count, int force_bn = 0, int force_splits = 0);
+
+cudaError_t tc_tangent(const TcPlan& p, const double* s1, const float* c, void* at_hi, void* at_lo,
+                       void* zt_hi, void* zt_lo, void* yt_hi, void* yt_lo, int ldo, int* err,
+                       cudaStream_t st);
+
+// Hp: splits x N x N floats (row stride N); partial sums of the lower triangle are added.
+cudaError_t tc_syrk(const TcPlan& p, float* Hp, int* err, cudaStream_t st);
+
+}  // namespace nnc

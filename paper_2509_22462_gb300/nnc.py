@@ -1,0 +1,225 @@
+"""ctypes binding of libnnc (include/nnc.h), with the same names as the C ABI.
+
+The binding only marshals arguments: every step of the computation runs in the CUDA library.
+If the library is missing or has no usable sm_103a device, calls raise; there is no fallback.
+Host calls take and return numpy float64 arrays; the *_dev calls take CUDA torch tensors
+(float64, contiguous) and queue work on the current torch stream.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnnc.so")
+
+FP64, FP32, BF16, BF16X3, FP8 = 0, 1, 2, 3, 4
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": BF16, "bf16x3": BF16X3, "fp8": FP8}
+ACTS = {"identity": 0, "tanh": 1, "sigmoid": 2, "softplus": 3, "gelu": 4}
+WANT_Y, WANT_J, WANT_H, WANT_G = 1, 2, 4, 8
+STATUS = {0: "NNC_OK", -1: "NNC_ERR_ARG", -2: "NNC_ERR_CUDA", -3: "NNC_ERR_NONFINITE",
+          -4: "NNC_ERR_TIMEOUT", -5: "NNC_ERR_OOM", -6: "NNC_ERR_UNSUPPORTED"}
+
+# Every symbol that include/nnc.h declares.
+EXPORTS = ["nnc_load_weights", "nnc_eval", "nnc_residual", "nnc_jacobian", "nnc_hessian_lag",
+           "nnc_eval_batched", "nnc_eval_dev", "nnc_residual_dev", "nnc_jacobian_dev",
+           "nnc_hessian_lag_dev", "nnc_eval_all_dev", "nnc_free", "nnc_last_error",
+           "nnc_net_info", "nnc_launch_count", "nnc_profile", "nnc_profile_read"]
+PROFILE_KINDS = ["tangent_gemm", "syrk", "forward", "reverse", "other"]
+
+
+class NNCError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+_P = ctypes.c_void_p
+_DP = ctypes.POINTER(ctypes.c_double)
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libnnc.so (raise if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"{path} not found: build it first (python -m paper_2509_22462_gb300.build)")
+    lib = ctypes.CDLL(path)
+    for name in EXPORTS:
+        getattr(lib, name)
+    lib.nnc_load_weights.argtypes = [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_DP),
+                                     ctypes.POINTER(_DP), ctypes.c_int, _P]
+    lib.nnc_eval.argtypes = [_P, _DP, _DP, ctypes.c_int]
+    lib.nnc_residual.argtypes = [_P, _DP, _DP, _DP]
+    lib.nnc_jacobian.argtypes = [_P, _DP, _DP]
+    lib.nnc_hessian_lag.argtypes = [_P, _DP, _DP, _DP, _DP]
+    lib.nnc_eval_batched.argtypes = [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_DP),
+                                     ctypes.POINTER(_DP), ctypes.POINTER(_DP), ctypes.POINTER(_DP),
+                                     ctypes.POINTER(_DP), ctypes.c_uint]
+    lib.nnc_eval_dev.argtypes = [_P, _P, _P, ctypes.c_int, _P]
+    lib.nnc_residual_dev.argtypes = [_P, _P, _P, _P, _P]
+    lib.nnc_jacobian_dev.argtypes = [_P, _P, _P, _P]
+    lib.nnc_hessian_lag_dev.argtypes = [_P, _P, _P, _P, _P, _P]
+    lib.nnc_eval_all_dev.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P]
+    lib.nnc_free.argtypes = [_P]
+    lib.nnc_free.restype = None
+    lib.nnc_last_error.restype = ctypes.c_char_p
+    lib.nnc_net_info.argtypes = [_P] + [ctypes.POINTER(ctypes.c_int)] * 4
+    lib.nnc_launch_count.restype = ctypes.c_longlong
+    lib.nnc_profile.argtypes = [_P, ctypes.c_int]
+    lib.nnc_profile_read.argtypes = [_P, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
+    for name in EXPORTS:
+        if name not in ("nnc_free", "nnc_last_error", "nnc_launch_count"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(code):
+    if code != 0:
+        raise NNCError(code, _lib.nnc_last_error().decode())
+
+
+def _dp(a):
+    return a.ctypes.data_as(_DP)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def launch_count() -> int:
+    return int(load_library().nnc_launch_count())
+
+
+def _stream_ptr():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _tp(t):
+    """Device pointer of a CUDA float64 tensor (None -> NULL)."""
+    if t is None:
+        return None
+    assert t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8 and t.is_contiguous()
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Net:
+    """An MLP y = NN(x) (Eq. 3) loaded into libnnc on the current CUDA device."""
+
+    def __init__(self, widths, acts, W, b=None, precision="fp64", stream=None):
+        lib = load_library()
+        self.widths = [int(w) for w in widths]
+        self.acts = list(acts)
+        L = len(self.widths) - 1
+        self.n_in, self.n_out = self.widths[0], self.widths[-1]
+        self.precision = precision if isinstance(precision, str) else \
+            {v: k for k, v in PRECISIONS.items()}[precision]
+        Wc = [_f64(w) for w in W]
+        bc = [_f64(x) for x in b] if b is not None else None
+        for l in range(L):
+            assert Wc[l].shape == (self.widths[l + 1], self.widths[l]), (l, Wc[l].shape)
+        wid = (ctypes.c_int * (L + 1))(*self.widths)
+        act = (ctypes.c_int * L)(*[ACTS[a] if isinstance(a, str) else int(a) for a in self.acts])
+        Wp = (_DP * L)(*[_dp(w) for w in Wc])
+        bp = (_DP * L)(*[_dp(x) for x in bc]) if bc is not None else None
+        h = _P()
+        _check(lib.nnc_load_weights(ctypes.byref(h), L, wid, act, Wp, bp,
+                                    PRECISIONS[self.precision], stream))
+        self._h = h
+
+    @classmethod
+    def from_mlp(cls, mlp, precision="fp64", stream=None):
+        return cls(mlp.spec.widths, mlp.spec.acts, mlp.W, mlp.b, precision, stream)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def free(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.nnc_free(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- host calls
+    def eval(self, x, fp64_residual=False):
+        x = _f64(x)
+        y = np.empty(self.n_out)
+        _check(_lib.nnc_eval(self._h, _dp(x), _dp(y), int(bool(fp64_residual))))
+        return y
+
+    def residual(self, x, y):
+        x, y = _f64(x), _f64(y)
+        r = np.empty(self.n_out)
+        _check(_lib.nnc_residual(self._h, _dp(x), _dp(y), _dp(r)))
+        return r
+
+    def jacobian(self, x):
+        x = _f64(x)
+        J = np.empty((self.n_out, self.n_in))
+        _check(_lib.nnc_jacobian(self._h, _dp(x), _dp(J)))
+        return J
+
+    def hessian_lag(self, x, lam, want_grad=False):
+        x, lam = _f64(x), _f64(lam)
+        H = np.empty((self.n_in, self.n_in))
+        g = np.empty(self.n_in) if want_grad else None
+        _check(_lib.nnc_hessian_lag(self._h, _dp(x), _dp(lam), _dp(H),
+                                    _dp(g) if want_grad else None))
+        return (H, g) if want_grad else H
+
+    def profile(self, enable=True):
+        _check(_lib.nnc_profile(self._h, int(bool(enable))))
+
+    def profile_read(self):
+        """{kind: (total ms, launches)} recorded since profile(True) (and clears the record)."""
+        n = len(PROFILE_KINDS)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_longlong * n)()
+        _check(_lib.nnc_profile_read(self._h, ms, cnt, n))
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(PROFILE_KINDS)}
+
+    # ---------------------------------------------------------------- device calls
+    def eval_dev(self, x, y, fp64_residual=False, stream=None):
+        _check(_lib.nnc_eval_dev(self._h, _tp(x), _tp(y), int(bool(fp64_residual)),
+                                 stream or _stream_ptr()))
+
+    def residual_dev(self, x, y, r, stream=None):
+        _check(_lib.nnc_residual_dev(self._h, _tp(x), _tp(y), _tp(r), stream or _stream_ptr()))
+
+    def jacobian_dev(self, x, J, stream=None):
+        _check(_lib.nnc_jacobian_dev(self._h, _tp(x), _tp(J), stream or _stream_ptr()))
+
+    def hessian_lag_dev(self, x, lam, H, grad=None, stream=None):
+        _check(_lib.nnc_hessian_lag_dev(self._h, _tp(x), _tp(lam), _tp(H), _tp(grad),
+                                        stream or _stream_ptr()))
+
+    def eval_all_dev(self, x, lam=None, y=None, J=None, H=None, grad=None, stream=None):
+        _check(_lib.nnc_eval_all_dev(self._h, _tp(x), _tp(lam), _tp(y), _tp(J), _tp(H), _tp(grad),
+                                     stream or _stream_ptr()))
+
+
+def eval_batched(nets, xs, lams=None, what=WANT_Y | WANT_J | WANT_H):
+    """nnc_eval_batched over host arrays: returns (ys, Js, Hs) lists (None where not asked)."""
+    lib = load_library()
+    K = len(nets)
+    xs = [_f64(x) for x in xs]
+    lams = [_f64(l) for l in lams] if lams is not None else None
+    ys = [np.empty(n.n_out) for n in nets] if what & WANT_Y else None
+    Js = [np.empty((n.n_out, n.n_in)) for n in nets] if what & WANT_J else None
+    Hs = [np.empty((n.n_in, n.n_in)) for n in nets] if what & WANT_H else None
+    arr = lambda lst: (_DP * K)(*[_dp(a) for a in lst]) if lst is not None else None  # noqa: E731
+    hs = (_P * K)(*[n.handle for n in nets])
+    _check(lib.nnc_eval_batched(hs, K, arr(xs), arr(lams), arr(ys), arr(Js), arr(Hs), what))
+    return ys, Js, Hs

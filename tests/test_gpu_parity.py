@@ -1,0 +1,150 @@
+"""GPU path against the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (relative Frobenius norm ||gpu - oracle|| / ||oracle||):
+  FP64 form                 : 1e-10 on the value, the Jacobian and the Hessian;
+  FP32 / BF16x3 / BF16 forms: 1e-6 on the value, 1e-3 on the Jacobian, 1e-2 on the Hessian;
+  FP64 residual y - NN(x)   : 1e-10 in every form.
+"""
+import numpy as np
+import pytest
+
+import synth
+from synth.nets import MLPSpec, make_mlp
+from oracle import nn as onn
+
+pytestmark = pytest.mark.gpu
+
+TOL = {
+    "fp64": dict(y=1e-10, J=1e-10, H=1e-10),
+    "fp32": dict(y=1e-6, J=1e-3, H=1e-2),
+    "bf16x3": dict(y=1e-6, J=1e-3, H=1e-2),
+    "bf16": dict(y=1e-6, J=1e-3, H=1e-2),
+}
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_22462_gb300 import build, nnc
+    build.build()
+    return nnc
+
+
+def _check_all(nnc, mlp, x, lam, prec, label=""):
+    net = nnc.Net.from_mlp(mlp, precision=prec)
+    y = net.eval(x)
+    J = net.jacobian(x)
+    H, g = net.hessian_lag(x, lam, want_grad=True)
+    yo, Jo, Ho, go = onn.all_outputs(mlp, x, lam)
+    e = dict(y=rel(y, yo), J=rel(J, Jo), H=rel(H, Ho), g=rel(g, go))
+    print(f"[{label} {prec}] rel err y={e['y']:.2e} J={e['J']:.2e} H={e['H']:.2e} g={e['g']:.2e}")
+    t = TOL[prec]
+    assert e["y"] < t["y"], e
+    assert e["J"] < t["J"], e
+    assert e["H"] < t["H"], e
+    assert e["g"] < t["J"], e
+    assert np.array_equal(H, H.T), "H must be exactly symmetric"
+    r = net.residual(x, yo)
+    assert np.max(np.abs(r)) <= 1e-10 * max(1.0, np.max(np.abs(yo))), r
+    y64 = net.eval(x, fp64_residual=True)
+    assert rel(y64, yo) < 1e-12
+    net.free()
+    return e
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3", "bf16"])
+def test_tiny_mnist_shape(lib, prec):
+    """784 -> 128 -> 128 -> 10 tanh (seed 0), x0 ~ U[0,1]^784, lambda ~ N(0,1)."""
+    mlp = make_mlp(synth.TINY, seed=0)
+    d = synth.adversarial_data(seed=0)
+    _check_all(lib, mlp, d.x0, d.lam, prec, "tiny")
+
+
+ODD = [
+    ([1, 5, 3], ["tanh", "identity"]),
+    ([17, 33, 1], ["sigmoid", "identity"]),
+    ([33, 130, 257, 10], ["tanh", "softplus", "tanh"]),
+    ([200, 129, 64, 37], ["gelu", "sigmoid", "identity"]),
+    ([7, 300, 300, 300, 2], ["softplus", "tanh", "sigmoid", "sigmoid"]),
+    ([257, 1, 3], ["tanh", "identity"]),
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3"])
+@pytest.mark.parametrize("case", range(len(ODD)))
+def test_odd_shapes(lib, prec, case):
+    widths, acts = ODD[case]
+    mlp = make_mlp(MLPSpec(widths, acts), seed=case + 1, tag="odd", bias_std=0.2)
+    x = synth.uniform01(synth.derive_key(case, "odd-x"), widths[0])
+    lam = synth.normal(synth.derive_key(case, "odd-lam"), widths[-1])
+    _check_all(lib, mlp, x, lam, prec, f"odd{case}")
+
+
+def test_nonfinite_and_argument_errors(lib):
+    mlp = make_mlp(MLPSpec([4, 3, 2], ["tanh", "identity"]), seed=0)
+    net = lib.Net.from_mlp(mlp, precision="fp64")
+    x = np.ones(4)
+    x[2] = np.nan
+    with pytest.raises(lib.NNCError) as e:
+        net.eval(x)
+    assert e.value.code == -3
+    with pytest.raises(lib.NNCError) as e:
+        net.hessian_lag(np.ones(4), np.array([np.inf, 0.0]))
+    assert e.value.code == -3
+    assert np.all(np.isfinite(net.eval(np.ones(4))))  # the net stays usable
+    net.free()
+
+
+def test_device_pointer_calls_match_host_calls(lib):
+    import torch
+    mlp = make_mlp(MLPSpec([40, 96, 96, 5], ["tanh", "sigmoid", "identity"]), seed=3)
+    x = synth.uniform01(synth.derive_key(3, "dev-x"), 40)
+    lam = synth.normal(synth.derive_key(3, "dev-lam"), 5)
+    for prec in ["fp64", "bf16x3"]:
+        net = lib.Net.from_mlp(mlp, precision=prec)
+        dev = torch.device("cuda:0")
+        xd = torch.tensor(x, device=dev)
+        ld = torch.tensor(lam, device=dev)
+        y = torch.empty(5, dtype=torch.float64, device=dev)
+        J = torch.empty(5, 40, dtype=torch.float64, device=dev)
+        H = torch.empty(40, 40, dtype=torch.float64, device=dev)
+        g = torch.empty(40, dtype=torch.float64, device=dev)
+        net.eval_all_dev(xd, ld, y, J, H, g)
+        torch.cuda.synchronize()
+        assert np.array_equal(y.cpu().numpy(), net.eval(x))
+        assert np.array_equal(J.cpu().numpy(), net.jacobian(x))
+        Hh, gh = net.hessian_lag(x, lam, want_grad=True)
+        assert np.array_equal(H.cpu().numpy(), Hh)
+        assert np.array_equal(g.cpu().numpy(), gh)
+        net.free()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_full_size_104m_sampled(lib, prec):
+    """The ~104M-parameter net (784 -> 4096 x 7 -> 10 tanh) in the launch configuration the
+    bench times: full value and Jacobian, and sampled Hessian columns against the oracle."""
+    mlp = make_mlp(synth.PAPER_104M, seed=0)
+    d = synth.adversarial_data(seed=0)
+    net = lib.Net.from_mlp(mlp, precision=prec)
+    y = net.eval(d.x0)
+    J = net.jacobian(d.x0)
+    H, g = net.hessian_lag(d.x0, d.lam, want_grad=True)
+    yo = onn.value(mlp, d.x0)
+    Jo = onn.jacobian(mlp, d.x0)
+    go = onn.vjp(mlp, d.x0, d.lam)
+    cols = [0, 1, 391, 392, 783]
+    Hc = onn.hessian_lag_columns(mlp, d.x0, d.lam, cols)
+    e = dict(y=rel(y, yo), J=rel(J, Jo), H=rel(H[:, cols], Hc), g=rel(g, go))
+    print(f"[104m {prec}] rel err y={e['y']:.2e} J={e['J']:.2e} Hcols={e['H']:.2e} g={e['g']:.2e}")
+    t = TOL[prec]
+    assert e["y"] < t["y"] and e["J"] < t["J"] and e["H"] < t["H"] and e["g"] < t["J"], e
+    assert np.array_equal(H, H.T)
+    r = net.residual(d.x0, yo)
+    assert np.max(np.abs(r)) <= 1e-10 * max(1.0, np.max(np.abs(yo)))
+    net.free()

@@ -169,3 +169,10 @@ def test_reduced_space_structure_matches_table2():
     d = synth.adversarial_data(seed=0)
     H = nn.hessian_lag(net, d.x0, d.lam)
     assert np.count_nonzero(np.tril(H)) == n * (n + 1) // 2
+
+
+def test_hessian_columns_match_full_sweep():
+    net = _net([11, 9, 8, 3], ["tanh", "softplus", "sigmoid"])
+    x, lam = _x(11), _lam(3)
+    cols = [0, 4, 10]
+    assert _rel(nn.hessian_lag_columns(net, x, lam, cols), nn.hessian_lag_for(net, x, lam)[:, cols]) < 1e-15
