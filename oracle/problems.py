@@ -1,0 +1,77 @@
+"""The test problems of Section 4 in the form of Eq. 1, built on the oracle network.
+
+TEST INFRASTRUCTURE ONLY.
+
+Adversarial problem (a synthetic variant of Eq. 7; the paper's L1 objective and softmax
+confidence threshold are replaced by an L2 objective and logit margins):
+    variables v = (x in [0,1]^n_in, y in R^n_out, s in R^(n_out-1), s >= 0)
+    min ||x - x0||^2
+    s.t. y - NN(x) = 0                                   (the reduced-space constraint, Eq. 5)
+         y_t - y_j - margin - s_j = 0   for j != t       (target class wins by `margin`)
+Start: x = x0, y = NN(x0), s_j = max(y_t - y_j - margin, 1e-2).
+"""
+import numpy as np
+
+from . import nn as onn
+from .ipm import Problem
+
+
+def adversarial(mlp, x0, target=3, margin=0.1):
+    n_in, n_out = mlp.spec.n_in, mlp.spec.n_out
+    others = [j for j in range(n_out) if j != target]
+    ns = len(others)
+    nv = n_in + n_out + ns
+    m = n_out + ns
+    ix, iy, is_ = slice(0, n_in), slice(n_in, n_in + n_out), slice(n_in + n_out, nv)
+    lb = np.concatenate([np.zeros(n_in), np.full(n_out, -np.inf), np.zeros(ns)])
+    ub = np.concatenate([np.ones(n_in), np.full(n_out, np.inf), np.full(ns, np.inf)])
+    y0 = onn.value(mlp, x0)
+    s0 = np.maximum(np.array([y0[target] - y0[j] - margin for j in others]), 1e-2)
+    v0 = np.concatenate([x0, y0, s0])
+    E = np.zeros((ns, n_out))
+    for r, j in enumerate(others):
+        E[r, target] = 1.0
+        E[r, j] = -1.0
+
+    def f(v):
+        d = v[ix] - x0
+        return float(d @ d)
+
+    def grad_f(v):
+        g = np.zeros(nv)
+        g[ix] = 2.0 * (v[ix] - x0)
+        return g
+
+    def hess_f(v):
+        Hh = np.zeros((nv, nv))
+        Hh[ix, ix] = 2.0 * np.eye(n_in)
+        return Hh
+
+    def c(v):
+        return np.concatenate([v[iy] - onn.value(mlp, v[ix]), E @ v[iy] - margin - v[is_]])
+
+    def jac_c(v):
+        A = np.zeros((m, nv))
+        A[:n_out, ix] = -onn.jacobian(mlp, v[ix])
+        A[:n_out, iy] = np.eye(n_out)
+        A[n_out:, iy] = E
+        A[n_out:, is_] = -np.eye(ns)
+        return A
+
+    def hess_c(v, lam):
+        Hh = np.zeros((nv, nv))
+        Hh[ix, ix] = -onn.hessian_lag(mlp, v[ix], lam[:n_out])
+        return Hh
+
+    p = Problem(nv, m, lb, ub, v0, f, grad_f, hess_f, c, jac_c, hess_c)
+    p.blocks = dict(n_in=n_in, n_out=n_out, ns=ns, target=target, margin=margin)
+    return p
+
+
+def box_projection(x0):
+    """min ||x - x0||^2 over [0,1]^n with no constraint: the solution is clip(x0, 0, 1)."""
+    n = x0.size
+    return Problem(n, 0, np.zeros(n), np.ones(n), np.full(n, 0.5),
+                   lambda v: float((v - x0) @ (v - x0)), lambda v: 2.0 * (v - x0),
+                   lambda v: 2.0 * np.eye(n), lambda v: np.zeros(0), lambda v: np.zeros((0, n)),
+                   lambda v, lam: np.zeros((n, n)))

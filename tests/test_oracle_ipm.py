@@ -1,0 +1,111 @@
+"""Pins for the oracle interior-point method (Eq. 1 / Eq. 2 with IPOPT's barrier terms).
+
+Pinned against closed forms (box projection), a one-dimensional reduction solved by scipy,
+a QP special case (identity activations) solved by scipy's SLSQP, and the KKT conditions of
+the adversarial problem recomputed from their definitions.
+"""
+import numpy as np
+import pytest
+
+import synth
+from synth.nets import MLPSpec, make_mlp
+from oracle import ipm, problems, nn as onn
+
+
+def test_box_projection_closed_form():
+    x0 = np.array([-0.7, 0.2, 1.3, 0.5, 2.0, -0.01])
+    r = ipm.solve(problems.box_projection(x0), ipm.Options(tol=1e-10))
+    assert r.status == ipm.OPTIMAL
+    # an active bound is met to within mu / z with z = 2 |x0 - bound| (0.02 for x0 = -0.01)
+    assert np.max(np.abs(r.v - np.clip(x0, 0.0, 1.0))) < 1e-7
+
+
+def _one_dim_problem(a, b, w, b1, v, c):
+    nn = lambda x: v * np.tanh(w * x + b1) + c  # noqa: E731
+    dnn = lambda x: v * w * (1 - np.tanh(w * x + b1) ** 2)  # noqa: E731
+    d2nn = lambda x: v * w * w * (-2 * np.tanh(w * x + b1) * (1 - np.tanh(w * x + b1) ** 2))  # noqa: E731
+    p = ipm.Problem(
+        2, 1, np.array([-2.0, -np.inf]), np.array([2.0, np.inf]), np.array([0.0, nn(0.0)]),
+        lambda z: (z[0] - a) ** 2 + (z[1] - b) ** 2,
+        lambda z: np.array([2 * (z[0] - a), 2 * (z[1] - b)]),
+        lambda z: 2 * np.eye(2),
+        lambda z: np.array([z[1] - nn(z[0])]),
+        lambda z: np.array([[-dnn(z[0]), 1.0]]),
+        lambda z, lam: np.array([[-lam[0] * d2nn(z[0]), 0.0], [0.0, 0.0]]))
+    return p, nn
+
+
+def test_one_dimensional_reduction_against_scipy():
+    from scipy.optimize import minimize_scalar
+    a, b, w, b1, v, c = 0.8, 1.5, 2.0, -0.3, 1.2, 0.1
+    p, nn = _one_dim_problem(a, b, w, b1, v, c)
+    r = ipm.solve(p)
+    assert r.status == ipm.OPTIMAL
+    h = lambda x: (x - a) ** 2 + (nn(x) - b) ** 2  # noqa: E731
+    grid = np.linspace(-2, 2, 4001)
+    x_best = grid[np.argmin(h(grid))]
+    s = minimize_scalar(h, bounds=(max(-2, x_best - 0.01), min(2, x_best + 0.01)), method="bounded",
+                        options={"xatol": 1e-12})
+    assert abs(r.v[0] - s.x) < 1e-5
+    assert abs(r.obj - s.fun) < 1e-8
+    assert abs(r.v[1] - nn(r.v[0])) < 1e-7
+
+
+def test_linear_network_qp_against_slsqp():
+    from scipy.optimize import minimize
+    spec = MLPSpec([30, 16, 4], ["identity", "identity"])
+    mlp = make_mlp(spec, seed=4, tag="qp", bias_std=0.3)
+    x0 = synth.uniform01(synth.derive_key(4, "qp-x0"), 30)
+    t, margin = 1, 0.1      # class 1 loses at x0 and can win by 1.1 inside the box (LP check)
+    r = ipm.solve(problems.adversarial(mlp, x0, target=t, margin=margin))
+    assert r.status == ipm.OPTIMAL
+    P = mlp.W[1] @ mlp.W[0]
+    q = mlp.W[1] @ mlp.b[0] + mlp.b[1]
+    cons = [{"type": "ineq", "fun": (lambda x, j=j: (P[t] - P[j]) @ x + q[t] - q[j] - margin),
+             "jac": (lambda x, j=j: P[t] - P[j])} for j in range(4) if j != t]
+    s = minimize(lambda x: (x - x0) @ (x - x0), x0, jac=lambda x: 2 * (x - x0), bounds=[(0, 1)] * 30,
+                 constraints=cons, method="SLSQP", options={"ftol": 1e-14, "maxiter": 500})
+    assert s.success
+    assert abs(r.obj - s.fun) <= 1e-6 * max(1.0, abs(s.fun))
+    assert np.max(np.abs(r.v[:30] - s.x)) < 1e-4
+
+
+def test_adversarial_tiny_kkt_certificate():
+    """784 -> 128 -> 128 -> 10 tanh: the solution satisfies the KKT conditions of Eq. 1 to 1e-6."""
+    mlp = make_mlp(synth.TINY, seed=0)
+    d = synth.adversarial_data(seed=0)
+    p = problems.adversarial(mlp, d.x0, d.target, d.margin)
+    r = ipm.solve(p)
+    assert r.status == ipm.OPTIMAL, ipm.STATUS_NAMES[r.status]
+    n_in, n_out = 784, 10
+    x, y, s = r.v[:n_in], r.v[n_in:n_in + n_out], r.v[n_in + n_out:]
+    # feasibility, from the definitions
+    assert np.max(np.abs(y - onn.value(mlp, x))) < 1e-6
+    others = [j for j in range(n_out) if j != d.target]
+    assert np.all(y[d.target] - y[others] - d.margin - s > -1e-6)
+    assert np.all(y[d.target] - y[others] - d.margin - s < 1e-6)
+    assert np.all((x >= 0) & (x <= 1)) and np.all(s >= 0)
+    # stationarity: 2(x - x0) - J^T lam_nn - zL + zU = 0, lam_nn + E^T lam_m = 0, -lam_m - zs = 0
+    lam_nn, lam_m = r.lam[:n_out], r.lam[n_out:]
+    J = onn.jacobian(mlp, x)
+    rx = 2 * (x - d.x0) - J.T @ lam_nn - r.zL[:n_in] + r.zU[:n_in]
+    E = np.zeros((len(others), n_out))
+    for i, j in enumerate(others):
+        E[i, d.target], E[i, j] = 1.0, -1.0
+    ry = lam_nn + E.T @ lam_m
+    rs = -lam_m - r.zL[n_in + n_out:]
+    scale = max(100.0, (np.abs(r.lam).sum() + np.abs(r.zL).sum() + np.abs(r.zU).sum()) / (19 + 784 * 2 + 9)) / 100.0
+    assert max(np.abs(rx).max(), np.abs(ry).max(), np.abs(rs).max()) / scale < 1e-6
+    # complementarity
+    assert np.max(np.abs(x * r.zL[:n_in])) < 1e-6 and np.max(np.abs((1 - x) * r.zU[:n_in])) < 1e-6
+    assert r.iters < 100
+    assert 0.0 < r.obj < 50.0
+
+
+def test_status_codes():
+    x0 = np.array([0.3, 1.4])
+    r = ipm.solve(problems.box_projection(x0), ipm.Options(max_iter=2))
+    assert r.status == ipm.MAX_ITER
+    p = problems.box_projection(x0)
+    p.f = lambda v: float("nan")
+    assert ipm.solve(p).status == ipm.NONFINITE
