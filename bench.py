@@ -244,6 +244,8 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)   # every launch and both timing events go on this stream
+    torch.cuda.set_stream(stream)
     from paper_2509_22462_gb300 import build as B
     if rank == 0:
         B.build()

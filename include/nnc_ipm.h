@@ -1,0 +1,98 @@
+/*
+ * nnc_ipm.h -- host FP64 interior-point driver of libnnc for problems with an embedded network
+ * constraint in the reduced-space form (Eq. 5): the network enters as y - NN(x) = 0 and its
+ * value, Jacobian and Hessian of lambda^T NN come from the nnc_* oracles of nnc.h.
+ *
+ * The method is a primal-dual barrier method for Eq. 1 whose Newton system is Eq. 2 with the
+ * unstated terms alpha, beta read as IPOPT's barrier terms (Waechter & Biegler 2006): inertia
+ * correction delta_w, barrier parameter mu with monotone decrease, fraction to the boundary,
+ * backtracking on an exact-penalty merit function.  The KKT factorization, the merit checks
+ * and all optimizer state stay in FP64 on the host; the constraint residual y - NN(x) is
+ * always evaluated with the FP64 weights (nnc_residual), whatever the net's precision form.
+ *
+ * Ownership: all pointers are host memory owned by the caller.  Errors: negative nnc_status
+ * for bad arguments or a failing oracle call; the solver's own outcome is in result->status.
+ */
+#ifndef NNC_IPM_H
+#define NNC_IPM_H
+
+#include "nnc.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* result->status */
+#define NNC_IPM_OPTIMAL 0           /* scaled KKT error <= tol */
+#define NNC_IPM_MAX_ITER 1          /* iteration limit reached */
+#define NNC_IPM_LINESEARCH_FAILED 2 /* max_ls_failures consecutive line searches failed */
+#define NNC_IPM_NONFINITE 3         /* NaN or Inf in a function or derivative */
+#define NNC_IPM_INERTIA_FAILED 4    /* delta_w exceeded delta_w_max */
+#define NNC_IPM_EVAL_ERROR 5        /* an nnc_* oracle call failed (see nnc_last_error) */
+
+typedef struct {
+  double tol;              /* 1e-6, the paper's IPOPT tolerance (Section 5.1) */
+  int max_iter;            /* 300 */
+  double mu0;              /* 0.1 */
+  double kappa_mu;         /* 0.2 */
+  double theta_mu;         /* 1.5 */
+  double kappa_eps;        /* 10 */
+  double tau_min;          /* 0.99 */
+  double kappa1, kappa2;   /* 1e-2: push of the start point into the bounds */
+  double s_max;            /* 100: scaling of the optimality error */
+  double eta;              /* 1e-4: Armijo constant */
+  double delta_w0, delta_w_min, delta_w_max;         /* 1e-4, 1e-20, 1e40 */
+  double kappa_w_plus, kappa_w_plus_bar, kappa_w_minus; /* 8, 100, 1/3 */
+  double kappa_sigma;      /* 1e10: safeguard of the bound multipliers */
+  int max_backtracks;      /* 40 */
+  int max_ls_failures;     /* 5 */
+  int verbose;             /* print one line per iteration */
+} nnc_ipm_options;
+
+typedef struct {
+  int status;              /* NNC_IPM_* */
+  int iters;
+  double obj;              /* objective at the returned point */
+  double kkt_error;        /* scaled optimality error E_0 at the returned point */
+  double solve_seconds;    /* wall time of the solve */
+  /* breakdown of Table 4: Function (constraint residuals), Jacobian, Hessian, Solver
+   * (factorization, solves, step computation); seconds and number of calls */
+  double t_function, t_jacobian, t_hessian, t_solver;
+  int n_function, n_jacobian, n_hessian;
+} nnc_ipm_result;
+
+void nnc_ipm_default_options(nnc_ipm_options* opt);
+
+/* The KKT system of Eq. 2 in the structured form the driver factorizes (host FP64):
+ *   K = [[W_DD + diag(sigma_D) + dw I, 0,                          A_D^T],
+ *        [0,                           diag(W_SS + sigma_S) + dw I, A_S^T],
+ *        [A_D,                         A_S,                         -dc I]]
+ * with nd dense-block variables, ns small-block variables and m constraints (n = nd + ns).
+ *   WDD : nd x nd row-major (symmetric);  WSS, sigma : ns and n entries;
+ *   AD  : m x nd row-major;  AS : m x ns row-major (NULL = zero when the size is 0);
+ *   rhs_sol : n + m doubles, the right-hand side on entry, the solution on return (left
+ *             unchanged when K is singular);
+ *   inertia : 4 ints (may be NULL): positive, negative and zero eigenvalue counts of K, and 1
+ *             if the whole matrix had to be factorized (W_DD block not positive definite).
+ * Factorization: blocked Cholesky of the first block and Bunch-Kaufman LDL^T of its Schur
+ * complement, or Bunch-Kaufman of all of K; the inertia is exact either way (Sylvester). */
+int nnc_kkt_solve(int nd, int ns, int m, const double* WDD, const double* WSS, const double* sigma,
+                  const double* AD, const double* AS, double delta_w, double delta_c,
+                  double* rhs_sol, int* inertia);
+
+/* The adversarial problem (a synthetic variant of Eq. 7): variables v = (x, y, s) with
+ * x in [0,1]^n_in, y in R^n_out, s in R^(n_out-1), s >= 0;
+ *   min ||x - x0||^2  s.t.  y - NN(x) = 0,  y_t - y_j - margin - s_j = 0 for j != t.
+ * Start: x = x0, y = NN(x0) (FP64), s_j = max(y_t - y_j - margin, 1e-2).
+ *   x0      : n_in doubles.      target : t in [0, n_out).     opt : NULL for defaults.
+ *   v_out   : n_in + 2 n_out - 1 doubles (may be NULL), the final (x, y, s).
+ *   lam_out : 2 n_out - 1 doubles (may be NULL), multipliers of (y - NN(x), margins).
+ *   result  : may be NULL. */
+int nnc_ipm_adversarial(nnc_net* net, const double* x0, int target, double margin,
+                        const nnc_ipm_options* opt, double* v_out, double* lam_out,
+                        nnc_ipm_result* result);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NNC_IPM_H */

@@ -32,6 +32,8 @@ def _flags():
 def _compile(src, verbose=False):
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
     cmd = [_nvcc()] + _flags() + ["-c", src, "-o", obj]
+    if src.endswith(".cpp"):
+        cmd += ["-Xcompiler", "-fopenmp"]
     if verbose:
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)

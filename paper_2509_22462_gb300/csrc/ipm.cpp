@@ -1,0 +1,793 @@
+// Host FP64 primal-dual interior-point driver (Eq. 1 with the Newton system of Eq. 2).
+//
+// The paper leaves the terms alpha and beta of Eq. 2 unstated; they are read as the barrier
+// terms of IPOPT (Waechter & Biegler 2006): alpha = Sigma + delta_w I with
+// Sigma = Z_L (V - L)^-1 + Z_U (U - V)^-1 and an inertia correction delta_w, beta the barrier
+// gradient.  Steps per iteration: evaluate, scaled optimality error (s_max = 100) and barrier
+// update (kappa_eps = 10, kappa_mu = 0.2, theta_mu = 1.5), inertia-corrected KKT factorization
+// (inertia must be (n, m, 0)), Newton step, fraction to the boundary (tau = max(0.99, 1 - mu)),
+// backtracking on the exact-penalty merit function (Armijo 1e-4), update and z safeguard
+// (kappa_Sigma = 1e10).
+//
+// The network constraint makes the variables split into a dense block D (the network inputs x,
+// whose Hessian block is the dense n_in x n_in matrix of Eq. 6) and a small block S (outputs,
+// slacks) with diagonal Hessian.  The KKT matrix K = [[K11, K12], [K12^T, K22]] with
+// K11 = W_DD + Sigma_D + delta_w I is factorized as: blocked Cholesky of K11 (parallel on the
+// host cores), Schur complement S = K22 - K12^T K11^-1 K12, Bunch-Kaufman LDL^T of S.  If K11 is
+// positive definite, inertia(K) = (n_D, 0, 0) + inertia(S) (Haynsworth); otherwise the whole K
+// is factorized by Bunch-Kaufman.  Either way the inertia is exact.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <string>
+#include <vector>
+
+#include "../../include/nnc.h"
+#include "../../include/nnc_ipm.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+double secs(Clock::time_point a, Clock::time_point b) {
+  return std::chrono::duration<double>(b - a).count();
+}
+
+// ---------------------------------------------------------------- dense linear algebra
+// Row-major n x n, lower triangle.  Returns false if the matrix is not positive definite.
+bool cholesky(int n, double* A) {
+  const int NB = 64;
+  for (int kb = 0; kb < n; kb += NB) {
+    const int nb = std::min(NB, n - kb);
+    // diagonal block (unblocked, right-looking)
+    for (int j = kb; j < kb + nb; ++j) {
+      double d = A[(size_t)j * n + j];
+      if (!(d > 0.0) || !std::isfinite(d)) return false;
+      d = std::sqrt(d);
+      A[(size_t)j * n + j] = d;
+      for (int i = j + 1; i < kb + nb; ++i) A[(size_t)i * n + j] /= d;
+      for (int i = j + 1; i < kb + nb; ++i) {
+        const double lij = A[(size_t)i * n + j];
+        for (int p = j + 1; p <= i; ++p) A[(size_t)i * n + p] -= lij * A[(size_t)p * n + j];
+      }
+    }
+    const int r0 = kb + nb;
+    // panel below: L21 = A21 L11^-T (row by row)
+#pragma omp parallel for schedule(static)
+    for (int i = r0; i < n; ++i) {
+      double* ai = A + (size_t)i * n;
+      for (int j = kb; j < kb + nb; ++j) {
+        const double* aj = A + (size_t)j * n;
+        double s = ai[j];
+        for (int p = kb; p < j; ++p) s -= ai[p] * aj[p];
+        ai[j] = s / aj[j];
+      }
+    }
+    // trailing update A22 -= L21 L21^T (lower triangle)
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int i = r0; i < n; ++i) {
+      double* ai = A + (size_t)i * n;
+      const double* li = ai + kb;
+      for (int p = r0; p <= i; ++p) {
+        const double* lp = A + (size_t)p * n + kb;
+        double s = 0.0;
+        for (int q = 0; q < nb; ++q) s += li[q] * lp[q];
+        ai[p] -= s;
+      }
+    }
+  }
+  return true;
+}
+
+// L y = b in place (L lower, row-major n x n), for r right-hand sides stored row-major n x r.
+void lower_solve(int n, const double* L, int r, double* B) {
+#pragma omp parallel for schedule(static) if (r >= 8)
+  for (int c0 = 0; c0 < r; c0 += 8) {
+    const int c1 = std::min(r, c0 + 8);
+    for (int i = 0; i < n; ++i) {
+      const double* li = L + (size_t)i * n;
+      double* bi = B + (size_t)i * r;
+      for (int j = 0; j < i; ++j) {
+        const double l = li[j];
+        if (l == 0.0) continue;
+        const double* bj = B + (size_t)j * r;
+        for (int c = c0; c < c1; ++c) bi[c] -= l * bj[c];
+      }
+      for (int c = c0; c < c1; ++c) bi[c] /= li[i];
+    }
+  }
+}
+
+// L^T x = y in place for one right-hand side.
+void upper_solve_lt(int n, const double* L, double* x) {
+  for (int i = n - 1; i >= 0; --i) {
+    x[i] /= L[(size_t)i * n + i];
+    const double xi = x[i];
+    const double* li = L + (size_t)i * n;
+    for (int j = 0; j < i; ++j) x[j] -= li[j] * xi;
+  }
+}
+
+void lower_solve1(int n, const double* L, double* x) {
+  for (int i = 0; i < n; ++i) {
+    const double* li = L + (size_t)i * n;
+    double s = x[i];
+    for (int j = 0; j < i; ++j) s -= li[j] * x[j];
+    x[i] = s / li[i];
+  }
+}
+
+// Bunch-Kaufman symmetric indefinite factorization P A P^T = L D L^T (Golub & Van Loan,
+// "Matrix Computations", Sec. 4.4), full symmetric storage, row-major.  Records the pivot
+// sequence and the inertia of A (via Sylvester's law from the 1x1 / 2x2 blocks of D).
+struct BK {
+  int n = 0;
+  std::vector<double> A;     // factored in place: L below the diagonal, D on/near it
+  std::vector<int> perm;     // row i of P A P^T is row perm[i] of A
+  std::vector<int> step;     // 1 or 2 at the first index of each pivot block
+  int npos = 0, nneg = 0, nzero = 0;
+  bool factor(int n_, const double* src, double zero_tol) {
+    n = n_;
+    A.assign(src, src + (size_t)n * n);
+    perm.resize(n);
+    step.assign(n, 0);
+    for (int i = 0; i < n; ++i) perm[i] = i;
+    npos = nneg = nzero = 0;
+    const double alpha = (1.0 + std::sqrt(17.0)) / 8.0;
+    auto a = [&](int i, int j) -> double& { return A[(size_t)i * n + j]; };
+    auto swap_rc = [&](int r, int s) {
+      if (r == s) return;
+      for (int j = 0; j < n; ++j) std::swap(a(r, j), a(s, j));
+      for (int i = 0; i < n; ++i) std::swap(a(i, r), a(i, s));
+      std::swap(perm[r], perm[s]);
+    };
+    int k = 0;
+    while (k < n) {
+      const double absakk = std::fabs(a(k, k));
+      int imax = k;
+      double colmax = 0.0;
+      for (int i = k + 1; i < n; ++i)
+        if (std::fabs(a(i, k)) > colmax) {
+          colmax = std::fabs(a(i, k));
+          imax = i;
+        }
+      int kstep = 1, kp = k;
+      if (std::max(absakk, colmax) <= zero_tol) {
+        ++nzero;
+        step[k] = 1;
+        a(k, k) = 0.0;
+        for (int i = k + 1; i < n; ++i) a(i, k) = 0.0;
+        ++k;
+        continue;
+      }
+      if (absakk >= alpha * colmax) {
+        kp = k;
+      } else {
+        double rowmax = 0.0;
+        for (int j = k; j < n; ++j)
+          if (j != imax) rowmax = std::max(rowmax, std::fabs(a(imax, j)));
+        if (absakk >= alpha * colmax * (colmax / rowmax)) {
+          kp = k;
+        } else if (std::fabs(a(imax, imax)) >= alpha * rowmax) {
+          kp = imax;
+        } else {
+          kp = imax;
+          kstep = 2;
+        }
+      }
+      const int kk = k + kstep - 1;
+      swap_rc(kk, kp);
+      step[k] = kstep;
+      if (kstep == 1) {
+        const double d = a(k, k);
+        if (std::fabs(d) <= zero_tol) ++nzero;
+        else if (d > 0) ++npos;
+        else ++nneg;
+        const double inv = d != 0.0 ? 1.0 / d : 0.0;
+        // trailing update A22 -= a21 a21^T / d (full symmetric storage)
+#pragma omp parallel for schedule(static) if (n - k > 256)
+        for (int i = k + 1; i < n; ++i) {
+          const double f = a(i, k) * inv;
+          if (f == 0.0) continue;
+          double* ai = &a(i, 0);
+          for (int j = k + 1; j < n; ++j) ai[j] -= f * A[(size_t)j * n + k];
+        }
+        for (int i = k + 1; i < n; ++i) a(i, k) *= inv;
+      } else {
+        const double d11 = a(k, k), d21 = a(k + 1, k), d22 = a(k + 1, k + 1);
+        const double det = d11 * d22 - d21 * d21;
+        if (det < 0) {
+          ++npos;
+          ++nneg;
+        } else if (std::fabs(det) <= zero_tol * zero_tol) {
+          nzero += 2;
+        } else if (d11 + d22 > 0) {
+          npos += 2;
+        } else {
+          nneg += 2;
+        }
+        const double i11 = d22 / det, i22 = d11 / det, i21 = -d21 / det;
+        // W = A(k+2:, k:k+2); L = W D^-1; A22 -= W D^-1 W^T
+        std::vector<double> l1(n, 0.0), l2(n, 0.0);
+        for (int i = k + 2; i < n; ++i) {
+          const double w1 = a(i, k), w2 = a(i, k + 1);
+          l1[i] = w1 * i11 + w2 * i21;
+          l2[i] = w1 * i21 + w2 * i22;
+        }
+#pragma omp parallel for schedule(static) if (n - k > 256)
+        for (int i = k + 2; i < n; ++i) {
+          double* ai = &a(i, 0);
+          const double f1 = l1[i], f2 = l2[i];
+          for (int j = k + 2; j < n; ++j) ai[j] -= f1 * A[(size_t)j * n + k] + f2 * A[(size_t)j * n + k + 1];
+        }
+        for (int i = k + 2; i < n; ++i) {
+          a(i, k) = l1[i];
+          a(i, k + 1) = l2[i];
+        }
+      }
+      k += kstep;
+    }
+    return true;
+  }
+  // Solve A x = b (b overwritten by x).
+  void solve(double* b) const {
+    std::vector<double> y(n);
+    for (int i = 0; i < n; ++i) y[i] = b[perm[i]];
+    auto a = [&](int i, int j) { return A[(size_t)i * n + j]; };
+    // L y' = y
+    for (int k = 0; k < n;) {
+      const int s = step[k];
+      for (int c = k; c < k + s; ++c)
+        for (int i = k + s; i < n; ++i) y[i] -= a(i, c) * y[c];
+      k += s;
+    }
+    // D z = y'
+    for (int k = 0; k < n;) {
+      if (step[k] == 1) {
+        const double d = a(k, k);
+        y[k] = d != 0.0 ? y[k] / d : 0.0;
+        k += 1;
+      } else {
+        const double d11 = a(k, k), d21 = a(k + 1, k), d22 = a(k + 1, k + 1);
+        const double det = d11 * d22 - d21 * d21;
+        const double y1 = y[k], y2 = y[k + 1];
+        y[k] = (d22 * y1 - d21 * y2) / det;
+        y[k + 1] = (-d21 * y1 + d11 * y2) / det;
+        k += 2;
+      }
+    }
+    // L^T x = z
+    int k = n - 1;
+    while (k >= 0) {
+      const int k0 = (k >= 1 && step[k - 1] == 2) ? k - 1 : k;
+      for (int c = k0; c <= k; ++c)
+        for (int i = k + 1; i < n; ++i) y[c] -= a(i, c) * y[i];
+      k = k0 - 1;
+    }
+    for (int i = 0; i < n; ++i) b[perm[i]] = y[i];
+  }
+};
+
+
+// ---------------------------------------------------------------- structured KKT solver
+// K = [[W_DD + diag(sig_D) + dw I, 0, A_D^T], [0, diag(W_SS + sig_S) + dw I, A_S^T],
+//      [A_D, A_S, -dc I]], n = nd + ns primal rows and m constraint rows.
+struct KktSolver {
+  int nd = 0, ns = 0, m = 0, n = 0, r = 0;
+  std::vector<double> K11, K12, Y, Sm, Kfull, tmp;
+  BK bkS, bkF;
+  bool full = false;
+  int npos = 0, nneg = 0, nzero = 0;
+  void factor(int nd_, int ns_, int m_, const double* WDD, const double* WSS, const double* sig,
+              const double* AD, const double* AS, double dw, double dc, double zero_tol) {
+    nd = nd_;
+    ns = ns_;
+    m = m_;
+    n = nd + ns;
+    r = ns + m;
+    K11.assign((size_t)nd * nd, 0.0);
+    std::memcpy(K11.data(), WDD, sizeof(double) * nd * nd);
+    for (int i = 0; i < nd; ++i) K11[(size_t)i * nd + i] += sig[i] + dw;
+    K12.assign((size_t)nd * r, 0.0);
+    for (int i = 0; i < nd; ++i)
+      for (int j = 0; j < m; ++j) K12[(size_t)i * r + ns + j] = AD[(size_t)j * nd + i];
+    const bool pd = nd == 0 || cholesky(nd, K11.data());
+    if (pd) {
+      Y = K12;
+      if (nd) lower_solve(nd, K11.data(), r, Y.data());
+      Sm.assign((size_t)r * r, 0.0);
+      for (int a = 0; a < ns; ++a) Sm[(size_t)a * r + a] = WSS[a] + sig[nd + a] + dw;
+      for (int j = 0; j < m; ++j)
+        for (int a = 0; a < ns; ++a) {
+          Sm[(size_t)(ns + j) * r + a] = AS[(size_t)j * ns + a];
+          Sm[(size_t)a * r + ns + j] = AS[(size_t)j * ns + a];
+        }
+      for (int j = 0; j < m; ++j) Sm[(size_t)(ns + j) * r + ns + j] = -dc;
+#pragma omp parallel for schedule(dynamic, 4) if (r >= 64)
+      for (int a = 0; a < r; ++a)
+        for (int b = 0; b <= a; ++b) {
+          double s = 0;
+          for (int i = 0; i < nd; ++i) s += Y[(size_t)i * r + a] * Y[(size_t)i * r + b];
+          Sm[(size_t)a * r + b] -= s;
+          if (b != a) Sm[(size_t)b * r + a] -= s;
+        }
+      bkS.factor(r, Sm.data(), zero_tol);
+      npos = nd + bkS.npos;
+      nneg = bkS.nneg;
+      nzero = bkS.nzero;
+      full = false;
+    } else {
+      const int N = n + m;
+      Kfull.assign((size_t)N * N, 0.0);
+      for (int i = 0; i < nd; ++i)
+        for (int j = 0; j < nd; ++j) Kfull[(size_t)i * N + j] = WDD[(size_t)i * nd + j];
+      for (int i = 0; i < n; ++i) Kfull[(size_t)i * N + i] += sig[i] + dw + (i >= nd ? WSS[i - nd] : 0.0);
+      for (int j = 0; j < m; ++j) {
+        for (int i = 0; i < nd; ++i)
+          Kfull[(size_t)(n + j) * N + i] = Kfull[(size_t)i * N + n + j] = AD[(size_t)j * nd + i];
+        for (int a = 0; a < ns; ++a)
+          Kfull[(size_t)(n + j) * N + nd + a] = Kfull[(size_t)(nd + a) * N + n + j] = AS[(size_t)j * ns + a];
+        Kfull[(size_t)(n + j) * N + n + j] = -dc;
+      }
+      bkF.factor(N, Kfull.data(), zero_tol);
+      npos = bkF.npos;
+      nneg = bkF.nneg;
+      nzero = bkF.nzero;
+      full = true;
+    }
+  }
+  // rhs (n + m) -> solution, in place
+  void solve(double* rhs) {
+    if (full) {
+      bkF.solve(rhs);
+      return;
+    }
+    // [K11 K12; K12^T K22] [u; w] = [r1; r2]: w = S^-1 (r2 - Y^T L^-1 r1), u = K11^-1 (r1 - K12 w)
+    tmp.assign(rhs, rhs + nd);
+    if (nd) lower_solve1(nd, K11.data(), tmp.data());
+    std::vector<double> w(r);
+    for (int a = 0; a < r; ++a) {
+      double s = 0;
+      for (int i = 0; i < nd; ++i) s += Y[(size_t)i * r + a] * tmp[i];
+      w[a] = rhs[nd + a] - s;
+    }
+    bkS.solve(w.data());
+    for (int i = 0; i < nd; ++i) {
+      double s = rhs[i];
+      for (int a = 0; a < r; ++a) s -= K12[(size_t)i * r + a] * w[a];
+      tmp[i] = s;
+    }
+    if (nd) {
+      lower_solve1(nd, K11.data(), tmp.data());
+      upper_solve_lt(nd, K11.data(), tmp.data());
+    }
+    for (int i = 0; i < nd; ++i) rhs[i] = tmp[i];
+    for (int a = 0; a < r; ++a) rhs[nd + a] = w[a];
+  }
+};
+
+// ---------------------------------------------------------------- problem interface
+// min f(v) s.t. c(v) = 0, lb <= v <= ub;  v = [D block (nd) | S block (ns)].
+struct IpmProblem {
+  int nd = 0, ns = 0, m = 0;
+  std::vector<double> lb, ub, v0;
+  virtual ~IpmProblem() = default;
+  virtual double f(const double* v) = 0;
+  virtual void grad_f(const double* v, double* g) = 0;
+  virtual int cons(const double* v, double* c) = 0;                         // "Function"
+  virtual int jac(const double* v, double* AD, double* AS) = 0;             // m x nd, m x ns
+  // W_DD (nd x nd, full) and diag(W_SS) (ns) of grad^2 f + sum_i lam_i grad^2 c_i
+  virtual int hess(const double* v, const double* lam, double* WDD, double* WSS) = 0;
+};
+
+struct Timers {
+  double fn = 0, jac = 0, hess = 0, solver = 0;
+  int n_fn = 0, n_jac = 0, n_hess = 0;
+};
+
+double inf_norm(const std::vector<double>& x) {
+  double s = 0;
+  for (double v : x) s = std::max(s, std::fabs(v));
+  return s;
+}
+
+int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_out,
+              std::vector<double>& lam_out, nnc_ipm_result* res) {
+  const auto t_start = Clock::now();
+  Timers T;
+  const int nd = p.nd, ns = p.ns, n = nd + ns, m = p.m, r = ns + m;
+  std::vector<char> hasL(n), hasU(n);
+  std::vector<double> lb0(n, 0.0), ub0(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    hasL[i] = std::isfinite(p.lb[i]);
+    hasU[i] = std::isfinite(p.ub[i]);
+    if (hasL[i]) lb0[i] = p.lb[i];
+    if (hasU[i]) ub0[i] = p.ub[i];
+  }
+  std::vector<double> v(p.v0);
+  for (int i = 0; i < n; ++i) {
+    const double width = (hasL[i] && hasU[i]) ? ub0[i] - lb0[i] : INFINITY;
+    if (hasL[i]) v[i] = std::max(v[i], lb0[i] + std::min(o.kappa1 * std::max(1.0, std::fabs(lb0[i])), o.kappa2 * width));
+    if (hasU[i]) v[i] = std::min(v[i], ub0[i] - std::min(o.kappa1 * std::max(1.0, std::fabs(ub0[i])), o.kappa2 * width));
+  }
+  std::vector<double> zL(n), zU(n), lam(m, 0.0);
+  for (int i = 0; i < n; ++i) {
+    zL[i] = hasL[i] ? 1.0 : 0.0;
+    zU[i] = hasU[i] ? 1.0 : 0.0;
+  }
+  double mu = o.mu0, tau = std::max(o.tau_min, 1.0 - mu), nu = 1.0, delta_w_last = 0.0;
+  int ls_fail = 0, status = NNC_IPM_MAX_ITER, it = 0;
+  double E0 = INFINITY;
+  std::vector<double> g(n), c(m), AD((size_t)m * nd), AS((size_t)m * ns), WDD((size_t)nd * nd),
+      WSS(ns), vt(n), ct(m), rhs(n + m), sol(n + m), dv(n), dl(m), dzL(n), dzU(n), sL(n), sU(n),
+      SigL(n), SigU(n), sig(n), gphi(n);
+  KktSolver kkt;
+  (void)r;
+  auto slackL = [&](const std::vector<double>& x, int i) { return hasL[i] ? x[i] - lb0[i] : 1.0; };
+  auto slackU = [&](const std::vector<double>& x, int i) { return hasU[i] ? ub0[i] - x[i] : 1.0; };
+  auto timed = [&](double& acc, int& cnt, auto fn) {
+    const auto a = Clock::now();
+    const int rc = fn();
+    acc += secs(a, Clock::now());
+    ++cnt;
+    return rc;
+  };
+  auto errors = [&](double mu_) {
+    int nb = 0;
+    double sl = 0, sz = 0;
+    for (int j = 0; j < m; ++j) sl += std::fabs(lam[j]);
+    for (int i = 0; i < n; ++i) {
+      nb += hasL[i] + hasU[i];
+      sz += std::fabs(zL[i]) + std::fabs(zU[i]);
+    }
+    const double s_d = std::max(o.s_max, (sl + sz) / std::max(1, m + nb)) / o.s_max;
+    const double s_c = std::max(o.s_max, sz / std::max(1, nb)) / o.s_max;
+    double rd = 0, comp = 0, cinf = 0;
+    for (int i = 0; i < n; ++i) {
+      double d = g[i] - zL[i] + zU[i];
+      for (int j = 0; j < m; ++j) d += (i < nd ? AD[(size_t)j * nd + i] : AS[(size_t)j * ns + i - nd]) * lam[j];
+      rd = std::max(rd, std::fabs(d));
+      if (hasL[i]) comp = std::max(comp, std::fabs((v[i] - lb0[i]) * zL[i] - mu_));
+      if (hasU[i]) comp = std::max(comp, std::fabs((ub0[i] - v[i]) * zU[i] - mu_));
+    }
+    for (int j = 0; j < m; ++j) cinf = std::max(cinf, std::fabs(c[j]));
+    return std::max(std::max(rd / s_d, cinf), comp / s_c);
+  };
+  auto merit = [&](const std::vector<double>& x, double fx, const std::vector<double>& cx, double nu_) {
+    double phi = fx;
+    for (int i = 0; i < n; ++i) {
+      if (hasL[i]) {
+        const double s = x[i] - lb0[i];
+        if (!(s > 0)) return (double)INFINITY;
+        phi -= mu * std::log(s);
+      }
+      if (hasU[i]) {
+        const double s = ub0[i] - x[i];
+        if (!(s > 0)) return (double)INFINITY;
+        phi -= mu * std::log(s);
+      }
+    }
+    double c1 = 0;
+    for (int j = 0; j < m; ++j) c1 += std::fabs(cx[j]);
+    return phi + nu_ * c1;
+  };
+
+  bool have_c = false;
+  for (it = 0; it <= o.max_iter; ++it) {
+    const double fv = p.f(v.data());
+    p.grad_f(v.data(), g.data());
+    if (!have_c && m) {
+      if (timed(T.fn, T.n_fn, [&] { return p.cons(v.data(), c.data()); })) { status = NNC_IPM_EVAL_ERROR; break; }
+    }
+    if (m && timed(T.jac, T.n_jac, [&] { return p.jac(v.data(), AD.data(), AS.data()); })) { status = NNC_IPM_EVAL_ERROR; break; }
+    bool finite = std::isfinite(fv);
+    for (double x : g) finite &= std::isfinite(x);
+    for (double x : c) finite &= std::isfinite(x);
+    for (double x : AD) finite &= std::isfinite(x);
+    if (!finite) { status = NNC_IPM_NONFINITE; break; }
+    E0 = errors(0.0);
+    if (o.verbose)
+      std::printf("iter %3d  f %.10e  inf_pr %.3e  E0 %.3e  mu %.1e\n", it, fv, m ? inf_norm(c) : 0.0, E0, mu);
+    if (E0 <= o.tol) { status = NNC_IPM_OPTIMAL; break; }
+    if (it == o.max_iter) break;
+    double Emu = errors(mu);
+    while (Emu <= o.kappa_eps * mu && mu > o.tol / 10.0) {
+      mu = std::max(o.tol / 10.0, std::min(o.kappa_mu * mu, std::pow(mu, o.theta_mu)));
+      tau = std::max(o.tau_min, 1.0 - mu);
+      Emu = errors(mu);
+    }
+    if (timed(T.hess, T.n_hess, [&] { return p.hess(v.data(), lam.data(), WDD.data(), WSS.data()); })) { status = NNC_IPM_EVAL_ERROR; break; }
+    const auto t_lin = Clock::now();
+    for (int i = 0; i < n; ++i) {
+      sL[i] = slackL(v, i);
+      sU[i] = slackU(v, i);
+      SigL[i] = hasL[i] ? zL[i] / sL[i] : 0.0;
+      SigU[i] = hasU[i] ? zU[i] / sU[i] : 0.0;
+      gphi[i] = g[i] - (hasL[i] ? mu / sL[i] : 0.0) + (hasU[i] ? mu / sU[i] : 0.0);
+    }
+    for (int i = 0; i < n; ++i) {
+      double d = gphi[i];
+      for (int j = 0; j < m; ++j) d += (i < nd ? AD[(size_t)j * nd + i] : AS[(size_t)j * ns + i - nd]) * lam[j];
+      rhs[i] = -d;
+    }
+    for (int j = 0; j < m; ++j) rhs[n + j] = -c[j];
+    // --- inertia-corrected factorization
+    double delta_w = 0.0, delta_c = 0.0;
+    bool first = true, ok = false;
+    double scale = 1.0;
+    for (size_t i = 0; i < WDD.size(); ++i) scale = std::max(scale, std::fabs(WDD[i]));
+    for (int i = 0; i < n; ++i) {
+      sig[i] = SigL[i] + SigU[i];
+      scale = std::max(scale, sig[i]);
+    }
+    for (double x : AD) scale = std::max(scale, std::fabs(x));
+    for (double x : AS) scale = std::max(scale, std::fabs(x));
+    const double zero_tol = 1e-14 * scale;
+    while (true) {
+      kkt.factor(nd, ns, m, WDD.data(), WSS.data(), sig.data(), AD.data(), AS.data(), delta_w,
+                 delta_c, zero_tol);
+      if (kkt.npos == n && kkt.nneg == m && kkt.nzero == 0) { ok = true; break; }
+      if (kkt.nzero > 0 && delta_c == 0.0 && m) delta_c = 1e-8 * std::pow(mu, 0.25);
+      if (first) {
+        delta_w = delta_w_last == 0.0 ? o.delta_w0 : std::max(o.delta_w_min, o.kappa_w_minus * delta_w_last);
+        first = false;
+      } else {
+        delta_w *= delta_w_last == 0.0 ? o.kappa_w_plus_bar : o.kappa_w_plus;
+      }
+      if (delta_w > o.delta_w_max) break;
+    }
+    if (!ok) { status = NNC_IPM_INERTIA_FAILED; T.solver += secs(t_lin, Clock::now()); break; }
+    if (delta_w > 0.0) delta_w_last = delta_w;
+    sol = rhs;
+    kkt.solve(sol.data());
+    for (int i = 0; i < n; ++i) dv[i] = sol[i];
+    for (int j = 0; j < m; ++j) dl[j] = sol[n + j];
+    for (int i = 0; i < n; ++i) {
+      dzL[i] = hasL[i] ? mu / sL[i] - zL[i] - SigL[i] * dv[i] : 0.0;
+      dzU[i] = hasU[i] ? mu / sU[i] - zU[i] + SigU[i] * dv[i] : 0.0;
+    }
+    // --- fraction to the boundary
+    double a_max = 1.0, a_z = 1.0;
+    for (int i = 0; i < n; ++i) {
+      if (hasL[i] && dv[i] < 0) a_max = std::min(a_max, -tau * sL[i] / dv[i]);
+      if (hasU[i] && dv[i] > 0) a_max = std::min(a_max, tau * sU[i] / dv[i]);
+      if (hasL[i] && dzL[i] < 0) a_z = std::min(a_z, -tau * zL[i] / dzL[i]);
+      if (hasU[i] && dzU[i] < 0) a_z = std::min(a_z, -tau * zU[i] / dzU[i]);
+    }
+    // --- penalty parameter and directional derivative
+    double c1 = 0, dphi = 0;
+    for (int j = 0; j < m; ++j) c1 += std::fabs(c[j]);
+    for (int i = 0; i < n; ++i) dphi += gphi[i] * dv[i];
+    if (m && c1 > 0) {
+      // curvature dv^T (W + Sigma + delta_w I) dv
+      double curv = 0;
+#pragma omp parallel for reduction(+ : curv) schedule(static)
+      for (int i = 0; i < nd; ++i) {
+        double s = 0;
+        for (int j = 0; j < nd; ++j) s += WDD[(size_t)i * nd + j] * dv[j];
+        curv += dv[i] * s;
+      }
+      for (int i = 0; i < n; ++i) curv += (SigL[i] + SigU[i] + delta_w + (i >= nd ? WSS[i - nd] : 0.0)) * dv[i] * dv[i];
+      double lmax = 0;
+      for (int j = 0; j < m; ++j) lmax = std::max(lmax, std::fabs(lam[j] + dl[j]));
+      const double nu_req = (dphi + 0.5 * std::max(curv, 0.0)) / (0.9 * c1);
+      nu = std::max(nu, std::max(lmax + 1.0, nu_req + 1.0));
+    }
+    const double D = dphi - nu * c1;
+    T.solver += secs(t_lin, Clock::now());
+    const double phi0 = merit(v, fv, c, nu);
+    double alpha = a_max;
+    bool accepted = false;
+    for (int bt = 0; bt < o.max_backtracks; ++bt) {
+      for (int i = 0; i < n; ++i) vt[i] = v[i] + alpha * dv[i];
+      const double ft = p.f(vt.data());
+      if (m && timed(T.fn, T.n_fn, [&] { return p.cons(vt.data(), ct.data()); })) { status = NNC_IPM_EVAL_ERROR; break; }
+      const double phit = merit(vt, ft, ct, nu);
+      if (std::isfinite(phit) && phit <= phi0 + o.eta * alpha * D) { accepted = true; break; }
+      alpha *= 0.5;
+    }
+    if (status == NNC_IPM_EVAL_ERROR) break;
+    if (!accepted) {
+      if (++ls_fail >= o.max_ls_failures) { status = NNC_IPM_LINESEARCH_FAILED; break; }
+      for (int i = 0; i < n; ++i) vt[i] = v[i] + alpha * dv[i];
+      if (m && timed(T.fn, T.n_fn, [&] { return p.cons(vt.data(), ct.data()); })) { status = NNC_IPM_EVAL_ERROR; break; }
+    } else {
+      ls_fail = 0;
+    }
+    v = vt;
+    c = ct;
+    have_c = true;
+    for (int j = 0; j < m; ++j) lam[j] += alpha * dl[j];
+    for (int i = 0; i < n; ++i) {
+      zL[i] += a_z * dzL[i];
+      zU[i] += a_z * dzU[i];
+      const double s_l = slackL(v, i), s_u = slackU(v, i);
+      zL[i] = hasL[i] ? std::max(std::min(zL[i], o.kappa_sigma * mu / s_l), mu / (o.kappa_sigma * s_l)) : 0.0;
+      zU[i] = hasU[i] ? std::max(std::min(zU[i], o.kappa_sigma * mu / s_u), mu / (o.kappa_sigma * s_u)) : 0.0;
+    }
+  }
+  v_out = v;
+  lam_out = lam;
+  if (res) {
+    res->status = status;
+    res->iters = it;
+    res->obj = p.f(v.data());
+    res->kkt_error = E0;
+    res->solve_seconds = secs(t_start, Clock::now());
+    res->t_function = T.fn;
+    res->t_jacobian = T.jac;
+    res->t_hessian = T.hess;
+    res->t_solver = T.solver;
+    res->n_function = T.n_fn;
+    res->n_jacobian = T.n_jac;
+    res->n_hessian = T.n_hess;
+  }
+  return NNC_OK;
+}
+
+// ---------------------------------------------------------------- adversarial problem
+// Variables v = (x in [0,1]^n_in | y free in R^n_out, s >= 0 in R^(n_out-1)).
+// min ||x - x0||^2  s.t.  y - NN(x) = 0,  y_t - y_j - margin - s_j = 0 (j != t).
+struct Adversarial : IpmProblem {
+  nnc_net* net;
+  int n_in, n_out, t;
+  double margin;
+  std::vector<double> x0, J, H, r;
+  std::vector<int> others;
+  Adversarial(nnc_net* net_, const double* x0_, int n_in_, int n_out_, int t_, double margin_)
+      : net(net_), n_in(n_in_), n_out(n_out_), t(t_), margin(margin_), x0(x0_, x0_ + n_in_) {
+    nd = n_in;
+    ns = n_out + (n_out - 1);
+    m = n_out + (n_out - 1);
+    for (int j = 0; j < n_out; ++j)
+      if (j != t) others.push_back(j);
+    lb.assign(nd + ns, -INFINITY);
+    ub.assign(nd + ns, INFINITY);
+    for (int i = 0; i < n_in; ++i) {
+      lb[i] = 0.0;
+      ub[i] = 1.0;
+    }
+    for (int j = 0; j < n_out - 1; ++j) lb[n_in + n_out + j] = 0.0;
+    J.resize((size_t)n_out * n_in);
+    H.resize((size_t)n_in * n_in);
+    r.resize(n_out);
+  }
+  int start() {
+    std::vector<double> y(n_out);
+    int rc = nnc_eval(net, x0.data(), y.data(), 1);
+    if (rc) return rc;
+    v0.assign(nd + ns, 0.0);
+    for (int i = 0; i < n_in; ++i) v0[i] = x0[i];
+    for (int j = 0; j < n_out; ++j) v0[n_in + j] = y[j];
+    for (int k = 0; k < n_out - 1; ++k)
+      v0[n_in + n_out + k] = std::max(y[t] - y[others[k]] - margin, 1e-2);
+    return NNC_OK;
+  }
+  double f(const double* v) override {
+    double s = 0;
+    for (int i = 0; i < n_in; ++i) s += (v[i] - x0[i]) * (v[i] - x0[i]);
+    return s;
+  }
+  void grad_f(const double* v, double* g) override {
+    for (int i = 0; i < nd + ns; ++i) g[i] = i < n_in ? 2.0 * (v[i] - x0[i]) : 0.0;
+  }
+  int cons(const double* v, double* c) override {
+    // y - NN(x) with the FP64 weights (the FP64 residual at step acceptance)
+    int rc = nnc_residual(net, v, v + n_in, r.data());
+    if (rc) return rc;
+    for (int j = 0; j < n_out; ++j) c[j] = r[j];
+    const double* y = v + n_in;
+    const double* s = v + n_in + n_out;
+    for (int k = 0; k < n_out - 1; ++k) c[n_out + k] = y[t] - y[others[k]] - margin - s[k];
+    return NNC_OK;
+  }
+  int jac(const double* v, double* AD, double* AS) override {
+    int rc = nnc_jacobian(net, v, J.data());
+    if (rc) return rc;
+    std::fill(AD, AD + (size_t)m * nd, 0.0);
+    std::fill(AS, AS + (size_t)m * ns, 0.0);
+    for (int j = 0; j < n_out; ++j) {
+      for (int i = 0; i < n_in; ++i) AD[(size_t)j * nd + i] = -J[(size_t)j * n_in + i];
+      AS[(size_t)j * ns + j] = 1.0;
+    }
+    for (int k = 0; k < n_out - 1; ++k) {
+      AS[(size_t)(n_out + k) * ns + t] = 1.0;
+      AS[(size_t)(n_out + k) * ns + others[k]] = -1.0;
+      AS[(size_t)(n_out + k) * ns + n_out + k] = -1.0;
+    }
+    return NNC_OK;
+  }
+  int hess(const double* v, const double* lam, double* WDD, double* WSS) override {
+    // grad^2 f = 2 I on x; sum_i lam_i grad^2 c_i = -sum_{i < n_out} lam_i grad^2 NN_i (Eq. 6)
+    int rc = nnc_hessian_lag(net, v, lam, H.data(), nullptr);
+    if (rc) return rc;
+    for (size_t i = 0; i < (size_t)nd * nd; ++i) WDD[i] = -H[i];
+    for (int i = 0; i < nd; ++i) WDD[(size_t)i * nd + i] += 2.0;
+    std::fill(WSS, WSS + ns, 0.0);
+    return NNC_OK;
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+int nnc_kkt_solve(int nd, int ns, int m, const double* WDD, const double* WSS, const double* sigma,
+                  const double* AD, const double* AS, double delta_w, double delta_c,
+                  double* rhs_sol, int* inertia) {
+  if (nd < 0 || ns < 0 || m < 0 || (nd && !WDD) || (ns && !WSS) || !sigma || !rhs_sol ||
+      (m && nd && !AD) || (m && ns && !AS))
+    return NNC_ERR_ARG;
+  const int n = nd + ns;
+  double scale = 1.0;
+  for (size_t i = 0; i < (size_t)nd * nd; ++i) scale = std::max(scale, std::fabs(WDD[i]));
+  for (int i = 0; i < n; ++i) scale = std::max(scale, std::fabs(sigma[i]));
+  for (size_t i = 0; i < (size_t)m * nd; ++i) scale = std::max(scale, std::fabs(AD[i]));
+  for (size_t i = 0; i < (size_t)m * ns; ++i) scale = std::max(scale, std::fabs(AS[i]));
+  std::vector<double> wss(WSS ? WSS : nullptr, WSS ? WSS + ns : nullptr);
+  wss.resize(ns, 0.0);
+  std::vector<double> ad(AD ? AD : nullptr, AD ? AD + (size_t)m * nd : nullptr);
+  ad.resize((size_t)m * nd, 0.0);
+  std::vector<double> as(AS ? AS : nullptr, AS ? AS + (size_t)m * ns : nullptr);
+  as.resize((size_t)m * ns, 0.0);
+  KktSolver k;
+  k.factor(nd, ns, m, WDD, wss.data(), sigma, ad.data(), as.data(), delta_w, delta_c, 1e-14 * scale);
+  if (inertia) {
+    inertia[0] = k.npos;
+    inertia[1] = k.nneg;
+    inertia[2] = k.nzero;
+    inertia[3] = k.full ? 1 : 0;
+  }
+  if (k.nzero == 0) k.solve(rhs_sol);
+  return NNC_OK;
+}
+
+void nnc_ipm_default_options(nnc_ipm_options* o) {
+  if (!o) return;
+  o->tol = 1e-6;
+  o->max_iter = 300;
+  o->mu0 = 0.1;
+  o->kappa_mu = 0.2;
+  o->theta_mu = 1.5;
+  o->kappa_eps = 10.0;
+  o->tau_min = 0.99;
+  o->kappa1 = 1e-2;
+  o->kappa2 = 1e-2;
+  o->s_max = 100.0;
+  o->eta = 1e-4;
+  o->delta_w0 = 1e-4;
+  o->delta_w_min = 1e-20;
+  o->delta_w_max = 1e40;
+  o->kappa_w_plus = 8.0;
+  o->kappa_w_plus_bar = 100.0;
+  o->kappa_w_minus = 1.0 / 3.0;
+  o->kappa_sigma = 1e10;
+  o->max_backtracks = 40;
+  o->max_ls_failures = 5;
+  o->verbose = 0;
+}
+
+int nnc_ipm_adversarial(nnc_net* net, const double* x0, int target, double margin,
+                        const nnc_ipm_options* opt, double* v_out, double* lam_out,
+                        nnc_ipm_result* res) {
+  int L = 0, n_in = 0, n_out = 0, prec = 0;
+  int rc = nnc_net_info(net, &L, &n_in, &n_out, &prec);
+  if (rc) return rc;
+  if (!x0 || target < 0 || target >= n_out || n_out < 2) return NNC_ERR_ARG;
+  nnc_ipm_options o;
+  if (opt) o = *opt;
+  else nnc_ipm_default_options(&o);
+  Adversarial p(net, x0, n_in, n_out, target, margin);
+  rc = p.start();
+  if (rc) return rc;
+  std::vector<double> v, lam;
+  rc = ipm_solve(p, o, v, lam, res);
+  if (rc) return rc;
+  if (v_out) std::copy(v.begin(), v.end(), v_out);
+  if (lam_out) std::copy(lam.begin(), lam.end(), lam_out);
+  return NNC_OK;
+}
+
+}  // extern "C"

@@ -19,30 +19,33 @@ __device__ __forceinline__ double warp_sum(double v) {
 template <typename TW>
 __global__ void __launch_bounds__(256) k_gemv_fwd(const TW* __restrict__ W, int ldw,
                                                   const double* __restrict__ bias,
-                                                  const double* __restrict__ a_in, int m, int k,
+                                                  const void* __restrict__ a_in_v, int m, int k,
                                                   int act, double* __restrict__ a_out,
+                                                  float* __restrict__ a_out_f,
                                                   double* __restrict__ s1, double* __restrict__ s2) {
   const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (row >= m) return;
   double acc;
   if constexpr (std::is_same<TW, float>::value) {
+    // FP32 weights meet the FP32 copy of the activations (no FP64 conversions in the loop).
     const float4* r4 = reinterpret_cast<const float4*>(W + (size_t)row * ldw);
+    const float4* a4 = reinterpret_cast<const float4*>(a_in_v);
     const int nk4 = (k + 3) >> 2;
     float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
 #pragma unroll 4
     for (int j = lane; j < nk4; j += 32) {
       const float4 w = __ldg(r4 + j);
-      const double2 a01 = *reinterpret_cast<const double2*>(a_in + 4 * j);
-      const double2 a23 = *reinterpret_cast<const double2*>(a_in + 4 * j + 2);
-      p0 = fmaf(w.x, (float)a01.x, p0);
-      p1 = fmaf(w.y, (float)a01.y, p1);
-      p2 = fmaf(w.z, (float)a23.x, p2);
-      p3 = fmaf(w.w, (float)a23.y, p3);
+      const float4 a = a4[j];
+      p0 = fmaf(w.x, a.x, p0);
+      p1 = fmaf(w.y, a.y, p1);
+      p2 = fmaf(w.z, a.z, p2);
+      p3 = fmaf(w.w, a.w, p3);
     }
     acc = ((double)p0 + (double)p1) + ((double)p2 + (double)p3);
   } else {
     const double2* r2 = reinterpret_cast<const double2*>(W + (size_t)row * ldw);
+    const double* a_in = reinterpret_cast<const double*>(a_in_v);
     const int nk2 = (k + 1) >> 1;
     double q0 = 0.0, q1 = 0.0;
 #pragma unroll 4
@@ -60,126 +63,132 @@ __global__ void __launch_bounds__(256) k_gemv_fwd(const TW* __restrict__ W, int 
     double a, d1, d2;
     act_eval(act, z, a, d1, d2);
     a_out[row] = a;
+    if (a_out_f) a_out_f[row] = (float)a;
     if (s1) s1[row] = d1;
     if (s2) s2[row] = d2;
   }
 }
 
-cudaError_t launch_gemv_fwd(bool fp64, const void* W, int ldw, const double* b, const double* a_in,
-                            int m, int k, int act, double* a_out, double* s1, double* s2,
-                            cudaStream_t st) {
+cudaError_t launch_gemv_fwd(bool fp64, const void* W, int ldw, const double* b, const void* a_in,
+                            int m, int k, int act, double* a_out, float* a_out_f, double* s1,
+                            double* s2, cudaStream_t st) {
   const int threads = 256;
   const int blocks = (m * 32 + threads - 1) / threads;
   if (fp64)
     k_gemv_fwd<double><<<blocks, threads, 0, st>>>((const double*)W, ldw, b, a_in, m, k, act, a_out,
-                                                   s1, s2);
+                                                   a_out_f, s1, s2);
   else
     k_gemv_fwd<float><<<blocks, threads, 0, st>>>((const float*)W, ldw, b, a_in, m, k, act, a_out,
-                                                  s1, s2);
+                                                  a_out_f, s1, s2);
   note_launch();
   return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ reverse sweep
 // part[c][kk][s] = sum_{r in chunk c} W[r][kk] * Zbar[r][s]: the transposed product W^T Zbar of
-// one reverse step, split over row chunks so that the grid fills the GPU; a thread owns two
-// adjacent columns kk and all S seeds.  FP32 weights run in FP32 (seeds rounded to FP32,
-// partial sums over one chunk in FP32), FP64 weights in FP64.
-constexpr int kRevCols = 256;   // columns per block (128 threads x 2)
-constexpr int kRevRows = 64;    // rows per chunk staged at once in shared memory
+// one reverse step.  A block of 256 threads covers 256 * VEC adjacent columns (VEC = 4 floats
+// or 2 doubles per 16-byte load) and one chunk of kRevRows rows, whose seeds are staged in
+// shared memory; many small blocks keep enough loads in flight to stream W at HBM rate.  FP32
+// weights run in FP32 (seeds rounded to FP32), FP64 weights in FP64; partial sums are written
+// in the same type and summed over chunks by k_rev_reduce.
+constexpr int kRevRows = 64;     // rows per chunk
+constexpr int kRevThreads = 256;
+
+template <typename TW>
+struct RevVec;
+template <>
+struct RevVec<float> {
+  static constexpr int V = 4;
+  __device__ static void load(const float* p, float (&w)[4]) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+  }
+};
+template <>
+struct RevVec<double> {
+  static constexpr int V = 2;
+  __device__ static void load(const double* p, double (&w)[2]) {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    w[0] = v.x; w[1] = v.y;
+  }
+};
 
 template <typename TW, int SMAX>
-__global__ void __launch_bounds__(128) k_gemv_rev(const TW* __restrict__ W, int ldw, int m,
-                                                  int kcols, const double* __restrict__ Zbar,
-                                                  int S, int rows_per_chunk,
-                                                  double* __restrict__ part) {
-  using TA = typename std::conditional<std::is_same<TW, float>::value, float, double>::type;
-  __shared__ TA zs[kRevRows][SMAX];
-  const int c0 = blockIdx.x * kRevCols + 2 * threadIdx.x;
-  const int rbeg = blockIdx.y * rows_per_chunk;
-  const int rend = min(m, rbeg + rows_per_chunk);
-  TA acc0[SMAX], acc1[SMAX];
+__global__ void __launch_bounds__(kRevThreads) k_gemv_rev(const TW* __restrict__ W, int ldw, int m,
+                                                          int kcols, const double* __restrict__ Zbar,
+                                                          int S, TW* __restrict__ part) {
+  constexpr int V = RevVec<TW>::V;
+  __shared__ TW zs[kRevRows][SMAX];
+  const int c0 = (blockIdx.x * kRevThreads + threadIdx.x) * V;
+  const int r0 = blockIdx.y * kRevRows;
+  const int nr = min(kRevRows, m - r0);
+  for (int i = threadIdx.x; i < kRevRows * SMAX; i += kRevThreads) {
+    const int r = i / SMAX, s = i % SMAX;
+    zs[r][s] = (r < nr && s < S) ? (TW)Zbar[(size_t)(r0 + r) * S + s] : TW(0);
+  }
+  __syncthreads();
+  if (c0 >= kcols) return;  // kcols is a multiple of 128, so a thread's V columns are all valid
+  TW acc[V][SMAX];
 #pragma unroll
-  for (int s = 0; s < SMAX; ++s) acc0[s] = acc1[s] = TA(0);
-  const bool active = c0 < kcols;  // kcols is even (padded), so c0 + 1 < kcols too
-  for (int r0 = rbeg; r0 < rend; r0 += kRevRows) {
-    const int nr = min(kRevRows, rend - r0);
-    __syncthreads();
-    for (int i = threadIdx.x; i < nr * SMAX; i += blockDim.x) {
-      const int r = i / SMAX, s = i % SMAX;
-      zs[r][s] = s < S ? (TA)Zbar[(size_t)(r0 + r) * S + s] : TA(0);
-    }
-    __syncthreads();
-    if (active) {
-      const TW* wp = W + (size_t)r0 * ldw + c0;
+  for (int v = 0; v < V; ++v)
+#pragma unroll
+    for (int s = 0; s < SMAX; ++s) acc[v][s] = TW(0);
+  const TW* wp = W + (size_t)r0 * ldw + c0;
 #pragma unroll 4
-      for (int r = 0; r < nr; ++r) {
-        TA w0, w1;
-        if constexpr (std::is_same<TW, float>::value) {
-          const float2 w = __ldg(reinterpret_cast<const float2*>(wp + (size_t)r * ldw));
-          w0 = w.x;
-          w1 = w.y;
-        } else {
-          const double2 w = __ldg(reinterpret_cast<const double2*>(wp + (size_t)r * ldw));
-          w0 = w.x;
-          w1 = w.y;
-        }
+  for (int r = 0; r < nr; ++r) {
+    TW w[V];
+    RevVec<TW>::load(wp + (size_t)r * ldw, w);
 #pragma unroll
-        for (int s = 0; s < SMAX; ++s) {
-          acc0[s] += w0 * zs[r][s];
-          acc1[s] += w1 * zs[r][s];
-        }
-      }
+    for (int s = 0; s < SMAX; ++s) {
+      const TW z = zs[r][s];
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[v][s] = fma(w[v], z, acc[v][s]);
     }
   }
-  if (active) {
-    double* out = part + ((size_t)blockIdx.y * kcols + c0) * S;
+  TW* out = part + ((size_t)blockIdx.y * kcols + c0) * S;
+#pragma unroll
+  for (int v = 0; v < V; ++v)
 #pragma unroll
     for (int s = 0; s < SMAX; ++s)
-      if (s < S) {
-        out[s] = (double)acc0[s];
-        out[S + s] = (double)acc1[s];
-      }
-  }
+      if (s < S) out[v * S + s] = acc[v][s];
 }
 
 int rev_chunks(int m, int kcols, int sm_count) {
-  const int col_blocks = (kcols + kRevCols - 1) / kRevCols;
-  int chunks = (2 * sm_count + col_blocks - 1) / col_blocks;  // about two waves of blocks
-  chunks = chunks < 1 ? 1 : chunks;
-  const int max_chunks = (m + 15) / 16;                   // at least 16 rows per chunk
-  return chunks > max_chunks ? max_chunks : chunks;
+  (void)kcols;
+  (void)sm_count;
+  return (m + kRevRows - 1) / kRevRows;
 }
 
 template <typename TW>
 static void rev_dispatch(const TW* W, int ldw, int m, int kcols, const double* Zbar, int S,
-                         int chunks, double* part, cudaStream_t st) {
-  const int rows_per_chunk = (m + chunks - 1) / chunks;
-  dim3 grid((kcols + kRevCols - 1) / kRevCols, chunks);
+                         int chunks, TW* part, cudaStream_t st) {
+  constexpr int V = RevVec<TW>::V;
+  dim3 grid((kcols + kRevThreads * V - 1) / (kRevThreads * V), chunks);
   if (S <= 1)
-    k_gemv_rev<TW, 1><<<grid, 128, 0, st>>>(W, ldw, m, kcols, Zbar, S, rows_per_chunk, part);
+    k_gemv_rev<TW, 1><<<grid, kRevThreads, 0, st>>>(W, ldw, m, kcols, Zbar, S, part);
   else if (S <= 4)
-    k_gemv_rev<TW, 4><<<grid, 128, 0, st>>>(W, ldw, m, kcols, Zbar, S, rows_per_chunk, part);
+    k_gemv_rev<TW, 4><<<grid, kRevThreads, 0, st>>>(W, ldw, m, kcols, Zbar, S, part);
   else if (S <= 12)
-    k_gemv_rev<TW, 12><<<grid, 128, 0, st>>>(W, ldw, m, kcols, Zbar, S, rows_per_chunk, part);
+    k_gemv_rev<TW, 12><<<grid, kRevThreads, 0, st>>>(W, ldw, m, kcols, Zbar, S, part);
   else if (S <= 24)
-    k_gemv_rev<TW, 24><<<grid, 128, 0, st>>>(W, ldw, m, kcols, Zbar, S, rows_per_chunk, part);
+    k_gemv_rev<TW, 24><<<grid, kRevThreads, 0, st>>>(W, ldw, m, kcols, Zbar, S, part);
   else
-    k_gemv_rev<TW, 48><<<grid, 128, 0, st>>>(W, ldw, m, kcols, Zbar, S, rows_per_chunk, part);
+    k_gemv_rev<TW, 48><<<grid, kRevThreads, 0, st>>>(W, ldw, m, kcols, Zbar, S, part);
 }
 
 cudaError_t launch_gemv_rev(bool fp64, const void* W, int ldw, int m, int kcols, const double* Zbar,
-                            int S, int chunks, double* part, cudaStream_t st) {
+                            int S, int chunks, void* part, cudaStream_t st) {
   if (S > 48) return cudaErrorInvalidValue;
   if (fp64)
-    rev_dispatch<double>((const double*)W, ldw, m, kcols, Zbar, S, chunks, part, st);
+    rev_dispatch<double>((const double*)W, ldw, m, kcols, Zbar, S, chunks, (double*)part, st);
   else
-    rev_dispatch<float>((const float*)W, ldw, m, kcols, Zbar, S, chunks, part, st);
+    rev_dispatch<float>((const float*)W, ldw, m, kcols, Zbar, S, chunks, (float*)part, st);
   note_launch();
   return cudaGetLastError();
 }
 
-__global__ void k_rev_reduce(const double* __restrict__ part, int chunks, int kcols, int kvalid,
+template <typename TP>
+__global__ void k_rev_reduce(const TP* __restrict__ part, int chunks, int kcols, int kvalid,
                              int S, const double* __restrict__ s1, const double* __restrict__ s2,
                              int lam_col, int nJ, double* __restrict__ Zbar_out,
                              double* __restrict__ c_out, float* __restrict__ c_out_f,
@@ -188,7 +197,7 @@ __global__ void k_rev_reduce(const double* __restrict__ part, int chunks, int kc
   if (idx >= kcols * S) return;
   const int kk = idx / S, s = idx % S;
   double v = 0.0;
-  for (int c = 0; c < chunks; ++c) v += part[((size_t)c * kcols + kk) * S + s];
+  for (int c = 0; c < chunks; ++c) v += (double)part[((size_t)c * kcols + kk) * S + s];
   if (Zbar_out) Zbar_out[idx] = s1 ? s1[kk] * v : v;
   if (s == lam_col) {
     if (c_out) c_out[kk] = s2[kk] * v;
@@ -198,13 +207,19 @@ __global__ void k_rev_reduce(const double* __restrict__ part, int chunks, int kc
   if (J_out && s < nJ && kk < kvalid) J_out[(size_t)s * kvalid + kk] = v;
 }
 
-cudaError_t launch_rev_reduce(const double* part, int chunks, int kcols, int kvalid, int S,
+cudaError_t launch_rev_reduce(bool fp64, const void* part, int chunks, int kcols, int kvalid, int S,
                               const double* s1, const double* s2, int lam_col, int nJ,
                               double* Zbar_out, double* c_out, float* c_out_f, double* J_out,
                               double* g_out, cudaStream_t st) {
   const int total = kcols * S;
-  k_rev_reduce<<<(total + 255) / 256, 256, 0, st>>>(part, chunks, kcols, kvalid, S, s1, s2, lam_col,
-                                                    nJ, Zbar_out, c_out, c_out_f, J_out, g_out);
+  if (fp64)
+    k_rev_reduce<double><<<(total + 255) / 256, 256, 0, st>>>(
+        (const double*)part, chunks, kcols, kvalid, S, s1, s2, lam_col, nJ, Zbar_out, c_out,
+        c_out_f, J_out, g_out);
+  else
+    k_rev_reduce<float><<<(total + 255) / 256, 256, 0, st>>>(
+        (const float*)part, chunks, kcols, kvalid, S, s1, s2, lam_col, nJ, Zbar_out, c_out,
+        c_out_f, J_out, g_out);
   note_launch();
   return cudaGetLastError();
 }
@@ -338,13 +353,18 @@ cudaError_t launch_sub(const double* y, const double* a, double* r, int n, cudaS
   return cudaGetLastError();
 }
 
-__global__ void k_copy_pad(const double* src, double* dst, int n, int n_pad) {
+__global__ void k_copy_pad(const double* src, double* dst, float* dst_f, int n, int n_pad) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n_pad) dst[i] = i < n ? src[i] : 0.0;
+  if (i < n_pad) {
+    const double v = i < n ? src[i] : 0.0;
+    dst[i] = v;
+    if (dst_f) dst_f[i] = (float)v;
+  }
 }
 
-cudaError_t launch_copy_pad(const double* src, double* dst, int n, int n_pad, cudaStream_t st) {
-  k_copy_pad<<<(n_pad + 255) / 256, 256, 0, st>>>(src, dst, n, n_pad);
+cudaError_t launch_copy_pad(const double* src, double* dst, float* dst_f, int n, int n_pad,
+                            cudaStream_t st) {
+  k_copy_pad<<<(n_pad + 255) / 256, 256, 0, st>>>(src, dst, dst_f, n, n_pad);
   note_launch();
   return cudaGetLastError();
 }

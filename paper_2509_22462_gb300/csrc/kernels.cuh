@@ -17,16 +17,18 @@ enum class Elem { F64, F32, BF16, BF16X3 };
 
 // ---- vector kernels (k_vector.cu)
 // Forward layer: z = W a_in + b, a_out = sigma(z), s1 = sigma'(z), s2 = sigma''(z).
-cudaError_t launch_gemv_fwd(bool fp64, const void* W, int ldw, const double* b, const double* a_in,
-                            int m, int k, int act, double* a_out, double* s1, double* s2,
-                            cudaStream_t st);
-// Reverse layer with S seed columns: part[c][kk][s] = sum over row chunk c of W[r][kk] Zbar[r][s].
+// a_in is double (fp64) or float (FP32 weights); a_out_f (may be NULL) receives a float copy.
+cudaError_t launch_gemv_fwd(bool fp64, const void* W, int ldw, const double* b, const void* a_in,
+                            int m, int k, int act, double* a_out, float* a_out_f, double* s1,
+                            double* s2, cudaStream_t st);
+// Reverse layer with S seed columns: part[c][kk][s] = sum over row chunk c of W[r][kk] Zbar[r][s]
+// (part is double for FP64 weights, float for FP32 weights).
 cudaError_t launch_gemv_rev(bool fp64, const void* W, int ldw, int m, int kcols, const double* Zbar,
-                            int S, int chunks, double* part, cudaStream_t st);
+                            int S, int chunks, void* part, cudaStream_t st);
 int rev_chunks(int m, int kcols, int sm_count);
 // Sum the chunks; then Zbar_out = s1 * Abar (if s1), c_out = s2 * Abar[:, lam_col] (if c_out),
 // J_out[s][kk] = Abar[kk][s] for s < nJ (if J_out), g_out[kk] = Abar[kk][lam_col] (if g_out).
-cudaError_t launch_rev_reduce(const double* part, int chunks, int kcols, int kvalid, int S,
+cudaError_t launch_rev_reduce(bool fp64, const void* part, int chunks, int kcols, int kvalid, int S,
                               const double* s1, const double* s2, int lam_col, int nJ,
                               double* Zbar_out, double* c_out, float* c_out_f, double* J_out,
                               double* g_out, cudaStream_t st);
@@ -43,8 +45,9 @@ cudaError_t launch_h_finish(bool part_f32, const void* Hp, int splits, int n, in
                             cudaStream_t st);
 // r = y - a  (FP64)
 cudaError_t launch_sub(const double* y, const double* a, double* r, int n, cudaStream_t st);
-// dst[i] = src[i] (double) for i < n; zero for n <= i < n_pad
-cudaError_t launch_copy_pad(const double* src, double* dst, int n, int n_pad, cudaStream_t st);
+// dst[i] = src[i] (double) for i < n; zero for n <= i < n_pad; dst_f (may be NULL) a float copy
+cudaError_t launch_copy_pad(const double* src, double* dst, float* dst_f, int n, int n_pad,
+                            cudaStream_t st);
 
 // ---- CUDA-core GEMMs for the FP64 / FP32 forms (k_simt.cu)
 // D[m][n] = sum_k A[m][k] B[n][k] (both K-major).

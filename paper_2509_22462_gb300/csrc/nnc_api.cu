@@ -44,6 +44,7 @@ struct LayerDev {
   double* c = nullptr;            // sigma_l''(z_l) * abar_l [mp]
   float* c_f = nullptr;           // FP32 copy of c for the tensor-core epilogue
   double* ra = nullptr;           // FP64-residual pass activations [mp]
+  float* af = nullptr;            // FP32 copy of a_l [mp] (input of the next FP32 layer)
   TcPlan plan_tan;                // tensor-core plan of this layer's tangent GEMM
   TcPlan plan_syrk;               // tensor-core plan of this layer's symmetric product
 };
@@ -56,6 +57,7 @@ struct nnc_net {
   int device = 0, sm_count = 0;
   std::vector<void*> allocs;
   double* x = nullptr;       // a_0 [n_in_pad]
+  float* xf = nullptr;       // FP32 copy of a_0 [n_in_pad]
   double* xin = nullptr;     // host-call staging of x [n_in_pad]
   double* lam = nullptr;     // [n_out]
   double* ydev = nullptr;    // [n_out] staging
@@ -179,12 +181,12 @@ struct ProfScope {
 
 // ---------------------------------------------------------------- forward value pass
 int run_forward(nnc_net* net, bool fp64, cudaStream_t st) {
-  const double* a_in = net->x;
+  const void* a_in = fp64 ? (const void*)net->x : (const void*)net->xf;
   for (auto& Ly : net->layers) {
     PROF(PK_FWD);
     CK(launch_gemv_fwd(fp64, fp64 ? (const void*)Ly.W64 : (const void*)Ly.W32, Ly.kp, Ly.b, a_in,
-                       Ly.m, Ly.kp, Ly.act, Ly.a, Ly.s1, Ly.s2, st));
-    a_in = Ly.a;
+                       Ly.m, Ly.kp, Ly.act, Ly.a, fp64 ? nullptr : Ly.af, Ly.s1, Ly.s2, st));
+    a_in = fp64 ? (const void*)Ly.a : (const void*)Ly.af;
   }
   return NNC_OK;
 }
@@ -194,7 +196,7 @@ int run_forward_fp64_values(nnc_net* net, cudaStream_t st) {
   for (auto& Ly : net->layers) {
     PROF(PK_FWD);
     CK(launch_gemv_fwd(true, Ly.W64, Ly.kp, Ly.b, a_in, Ly.m, Ly.kp, Ly.act, Ly.ra, nullptr,
-                       nullptr, st));
+                       nullptr, nullptr, st));
     a_in = Ly.ra;
   }
   return NNC_OK;
@@ -221,12 +223,12 @@ int run_reverse(nnc_net* net, bool fp64, int nJ, bool with_lam, const double* la
                        net->Zbar[cur], S, chunks, net->part, st));
     if (l > 0) {
       LayerDev& Lp = net->layers[l - 1];
-      CK(launch_rev_reduce(net->part, chunks, Ly.kp, Ly.k, S, Lp.s1, Lp.s2, lam_col, nJ,
+      CK(launch_rev_reduce(fp64, net->part, chunks, Ly.kp, Ly.k, S, Lp.s1, Lp.s2, lam_col, nJ,
                            net->Zbar[1 - cur], with_lam ? Lp.c : nullptr,
                            (with_lam && tc) ? Lp.c_f : nullptr, nullptr, nullptr, st));
       cur = 1 - cur;
     } else {
-      CK(launch_rev_reduce(net->part, chunks, Ly.kp, Ly.k, S, nullptr, nullptr, lam_col, nJ,
+      CK(launch_rev_reduce(fp64, net->part, chunks, Ly.kp, Ly.k, S, nullptr, nullptr, lam_col, nJ,
                            nullptr, nullptr, nullptr, J, g, st));
     }
   }
@@ -287,7 +289,7 @@ int run_hessian(nnc_net* net, double* H, cudaStream_t st) {
 
 int eval_all(nnc_net* net, const double* x, const double* lam, double* y, double* J, double* H,
              double* g, cudaStream_t st) {
-  CK(launch_copy_pad(x, net->x, net->n_in, net->n_in_pad, st));
+  CK(launch_copy_pad(x, net->x, net->xf, net->n_in, net->n_in_pad, st));
   const bool fp64 = net->prec == NNC_FP64;
   int r = run_forward(net, fp64, st);
   if (r != NNC_OK) return r;
@@ -453,6 +455,7 @@ static int load_impl(nnc_net* net, int n_layers, const int* widths, const int* a
     AL(Ly.s2, Ly.mp);
     AL(Ly.c, Ly.mp);
     AL(Ly.ra, Ly.mp);
+    AL(Ly.af, Ly.mp);
     if (tc) AL(Ly.c_f, Ly.mp);
     const int chunks = rev_chunks(Ly.m, Ly.kp, net->sm_count);
     part_max = std::max(part_max, (size_t)chunks * Ly.kp * net->S_max);
@@ -460,6 +463,7 @@ static int load_impl(nnc_net* net, int n_layers, const int* widths, const int* a
   net->mp_max = mp_max;
   AL(net->x, net->n_in_pad);
   AL(net->xin, net->n_in_pad);
+  AL(net->xf, net->n_in_pad);
   AL(net->lam, net->n_out);
   AL(net->ydev, net->n_out);
   AL(net->rdev, net->n_out);
@@ -582,7 +586,7 @@ int nnc_eval(nnc_net* net, const double* x, double* y, int fp64_residual) {
   cudaStream_t st = net->stream;
   std::memcpy(net->h_stage, x, sizeof(double) * net->n_in);
   CK(cudaMemcpyAsync(net->xin, net->h_stage, sizeof(double) * net->n_in, cudaMemcpyHostToDevice, st));
-  CK(launch_copy_pad(net->xin, net->x, net->n_in, net->n_in_pad, st));
+  CK(launch_copy_pad(net->xin, net->x, net->xf, net->n_in, net->n_in_pad, st));
   r = run_forward_fp64_values(net, st);
   if (r) return r;
   CK(cudaMemcpyAsync(y, net->layers.back().ra, sizeof(double) * net->n_out, cudaMemcpyDeviceToHost, st));
@@ -595,7 +599,7 @@ int nnc_eval_dev(nnc_net* net, const double* x, double* y, int fp64_residual, vo
   if (r) return r;
   if (!x || !y) return fail(NNC_ERR_ARG, "x or y is NULL");
   cudaStream_t st = pick(net, stream);
-  CK(launch_copy_pad(x, net->x, net->n_in, net->n_in_pad, st));
+  CK(launch_copy_pad(x, net->x, net->xf, net->n_in, net->n_in_pad, st));
   r = fp64_residual ? run_forward_fp64_values(net, st) : run_forward(net, net->prec == NNC_FP64, st);
   if (r) return r;
   const double* aL = fp64_residual ? net->layers.back().ra : net->layers.back().a;
@@ -608,7 +612,7 @@ int nnc_residual_dev(nnc_net* net, const double* x, const double* y, double* rr,
   if (r) return r;
   if (!x || !y || !rr) return fail(NNC_ERR_ARG, "x, y or r is NULL");
   cudaStream_t st = pick(net, stream);
-  CK(launch_copy_pad(x, net->x, net->n_in, net->n_in_pad, st));
+  CK(launch_copy_pad(x, net->x, net->xf, net->n_in, net->n_in_pad, st));
   r = run_forward_fp64_values(net, st);
   if (r) return r;
   CK(launch_sub(y, net->layers.back().ra, rr, net->n_out, st));

@@ -24,7 +24,37 @@ STATUS = {0: "NNC_OK", -1: "NNC_ERR_ARG", -2: "NNC_ERR_CUDA", -3: "NNC_ERR_NONFI
 EXPORTS = ["nnc_load_weights", "nnc_eval", "nnc_residual", "nnc_jacobian", "nnc_hessian_lag",
            "nnc_eval_batched", "nnc_eval_dev", "nnc_residual_dev", "nnc_jacobian_dev",
            "nnc_hessian_lag_dev", "nnc_eval_all_dev", "nnc_free", "nnc_last_error",
-           "nnc_net_info", "nnc_launch_count", "nnc_profile", "nnc_profile_read"]
+           "nnc_net_info", "nnc_launch_count", "nnc_profile", "nnc_profile_read",
+           "nnc_ipm_default_options", "nnc_ipm_adversarial", "nnc_kkt_solve"]
+IPM_STATUS = {0: "optimal", 1: "max_iter", 2: "linesearch_failed", 3: "nonfinite",
+              4: "inertia_failed", 5: "eval_error"}
+
+
+class IpmOptions(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mu0", ctypes.c_double),
+                ("kappa_mu", ctypes.c_double), ("theta_mu", ctypes.c_double),
+                ("kappa_eps", ctypes.c_double), ("tau_min", ctypes.c_double),
+                ("kappa1", ctypes.c_double), ("kappa2", ctypes.c_double), ("s_max", ctypes.c_double),
+                ("eta", ctypes.c_double), ("delta_w0", ctypes.c_double),
+                ("delta_w_min", ctypes.c_double), ("delta_w_max", ctypes.c_double),
+                ("kappa_w_plus", ctypes.c_double), ("kappa_w_plus_bar", ctypes.c_double),
+                ("kappa_w_minus", ctypes.c_double), ("kappa_sigma", ctypes.c_double),
+                ("max_backtracks", ctypes.c_int), ("max_ls_failures", ctypes.c_int),
+                ("verbose", ctypes.c_int)]
+
+
+class IpmResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("obj", ctypes.c_double),
+                ("kkt_error", ctypes.c_double), ("solve_seconds", ctypes.c_double),
+                ("t_function", ctypes.c_double), ("t_jacobian", ctypes.c_double),
+                ("t_hessian", ctypes.c_double), ("t_solver", ctypes.c_double),
+                ("n_function", ctypes.c_int), ("n_jacobian", ctypes.c_int),
+                ("n_hessian", ctypes.c_int)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["status_name"] = IPM_STATUS.get(self.status, str(self.status))
+        return d
 PROFILE_KINDS = ["tangent_gemm", "syrk", "forward", "reverse", "other"]
 
 
@@ -66,14 +96,21 @@ def load_library(path: str = LIB_PATH):
     lib.nnc_eval_all_dev.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P]
     lib.nnc_free.argtypes = [_P]
     lib.nnc_free.restype = None
+    lib.nnc_ipm_default_options.restype = None
     lib.nnc_last_error.restype = ctypes.c_char_p
     lib.nnc_net_info.argtypes = [_P] + [ctypes.POINTER(ctypes.c_int)] * 4
     lib.nnc_launch_count.restype = ctypes.c_longlong
     lib.nnc_profile.argtypes = [_P, ctypes.c_int]
+    lib.nnc_ipm_default_options.argtypes = [ctypes.POINTER(IpmOptions)]
+    lib.nnc_kkt_solve.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _DP, _DP, _DP, _DP, _DP,
+                                  ctypes.c_double, ctypes.c_double, _DP, ctypes.POINTER(ctypes.c_int)]
+    lib.nnc_ipm_adversarial.argtypes = [_P, _DP, ctypes.c_int, ctypes.c_double,
+                                        ctypes.POINTER(IpmOptions), _DP, _DP,
+                                        ctypes.POINTER(IpmResult)]
     lib.nnc_profile_read.argtypes = [_P, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
     for name in EXPORTS:
-        if name not in ("nnc_free", "nnc_last_error", "nnc_launch_count"):
+        if name not in ("nnc_free", "nnc_last_error", "nnc_launch_count", "nnc_ipm_default_options"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -97,8 +134,11 @@ def launch_count() -> int:
 
 
 def _stream_ptr():
+    """torch's current stream as a cudaStream_t.  torch reports the legacy default stream as 0,
+    which the C ABI reads as "the net's own stream", so it is passed as cudaStreamLegacy (1)."""
     import torch
-    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    h = torch.cuda.current_stream().cuda_stream
+    return ctypes.c_void_p(h if h else 1)
 
 
 def _tp(t):
@@ -223,3 +263,42 @@ def eval_batched(nets, xs, lams=None, what=WANT_Y | WANT_J | WANT_H):
     hs = (_P * K)(*[n.handle for n in nets])
     _check(lib.nnc_eval_batched(hs, K, arr(xs), arr(lams), arr(ys), arr(Js), arr(Hs), what))
     return ys, Js, Hs
+
+
+def ipm_options(**kw) -> IpmOptions:
+    o = IpmOptions()
+    load_library().nnc_ipm_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def ipm_adversarial(net, x0, target=3, margin=0.1, **options):
+    """Solve the adversarial problem with the host interior-point driver (include/nnc_ipm.h).
+    Returns (result dict, v = (x, y, s), lambda)."""
+    lib = load_library()
+    x0 = _f64(x0)
+    o = ipm_options(**options)
+    nv = net.n_in + 2 * net.n_out - 1
+    v = np.empty(nv)
+    lam = np.empty(2 * net.n_out - 1)
+    res = IpmResult()
+    _check(lib.nnc_ipm_adversarial(net.handle, _dp(x0), int(target), float(margin), ctypes.byref(o),
+                                   _dp(v), _dp(lam), ctypes.byref(res)))
+    return res.as_dict(), v, lam
+
+
+def kkt_solve(WDD, WSS, sigma, AD, AS, rhs, delta_w=0.0, delta_c=0.0):
+    """nnc_kkt_solve (host FP64, no device work): returns (solution, (npos, nneg, nzero, full))."""
+    lib = load_library()
+    nd = WDD.shape[0]
+    ns = len(WSS)
+    m = AD.shape[0] if AD is not None and AD.size else (AS.shape[0] if AS is not None else 0)
+    WDD, WSS, sigma = _f64(WDD), _f64(WSS), _f64(sigma)
+    AD = _f64(AD if AD is not None else np.zeros((m, nd)))
+    AS = _f64(AS if AS is not None else np.zeros((m, ns)))
+    x = _f64(rhs).copy()
+    inert = (ctypes.c_int * 4)()
+    _check(lib.nnc_kkt_solve(nd, ns, m, _dp(WDD), _dp(WSS), _dp(sigma), _dp(AD), _dp(AS),
+                             float(delta_w), float(delta_c), _dp(x), inert))
+    return x, tuple(inert)

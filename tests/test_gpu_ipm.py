@@ -1,0 +1,73 @@
+"""Host interior-point driver with the GPU oracles against the oracle interior-point method.
+
+Both follow the same reading of Eq. 2 step by step, so with the FP64 form the iterates agree
+to round-off and the iteration counts match; the tensor-core forms must reach the same
+converged objective within 1e-6 relative, each with its own KKT certificate <= 1e-6."""
+import numpy as np
+import pytest
+
+import synth
+from synth.nets import MLPSpec, make_mlp
+from oracle import ipm as oipm, problems
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nnc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_22462_gb300 import build, nnc as m
+    build.build()
+    return m
+
+
+@pytest.fixture(scope="module")
+def tiny_oracle_solution():
+    mlp = make_mlp(synth.TINY, seed=0)
+    d = synth.adversarial_data(seed=0)
+    r = oipm.solve(problems.adversarial(mlp, d.x0, d.target, d.margin))
+    assert r.status == oipm.OPTIMAL
+    return mlp, d, r
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3"])
+def test_adversarial_tiny_matches_oracle(nnc, tiny_oracle_solution, prec):
+    mlp, d, ro = tiny_oracle_solution
+    net = nnc.Net.from_mlp(mlp, precision=prec)
+    res, v, lam = nnc.ipm_adversarial(net, d.x0, d.target, d.margin)
+    print(f"[ipm tiny {prec}] status={res['status_name']} iters={res['iters']} (oracle {ro.iters}) "
+          f"obj={res['obj']:.12g} (oracle {ro.obj:.12g}) kkt={res['kkt_error']:.2e} "
+          f"t={res['solve_seconds']:.3f}s fn={res['t_function']:.3f} jac={res['t_jacobian']:.3f} "
+          f"hess={res['t_hessian']:.3f} solver={res['t_solver']:.3f}")
+    assert res["status"] == 0
+    assert res["kkt_error"] <= 1e-6
+    assert abs(res["obj"] - ro.obj) <= 1e-6 * abs(ro.obj)
+    if prec == "fp64":
+        assert res["iters"] == ro.iters
+        assert np.max(np.abs(v - ro.v)) < 1e-6
+    net.free()
+
+
+def test_box_only_network_with_slack_margin(nnc):
+    """A net whose margins hold with slack at the start: the solution is x = x0 (objective 0)."""
+    spec = MLPSpec([20, 16, 3], ["tanh", "identity"])
+    mlp = make_mlp(spec, seed=7, tag="easy")
+    mlp.b[1][:] = [0.0, 5.0, 0.0]      # class 1 wins by ~5 everywhere in the box
+    x0 = synth.uniform01(synth.derive_key(7, "easy-x0"), 20)
+    net = nnc.Net.from_mlp(mlp, precision="fp64")
+    res, v, lam = nnc.ipm_adversarial(net, x0, target=1, margin=0.1)
+    assert res["status"] == 0
+    assert res["obj"] < 1e-8
+    assert np.max(np.abs(v[:20] - x0)) < 1e-4
+    net.free()
+
+
+def test_iteration_limit_status(nnc):
+    mlp = make_mlp(synth.TINY, seed=0)
+    d = synth.adversarial_data(seed=0)
+    net = nnc.Net.from_mlp(mlp, precision="fp64")
+    res, _, _ = nnc.ipm_adversarial(net, d.x0, d.target, d.margin, max_iter=2)
+    assert res["status"] == 1 and res["iters"] == 2
+    net.free()

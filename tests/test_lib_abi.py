@@ -10,9 +10,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "nnc.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(nnc_[a-z0-9_]+)\s*\(", src)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(nnc_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_build_and_exports():
@@ -26,6 +30,18 @@ def test_build_and_exports():
         assert hasattr(lib, name), name
     from paper_2509_22462_gb300 import nnc
     assert sorted(nnc.EXPORTS) == sorted(names)
+
+
+def test_ipm_option_defaults_match_oracle():
+    """The C driver's defaults are the constants of the oracle's reading of Eq. 2."""
+    from paper_2509_22462_gb300 import nnc
+    from oracle import ipm
+    o = nnc.ipm_options()
+    ref = ipm.Options()
+    for name, _ in nnc.IpmOptions._fields_:
+        if name == "verbose":
+            continue
+        assert getattr(o, name) == getattr(ref, name), name
 
 
 def test_status_codes_match_header():
