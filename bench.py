@@ -43,6 +43,7 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64-form", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-ipm", action="store_true")
     return p.parse_args()
 
 
@@ -345,11 +346,20 @@ def run_ours(args, rank, world, local_rank):
         e2e = {"value": world * args.steps / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
+    # IPM solve of the adversarial problem to KKT tolerance 1e-6 with this form
+    ipm = {}
+    if rank == 0 and not args.no_ipm:
+        res, v, lam_ipm = nnc.ipm_adversarial(net, d.x0, d.target, d.margin)
+        ipm[args.prec] = res
+
     # the FP64 form on the same GPU, for the TC-vs-FP64 comparison of the metric
     forms = {args.prec: {"evals_per_s": value / world, "ms_per_eval": el_ms / args.steps}}
     if rank == 0 and not args.no_fp64_form and args.prec != "fp64":
         net.free()
         n64 = nnc.Net.from_mlp(mlp, precision="fp64")
+        if not args.no_ipm:
+            res, v, lam_ipm = nnc.ipm_adversarial(n64, d.x0, d.target, d.margin)
+            ipm["fp64"] = res
 
         def step64():
             n64.eval_all_dev(x, lam, y, J, H, g)
@@ -375,7 +385,7 @@ def run_ours(args, rank, world, local_rank):
                ("f32" if args.prec == "fp32" else "f64"),
                "data": "synthetic", "config": _workload_config(spec, args.workload, args.prec),
                "roofline": roof, "cpu_baseline": cpu_baseline, "e2e": e2e, "gpu_launches": launches,
-               "clocks": clk, "kernels": kernel_ms, "forms": forms,
+               "clocks": clk, "kernels": kernel_ms, "forms": forms, "ipm_solve": ipm,
                "hessian_algorithmic_gflop": hessian_flops(spec) / 1e9}
         print(json.dumps(out), flush=True)
     return 0

@@ -19,7 +19,7 @@ __global__ void __launch_bounds__(256) k_simt_gemm(const T* __restrict__ A, int 
                                                    const double* __restrict__ s1,
                                                    const double* __restrict__ c,
                                                    T* __restrict__ At, T* __restrict__ Zt,
-                                                   T* __restrict__ Yt, int ldo,
+                                                   T* __restrict__ Yt, int ldo, int ldz,
                                                    double* __restrict__ Hp) {
   constexpr int BM = 16 * TM, BN = 16 * TN, BK = 16;
   __shared__ T As[BK][BM + 1];
@@ -74,10 +74,12 @@ __global__ void __launch_bounds__(256) k_simt_gemm(const T* __restrict__ A, int 
         const int n = n0 + ty + 16 * j;
         if (n >= N) continue;
         const double v = (double)acc[i][j];
-        const size_t o = (size_t)n * ldo + m;
-        if (At) At[o] = (T)(sm * v);
-        Zt[o] = (T)v;
-        Yt[o] = (T)(cm * v);
+        if (At) At[(size_t)n * ldo + m] = (T)(sm * v);
+        if (Zt) {
+          const size_t oz = (size_t)n * ldz + m;
+          Zt[oz] = (T)v;
+          Yt[oz] = (T)(cm * v);
+        }
       }
     }
   } else {
@@ -97,18 +99,18 @@ __global__ void __launch_bounds__(256) k_simt_gemm(const T* __restrict__ A, int 
 }
 
 cudaError_t launch_simt_tangent(bool fp64, const void* A, int lda, const void* B, int ldb, int M,
-                                int N, int K, const double* s1, const double* c, void* At,
-                                void* Zt, void* Yt, int ldo, cudaStream_t st) {
+                                int N, int K, const double* s1, const double* c, void* At, int ldo,
+                                void* Zt, void* Yt, int ldz, cudaStream_t st) {
   if (fp64) {
     dim3 grid((N + 63) / 64, (M + 63) / 64, 1);
     k_simt_gemm<double, 4, 4, EPI_TANGENT><<<grid, 256, 0, st>>>(
         (const double*)A, lda, (const double*)B, ldb, M, N, K, K, s1, c, (double*)At, (double*)Zt,
-        (double*)Yt, ldo, nullptr);
+        (double*)Yt, ldo, ldz, nullptr);
   } else {
     dim3 grid((N + 127) / 128, (M + 127) / 128, 1);
     k_simt_gemm<float, 8, 8, EPI_TANGENT><<<grid, 256, 0, st>>>(
         (const float*)A, lda, (const float*)B, ldb, M, N, K, K, s1, c, (float*)At, (float*)Zt,
-        (float*)Yt, ldo, nullptr);
+        (float*)Yt, ldo, ldz, nullptr);
   }
   note_launch();
   return cudaGetLastError();
@@ -121,12 +123,12 @@ cudaError_t launch_simt_syrk(bool fp64, const void* Zt, const void* Yt, int ld, 
     dim3 grid((n + 63) / 64, (n + 63) / 64, splits);
     k_simt_gemm<double, 4, 4, EPI_SYRK><<<grid, 256, 0, st>>>(
         (const double*)Zt, ld, (const double*)Yt, ld, n, n, K, kps, nullptr, nullptr, nullptr,
-        nullptr, nullptr, 0, Hp);
+        nullptr, nullptr, 0, 0, Hp);
   } else {
     dim3 grid((n + 127) / 128, (n + 127) / 128, splits);
     k_simt_gemm<float, 8, 8, EPI_SYRK><<<grid, 256, 0, st>>>(
         (const float*)Zt, ld, (const float*)Yt, ld, n, n, K, kps, nullptr, nullptr, nullptr,
-        nullptr, nullptr, 0, Hp);
+        nullptr, nullptr, 0, 0, Hp);
   }
   note_launch();
   return cudaGetLastError();

@@ -35,7 +35,8 @@ struct TcArgs {
   const double* s1;
   const float* c;
   __nv_bfloat16 *at_hi, *at_lo, *zt_hi, *zt_lo, *yt_hi, *yt_lo;
-  int ldo;
+  int ldo;   // row stride of at_*
+  int ldz;   // row stride of zt_* / yt_*
   float* Hp;
   int* err;
 };
@@ -288,10 +289,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int j = 0; j < 16; ++j) {
             const int n = n0 + c0 + j;
             if (n < args.N) {
-              const size_t o = (size_t)n * args.ldo + m;
-              if (args.at_hi) put<X3>(args.at_hi, args.at_lo, o, sm * v[j]);
-              put<X3>(args.zt_hi, args.zt_lo, o, v[j]);
-              put<X3>(args.yt_hi, args.yt_lo, o, cm * v[j]);
+              if (args.at_hi) put<X3>(args.at_hi, args.at_lo, (size_t)n * args.ldo + m, sm * v[j]);
+              if (args.zt_hi) {
+                const size_t oz = (size_t)n * args.ldz + m;
+                put<X3>(args.zt_hi, args.zt_lo, oz, v[j]);
+                put<X3>(args.yt_hi, args.yt_lo, oz, cm * v[j]);
+              }
             }
           }
         }
@@ -463,8 +466,8 @@ int tc_plan_make(TcPlan& p, int kind, int prec, const void* a_hi, const void* a_
 }
 
 cudaError_t tc_tangent(const TcPlan& p, const double* s1, const float* c, void* at_hi, void* at_lo,
-                       void* zt_hi, void* zt_lo, void* yt_hi, void* yt_lo, int ldo, int* err,
-                       cudaStream_t st) {
+                       int ldo, void* zt_hi, void* zt_lo, void* yt_hi, void* yt_lo, int ldz,
+                       int* err, cudaStream_t st) {
   if (!p.ready || p.kind != TC_TANGENT) return cudaErrorInvalidValue;
   TcArgs a{};
   a.M = p.M;
@@ -483,6 +486,7 @@ cudaError_t tc_tangent(const TcPlan& p, const double* s1, const float* c, void* 
   a.yt_hi = (__nv_bfloat16*)yt_hi;
   a.yt_lo = (__nv_bfloat16*)yt_lo;
   a.ldo = ldo;
+  a.ldz = ldz;
   a.err = err;
   return launch_any<TC_TANGENT>(p, a, dim3(p.ntn, p.ntm, 1), st);
 }

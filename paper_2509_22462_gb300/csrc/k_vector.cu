@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(256) k_gemv_fwd(const TW* __restrict__ W, int 
     const float4* a4 = reinterpret_cast<const float4*>(a_in_v);
     const int nk4 = (k + 3) >> 2;
     float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
-#pragma unroll 4
+#pragma unroll 8
     for (int j = lane; j < nk4; j += 32) {
       const float4 w = __ldg(r4 + j);
       const float4 a = a4[j];
@@ -197,7 +197,10 @@ __global__ void k_rev_reduce(const TP* __restrict__ part, int chunks, int kcols,
   if (idx >= kcols * S) return;
   const int kk = idx / S, s = idx % S;
   double v = 0.0;
-  for (int c = 0; c < chunks; ++c) v += (double)part[((size_t)c * kcols + kk) * S + s];
+  const size_t stride = (size_t)kcols * S;
+  const TP* pp = part + idx;
+#pragma unroll 8
+  for (int c = 0; c < chunks; ++c) v += (double)pp[c * stride];
   if (Zbar_out) Zbar_out[idx] = s1 ? s1[kk] * v : v;
   if (s == lam_col) {
     if (c_out) c_out[kk] = s2[kk] * v;
@@ -256,14 +259,13 @@ cudaError_t launch_rev_seed(int m, int S, int nJ, int lam_col, const double* s1,
 // ------------------------------------------------------------------ first-layer tangents
 // Zdot_1 = W_1 I = W_1, so the tangents of layer 1 are a scaled transpose of W_1.  32 x 32
 // tiles through shared memory keep both the read (along n) and the write (along m) coalesced.
+// The FP32 copy of W_1 is used (FP64 for the FP64 form); the scaling runs in the same type.
 template <Elem E>
-__device__ __forceinline__ void put_tan(TanBuf b, size_t i, double v) {
-  if constexpr (E == Elem::F64) {
-    ((double*)b.hi)[i] = v;
-  } else if constexpr (E == Elem::F32) {
-    ((float*)b.hi)[i] = (float)v;
+__device__ __forceinline__ void put_tan(TanBuf b, size_t i, float v) {
+  if constexpr (E == Elem::F32) {
+    ((float*)b.hi)[i] = v;
   } else if constexpr (E == Elem::BF16) {
-    ((__nv_bfloat16*)b.hi)[i] = __double2bfloat16(v);
+    ((__nv_bfloat16*)b.hi)[i] = __float2bfloat16_rn(v);
   } else {
     __nv_bfloat16 h, l;
     split_bf16(v, h, l);
@@ -272,46 +274,61 @@ __device__ __forceinline__ void put_tan(TanBuf b, size_t i, double v) {
   }
 }
 
-template <Elem E>
-__global__ void k_first_tangent(const double* __restrict__ W1, int ldw, int m_pad, int n,
+template <Elem E, typename TW>
+__global__ void k_first_tangent(const TW* __restrict__ W1, int ldw, int m_pad, int n,
                                 const double* __restrict__ s1, const double* __restrict__ c,
-                                TanBuf At, TanBuf Zt, TanBuf Yt, int ld_out) {
-  __shared__ double tile[32][33];
+                                TanBuf At, int lda, TanBuf Zt, TanBuf Yt, int ldz) {
+  __shared__ TW tile[32][33];
   const int m0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int mm = m0 + r, nn = n0 + threadIdx.x;
-    tile[r][threadIdx.x] = (mm < m_pad && nn < n) ? W1[(size_t)mm * ldw + nn] : 0.0;
+    tile[r][threadIdx.x] = (mm < m_pad && nn < n) ? W1[(size_t)mm * ldw + nn] : TW(0);
   }
   __syncthreads();
+  const int mm = m0 + threadIdx.x;
+  if (mm >= m_pad) return;
+  const TW sm = (TW)s1[mm], cm = (TW)c[mm];
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const int nn = n0 + r, mm = m0 + threadIdx.x;
-    if (nn < n && mm < m_pad) {
-      const double w = tile[threadIdx.x][r];
-      const size_t o = (size_t)nn * ld_out + mm;
-      if (At.hi) put_tan<E>(At, o, s1[mm] * w);
-      put_tan<E>(Zt, o, w);
-      put_tan<E>(Yt, o, c[mm] * w);
+    const int nn = n0 + r;
+    if (nn >= n) continue;
+    const TW w = tile[threadIdx.x][r];
+    if constexpr (E == Elem::F64) {
+      if (At.hi) ((double*)At.hi)[(size_t)nn * lda + mm] = sm * w;
+      if (Zt.hi) {
+        ((double*)Zt.hi)[(size_t)nn * ldz + mm] = w;
+        ((double*)Yt.hi)[(size_t)nn * ldz + mm] = cm * w;
+      }
+    } else {
+      if (At.hi) put_tan<E>(At, (size_t)nn * lda + mm, sm * w);
+      if (Zt.hi) {
+        put_tan<E>(Zt, (size_t)nn * ldz + mm, w);
+        put_tan<E>(Yt, (size_t)nn * ldz + mm, cm * w);
+      }
     }
   }
 }
 
-cudaError_t launch_first_tangent(Elem e, const double* W1, int ldw, int m_pad, int n,
-                                 const double* s1, const double* c, TanBuf At, TanBuf Zt,
-                                 TanBuf Yt, int ld_out, cudaStream_t st) {
+cudaError_t launch_first_tangent(Elem e, const void* W1, int ldw, int m_pad, int n,
+                                 const double* s1, const double* c, TanBuf At, int lda, TanBuf Zt,
+                                 TanBuf Yt, int ldz, cudaStream_t st) {
   dim3 grid((n + 31) / 32, (m_pad + 31) / 32), block(32, 8);
+  const float* Wf = (const float*)W1;
   switch (e) {
     case Elem::F64:
-      k_first_tangent<Elem::F64><<<grid, block, 0, st>>>(W1, ldw, m_pad, n, s1, c, At, Zt, Yt, ld_out);
+      k_first_tangent<Elem::F64, double><<<grid, block, 0, st>>>((const double*)W1, ldw, m_pad, n, s1,
+                                                                 c, At, lda, Zt, Yt, ldz);
       break;
     case Elem::F32:
-      k_first_tangent<Elem::F32><<<grid, block, 0, st>>>(W1, ldw, m_pad, n, s1, c, At, Zt, Yt, ld_out);
+      k_first_tangent<Elem::F32, float><<<grid, block, 0, st>>>(Wf, ldw, m_pad, n, s1, c, At, lda, Zt,
+                                                                Yt, ldz);
       break;
     case Elem::BF16:
-      k_first_tangent<Elem::BF16><<<grid, block, 0, st>>>(W1, ldw, m_pad, n, s1, c, At, Zt, Yt, ld_out);
+      k_first_tangent<Elem::BF16, float><<<grid, block, 0, st>>>(Wf, ldw, m_pad, n, s1, c, At, lda,
+                                                                 Zt, Yt, ldz);
       break;
     case Elem::BF16X3:
-      k_first_tangent<Elem::BF16X3><<<grid, block, 0, st>>>(W1, ldw, m_pad, n, s1, c, At, Zt, Yt,
-                                                            ld_out);
+      k_first_tangent<Elem::BF16X3, float><<<grid, block, 0, st>>>(Wf, ldw, m_pad, n, s1, c, At, lda,
+                                                                   Zt, Yt, ldz);
       break;
   }
   note_launch();
@@ -319,25 +336,40 @@ cudaError_t launch_first_tangent(Elem e, const double* W1, int ldw, int m_pad, i
 }
 
 // ------------------------------------------------------------------ Hessian finish
+// H[i][j] = sum_s Hp[s][max(i,j)][min(i,j)]: the split partial sums hold the lower triangle; a
+// 32 x 32 tile of H and its mirror tile are read coalesced and written coalesced.
 template <typename TP>
 __global__ void k_h_finish(const TP* __restrict__ Hp, int splits, int n, int ldp,
                            double* __restrict__ H) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = blockIdx.y;
-  if (j >= n) return;
-  const int r = i > j ? i : j, c = i > j ? j : i;
-  double v = 0.0;
-  for (int s = 0; s < splits; ++s) v += (double)Hp[((size_t)s * n + r) * ldp + c];
-  H[(size_t)i * n + j] = v;
+  __shared__ double t[32][33];
+  const int bi = blockIdx.y, bj = blockIdx.x;   // tile row / column of H
+  const int i0 = bi * 32, j0 = bj * 32;
+  // source tile: lower-triangle storage of block (max, min)
+  const int r0 = bi >= bj ? i0 : j0, c0 = bi >= bj ? j0 : i0;
+  for (int rr = threadIdx.y; rr < 32; rr += blockDim.y) {
+    const int r = r0 + rr, c = c0 + threadIdx.x;
+    double v = 0.0;
+    if (r < n && c < n) {
+      const int R = r >= c ? r : c, C = r >= c ? c : r;
+#pragma unroll 4
+      for (int s = 0; s < splits; ++s) v += (double)Hp[((size_t)s * n + R) * ldp + C];
+    }
+    t[rr][threadIdx.x] = v;
+  }
+  __syncthreads();
+  for (int rr = threadIdx.y; rr < 32; rr += blockDim.y) {
+    const int i = i0 + rr, j = j0 + threadIdx.x;
+    if (i < n && j < n) H[(size_t)i * n + j] = bi >= bj ? t[rr][threadIdx.x] : t[threadIdx.x][rr];
+  }
 }
 
 cudaError_t launch_h_finish(bool part_f32, const void* Hp, int splits, int n, int ldp, double* H,
                             cudaStream_t st) {
-  dim3 grid((n + 127) / 128, n);
+  dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
   if (part_f32)
-    k_h_finish<float><<<grid, 128, 0, st>>>((const float*)Hp, splits, n, ldp, H);
+    k_h_finish<float><<<grid, block, 0, st>>>((const float*)Hp, splits, n, ldp, H);
   else
-    k_h_finish<double><<<grid, 128, 0, st>>>((const double*)Hp, splits, n, ldp, H);
+    k_h_finish<double><<<grid, block, 0, st>>>((const double*)Hp, splits, n, ldp, H);
   note_launch();
   return cudaGetLastError();
 }

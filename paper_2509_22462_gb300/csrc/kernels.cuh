@@ -36,10 +36,12 @@ cudaError_t launch_rev_reduce(bool fp64, const void* part, int chunks, int kcols
 cudaError_t launch_rev_seed(int m, int S, int nJ, int lam_col, const double* s1, const double* s2,
                             const double* lam, double* Zbar, double* c_out, float* c_out_f,
                             cudaStream_t st);
-// First-layer tangents: Zdot_1 = W_1, so At[n][m] = s1[m] W1[m][n], Zt = W1^T, Yt = c[m] W1[m][n].
-cudaError_t launch_first_tangent(Elem e, const double* W1, int ldw, int m_pad, int n,
-                                 const double* s1, const double* c, TanBuf At, TanBuf Zt,
-                                 TanBuf Yt, int ld_out, cudaStream_t st);
+// First-layer tangents: Zdot_1 = W_1, so At[n][m] = s1[m] W1[m][n] (row stride lda), and
+// Zt = W1^T, Yt[n][m] = c[m] W1[m][n] (row stride ldz; skipped if Zt.hi is NULL).  W1 is the
+// FP32 copy of the first layer (the FP64 copy for the FP64 form).
+cudaError_t launch_first_tangent(Elem e, const void* W1, int ldw, int m_pad, int n,
+                                 const double* s1, const double* c, TanBuf At, int lda, TanBuf Zt,
+                                 TanBuf Yt, int ldz, cudaStream_t st);
 // H[i][j] = sum_s Hp[s][max(i,j)][min(i,j)]  (exactly symmetric); Hp is double or float.
 cudaError_t launch_h_finish(bool part_f32, const void* Hp, int splits, int n, int ldp, double* H,
                             cudaStream_t st);
@@ -51,10 +53,11 @@ cudaError_t launch_copy_pad(const double* src, double* dst, float* dst_f, int n,
 
 // ---- CUDA-core GEMMs for the FP64 / FP32 forms (k_simt.cu)
 // D[m][n] = sum_k A[m][k] B[n][k] (both K-major).
-// Tangent epilogue: At[n][m] = s1[m] D, Zt[n][m] = D, Yt[n][m] = c[m] D  (n < N).
+// Tangent epilogue: At[n][m] = s1[m] D (row stride ldo; At may be NULL), Zt[n][m] = D and
+// Yt[n][m] = c[m] D (row stride ldz; both may be NULL)  for n < N.
 cudaError_t launch_simt_tangent(bool fp64, const void* A, int lda, const void* B, int ldb, int M,
-                                int N, int K, const double* s1, const double* c, void* At,
-                                void* Zt, void* Yt, int ldo, cudaStream_t st);
+                                int N, int K, const double* s1, const double* c, void* At, int ldo,
+                                void* Zt, void* Yt, int ldz, cudaStream_t st);
 // Symmetric-product epilogue: Hp[s][i][j] += D over the lower-triangle tiles, split-K `splits`.
 cudaError_t launch_simt_syrk(bool fp64, const void* Zt, const void* Yt, int ld, int n, int K,
                              int splits, double* Hp, cudaStream_t st);

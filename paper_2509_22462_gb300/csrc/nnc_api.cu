@@ -27,6 +27,7 @@ static int fail(int code, const std::string& msg) {
   g_err = msg;
   return code;
 }
+void set_last_error(const std::string& msg) { g_err = msg; }
 }  // namespace nnc
 
 using namespace nnc;
@@ -46,7 +47,7 @@ struct LayerDev {
   double* ra = nullptr;           // FP64-residual pass activations [mp]
   float* af = nullptr;            // FP32 copy of a_l [mp] (input of the next FP32 layer)
   TcPlan plan_tan;                // tensor-core plan of this layer's tangent GEMM
-  TcPlan plan_syrk;               // tensor-core plan of this layer's symmetric product
+  int zy_off = -1;                // column offset of this layer's Zdot / Ydot block (-1: none)
 };
 
 struct nnc_net {
@@ -68,8 +69,10 @@ struct nnc_net {
   double* gdev = nullptr;    // [n_in]
   double* Hdev = nullptr;    // [n_in][n_in]
   void* At[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [ping-pong][hi, lo]
-  void* Zt[2] = {nullptr, nullptr};
-  void* Yt[2] = {nullptr, nullptr};
+  void* Zt[2] = {nullptr, nullptr};  // [hi, lo]: Zdot_l^T of all curved layers, n x K_total
+  void* Yt[2] = {nullptr, nullptr};  // [hi, lo]: (c_l * Zdot_l)^T, n x K_total
+  int K_total = 0;                   // sum of mp_l over layers with sigma'' != 0
+  TcPlan plan_syrk;                  // tensor-core plan of the one symmetric product
   void* Hp = nullptr;        // split partial sums of H (double for CUDA-core forms, float for TC)
   int h_splits = 1;
   bool hp_f32 = false;
@@ -236,54 +239,68 @@ int run_reverse(nnc_net* net, bool fp64, int nJ, bool with_lam, const double* la
 }
 
 // ---------------------------------------------------------------- tangent sweep + H
+// Forward tangents layer by layer (Zdot_1 = W_1 elementwise; Zdot_l = W_l Adot_{l-1} as a GEMM
+// with the n_in tangents as columns), each layer's Zdot_l and c_l * Zdot_l stored side by side
+// along K; then one symmetric product H = sum_l Zdot_l^T diag(c_l) Zdot_l.
 int run_hessian(nnc_net* net, double* H, cudaStream_t st) {
   const int n = net->n_in;
   const int prec = net->prec;
   const bool tc = is_tc(prec);
   const Elem e = tan_elem(prec);
-  const size_t hp_bytes = (size_t)net->h_splits * n * n * (net->hp_f32 ? 4 : 8);
-  CK(cudaMemsetAsync(net->Hp, 0, hp_bytes, st));
-  LayerDev& L1 = net->layers[0];
-  TanBuf At0{net->At[0][0], net->At[0][1]}, Zt{net->Zt[0], net->Zt[1]}, Yt{net->Yt[0], net->Yt[1]};
-  CK(launch_first_tangent(e, L1.W64, L1.kp, L1.mp, n, L1.s1, L1.c, net->L > 1 ? At0 : TanBuf{},
-                          Zt, Yt, L1.mp, st));
-  auto syrk = [&](LayerDev& Ly) -> int {
-    if (Ly.act == NNC_IDENTITY) return NNC_OK;  // sigma'' = 0: no curvature from this layer
-    PROF(PK_SYRK);
-    if (tc) {
-      CK(tc_syrk(Ly.plan_syrk, (float*)net->Hp, net->dev_err, st));
-    } else {
-      CK(launch_simt_syrk(prec == NNC_FP64, net->Zt[0], net->Yt[0], Ly.mp, n, Ly.mp, net->h_splits,
-                          (double*)net->Hp, st));
-    }
-    return NNC_OK;
+  const size_t es = elem_size(prec);
+  auto zoff = [&](void* base, int off) -> void* {
+    return (base && off >= 0) ? (void*)((char*)base + (size_t)off * es) : nullptr;
   };
-  int r = syrk(L1);
-  if (r != NNC_OK) return r;
+  LayerDev& L1 = net->layers[0];
+  {
+    PROF(PK_OTHER);
+    TanBuf At0{net->At[0][0], net->At[0][1]};
+    TanBuf Zt{zoff(net->Zt[0], L1.zy_off), zoff(net->Zt[1], L1.zy_off)};
+    TanBuf Yt{zoff(net->Yt[0], L1.zy_off), zoff(net->Yt[1], L1.zy_off)};
+    CK(launch_first_tangent(e, prec == NNC_FP64 ? (const void*)L1.W64 : (const void*)L1.W32, L1.kp,
+                            L1.mp, n, L1.s1, L1.c, net->L > 1 ? At0 : TanBuf{}, L1.mp, Zt, Yt,
+                            net->K_total, st));
+  }
   int cur = 0;
   for (int l = 1; l < net->L; ++l) {
     LayerDev& Ly = net->layers[l];
     const bool last = (l == net->L - 1);
-    if (last && Ly.act == NNC_IDENTITY) break;  // linear output layer adds nothing to H
+    if (last && Ly.zy_off < 0) break;  // a linear output layer adds nothing to H
     void* Anext_hi = last ? nullptr : net->At[1 - cur][0];
     void* Anext_lo = last ? nullptr : net->At[1 - cur][1];
-    {
-      PROF(PK_TANGENT);
-      if (tc) {
-        CK(tc_tangent(Ly.plan_tan, Ly.s1, Ly.c_f, Anext_hi, Anext_lo, net->Zt[0], net->Zt[1],
-                      net->Yt[0], net->Yt[1], Ly.mp, net->dev_err, st));
-      } else {
-        CK(launch_simt_tangent(prec == NNC_FP64,
-                               prec == NNC_FP64 ? (const void*)Ly.W64 : (const void*)Ly.W32,
-                               Ly.kp, net->At[cur][0], Ly.kp, Ly.mp, n, Ly.kp, Ly.s1, Ly.c,
-                               Anext_hi, net->Zt[0], net->Yt[0], Ly.mp, st));
-      }
+    PROF(PK_TANGENT);
+    if (tc) {
+      CK(tc_tangent(Ly.plan_tan, Ly.s1, Ly.c_f, Anext_hi, Anext_lo, Ly.mp,
+                    zoff(net->Zt[0], Ly.zy_off), zoff(net->Zt[1], Ly.zy_off),
+                    zoff(net->Yt[0], Ly.zy_off), zoff(net->Yt[1], Ly.zy_off), net->K_total,
+                    net->dev_err, st));
+    } else {
+      CK(launch_simt_tangent(prec == NNC_FP64,
+                             prec == NNC_FP64 ? (const void*)Ly.W64 : (const void*)Ly.W32, Ly.kp,
+                             net->At[cur][0], Ly.kp, Ly.mp, n, Ly.kp, Ly.s1, Ly.c, Anext_hi, Ly.mp,
+                             zoff(net->Zt[0], Ly.zy_off), zoff(net->Yt[0], Ly.zy_off),
+                             net->K_total, st));
     }
-    r = syrk(Ly);
-    if (r != NNC_OK) return r;
     cur = 1 - cur;
   }
-  CK(launch_h_finish(net->hp_f32, net->Hp, net->h_splits, n, n, H, st));
+  if (net->K_total == 0) {  // every layer is linear: H = 0
+    CK(cudaMemsetAsync(H, 0, sizeof(double) * n * n, st));
+    return NNC_OK;
+  }
+  {
+    PROF(PK_SYRK);
+    const size_t hp_bytes = (size_t)net->h_splits * n * n * (net->hp_f32 ? 4 : 8);
+    CK(cudaMemsetAsync(net->Hp, 0, hp_bytes, st));
+    if (tc)
+      CK(tc_syrk(net->plan_syrk, (float*)net->Hp, net->dev_err, st));
+    else
+      CK(launch_simt_syrk(prec == NNC_FP64, net->Zt[0], net->Yt[0], net->K_total, n, net->K_total,
+                          net->h_splits, (double*)net->Hp, st));
+  }
+  {
+    PROF(PK_OTHER);
+    CK(launch_h_finish(net->hp_f32, net->Hp, net->h_splits, n, n, H, st));
+  }
   return NNC_OK;
 }
 
@@ -474,9 +491,15 @@ static int load_impl(nnc_net* net, int n_layers, const int* widths, const int* a
   AL(net->gdev, net->n_in_pad);
   AL(net->Hdev, (size_t)net->n_in * net->n_in);
   AL(net->dev_err, 1);
-  // tangent buffers: n_in rows of mp_max elements
+  // tangent buffers: Adot ping-pong (n_in x mp_max) and the side-by-side Zdot / Ydot blocks
   const int n = net->n_in;
+  net->K_total = 0;
+  for (auto& Ly : net->layers) {
+    Ly.zy_off = Ly.act == NNC_IDENTITY ? -1 : net->K_total;
+    if (Ly.zy_off >= 0) net->K_total += Ly.mp;
+  }
   const size_t tan_elems = (size_t)n * mp_max;
+  const size_t zy_elems = (size_t)n * std::max(net->K_total, kPad);
   const size_t es = elem_size(prec);
   const bool x3 = prec == NNC_BF16X3;
   unsigned char* p;
@@ -488,33 +511,30 @@ static int load_impl(nnc_net* net, int n_layers, const int* widths, const int* a
       net->At[pp][1] = p;
     }
   }
-  AL(p, tan_elems * es);
-  net->Zt[0] = p;
-  AL(p, tan_elems * es);
-  net->Yt[0] = p;
-  if (x3) {
-    AL(p, tan_elems * es);
-    net->Zt[1] = p;
-    AL(p, tan_elems * es);
-    net->Yt[1] = p;
+  for (int part = 0; part < (x3 ? 2 : 1); ++part) {
+    AL(p, zy_elems * es);
+    net->Zt[part] = p;
+    AL(p, zy_elems * es);
+    net->Yt[part] = p;
   }
   // split-K partial sums of H
   if (tc) {
     net->hp_f32 = true;
-    int splits = 1;
-    for (int l = 0; l < n_layers; ++l) {
+    for (int l = 1; l < n_layers; ++l) {
       LayerDev& Ly = net->layers[l];
-      int r = tc_plan_make(Ly.plan_syrk, TC_SYRK, prec, net->Zt[0], net->Zt[1], n, Ly.mp,
-                           net->Yt[0], net->Yt[1], n, Ly.mp, n, n, Ly.mp, net->sm_count);
+      const int cur = (l - 1) % 2;
+      int r = tc_plan_make(Ly.plan_tan, TC_TANGENT, prec, Ly.Whi, Ly.Wlo, Ly.mp, Ly.kp,
+                           net->At[cur][0], net->At[cur][1], n, Ly.kp, Ly.mp, n, Ly.kp,
+                           net->sm_count);
+      if (r != NNC_OK) return fail(r, "tensor-core tangent plan failed");
+    }
+    int splits = 1;
+    if (net->K_total > 0) {
+      int r = tc_plan_make(net->plan_syrk, TC_SYRK, prec, net->Zt[0], net->Zt[1], n, net->K_total,
+                           net->Yt[0], net->Yt[1], n, net->K_total, n, n, net->K_total,
+                           net->sm_count);
       if (r != NNC_OK) return fail(r, "tensor-core symmetric-product plan failed");
-      splits = std::max(splits, Ly.plan_syrk.splits);
-      if (l > 0) {
-        const int cur = (l - 1) % 2;
-        r = tc_plan_make(Ly.plan_tan, TC_TANGENT, prec, Ly.Whi, Ly.Wlo, Ly.mp, Ly.kp,
-                         net->At[cur][0], net->At[cur][1], n, Ly.kp, Ly.mp, n, Ly.kp,
-                         net->sm_count);
-        if (r != NNC_OK) return fail(r, "tensor-core tangent plan failed");
-      }
+      splits = net->plan_syrk.splits;
     }
     net->h_splits = splits;
     float* hp;
@@ -525,9 +545,7 @@ static int load_impl(nnc_net* net, int n_layers, const int* widths, const int* a
     const int T = (n + tile - 1) / tile;
     const int tiles = T * (T + 1) / 2;
     int splits = (2 * net->sm_count + tiles - 1) / tiles;
-    int kmin = mp_max;
-    for (auto& Ly : net->layers) kmin = std::min(kmin, Ly.mp);
-    splits = std::max(1, std::min(splits, kmin / 256));
+    splits = std::max(1, std::min(splits, std::max(net->K_total, kPad) / 256));
     net->h_splits = splits;
     net->hp_f32 = false;
     double* hp;

@@ -4,9 +4,10 @@
 // (optionally split into hi and lo parts), FP32 accumulation in tensor memory, and a fused
 // epilogue:
 //   tangent : A = W_l (mp x kp), B = Adot_{l-1}^T (n x kp);  writes Adot_l^T = sigma_l' * D,
-//             Zdot_l^T = D and Ydot_l^T = c_l * D (n x mp, BF16 hi/lo), c_l = sigma_l'' * abar_l
-//   syrk    : A = Zdot_l^T, B = Ydot_l^T (n x mp); adds D into the split-K partial sum of H
-//             over the lower-triangle tiles.
+//             Zdot_l^T = D and Ydot_l^T = c_l * D (BF16 hi/lo), c_l = sigma_l'' * abar_l; the
+//             Zdot / Ydot blocks of all layers sit side by side along K in one n x K_total array
+//   syrk    : A = [Zdot_1 .. Zdot_L]^T, B = [Ydot_1 .. Ydot_L]^T (n x K_total): one product
+//             H = sum_l Zdot_l^T diag(c_l) Zdot_l, split over K, lower-triangle tiles only.
 #pragma once
 #include <cuda.h>
 
@@ -34,9 +35,11 @@ int tc_plan_make(TcPlan& p, int kind, int prec, const void* a_hi, const void* a_
                  int ld_a, const void* b_hi, const void* b_lo, int b_rows, int ld_b, int M, int N,
                  int K, int sm_count, int force_bn = 0, int force_splits = 0);
 
+// at_* (row stride ldo) may be NULL on the last layer; zt_* / yt_* (row stride ldz) may be NULL
+// for a layer without curvature.
 cudaError_t tc_tangent(const TcPlan& p, const double* s1, const float* c, void* at_hi, void* at_lo,
-                       void* zt_hi, void* zt_lo, void* yt_hi, void* yt_lo, int ldo, int* err,
-                       cudaStream_t st);
+                       int ldo, void* zt_hi, void* zt_lo, void* yt_hi, void* yt_lo, int ldz,
+                       int* err, cudaStream_t st);
 
 // Hp: splits x N x N floats (row stride N); partial sums of the lower triangle are added.
 cudaError_t tc_syrk(const TcPlan& p, float* Hp, int* err, cudaStream_t st);
