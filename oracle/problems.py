@@ -75,3 +75,90 @@ def box_projection(x0):
                    lambda v: float((v - x0) @ (v - x0)), lambda v: 2.0 * (v - x0),
                    lambda v: 2.0 * np.eye(n), lambda v: np.zeros(0), lambda v: np.zeros((0, n)),
                    lambda v, lam: np.zeros((n, n)))
+
+
+# ---------------------------------------------------------------- SCOPF-shaped batch (Eq. 8 variant)
+
+
+def scopf_first_bias(data, k, d):
+    """First-layer bias of surrogate k under the load vector d: b_1^(k) + A_k d[B_k] (the load
+    dependence G_k(S^g, S^d) of Eq. 8 entering through the first layer)."""
+    net = data.nets[k]
+    return net.b[0] + data.load_proj[k] @ d[data.load_buses[k]]
+
+
+def scopf_surrogate(data, k, d, calibrate=True):
+    """The MLP of contingency k at load d, with its output bias calibrated so that the margin at
+    the flat dispatch xbar = (D(d)/G) 1 equals delta_k (strictly feasible start)."""
+    from copy import deepcopy
+    net = deepcopy(data.nets[k])
+    net.b[0] = scopf_first_bias(data, k, d)
+    if calibrate:
+        D = scopf_demand(data, d)
+        xbar = np.full(len(data.subsets[k]), D / data.G)
+        net.b[-1] = net.b[-1] - onn.value(net, xbar) + data.delta[k]
+    return net
+
+
+def scopf_demand(data, d):
+    """Total demand D(d) = 0.5 G mean(d): the generators run at half capacity on average."""
+    return 0.5 * data.G * float(np.mean(d))
+
+
+def scopf(data, d=None, nets=None):
+    """min sum_i c_i x_i^2  s.t.  y_k - NN_k(x[S_k]) = 0 (k < K),  sum_i x_i - D(d) = 0,
+    x in [0,1]^G, y_k >= 0 (every contingency keeps a non-negative stability margin).
+    Variables v = (x in R^G, y in R^K).  Start: x = xbar, y_k = NN_k(xbar) = delta_k."""
+    G, K = data.G, len(data.nets)
+    d = np.ones(data.n_bus) if d is None else np.asarray(d, dtype=np.float64)
+    nets = nets if nets is not None else [scopf_surrogate(data, k, d) for k in range(K)]
+    D = scopf_demand(data, d)
+    nv, m = G + K, K + 1
+    lb = np.concatenate([np.zeros(G), np.zeros(K)])
+    ub = np.concatenate([np.ones(G), np.full(K, np.inf)])
+    xbar = np.full(G, D / G)
+    v0 = np.concatenate([xbar, [onn.value(nets[k], xbar[data.subsets[k]])[0] for k in range(K)]])
+    cost = data.cost
+
+    def f(v):
+        return float(cost @ (v[:G] ** 2))
+
+    def grad_f(v):
+        g = np.zeros(nv)
+        g[:G] = 2.0 * cost * v[:G]
+        return g
+
+    def hess_f(v):
+        Hh = np.zeros((nv, nv))
+        Hh[:G, :G] = np.diag(2.0 * cost)
+        return Hh
+
+    def c(v):
+        x = v[:G]
+        out = np.empty(m)
+        for k in range(K):
+            out[k] = v[G + k] - onn.value(nets[k], x[data.subsets[k]])[0]
+        out[K] = x.sum() - D
+        return out
+
+    def jac_c(v):
+        x = v[:G]
+        A = np.zeros((m, nv))
+        for k in range(K):
+            A[k, data.subsets[k]] = -onn.jacobian(nets[k], x[data.subsets[k]])[0]
+            A[k, G + k] = 1.0
+        A[K, :G] = 1.0
+        return A
+
+    def hess_c(v, lam):
+        x = v[:G]
+        Hh = np.zeros((nv, nv))
+        for k in range(K):
+            S = data.subsets[k]
+            Hh[np.ix_(S, S)] -= onn.hessian_lag(nets[k], x[S], lam[k:k + 1])
+        return Hh
+
+    p = Problem(nv, m, lb, ub, v0, f, grad_f, hess_f, c, jac_c, hess_c)
+    p.nets = nets
+    p.demand = D
+    return p
