@@ -143,6 +143,24 @@ long long nnc_launch_count(void);
 int nnc_profile(nnc_net* net, int enable);
 int nnc_profile_read(nnc_net* net, double* ms, long long* count, int n_kinds);
 
+/* r = y - NN(x) in FP64 without allocating any device memory.  The paper has no counterpart:
+ * this entry point serves callers that cannot call cudaMalloc (code running while a CUDA graph
+ * is being captured, or inside a host framework that owns the device allocator), and who
+ * therefore cannot create a net with nnc_load_weights.  The caller passes every buffer:
+ *   n_layers, widths (L+1 host ints, each in [1, 65536]), act (L host nnc_act codes);
+ *   W : L host pointers to device arrays, W[l] = d_{l+1} x d_l row-major FP64, no padding;
+ *   b : NULL, or L host pointers to device arrays of d_{l+1} doubles (entries may be NULL);
+ *   x (n_in), y (n_out), r (n_out): device arrays of doubles;  stream: cudaStream_t or NULL.
+ * The layer activations go to one file-scope device array of 2 x 65536 doubles (1 MiB), which
+ * every GPU that loads the library keeps until the process exits; a width above 65536 returns
+ * NNC_ERR_ARG.  The first call on a device looks up that array's address (with the device
+ * current), so make that first call before any stream capture.  All calls share the array:
+ * calls whose work overlaps on the GPU race and must be ordered by the caller.  The call is
+ * asynchronous on `stream`. */
+int nnc_residual_noalloc(int n_layers, const int* widths, const int* act, const double* const* W,
+                         const double* const* b, const double* x, const double* y, double* r,
+                         void* stream);
+
 #ifdef __cplusplus
 }
 #endif

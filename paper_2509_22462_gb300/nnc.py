@@ -25,7 +25,8 @@ EXPORTS = ["nnc_load_weights", "nnc_eval", "nnc_residual", "nnc_jacobian", "nnc_
            "nnc_eval_batched", "nnc_eval_dev", "nnc_residual_dev", "nnc_jacobian_dev",
            "nnc_hessian_lag_dev", "nnc_eval_all_dev", "nnc_free", "nnc_last_error",
            "nnc_net_info", "nnc_launch_count", "nnc_profile", "nnc_profile_read",
-           "nnc_ipm_default_options", "nnc_ipm_adversarial", "nnc_kkt_solve"]
+           "nnc_ipm_default_options", "nnc_ipm_adversarial", "nnc_kkt_solve",
+           "nnc_residual_noalloc"]
 IPM_STATUS = {0: "optimal", 1: "max_iter", 2: "linesearch_failed", 3: "nonfinite",
               4: "inertia_failed", 5: "eval_error"}
 
@@ -102,6 +103,9 @@ def load_library(path: str = LIB_PATH):
     lib.nnc_launch_count.restype = ctypes.c_longlong
     lib.nnc_profile.argtypes = [_P, ctypes.c_int]
     lib.nnc_ipm_default_options.argtypes = [ctypes.POINTER(IpmOptions)]
+    lib.nnc_residual_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_P),
+                                         ctypes.POINTER(_P), _P, _P, _P, _P]
     lib.nnc_kkt_solve.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _DP, _DP, _DP, _DP, _DP,
                                   ctypes.c_double, ctypes.c_double, _DP, ctypes.POINTER(ctypes.c_int)]
     lib.nnc_ipm_adversarial.argtypes = [_P, _DP, ctypes.c_int, ctypes.c_double,
@@ -302,3 +306,16 @@ def kkt_solve(WDD, WSS, sigma, AD, AS, rhs, delta_w=0.0, delta_c=0.0):
     _check(lib.nnc_kkt_solve(nd, ns, m, _dp(WDD), _dp(WSS), _dp(sigma), _dp(AD), _dp(AS),
                              float(delta_w), float(delta_c), _dp(x), inert))
     return x, tuple(inert)
+
+
+def residual_noalloc(widths, acts, W_dev, b_dev, x, y, r, stream=None):
+    """nnc_residual_noalloc: r = y - NN(x) in FP64 with caller-owned CUDA float64 tensors only
+    (W_dev[l] of shape (d_{l+1}, d_l), b_dev[l] or None); the library allocates nothing."""
+    lib = load_library()
+    L = len(widths) - 1
+    wid = (ctypes.c_int * (L + 1))(*[int(w) for w in widths])
+    act = (ctypes.c_int * L)(*[ACTS[a] if isinstance(a, str) else int(a) for a in acts])
+    Wp = (_P * L)(*[_tp(w) for w in W_dev])
+    bp = (_P * L)(*[_tp(v) for v in b_dev]) if b_dev is not None else None
+    _check(lib.nnc_residual_noalloc(L, wid, act, Wp, bp, _tp(x), _tp(y), _tp(r),
+                                    stream or _stream_ptr()))
