@@ -122,6 +122,41 @@ int nnc_hessian_lag_dev(nnc_net* net, const double* x, const double* lambda, dou
 int nnc_eval_all_dev(nnc_net* net, const double* x, const double* lambda, double* y, double* J,
                      double* H, double* grad, void* stream);
 
+/* ---- Grouped batch (many networks of equal hidden widths, different input sizes) ----------
+ * One stability-margin surrogate per contingency of Eq. 8: K nets with the same depth, hidden
+ * widths, activations and n_out (<= 3), each with its own n_in (<= 256), all BF16 or BF16X3.
+ * nnc_batch_create stacks their packed weights (the nets stay valid and unchanged) so that
+ * every step of the evaluation is one grouped launch for all K nets.  Concatenated layouts:
+ *   x_cat      : sum_k n_in_k doubles, net k's input at offset off_k = sum_{j<k} n_in_j;
+ *   lambda_cat : K x n_out;  y_cat, r_cat : K x n_out;  grad_cat : like x_cat;
+ *   J_cat      : net k's n_out x n_in_k block (row-major) at offset off_k * n_out;
+ *   H_cat      : net k's n_in_k x n_in_k block (row-major, symmetric) at offset
+ *                hoff_k = sum_{j<k} n_in_j^2.
+ * nnc_eval_batched uses this path (with a cached batch) when its nets qualify and evaluates
+ * the nets one after another otherwise. */
+typedef struct nnc_batch nnc_batch;
+int nnc_batch_create(nnc_batch** out, nnc_net* const* nets, int K, void* stream);
+void nnc_batch_free(nnc_batch* batch);
+/* K, n_out, sum_k n_in_k, sum_k n_in_k^2 (any pointer may be NULL). */
+int nnc_batch_info(const nnc_batch* batch, int* K, int* n_out, int* n_sum, long long* h_sum);
+/* Replace the biases of one layer of every net: bias = K x d_{layer+1} host doubles (problem
+ * data such as loads entering the first layer; the nets themselves are not changed). */
+int nnc_batch_set_bias(nnc_batch* batch, int layer, const double* bias);
+/* Capture one evaluation in a CUDA graph on first use and replay it while the device pointers
+ * passed to nnc_batch_eval_dev stay the same (enable = 0 drops the graph). */
+int nnc_batch_use_graph(nnc_batch* batch, int enable);
+/* Device pointers (any output may be NULL; lambda_cat needed for H or grad). */
+int nnc_batch_eval_dev(nnc_batch* batch, const double* x_cat, const double* lambda_cat,
+                       double* y_cat, double* J_cat, double* H_cat, double* grad_cat,
+                       void* stream);
+/* FP64 residual r_cat = y_cat - NN(x_cat) of every net (FP64 weights), device pointers. */
+int nnc_batch_residual_dev(nnc_batch* batch, const double* x_cat, const double* y_cat,
+                           double* r_cat, void* stream);
+/* Host-pointer twins (copy, run, copy back, wait). */
+int nnc_batch_eval(nnc_batch* batch, const double* x_cat, const double* lambda_cat, double* y_cat,
+                   double* J_cat, double* H_cat, double* grad_cat);
+int nnc_batch_residual(nnc_batch* batch, const double* x_cat, const double* y_cat, double* r_cat);
+
 /* Free a net and all of its device memory (waits for its stream).  NULL is ignored. */
 void nnc_free(nnc_net* net);
 

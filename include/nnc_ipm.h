@@ -92,6 +92,19 @@ int nnc_ipm_adversarial(nnc_net* net, const double* x0, int target, double margi
                         const nnc_ipm_options* opt, double* v_out, double* lam_out,
                         nnc_ipm_result* result);
 
+/* The SCOPF-shaped problem (a synthetic variant of Eq. 8), one surrogate per contingency in
+ * `batch` (n_out = 1; see nnc_batch_create):  variables v = (x in [0,1]^G, y in R^K, y >= 0);
+ *   min sum_i c_i x_i^2  s.t.  y_k - (NN_k(x[S_k]) + shift_k) = 0 (k < K),  sum_i x_i = demand,
+ * where shift_k = delta_k - NN_k(xbar[S_k]) puts every margin at delta_k for the flat dispatch
+ * xbar = demand / G (the start point).
+ *   n_in    : K ints, the input count of each surrogate (must match the batch);
+ *   subsets : sum_k n_in[k] ints, S_k concatenated (generator indices in [0, G));
+ *   cost    : G doubles;  delta : K doubles (> 0);  opt : NULL for defaults;
+ *   v_out   : G + K doubles (may be NULL);  lam_out : K + 1 doubles (may be NULL). */
+int nnc_ipm_scopf(nnc_batch* batch, int G, const int* n_in, const int* subsets, const double* cost,
+                  double demand, const double* delta, const nnc_ipm_options* opt, double* v_out,
+                  double* lam_out, nnc_ipm_result* result);
+
 #ifdef __cplusplus
 }
 #endif

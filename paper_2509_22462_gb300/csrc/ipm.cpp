@@ -710,9 +710,144 @@ struct Adversarial : IpmProblem {
   }
 };
 
+// ---------------------------------------------------------------- SCOPF-shaped batch problem
+// Variables v = (x in [0,1]^G | y in R^K, y >= 0).
+// min sum_i c_i x_i^2  s.t.  y_k - (NN_k(x[S_k]) + shift_k) = 0,  sum_i x_i - D = 0.
+// shift_k = delta_k - NN_k(xbar[S_k]) calibrates every margin to delta_k at xbar = D/G.
+struct Scopf : IpmProblem {
+  nnc_batch* b;
+  int G, K, n_sum;
+  long long h_sum;
+  std::vector<int> sub, off, nk;
+  std::vector<double> cost, shift, xc, yc, lc, Jc, Hc, rc;
+  double D;
+  Scopf(nnc_batch* b_, int G_, const int* subsets, const double* cost_, double D_)
+      : b(b_), G(G_), D(D_) {
+    int no = 0;
+    nnc_batch_info(b, &K, &no, &n_sum, &h_sum);
+    sub.assign(subsets, subsets + n_sum);
+    cost.assign(cost_, cost_ + G);
+    nd = G;
+    ns = K;
+    m = K + 1;
+    lb.assign(nd + ns, 0.0);
+    ub.assign(nd + ns, INFINITY);
+    for (int i = 0; i < G; ++i) ub[i] = 1.0;
+    xc.resize(n_sum);
+    yc.resize(K);
+    lc.resize(K);
+    Jc.resize(n_sum);
+    Hc.resize(h_sum);
+    rc.resize(K);
+    shift.assign(K, 0.0);
+  }
+  void set_offsets(const std::vector<int>& n_in) {
+    nk = n_in;
+    off.resize(K);
+    int o = 0;
+    for (int k = 0; k < K; ++k) {
+      off[k] = o;
+      o += nk[k];
+    }
+  }
+  void gather(const double* v) {
+    for (int j = 0; j < n_sum; ++j) xc[j] = v[sub[j]];
+  }
+  int start(const double* delta) {
+    v0.assign(nd + ns, D / G);
+    gather(v0.data());
+    std::fill(yc.begin(), yc.end(), 0.0);
+    int r = nnc_batch_residual(b, xc.data(), yc.data(), rc.data());  // r = -NN(xbar)
+    if (r) return r;
+    for (int k = 0; k < K; ++k) {
+      shift[k] = delta[k] + rc[k];
+      v0[G + k] = delta[k];
+    }
+    return NNC_OK;
+  }
+  double f(const double* v) override {
+    double s = 0;
+    for (int i = 0; i < G; ++i) s += cost[i] * v[i] * v[i];
+    return s;
+  }
+  void grad_f(const double* v, double* g) override {
+    for (int i = 0; i < nd + ns; ++i) g[i] = i < G ? 2.0 * cost[i] * v[i] : 0.0;
+  }
+  int cons(const double* v, double* c) override {
+    gather(v);
+    for (int k = 0; k < K; ++k) yc[k] = v[G + k] - shift[k];
+    int r = nnc_batch_residual(b, xc.data(), yc.data(), rc.data());
+    if (r) return r;
+    double sx = 0;
+    for (int i = 0; i < G; ++i) sx += v[i];
+    for (int k = 0; k < K; ++k) c[k] = rc[k];
+    c[K] = sx - D;
+    return NNC_OK;
+  }
+  int jac(const double* v, double* AD, double* AS) override {
+    gather(v);
+    int r = nnc_batch_eval(b, xc.data(), nullptr, nullptr, Jc.data(), nullptr, nullptr);
+    if (r) return r;
+    std::fill(AD, AD + (size_t)m * nd, 0.0);
+    std::fill(AS, AS + (size_t)m * ns, 0.0);
+    for (int k = 0; k < K; ++k) {
+      for (int j = 0; j < nk[k]; ++j) AD[(size_t)k * nd + sub[off[k] + j]] -= Jc[off[k] + j];
+      AS[(size_t)k * ns + k] = 1.0;
+    }
+    for (int i = 0; i < G; ++i) AD[(size_t)K * nd + i] = 1.0;
+    return NNC_OK;
+  }
+  int hess(const double* v, const double* lam, double* WDD, double* WSS) override {
+    gather(v);
+    for (int k = 0; k < K; ++k) lc[k] = lam[k];
+    int r = nnc_batch_eval(b, xc.data(), lc.data(), nullptr, nullptr, Hc.data(), nullptr);
+    if (r) return r;
+    std::fill(WDD, WDD + (size_t)nd * nd, 0.0);
+    for (int i = 0; i < G; ++i) WDD[(size_t)i * nd + i] = 2.0 * cost[i];
+    long long h = 0;
+    for (int k = 0; k < K; ++k) {
+      const int n = nk[k];
+      const int* S = &sub[off[k]];
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) WDD[(size_t)S[i] * nd + S[j]] -= Hc[h + (long long)i * n + j];
+      h += (long long)n * n;
+    }
+    std::fill(WSS, WSS + ns, 0.0);
+    return NNC_OK;
+  }
+};
+
 }  // namespace
 
 extern "C" {
+
+int nnc_ipm_scopf(nnc_batch* batch, int G, const int* n_in, const int* subsets, const double* cost,
+                  double demand, const double* delta, const nnc_ipm_options* opt, double* v_out,
+                  double* lam_out, nnc_ipm_result* res) {
+  int K = 0, no = 0, n_sum = 0;
+  long long h_sum = 0;
+  int rc = nnc_batch_info(batch, &K, &no, &n_sum, &h_sum);
+  if (rc) return rc;
+  if (G < 1 || !n_in || !subsets || !cost || !delta || no != 1) return NNC_ERR_ARG;
+  int tot = 0;
+  for (int k = 0; k < K; ++k) tot += n_in[k];
+  if (tot != n_sum) return NNC_ERR_ARG;
+  for (int j = 0; j < n_sum; ++j)
+    if (subsets[j] < 0 || subsets[j] >= G) return NNC_ERR_ARG;
+  nnc_ipm_options o;
+  if (opt) o = *opt;
+  else nnc_ipm_default_options(&o);
+  Scopf p(batch, G, subsets, cost, demand);
+  p.set_offsets(std::vector<int>(n_in, n_in + K));
+  rc = p.start(delta);
+  if (rc) return rc;
+  std::vector<double> v, lam;
+  rc = ipm_solve(p, o, v, lam, res);
+  if (rc) return rc;
+  if (v_out) std::copy(v.begin(), v.end(), v_out);
+  if (lam_out) std::copy(lam.begin(), lam.end(), lam_out);
+  return NNC_OK;
+}
 
 int nnc_kkt_solve(int nd, int ns, int m, const double* WDD, const double* WSS, const double* sigma,
                   const double* AD, const double* AS, double delta_w, double delta_c,

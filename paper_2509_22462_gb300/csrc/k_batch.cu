@@ -1,0 +1,350 @@
+// Grouped bandwidth-bound kernels for a batch of networks with equal hidden widths and
+// different input sizes (one stability-margin surrogate per contingency, Eq. 8 / Section 4.2).
+// Every network's arrays are stacked: group g's rows of layer l start at g * mp_l; its input
+// sits in row g of an n_max-padded block; its tangent rows start at boff[g] (n_g of them).
+// One launch covers the same step of every network.
+#include <type_traits>
+
+#include "batch.cuh"
+
+namespace nnc {
+
+__device__ __forceinline__ double bwarp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// x_cat (sum n_g, concatenated) -> xs[g][0..kp) (zero padded) in FP64 and FP32.
+__global__ void k_bx_scatter(const double* __restrict__ xcat, const int* __restrict__ gn,
+                             const int* __restrict__ goff, int kp, double* __restrict__ xs,
+                             float* __restrict__ xf) {
+  const int g = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= kp) return;
+  const double v = j < gn[g] ? xcat[goff[g] + j] : 0.0;
+  xs[(size_t)g * kp + j] = v;
+  if (xf) xf[(size_t)g * kp + j] = (float)v;
+}
+
+cudaError_t launch_bx_scatter(const double* xcat, const int* gn, const int* goff, int kp, int groups,
+                              double* xs, float* xf, cudaStream_t st) {
+  dim3 grid((kp + 255) / 256, groups);
+  k_bx_scatter<<<grid, 256, 0, st>>>(xcat, gn, goff, kp, xs, xf);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// One warp per output row of every group: z = W a + b, a = sigma(z), sigma', sigma''.
+template <typename TW>
+__global__ void __launch_bounds__(256) k_bgemv_fwd(const TW* __restrict__ W, int ldw, int mp,
+                                                   int m, const double* __restrict__ bias,
+                                                   const void* __restrict__ a_in_v, int ld_in,
+                                                   int act, double* __restrict__ a_out,
+                                                   float* __restrict__ a_out_f,
+                                                   double* __restrict__ s1,
+                                                   double* __restrict__ s2) {
+  const int g = blockIdx.y;
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= m) return;
+  const size_t grow = (size_t)g * mp + row;
+  double acc;
+  if constexpr (std::is_same<TW, float>::value) {
+    const float4* r4 = reinterpret_cast<const float4*>(W + grow * ldw);
+    const float4* a4 = reinterpret_cast<const float4*>((const float*)a_in_v + (size_t)g * ld_in);
+    const int nk4 = ldw >> 2;
+    float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#pragma unroll 8
+    for (int j = lane; j < nk4; j += 32) {
+      const float4 w = __ldg(r4 + j);
+      const float4 a = a4[j];
+      p0 = fmaf(w.x, a.x, p0);
+      p1 = fmaf(w.y, a.y, p1);
+      p2 = fmaf(w.z, a.z, p2);
+      p3 = fmaf(w.w, a.w, p3);
+    }
+    acc = ((double)p0 + (double)p1) + ((double)p2 + (double)p3);
+  } else {
+    const double2* r2 = reinterpret_cast<const double2*>(W + grow * ldw);
+    const double2* a2 = reinterpret_cast<const double2*>((const double*)a_in_v + (size_t)g * ld_in);
+    const int nk2 = ldw >> 1;
+    double q0 = 0.0, q1 = 0.0;
+#pragma unroll 4
+    for (int j = lane; j < nk2; j += 32) {
+      const double2 w = __ldg(r2 + j);
+      const double2 a = a2[j];
+      q0 = fma(w.x, a.x, q0);
+      q1 = fma(w.y, a.y, q1);
+    }
+    acc = q0 + q1;
+  }
+  acc = bwarp_sum(acc);
+  if (lane == 0) {
+    double a, d1, d2;
+    act_eval(act, acc + (bias ? bias[grow] : 0.0), a, d1, d2);
+    a_out[grow] = a;
+    if (a_out_f) a_out_f[grow] = (float)a;
+    if (s1) s1[grow] = d1;
+    if (s2) s2[grow] = d2;
+  }
+}
+
+cudaError_t launch_bgemv_fwd(bool fp64, const void* W, int ldw, int mp, int m, int groups,
+                             const double* b, const void* a_in, int ld_in, int act, double* a_out,
+                             float* a_out_f, double* s1, double* s2, cudaStream_t st) {
+  dim3 grid((m * 32 + 255) / 256, groups);
+  if (fp64)
+    k_bgemv_fwd<double><<<grid, 256, 0, st>>>((const double*)W, ldw, mp, m, b, a_in, ld_in, act,
+                                              a_out, a_out_f, s1, s2);
+  else
+    k_bgemv_fwd<float><<<grid, 256, 0, st>>>((const float*)W, ldw, mp, m, b, a_in, ld_in, act,
+                                             a_out, a_out_f, s1, s2);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// Reverse step of every group: part[g][c][kk][s] = sum_{r in chunk c} W_g[r][kk] Zbar_g[r][s]
+// (FP32 weights, FP32 seeds), 256 threads x 4 columns per block, kBRows rows per chunk.
+constexpr int kBRows = 64;
+template <int SMAX>
+__global__ void __launch_bounds__(256) k_bgemv_rev(const float* __restrict__ W, int ldw, int mp,
+                                                   int m, const double* __restrict__ Zbar, int S,
+                                                   int chunks, float* __restrict__ part) {
+  __shared__ float zs[kBRows][SMAX];
+  const int g = blockIdx.z;
+  const int c0 = (blockIdx.x * 256 + threadIdx.x) * 4;
+  const int r0 = blockIdx.y * kBRows;
+  const int nr = min(kBRows, m - r0);
+  const double* zg = Zbar + (size_t)g * mp * S;
+  for (int i = threadIdx.x; i < kBRows * SMAX; i += 256) {
+    const int r = i / SMAX, s = i % SMAX;
+    zs[r][s] = (r < nr && s < S) ? (float)zg[(size_t)(r0 + r) * S + s] : 0.f;
+  }
+  __syncthreads();
+  if (c0 >= ldw || nr <= 0) return;
+  float acc[4][SMAX];
+#pragma unroll
+  for (int v = 0; v < 4; ++v)
+#pragma unroll
+    for (int s = 0; s < SMAX; ++s) acc[v][s] = 0.f;
+  const float* wp = W + ((size_t)g * mp + r0) * ldw + c0;
+#pragma unroll 4
+  for (int r = 0; r < nr; ++r) {
+    const float4 w = __ldg(reinterpret_cast<const float4*>(wp + (size_t)r * ldw));
+#pragma unroll
+    for (int s = 0; s < SMAX; ++s) {
+      const float z = zs[r][s];
+      acc[0][s] = fmaf(w.x, z, acc[0][s]);
+      acc[1][s] = fmaf(w.y, z, acc[1][s]);
+      acc[2][s] = fmaf(w.z, z, acc[2][s]);
+      acc[3][s] = fmaf(w.w, z, acc[3][s]);
+    }
+  }
+  float* out = part + (((size_t)g * chunks + blockIdx.y) * ldw + c0) * S;
+#pragma unroll
+  for (int v = 0; v < 4; ++v)
+#pragma unroll
+    for (int s = 0; s < SMAX; ++s)
+      if (s < S) out[v * S + s] = acc[v][s];
+}
+
+cudaError_t launch_bgemv_rev(const float* W, int ldw, int mp, int m, int groups, const double* Zbar,
+                             int S, float* part, cudaStream_t st) {
+  const int chunks = (m + kBRows - 1) / kBRows;
+  dim3 grid((ldw + 1023) / 1024, chunks, groups);
+  if (S <= 2)
+    k_bgemv_rev<2><<<grid, 256, 0, st>>>(W, ldw, mp, m, Zbar, S, chunks, part);
+  else if (S <= 4)
+    k_bgemv_rev<4><<<grid, 256, 0, st>>>(W, ldw, mp, m, Zbar, S, chunks, part);
+  else
+    return cudaErrorInvalidValue;
+  note_launch();
+  return cudaGetLastError();
+}
+
+int bgemv_rev_chunks(int m) { return (m + kBRows - 1) / kBRows; }
+
+// Sum the chunks of every group; Zbar_out = s1 * Abar (next seeds), c = s2 * Abar[:, lam_col];
+// on the first layer (s1 == NULL): J_cat[goff*nJ + s*n_g + kk] and grad_cat[goff + kk], kk < n_g.
+__global__ void k_brev_reduce(const float* __restrict__ part, int chunks, int kcols, int mp_out,
+                              int S, const double* __restrict__ s1, const double* __restrict__ s2,
+                              int lam_col, int nJ, double* __restrict__ Zbar_out,
+                              double* __restrict__ c_out, float* __restrict__ c_f,
+                              const int* __restrict__ gn, const int* __restrict__ goff,
+                              double* __restrict__ J_cat, double* __restrict__ g_cat) {
+  const int g = blockIdx.y;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= kcols * S) return;
+  const int kk = idx / S, s = idx % S;
+  const float* pp = part + (size_t)g * chunks * kcols * S + idx;
+  double v = 0.0;
+#pragma unroll 8
+  for (int c = 0; c < chunks; ++c) v += (double)pp[(size_t)c * kcols * S];
+  if (s1) {
+    const size_t gi = (size_t)g * mp_out + kk;
+    if (kk < mp_out) Zbar_out[(size_t)g * mp_out * S + idx] = s1[gi] * v;
+    if (s == lam_col && kk < mp_out) {
+      c_out[gi] = s2[gi] * v;
+      if (c_f) c_f[gi] = (float)(s2[gi] * v);
+    }
+  } else {
+    const int n = gn[g];
+    if (kk < n) {
+      if (s < nJ && J_cat) J_cat[(size_t)goff[g] * nJ + (size_t)s * n + kk] = v;
+      if (s == lam_col && g_cat) g_cat[goff[g] + kk] = v;
+    }
+  }
+}
+
+cudaError_t launch_brev_reduce(const float* part, int chunks, int kcols, int mp_out, int groups,
+                               int S, const double* s1, const double* s2, int lam_col, int nJ,
+                               double* Zbar_out, double* c_out, float* c_f, const int* gn,
+                               const int* goff, double* J_cat, double* g_cat, cudaStream_t st) {
+  dim3 grid((kcols * S + 255) / 256, groups);
+  k_brev_reduce<<<grid, 256, 0, st>>>(part, chunks, kcols, mp_out, S, s1, s2, lam_col, nJ, Zbar_out,
+                                      c_out, c_f, gn, goff, J_cat, g_cat);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// Output-layer seeds of every group (m = n_out rows per group, stacked with stride mp).
+__global__ void k_brev_seed(int m, int mp, int S, int nJ, int lam_col, const double* __restrict__ s1,
+                            const double* __restrict__ s2, const double* __restrict__ lam,
+                            double* __restrict__ Zbar, double* __restrict__ c_out,
+                            float* __restrict__ c_f) {
+  const int g = blockIdx.y;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * S) return;
+  const int i = idx / S, s = idx % S;
+  const size_t gi = (size_t)g * mp + i;
+  double ab = 0.0;
+  if (s == lam_col) ab = lam[(size_t)g * m + i];
+  else if (s < nJ) ab = (s == i) ? 1.0 : 0.0;
+  Zbar[(size_t)g * mp * S + idx] = s1[gi] * ab;
+  if (s == lam_col) {
+    c_out[gi] = s2[gi] * ab;
+    if (c_f) c_f[gi] = (float)(s2[gi] * ab);
+  }
+}
+
+cudaError_t launch_brev_seed(int m, int mp, int groups, int S, int nJ, int lam_col, const double* s1,
+                             const double* s2, const double* lam, double* Zbar, double* c_out,
+                             float* c_f, cudaStream_t st) {
+  dim3 grid((m * S + 255) / 256, groups);
+  k_brev_seed<<<grid, 256, 0, st>>>(m, mp, S, nJ, lam_col, s1, s2, lam, Zbar, c_out, c_f);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// First-layer tangents of every group: At[boff+n][m] = s1[m] W1_g[m][n], Zt/Yt likewise at
+// column offset 0 of the side-by-side array (row stride ldz), n < n_g.
+__global__ void k_bfirst_tangent(const float* __restrict__ W1, int ldw, int mp,
+                                 const int* __restrict__ gn, const int* __restrict__ goff,
+                                 const double* __restrict__ s1, const double* __restrict__ c,
+                                 __nv_bfloat16* at_hi, __nv_bfloat16* at_lo, int lda,
+                                 __nv_bfloat16* zt_hi, __nv_bfloat16* zt_lo,
+                                 __nv_bfloat16* yt_hi, __nv_bfloat16* yt_lo, int ldz, int x3) {
+  __shared__ float tile[32][33];
+  const int g = blockIdx.z;
+  const int n_g = gn[g];
+  const int m0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+  if (n0 >= n_g) return;
+  const float* Wg = W1 + (size_t)g * mp * ldw;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int mm = m0 + r, nn = n0 + threadIdx.x;
+    tile[r][threadIdx.x] = (mm < mp && nn < n_g) ? Wg[(size_t)mm * ldw + nn] : 0.f;
+  }
+  __syncthreads();
+  const int mm = m0 + threadIdx.x;
+  if (mm >= mp) return;
+  const float sm = (float)s1[(size_t)g * mp + mm], cm = (float)c[(size_t)g * mp + mm];
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int nn = n0 + r;
+    if (nn >= n_g) continue;
+    const float w = tile[threadIdx.x][r];
+    const size_t row = (size_t)goff[g] + nn;
+    __nv_bfloat16 h, l;
+    if (at_hi) {
+      split_bf16(sm * w, h, l);
+      at_hi[row * lda + mm] = h;
+      if (x3) at_lo[row * lda + mm] = l;
+    }
+    if (zt_hi) {
+      split_bf16(w, h, l);
+      zt_hi[row * ldz + mm] = h;
+      if (x3) zt_lo[row * ldz + mm] = l;
+      split_bf16(cm * w, h, l);
+      yt_hi[row * ldz + mm] = h;
+      if (x3) yt_lo[row * ldz + mm] = l;
+    }
+  }
+}
+
+cudaError_t launch_bfirst_tangent(const float* W1, int ldw, int mp, int groups, int n_max,
+                                  const int* gn, const int* goff, const double* s1, const double* c,
+                                  void* at_hi, void* at_lo, int lda, void* zt_hi, void* zt_lo,
+                                  void* yt_hi, void* yt_lo, int ldz, bool x3, cudaStream_t st) {
+  dim3 grid((n_max + 31) / 32, (mp + 31) / 32, groups), block(32, 8);
+  k_bfirst_tangent<<<grid, block, 0, st>>>(
+      W1, ldw, mp, gn, goff, s1, c, (__nv_bfloat16*)at_hi, (__nv_bfloat16*)at_lo, lda,
+      (__nv_bfloat16*)zt_hi, (__nv_bfloat16*)zt_lo, (__nv_bfloat16*)yt_hi, (__nv_bfloat16*)yt_lo, ldz,
+      x3 ? 1 : 0);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// H_g[i][j] = sum_s Hp[s][g][max][min] for every group (row-major n_g x n_g at hoff[g]).
+__global__ void k_bh_finish(const float* __restrict__ Hp, int splits, long long ldh_split,
+                            const int* __restrict__ gn, const long long* __restrict__ hoff,
+                            double* __restrict__ H) {
+  const int g = blockIdx.y;
+  const int n = gn[g];
+  const long long base = hoff[g];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n * n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    const int r = i > j ? i : j, cc = i > j ? j : i;
+    double v = 0.0;
+    for (int s = 0; s < splits; ++s) v += (double)Hp[s * ldh_split + base + (long long)r * n + cc];
+    H[base + e] = v;
+  }
+}
+
+cudaError_t launch_bh_finish(const float* Hp, int splits, long long ldh_split, int groups,
+                             const int* gn, const long long* hoff, double* H, cudaStream_t st) {
+  dim3 grid(32, groups);
+  k_bh_finish<<<grid, 256, 0, st>>>(Hp, splits, ldh_split, gn, hoff, H);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// r_cat[g*m + i] = y_cat[g*m + i] - a[g*mp + i]
+__global__ void k_bsub(const double* y, const double* a, int m, int mp, int groups, double* r) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * groups) return;
+  const int g = idx / m, i = idx % m;
+  r[idx] = y[idx] - a[(size_t)g * mp + i];
+}
+
+cudaError_t launch_bsub(const double* y, const double* a, int m, int mp, int groups, double* r,
+                        cudaStream_t st) {
+  k_bsub<<<(m * groups + 255) / 256, 256, 0, st>>>(y, a, m, mp, groups, r);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// y_cat[g*m + i] = a[g*mp + i]
+__global__ void k_bgather(const double* a, int m, int mp, int groups, double* y) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * groups) return;
+  y[idx] = a[(size_t)(idx / m) * mp + idx % m];
+}
+
+cudaError_t launch_bgather(const double* a, int m, int mp, int groups, double* y, cudaStream_t st) {
+  k_bgather<<<(m * groups + 255) / 256, 256, 0, st>>>(a, m, mp, groups, y);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace nnc

@@ -39,6 +39,14 @@ struct TcArgs {
   int ldz;   // row stride of zt_* / yt_*
   float* Hp;
   int* err;
+  // grouped modes: group g owns A rows [g * a_group_rows, ...) (tangent) and B / output rows
+  // starting at g_boff[g]; g_n[g] valid columns; syrk: tile list `work` and H_g at g_hoff[g]
+  const int* g_n;
+  const int* g_boff;
+  const long long* g_hoff;
+  const int4* work;
+  int a_group_rows;
+  long long ldh_split;
 };
 
 template <int BN, bool X3>
@@ -55,8 +63,8 @@ struct Cfg {
   static constexpr int TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
   // Instruction descriptor of tcgen05.mma kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
   // (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17, M >> 4 at bit 24.
-  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
-                                    ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+  static constexpr uint32_t IDESC_NO_N = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BM >> 4) << 24);
+  static constexpr uint32_t IDESC = IDESC_NO_N | ((uint32_t)(BN >> 3) << 17);
   static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N for M = 128");
   static_assert(B_BYTES % 1024 == 0, "stage parts must stay 1024-byte aligned");
   static_assert(STAGES >= 2, "at least two stages");
@@ -187,17 +195,47 @@ __global__ void __launch_bounds__(kThreads, 1)
   volatile int* consumed_sh = (volatile int*)(tmem_slot + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int tm, tn, split;
+  int tm, tn, split, grp = 0, a_row0, b_row0, n_valid, n_eff = BN;
   if (KIND == TC_TANGENT) {
     tn = blockIdx.x;
     tm = blockIdx.y;
     split = 0;
-  } else {
+    a_row0 = tm * BM;
+    b_row0 = tn * BN;
+    n_valid = args.N;
+  } else if (KIND == TC_SYRK) {
     tn = blockIdx.x % args.ntn;
     tm = blockIdx.x / args.ntn;
     split = blockIdx.y;
     if (tm * BM + BM - 1 < tn * BN) return;  // tile lies strictly above the diagonal
+    a_row0 = tm * BM;
+    b_row0 = tn * BN;
+    n_valid = args.N;
+  } else if (KIND == TC_TANGENT_G) {
+    tm = blockIdx.x;
+    grp = blockIdx.y;
+    tn = 0;
+    split = 0;
+    a_row0 = grp * args.a_group_rows + tm * BM;
+    b_row0 = args.g_boff[grp];
+    n_valid = args.g_n[grp];
+  } else {
+    const int4 w = args.work[blockIdx.x];
+    grp = w.x;
+    tm = w.y;
+    tn = w.z;
+    split = blockIdx.y;
+    n_valid = args.g_n[grp];
+    a_row0 = args.g_boff[grp] + tm * BM;
+    b_row0 = args.g_boff[grp] + tn * BN;
   }
+  if (KIND == TC_TANGENT_G || KIND == TC_SYRK_G) {
+    // the MMA's N is chosen per CTA: the group's valid columns rounded up to 16
+    const int cols = min(BN, n_valid - tn * BN);
+    n_eff = (cols + 15) / 16 * 16;
+    if (cols <= 0) return;
+  }
+  const uint32_t idesc = C::IDESC_NO_N | ((uint32_t)(n_eff >> 3) << 17);
   const int m0 = tm * BM, n0 = tn * BN;
   const int kb0 = split * args.kb_per_split;
   const int kb1 = min(args.nkb, kb0 + args.kb_per_split);
@@ -238,10 +276,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t fb = smem_u32(&full[s]);
         mbar_expect_tx(fb, C::TX_BYTES);
         const int kx = (kb0 + i) * BK;
-        tma_load_2d(smem_u32(st), &ta_hi, fb, kx, m0);
-        if (X3) tma_load_2d(smem_u32(st + C::A_BYTES), &ta_lo, fb, kx, m0);
-        tma_load_2d(smem_u32(st + C::NPARTS * C::A_BYTES), &tb_hi, fb, kx, n0);
-        if (X3) tma_load_2d(smem_u32(st + C::NPARTS * C::A_BYTES + C::B_BYTES), &tb_lo, fb, kx, n0);
+        tma_load_2d(smem_u32(st), &ta_hi, fb, kx, a_row0);
+        if (X3) tma_load_2d(smem_u32(st + C::A_BYTES), &ta_lo, fb, kx, a_row0);
+        tma_load_2d(smem_u32(st + C::NPARTS * C::A_BYTES), &tb_hi, fb, kx, b_row0);
+        if (X3) tma_load_2d(smem_u32(st + C::NPARTS * C::A_BYTES + C::B_BYTES), &tb_lo, fb, kx, b_row0);
         issued = i + 1;
       }
     }
@@ -260,10 +298,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int kk = 0; kk < BK / 16; ++kk) {
           const uint32_t off = kk * 32;
-          umma_bf16(tmem, sdesc(a_hi + off), sdesc(b_hi + off), C::IDESC, (i > 0 || kk > 0) ? 1u : 0u);
+          umma_bf16(tmem, sdesc(a_hi + off), sdesc(b_hi + off), idesc, (i > 0 || kk > 0) ? 1u : 0u);
           if (X3) {
-            umma_bf16(tmem, sdesc(a_hi + off), sdesc(b_lo + off), C::IDESC, 1u);
-            umma_bf16(tmem, sdesc(a_lo + off), sdesc(b_hi + off), C::IDESC, 1u);
+            umma_bf16(tmem, sdesc(a_hi + off), sdesc(b_lo + off), idesc, 1u);
+            umma_bf16(tmem, sdesc(a_lo + off), sdesc(b_hi + off), idesc, 1u);
           }
         }
         umma_commit(smem_u32(&empty[s]));
@@ -277,21 +315,23 @@ __global__ void __launch_bounds__(kThreads, 1)
     const bool ok = mbar_wait(smem_u32(accf), 0, args.err, 3, abort_flag);
     tc_fence_after();
     if (ok) {
-      if (KIND == TC_TANGENT) {
-        const int m = m0 + row;
-        const float sm = (float)args.s1[m];
-        const float cm = args.c[m];
+      if (KIND == TC_TANGENT || KIND == TC_TANGENT_G) {
+        const int m = m0 + row;                        // row of W_l inside the group
+        const int ms = (KIND == TC_TANGENT_G ? grp * args.a_group_rows : 0) + m;
+        const float sm = (float)args.s1[ms];
+        const float cm = args.c[ms];
 #pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 16) {
+        for (int c0 = 0; c0 < n_eff; c0 += 16) {
           float v[16];
           tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int n = n0 + c0 + j;
-            if (n < args.N) {
-              if (args.at_hi) put<X3>(args.at_hi, args.at_lo, (size_t)n * args.ldo + m, sm * v[j]);
+            if (n < n_valid) {
+              const size_t orow = (size_t)(KIND == TC_TANGENT_G ? b_row0 + n : n);
+              if (args.at_hi) put<X3>(args.at_hi, args.at_lo, orow * args.ldo + m, sm * v[j]);
               if (args.zt_hi) {
-                const size_t oz = (size_t)n * args.ldz + m;
+                const size_t oz = orow * args.ldz + m;
                 put<X3>(args.zt_hi, args.zt_lo, oz, v[j]);
                 put<X3>(args.yt_hi, args.yt_lo, oz, cm * v[j]);
               }
@@ -301,11 +341,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       } else {
         const int i = m0 + row;
 #pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 16) {
+        for (int c0 = 0; c0 < n_eff; c0 += 16) {
           float v[16];
           tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
-          if (i < args.N) {
-            float* hp = args.Hp + ((size_t)split * args.N + i) * args.N;
+          if (i < n_valid) {
+            float* hp = KIND == TC_SYRK
+                            ? args.Hp + ((size_t)split * args.N + i) * args.N
+                            : args.Hp + split * args.ldh_split + args.g_hoff[grp] + (size_t)i * n_valid;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
               const int n = n0 + c0 + j;
@@ -423,9 +465,29 @@ int tc_plan_make(TcPlan& p, int kind, int prec, const void* a_hi, const void* a_
   p.N = N;
   p.K = K;
   if (K % BK != 0 || K <= 0 || N <= 0 || M <= 0) return NNC_ERR_ARG;
-  if (kind == TC_TANGENT && M % BM != 0) return NNC_ERR_ARG;
+  if ((kind == TC_TANGENT || kind == TC_TANGENT_G) && M % BM != 0) return NNC_ERR_ARG;
   const int nkb = K / BK;
-  if (kind == TC_TANGENT) {
+  if (kind == TC_TANGENT_G || kind == TC_SYRK_G) {
+    // grouped: N is the widest group's column count (rounded to 16); the MMA N of each CTA is
+    // chosen at run time from its group's width.
+    int bn = (N + 15) / 16 * 16;
+    if (force_bn) bn = force_bn;
+    const int cands[4] = {112, 128, 208, 256};
+    int pick = 256;
+    for (int c : cands)
+      if (c >= bn) {
+        pick = c;
+        break;
+      }
+    if (bn > 256) return NNC_ERR_UNSUPPORTED;
+    p.bn = kind == TC_SYRK_G ? 128 : pick;
+    p.ntm = kind == TC_TANGENT_G ? M / BM : 0;
+    p.ntn = 1;
+    p.splits = force_splits ? force_splits : 1;
+    if (p.splits > nkb) p.splits = nkb;
+    p.kb_per_split = (nkb + p.splits - 1) / p.splits;
+    p.splits = (nkb + p.kb_per_split - 1) / p.kb_per_split;
+  } else if (kind == TC_TANGENT) {
     int best_bn = 208;
     double best = 1e30;
     const int cands[4] = {256, 208, 128, 112};
@@ -489,6 +551,54 @@ cudaError_t tc_tangent(const TcPlan& p, const double* s1, const float* c, void* 
   a.ldz = ldz;
   a.err = err;
   return launch_any<TC_TANGENT>(p, a, dim3(p.ntn, p.ntm, 1), st);
+}
+
+cudaError_t tc_tangent_grouped(const TcPlan& p, int groups, const int* g_n, const int* g_boff,
+                               const double* s1, const float* c, void* at_hi, void* at_lo, int ldo,
+                               void* zt_hi, void* zt_lo, void* yt_hi, void* yt_lo, int ldz,
+                               int* err, cudaStream_t st) {
+  if (!p.ready || p.kind != TC_TANGENT_G) return cudaErrorInvalidValue;
+  TcArgs a{};
+  a.M = p.M;
+  a.N = p.N;
+  a.K = p.K;
+  a.ntm = p.ntm;
+  a.ntn = 1;
+  a.nkb = p.K / BK;
+  a.kb_per_split = a.nkb;
+  a.s1 = s1;
+  a.c = c;
+  a.at_hi = (__nv_bfloat16*)at_hi;
+  a.at_lo = (__nv_bfloat16*)at_lo;
+  a.zt_hi = (__nv_bfloat16*)zt_hi;
+  a.zt_lo = (__nv_bfloat16*)zt_lo;
+  a.yt_hi = (__nv_bfloat16*)yt_hi;
+  a.yt_lo = (__nv_bfloat16*)yt_lo;
+  a.ldo = ldo;
+  a.ldz = ldz;
+  a.err = err;
+  a.g_n = g_n;
+  a.g_boff = g_boff;
+  a.a_group_rows = p.M;
+  return launch_any<TC_TANGENT_G>(p, a, dim3(p.ntm, groups, 1), st);
+}
+
+cudaError_t tc_syrk_grouped(const TcPlan& p, int n_tiles, const int4* work, const int* g_n,
+                            const int* g_boff, const long long* g_hoff, long long ldh_split,
+                            float* Hp, int* err, cudaStream_t st) {
+  if (!p.ready || p.kind != TC_SYRK_G) return cudaErrorInvalidValue;
+  TcArgs a{};
+  a.K = p.K;
+  a.nkb = p.K / BK;
+  a.kb_per_split = p.kb_per_split;
+  a.Hp = Hp;
+  a.err = err;
+  a.g_n = g_n;
+  a.g_boff = g_boff;
+  a.g_hoff = g_hoff;
+  a.work = work;
+  a.ldh_split = ldh_split;
+  return launch_any<TC_SYRK_G>(p, a, dim3(n_tiles, p.splits, 1), st);
 }
 
 cudaError_t tc_syrk(const TcPlan& p, float* Hp, int* err, cudaStream_t st) {

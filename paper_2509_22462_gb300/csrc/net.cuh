@@ -1,0 +1,73 @@
+// Internal definitions shared by the library's translation units: the per-layer device state
+// of a net and the net object behind the opaque nnc_net handle of include/nnc.h.
+#pragma once
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "tc.cuh"
+
+struct nnc_net;
+namespace nnc {
+void set_last_error(const std::string& msg);
+void batch_cache_forget(const nnc_net* net);
+int eval_batched_grouped(nnc_net* const* nets, int K, const double* const* x,
+                         const double* const* lambda, double* const* y, double* const* J,
+                         double* const* H, unsigned what);
+}
+
+struct LayerDev {
+  int m = 0, k = 0, act = 0, mp = 0, kp = 0;
+  double* W64 = nullptr;          // [mp][kp], zero padded
+  float* W32 = nullptr;           // [mp][kp]
+  __nv_bfloat16* Whi = nullptr;   // [mp][kp]
+  __nv_bfloat16* Wlo = nullptr;   // [mp][kp]
+  double* b = nullptr;            // [mp]
+  double* a = nullptr;            // a_l [mp]
+  double* s1 = nullptr;           // sigma_l'(z_l) [mp]
+  double* s2 = nullptr;           // sigma_l''(z_l) [mp]
+  double* c = nullptr;            // sigma_l''(z_l) * abar_l [mp]
+  float* c_f = nullptr;           // FP32 copy of c for the tensor-core epilogue
+  double* ra = nullptr;           // FP64-residual pass activations [mp]
+  float* af = nullptr;            // FP32 copy of a_l [mp] (input of the next FP32 layer)
+  nnc::TcPlan plan_tan;                // tensor-core plan of this layer's tangent GEMM
+  int zy_off = -1;                // column offset of this layer's Zdot / Ydot block (-1: none)
+};
+
+struct nnc_net {
+  int L = 0, n_in = 0, n_out = 0, prec = 0, n_in_pad = 0, mp_max = 0, S_max = 0;
+  std::vector<LayerDev> layers;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0, sm_count = 0;
+  std::vector<void*> allocs;
+  double* x = nullptr;       // a_0 [n_in_pad]
+  float* xf = nullptr;       // FP32 copy of a_0 [n_in_pad]
+  double* xin = nullptr;     // host-call staging of x [n_in_pad]
+  double* lam = nullptr;     // [n_out]
+  double* ydev = nullptr;    // [n_out] staging
+  double* rdev = nullptr;    // [n_out]
+  double* Zbar[2] = {nullptr, nullptr};
+  double* part = nullptr;
+  double* Jdev = nullptr;    // [n_out][n_in]
+  double* gdev = nullptr;    // [n_in]
+  double* Hdev = nullptr;    // [n_in][n_in]
+  void* At[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [ping-pong][hi, lo]
+  void* Zt[2] = {nullptr, nullptr};  // [hi, lo]: Zdot_l^T of all curved layers, n x K_total
+  void* Yt[2] = {nullptr, nullptr};  // [hi, lo]: (c_l * Zdot_l)^T, n x K_total
+  int K_total = 0;                   // sum of mp_l over layers with sigma'' != 0
+  nnc::TcPlan plan_syrk;                  // tensor-core plan of the one symmetric product
+  void* Hp = nullptr;        // split partial sums of H (double for CUDA-core forms, float for TC)
+  int h_splits = 1;
+  bool hp_f32 = false;
+  int* dev_err = nullptr;    // device error word of bounded waits
+  double* h_stage = nullptr; // pinned host staging
+  size_t h_stage_elems = 0;
+  size_t bytes = 0;
+  // optional per-kernel-kind CUDA-event timing (nnc_profile)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<int> ev_kind;
+};
+

@@ -15,7 +15,7 @@
 
 namespace nnc {
 
-enum { TC_TANGENT = 0, TC_SYRK = 1 };
+enum { TC_TANGENT = 0, TC_SYRK = 1, TC_TANGENT_G = 2, TC_SYRK_G = 3 };
 
 struct TcPlan {
   CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;
@@ -43,5 +43,17 @@ cudaError_t tc_tangent(const TcPlan& p, const double* s1, const float* c, void* 
 
 // Hp: splits x N x N floats (row stride N); partial sums of the lower triangle are added.
 cudaError_t tc_syrk(const TcPlan& p, float* Hp, int* err, cudaStream_t st);
+
+// Grouped forms for a batch of networks of equal hidden widths (stacked buffers): group g's
+// W_l rows start at g * M, its tangent rows at g_boff[g] (g_n[g] of them, <= the plan's N).
+cudaError_t tc_tangent_grouped(const TcPlan& p, int groups, const int* g_n, const int* g_boff,
+                               const double* s1, const float* c, void* at_hi, void* at_lo, int ldo,
+                               void* zt_hi, void* zt_lo, void* yt_hi, void* yt_lo, int ldz,
+                               int* err, cudaStream_t st);
+// work[t] = (group, row tile, column tile, 0) over the lower-triangle tiles of every group;
+// H_g (g_n[g]^2 floats, row-major) sits at Hp + split * ldh_split + g_hoff[g].
+cudaError_t tc_syrk_grouped(const TcPlan& p, int n_tiles, const int4* work, const int* g_n,
+                            const int* g_boff, const long long* g_hoff, long long ldh_split,
+                            float* Hp, int* err, cudaStream_t st);
 
 }  // namespace nnc

@@ -26,7 +26,9 @@ EXPORTS = ["nnc_load_weights", "nnc_eval", "nnc_residual", "nnc_jacobian", "nnc_
            "nnc_hessian_lag_dev", "nnc_eval_all_dev", "nnc_free", "nnc_last_error",
            "nnc_net_info", "nnc_launch_count", "nnc_profile", "nnc_profile_read",
            "nnc_ipm_default_options", "nnc_ipm_adversarial", "nnc_kkt_solve",
-           "nnc_residual_noalloc"]
+           "nnc_residual_noalloc", "nnc_batch_create", "nnc_batch_free", "nnc_batch_info",
+           "nnc_batch_set_bias", "nnc_batch_use_graph", "nnc_batch_eval_dev", "nnc_batch_residual_dev",
+           "nnc_batch_eval", "nnc_batch_residual", "nnc_ipm_scopf"]
 IPM_STATUS = {0: "optimal", 1: "max_iter", 2: "linesearch_failed", 3: "nonfinite",
               4: "inertia_failed", 5: "eval_error"}
 
@@ -103,6 +105,20 @@ def load_library(path: str = LIB_PATH):
     lib.nnc_launch_count.restype = ctypes.c_longlong
     lib.nnc_profile.argtypes = [_P, ctypes.c_int]
     lib.nnc_ipm_default_options.argtypes = [ctypes.POINTER(IpmOptions)]
+    lib.nnc_batch_create.argtypes = [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int, _P]
+    lib.nnc_batch_free.argtypes = [_P]
+    lib.nnc_batch_free.restype = None
+    lib.nnc_batch_info.argtypes = [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)]
+    lib.nnc_batch_set_bias.argtypes = [_P, ctypes.c_int, _DP]
+    lib.nnc_batch_use_graph.argtypes = [_P, ctypes.c_int]
+    lib.nnc_batch_eval_dev.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P]
+    lib.nnc_batch_residual_dev.argtypes = [_P, _P, _P, _P, _P]
+    lib.nnc_batch_eval.argtypes = [_P, _DP, _DP, _DP, _DP, _DP, _DP]
+    lib.nnc_batch_residual.argtypes = [_P, _DP, _DP, _DP]
+    lib.nnc_ipm_scopf.argtypes = [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                  ctypes.POINTER(ctypes.c_int), _DP, ctypes.c_double, _DP,
+                                  ctypes.POINTER(IpmOptions), _DP, _DP, ctypes.POINTER(IpmResult)]
     lib.nnc_residual_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_P),
                                          ctypes.POINTER(_P), _P, _P, _P, _P]
@@ -114,7 +130,8 @@ def load_library(path: str = LIB_PATH):
     lib.nnc_profile_read.argtypes = [_P, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
     for name in EXPORTS:
-        if name not in ("nnc_free", "nnc_last_error", "nnc_launch_count", "nnc_ipm_default_options"):
+        if name not in ("nnc_free", "nnc_last_error", "nnc_launch_count", "nnc_ipm_default_options",
+                        "nnc_batch_free"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -319,3 +336,98 @@ def residual_noalloc(widths, acts, W_dev, b_dev, x, y, r, stream=None):
     bp = (_P * L)(*[_tp(v) for v in b_dev]) if b_dev is not None else None
     _check(lib.nnc_residual_noalloc(L, wid, act, Wp, bp, _tp(x), _tp(y), _tp(r),
                                     stream or _stream_ptr()))
+
+
+class Batch:
+    """nnc_batch: K nets of equal hidden widths (different n_in) evaluated by grouped launches."""
+
+    def __init__(self, nets, stream=None):
+        lib = load_library()
+        self.nets = list(nets)
+        K = len(self.nets)
+        hs = (_P * K)(*[n.handle for n in self.nets])
+        h = _P()
+        _check(lib.nnc_batch_create(ctypes.byref(h), hs, K, stream))
+        self._h = h
+        k, no, ns, hsum = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+        _check(lib.nnc_batch_info(h, ctypes.byref(k), ctypes.byref(no), ctypes.byref(ns), ctypes.byref(hsum)))
+        self.K, self.n_out, self.n_sum, self.h_sum = k.value, no.value, ns.value, hsum.value
+        self.n_in = [n.n_in for n in self.nets]
+        self.off = np.concatenate([[0], np.cumsum(self.n_in)[:-1]]).astype(np.int64)
+        self.hoff = np.concatenate([[0], np.cumsum(np.square(self.n_in))[:-1]]).astype(np.int64)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def free(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.nnc_batch_free(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def use_graph(self, enable=True):
+        _check(_lib.nnc_batch_use_graph(self._h, int(bool(enable))))
+
+    def set_bias(self, layer, bias):
+        bias = _f64(bias)
+        _check(_lib.nnc_batch_set_bias(self._h, int(layer), _dp(bias)))
+
+    def concat(self, xs):
+        return np.concatenate([_f64(x) for x in xs])
+
+    def split_outputs(self, y, J, H, g):
+        ys = [y[k * self.n_out:(k + 1) * self.n_out] for k in range(self.K)] if y is not None else None
+        Js = [J[self.off[k] * self.n_out:(self.off[k] + self.n_in[k]) * self.n_out].reshape(self.n_out, self.n_in[k])
+              for k in range(self.K)] if J is not None else None
+        Hs = [H[self.hoff[k]:self.hoff[k] + self.n_in[k] ** 2].reshape(self.n_in[k], self.n_in[k])
+              for k in range(self.K)] if H is not None else None
+        gs = [g[self.off[k]:self.off[k] + self.n_in[k]] for k in range(self.K)] if g is not None else None
+        return ys, Js, Hs, gs
+
+    def eval(self, xs, lams=None, want=("y", "J", "H", "g")):
+        x = self.concat(xs)
+        lam = self.concat(lams) if lams is not None else None
+        y = np.empty(self.K * self.n_out) if "y" in want else None
+        J = np.empty(self.n_sum * self.n_out) if "J" in want else None
+        H = np.empty(self.h_sum) if ("H" in want and lam is not None) else None
+        g = np.empty(self.n_sum) if ("g" in want and lam is not None) else None
+        p = lambda a: _dp(a) if a is not None else None  # noqa: E731
+        _check(_lib.nnc_batch_eval(self._h, _dp(x), p(lam), p(y), p(J), p(H), p(g)))
+        return self.split_outputs(y, J, H, g)
+
+    def residual(self, xs, ys):
+        x, y = self.concat(xs), self.concat(ys)
+        r = np.empty(self.K * self.n_out)
+        _check(_lib.nnc_batch_residual(self._h, _dp(x), _dp(y), _dp(r)))
+        return [r[k * self.n_out:(k + 1) * self.n_out] for k in range(self.K)]
+
+    def eval_dev(self, x, lam=None, y=None, J=None, H=None, g=None, stream=None):
+        _check(_lib.nnc_batch_eval_dev(self._h, _tp(x), _tp(lam), _tp(y), _tp(J), _tp(H), _tp(g),
+                                       stream or _stream_ptr()))
+
+    def residual_dev(self, x, y, r, stream=None):
+        _check(_lib.nnc_batch_residual_dev(self._h, _tp(x), _tp(y), _tp(r), stream or _stream_ptr()))
+
+
+def ipm_scopf(batch, G, subsets, cost, demand, delta, **options):
+    """The SCOPF-shaped problem with the host interior-point driver (include/nnc_ipm.h).
+    subsets: list of K index arrays S_k.  Returns (result dict, v = (x, y), lambda)."""
+    lib = load_library()
+    K = batch.K
+    n_in = (ctypes.c_int * K)(*[len(s) for s in subsets])
+    sub = np.concatenate([np.asarray(s, dtype=np.int32) for s in subsets]).astype(np.int32)
+    subp = sub.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    cost, delta = _f64(cost), _f64(delta)
+    o = ipm_options(**options)
+    v = np.empty(G + K)
+    lam = np.empty(K + 1)
+    res = IpmResult()
+    _check(lib.nnc_ipm_scopf(batch.handle, int(G), n_in, subp, _dp(cost), float(demand), _dp(delta),
+                             ctypes.byref(o), _dp(v), _dp(lam), ctypes.byref(res)))
+    return res.as_dict(), v, lam

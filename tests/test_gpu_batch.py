@@ -1,0 +1,130 @@
+"""Grouped batch of uneven surrogates (the SCOPF-shaped workload) against the FP64 oracle, and
+the SCOPF-shaped interior-point solve against the oracle interior-point method.
+
+Tolerances: value 1e-6 (relative over the batch), Jacobian 1e-3 and Hessian 1e-2 relative
+Frobenius per network, FP64 residual 1e-10; IPM objective 1e-6 relative with KKT <= 1e-6."""
+import numpy as np
+import pytest
+
+import synth
+from synth.problems import scopf_data
+from oracle import nn as onn, problems, ipm as oipm
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def nnc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_22462_gb300 import build, nnc as m
+    build.build()
+    return m
+
+
+def _raw_nets(data, d):
+    """Surrogates with the load shift in the first-layer bias and no output calibration."""
+    return [problems.scopf_surrogate(data, k, d, calibrate=False) for k in range(len(data.nets))]
+
+
+@pytest.fixture(scope="module")
+def small_batch(nnc):
+    data = scopf_data(K=12, G=60, n_bus=64, n_min=5, n_max=60, hidden=256, depth=3, seed=3)
+    d = np.ones(64)
+    raw = _raw_nets(data, d)
+    nets = [nnc.Net.from_mlp(m, precision="bf16x3") for m in raw]
+    return data, raw, nets
+
+
+def test_batch_matches_oracle(nnc, small_batch):
+    data, raw, nets = small_batch
+    b = nnc.Batch(nets)
+    x = synth.uniform01(synth.derive_key(1, "bx"), data.G)
+    xs = [x[S] for S in data.subsets]
+    lams = [synth.normal(synth.derive_key(k, "blam"), 1) for k in range(len(raw))]
+    ys, Js, Hs, gs = b.eval(xs, lams)
+    yo = np.concatenate([onn.value(raw[k], xs[k]) for k in range(len(raw))])
+    assert rel(np.concatenate(ys), yo) < 1e-6
+    worst = dict(J=0.0, H=0.0, g=0.0)
+    for k in range(len(raw)):
+        Jo = onn.jacobian(raw[k], xs[k])
+        Ho = onn.hessian_lag(raw[k], xs[k], lams[k])
+        go = onn.vjp(raw[k], xs[k], lams[k])
+        worst["J"] = max(worst["J"], rel(Js[k], Jo))
+        worst["H"] = max(worst["H"], rel(Hs[k], Ho))
+        worst["g"] = max(worst["g"], rel(gs[k], go))
+        assert np.array_equal(Hs[k], Hs[k].T)
+    print(f"[batch bf16x3] worst rel err J={worst['J']:.2e} H={worst['H']:.2e} g={worst['g']:.2e}")
+    assert worst["J"] < 1e-3 and worst["H"] < 1e-2 and worst["g"] < 1e-3
+    rs = b.residual(xs, [yo[k:k + 1] for k in range(len(raw))])
+    assert np.max(np.abs(np.concatenate(rs))) < 1e-10 * max(1.0, np.max(np.abs(yo)))
+    b.free()
+
+
+def test_graph_replay_and_eval_batched_agree(nnc, small_batch):
+    import torch
+    data, raw, nets = small_batch
+    b = nnc.Batch(nets)
+    dev = torch.device("cuda:0")
+    x = synth.uniform01(synth.derive_key(2, "bx"), data.G)
+    xs = [x[S] for S in data.subsets]
+    lams = [np.array([0.7 - 0.1 * k]) for k in range(len(raw))]
+    xc = torch.tensor(b.concat(xs), device=dev)
+    lc = torch.tensor(b.concat(lams), device=dev)
+    outs = []
+    for graph in (False, True, True):
+        b.use_graph(graph)
+        y = torch.empty(b.K, dtype=torch.float64, device=dev)
+        J = torch.empty(b.n_sum, dtype=torch.float64, device=dev)
+        H = torch.empty(b.h_sum, dtype=torch.float64, device=dev)
+        g = torch.empty(b.n_sum, dtype=torch.float64, device=dev)
+        b.eval_dev(xc, lc, y, J, H, g)
+        torch.cuda.synchronize()
+        outs.append([t.cpu().numpy() for t in (y, J, H, g)])
+    for o in outs[1:]:
+        for a, c in zip(o, outs[0]):
+            assert np.array_equal(a, c)
+    ys, Js, Hs = nnc.eval_batched(nets, xs, lams)
+    yb, Jb, Hb, _ = b.split_outputs(*outs[0])
+    for k in range(len(raw)):
+        assert np.array_equal(ys[k], yb[k]) and np.array_equal(Js[k], Jb[k]) and np.array_equal(Hs[k], Hb[k])
+    b.free()
+
+
+def test_set_bias_changes_the_load(nnc, small_batch):
+    data, raw, nets = small_batch
+    b = nnc.Batch(nets)
+    d2 = synth.load_vectors(1, 64, seed=5)[0]
+    raw2 = _raw_nets(data, d2)
+    b.set_bias(0, np.stack([m.b[0] for m in raw2]))
+    x = synth.uniform01(synth.derive_key(3, "bx"), data.G)
+    xs = [x[S] for S in data.subsets]
+    ys, _, _, _ = b.eval(xs, None, want=("y",))
+    yo = np.concatenate([onn.value(raw2[k], xs[k]) for k in range(len(raw2))])
+    assert rel(np.concatenate(ys), yo) < 1e-6
+    b.free()
+
+
+def test_scopf_ipm_matches_oracle(nnc):
+    data = scopf_data(K=16, G=40, n_bus=64, n_min=5, n_max=30, hidden=128, depth=3, seed=0)
+    d = np.ones(64)
+    po = problems.scopf(data, d)
+    ro = oipm.solve(po)
+    assert ro.status == oipm.OPTIMAL
+    raw = _raw_nets(data, d)
+    nets = [nnc.Net.from_mlp(m, precision="bf16x3") for m in raw]
+    b = nnc.Batch(nets)
+    res, v, lam = nnc.ipm_scopf(b, data.G, data.subsets, data.cost, problems.scopf_demand(data, d),
+                                data.delta)
+    print(f"[ipm scopf bf16x3] status={res['status_name']} iters={res['iters']} (oracle {ro.iters}) "
+          f"obj={res['obj']:.12g} (oracle {ro.obj:.12g}) kkt={res['kkt_error']:.2e} t={res['solve_seconds']:.3f}s")
+    assert res["status"] == 0 and res["kkt_error"] <= 1e-6
+    assert abs(res["obj"] - ro.obj) <= 1e-6 * abs(ro.obj)
+    b.free()
+    for n in nets:
+        n.free()
