@@ -39,7 +39,8 @@ def _args():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--prec", default="bf16x3", choices=["bf16x3", "bf16", "fp32", "fp64"])
-    p.add_argument("--workload", default="104m", choices=["104m", "87m", "tiny"])
+    p.add_argument("--workload", default="104m", choices=["104m", "87m", "tiny", "scopf"])
+    p.add_argument("--scopf-k", type=int, default=256)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64-form", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -234,9 +235,153 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------ our arm
+def _scopf_workload(K):
+    """256 stability-margin surrogates n_k -> 1024 x 5 sigmoid -> 1, n_k ~ U{20..200}, G = 200,
+    loads d = 1 entering each first-layer bias (the synthetic SCOPF-shaped batch)."""
+    import copy
+    import synth
+    data = synth.scopf_data(K=K, G=200, n_bus=512, seed=0)
+    d = np.ones(data.n_bus)
+    raw = []
+    for k in range(K):
+        m = copy.copy(data.nets[k])
+        m.b = list(m.b)
+        m.b[0] = synth.scopf_first_bias(data, k, d)
+        raw.append(m)
+    return data, d, raw
+
+
+def scopf_flops(n_in, hidden=1024, depth=5):
+    """Algorithmic FLOPs of one batched Hessian (sum form): per net 2 n m k for the depth-1
+    hidden-to-hidden tangent GEMMs plus n (n+1) m per sigmoid layer (lower triangles)."""
+    f = 0
+    for n in n_in:
+        f += (depth - 1) * 2 * n * hidden * hidden + depth * n * (n + 1) * hidden
+    return f
+
+
+def run_ours_scopf(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    import synth
+
+    data, d, raw = _scopf_workload(args.scopf_k)
+    K = len(raw)
+    n_in = [len(s) for s in data.subsets]
+    cpu_baseline = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import problems as oproblems, nn as onn
+        sample = 8
+        x = np.full(data.G, synth.scopf_demand(data, d) / data.G)
+        t0 = time.perf_counter()
+        for k in range(sample):
+            xs = x[data.subsets[k]]
+            onn.value(raw[k], xs)
+            onn.jacobian(raw[k], xs)
+            onn.vjp(raw[k], xs, np.ones(1))
+            onn.hessian_lag(raw[k], xs, np.ones(1))
+        el = time.perf_counter() - t0
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+        cpu_baseline = {"value": 1.0 / (el * K / sample), "unit": UNIT, "cores": cores, "kind": "oracle",
+                        "sample": f"value, Jacobian, gradient and Hessian of {sample} of the {K} surrogates "
+                                  f"in {el:.1f} s, scaled by {K}/{sample} to one batched evaluation"}
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    from paper_2509_22462_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2509_22462_gb300 import nnc
+    nets = [nnc.Net.from_mlp(m, precision=args.prec) for m in raw]
+    batch = nnc.Batch(nets)
+    for n in nets:
+        n.free()      # the batch keeps its own stacked copy
+    batch.use_graph(True)
+    x = np.full(data.G, synth.scopf_demand(data, d) / data.G)
+    xc = torch.tensor(batch.concat([x[s] for s in data.subsets]), device=dev)
+    lc = torch.ones(K, dtype=torch.float64, device=dev)
+    y = torch.empty(K, dtype=torch.float64, device=dev)
+    J = torch.empty(batch.n_sum, dtype=torch.float64, device=dev)
+    H = torch.empty(batch.h_sum, dtype=torch.float64, device=dev)
+    g = torch.empty(batch.n_sum, dtype=torch.float64, device=dev)
+    r = torch.empty(K, dtype=torch.float64, device=dev)
+
+    def step():
+        batch.eval_dev(xc, lc, y, J, H, g)
+        batch.residual_dev(xc, y, r)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(_gpu_index(local_rank)) if rank == 0 else None
+    launches0 = nnc.launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = nnc.launch_count() - launches0
+    clk = clocks.stop() if clocks else None
+    el_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([el_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el_ms = float(t.item())
+    value = world * args.steps / (el_ms / 1e3)
+    # end to end through the host-pointer batch call
+    xs = [x[s] for s in data.subsets]
+    lams = [np.ones(1)] * K
+    batch.eval(xs, lams)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ys, Js, Hs, gs = batch.eval(xs, lams)
+        batch.residual(xs, ys)
+    el = time.perf_counter() - t0
+    e2e = {"value": world * args.steps / el, "unit": UNIT,
+           "h2d_bytes_per_step": 8 * (batch.n_sum + K) + 8 * (batch.n_sum + K),
+           "d2h_bytes_per_step": 8 * (K + batch.n_sum + batch.h_sum + batch.n_sum) + 8 * K}
+    ipm = {}
+    if rank == 0 and not args.no_ipm:
+        res, v, lam = nnc.ipm_scopf(batch, data.G, data.subsets, data.cost, synth.scopf_demand(data, d),
+                                    data.delta)
+        ipm[args.prec] = res
+    fl = scopf_flops(n_in)
+    if rank == 0:
+        out = {"metric": "batched_hessian_lag_evals_per_s", "value": value, "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": el_ms / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+               "data": "synthetic",
+               "config": {"workload": f"scopf_{K}x(n_k->1024x5->1)_sigmoid", "n_params": int(sum(
+                   sum(w.size + b.size for w, b in zip(m.W, m.b)) for m in raw)), "G": data.G,
+                   "n_in_range": [min(n_in), max(n_in)], "precision_form": args.prec,
+                   "l2": "weights exceed L2 (no flush needed)", "cuda_graph": True},
+               "roofline": {"kernel": "grouped k_tc_gemm + all other grouped launches (whole step)",
+                            "bound": "tensor", "achieved": fl / (el_ms / args.steps / 1e3) / 1e12,
+                            "peak": _peaks()[0].get("bf16_tflops_sustained"), "unit": "TFLOP/s",
+                            "frac": fl / (el_ms / args.steps / 1e3) / 1e12 / _peaks()[0].get("bf16_tflops_sustained"),
+                            "traffic": None},
+               "cpu_baseline": cpu_baseline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+               "ipm_solve": ipm, "hessian_algorithmic_gflop": fl / 1e9}
+        print(json.dumps(out), flush=True)
+    batch.free()
+    return 0
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
+
+    if args.workload == "scopf":
+        return run_ours_scopf(args, rank, world, local_rank)
 
     spec, mlp, d = _workload(args.workload)
     cpu_baseline = None

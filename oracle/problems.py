@@ -14,6 +14,7 @@ import numpy as np
 
 from . import nn as onn
 from .ipm import Problem
+from synth.problems import scopf_first_bias, scopf_demand  # noqa: F401  (problem data)
 
 
 def adversarial(mlp, x0, target=3, margin=0.1):
@@ -80,13 +81,6 @@ def box_projection(x0):
 # ---------------------------------------------------------------- SCOPF-shaped batch (Eq. 8 variant)
 
 
-def scopf_first_bias(data, k, d):
-    """First-layer bias of surrogate k under the load vector d: b_1^(k) + A_k d[B_k] (the load
-    dependence G_k(S^g, S^d) of Eq. 8 entering through the first layer)."""
-    net = data.nets[k]
-    return net.b[0] + data.load_proj[k] @ d[data.load_buses[k]]
-
-
 def scopf_surrogate(data, k, d, calibrate=True):
     """The MLP of contingency k at load d, with its output bias calibrated so that the margin at
     the flat dispatch xbar = (D(d)/G) 1 equals delta_k (strictly feasible start)."""
@@ -98,11 +92,6 @@ def scopf_surrogate(data, k, d, calibrate=True):
         xbar = np.full(len(data.subsets[k]), D / data.G)
         net.b[-1] = net.b[-1] - onn.value(net, xbar) + data.delta[k]
     return net
-
-
-def scopf_demand(data, d):
-    """Total demand D(d) = 0.5 G mean(d): the generators run at half capacity on average."""
-    return 0.5 * data.G * float(np.mean(d))
 
 
 def scopf(data, d=None, nets=None):

@@ -276,9 +276,10 @@ struct BK {
 //      [A_D, A_S, -dc I]], n = nd + ns primal rows and m constraint rows.
 struct KktSolver {
   int nd = 0, ns = 0, m = 0, n = 0, r = 0;
-  std::vector<double> K11, K12, Y, Sm, Kfull, tmp;
-  BK bkS, bkF;
-  bool full = false;
+  std::vector<double> K11, K12, Y, Sm, Kfull, tmp, Dinv, T, AS_;
+  BK bkS, bkF, bkT;
+  int mode = 0;  // 0: Schur of the small block (BK); 1: whole matrix (BK); 2: diagonal small block
+  bool t_chol = false;
   int npos = 0, nneg = 0, nzero = 0;
   void factor(int nd_, int ns_, int m_, const double* WDD, const double* WSS, const double* sig,
               const double* AD, const double* AS, double dw, double dc, double zero_tol) {
@@ -290,10 +291,54 @@ struct KktSolver {
     K11.assign((size_t)nd * nd, 0.0);
     std::memcpy(K11.data(), WDD, sizeof(double) * nd * nd);
     for (int i = 0; i < nd; ++i) K11[(size_t)i * nd + i] += sig[i] + dw;
+    const bool pd = nd == 0 || cholesky(nd, K11.data());
+    bool diag_pd = pd && ns > 0;
+    for (int a = 0; a < ns && diag_pd; ++a) diag_pd = WSS[a] + sig[nd + a] + dw > 0.0;
+    if (diag_pd) {
+      // Eliminate the diagonal small block as well: T = -dc I - A_D K11^-1 A_D^T - A_S D^-1 A_S^T.
+      // inertia(K) = (nd + ns, 0, 0) + inertia(T); T must be negative definite.
+      mode = 2;
+      Dinv.resize(ns);
+      for (int a = 0; a < ns; ++a) Dinv[a] = 1.0 / (WSS[a] + sig[nd + a] + dw);
+      AS_.assign(AS, AS + (size_t)m * ns);
+      Y.assign((size_t)nd * m, 0.0);
+      for (int i = 0; i < nd; ++i)
+        for (int j = 0; j < m; ++j) Y[(size_t)i * m + j] = AD[(size_t)j * nd + i];
+      if (nd) lower_solve(nd, K11.data(), m, Y.data());
+      T.assign((size_t)m * m, 0.0);
+#pragma omp parallel for schedule(dynamic, 4) if (m >= 64)
+      for (int a = 0; a < m; ++a) {
+        for (int b = 0; b <= a; ++b) {
+          double s = 0;
+          for (int i = 0; i < nd; ++i) s += Y[(size_t)i * m + a] * Y[(size_t)i * m + b];
+          const double* ra = &AS_[(size_t)a * ns];
+          const double* rb = &AS_[(size_t)b * ns];
+          for (int c = 0; c < ns; ++c)
+            if (ra[c] != 0.0 && rb[c] != 0.0) s += ra[c] * rb[c] * Dinv[c];
+          // store -T (expected positive definite)
+          T[(size_t)a * m + b] = s + (a == b ? dc : 0.0);
+          T[(size_t)b * m + a] = T[(size_t)a * m + b];
+        }
+      }
+      std::vector<double> Tc(T);
+      t_chol = m == 0 || cholesky(m, Tc.data());
+      if (t_chol) {
+        T.swap(Tc);
+        npos = n;
+        nneg = m;
+        nzero = 0;
+      } else {
+        for (auto& v : T) v = -v;   // T itself, for the exact inertia
+        bkT.factor(m, T.data(), zero_tol);
+        npos = n + bkT.npos;
+        nneg = bkT.nneg;
+        nzero = bkT.nzero;
+      }
+      return;
+    }
     K12.assign((size_t)nd * r, 0.0);
     for (int i = 0; i < nd; ++i)
       for (int j = 0; j < m; ++j) K12[(size_t)i * r + ns + j] = AD[(size_t)j * nd + i];
-    const bool pd = nd == 0 || cholesky(nd, K11.data());
     if (pd) {
       Y = K12;
       if (nd) lower_solve(nd, K11.data(), r, Y.data());
@@ -317,7 +362,7 @@ struct KktSolver {
       npos = nd + bkS.npos;
       nneg = bkS.nneg;
       nzero = bkS.nzero;
-      full = false;
+      mode = 0;
     } else {
       const int N = n + m;
       Kfull.assign((size_t)N * N, 0.0);
@@ -335,13 +380,62 @@ struct KktSolver {
       npos = bkF.npos;
       nneg = bkF.nneg;
       nzero = bkF.nzero;
-      full = true;
+      mode = 1;
     }
   }
+  bool full() const { return mode == 1; }
   // rhs (n + m) -> solution, in place
   void solve(double* rhs) {
-    if (full) {
+    if (mode == 1) {
       bkF.solve(rhs);
+      return;
+    }
+    if (mode == 2) {
+      // z = T^-1 (r3 - A_D K11^-1 r1 - A_S D^-1 r2); u = K11^-1 (r1 - A_D^T z); w = D^-1 (r2 - A_S^T z)
+      tmp.assign(rhs, rhs + nd);
+      if (nd) lower_solve1(nd, K11.data(), tmp.data());     // t = L^-1 r1; A_D K11^-1 r1 = Y^T t
+      std::vector<double> z(m);
+      for (int j = 0; j < m; ++j) {
+        double s = rhs[n + j];
+        for (int i = 0; i < nd; ++i) s -= Y[(size_t)i * m + j] * tmp[i];
+        const double* ra = &AS_[(size_t)j * ns];
+        for (int c = 0; c < ns; ++c)
+          if (ra[c] != 0.0) s -= ra[c] * Dinv[c] * rhs[nd + c];
+        z[j] = s;
+      }
+      if (t_chol) {      // T = -(L_T L_T^T)
+        lower_solve1(m, T.data(), z.data());
+        upper_solve_lt(m, T.data(), z.data());
+        for (double& v : z) v = -v;
+      } else {
+        bkT.solve(z.data());
+      }
+      std::vector<double> u(rhs, rhs + nd);
+      // r1 - A_D^T z, with A_D^T = L Y (Y = L^-1 A_D^T is stored): A_D^T z = L (Y z)
+      std::vector<double> yz(nd, 0.0);
+      for (int i = 0; i < nd; ++i) {
+        double s = 0;
+        for (int j = 0; j < m; ++j) s += Y[(size_t)i * m + j] * z[j];
+        yz[i] = s;
+      }
+      // L yz
+      for (int i = nd - 1; i >= 0; --i) {
+        double s = 0;
+        const double* li = &K11[(size_t)i * nd];
+        for (int j = 0; j <= i; ++j) s += li[j] * yz[j];
+        u[i] -= s;
+      }
+      if (nd) {
+        lower_solve1(nd, K11.data(), u.data());
+        upper_solve_lt(nd, K11.data(), u.data());
+      }
+      for (int c = 0; c < ns; ++c) {
+        double s = rhs[nd + c];
+        for (int j = 0; j < m; ++j) s -= AS_[(size_t)j * ns + c] * z[j];
+        rhs[nd + c] = s * Dinv[c];
+      }
+      for (int i = 0; i < nd; ++i) rhs[i] = u[i];
+      for (int j = 0; j < m; ++j) rhs[n + j] = z[j];
       return;
     }
     // [K11 K12; K12^T K22] [u; w] = [r1; r2]: w = S^-1 (r2 - Y^T L^-1 r1), u = K11^-1 (r1 - K12 w)
@@ -873,7 +967,7 @@ int nnc_kkt_solve(int nd, int ns, int m, const double* WDD, const double* WSS, c
     inertia[0] = k.npos;
     inertia[1] = k.nneg;
     inertia[2] = k.nzero;
-    inertia[3] = k.full ? 1 : 0;
+    inertia[3] = k.full() ? 1 : 0;
   }
   if (k.nzero == 0) k.solve(rhs_sol);
   return NNC_OK;

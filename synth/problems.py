@@ -64,3 +64,14 @@ def scopf_data(K: int = 256, G: int = 200, n_bus: int = 512, seed: int = 0,
 def load_vectors(n: int, n_bus: int = 512, seed: int = 0, tag: str = "loads") -> np.ndarray:
     """n load vectors d ~ N(1, 0.1^2) per bus, shape (n, n_bus)."""
     return 1.0 + 0.1 * normal(derive_key(seed, tag), n * n_bus).reshape(n, n_bus)
+
+
+def scopf_first_bias(data: ScopfData, k: int, d: np.ndarray) -> np.ndarray:
+    """First-layer bias of surrogate k under the load vector d: b_1^(k) + A_k d[B_k] -- the load
+    dependence of the stability map G_k(S^g, S^d) in Eq. 8 (problem data, not network work)."""
+    return data.nets[k].b[0] + data.load_proj[k] @ d[data.load_buses[k]]
+
+
+def scopf_demand(data: ScopfData, d: np.ndarray) -> float:
+    """Total demand D(d) = 0.5 G mean(d): the generators run at half capacity on average."""
+    return 0.5 * data.G * float(np.mean(d))
