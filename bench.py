@@ -29,6 +29,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "hessian_lag_evals_per_s"
+
+# DRAM bytes (read + write) of one tangent-GEMM launch from the ncu capture summarised in
+# profiles/k_tc_gemm_tangent_784x4096x4096.md; valid for the kernel version it was taken on.
+TANGENT_TRAFFIC = {("104m", "bf16x3"): 83.97e6}
 UNIT = "evals/s"
 
 
@@ -443,10 +447,12 @@ def run_ours(args, rank, world, local_rank):
         el_ms = float(t.item())
     value = world * args.steps / (el_ms / 1e3)
 
-    # roofline of the dominant kernel kind (by total time in the timed region)
+    # roofline of the dominant kernel: the tangent GEMM (the largest single kernel of a step;
+    # the value pass and the FP64 residual are 16 smaller launches of two different kernels)
     peaks, peak_src = _peaks()
-    dom = max(prof.items(), key=lambda kv: kv[1][0])
-    dom_name, (dom_ms, dom_cnt) = dom
+    dom_name = "tangent_gemm" if prof.get("tangent_gemm", (0, 0))[1] > 0 else \
+        max(prof.items(), key=lambda kv: kv[1][0])[0]
+    dom_ms, dom_cnt = prof[dom_name]
     roof = None
     if dom_name == "tangent_gemm" and dom_cnt > 0:
         per = tangent_gemm_flops(spec)
@@ -457,7 +463,8 @@ def run_ours(args, rank, world, local_rank):
         roof = {"kernel": "k_tc_gemm (tangent: Zdot_l = W_l Adot_{l-1}, fused sigma' / sigma'' epilogue)"
                 if args.prec.startswith("bf16") else "k_simt_gemm (tangent)",
                 "bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                "traffic": None, "peak_source": f"{peak_src} bf16 sustained",
+                "traffic": TANGENT_TRAFFIC.get((args.workload, args.prec)),
+                "peak_source": f"{peak_src} bf16 sustained",
                 "executed_frac": ach * (3 if args.prec == "bf16x3" else 1) / pk,
                 "avg_launch_us": avg_s * 1e6, "launches": dom_cnt,
                 "algorithmic_flops_per_launch": fl_per_launch}

@@ -157,6 +157,36 @@ int nnc_batch_eval(nnc_batch* batch, const double* x_cat, const double* lambda_c
                    double* J_cat, double* H_cat, double* grad_cat);
 int nnc_batch_residual(nnc_batch* batch, const double* x_cat, const double* y_cat, double* r_cat);
 
+/* ---- Learned warm start ---------------------------------------------------------------------
+ * An MLP n_in -> h1 -> h2 -> n_out with GELU hidden layers (GELU(z) = z Phi(z)) and a linear
+ * output that maps problem parameters to an interior-point starting point, trained on the GPU
+ * by the library's own forward, backward and Adam kernels.  Operands are BF16 (prec = NNC_BF16)
+ * or FP32 (NNC_FP32) with FP32 accumulation; master weights and Adam moments are FP32.
+ *   params : 6 host arrays W1 (h1 x n_in), b1, W2 (h2 x h1), b2, W3 (n_out x h2), b3 (row-major).
+ * Inputs and targets are standardized per coordinate (nnc_ws_train sets the scaling from its
+ * data; nnc_ws_set_scaling sets it directly); the loss is the mean squared error on
+ * standardized targets; nnc_ws_predict returns de-standardized predictions. */
+typedef struct nnc_ws nnc_ws;
+int nnc_ws_create(nnc_ws** out, int n_in, int h1, int h2, int n_out, const double* const* params,
+                  int prec, void* stream);
+void nnc_ws_free(nnc_ws* ws);
+int nnc_ws_set_scaling(nnc_ws* ws, const double* in_mean, const double* in_std,
+                       const double* out_mean, const double* out_std);
+/* Loss and gradients (6 host arrays like params, each may be NULL) on B rows U (B x n_in),
+ * T (B x n_out) with the current weights; no update. */
+int nnc_ws_loss_grad(nnc_ws* ws, const double* U, const double* T, int B, double* loss,
+                     double* const* grads);
+/* One Adam step (Kingma & Ba) with the gradients of the last nnc_ws_loss_grad. */
+int nnc_ws_adam_step(nnc_ws* ws, double lr, double beta1, double beta2, double eps);
+/* Mini-batch training: `epochs` passes over N rows in seeded random order, batch rows per step. */
+int nnc_ws_train(nnc_ws* ws, const double* U, const double* T, int N, int epochs, int batch,
+                 double lr, double beta1, double beta2, double eps, unsigned long long seed,
+                 double* final_loss);
+/* P (N x n_out) for U (N x n_in). */
+int nnc_ws_predict(nnc_ws* ws, const double* U, int N, double* P);
+/* Current FP32 master weights, widened to FP64 (6 host arrays, each may be NULL). */
+int nnc_ws_get_params(nnc_ws* ws, double* const* params);
+
 /* Free a net and all of its device memory (waits for its stream).  NULL is ignored. */
 void nnc_free(nnc_net* net);
 

@@ -47,6 +47,7 @@ typedef struct {
   int max_backtracks;      /* 40 */
   int max_ls_failures;     /* 5 */
   int verbose;             /* print one line per iteration */
+  double warm_mu0;         /* 1e-3: barrier parameter of a warm start (z = warm_mu0 / slack) */
 } nnc_ipm_options;
 
 typedef struct {
@@ -104,6 +105,13 @@ int nnc_ipm_adversarial(nnc_net* net, const double* x0, int target, double margi
 int nnc_ipm_scopf(nnc_batch* batch, int G, const int* n_in, const int* subsets, const double* cost,
                   double demand, const double* delta, const nnc_ipm_options* opt, double* v_out,
                   double* lam_out, nnc_ipm_result* result);
+/* The same problem from a predicted start (a learned warm start): v_start (G + K) is pushed into
+ * the bounds like any start, the constraint multipliers start at lam_start (K + 1), the barrier
+ * parameter at opt->warm_mu0 and every bound multiplier at warm_mu0 / slack. */
+int nnc_ipm_scopf_warm(nnc_batch* batch, int G, const int* n_in, const int* subsets,
+                       const double* cost, double demand, const double* delta,
+                       const double* v_start, const double* lam_start, const nnc_ipm_options* opt,
+                       double* v_out, double* lam_out, nnc_ipm_result* result);
 
 #ifdef __cplusplus
 }

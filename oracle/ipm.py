@@ -28,6 +28,9 @@ terms -mu/(v - L) + mu/(U - v) plus the bound multipliers they replace.  The ste
        nu raised so that the step is a descent direction
     7  v += alpha dv, lambda += alpha dl, z += alpha_z dz; keep z within a factor
        kappa_Sigma = 1e10 of mu / slack.
+A warm start (a predicted point v, lambda) replaces the start: v pushed into the bounds as above,
+lambda as given, mu = warm_mu0 = 1e-3 and z = mu / slack, so every complementarity product starts
+at mu.
 The inertia here is the plain definition (signs of the eigenvalues, numpy eigvalsh); the
 solve is numpy's dense solver.  Iteration counts need not match IPOPT's (no filter, no
 second-order correction, no restoration phase).
@@ -64,6 +67,7 @@ class Options:
     kappa_sigma: float = 1e10
     max_backtracks: int = 40
     max_ls_failures: int = 5
+    warm_mu0: float = 1e-3
 
 
 @dataclass
@@ -115,13 +119,16 @@ def _inertia(K, tol=0.0):
     return int(((ev > 0) & ~zero).sum()), int(((ev < 0) & ~zero).sum()), int(zero.sum())
 
 
-def solve(p: Problem, opt: Optional[Options] = None, callback=None) -> Result:
+def solve(p: Problem, opt: Optional[Options] = None, callback=None, warm=None) -> Result:
+    """warm = (v_start, lam_start) starts from a predicted point (a learned warm start): v_start
+    is pushed into the bounds like any start, lambda = lam_start, mu = warm_mu0 and every bound
+    multiplier is rebuilt as z = mu / slack."""
     opt = opt or Options()
     n, m = p.n, p.m
     lb, ub = np.asarray(p.lb, float), np.asarray(p.ub, float)
     hasL, hasU = np.isfinite(lb), np.isfinite(ub)
     # --- start: push v0 into the bounds
-    v = np.array(p.v0, dtype=np.float64)
+    v = np.array(p.v0 if warm is None else warm[0], dtype=np.float64)
     width = np.where(hasL & hasU, ub - lb, np.inf)
     pL = np.minimum(opt.kappa1 * np.maximum(1.0, np.abs(np.where(hasL, lb, 0.0))), opt.kappa2 * width)
     pU = np.minimum(opt.kappa1 * np.maximum(1.0, np.abs(np.where(hasU, ub, 0.0))), opt.kappa2 * width)
@@ -131,6 +138,11 @@ def solve(p: Problem, opt: Optional[Options] = None, callback=None) -> Result:
     zU = np.where(hasU, 1.0, 0.0)
     lam = np.zeros(m)
     mu = opt.mu0
+    if warm is not None:
+        lam = np.array(warm[1], dtype=np.float64)
+        mu = opt.warm_mu0
+        zL = np.where(hasL, mu / np.where(hasL, v - np.where(hasL, lb, 0.0), 1.0), 0.0)
+        zU = np.where(hasU, mu / np.where(hasU, np.where(hasU, ub, 0.0) - v, 1.0), 0.0)
     tau = max(opt.tau_min, 1.0 - mu)
     nu = 1.0
     delta_w_last = 0.0

@@ -151,3 +151,8 @@ def scopf(data, d=None, nets=None):
     p.nets = nets
     p.demand = D
     return p
+
+
+def scopf_raw_nets(data, d):
+    """The surrogates with the load shift in the first-layer bias and no output calibration."""
+    return [scopf_surrogate(data, k, d, calibrate=False) for k in range(len(data.nets))]

@@ -488,7 +488,8 @@ double inf_norm(const std::vector<double>& x) {
 }
 
 int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_out,
-              std::vector<double>& lam_out, nnc_ipm_result* res) {
+              std::vector<double>& lam_out, nnc_ipm_result* res, const double* v_start = nullptr,
+              const double* lam_start = nullptr) {
   const auto t_start = Clock::now();
   Timers T;
   const int nd = p.nd, ns = p.ns, n = nd + ns, m = p.m, r = ns + m;
@@ -501,6 +502,7 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
     if (hasU[i]) ub0[i] = p.ub[i];
   }
   std::vector<double> v(p.v0);
+  if (v_start) v.assign(v_start, v_start + n);
   for (int i = 0; i < n; ++i) {
     const double width = (hasL[i] && hasU[i]) ? ub0[i] - lb0[i] : INFINITY;
     if (hasL[i]) v[i] = std::max(v[i], lb0[i] + std::min(o.kappa1 * std::max(1.0, std::fabs(lb0[i])), o.kappa2 * width));
@@ -511,7 +513,17 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
     zL[i] = hasL[i] ? 1.0 : 0.0;
     zU[i] = hasU[i] ? 1.0 : 0.0;
   }
-  double mu = o.mu0, tau = std::max(o.tau_min, 1.0 - mu), nu = 1.0, delta_w_last = 0.0;
+  double mu = o.mu0;
+  if (v_start && lam_start) {
+    // warm start: given multipliers, small barrier parameter, z = mu / slack
+    mu = o.warm_mu0;
+    for (int j = 0; j < m; ++j) lam[j] = lam_start[j];
+    for (int i = 0; i < n; ++i) {
+      zL[i] = hasL[i] ? mu / (v[i] - lb0[i]) : 0.0;
+      zU[i] = hasU[i] ? mu / (ub0[i] - v[i]) : 0.0;
+    }
+  }
+  double tau = std::max(o.tau_min, 1.0 - mu), nu = 1.0, delta_w_last = 0.0;
   int ls_fail = 0, status = NNC_IPM_MAX_ITER, it = 0;
   double E0 = INFINITY;
   std::vector<double> g(n), c(m), AD((size_t)m * nd), AS((size_t)m * ns), WDD((size_t)nd * nd),
@@ -915,9 +927,10 @@ struct Scopf : IpmProblem {
 
 extern "C" {
 
-int nnc_ipm_scopf(nnc_batch* batch, int G, const int* n_in, const int* subsets, const double* cost,
-                  double demand, const double* delta, const nnc_ipm_options* opt, double* v_out,
-                  double* lam_out, nnc_ipm_result* res) {
+int nnc_ipm_scopf_warm(nnc_batch* batch, int G, const int* n_in, const int* subsets,
+                       const double* cost, double demand, const double* delta,
+                       const double* v_start, const double* lam_start, const nnc_ipm_options* opt,
+                       double* v_out, double* lam_out, nnc_ipm_result* res) {
   int K = 0, no = 0, n_sum = 0;
   long long h_sum = 0;
   int rc = nnc_batch_info(batch, &K, &no, &n_sum, &h_sum);
@@ -936,11 +949,18 @@ int nnc_ipm_scopf(nnc_batch* batch, int G, const int* n_in, const int* subsets, 
   rc = p.start(delta);
   if (rc) return rc;
   std::vector<double> v, lam;
-  rc = ipm_solve(p, o, v, lam, res);
+  rc = ipm_solve(p, o, v, lam, res, v_start, v_start ? lam_start : nullptr);
   if (rc) return rc;
   if (v_out) std::copy(v.begin(), v.end(), v_out);
   if (lam_out) std::copy(lam.begin(), lam.end(), lam_out);
   return NNC_OK;
+}
+
+int nnc_ipm_scopf(nnc_batch* batch, int G, const int* n_in, const int* subsets, const double* cost,
+                  double demand, const double* delta, const nnc_ipm_options* opt, double* v_out,
+                  double* lam_out, nnc_ipm_result* res) {
+  return nnc_ipm_scopf_warm(batch, G, n_in, subsets, cost, demand, delta, nullptr, nullptr, opt,
+                            v_out, lam_out, res);
 }
 
 int nnc_kkt_solve(int nd, int ns, int m, const double* WDD, const double* WSS, const double* sigma,
@@ -996,6 +1016,7 @@ void nnc_ipm_default_options(nnc_ipm_options* o) {
   o->max_backtracks = 40;
   o->max_ls_failures = 5;
   o->verbose = 0;
+  o->warm_mu0 = 1e-3;
 }
 
 int nnc_ipm_adversarial(nnc_net* net, const double* x0, int target, double margin,

@@ -28,7 +28,9 @@ EXPORTS = ["nnc_load_weights", "nnc_eval", "nnc_residual", "nnc_jacobian", "nnc_
            "nnc_ipm_default_options", "nnc_ipm_adversarial", "nnc_kkt_solve",
            "nnc_residual_noalloc", "nnc_batch_create", "nnc_batch_free", "nnc_batch_info",
            "nnc_batch_set_bias", "nnc_batch_use_graph", "nnc_batch_eval_dev", "nnc_batch_residual_dev",
-           "nnc_batch_eval", "nnc_batch_residual", "nnc_ipm_scopf"]
+           "nnc_batch_eval", "nnc_batch_residual", "nnc_ipm_scopf", "nnc_ws_create", "nnc_ws_free",
+           "nnc_ws_set_scaling", "nnc_ws_loss_grad", "nnc_ws_adam_step", "nnc_ws_train",
+           "nnc_ws_predict", "nnc_ws_get_params", "nnc_ipm_scopf_warm"]
 IPM_STATUS = {0: "optimal", 1: "max_iter", 2: "linesearch_failed", 3: "nonfinite",
               4: "inertia_failed", 5: "eval_error"}
 
@@ -43,7 +45,7 @@ class IpmOptions(ctypes.Structure):
                 ("kappa_w_plus", ctypes.c_double), ("kappa_w_plus_bar", ctypes.c_double),
                 ("kappa_w_minus", ctypes.c_double), ("kappa_sigma", ctypes.c_double),
                 ("max_backtracks", ctypes.c_int), ("max_ls_failures", ctypes.c_int),
-                ("verbose", ctypes.c_int)]
+                ("verbose", ctypes.c_int), ("warm_mu0", ctypes.c_double)]
 
 
 class IpmResult(ctypes.Structure):
@@ -119,6 +121,20 @@ def load_library(path: str = LIB_PATH):
     lib.nnc_ipm_scopf.argtypes = [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                   ctypes.POINTER(ctypes.c_int), _DP, ctypes.c_double, _DP,
                                   ctypes.POINTER(IpmOptions), _DP, _DP, ctypes.POINTER(IpmResult)]
+    lib.nnc_ipm_scopf_warm.argtypes = [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int), _DP, ctypes.c_double, _DP, _DP, _DP,
+                                       ctypes.POINTER(IpmOptions), _DP, _DP, ctypes.POINTER(IpmResult)]
+    lib.nnc_ws_create.argtypes = [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_int, ctypes.POINTER(_DP), ctypes.c_int, _P]
+    lib.nnc_ws_free.argtypes = [_P]
+    lib.nnc_ws_free.restype = None
+    lib.nnc_ws_set_scaling.argtypes = [_P, _DP, _DP, _DP, _DP]
+    lib.nnc_ws_loss_grad.argtypes = [_P, _DP, _DP, ctypes.c_int, _DP, ctypes.POINTER(_DP)]
+    lib.nnc_ws_adam_step.argtypes = [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    lib.nnc_ws_train.argtypes = [_P, _DP, _DP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                 ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_ulonglong, _DP]
+    lib.nnc_ws_predict.argtypes = [_P, _DP, ctypes.c_int, _DP]
+    lib.nnc_ws_get_params.argtypes = [_P, ctypes.POINTER(_DP)]
     lib.nnc_residual_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_P),
                                          ctypes.POINTER(_P), _P, _P, _P, _P]
@@ -131,7 +147,7 @@ def load_library(path: str = LIB_PATH):
                                      ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
     for name in EXPORTS:
         if name not in ("nnc_free", "nnc_last_error", "nnc_launch_count", "nnc_ipm_default_options",
-                        "nnc_batch_free"):
+                        "nnc_batch_free", "nnc_ws_free"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -415,9 +431,10 @@ class Batch:
         _check(_lib.nnc_batch_residual_dev(self._h, _tp(x), _tp(y), _tp(r), stream or _stream_ptr()))
 
 
-def ipm_scopf(batch, G, subsets, cost, demand, delta, **options):
-    """The SCOPF-shaped problem with the host interior-point driver (include/nnc_ipm.h).
-    subsets: list of K index arrays S_k.  Returns (result dict, v = (x, y), lambda)."""
+def ipm_scopf(batch, G, subsets, cost, demand, delta, v_start=None, lam_start=None, **options):
+    """The SCOPF-shaped problem with the host interior-point driver (include/nnc_ipm.h), cold or
+    (with v_start, lam_start) warm-started.  subsets: list of K index arrays S_k.
+    Returns (result dict, v = (x, y), lambda)."""
     lib = load_library()
     K = batch.K
     n_in = (ctypes.c_int * K)(*[len(s) for s in subsets])
@@ -428,6 +445,75 @@ def ipm_scopf(batch, G, subsets, cost, demand, delta, **options):
     v = np.empty(G + K)
     lam = np.empty(K + 1)
     res = IpmResult()
-    _check(lib.nnc_ipm_scopf(batch.handle, int(G), n_in, subp, _dp(cost), float(demand), _dp(delta),
-                             ctypes.byref(o), _dp(v), _dp(lam), ctypes.byref(res)))
+    if v_start is None:
+        _check(lib.nnc_ipm_scopf(batch.handle, int(G), n_in, subp, _dp(cost), float(demand), _dp(delta),
+                                 ctypes.byref(o), _dp(v), _dp(lam), ctypes.byref(res)))
+    else:
+        vs, ls = _f64(v_start), _f64(lam_start)
+        _check(lib.nnc_ipm_scopf_warm(batch.handle, int(G), n_in, subp, _dp(cost), float(demand), _dp(delta),
+                                      _dp(vs), _dp(ls), ctypes.byref(o), _dp(v), _dp(lam), ctypes.byref(res)))
     return res.as_dict(), v, lam
+
+
+class WarmStart:
+    """nnc_ws: the warm-start MLP n_in -> h1 -> h2 -> n_out (GELU) trained by the library's kernels."""
+
+    def __init__(self, params, precision="bf16", stream=None):
+        lib = load_library()
+        self.params0 = [_f64(p) for p in params]
+        W1, _, W2, _, W3, _ = self.params0
+        self.h1, self.n_in = W1.shape
+        self.h2 = W2.shape[0]
+        self.n_out = W3.shape[0]
+        pp = (_DP * 6)(*[_dp(p) for p in self.params0])
+        h = _P()
+        _check(lib.nnc_ws_create(ctypes.byref(h), self.n_in, self.h1, self.h2, self.n_out, pp,
+                                 PRECISIONS[precision], stream))
+        self._h = h
+
+    def free(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.nnc_ws_free(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def _shapes(self):
+        return [(self.h1, self.n_in), (self.h1,), (self.h2, self.h1), (self.h2,), (self.n_out, self.h2), (self.n_out,)]
+
+    def set_scaling(self, in_mean, in_std, out_mean, out_std):
+        a = [_f64(x) for x in (in_mean, in_std, out_mean, out_std)]
+        _check(_lib.nnc_ws_set_scaling(self._h, *[_dp(x) for x in a]))
+
+    def loss_grad(self, U, T):
+        U, T = _f64(U), _f64(T)
+        grads = [np.empty(s) for s in self._shapes()]
+        loss = ctypes.c_double()
+        gp = (_DP * 6)(*[_dp(g) for g in grads])
+        _check(_lib.nnc_ws_loss_grad(self._h, _dp(U), _dp(T), U.shape[0], ctypes.byref(loss), gp))
+        return loss.value, grads
+
+    def adam_step(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        _check(_lib.nnc_ws_adam_step(self._h, lr, beta1, beta2, eps))
+
+    def train(self, U, T, epochs, batch=64, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, seed=0):
+        U, T = _f64(U), _f64(T)
+        loss = ctypes.c_double()
+        _check(_lib.nnc_ws_train(self._h, _dp(U), _dp(T), U.shape[0], int(epochs), int(batch), lr, beta1,
+                                 beta2, eps, int(seed), ctypes.byref(loss)))
+        return loss.value
+
+    def predict(self, U):
+        U = _f64(U)
+        P = np.empty((U.shape[0], self.n_out))
+        _check(_lib.nnc_ws_predict(self._h, _dp(U), U.shape[0], _dp(P)))
+        return P
+
+    def params(self):
+        out = [np.empty(s) for s in self._shapes()]
+        _check(_lib.nnc_ws_get_params(self._h, (_DP * 6)(*[_dp(o) for o in out])))
+        return out

@@ -90,3 +90,13 @@ PAPER_87M = mnist_like_spec(4096, 6)           # literal "6 hidden layers" readi
 
 def spec_by_name(name: str) -> Optional[MLPSpec]:
     return {"tiny": TINY, "104m": PAPER_104M, "87m": PAPER_87M}.get(name)
+
+
+def warmstart_params(n_in: int, h1: int, h2: int, n_out: int, seed: int = 0):
+    """Initial weights of the warm-start MLP n_in -> h1 -> h2 -> n_out: N(0, 2/fan_in) (He et al.
+    2015, suited to GELU layers), zero biases.  Returned as [W1, b1, W2, b2, W3, b3]."""
+    out = []
+    for l, (m, k) in enumerate(((h1, n_in), (h2, h1), (n_out, h2))):
+        out.append(normal(derive_key(seed, "warmstart", "W", l), m * k).reshape(m, k) * np.sqrt(2.0 / k))
+        out.append(np.zeros(m))
+    return out
