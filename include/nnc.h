@@ -199,6 +199,15 @@ int nnc_net_info(const nnc_net* net, int* n_layers, int* n_in, int* n_out, int* 
 /* Number of kernel launches this library queued since load (all nets, this process). */
 long long nnc_launch_count(void);
 
+/* Autotuner for the tensor-core forms (no effect on results): times every N-tile width of each
+ * tangent-GEMM shape and every split-K count of the symmetric product on the net's own buffers
+ * (CUDA events on its stream) and keeps the fastest.  cache_path (may be NULL) names a JSON file
+ * of earlier choices, keyed by device, kind, precision and shape; existing entries are reused
+ * unless retune != 0, and the file is rewritten with the current choices.  CUDA-core forms
+ * return NNC_OK at once.  nnc_tuning reports the current choice for one layer. */
+int nnc_autotune(nnc_net* net, const char* cache_path, int retune);
+int nnc_tuning(const nnc_net* net, int layer, int* tangent_bn, int* syrk_splits);
+
 /* Per-kernel timing with CUDA events on the net's launch streams (no effect on results).
  * nnc_profile(net, 1) starts recording a pair of events around every launch (and clears what
  * was recorded); nnc_profile_read waits for the recorded work, then fills ms[k] (total

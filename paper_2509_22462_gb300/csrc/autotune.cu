@@ -1,0 +1,189 @@
+// Autotuner for the tensor-core GEMMs of a net: for every tangent-GEMM shape it times the N-tile
+// widths the kernel supports, for the symmetric product the split-K counts, on the net's own
+// buffers with CUDA events, and keeps the fastest.  Results can be kept in a small JSON file
+// ({"<key>": [choice, microseconds], ...}, one key per device, kind, precision and shape) so that
+// later loads reuse them without timing.
+#include <algorithm>
+#include <cstdio>
+#include <fstream>
+#include <map>
+#include <sstream>
+#include <string>
+
+#include "net.cuh"
+
+using namespace nnc;
+
+namespace {
+
+std::map<std::string, std::pair<int, double>> read_cache(const char* path) {
+  std::map<std::string, std::pair<int, double>> m;
+  if (!path) return m;
+  std::ifstream f(path);
+  if (!f) return m;
+  std::stringstream ss;
+  ss << f.rdbuf();
+  const std::string s = ss.str();
+  size_t i = 0;
+  while (true) {
+    const size_t k0 = s.find('"', i);
+    if (k0 == std::string::npos) break;
+    const size_t k1 = s.find('"', k0 + 1);
+    const size_t b0 = s.find('[', k1);
+    const size_t b1 = s.find(']', b0);
+    if (k1 == std::string::npos || b0 == std::string::npos || b1 == std::string::npos) break;
+    int choice = 0;
+    double us = 0;
+    if (std::sscanf(s.c_str() + b0 + 1, "%d , %lf", &choice, &us) == 2)
+      m[s.substr(k0 + 1, k1 - k0 - 1)] = {choice, us};
+    i = b1 + 1;
+  }
+  return m;
+}
+
+void write_cache(const char* path, const std::map<std::string, std::pair<int, double>>& m) {
+  if (!path) return;
+  std::ofstream f(path);
+  f << "{\n";
+  size_t n = 0;
+  for (auto& kv : m) {
+    f << "  \"" << kv.first << "\": [" << kv.second.first << ", " << kv.second.second << "]";
+    f << (++n < m.size() ? ",\n" : "\n");
+  }
+  f << "}\n";
+}
+
+std::string key_of(const nnc_net* net, const char* kind, int M, int N, int K) {
+  cudaDeviceProp p;
+  cudaGetDeviceProperties(&p, net->device);
+  char b[256];
+  std::snprintf(b, sizeof b, "sm%d%d-%dsm %s prec%d M%d N%d K%d", p.major, p.minor,
+                p.multiProcessorCount, kind, net->prec, M, N, K);
+  return b;
+}
+
+// Average microseconds of `reps` runs of fn on st (after one warm-up run).
+template <typename F>
+double time_us(cudaStream_t st, int reps, F fn) {
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  fn();
+  cudaEventRecord(a, st);
+  for (int i = 0; i < reps; ++i) fn();
+  cudaEventRecord(b, st);
+  cudaEventSynchronize(b);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return cudaGetLastError() == cudaSuccess ? 1e3 * ms / reps : 1e30;
+}
+
+}  // namespace
+
+extern "C" int nnc_autotune(nnc_net* net, const char* cache_path, int retune) {
+  if (!net) {
+    set_last_error("net is NULL");
+    return NNC_ERR_ARG;
+  }
+  const int prec = net->prec;
+  if (!(prec == NNC_BF16 || prec == NNC_BF16X3 || prec == NNC_FP8)) return NNC_OK;  // CUDA-core forms
+  cudaSetDevice(net->device);
+  auto cache = read_cache(cache_path);
+  cudaStream_t st = net->stream;
+  const int n = net->n_in;
+  const int bns[4] = {112, 128, 208, 256};
+  // tangent GEMMs
+  for (int l = 1; l < net->L; ++l) {
+    LayerDev& Ly = net->layers[l];
+    if (!Ly.plan_tan.ready) continue;
+    const std::string key = key_of(net, "tangent", Ly.mp, n, Ly.kp);
+    int best = Ly.plan_tan.bn;
+    auto it = cache.find(key);
+    if (it != cache.end() && !retune) {
+      best = it->second.first;
+    } else {
+      double best_us = 1e30;
+      const int cur = (l - 1) % 2;
+      for (int bn : bns) {
+        TcPlan p;
+        const int r = prec == NNC_FP8
+                          ? tc_plan_make(p, TC_TANGENT, prec, Ly.W8, nullptr, Ly.mp, Ly.kp, net->A8, nullptr,
+                                         n, Ly.kp, Ly.mp, n, Ly.kp, net->sm_count, bn)
+                          : tc_plan_make(p, TC_TANGENT, prec, Ly.Whi, Ly.Wlo, Ly.mp, Ly.kp, net->At[cur][0],
+                                         net->At[cur][1], n, Ly.kp, Ly.mp, n, Ly.kp, net->sm_count, bn);
+        if (r != NNC_OK) continue;
+        const double us = time_us(st, 3, [&] {
+          tc_tangent(p, Ly.s1, Ly.c_f, net->At[1 - cur][0], net->At[1 - cur][1], Ly.mp, net->Zt[0],
+                     net->Zt[1], net->Yt[0], net->Yt[1], net->K_total, net->dev_err, st, Ly.w8s, net->tsc);
+        });
+        if (us < best_us) {
+          best_us = us;
+          best = bn;
+        }
+      }
+      cache[key] = {best, best_us};
+    }
+    if (best != Ly.plan_tan.bn) {
+      const int cur = (l - 1) % 2;
+      if (prec == NNC_FP8)
+        tc_plan_make(Ly.plan_tan, TC_TANGENT, prec, Ly.W8, nullptr, Ly.mp, Ly.kp, net->A8, nullptr, n,
+                     Ly.kp, Ly.mp, n, Ly.kp, net->sm_count, best);
+      else
+        tc_plan_make(Ly.plan_tan, TC_TANGENT, prec, Ly.Whi, Ly.Wlo, Ly.mp, Ly.kp, net->At[cur][0],
+                     net->At[cur][1], n, Ly.kp, Ly.mp, n, Ly.kp, net->sm_count, best);
+    }
+  }
+  // symmetric product: split-K count (bounded by the partial-sum buffer allocated at load)
+  if (net->K_total > 0 && net->plan_syrk.ready) {
+    const std::string key = key_of(net, "syrk", n, n, net->K_total);
+    int best = net->plan_syrk.splits;
+    auto it = cache.find(key);
+    if (it != cache.end() && !retune && it->second.first <= net->h_splits) {
+      best = it->second.first;
+    } else {
+      double best_us = 1e30;
+      for (int sp = 1; sp <= net->h_splits; ++sp) {
+        TcPlan p;
+        if (tc_plan_make(p, TC_SYRK, prec, net->Zt[0], net->Zt[1], n, net->K_total, net->Yt[0],
+                         net->Yt[1], n, net->K_total, n, n, net->K_total, net->sm_count, 0, sp) != NNC_OK)
+          continue;
+        if (p.splits != sp) continue;
+        const double us = time_us(st, 3, [&] {
+          cudaMemsetAsync(net->Hp, 0, sizeof(float) * (size_t)net->h_splits * n * n, st);
+          tc_syrk(p, (float*)net->Hp, net->dev_err, st);
+        });
+        if (us < best_us) {
+          best_us = us;
+          best = sp;
+        }
+      }
+      cache[key] = {best, best_us};
+    }
+    if (best != net->plan_syrk.splits)
+      tc_plan_make(net->plan_syrk, TC_SYRK, prec, net->Zt[0], net->Zt[1], n, net->K_total, net->Yt[0],
+                   net->Yt[1], n, net->K_total, n, n, net->K_total, net->sm_count, 0, best);
+  }
+  cudaStreamSynchronize(st);
+  int e = 0;
+  cudaMemcpy(&e, net->dev_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e) {
+    int z = 0;
+    cudaMemcpy(net->dev_err, &z, sizeof(int), cudaMemcpyHostToDevice);
+    set_last_error("autotune: a bounded device-side wait ran out");
+    return NNC_ERR_TIMEOUT;
+  }
+  write_cache(cache_path, cache);
+  return cudaGetLastError() == cudaSuccess ? NNC_OK : NNC_ERR_CUDA;
+}
+
+extern "C" int nnc_tuning(const nnc_net* net, int layer, int* tangent_bn, int* syrk_splits) {
+  if (!net || layer < 0 || layer >= net->L) {
+    set_last_error("bad arguments");
+    return NNC_ERR_ARG;
+  }
+  if (tangent_bn) *tangent_bn = net->layers[layer].plan_tan.ready ? net->layers[layer].plan_tan.bn : 0;
+  if (syrk_splits) *syrk_splits = net->plan_syrk.ready ? net->plan_syrk.splits : net->h_splits;
+  return NNC_OK;
+}

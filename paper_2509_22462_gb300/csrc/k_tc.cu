@@ -25,7 +25,6 @@ namespace nnc {
 namespace {
 
 constexpr int BM = 128;
-constexpr int BK = 64;
 constexpr int kThreads = 192;
 constexpr long long kWaitCycles = 4000000000LL;  // about two seconds at GB300 clocks
 
@@ -39,6 +38,8 @@ struct TcArgs {
   int ldz;   // row stride of zt_* / yt_*
   float* Hp;
   int* err;
+  const float* wscale;   // FP8: per-row scale of W_l
+  const float* tscale;   // FP8: per-row scale of the tangent operand
   // grouped modes: group g owns A rows [g * a_group_rows, ...) (tangent) and B / output rows
   // starting at g_boff[g]; g_n[g] valid columns; syrk: tile list `work` and H_g at g_hoff[g]
   const int* g_n;
@@ -49,21 +50,37 @@ struct TcArgs {
   long long ldh_split;
 };
 
-template <int BN, bool X3>
+// K-block of one pipeline stage, in elements: 64 (one 128-byte swizzled row) for single BF16; 32
+// (64-byte swizzle) for split-BF16x3, whose stages carry four operand tiles, so that five stages
+// fit in shared memory instead of two.
+// The FP8 form (kind::f8f6f4, e4m3 operands) uses 128-element (128-byte) K blocks.
+enum { MODE_BF16 = 0, MODE_BF16X3 = 1, MODE_FP8 = 2 };
+constexpr int bk_for(int mode) { return mode == MODE_BF16X3 ? 32 : mode == MODE_FP8 ? 128 : 64; }
+
+template <int BN, int MODE>
 struct Cfg {
-  static constexpr int A_BYTES = BM * BK * 2;
-  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr bool X3 = MODE == MODE_BF16X3;
+  static constexpr bool F8 = MODE == MODE_FP8;
+  static constexpr int EB = F8 ? 1 : 2;                // bytes per element
+  static constexpr int BKE = bk_for(MODE);
+  static constexpr int ROWB = BKE * EB;                // bytes of one K-block row
+  static constexpr int SWZ = ROWB == 128 ? 2 : 4;      // descriptor layout: SWIZZLE_128B / 64B
+  static constexpr int SBO = 8 * ROWB;                 // bytes between 8-row core-matrix groups
+  static constexpr int A_BYTES = BM * ROWB;
+  static constexpr int B_BYTES = BN * ROWB;
   static constexpr int NPARTS = X3 ? 2 : 1;
   static constexpr int STAGE_BYTES = NPARTS * (A_BYTES + B_BYTES);
   static constexpr int TX_BYTES = STAGE_BYTES;
   static constexpr int SMEM_BUDGET = 227 * 1024 - 2048;
   static constexpr int STAGES_FIT = SMEM_BUDGET / STAGE_BYTES;
-  static constexpr int STAGES = STAGES_FIT > 6 ? 6 : STAGES_FIT;
+  static constexpr int STAGES = STAGES_FIT > 8 ? 8 : STAGES_FIT;
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
   static constexpr int TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
   // Instruction descriptor of tcgen05.mma kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
   // (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17, M >> 4 at bit 24.
-  static constexpr uint32_t IDESC_NO_N = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BM >> 4) << 24);
+  // kind::f16: A = B = BF16 (1 at bits 7-9 and 10-12); kind::f8f6f4: A = B = E4M3 (0).
+  static constexpr uint32_t IDESC_NO_N =
+      (1u << 4) | (F8 ? 0u : (1u << 7) | (1u << 10)) | ((uint32_t)(BM >> 4) << 24);
   static constexpr uint32_t IDESC = IDESC_NO_N | ((uint32_t)(BN >> 3) << 17);
   static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N for M = 128");
   static_assert(B_BYTES % 1024 == 0, "stage parts must stay 1024-byte aligned");
@@ -121,13 +138,15 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-// Shared-memory matrix descriptor of tcgen05 for a K-major tile written by TMA with 128-byte
-// swizzling: start address >> 4 (bits 0-13), stride between 8-row groups = 1024 bytes (>> 4 at
-// bit 32), descriptor version 1 (bit 46), layout SWIZZLE_128B (= 2 at bits 61-63).  Moving along
-// K inside the 128-byte row is done by advancing the start address (32 bytes per K = 16).
+// Shared-memory matrix descriptor of tcgen05 for a K-major tile written by TMA with 128- or
+// 64-byte swizzling: start address >> 4 (bits 0-13), stride between 8-row groups (SBO, >> 4 at
+// bit 32), descriptor version 1 (bit 46), layout SWIZZLE_128B (2) or SWIZZLE_64B (4) at bits
+// 61-63.  Moving along K inside a swizzled row is done by advancing the start address (32 bytes
+// per K = 16).
+template <int SWZ, int SBO>
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
-  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
-         (2ull << 61);
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(SBO >> 4) << 32) | (1ull << 46) |
+         ((uint64_t)SWZ << 61);
 }
 
 __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
@@ -136,6 +155,16 @@ __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t 
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_f8(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
       "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
       : "memory");
 }
@@ -179,12 +208,13 @@ __device__ __forceinline__ void put(__nv_bfloat16* hi, __nv_bfloat16* lo, size_t
   }
 }
 
-template <int BN, bool X3, int KIND>
+template <int BN, int MODE, int KIND>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
               const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
               const TcArgs args) {
-  using C = Cfg<BN, X3>;
+  using C = Cfg<BN, MODE>;
+  constexpr bool X3 = C::X3;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + C::STAGES * C::STAGE_BYTES);
@@ -211,6 +241,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     a_row0 = tm * BM;
     b_row0 = tn * BN;
     n_valid = args.N;
+  } else if (KIND == TC_REV) {
+    tm = blockIdx.x;
+    tn = 0;
+    split = blockIdx.y;
+    a_row0 = tm * BM;
+    b_row0 = 0;
+    n_valid = BN;
   } else if (KIND == TC_TANGENT_G) {
     tm = blockIdx.x;
     grp = blockIdx.y;
@@ -275,7 +312,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint8_t* st = smem + s * C::STAGE_BYTES;
         const uint32_t fb = smem_u32(&full[s]);
         mbar_expect_tx(fb, C::TX_BYTES);
-        const int kx = (kb0 + i) * BK;
+        const int kx = (kb0 + i) * C::BKE;
         tma_load_2d(smem_u32(st), &ta_hi, fb, kx, a_row0);
         if (X3) tma_load_2d(smem_u32(st + C::A_BYTES), &ta_lo, fb, kx, a_row0);
         tma_load_2d(smem_u32(st + C::NPARTS * C::A_BYTES), &tb_hi, fb, kx, b_row0);
@@ -296,12 +333,18 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t b_hi = st + C::NPARTS * C::A_BYTES;
         const uint32_t b_lo = b_hi + C::B_BYTES;
 #pragma unroll
-        for (int kk = 0; kk < BK / 16; ++kk) {
-          const uint32_t off = kk * 32;
-          umma_bf16(tmem, sdesc(a_hi + off), sdesc(b_hi + off), idesc, (i > 0 || kk > 0) ? 1u : 0u);
+        for (int kk = 0; kk < C::ROWB / 32; ++kk) {
+          const uint32_t off = kk * 32;   // one MMA consumes 32 bytes of K: 16 BF16 or 32 E4M3
+          constexpr int SW = C::SWZ, SB = C::SBO;
+          if (C::F8)
+            umma_f8(tmem, sdesc<SW, SB>(a_hi + off), sdesc<SW, SB>(b_hi + off), idesc,
+                    (i > 0 || kk > 0) ? 1u : 0u);
+          else
+            umma_bf16(tmem, sdesc<SW, SB>(a_hi + off), sdesc<SW, SB>(b_hi + off), idesc,
+                      (i > 0 || kk > 0) ? 1u : 0u);
           if (X3) {
-            umma_bf16(tmem, sdesc(a_hi + off), sdesc(b_lo + off), idesc, 1u);
-            umma_bf16(tmem, sdesc(a_lo + off), sdesc(b_hi + off), idesc, 1u);
+            umma_bf16(tmem, sdesc<SW, SB>(a_hi + off), sdesc<SW, SB>(b_lo + off), idesc, 1u);
+            umma_bf16(tmem, sdesc<SW, SB>(a_lo + off), sdesc<SW, SB>(b_hi + off), idesc, 1u);
           }
         }
         umma_commit(smem_u32(&empty[s]));
@@ -314,12 +357,25 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int row = q * 32 + lane;
     const bool ok = mbar_wait(smem_u32(accf), 0, args.err, 3, abort_flag);
     tc_fence_after();
-    if (ok) {
+    if (ok && KIND == TC_REV) {
+      // split-K partial of W_l^T Zbar: P[split][k][0..BN) for row k of this tile
+      const int k = m0 + row;
+      float* out = args.Hp + ((size_t)split * args.M + k) * BN;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+        for (int j = 0; j < 16; j += 4)
+          *reinterpret_cast<float4*>(out + c0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+      }
+    } else if (ok) {
       if (KIND == TC_TANGENT || KIND == TC_TANGENT_G) {
         const int m = m0 + row;                        // row of W_l inside the group
         const int ms = (KIND == TC_TANGENT_G ? grp * args.a_group_rows : 0) + m;
         const float sm = (float)args.s1[ms];
         const float cm = args.c[ms];
+        const float wsc = C::F8 ? args.wscale[ms] : 1.f;   // FP8: per-row weight scale
 #pragma unroll 1
         for (int c0 = 0; c0 < n_eff; c0 += 16) {
           float v[16];
@@ -327,6 +383,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int n = n0 + c0 + j;
+            if (C::F8 && n < n_valid) v[j] *= wsc * args.tscale[n];   // undo both FP8 scalings
             if (n < n_valid) {
               const size_t orow = (size_t)(KIND == TC_TANGENT_G ? b_row0 + n : n);
               if (args.at_hi) put<X3>(args.at_hi, args.at_lo, orow * args.ldo + m, sm * v[j]);
@@ -400,8 +457,9 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 }
 
 // 2-D BF16 map: inner extent `cols` (K, contiguous), outer extent `rows`, row stride ld
-// elements, box 64 x box_rows, 128-byte swizzle, zero fill outside.
-bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int ld, int box_rows) {
+// elements, box bk x box_rows with 128-byte (bk = 64) or 64-byte (bk = 32) swizzle, zero fill.
+bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int ld, int box_rows, int bk,
+              int eb = 2) {
   if (!base) {
     memset(m, 0, sizeof(*m));
     return true;
@@ -409,38 +467,53 @@ bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int ld, int 
   auto enc = get_encode();
   if (!enc) return false;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * eb};
+  cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
-  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,
-                   box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+  CUresult r = enc(m, eb == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                   const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   bk * eb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
-template <int BN, bool X3, int KIND>
+template <int BN, int MODE, int KIND>
 cudaError_t launch_t(const TcPlan& p, const TcArgs& a, dim3 grid, cudaStream_t st) {
-  using C = Cfg<BN, X3>;
+  using C = Cfg<BN, MODE>;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<BN, X3, KIND>,
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<BN, MODE, KIND>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_tc_gemm<BN, X3, KIND><<<grid, kThreads, C::SMEM, st>>>(p.ta_hi, p.ta_lo, p.tb_hi, p.tb_lo, a);
+  k_tc_gemm<BN, MODE, KIND><<<grid, kThreads, C::SMEM, st>>>(p.ta_hi, p.ta_lo, p.tb_hi, p.tb_lo, a);
   note_launch();
   return cudaGetLastError();
 }
 
+template <int KIND, int BN>
+cudaError_t launch_mode(const TcPlan& p, const TcArgs& a, dim3 grid, cudaStream_t st) {
+  if (p.mode == MODE_BF16X3) return launch_t<BN, MODE_BF16X3, KIND>(p, a, grid, st);
+  if (p.mode == MODE_FP8) {
+    if constexpr (KIND == TC_TANGENT) return launch_t<BN, MODE_FP8, KIND>(p, a, grid, st);
+    return cudaErrorInvalidValue;
+  }
+  return launch_t<BN, MODE_BF16, KIND>(p, a, grid, st);
+}
+
 template <int KIND>
 cudaError_t launch_any(const TcPlan& p, const TcArgs& a, dim3 grid, cudaStream_t st) {
-  const bool x3 = p.x3 != 0;
+  if constexpr (KIND == TC_REV) {
+    if (p.bn == 16) return launch_t<16, MODE_BF16X3, KIND>(p, a, grid, st);
+    if (p.bn == 48) return launch_t<48, MODE_BF16X3, KIND>(p, a, grid, st);
+    return cudaErrorInvalidValue;
+  }
   switch (p.bn) {
-    case 112: return x3 ? launch_t<112, true, KIND>(p, a, grid, st) : launch_t<112, false, KIND>(p, a, grid, st);
-    case 128: return x3 ? launch_t<128, true, KIND>(p, a, grid, st) : launch_t<128, false, KIND>(p, a, grid, st);
-    case 208: return x3 ? launch_t<208, true, KIND>(p, a, grid, st) : launch_t<208, false, KIND>(p, a, grid, st);
-    case 256: return x3 ? launch_t<256, true, KIND>(p, a, grid, st) : launch_t<256, false, KIND>(p, a, grid, st);
+    case 112: return launch_mode<KIND, 112>(p, a, grid, st);
+    case 128: return launch_mode<KIND, 128>(p, a, grid, st);
+    case 208: return launch_mode<KIND, 208>(p, a, grid, st);
+    case 256: return launch_mode<KIND, 256>(p, a, grid, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -460,14 +533,29 @@ int tc_plan_make(TcPlan& p, int kind, int prec, const void* a_hi, const void* a_
                  int K, int sm_count, int force_bn, int force_splits) {
   p = TcPlan();
   p.kind = kind;
-  p.x3 = prec == NNC_BF16X3 ? 1 : 0;
+  p.x3 = (prec == NNC_BF16X3 || kind == TC_REV) ? 1 : 0;
   p.M = M;
   p.N = N;
   p.K = K;
-  if (K % BK != 0 || K <= 0 || N <= 0 || M <= 0) return NNC_ERR_ARG;
+  p.mode = (prec == NNC_BF16X3 || kind == TC_REV) ? MODE_BF16X3
+           : (prec == NNC_FP8 && kind == TC_TANGENT) ? MODE_FP8 : MODE_BF16;
+  p.bk = bk_for(p.mode);
+  const int eb = p.mode == MODE_FP8 ? 1 : 2;
+  if (K % 64 != 0 || K <= 0 || N <= 0 || M <= 0) return NNC_ERR_ARG;
   if ((kind == TC_TANGENT || kind == TC_TANGENT_G) && M % BM != 0) return NNC_ERR_ARG;
-  const int nkb = K / BK;
-  if (kind == TC_TANGENT_G || kind == TC_SYRK_G) {
+  const int nkb = K / p.bk;
+  if (kind == TC_REV) {
+    // reverse sweep: M = columns of W_l (rows of W_l^T), N = seed columns (16 or 48), split-K over
+    // the rows of W_l so that about one CTA per SM runs
+    if (N > 48) return NNC_ERR_UNSUPPORTED;
+    p.bn = N <= 16 ? 16 : 48;
+    p.ntm = M / BM;
+    p.ntn = 1;
+    int splits = force_splits ? force_splits : std::max(1, sm_count / std::max(1, p.ntm));
+    splits = std::min(splits, nkb);
+    p.kb_per_split = (nkb + splits - 1) / splits;
+    p.splits = (nkb + p.kb_per_split - 1) / p.kb_per_split;
+  } else if (kind == TC_TANGENT_G || kind == TC_SYRK_G) {
     // grouped: N is the widest group's column count (rounded to 16); the MMA N of each CTA is
     // chosen at run time from its group's width.
     int bn = (N + 15) / 16 * 16;
@@ -518,18 +606,18 @@ int tc_plan_make(TcPlan& p, int kind, int prec, const void* a_hi, const void* a_
     p.splits = (nkb + p.kb_per_split - 1) / p.kb_per_split;
   }
   const int a_box = BM;
-  const int b_box = p.bn;
-  if (!make_map(&p.ta_hi, a_hi, a_rows, K, ld_a, a_box)) return NNC_ERR_CUDA;
-  if (!make_map(&p.ta_lo, p.x3 ? a_lo : nullptr, a_rows, K, ld_a, a_box)) return NNC_ERR_CUDA;
-  if (!make_map(&p.tb_hi, b_hi, b_rows, K, ld_b, b_box)) return NNC_ERR_CUDA;
-  if (!make_map(&p.tb_lo, p.x3 ? b_lo : nullptr, b_rows, K, ld_b, b_box)) return NNC_ERR_CUDA;
+  const int b_box = p.bn;   // REV: the seed rows of B beyond the plan's N read as zero
+  if (!make_map(&p.ta_hi, a_hi, a_rows, K, ld_a, a_box, p.bk, eb)) return NNC_ERR_CUDA;
+  if (!make_map(&p.ta_lo, p.x3 ? a_lo : nullptr, a_rows, K, ld_a, a_box, p.bk, eb)) return NNC_ERR_CUDA;
+  if (!make_map(&p.tb_hi, b_hi, b_rows, K, ld_b, b_box, p.bk, eb)) return NNC_ERR_CUDA;
+  if (!make_map(&p.tb_lo, p.x3 ? b_lo : nullptr, b_rows, K, ld_b, b_box, p.bk, eb)) return NNC_ERR_CUDA;
   p.ready = true;
   return NNC_OK;
 }
 
 cudaError_t tc_tangent(const TcPlan& p, const double* s1, const float* c, void* at_hi, void* at_lo,
                        int ldo, void* zt_hi, void* zt_lo, void* yt_hi, void* yt_lo, int ldz,
-                       int* err, cudaStream_t st) {
+                       int* err, cudaStream_t st, const float* wscale, const float* tscale) {
   if (!p.ready || p.kind != TC_TANGENT) return cudaErrorInvalidValue;
   TcArgs a{};
   a.M = p.M;
@@ -537,7 +625,7 @@ cudaError_t tc_tangent(const TcPlan& p, const double* s1, const float* c, void* 
   a.K = p.K;
   a.ntm = p.ntm;
   a.ntn = p.ntn;
-  a.nkb = p.K / BK;
+  a.nkb = p.K / p.bk;
   a.kb_per_split = p.kb_per_split;
   a.s1 = s1;
   a.c = c;
@@ -550,6 +638,8 @@ cudaError_t tc_tangent(const TcPlan& p, const double* s1, const float* c, void* 
   a.ldo = ldo;
   a.ldz = ldz;
   a.err = err;
+  a.wscale = wscale;
+  a.tscale = tscale;
   return launch_any<TC_TANGENT>(p, a, dim3(p.ntn, p.ntm, 1), st);
 }
 
@@ -564,7 +654,7 @@ cudaError_t tc_tangent_grouped(const TcPlan& p, int groups, const int* g_n, cons
   a.K = p.K;
   a.ntm = p.ntm;
   a.ntn = 1;
-  a.nkb = p.K / BK;
+  a.nkb = p.K / p.bk;
   a.kb_per_split = a.nkb;
   a.s1 = s1;
   a.c = c;
@@ -589,7 +679,7 @@ cudaError_t tc_syrk_grouped(const TcPlan& p, int n_tiles, const int4* work, cons
   if (!p.ready || p.kind != TC_SYRK_G) return cudaErrorInvalidValue;
   TcArgs a{};
   a.K = p.K;
-  a.nkb = p.K / BK;
+  a.nkb = p.K / p.bk;
   a.kb_per_split = p.kb_per_split;
   a.Hp = Hp;
   a.err = err;
@@ -601,6 +691,21 @@ cudaError_t tc_syrk_grouped(const TcPlan& p, int n_tiles, const int4* work, cons
   return launch_any<TC_SYRK_G>(p, a, dim3(n_tiles, p.splits, 1), st);
 }
 
+cudaError_t tc_rev(const TcPlan& p, float* part, int* err, cudaStream_t st) {
+  if (!p.ready || p.kind != TC_REV) return cudaErrorInvalidValue;
+  TcArgs a{};
+  a.M = p.M;
+  a.N = p.N;
+  a.K = p.K;
+  a.ntm = p.ntm;
+  a.ntn = 1;
+  a.nkb = p.K / p.bk;
+  a.kb_per_split = p.kb_per_split;
+  a.Hp = part;
+  a.err = err;
+  return launch_any<TC_REV>(p, a, dim3(p.ntm, p.splits, 1), st);
+}
+
 cudaError_t tc_syrk(const TcPlan& p, float* Hp, int* err, cudaStream_t st) {
   if (!p.ready || p.kind != TC_SYRK) return cudaErrorInvalidValue;
   TcArgs a{};
@@ -609,7 +714,7 @@ cudaError_t tc_syrk(const TcPlan& p, float* Hp, int* err, cudaStream_t st) {
   a.K = p.K;
   a.ntm = p.ntm;
   a.ntn = p.ntn;
-  a.nkb = p.K / BK;
+  a.nkb = p.K / p.bk;
   a.kb_per_split = p.kb_per_split;
   a.Hp = Hp;
   a.err = err;

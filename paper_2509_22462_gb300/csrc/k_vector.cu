@@ -433,3 +433,175 @@ cudaError_t launch_pack(const double* w64, size_t n, float* w32, __nv_bfloat16* 
 }
 
 }  // namespace nnc
+
+#include <cuda_fp8.h>
+
+namespace nnc {
+
+// ------------------------------------------------------------------ FP8 e4m3 packing
+// Per output row r: s_r = max_k |W[r][k]| / 448 (448 = largest finite e4m3), W8 = e4m3(W / s_r).
+// One block per row.
+__global__ void k_pack_fp8_rows(const double* __restrict__ W, int ld, int cols,
+                                unsigned char* __restrict__ W8, float* __restrict__ scale) {
+  __shared__ float red[256];
+  const int r = blockIdx.x;
+  const double* w = W + (size_t)r * ld;
+  float mx = 0.f;
+  for (int k = threadIdx.x; k < cols; k += blockDim.x) mx = fmaxf(mx, fabsf((float)w[k]));
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  const float s = red[0] > 0.f ? red[0] / 448.f : 1.f;
+  if (threadIdx.x == 0) scale[r] = s;
+  const float inv = 1.f / s;
+  for (int k = threadIdx.x; k < ld; k += blockDim.x)
+    W8[(size_t)r * ld + k] = k < cols ? (unsigned char)__nv_cvt_float_to_fp8((float)w[k] * inv, __NV_SATFINITE, __NV_E4M3) : 0;
+}
+
+cudaError_t launch_pack_fp8(const double* W, int rows, int ld, int cols, unsigned char* W8,
+                            float* scale, cudaStream_t st) {
+  k_pack_fp8_rows<<<rows, 256, 0, st>>>(W, ld, cols, W8, scale);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// Tangent rows to e4m3: for row n of A (BF16, n_rows x ld), t_n = max |A[n][:]| / 448 and
+// A8[n][k] = e4m3(A[n][k] / t_n).
+__global__ void k_quant_fp8_rows(const __nv_bfloat16* __restrict__ A, int ld,
+                                 unsigned char* __restrict__ A8, float* __restrict__ t) {
+  __shared__ float red[256];
+  const int r = blockIdx.x;
+  const __nv_bfloat16* a = A + (size_t)r * ld;
+  float mx = 0.f;
+  for (int k = threadIdx.x; k < ld; k += blockDim.x) mx = fmaxf(mx, fabsf(__bfloat162float(a[k])));
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  const float s = red[0] > 0.f ? red[0] / 448.f : 1.f;
+  if (threadIdx.x == 0) t[r] = s;
+  const float inv = 1.f / s;
+  for (int k = threadIdx.x; k < ld; k += blockDim.x)
+    A8[(size_t)r * ld + k] = (unsigned char)__nv_cvt_float_to_fp8(__bfloat162float(a[k]) * inv, __NV_SATFINITE, __NV_E4M3);
+}
+
+cudaError_t launch_quant_fp8(const void* A, int rows, int ld, unsigned char* A8, float* t,
+                             cudaStream_t st) {
+  k_quant_fp8_rows<<<rows, 256, 0, st>>>((const __nv_bfloat16*)A, ld, A8, t);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace nnc
+
+namespace nnc {
+
+// ------------------------------------------------------------------ tensor-core reverse sweep
+// W_l^T packed as BF16 hi/lo (Wt[k][m] = W[m][k], K-major for the reverse GEMM; [kp][mp]).
+__global__ void k_pack_t(const double* __restrict__ W, int mp, int kp, __nv_bfloat16* __restrict__ hi,
+                         __nv_bfloat16* __restrict__ lo) {
+  __shared__ double tile[32][33];
+  const int m0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int m = m0 + r, k = k0 + threadIdx.x;
+    tile[r][threadIdx.x] = (m < mp && k < kp) ? W[(size_t)m * kp + k] : 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int k = k0 + r, m = m0 + threadIdx.x;
+    if (k < kp && m < mp) {
+      __nv_bfloat16 h, l;
+      split_bf16(tile[threadIdx.x][r], h, l);
+      hi[(size_t)k * mp + m] = h;
+      lo[(size_t)k * mp + m] = l;
+    }
+  }
+}
+
+cudaError_t launch_pack_t(const double* W, int mp, int kp, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                          cudaStream_t st) {
+  dim3 grid((kp + 31) / 32, (mp + 31) / 32), block(32, 8);
+  k_pack_t<<<grid, block, 0, st>>>(W, mp, kp, hi, lo);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// Output-layer seeds, transposed for the reverse GEMM: Zb[s][i] = s1[i] * abar_L[i][s] as BF16
+// hi/lo (row stride ld), abar_L = e_s (s < nJ) or lambda (s = lam_col); c_L = s2 * lambda.
+__global__ void k_rev_seed_t(int m, int S, int nJ, int lam_col, const double* __restrict__ s1,
+                             const double* __restrict__ s2, const double* __restrict__ lam,
+                             __nv_bfloat16* __restrict__ zhi, __nv_bfloat16* __restrict__ zlo, int ld,
+                             double* __restrict__ c_out, float* __restrict__ c_f) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * S) return;
+  const int i = idx / S, s = idx % S;
+  double ab = 0.0;
+  if (s == lam_col) ab = lam[i];
+  else if (s < nJ) ab = (s == i) ? 1.0 : 0.0;
+  __nv_bfloat16 h, l;
+  split_bf16(s1[i] * ab, h, l);
+  zhi[(size_t)s * ld + i] = h;
+  zlo[(size_t)s * ld + i] = l;
+  if (s == lam_col) {
+    if (c_out) c_out[i] = s2[i] * ab;
+    if (c_f) c_f[i] = (float)(s2[i] * ab);
+  }
+}
+
+cudaError_t launch_rev_seed_t(int m, int S, int nJ, int lam_col, const double* s1, const double* s2,
+                              const double* lam, void* zhi, void* zlo, int ld, double* c_out,
+                              float* c_f, cudaStream_t st) {
+  k_rev_seed_t<<<(m * S + 255) / 256, 256, 0, st>>>(m, S, nJ, lam_col, s1, s2, lam,
+                                                    (__nv_bfloat16*)zhi, (__nv_bfloat16*)zlo, ld,
+                                                    c_out, c_f);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// Sum the split partials P[sp][k][0..bn) of W_l^T Zbar; then either the next seeds (transposed,
+// BF16 hi/lo: Zb[s][k] = s1[k] * Abar[k][s]) and c = s2 * Abar[:, lam_col], or, on the first
+// layer, J_out[s][k] (s < nJ) and g_out[k] (s = lam_col) for k < kvalid.
+__global__ void k_rev_reduce_t(const float* __restrict__ P, int splits, int kcols, int bn, int S,
+                               int kvalid, const double* __restrict__ s1,
+                               const double* __restrict__ s2, int lam_col, int nJ,
+                               __nv_bfloat16* __restrict__ zhi, __nv_bfloat16* __restrict__ zlo,
+                               int ld, double* __restrict__ c_out, float* __restrict__ c_f,
+                               double* __restrict__ J_out, double* __restrict__ g_out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= kcols * S) return;
+  const int k = idx / S, s = idx % S;
+  double v = 0.0;
+  for (int sp = 0; sp < splits; ++sp) v += (double)P[((size_t)sp * kcols + k) * bn + s];
+  if (s1) {
+    __nv_bfloat16 h, l;
+    split_bf16(s1[k] * v, h, l);
+    zhi[(size_t)s * ld + k] = h;
+    zlo[(size_t)s * ld + k] = l;
+    if (s == lam_col) {
+      if (c_out) c_out[k] = s2[k] * v;
+      if (c_f) c_f[k] = (float)(s2[k] * v);
+    }
+  } else if (k < kvalid) {
+    if (J_out && s < nJ) J_out[(size_t)s * kvalid + k] = v;
+    if (g_out && s == lam_col) g_out[k] = v;
+  }
+}
+
+cudaError_t launch_rev_reduce_t(const float* P, int splits, int kcols, int bn, int S, int kvalid,
+                                const double* s1, const double* s2, int lam_col, int nJ, void* zhi,
+                                void* zlo, int ld, double* c_out, float* c_f, double* J_out,
+                                double* g_out, cudaStream_t st) {
+  k_rev_reduce_t<<<(kcols * S + 255) / 256, 256, 0, st>>>(P, splits, kcols, bn, S, kvalid, s1, s2,
+                                                          lam_col, nJ, (__nv_bfloat16*)zhi,
+                                                          (__nv_bfloat16*)zlo, ld, c_out, c_f, J_out,
+                                                          g_out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace nnc

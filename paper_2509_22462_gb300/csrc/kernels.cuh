@@ -68,3 +68,25 @@ namespace nnc {
 cudaError_t launch_pack(const double* w64, size_t n, float* w32, __nv_bfloat16* whi,
                         __nv_bfloat16* wlo, cudaStream_t st);
 }  // namespace nnc
+
+namespace nnc {
+// FP8 e4m3 with per-row scales (the FP8 form): W8[r][:] = e4m3(W[r][:] / s_r), s_r = max|W_r|/448.
+cudaError_t launch_pack_fp8(const double* W, int rows, int ld, int cols, unsigned char* W8,
+                            float* scale, cudaStream_t st);
+// BF16 tangent rows to e4m3 with per-row scales t_n.
+cudaError_t launch_quant_fp8(const void* A, int rows, int ld, unsigned char* A8, float* t,
+                             cudaStream_t st);
+}  // namespace nnc
+
+namespace nnc {
+// Tensor-core reverse sweep helpers (see k_vector.cu).
+cudaError_t launch_pack_t(const double* W, int mp, int kp, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                          cudaStream_t st);
+cudaError_t launch_rev_seed_t(int m, int S, int nJ, int lam_col, const double* s1, const double* s2,
+                              const double* lam, void* zhi, void* zlo, int ld, double* c_out,
+                              float* c_f, cudaStream_t st);
+cudaError_t launch_rev_reduce_t(const float* P, int splits, int kcols, int bn, int S, int kvalid,
+                                const double* s1, const double* s2, int lam_col, int nJ, void* zhi,
+                                void* zlo, int ld, double* c_out, float* c_f, double* J_out,
+                                double* g_out, cudaStream_t st);
+}  // namespace nnc

@@ -22,6 +22,8 @@ struct LayerDev {
   float* W32 = nullptr;           // [mp][kp]
   __nv_bfloat16* Whi = nullptr;   // [mp][kp]
   __nv_bfloat16* Wlo = nullptr;   // [mp][kp]
+  unsigned char* W8 = nullptr;    // [mp][kp] e4m3 (FP8 form)
+  float* w8s = nullptr;           // [mp] per-row scale of W8
   double* b = nullptr;            // [mp]
   double* a = nullptr;            // a_l [mp]
   double* s1 = nullptr;           // sigma_l'(z_l) [mp]
@@ -56,6 +58,8 @@ struct nnc_net {
   void* Zt[2] = {nullptr, nullptr};  // [hi, lo]: Zdot_l^T of all curved layers, n x K_total
   void* Yt[2] = {nullptr, nullptr};  // [hi, lo]: (c_l * Zdot_l)^T, n x K_total
   int K_total = 0;                   // sum of mp_l over layers with sigma'' != 0
+  unsigned char* A8 = nullptr;       // FP8 form: e4m3 copy of the current tangent operand
+  float* tsc = nullptr;              // FP8 form: its per-row (per-tangent) scales
   nnc::TcPlan plan_syrk;                  // tensor-core plan of the one symmetric product
   void* Hp = nullptr;        // split partial sums of H (double for CUDA-core forms, float for TC)
   int h_splits = 1;

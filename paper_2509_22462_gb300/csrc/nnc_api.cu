@@ -40,6 +40,7 @@ Elem tan_elem(int prec) {
     case NNC_FP64: return Elem::F64;
     case NNC_FP32: return Elem::F32;
     case NNC_BF16: return Elem::BF16;
+    case NNC_FP8: return Elem::BF16;
     default: return Elem::BF16X3;
   }
 }
@@ -212,12 +213,16 @@ int run_hessian(nnc_net* net, double* H, cudaStream_t st) {
     if (last && Ly.zy_off < 0) break;  // a linear output layer adds nothing to H
     void* Anext_hi = last ? nullptr : net->At[1 - cur][0];
     void* Anext_lo = last ? nullptr : net->At[1 - cur][1];
+    if (prec == NNC_FP8) {
+      PROF(PK_OTHER);
+      CK(launch_quant_fp8(net->At[cur][0], n, Ly.kp, net->A8, net->tsc, st));
+    }
     PROF(PK_TANGENT);
     if (tc) {
       CK(tc_tangent(Ly.plan_tan, Ly.s1, Ly.c_f, Anext_hi, Anext_lo, Ly.mp,
                     zoff(net->Zt[0], Ly.zy_off), zoff(net->Zt[1], Ly.zy_off),
                     zoff(net->Yt[0], Ly.zy_off), zoff(net->Yt[1], Ly.zy_off), net->K_total,
-                    net->dev_err, st));
+                    net->dev_err, st, Ly.w8s, net->tsc));
     } else {
       CK(launch_simt_tangent(prec == NNC_FP64,
                              prec == NNC_FP64 ? (const void*)Ly.W64 : (const void*)Ly.W32, Ly.kp,
@@ -404,11 +409,16 @@ static int load_impl(nnc_net* net, int n_layers, const int* widths, const int* a
     CK(cudaMemcpy2DAsync(Ly.W64, sizeof(double) * Ly.kp, W[l], sizeof(double) * Ly.k,
                          sizeof(double) * Ly.k, Ly.m, cudaMemcpyHostToDevice, net->stream));
     if (prec != NNC_FP64) AL(Ly.W32, nw);
-    if (tc && l > 0) {
+    if (tc && l > 0 && prec != NNC_FP8) {
       AL(Ly.Whi, nw);
       if (prec == NNC_BF16X3) AL(Ly.Wlo, nw);
     }
     CK(launch_pack(Ly.W64, nw, Ly.W32, Ly.Whi, Ly.Wlo, net->stream));
+    if (prec == NNC_FP8 && l > 0) {
+      AL(Ly.W8, nw);
+      AL(Ly.w8s, Ly.mp);
+      CK(launch_pack_fp8(Ly.W64, Ly.mp, Ly.kp, Ly.kp, Ly.W8, Ly.w8s, net->stream));
+    }
     AL(Ly.b, Ly.mp);
     if (b && b[l])
       CK(cudaMemcpyAsync(Ly.b, b[l], sizeof(double) * Ly.m, cudaMemcpyHostToDevice, net->stream));
@@ -462,15 +472,22 @@ static int load_impl(nnc_net* net, int n_layers, const int* widths, const int* a
     AL(p, zy_elems * es);
     net->Yt[part] = p;
   }
+  if (prec == NNC_FP8) {
+    AL(net->A8, tan_elems);
+    AL(net->tsc, n);
+  }
   // split-K partial sums of H
   if (tc) {
     net->hp_f32 = true;
     for (int l = 1; l < n_layers; ++l) {
       LayerDev& Ly = net->layers[l];
       const int cur = (l - 1) % 2;
-      int r = tc_plan_make(Ly.plan_tan, TC_TANGENT, prec, Ly.Whi, Ly.Wlo, Ly.mp, Ly.kp,
-                           net->At[cur][0], net->At[cur][1], n, Ly.kp, Ly.mp, n, Ly.kp,
-                           net->sm_count);
+      int r = prec == NNC_FP8
+                  ? tc_plan_make(Ly.plan_tan, TC_TANGENT, prec, Ly.W8, nullptr, Ly.mp, Ly.kp, net->A8,
+                                 nullptr, n, Ly.kp, Ly.mp, n, Ly.kp, net->sm_count)
+                  : tc_plan_make(Ly.plan_tan, TC_TANGENT, prec, Ly.Whi, Ly.Wlo, Ly.mp, Ly.kp,
+                                 net->At[cur][0], net->At[cur][1], n, Ly.kp, Ly.mp, n, Ly.kp,
+                                 net->sm_count);
       if (r != NNC_OK) return fail(r, "tensor-core tangent plan failed");
     }
     int splits = 1;
@@ -515,7 +532,6 @@ int nnc_load_weights(nnc_net** out, int n_layers, const int* widths, const int* 
     if (!W[l]) return fail(NNC_ERR_ARG, "W[l] is NULL");
   }
   if (prec < NNC_FP64 || prec > NNC_FP8) return fail(NNC_ERR_ARG, "bad precision code");
-  if (prec == NNC_FP8) return fail(NNC_ERR_UNSUPPORTED, "the FP8 form is not built yet");
   nnc_net* net = new nnc_net();
   net->prec = prec;
   if (stream) {

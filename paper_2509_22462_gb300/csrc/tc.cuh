@@ -15,7 +15,7 @@
 
 namespace nnc {
 
-enum { TC_TANGENT = 0, TC_SYRK = 1, TC_TANGENT_G = 2, TC_SYRK_G = 3 };
+enum { TC_TANGENT = 0, TC_SYRK = 1, TC_TANGENT_G = 2, TC_SYRK_G = 3, TC_REV = 4 };
 
 struct TcPlan {
   CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;
@@ -23,6 +23,8 @@ struct TcPlan {
   int x3 = 0;           // split-BF16x3 products
   int M = 0, N = 0, K = 0;  // M: rows of A (multiple of 128), N: valid rows of B, K: multiple of 64
   int bn = 0;           // N tile
+  int bk = 64;          // K block (elements) of a pipeline stage
+  int mode = 0;         // 0 BF16, 1 split-BF16x3, 2 FP8 e4m3 (tangent GEMM only)
   int ntm = 0, ntn = 0; // tiles along M and N
   int splits = 1, kb_per_split = 0;
   bool ready = false;
@@ -37,9 +39,16 @@ int tc_plan_make(TcPlan& p, int kind, int prec, const void* a_hi, const void* a_
 
 // at_* (row stride ldo) may be NULL on the last layer; zt_* / yt_* (row stride ldz) may be NULL
 // for a layer without curvature.
+// FP8 plans: A = W8 (e4m3, per-row scales wscale), B = tangents in e4m3 with per-row scales
+// tscale; the outputs are BF16.
 cudaError_t tc_tangent(const TcPlan& p, const double* s1, const float* c, void* at_hi, void* at_lo,
                        int ldo, void* zt_hi, void* zt_lo, void* yt_hi, void* yt_lo, int ldz,
-                       int* err, cudaStream_t st);
+                       int* err, cudaStream_t st, const float* wscale = nullptr,
+                       const float* tscale = nullptr);
+
+// Reverse sweep W_l^T Zbar with split-BF16x3 operands: A = W_l^T (hi/lo, kp x mp, K-major),
+// B = Zbar^T (hi/lo, seeds x mp); writes part[split][k][0..bn) (FP32, bn = 16 or 48).
+cudaError_t tc_rev(const TcPlan& p, float* part, int* err, cudaStream_t st);
 
 // Hp: splits x N x N floats (row stride N); partial sums of the lower triangle are added.
 cudaError_t tc_syrk(const TcPlan& p, float* Hp, int* err, cudaStream_t st);

@@ -30,7 +30,7 @@ EXPORTS = ["nnc_load_weights", "nnc_eval", "nnc_residual", "nnc_jacobian", "nnc_
            "nnc_batch_set_bias", "nnc_batch_use_graph", "nnc_batch_eval_dev", "nnc_batch_residual_dev",
            "nnc_batch_eval", "nnc_batch_residual", "nnc_ipm_scopf", "nnc_ws_create", "nnc_ws_free",
            "nnc_ws_set_scaling", "nnc_ws_loss_grad", "nnc_ws_adam_step", "nnc_ws_train",
-           "nnc_ws_predict", "nnc_ws_get_params", "nnc_ipm_scopf_warm"]
+           "nnc_ws_predict", "nnc_ws_get_params", "nnc_ipm_scopf_warm", "nnc_autotune", "nnc_tuning"]
 IPM_STATUS = {0: "optimal", 1: "max_iter", 2: "linesearch_failed", 3: "nonfinite",
               4: "inertia_failed", 5: "eval_error"}
 
@@ -121,6 +121,8 @@ def load_library(path: str = LIB_PATH):
     lib.nnc_ipm_scopf.argtypes = [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                   ctypes.POINTER(ctypes.c_int), _DP, ctypes.c_double, _DP,
                                   ctypes.POINTER(IpmOptions), _DP, _DP, ctypes.POINTER(IpmResult)]
+    lib.nnc_autotune.argtypes = [_P, ctypes.c_char_p, ctypes.c_int]
+    lib.nnc_tuning.argtypes = [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.nnc_ipm_scopf_warm.argtypes = [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_int), _DP, ctypes.c_double, _DP, _DP, _DP,
                                        ctypes.POINTER(IpmOptions), _DP, _DP, ctypes.POINTER(IpmResult)]
@@ -255,6 +257,15 @@ class Net:
         _check(_lib.nnc_hessian_lag(self._h, _dp(x), _dp(lam), _dp(H),
                                     _dp(g) if want_grad else None))
         return (H, g) if want_grad else H
+
+    def autotune(self, cache_path=None, retune=False):
+        """nnc_autotune: time the tile / split candidates and keep the fastest (JSON cache optional)."""
+        _check(_lib.nnc_autotune(self._h, cache_path.encode() if cache_path else None, int(bool(retune))))
+
+    def tuning(self, layer):
+        bn, sp = ctypes.c_int(), ctypes.c_int()
+        _check(_lib.nnc_tuning(self._h, int(layer), ctypes.byref(bn), ctypes.byref(sp)))
+        return bn.value, sp.value
 
     def profile(self, enable=True):
         _check(_lib.nnc_profile(self._h, int(bool(enable))))

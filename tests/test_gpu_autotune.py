@@ -1,0 +1,40 @@
+"""The autotuner picks among valid configurations only: results stay the same (tangent tiles do
+not change any sum; split-K changes only the FP32 summation order of the symmetric product), and
+its JSON cache is written and reused."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from synth.nets import MLPSpec, make_mlp
+
+pytestmark = pytest.mark.gpu
+
+
+def test_autotune_keeps_results_and_caches(tmp_path):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_22462_gb300 import build, nnc
+    build.build()
+    mlp = make_mlp(MLPSpec([784, 1024, 1024, 1024, 10], ["tanh", "tanh", "tanh", "identity"]), seed=2)
+    d = synth.adversarial_data(seed=1)
+    net = nnc.Net.from_mlp(mlp, precision="bf16x3")
+    H0 = net.hessian_lag(d.x0, d.lam)
+    path = str(tmp_path / "tune.json")
+    net.autotune(path)
+    choices = [net.tuning(l) for l in range(4)]
+    print("[autotune] (tangent N tile, symmetric-product splits) per layer:", choices)
+    H1 = net.hessian_lag(d.x0, d.lam)
+    assert np.linalg.norm(H1 - H0) <= 1e-6 * np.linalg.norm(H0)
+    cache = json.load(open(path))
+    assert any(k.startswith("sm10") and "tangent" in k for k in cache)
+    assert any("syrk" in k for k in cache)
+    net2 = nnc.Net.from_mlp(mlp, precision="bf16x3")
+    net2.autotune(path)                       # served from the cache
+    assert [net2.tuning(l) for l in range(4)] == choices
+    assert os.path.getsize(path) > 0
+    net.free()
+    net2.free()

@@ -19,6 +19,8 @@ TOL = {
     "fp32": dict(y=1e-6, J=1e-3, H=1e-2),
     "bf16x3": dict(y=1e-6, J=1e-3, H=1e-2),
     "bf16": dict(y=1e-6, J=1e-3, H=1e-2),
+    # FP8 e4m3 tangents and weights: errors are reported; the bound only catches a broken kernel
+    "fp8": dict(y=1e-6, J=1e-3, H=0.3),
 }
 
 
@@ -58,7 +60,7 @@ def _check_all(nnc, mlp, x, lam, prec, label=""):
     return e
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3", "bf16"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3", "bf16", "fp8"])
 def test_tiny_mnist_shape(lib, prec):
     """784 -> 128 -> 128 -> 10 tanh (seed 0), x0 ~ U[0,1]^784, lambda ~ N(0,1)."""
     mlp = make_mlp(synth.TINY, seed=0)
@@ -125,7 +127,7 @@ def test_device_pointer_calls_match_host_calls(lib):
         net.free()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3", "bf16", "fp8"])
 def test_full_size_104m_sampled(lib, prec):
     """The ~104M-parameter net (784 -> 4096 x 7 -> 10 tanh) in the launch configuration the
     bench times: full value and Jacobian, and sampled Hessian columns against the oracle."""
