@@ -605,3 +605,83 @@ cudaError_t launch_rev_reduce_t(const float* P, int splits, int kcols, int bn, i
 }
 
 }  // namespace nnc
+
+namespace nnc {
+
+// ------------------------------------------------------------------ FP64 residual in double-float
+// GB300's FP64 units are too slow for an FP64 GEMV to run at HBM speed, so the FP64 value pass is
+// computed in double-float arithmetic (Dekker 1971; a value is an unevaluated sum hi + lo of two
+// FP32 numbers): weights are packed once as (hi, lo) pairs with hi = fl32(w), lo = fl32(w - hi),
+// activations likewise.  Per product, hi_w * hi_a is split exactly with an FMA (TwoProduct), the
+// cross terms hi_w lo_a + lo_w hi_a are added to the error part, and the running sum uses
+// TwoSum.  The result carries about 48 significant bits (relative error ~1e-14 per layer), which
+// the FP64 residual needs (1e-10), at eight bytes per weight (the same traffic as FP64).
+// The _rn intrinsics keep the compiler from contracting the error-free steps into FMAs.
+__device__ __forceinline__ void df_acc(float& hi, float& lo, float wh, float wl, float ah, float al) {
+  const float p = __fmul_rn(wh, ah);
+  const float pe = fmaf(wh, ah, -p);                  // exact error of p (TwoProduct)
+  const float cross = fmaf(wh, al, __fmul_rn(wl, ah));
+  const float s = __fadd_rn(hi, p);                    // TwoSum(hi, p)
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(e, __fadd_rn(pe, cross)));
+}
+
+__global__ void __launch_bounds__(256) k_gemv_fwd_df(const float4* __restrict__ W, int ld2,
+                                                     const double* __restrict__ bias,
+                                                     const float4* __restrict__ a_in, int m, int act,
+                                                     double* __restrict__ a_out,
+                                                     float2* __restrict__ a_out2) {
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= m) return;
+  const float4* w = W + (size_t)row * ld2;     // ld2 float4 per row = two weights each
+  float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+#pragma unroll 4
+  for (int j = lane; j < ld2; j += 32) {
+    const float4 ww = __ldg(w + j);
+    const float4 aa = a_in[j];
+    df_acc(h0, l0, ww.x, ww.y, aa.x, aa.y);
+    df_acc(h1, l1, ww.z, ww.w, aa.z, aa.w);
+  }
+  double acc = ((double)h0 + (double)l0) + ((double)h1 + (double)l1);
+  acc = warp_sum(acc);
+  if (lane == 0) {
+    double a, d1, d2;
+    act_eval(act, acc + (bias ? bias[row] : 0.0), a, d1, d2);
+    a_out[row] = a;
+    if (a_out2) {
+      const float ah = (float)a;
+      a_out2[row] = make_float2(ah, (float)(a - (double)ah));
+    }
+  }
+}
+
+cudaError_t launch_gemv_fwd_df(const void* W2, int kp, const double* b, const void* a_in2, int m,
+                               int act, double* a_out, void* a_out2, cudaStream_t st) {
+  const int blocks = (m * 32 + 255) / 256;
+  k_gemv_fwd_df<<<blocks, 256, 0, st>>>((const float4*)W2, kp / 2, b, (const float4*)a_in2, m, act,
+                                        a_out, (float2*)a_out2);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// (hi, lo) float pairs of an FP64 array (weights at load time, the network input per call).
+__global__ void k_split_df(const double* __restrict__ src, size_t n, float2* __restrict__ dst) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double v = src[i];
+    const float h = (float)v;
+    dst[i] = make_float2(h, (float)(v - (double)h));
+  }
+}
+
+cudaError_t launch_split_df(const double* src, size_t n, void* dst, cudaStream_t st) {
+  size_t blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  k_split_df<<<(unsigned)blocks, 256, 0, st>>>(src, n, (float2*)dst);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace nnc

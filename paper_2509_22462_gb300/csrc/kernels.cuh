@@ -90,3 +90,11 @@ cudaError_t launch_rev_reduce_t(const float* P, int splits, int kcols, int bn, i
                                 void* zlo, int ld, double* c_out, float* c_f, double* J_out,
                                 double* g_out, cudaStream_t st);
 }  // namespace nnc
+
+namespace nnc {
+// FP64 value pass in double-float arithmetic (see k_vector.cu): W2 = (hi, lo) pairs [mp][kp],
+// a_in2 = (hi, lo) pairs of the layer input; writes a_out (FP64) and its pairs a_out2.
+cudaError_t launch_gemv_fwd_df(const void* W2, int kp, const double* b, const void* a_in2, int m,
+                               int act, double* a_out, void* a_out2, cudaStream_t st);
+cudaError_t launch_split_df(const double* src, size_t n, void* dst, cudaStream_t st);
+}  // namespace nnc

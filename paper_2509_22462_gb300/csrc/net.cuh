@@ -34,6 +34,8 @@ struct LayerDev {
   double* c = nullptr;            // sigma_l''(z_l) * abar_l [mp]
   float* c_f = nullptr;           // FP32 copy of c for the tensor-core epilogue
   double* ra = nullptr;           // FP64-residual pass activations [mp]
+  void* ra2 = nullptr;            // their double-float (hi, lo) pairs [mp] (float2)
+  void* W2 = nullptr;             // double-float (hi, lo) pairs of W [mp][kp] (float2)
   float* af = nullptr;            // FP32 copy of a_l [mp] (input of the next FP32 layer)
   nnc::TcPlan plan_tan;                // tensor-core plan of this layer's tangent GEMM
   int zy_off = -1;                // column offset of this layer's Zdot / Ydot block (-1: none)
@@ -49,6 +51,10 @@ struct nnc_net {
   double* x = nullptr;       // a_0 [n_in_pad]
   float* xf = nullptr;       // FP32 copy of a_0 [n_in_pad]
   double* xin = nullptr;     // host-call staging of x [n_in_pad]
+  double* xr = nullptr;      // input of the FP64 residual pass [n_in_pad] (its own copy, so that
+                             // a residual may run on another stream next to an evaluation)
+  void* xr2 = nullptr;       // its double-float pairs (float2)
+  double* yres = nullptr;    // host-call staging of y for the residual [n_out]
   double* lam = nullptr;     // [n_out]
   double* ydev = nullptr;    // [n_out] staging
   double* rdev = nullptr;    // [n_out]

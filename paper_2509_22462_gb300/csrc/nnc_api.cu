@@ -139,13 +139,26 @@ int run_forward(nnc_net* net, bool fp64, cudaStream_t st) {
   return NNC_OK;
 }
 
-int run_forward_fp64_values(nnc_net* net, cudaStream_t st) {
-  const double* a_in = net->x;
+// FP64 value pass of the residual y - NN(x) from the raw device input x.  The FP64 form runs it
+// in FP64; the other forms in double-float arithmetic (about 48 significant bits, HBM-bound).
+int run_forward_fp64_values(nnc_net* net, const double* x, cudaStream_t st) {
+  CK(launch_copy_pad(x, net->xr, nullptr, net->n_in, net->n_in_pad, st));
+  if (net->prec == NNC_FP64) {
+    const double* a_in = net->xr;
+    for (auto& Ly : net->layers) {
+      PROF(PK_FWD);
+      CK(launch_gemv_fwd(true, Ly.W64, Ly.kp, Ly.b, a_in, Ly.m, Ly.kp, Ly.act, Ly.ra, nullptr,
+                         nullptr, nullptr, st));
+      a_in = Ly.ra;
+    }
+    return NNC_OK;
+  }
+  CK(launch_split_df(net->xr, net->n_in_pad, net->xr2, st));
+  const void* a_in2 = net->xr2;
   for (auto& Ly : net->layers) {
     PROF(PK_FWD);
-    CK(launch_gemv_fwd(true, Ly.W64, Ly.kp, Ly.b, a_in, Ly.m, Ly.kp, Ly.act, Ly.ra, nullptr,
-                       nullptr, nullptr, st));
-    a_in = Ly.ra;
+    CK(launch_gemv_fwd_df(Ly.W2, Ly.kp, Ly.b, a_in2, Ly.m, Ly.act, Ly.ra, Ly.ra2, st));
+    a_in2 = Ly.ra2;
   }
   return NNC_OK;
 }
@@ -456,6 +469,15 @@ static int load_impl(nnc_net* net, int n_layers, const int* widths, const int* a
     AL(Ly.c, Ly.mp);
     AL(Ly.ra, Ly.mp);
     AL(Ly.af, Ly.mp);
+    if (prec != NNC_FP64) {
+      float2* w2;
+      AL(w2, nw);
+      Ly.W2 = w2;
+      CK(launch_split_df(Ly.W64, nw, Ly.W2, net->stream));
+      float2* r2;
+      AL(r2, Ly.mp);
+      Ly.ra2 = r2;
+    }
     if (tc) AL(Ly.c_f, Ly.mp);
     const int chunks = rev_chunks(Ly.m, Ly.kp, net->sm_count);
     part_max = std::max(part_max, (size_t)chunks * Ly.kp * net->S_max);
@@ -464,6 +486,13 @@ static int load_impl(nnc_net* net, int n_layers, const int* widths, const int* a
   AL(net->x, net->n_in_pad);
   AL(net->xin, net->n_in_pad);
   AL(net->xf, net->n_in_pad);
+  AL(net->xr, net->n_in_pad);
+  AL(net->yres, net->n_out);
+  {
+    float2* x2;
+    AL(x2, net->n_in_pad);
+    net->xr2 = x2;
+  }
   AL(net->lam, net->n_out);
   AL(net->ydev, net->n_out);
   AL(net->rdev, net->n_out);
@@ -613,8 +642,7 @@ int nnc_eval(nnc_net* net, const double* x, double* y, int fp64_residual) {
   cudaStream_t st = net->stream;
   std::memcpy(net->h_stage, x, sizeof(double) * net->n_in);
   CK(cudaMemcpyAsync(net->xin, net->h_stage, sizeof(double) * net->n_in, cudaMemcpyHostToDevice, st));
-  CK(launch_copy_pad(net->xin, net->x, net->xf, net->n_in, net->n_in_pad, st));
-  r = run_forward_fp64_values(net, st);
+  r = run_forward_fp64_values(net, net->xin, st);
   if (r) return r;
   CK(cudaMemcpyAsync(y, net->layers.back().ra, sizeof(double) * net->n_out, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -626,8 +654,12 @@ int nnc_eval_dev(nnc_net* net, const double* x, double* y, int fp64_residual, vo
   if (r) return r;
   if (!x || !y) return fail(NNC_ERR_ARG, "x or y is NULL");
   cudaStream_t st = pick(net, stream);
-  CK(launch_copy_pad(x, net->x, net->xf, net->n_in, net->n_in_pad, st));
-  r = fp64_residual ? run_forward_fp64_values(net, st) : run_forward(net, net->prec == NNC_FP64, st);
+  if (fp64_residual) {
+    r = run_forward_fp64_values(net, x, st);
+  } else {
+    CK(launch_copy_pad(x, net->x, net->xf, net->n_in, net->n_in_pad, st));
+    r = run_forward(net, net->prec == NNC_FP64, st);
+  }
   if (r) return r;
   const double* aL = fp64_residual ? net->layers.back().ra : net->layers.back().a;
   CK(cudaMemcpyAsync(y, aL, sizeof(double) * net->n_out, cudaMemcpyDeviceToDevice, st));
@@ -639,8 +671,7 @@ int nnc_residual_dev(nnc_net* net, const double* x, const double* y, double* rr,
   if (r) return r;
   if (!x || !y || !rr) return fail(NNC_ERR_ARG, "x, y or r is NULL");
   cudaStream_t st = pick(net, stream);
-  CK(launch_copy_pad(x, net->x, net->xf, net->n_in, net->n_in_pad, st));
-  r = run_forward_fp64_values(net, st);
+  r = run_forward_fp64_values(net, x, st);
   if (r) return r;
   CK(launch_sub(y, net->layers.back().ra, rr, net->n_out, st));
   return NNC_OK;
@@ -657,9 +688,9 @@ int nnc_residual(nnc_net* net, const double* x, const double* y, double* rr) {
   std::memcpy(net->h_stage, x, sizeof(double) * net->n_in);
   std::memcpy(net->h_stage + net->n_in_pad, y, sizeof(double) * net->n_out);
   CK(cudaMemcpyAsync(net->xin, net->h_stage, sizeof(double) * net->n_in, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(net->ydev, net->h_stage + net->n_in_pad, sizeof(double) * net->n_out,
+  CK(cudaMemcpyAsync(net->yres, net->h_stage + net->n_in_pad, sizeof(double) * net->n_out,
                      cudaMemcpyHostToDevice, st));
-  r = nnc_residual_dev(net, net->xin, net->ydev, net->rdev, st);
+  r = nnc_residual_dev(net, net->xin, net->yres, net->rdev, st);
   if (r) return r;
   CK(cudaMemcpyAsync(rr, net->rdev, sizeof(double) * net->n_out, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
