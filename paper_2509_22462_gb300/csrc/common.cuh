@@ -69,5 +69,14 @@ __device__ __forceinline__ void split_bf16(double v, __nv_bfloat16& hi, __nv_bfl
   hi = __double2bfloat16(v);
   lo = __double2bfloat16(v - (double)__bfloat162float(hi));
 }
+// Three-way split v ~ p0 + p1 + p2, each part the BF16 rounding of what the earlier parts leave;
+// the residual is below 2^-24 |v| (outside the BF16 underflow range).
+__device__ __forceinline__ void split3_bf16(double v, __nv_bfloat16& p0, __nv_bfloat16& p1,
+                                            __nv_bfloat16& p2) {
+  p0 = __double2bfloat16(v);
+  const double r1 = v - (double)__bfloat162float(p0);
+  p1 = __double2bfloat16(r1);
+  p2 = __double2bfloat16(r1 - (double)__bfloat162float(p1));
+}
 
 }  // namespace nnc

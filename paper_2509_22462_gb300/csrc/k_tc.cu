@@ -54,12 +54,18 @@ struct TcArgs {
 // (64-byte swizzle) for split-BF16x3, whose stages carry four operand tiles, so that five stages
 // fit in shared memory instead of two.
 // The FP8 form (kind::f8f6f4, e4m3 operands) uses 128-element (128-byte) K blocks.
-enum { MODE_BF16 = 0, MODE_BF16X3 = 1, MODE_FP8 = 2 };
-constexpr int bk_for(int mode) { return mode == MODE_BF16X3 ? 32 : mode == MODE_FP8 ? 128 : 64; }
+// MODE_BF16X6: three-way split v ~ p0 + p1 + p2 (about 24 significant bits) with the six products
+// p_i q_j, i + j <= 2 -- FP32-level accuracy; used by the bandwidth-bound reverse sweep, whose
+// Jacobian feeds the interior-point method's dual residual.
+enum { MODE_BF16 = 0, MODE_BF16X3 = 1, MODE_FP8 = 2, MODE_BF16X6 = 3 };
+constexpr int bk_for(int mode) {
+  return (mode == MODE_BF16X3 || mode == MODE_BF16X6) ? 32 : mode == MODE_FP8 ? 128 : 64;
+}
 
 template <int BN, int MODE>
 struct Cfg {
-  static constexpr bool X3 = MODE == MODE_BF16X3;
+  static constexpr bool X6 = MODE == MODE_BF16X6;
+  static constexpr bool X3 = MODE == MODE_BF16X3 || X6;   // has a second (lo) part
   static constexpr bool F8 = MODE == MODE_FP8;
   static constexpr int EB = F8 ? 1 : 2;                // bytes per element
   static constexpr int BKE = bk_for(MODE);
@@ -68,7 +74,7 @@ struct Cfg {
   static constexpr int SBO = 8 * ROWB;                 // bytes between 8-row core-matrix groups
   static constexpr int A_BYTES = BM * ROWB;
   static constexpr int B_BYTES = BN * ROWB;
-  static constexpr int NPARTS = X3 ? 2 : 1;
+  static constexpr int NPARTS = X6 ? 3 : X3 ? 2 : 1;
   static constexpr int STAGE_BYTES = NPARTS * (A_BYTES + B_BYTES);
   static constexpr int TX_BYTES = STAGE_BYTES;
   static constexpr int SMEM_BUDGET = 227 * 1024 - 2048;
@@ -212,6 +218,7 @@ template <int BN, int MODE, int KIND>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
               const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
+              const __grid_constant__ CUtensorMap ta_p2, const __grid_constant__ CUtensorMap tb_p2,
               const TcArgs args) {
   using C = Cfg<BN, MODE>;
   constexpr bool X3 = C::X3;
@@ -317,6 +324,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (X3) tma_load_2d(smem_u32(st + C::A_BYTES), &ta_lo, fb, kx, a_row0);
         tma_load_2d(smem_u32(st + C::NPARTS * C::A_BYTES), &tb_hi, fb, kx, b_row0);
         if (X3) tma_load_2d(smem_u32(st + C::NPARTS * C::A_BYTES + C::B_BYTES), &tb_lo, fb, kx, b_row0);
+        if (C::X6) {
+          tma_load_2d(smem_u32(st + 2 * C::A_BYTES), &ta_p2, fb, kx, a_row0);
+          tma_load_2d(smem_u32(st + C::NPARTS * C::A_BYTES + 2 * C::B_BYTES), &tb_p2, fb, kx, b_row0);
+        }
         issued = i + 1;
       }
     }
@@ -345,6 +356,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (X3) {
             umma_bf16(tmem, sdesc<SW, SB>(a_hi + off), sdesc<SW, SB>(b_lo + off), idesc, 1u);
             umma_bf16(tmem, sdesc<SW, SB>(a_lo + off), sdesc<SW, SB>(b_hi + off), idesc, 1u);
+          }
+          if (C::X6) {
+            const uint32_t a_p2 = a_hi + 2 * C::A_BYTES, b_p2 = b_hi + 2 * C::B_BYTES;
+            umma_bf16(tmem, sdesc<SW, SB>(a_hi + off), sdesc<SW, SB>(b_p2 + off), idesc, 1u);
+            umma_bf16(tmem, sdesc<SW, SB>(a_lo + off), sdesc<SW, SB>(b_lo + off), idesc, 1u);
+            umma_bf16(tmem, sdesc<SW, SB>(a_p2 + off), sdesc<SW, SB>(b_hi + off), idesc, 1u);
           }
         }
         umma_commit(smem_u32(&empty[s]));
@@ -487,7 +504,8 @@ cudaError_t launch_t(const TcPlan& p, const TcArgs& a, dim3 grid, cudaStream_t s
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_tc_gemm<BN, MODE, KIND><<<grid, kThreads, C::SMEM, st>>>(p.ta_hi, p.ta_lo, p.tb_hi, p.tb_lo, a);
+  k_tc_gemm<BN, MODE, KIND><<<grid, kThreads, C::SMEM, st>>>(p.ta_hi, p.ta_lo, p.tb_hi, p.tb_lo, p.ta_p2,
+                                                             p.tb_p2, a);
   note_launch();
   return cudaGetLastError();
 }
@@ -505,8 +523,8 @@ cudaError_t launch_mode(const TcPlan& p, const TcArgs& a, dim3 grid, cudaStream_
 template <int KIND>
 cudaError_t launch_any(const TcPlan& p, const TcArgs& a, dim3 grid, cudaStream_t st) {
   if constexpr (KIND == TC_REV) {
-    if (p.bn == 16) return launch_t<16, MODE_BF16X3, KIND>(p, a, grid, st);
-    if (p.bn == 48) return launch_t<48, MODE_BF16X3, KIND>(p, a, grid, st);
+    if (p.bn == 16) return launch_t<16, MODE_BF16X6, KIND>(p, a, grid, st);
+    if (p.bn == 48) return launch_t<48, MODE_BF16X6, KIND>(p, a, grid, st);
     return cudaErrorInvalidValue;
   }
   switch (p.bn) {
@@ -530,14 +548,16 @@ int count_lower_tiles(int ntm, int ntn, int bn) {
 
 int tc_plan_make(TcPlan& p, int kind, int prec, const void* a_hi, const void* a_lo, int a_rows,
                  int ld_a, const void* b_hi, const void* b_lo, int b_rows, int ld_b, int M, int N,
-                 int K, int sm_count, int force_bn, int force_splits) {
+                 int K, int sm_count, int force_bn, int force_splits, const void* a_p2,
+                 const void* b_p2) {
   p = TcPlan();
   p.kind = kind;
   p.x3 = (prec == NNC_BF16X3 || kind == TC_REV) ? 1 : 0;
   p.M = M;
   p.N = N;
   p.K = K;
-  p.mode = (prec == NNC_BF16X3 || kind == TC_REV) ? MODE_BF16X3
+  p.mode = kind == TC_REV ? MODE_BF16X6
+           : prec == NNC_BF16X3 ? MODE_BF16X3
            : (prec == NNC_FP8 && kind == TC_TANGENT) ? MODE_FP8 : MODE_BF16;
   p.bk = bk_for(p.mode);
   const int eb = p.mode == MODE_FP8 ? 1 : 2;
@@ -611,6 +631,10 @@ int tc_plan_make(TcPlan& p, int kind, int prec, const void* a_hi, const void* a_
   if (!make_map(&p.ta_lo, p.x3 ? a_lo : nullptr, a_rows, K, ld_a, a_box, p.bk, eb)) return NNC_ERR_CUDA;
   if (!make_map(&p.tb_hi, b_hi, b_rows, K, ld_b, b_box, p.bk, eb)) return NNC_ERR_CUDA;
   if (!make_map(&p.tb_lo, p.x3 ? b_lo : nullptr, b_rows, K, ld_b, b_box, p.bk, eb)) return NNC_ERR_CUDA;
+  const bool x6 = p.mode == MODE_BF16X6;
+  if (x6 && (!a_p2 || !b_p2)) return NNC_ERR_ARG;
+  if (!make_map(&p.ta_p2, x6 ? a_p2 : nullptr, a_rows, K, ld_a, a_box, p.bk, eb)) return NNC_ERR_CUDA;
+  if (!make_map(&p.tb_p2, x6 ? b_p2 : nullptr, b_rows, K, ld_b, b_box, p.bk, eb)) return NNC_ERR_CUDA;
   p.ready = true;
   return NNC_OK;
 }

@@ -503,8 +503,8 @@ namespace nnc {
 
 // ------------------------------------------------------------------ tensor-core reverse sweep
 // W_l^T packed as BF16 hi/lo (Wt[k][m] = W[m][k], K-major for the reverse GEMM; [kp][mp]).
-__global__ void k_pack_t(const double* __restrict__ W, int mp, int kp, __nv_bfloat16* __restrict__ hi,
-                         __nv_bfloat16* __restrict__ lo) {
+__global__ void k_pack_t(const double* __restrict__ W, int mp, int kp, __nv_bfloat16* __restrict__ p0,
+                         __nv_bfloat16* __restrict__ p1, __nv_bfloat16* __restrict__ p2) {
   __shared__ double tile[32][33];
   const int m0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
@@ -515,38 +515,44 @@ __global__ void k_pack_t(const double* __restrict__ W, int mp, int kp, __nv_bflo
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int k = k0 + r, m = m0 + threadIdx.x;
     if (k < kp && m < mp) {
-      __nv_bfloat16 h, l;
-      split_bf16(tile[threadIdx.x][r], h, l);
-      hi[(size_t)k * mp + m] = h;
-      lo[(size_t)k * mp + m] = l;
+      __nv_bfloat16 a, b, c;
+      split3_bf16(tile[threadIdx.x][r], a, b, c);
+      const size_t o = (size_t)k * mp + m;
+      p0[o] = a;
+      p1[o] = b;
+      p2[o] = c;
     }
   }
 }
 
-cudaError_t launch_pack_t(const double* W, int mp, int kp, __nv_bfloat16* hi, __nv_bfloat16* lo,
-                          cudaStream_t st) {
+cudaError_t launch_pack_t(const double* W, int mp, int kp, __nv_bfloat16* p0, __nv_bfloat16* p1,
+                          __nv_bfloat16* p2, cudaStream_t st) {
   dim3 grid((kp + 31) / 32, (mp + 31) / 32), block(32, 8);
-  k_pack_t<<<grid, block, 0, st>>>(W, mp, kp, hi, lo);
+  k_pack_t<<<grid, block, 0, st>>>(W, mp, kp, p0, p1, p2);
   note_launch();
   return cudaGetLastError();
 }
 
-// Output-layer seeds, transposed for the reverse GEMM: Zb[s][i] = s1[i] * abar_L[i][s] as BF16
-// hi/lo (row stride ld), abar_L = e_s (s < nJ) or lambda (s = lam_col); c_L = s2 * lambda.
+// Output-layer seeds, transposed for the reverse GEMM: Zb[s][i] = s1[i] * abar_L[i][s] as three
+// BF16 parts z0/z1/z2 (row stride ld), abar_L = e_s (s < nJ) or lambda (s = lam_col);
+// c_L = s2 * lambda.
 __global__ void k_rev_seed_t(int m, int S, int nJ, int lam_col, const double* __restrict__ s1,
                              const double* __restrict__ s2, const double* __restrict__ lam,
-                             __nv_bfloat16* __restrict__ zhi, __nv_bfloat16* __restrict__ zlo, int ld,
-                             double* __restrict__ c_out, float* __restrict__ c_f) {
+                             __nv_bfloat16* __restrict__ z0, __nv_bfloat16* __restrict__ z1,
+                             __nv_bfloat16* __restrict__ z2, int ld, double* __restrict__ c_out,
+                             float* __restrict__ c_f) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= m * S) return;
   const int i = idx / S, s = idx % S;
   double ab = 0.0;
   if (s == lam_col) ab = lam[i];
   else if (s < nJ) ab = (s == i) ? 1.0 : 0.0;
-  __nv_bfloat16 h, l;
-  split_bf16(s1[i] * ab, h, l);
-  zhi[(size_t)s * ld + i] = h;
-  zlo[(size_t)s * ld + i] = l;
+  __nv_bfloat16 a, b, c;
+  split3_bf16(s1[i] * ab, a, b, c);
+  const size_t o = (size_t)s * ld + i;
+  z0[o] = a;
+  z1[o] = b;
+  z2[o] = c;
   if (s == lam_col) {
     if (c_out) c_out[i] = s2[i] * ab;
     if (c_f) c_f[i] = (float)(s2[i] * ab);
@@ -554,23 +560,24 @@ __global__ void k_rev_seed_t(int m, int S, int nJ, int lam_col, const double* __
 }
 
 cudaError_t launch_rev_seed_t(int m, int S, int nJ, int lam_col, const double* s1, const double* s2,
-                              const double* lam, void* zhi, void* zlo, int ld, double* c_out,
-                              float* c_f, cudaStream_t st) {
+                              const double* lam, void* const z[3], int ld, double* c_out, float* c_f,
+                              cudaStream_t st) {
   k_rev_seed_t<<<(m * S + 255) / 256, 256, 0, st>>>(m, S, nJ, lam_col, s1, s2, lam,
-                                                    (__nv_bfloat16*)zhi, (__nv_bfloat16*)zlo, ld,
-                                                    c_out, c_f);
+                                                    (__nv_bfloat16*)z[0], (__nv_bfloat16*)z[1],
+                                                    (__nv_bfloat16*)z[2], ld, c_out, c_f);
   note_launch();
   return cudaGetLastError();
 }
 
 // Sum the split partials P[sp][k][0..bn) of W_l^T Zbar; then either the next seeds (transposed,
-// BF16 hi/lo: Zb[s][k] = s1[k] * Abar[k][s]) and c = s2 * Abar[:, lam_col], or, on the first
+// three BF16 parts: Zb[s][k] = s1[k] * Abar[k][s]) and c = s2 * Abar[:, lam_col], or, on the first
 // layer, J_out[s][k] (s < nJ) and g_out[k] (s = lam_col) for k < kvalid.
 __global__ void k_rev_reduce_t(const float* __restrict__ P, int splits, int kcols, int bn, int S,
                                int kvalid, const double* __restrict__ s1,
                                const double* __restrict__ s2, int lam_col, int nJ,
-                               __nv_bfloat16* __restrict__ zhi, __nv_bfloat16* __restrict__ zlo,
-                               int ld, double* __restrict__ c_out, float* __restrict__ c_f,
+                               __nv_bfloat16* __restrict__ z0, __nv_bfloat16* __restrict__ z1,
+                               __nv_bfloat16* __restrict__ z2, int ld, double* __restrict__ c_out,
+                               float* __restrict__ c_f,
                                double* __restrict__ J_out, double* __restrict__ g_out) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= kcols * S) return;
@@ -578,10 +585,12 @@ __global__ void k_rev_reduce_t(const float* __restrict__ P, int splits, int kcol
   double v = 0.0;
   for (int sp = 0; sp < splits; ++sp) v += (double)P[((size_t)sp * kcols + k) * bn + s];
   if (s1) {
-    __nv_bfloat16 h, l;
-    split_bf16(s1[k] * v, h, l);
-    zhi[(size_t)s * ld + k] = h;
-    zlo[(size_t)s * ld + k] = l;
+    __nv_bfloat16 a, b, c;
+    split3_bf16(s1[k] * v, a, b, c);
+    const size_t o = (size_t)s * ld + k;
+    z0[o] = a;
+    z1[o] = b;
+    z2[o] = c;
     if (s == lam_col) {
       if (c_out) c_out[k] = s2[k] * v;
       if (c_f) c_f[k] = (float)(s2[k] * v);
@@ -593,13 +602,15 @@ __global__ void k_rev_reduce_t(const float* __restrict__ P, int splits, int kcol
 }
 
 cudaError_t launch_rev_reduce_t(const float* P, int splits, int kcols, int bn, int S, int kvalid,
-                                const double* s1, const double* s2, int lam_col, int nJ, void* zhi,
-                                void* zlo, int ld, double* c_out, float* c_f, double* J_out,
+                                const double* s1, const double* s2, int lam_col, int nJ,
+                                void* const z[3], int ld, double* c_out, float* c_f, double* J_out,
                                 double* g_out, cudaStream_t st) {
+  __nv_bfloat16* z0 = z ? (__nv_bfloat16*)z[0] : nullptr;
+  __nv_bfloat16* z1 = z ? (__nv_bfloat16*)z[1] : nullptr;
+  __nv_bfloat16* z2 = z ? (__nv_bfloat16*)z[2] : nullptr;
   k_rev_reduce_t<<<(kcols * S + 255) / 256, 256, 0, st>>>(P, splits, kcols, bn, S, kvalid, s1, s2,
-                                                          lam_col, nJ, (__nv_bfloat16*)zhi,
-                                                          (__nv_bfloat16*)zlo, ld, c_out, c_f, J_out,
-                                                          g_out);
+                                                          lam_col, nJ, z0, z1, z2, ld, c_out, c_f,
+                                                          J_out, g_out);
   note_launch();
   return cudaGetLastError();
 }

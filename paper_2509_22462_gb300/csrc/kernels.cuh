@@ -80,14 +80,15 @@ cudaError_t launch_quant_fp8(const void* A, int rows, int ld, unsigned char* A8,
 
 namespace nnc {
 // Tensor-core reverse sweep helpers (see k_vector.cu).
-cudaError_t launch_pack_t(const double* W, int mp, int kp, __nv_bfloat16* hi, __nv_bfloat16* lo,
-                          cudaStream_t st);
+// Operands are split three ways into BF16 parts (W^T: p0/p1/p2; seeds: z[0..2]).
+cudaError_t launch_pack_t(const double* W, int mp, int kp, __nv_bfloat16* p0, __nv_bfloat16* p1,
+                          __nv_bfloat16* p2, cudaStream_t st);
 cudaError_t launch_rev_seed_t(int m, int S, int nJ, int lam_col, const double* s1, const double* s2,
-                              const double* lam, void* zhi, void* zlo, int ld, double* c_out,
-                              float* c_f, cudaStream_t st);
+                              const double* lam, void* const z[3], int ld, double* c_out, float* c_f,
+                              cudaStream_t st);
 cudaError_t launch_rev_reduce_t(const float* P, int splits, int kcols, int bn, int S, int kvalid,
-                                const double* s1, const double* s2, int lam_col, int nJ, void* zhi,
-                                void* zlo, int ld, double* c_out, float* c_f, double* J_out,
+                                const double* s1, const double* s2, int lam_col, int nJ,
+                                void* const z[3], int ld, double* c_out, float* c_f, double* J_out,
                                 double* g_out, cudaStream_t st);
 }  // namespace nnc
 

@@ -24,7 +24,8 @@ struct LayerDev {
   __nv_bfloat16* Wlo = nullptr;   // [mp][kp]
   unsigned char* W8 = nullptr;    // [mp][kp] e4m3 (FP8 form)
   __nv_bfloat16* WThi = nullptr;  // W_l^T [kp][mp] BF16 hi (tensor-core reverse sweep)
-  __nv_bfloat16* WTlo = nullptr;  // W_l^T [kp][mp] BF16 lo
+  __nv_bfloat16* WTlo = nullptr;  // W_l^T [kp][mp] BF16 second part
+  __nv_bfloat16* WTp2 = nullptr;  // W_l^T [kp][mp] BF16 third part
   nnc::TcPlan plan_rev;           // tensor-core plan of this layer's reverse step
   float* w8s = nullptr;           // [mp] per-row scale of W8
   double* b = nullptr;            // [mp]
@@ -67,7 +68,7 @@ struct nnc_net {
   void* Zt[2] = {nullptr, nullptr};  // [hi, lo]: Zdot_l^T of all curved layers, n x K_total
   void* Yt[2] = {nullptr, nullptr};  // [hi, lo]: (c_l * Zdot_l)^T, n x K_total
   int K_total = 0;                   // sum of mp_l over layers with sigma'' != 0
-  void* Zb[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // reverse seeds^T [48][mp_max] hi/lo
+  void* Zb[2][3] = {};  // reverse seeds^T [48][mp_max], ping-pong x three BF16 parts
   float* Prev = nullptr;             // split partials of the tensor-core reverse step
   bool tc_rev = false;               // reverse sweep on the tensor cores
   unsigned char* A8 = nullptr;       // FP8 form: e4m3 copy of the current tangent operand

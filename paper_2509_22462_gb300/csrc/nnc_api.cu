@@ -174,9 +174,9 @@ int run_reverse(nnc_net* net, bool fp64, int nJ, bool with_lam, const double* la
   const bool tc = is_tc(net->prec);
   LayerDev& Lo = net->layers.back();
   if (net->tc_rev) {
-    // seeds^T in BF16 hi/lo, then per layer: split-K tensor-core product W_l^T Zbar and a reduce
+    // seeds^T in three BF16 parts, then per layer: split-K tensor-core product W_l^T Zbar and a reduce
     // that forms the next seeds (or J and the gradient on the first layer)
-    CK(launch_rev_seed_t(Lo.m, S, nJ, lam_col, Lo.s1, Lo.s2, lam, net->Zb[0][0], net->Zb[0][1], Lo.mp,
+    CK(launch_rev_seed_t(Lo.m, S, nJ, lam_col, Lo.s1, Lo.s2, lam, net->Zb[0], Lo.mp,
                          with_lam ? Lo.c : nullptr, with_lam ? Lo.c_f : nullptr, st));
     for (int l = net->L - 1; l >= 0; --l) {
       LayerDev& Ly = net->layers[l];
@@ -186,12 +186,12 @@ int run_reverse(nnc_net* net, bool fp64, int nJ, bool with_lam, const double* la
       if (l > 0) {
         LayerDev& Lp = net->layers[l - 1];
         CK(launch_rev_reduce_t(net->Prev, Ly.plan_rev.splits, Ly.kp, Ly.plan_rev.bn, S, Ly.k, Lp.s1,
-                               Lp.s2, lam_col, nJ, net->Zb[zn][0], net->Zb[zn][1], Ly.kp,
+                               Lp.s2, lam_col, nJ, net->Zb[zn], Ly.kp,
                                with_lam ? Lp.c : nullptr, with_lam ? Lp.c_f : nullptr, nullptr,
                                nullptr, st));
       } else {
         CK(launch_rev_reduce_t(net->Prev, Ly.plan_rev.splits, Ly.kp, Ly.plan_rev.bn, S, Ly.k, nullptr,
-                               nullptr, lam_col, nJ, nullptr, nullptr, 0, nullptr, nullptr, J, g, st));
+                               nullptr, lam_col, nJ, nullptr, 0, nullptr, nullptr, J, g, st));
       }
     }
     return NNC_OK;
@@ -453,7 +453,8 @@ static int load_impl(nnc_net* net, int n_layers, const int* widths, const int* a
     if (tc) {
       AL(Ly.WThi, nw);
       AL(Ly.WTlo, nw);
-      CK(launch_pack_t(Ly.W64, Ly.mp, Ly.kp, Ly.WThi, Ly.WTlo, net->stream));
+      AL(Ly.WTp2, nw);
+      CK(launch_pack_t(Ly.W64, Ly.mp, Ly.kp, Ly.WThi, Ly.WTlo, Ly.WTp2, net->stream));
     }
     if (prec == NNC_FP8 && l > 0) {
       AL(Ly.W8, nw);
@@ -551,7 +552,7 @@ static int load_impl(nnc_net* net, int n_layers, const int* widths, const int* a
     if (net->S_max <= 48) {
       size_t prev = 1;
       for (int pp = 0; pp < 2; ++pp)
-        for (int part = 0; part < 2; ++part) {
+        for (int part = 0; part < 3; ++part) {
           __nv_bfloat16* zb;
           AL(zb, (size_t)48 * mp_max);
           net->Zb[pp][part] = zb;
@@ -560,7 +561,8 @@ static int load_impl(nnc_net* net, int n_layers, const int* widths, const int* a
         LayerDev& Ly = net->layers[l];
         const int zi = (n_layers - 1 - l) % 2;
         int r = tc_plan_make(Ly.plan_rev, TC_REV, prec, Ly.WThi, Ly.WTlo, Ly.kp, Ly.mp, net->Zb[zi][0],
-                             net->Zb[zi][1], 48, Ly.mp, Ly.kp, net->S_max, Ly.mp, net->sm_count);
+                             net->Zb[zi][1], 48, Ly.mp, Ly.kp, net->S_max, Ly.mp, net->sm_count, 0, 0,
+                             Ly.WTp2, net->Zb[zi][2]);
         if (r != NNC_OK) return fail(r, "tensor-core reverse plan failed");
         prev = std::max(prev, (size_t)Ly.plan_rev.splits * Ly.kp * Ly.plan_rev.bn);
       }

@@ -19,6 +19,7 @@ enum { TC_TANGENT = 0, TC_SYRK = 1, TC_TANGENT_G = 2, TC_SYRK_G = 3, TC_REV = 4 
 
 struct TcPlan {
   CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;
+  CUtensorMap ta_p2, tb_p2;   // third split parts (reverse sweep only)
   int kind = TC_TANGENT;
   int x3 = 0;           // split-BF16x3 products
   int M = 0, N = 0, K = 0;  // M: rows of A (multiple of 128), N: valid rows of B, K: multiple of 64
@@ -35,7 +36,8 @@ struct TcPlan {
 // strides in elements.  Returns NNC_OK or a negative status.
 int tc_plan_make(TcPlan& p, int kind, int prec, const void* a_hi, const void* a_lo, int a_rows,
                  int ld_a, const void* b_hi, const void* b_lo, int b_rows, int ld_b, int M, int N,
-                 int K, int sm_count, int force_bn = 0, int force_splits = 0);
+                 int K, int sm_count, int force_bn = 0, int force_splits = 0,
+                 const void* a_p2 = nullptr, const void* b_p2 = nullptr);
 
 // at_* (row stride ldo) may be NULL on the last layer; zt_* / yt_* (row stride ldz) may be NULL
 // for a layer without curvature.
@@ -46,8 +48,9 @@ cudaError_t tc_tangent(const TcPlan& p, const double* s1, const float* c, void* 
                        int* err, cudaStream_t st, const float* wscale = nullptr,
                        const float* tscale = nullptr);
 
-// Reverse sweep W_l^T Zbar with split-BF16x3 operands: A = W_l^T (hi/lo, kp x mp, K-major),
-// B = Zbar^T (hi/lo, seeds x mp); writes part[split][k][0..bn) (FP32, bn = 16 or 48).
+// Reverse sweep W_l^T Zbar with three-way split BF16 operands (six products, ~FP32 accuracy):
+// A = W_l^T (parts 0/1/2, kp x mp, K-major), B = Zbar^T (parts, seeds x mp); writes
+// part[split][k][0..bn) (FP32, bn = 16 or 48).
 cudaError_t tc_rev(const TcPlan& p, float* part, int* err, cudaStream_t st);
 
 // Hp: splits x N x N floats (row stride N); partial sums of the lower triangle are added.

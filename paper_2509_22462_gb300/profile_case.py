@@ -3,7 +3,8 @@
   python -m paper_2509_22462_gb300.profile_case --widths 784,4096,4096,4096,10 --prec bf16x3 --reps 2
 
 Builds a tanh MLP with N(0, 1/fan_in) weights (seed 0) and runs `reps` full oracle calls
-(value, Jacobian, gradient and Hessian of lambda^T NN) on device-resident inputs, then prints
+(value, Jacobian, gradient and Hessian of lambda^T NN, then the FP64 residual) on device-resident
+inputs, then prints
 the per-kernel-kind times of the last call.  With the default widths every tangent GEMM has the
 shape of the 104M network's (M = 4096, N = 784, K = 4096).
 """
@@ -43,10 +44,12 @@ def main():
     J = torch.empty(m, n, dtype=torch.float64, device=dev)
     H = torch.empty(n, n, dtype=torch.float64, device=dev)
     g = torch.empty(n, dtype=torch.float64, device=dev)
+    r = torch.empty(m, dtype=torch.float64, device=dev)
     for i in range(a.reps):
         if i == a.reps - 1:
             net.profile(True)
         net.eval_all_dev(x, lam, y, J, H, g)
+        net.residual_dev(x, y, r)
     torch.cuda.synchronize()
     prof = net.profile_read()
     for k, (ms, cnt) in prof.items():

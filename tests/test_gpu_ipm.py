@@ -71,3 +71,29 @@ def test_iteration_limit_status(nnc):
     res, _, _ = nnc.ipm_adversarial(net, d.x0, d.target, d.margin, max_iter=2)
     assert res["status"] == 1 and res["iters"] == 2
     net.free()
+
+
+@pytest.fixture(scope="module")
+def m104_oracle_solution():
+    mlp = make_mlp(synth.PAPER_104M, seed=0)
+    d = synth.adversarial_data(seed=0)
+    r = oipm.solve(problems.adversarial(mlp, d.x0, d.target, d.margin))
+    assert r.status == oipm.OPTIMAL
+    return mlp, d, r
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_adversarial_104m_matches_oracle(nnc, m104_oracle_solution, prec):
+    """The ~104M-parameter net (784 -> 4096 x 7 -> 10): the converged objective within 1e-6 of
+    the oracle's, so the tensor-core Jacobian and Hessian are accurate enough not to move the
+    solution the dual residual certifies."""
+    mlp, d, ro = m104_oracle_solution
+    net = nnc.Net.from_mlp(mlp, precision=prec)
+    res, v, lam = nnc.ipm_adversarial(net, d.x0, d.target, d.margin)
+    print(f"[ipm 104m {prec}] status={res['status_name']} iters={res['iters']} (oracle {ro.iters}) "
+          f"obj={res['obj']:.13g} (oracle {ro.obj:.13g}) kkt={res['kkt_error']:.2e} "
+          f"t={res['solve_seconds']:.3f}s")
+    assert res["status"] == 0
+    assert res["kkt_error"] <= 1e-6
+    assert abs(res["obj"] - ro.obj) <= 1e-6 * abs(ro.obj)
+    net.free()
