@@ -31,8 +31,9 @@ sys.path.insert(0, ROOT)
 METRIC = "hessian_lag_evals_per_s"
 
 # DRAM bytes (read + write) of one tangent-GEMM launch from the ncu capture summarised in
-# profiles/k_tc_gemm_tangent_784x4096x4096.md; valid for the kernel version it was taken on.
-TANGENT_TRAFFIC = {("104m", "bf16x3"): 83.97e6}
+# profiles/k_tc_gemm_tangent_784x4096x4096.md; an entry is valid only for the kernel version it
+# was taken on (none is recorded for the current one yet).
+TANGENT_TRAFFIC = {}
 UNIT = "evals/s"
 
 
@@ -422,16 +423,10 @@ def run_ours(args, rank, world, local_rank):
     g = torch.empty(n, dtype=torch.float64, device=dev)
     r = torch.empty(m, dtype=torch.float64, device=dev)
     y_it = torch.zeros(m, dtype=torch.float64, device=dev)   # the iterate's y of g(x, y) = y - NN(x)
-    aux = torch.cuda.Stream(device=dev)
 
     def step():
-        # the FP64 residual of the iterate is independent of the derivatives: it runs on a second
-        # stream next to them (separate buffers in the library), joined at the end of the step
-        aux.wait_stream(stream)
-        with torch.cuda.stream(aux):
-            net.residual_dev(x, y_it, r)
-        net.eval_all_dev(x, lam, y, J, H, g)
-        stream.wait_stream(aux)
+        # one interior-point iterate: FP64-accurate residual, J, H and gradient from one value pass
+        net.eval_kkt_dev(x, y_it, lam, r, J, H, g)
 
     for _ in range(args.warmup):
         step()
@@ -439,7 +434,9 @@ def run_ours(args, rank, world, local_rank):
 
     clocks = Clocks(_gpu_index(local_rank)) if rank == 0 else None
     time.sleep(0.3 if clocks else 0)
-    net.profile(True)
+    # events bracket only the tangent GEMM (the roofline kernel) inside the timed region; the
+    # per-kind breakdown comes from a separate profiled pass below
+    net.profile(True, kinds=["tangent_gemm"])
     launches0 = nnc.launch_count()
     if world > 1:
         dist.barrier()
@@ -453,17 +450,24 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         dist.barrier()
     launches = nnc.launch_count() - launches0
-    prof = net.profile_read()
-    net.profile(False)
+    prof_timed = net.profile_read()
     clk = clocks.stop() if clocks else None
     value, el_ms = aggregate(e0.elapsed_time(e1), args.steps, world, dev)
+    # per-kind breakdown (events around every launch, outside the timed region)
+    net.profile(True)
+    for _ in range(min(args.steps, 10)):
+        step()
+    torch.cuda.synchronize()
+    prof = net.profile_read()
+    net.profile(False)
+    n_prof = min(args.steps, 10)
 
     # roofline of the dominant kernel: the tangent GEMM (the largest single kernel of a step;
     # the value pass and the FP64 residual are 16 smaller launches of two different kernels)
     peaks, peak_src = _peaks()
     dom_name = "tangent_gemm" if prof.get("tangent_gemm", (0, 0))[1] > 0 else \
         max(prof.items(), key=lambda kv: kv[1][0])[0]
-    dom_ms, dom_cnt = prof[dom_name]
+    dom_ms, dom_cnt = prof_timed[dom_name] if prof_timed.get(dom_name, (0, 0))[1] else prof[dom_name]
     roof = None
     if dom_name == "tangent_gemm" and dom_cnt > 0:
         per = tangent_gemm_flops(spec)
@@ -483,29 +487,27 @@ def run_ours(args, rank, world, local_rank):
         avg_s = dom_ms / dom_cnt / 1e3
         roof = {"kernel": dom_name, "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"),
                 "unit": "GB/s", "frac": None, "traffic": None, "avg_launch_us": avg_s * 1e6}
-    kernel_ms = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+    kernel_ms = {k: {"ms_per_step": v[0] / n_prof, "launches_per_step": v[1] / n_prof}
                  for k, v in prof.items()}
 
     # end to end through the host-pointer C ABI (copies inside the timed region)
     e2e = None
     if not args.no_e2e:
-        xh, lh = d.x0.copy(), d.lam.copy()
+        xh, lh, yh = d.x0.copy(), d.lam.copy(), np.zeros(m)
         for _ in range(2):
-            ys, Js, Hs = nnc.eval_batched([net], [xh], [lh])
-            net.residual(xh, ys[0])
+            net.eval_kkt(xh, yh, lh)
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            ys, Js, Hs = nnc.eval_batched([net], [xh], [lh])
-            net.residual(xh, ys[0])
+            net.eval_kkt(xh, yh, lh)
         el = time.perf_counter() - t0
         if world > 1:
             t = torch.tensor([el], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             el = float(t.item())
-        h2d = 8 * (n + m) + 8 * (n + m)          # x, lambda; then x, y for the residual
-        d2h = 8 * (m + m * n + n * n) + 8 * m    # y, J, H; then r
+        h2d = 8 * (n + m + m)                    # x, lambda, y
+        d2h = 8 * (m + m * n + n * n + n)        # r, J, H, grad
         e2e = {"value": world * args.steps / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
@@ -525,11 +527,7 @@ def run_ours(args, rank, world, local_rank):
             ipm["fp64"] = res
 
         def step64():
-            aux.wait_stream(stream)
-            with torch.cuda.stream(aux):
-                n64.residual_dev(x, y_it, r)
-            n64.eval_all_dev(x, lam, y, J, H, g)
-            stream.wait_stream(aux)
+            n64.eval_kkt_dev(x, y_it, lam, r, J, H, g)
 
         step64()
         torch.cuda.synchronize()

@@ -121,6 +121,17 @@ int nnc_hessian_lag_dev(nnc_net* net, const double* x, const double* lambda, dou
 /* One-net "everything" call on device pointers: y, J, H, grad may each be NULL (skipped). */
 int nnc_eval_all_dev(nnc_net* net, const double* x, const double* lambda, double* y, double* J,
                      double* H, double* grad, void* stream);
+/* What one interior-point iteration asks of the constraint y - NN(x) = 0 at the iterate (x, y)
+ * (Eq. 2 with the constraint of Eq. 3, Hessian term of Eq. 6), from a single value pass: the
+ * residual r = y - NN(x) at the accuracy of nnc_residual (FP64, or double-float with about 48
+ * significant bits in the other forms), J = dNN/dx, H = sum_i lambda_i d2 NN_i/dx2 and
+ * grad = lambda^T J.  Device pointers; r, J, H, grad may each be NULL (y is needed for r, lambda
+ * for H and grad).  Asynchronous on `stream` (NULL = the net's stream). */
+int nnc_eval_kkt_dev(nnc_net* net, const double* x, const double* y, const double* lambda,
+                     double* r, double* J, double* H, double* grad, void* stream);
+/* Host-pointer twin of nnc_eval_kkt_dev (copies in, evaluates, copies out, waits). */
+int nnc_eval_kkt(nnc_net* net, const double* x, const double* y, const double* lambda, double* r,
+                 double* J, double* H, double* grad);
 
 /* ---- Grouped batch (many networks of equal hidden widths, different input sizes) ----------
  * One stability-margin surrogate per contingency of Eq. 8: K nets with the same depth, hidden
@@ -213,7 +224,10 @@ int nnc_tuning(const nnc_net* net, int layer, int* tangent_bn, int* syrk_splits)
  * was recorded); nnc_profile_read waits for the recorded work, then fills ms[k] (total
  * milliseconds) and count[k] (launches) for kernel kind k < n_kinds and clears the record:
  *   0 tangent GEMM, 1 symmetric product (Hessian accumulation), 2 forward layer,
- *   3 reverse layer, 4 other. */
+ *   3 reverse layer, 4 other.
+ * enable = 0 stops recording; enable > 1 records only the kinds whose bit (k + 1) is set, so that
+ * events do not sit between the forward layers, which overlap through programmatic dependent
+ * launch. */
 int nnc_profile(nnc_net* net, int enable);
 int nnc_profile_read(nnc_net* net, double* ms, long long* count, int n_kinds);
 

@@ -69,6 +69,54 @@ __device__ __forceinline__ void split_bf16(double v, __nv_bfloat16& hi, __nv_bfl
   hi = __double2bfloat16(v);
   lo = __double2bfloat16(v - (double)__bfloat162float(hi));
 }
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// One step of a double-float dot product (hi, lo) += (wh + wl)(ah + al): TwoProduct of the
+// leading terms with an FMA, the cross terms into the error part, TwoSum for the running sum
+// (Dekker 1971).  The _rn intrinsics keep the compiler from contracting the error-free steps.
+__device__ __forceinline__ void df_acc(float& hi, float& lo, float wh, float wl, float ah, float al) {
+  const float p = __fmul_rn(wh, ah);
+  const float pe = fmaf(wh, ah, -p);                  // exact error of p (TwoProduct)
+  const float cross = fmaf(wh, al, __fmul_rn(wl, ah));
+  const float s = __fadd_rn(hi, p);                    // TwoSum(hi, p)
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(e, __fadd_rn(pe, cross)));
+}
+
+// (h, l) += (bh, bl) in double-float arithmetic with FP32 operations only: TwoSum of the leading
+// terms, the trailing terms and the rounding error added, then a TwoSum renormalisation.  GB300
+// runs FP64 at a small fraction of its FP32 rate, so reductions of double-float sums stay in FP32.
+__device__ __forceinline__ void df_add(float& h, float& l, float bh, float bl) {
+  float s = __fadd_rn(h, bh);
+  float bb = __fsub_rn(s, h);
+  const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+  const float t = __fadd_rn(__fadd_rn(l, bl), e);
+  h = __fadd_rn(s, t);
+  bb = __fsub_rn(h, s);
+  l = __fadd_rn(__fsub_rn(s, __fsub_rn(h, bb)), __fsub_rn(t, bb));
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ void warp_sum_df(float& h, float& l) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, h, o);
+    const float ol = __shfl_xor_sync(0xffffffffu, l, o);
+    df_add(h, l, oh, ol);
+  }
+}
+
 // Three-way split v ~ p0 + p1 + p2, each part the BF16 rounding of what the earlier parts leave;
 // the residual is below 2^-24 |v| (outside the BF16 underflow range).
 __device__ __forceinline__ void split3_bf16(double v, __nv_bfloat16& p0, __nv_bfloat16& p1,

@@ -7,12 +7,6 @@
 
 namespace nnc {
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
 // ------------------------------------------------------------------ forward value pass
 // One warp per output row.  FP32 weights are multiplied in FP32 with four independent
 // partial sums per lane (32 terms each for k = 4096), which are summed in FP64.
@@ -385,18 +379,21 @@ cudaError_t launch_sub(const double* y, const double* a, double* r, int n, cudaS
   return cudaGetLastError();
 }
 
-__global__ void k_copy_pad(const double* src, double* dst, float* dst_f, int n, int n_pad) {
+__global__ void k_copy_pad(const double* src, double* dst, float2* dst2, int n, int n_pad) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n_pad) {
     const double v = i < n ? src[i] : 0.0;
     dst[i] = v;
-    if (dst_f) dst_f[i] = (float)v;
+    if (dst2) {
+      const float h = (float)v;
+      dst2[i] = make_float2(h, (float)(v - (double)h));
+    }
   }
 }
 
-cudaError_t launch_copy_pad(const double* src, double* dst, float* dst_f, int n, int n_pad,
+cudaError_t launch_copy_pad(const double* src, double* dst, void* dst2, int n, int n_pad,
                             cudaStream_t st) {
-  k_copy_pad<<<(n_pad + 255) / 256, 256, 0, st>>>(src, dst, dst_f, n, n_pad);
+  k_copy_pad<<<(n_pad + 255) / 256, 256, 0, st>>>(src, dst, (float2*)dst2, n, n_pad);
   note_launch();
   return cudaGetLastError();
 }
@@ -619,65 +616,10 @@ cudaError_t launch_rev_reduce_t(const float* P, int splits, int kcols, int bn, i
 
 namespace nnc {
 
-// ------------------------------------------------------------------ FP64 residual in double-float
-// GB300's FP64 units are too slow for an FP64 GEMV to run at HBM speed, so the FP64 value pass is
-// computed in double-float arithmetic (Dekker 1971; a value is an unevaluated sum hi + lo of two
-// FP32 numbers): weights are packed once as (hi, lo) pairs with hi = fl32(w), lo = fl32(w - hi),
-// activations likewise.  Per product, hi_w * hi_a is split exactly with an FMA (TwoProduct), the
-// cross terms hi_w lo_a + lo_w hi_a are added to the error part, and the running sum uses
-// TwoSum.  The result carries about 48 significant bits (relative error ~1e-14 per layer), which
-// the FP64 residual needs (1e-10), at eight bytes per weight (the same traffic as FP64).
-// The _rn intrinsics keep the compiler from contracting the error-free steps into FMAs.
-__device__ __forceinline__ void df_acc(float& hi, float& lo, float wh, float wl, float ah, float al) {
-  const float p = __fmul_rn(wh, ah);
-  const float pe = fmaf(wh, ah, -p);                  // exact error of p (TwoProduct)
-  const float cross = fmaf(wh, al, __fmul_rn(wl, ah));
-  const float s = __fadd_rn(hi, p);                    // TwoSum(hi, p)
-  const float bb = __fsub_rn(s, hi);
-  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-  hi = s;
-  lo = __fadd_rn(lo, __fadd_rn(e, __fadd_rn(pe, cross)));
-}
-
-__global__ void __launch_bounds__(256) k_gemv_fwd_df(const float4* __restrict__ W, int ld2,
-                                                     const double* __restrict__ bias,
-                                                     const float4* __restrict__ a_in, int m, int act,
-                                                     double* __restrict__ a_out,
-                                                     float2* __restrict__ a_out2) {
-  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (row >= m) return;
-  const float4* w = W + (size_t)row * ld2;     // ld2 float4 per row = two weights each
-  float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
-#pragma unroll 4
-  for (int j = lane; j < ld2; j += 32) {
-    const float4 ww = __ldg(w + j);
-    const float4 aa = a_in[j];
-    df_acc(h0, l0, ww.x, ww.y, aa.x, aa.y);
-    df_acc(h1, l1, ww.z, ww.w, aa.z, aa.w);
-  }
-  double acc = ((double)h0 + (double)l0) + ((double)h1 + (double)l1);
-  acc = warp_sum(acc);
-  if (lane == 0) {
-    double a, d1, d2;
-    act_eval(act, acc + (bias ? bias[row] : 0.0), a, d1, d2);
-    a_out[row] = a;
-    if (a_out2) {
-      const float ah = (float)a;
-      a_out2[row] = make_float2(ah, (float)(a - (double)ah));
-    }
-  }
-}
-
-cudaError_t launch_gemv_fwd_df(const void* W2, int kp, const double* b, const void* a_in2, int m,
-                               int act, double* a_out, void* a_out2, cudaStream_t st) {
-  const int blocks = (m * 32 + 255) / 256;
-  k_gemv_fwd_df<<<blocks, 256, 0, st>>>((const float4*)W2, kp / 2, b, (const float4*)a_in2, m, act,
-                                        a_out, (float2*)a_out2);
-  note_launch();
-  return cudaGetLastError();
-}
-
+// ------------------------------------------------------------------ double-float packing
+// GB300's FP64 units are too slow for an FP64 GEMV to run at HBM speed, so the FP64-accurate value
+// pass (k_stream.cu) runs in double-float arithmetic (Dekker 1971): a value is the unevaluated sum
+// hi + lo of two FP32 numbers, hi = fl32(v), lo = fl32(v - hi).
 // (hi, lo) float pairs of an FP64 array (weights at load time, the network input per call).
 __global__ void k_split_df(const double* __restrict__ src, size_t n, float2* __restrict__ dst) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {

@@ -47,8 +47,9 @@ cudaError_t launch_h_finish(bool part_f32, const void* Hp, int splits, int n, in
                             cudaStream_t st);
 // r = y - a  (FP64)
 cudaError_t launch_sub(const double* y, const double* a, double* r, int n, cudaStream_t st);
-// dst[i] = src[i] (double) for i < n; zero for n <= i < n_pad; dst_f (may be NULL) a float copy
-cudaError_t launch_copy_pad(const double* src, double* dst, float* dst_f, int n, int n_pad,
+// dst[i] = src[i] (double) for i < n; zero for n <= i < n_pad; dst2 (float2, may be NULL) its
+// double-float (hi, lo) pairs
+cudaError_t launch_copy_pad(const double* src, double* dst, void* dst2, int n, int n_pad,
                             cudaStream_t st);
 
 // ---- CUDA-core GEMMs for the FP64 / FP32 forms (k_simt.cu)
@@ -79,6 +80,16 @@ cudaError_t launch_quant_fp8(const void* A, int rows, int ld, unsigned char* A8,
 }  // namespace nnc
 
 namespace nnc {
+// Streaming value-pass layer in double-float arithmetic (k_stream.cu), launched with
+// programmatic dependent launch: z = W a_in + b from (hi, lo) float2 weights and activations;
+// a_out = sigma(z), a_df its (hi, lo) float2 copy, s1 = sigma'(z), s2 = sigma''(z) (each may be
+// NULL).  ldw (elements per row) must be a multiple of 128.
+cudaError_t launch_gemv_stream_df(const void* W2, int ldw, int m, const double* b, const void* a_in2,
+                                  int act, double* a_out, void* a_df, double* s1, double* s2,
+                                  int* err, int sm_count, cudaStream_t st);
+}  // namespace nnc
+
+namespace nnc {
 // Tensor-core reverse sweep helpers (see k_vector.cu).
 // Operands are split three ways into BF16 parts (W^T: p0/p1/p2; seeds: z[0..2]).
 cudaError_t launch_pack_t(const double* W, int mp, int kp, __nv_bfloat16* p0, __nv_bfloat16* p1,
@@ -93,9 +104,5 @@ cudaError_t launch_rev_reduce_t(const float* P, int splits, int kcols, int bn, i
 }  // namespace nnc
 
 namespace nnc {
-// FP64 value pass in double-float arithmetic (see k_vector.cu): W2 = (hi, lo) pairs [mp][kp],
-// a_in2 = (hi, lo) pairs of the layer input; writes a_out (FP64) and its pairs a_out2.
-cudaError_t launch_gemv_fwd_df(const void* W2, int kp, const double* b, const void* a_in2, int m,
-                               int act, double* a_out, void* a_out2, cudaStream_t st);
 cudaError_t launch_split_df(const double* src, size_t n, void* dst, cudaStream_t st);
 }  // namespace nnc

@@ -37,7 +37,7 @@ struct LayerDev {
   double* ra = nullptr;           // FP64-residual pass activations [mp]
   void* ra2 = nullptr;            // their double-float (hi, lo) pairs [mp] (float2)
   void* W2 = nullptr;             // double-float (hi, lo) pairs of W [mp][kp] (float2)
-  float* af = nullptr;            // FP32 copy of a_l [mp] (input of the next FP32 layer)
+  void* a2 = nullptr;             // double-float (hi, lo) pairs of a_l [mp] (float2)
   nnc::TcPlan plan_tan;                // tensor-core plan of this layer's tangent GEMM
   int zy_off = -1;                // column offset of this layer's Zdot / Ydot block (-1: none)
 };
@@ -50,7 +50,7 @@ struct nnc_net {
   int device = 0, sm_count = 0;
   std::vector<void*> allocs;
   double* x = nullptr;       // a_0 [n_in_pad]
-  float* xf = nullptr;       // FP32 copy of a_0 [n_in_pad]
+  void* x2 = nullptr;        // double-float (hi, lo) pairs of a_0 [n_in_pad] (float2)
   double* xin = nullptr;     // host-call staging of x [n_in_pad]
   double* xr = nullptr;      // input of the FP64 residual pass [n_in_pad] (its own copy, so that
                              // a residual may run on another stream next to an evaluation)
@@ -82,7 +82,7 @@ struct nnc_net {
   size_t h_stage_elems = 0;
   size_t bytes = 0;
   // optional per-kernel-kind CUDA-event timing (nnc_profile)
-  bool prof = false;
+  unsigned prof_mask = 0;   // kernel kinds whose launches are bracketed by events
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   std::vector<int> ev_kind;

@@ -106,7 +106,8 @@ struct ProfScope {
   cudaStream_t st;
   bool on;
   size_t idx = 0;
-  ProfScope(nnc_net* n, int kind, cudaStream_t s) : net(n), st(s), on(n->prof) {
+  ProfScope(nnc_net* n, int kind, cudaStream_t s)
+      : net(n), st(s), on(((n->prof_mask >> kind) & 1u) != 0) {
     if (!on) return;
     while (net->ev_used + 2 > net->ev_pool.size()) {
       cudaEvent_t e;
@@ -128,13 +129,26 @@ struct ProfScope {
 #define PROF(kind) ProfScope prof_scope_(net, kind, st)
 
 // ---------------------------------------------------------------- forward value pass
+// FP64 form: FP64 GEMV layers.  Other forms: one double-float streaming pass (about 48
+// significant bits) whose sigma, sigma' and sigma'' feed the derivative sweeps; expects net->x and
+// its pairs net->x2 (launch_copy_pad).
 int run_forward(nnc_net* net, bool fp64, cudaStream_t st) {
-  const void* a_in = fp64 ? (const void*)net->x : (const void*)net->xf;
+  if (fp64) {
+    const double* a_in = net->x;
+    for (auto& Ly : net->layers) {
+      PROF(PK_FWD);
+      CK(launch_gemv_fwd(true, Ly.W64, Ly.kp, Ly.b, a_in, Ly.m, Ly.kp, Ly.act, Ly.a, nullptr, Ly.s1,
+                         Ly.s2, st));
+      a_in = Ly.a;
+    }
+    return NNC_OK;
+  }
+  const void* a_in2 = net->x2;
   for (auto& Ly : net->layers) {
     PROF(PK_FWD);
-    CK(launch_gemv_fwd(fp64, fp64 ? (const void*)Ly.W64 : (const void*)Ly.W32, Ly.kp, Ly.b, a_in,
-                       Ly.m, Ly.kp, Ly.act, Ly.a, fp64 ? nullptr : Ly.af, Ly.s1, Ly.s2, st));
-    a_in = fp64 ? (const void*)Ly.a : (const void*)Ly.af;
+    CK(launch_gemv_stream_df(Ly.W2, Ly.kp, Ly.m, Ly.b, a_in2, Ly.act, Ly.a, Ly.a2, Ly.s1, Ly.s2,
+                             net->dev_err, net->sm_count, st));
+    a_in2 = Ly.a2;
   }
   return NNC_OK;
 }
@@ -142,7 +156,8 @@ int run_forward(nnc_net* net, bool fp64, cudaStream_t st) {
 // FP64 value pass of the residual y - NN(x) from the raw device input x.  The FP64 form runs it
 // in FP64; the other forms in double-float arithmetic (about 48 significant bits, HBM-bound).
 int run_forward_fp64_values(nnc_net* net, const double* x, cudaStream_t st) {
-  CK(launch_copy_pad(x, net->xr, nullptr, net->n_in, net->n_in_pad, st));
+  CK(launch_copy_pad(x, net->xr, net->prec == NNC_FP64 ? nullptr : net->xr2, net->n_in,
+                     net->n_in_pad, st));
   if (net->prec == NNC_FP64) {
     const double* a_in = net->xr;
     for (auto& Ly : net->layers) {
@@ -153,11 +168,11 @@ int run_forward_fp64_values(nnc_net* net, const double* x, cudaStream_t st) {
     }
     return NNC_OK;
   }
-  CK(launch_split_df(net->xr, net->n_in_pad, net->xr2, st));
   const void* a_in2 = net->xr2;
   for (auto& Ly : net->layers) {
     PROF(PK_FWD);
-    CK(launch_gemv_fwd_df(Ly.W2, Ly.kp, Ly.b, a_in2, Ly.m, Ly.act, Ly.ra, Ly.ra2, st));
+    CK(launch_gemv_stream_df(Ly.W2, Ly.kp, Ly.m, Ly.b, a_in2, Ly.act, Ly.ra, Ly.ra2, nullptr,
+                             nullptr, net->dev_err, net->sm_count, st));
     a_in2 = Ly.ra2;
   }
   return NNC_OK;
@@ -289,15 +304,18 @@ int run_hessian(nnc_net* net, double* H, cudaStream_t st) {
   return NNC_OK;
 }
 
+// One value pass at x, then whatever is asked: y = NN(x), the residual rr = yv - NN(x), J, H and
+// the gradient lambda^T J.
 int eval_all(nnc_net* net, const double* x, const double* lam, double* y, double* J, double* H,
-             double* g, cudaStream_t st) {
-  CK(launch_copy_pad(x, net->x, net->xf, net->n_in, net->n_in_pad, st));
+             double* g, cudaStream_t st, const double* yv = nullptr, double* rr = nullptr) {
+  CK(launch_copy_pad(x, net->x, net->x2, net->n_in, net->n_in_pad, st));
   const bool fp64 = net->prec == NNC_FP64;
   int r = run_forward(net, fp64, st);
   if (r != NNC_OK) return r;
   if (y)
     CK(cudaMemcpyAsync(y, net->layers.back().a, sizeof(double) * net->n_out,
                        cudaMemcpyDeviceToDevice, st));
+  if (rr) CK(launch_sub(yv, net->layers.back().a, rr, net->n_out, st));
   const bool need_lam = (H != nullptr) || (g != nullptr);
   if (J || need_lam) {
     r = run_reverse(net, fp64, J ? net->n_out : 0, need_lam, lam, J, g, st);
@@ -317,7 +335,7 @@ int check_net(const nnc_net* net) {
 
 // Host-pointer wrapper: copy inputs in, run, copy outputs out, wait.
 int host_call(nnc_net* net, const double* x, const double* lam, double* y, double* J, double* H,
-              double* g) {
+              double* g, const double* yv = nullptr, double* rr = nullptr) {
   int r = check_net(net);
   if (r) return r;
   if (!x) return fail(NNC_ERR_ARG, "x is NULL");
@@ -332,13 +350,20 @@ int host_call(nnc_net* net, const double* x, const double* lam, double* y, doubl
   cudaStream_t st = net->stream;
   double* hs = net->h_stage;
   std::memcpy(hs, x, sizeof(double) * net->n_in);
-  if (lam) std::memcpy(hs + net->n_in, lam, sizeof(double) * net->n_out);
+  double* hl = hs + net->n_in_pad;
+  double* hy = hl + net->n_out;
+  if (lam) std::memcpy(hl, lam, sizeof(double) * net->n_out);
   CK(cudaMemcpyAsync(net->xin, hs, sizeof(double) * net->n_in, cudaMemcpyHostToDevice, st));
-  if (lam) CK(cudaMemcpyAsync(net->lam, hs + net->n_in, sizeof(double) * net->n_out,
-                              cudaMemcpyHostToDevice, st));
+  if (lam) CK(cudaMemcpyAsync(net->lam, hl, sizeof(double) * net->n_out, cudaMemcpyHostToDevice, st));
+  if (rr) {
+    std::memcpy(hy, yv, sizeof(double) * net->n_out);
+    CK(cudaMemcpyAsync(net->yres, hy, sizeof(double) * net->n_out, cudaMemcpyHostToDevice, st));
+  }
   r = eval_all(net, net->xin, lam ? net->lam : nullptr, y ? net->ydev : nullptr,
-               J ? net->Jdev : nullptr, H ? net->Hdev : nullptr, g ? net->gdev : nullptr, st);
+               J ? net->Jdev : nullptr, H ? net->Hdev : nullptr, g ? net->gdev : nullptr, st,
+               rr ? net->yres : nullptr, rr ? net->rdev : nullptr);
   if (r) return r;
+  if (rr) CK(cudaMemcpyAsync(rr, net->rdev, sizeof(double) * net->n_out, cudaMemcpyDeviceToHost, st));
   if (y) CK(cudaMemcpyAsync(y, net->ydev, sizeof(double) * net->n_out, cudaMemcpyDeviceToHost, st));
   if (J) CK(cudaMemcpyAsync(J, net->Jdev, sizeof(double) * net->n_out * net->n_in,
                             cudaMemcpyDeviceToHost, st));
@@ -362,7 +387,8 @@ long long nnc_launch_count(void) { return g_launches.load(); }
 int nnc_profile(nnc_net* net, int enable) {
   int r = check_net(net);
   if (r) return r;
-  net->prof = enable != 0;
+  // 1: every kind; other nonzero values: a mask of kinds, bit (k + 1) for kind k
+  net->prof_mask = enable == 0 ? 0u : enable == 1 ? ~0u : (unsigned)enable >> 1;
   net->ev_used = 0;
   net->ev_kind.clear();
   return NNC_OK;
@@ -469,8 +495,10 @@ static int load_impl(nnc_net* net, int n_layers, const int* widths, const int* a
     AL(Ly.s2, Ly.mp);
     AL(Ly.c, Ly.mp);
     AL(Ly.ra, Ly.mp);
-    AL(Ly.af, Ly.mp);
     if (prec != NNC_FP64) {
+      float2* a2;
+      AL(a2, Ly.mp);
+      Ly.a2 = a2;
       float2* w2;
       AL(w2, nw);
       Ly.W2 = w2;
@@ -486,7 +514,11 @@ static int load_impl(nnc_net* net, int n_layers, const int* widths, const int* a
   net->mp_max = mp_max;
   AL(net->x, net->n_in_pad);
   AL(net->xin, net->n_in_pad);
-  AL(net->xf, net->n_in_pad);
+  {
+    float2* x2;
+    AL(x2, net->n_in_pad);
+    net->x2 = x2;
+  }
   AL(net->xr, net->n_in_pad);
   AL(net->yres, net->n_out);
   {
@@ -593,7 +625,8 @@ static int load_impl(nnc_net* net, int n_layers, const int* widths, const int* a
     AL(hp, (size_t)splits * n * n);
     net->Hp = hp;
   }
-  net->h_stage_elems = (size_t)net->n_in_pad + net->n_out;
+  // pinned staging of the host calls: x [n_in_pad] | lambda [n_out] | y [n_out]
+  net->h_stage_elems = (size_t)net->n_in_pad + 2 * (size_t)net->n_out;
   CK(cudaMallocHost(&net->h_stage, sizeof(double) * net->h_stage_elems));
   CK(cudaStreamSynchronize(net->stream));
   return NNC_OK;
@@ -659,7 +692,7 @@ int nnc_eval_dev(nnc_net* net, const double* x, double* y, int fp64_residual, vo
   if (fp64_residual) {
     r = run_forward_fp64_values(net, x, st);
   } else {
-    CK(launch_copy_pad(x, net->x, net->xf, net->n_in, net->n_in_pad, st));
+    CK(launch_copy_pad(x, net->x, net->x2, net->n_in, net->n_in_pad, st));
     r = run_forward(net, net->prec == NNC_FP64, st);
   }
   if (r) return r;
@@ -688,9 +721,10 @@ int nnc_residual(nnc_net* net, const double* x, const double* y, double* rr) {
   CK(cudaSetDevice(net->device));
   cudaStream_t st = net->stream;
   std::memcpy(net->h_stage, x, sizeof(double) * net->n_in);
-  std::memcpy(net->h_stage + net->n_in_pad, y, sizeof(double) * net->n_out);
+  double* hy = net->h_stage + net->n_in_pad + net->n_out;
+  std::memcpy(hy, y, sizeof(double) * net->n_out);
   CK(cudaMemcpyAsync(net->xin, net->h_stage, sizeof(double) * net->n_in, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(net->yres, net->h_stage + net->n_in_pad, sizeof(double) * net->n_out,
+  CK(cudaMemcpyAsync(net->yres, hy, sizeof(double) * net->n_out,
                      cudaMemcpyHostToDevice, st));
   r = nnc_residual_dev(net, net->xin, net->yres, net->rdev, st);
   if (r) return r;
@@ -731,6 +765,26 @@ int nnc_eval_all_dev(nnc_net* net, const double* x, const double* lambda, double
   if (!x) return fail(NNC_ERR_ARG, "x is NULL");
   if ((H || grad) && !lambda) return fail(NNC_ERR_ARG, "lambda is NULL");
   return eval_all(net, x, lambda, y, J, H, grad, pick(net, stream));
+}
+
+int nnc_eval_kkt(nnc_net* net, const double* x, const double* y, const double* lambda, double* r,
+                 double* J, double* H, double* grad) {
+  if (r && !y) return fail(NNC_ERR_ARG, "y is NULL");
+  if (y) {
+    const int rc = check_finite(y, net ? net->n_out : 0, "y");
+    if (rc) return rc;
+  }
+  return host_call(net, x, lambda, nullptr, J, H, grad, y, r);
+}
+
+int nnc_eval_kkt_dev(nnc_net* net, const double* x, const double* y, const double* lambda,
+                     double* r, double* J, double* H, double* grad, void* stream) {
+  int rc = check_net(net);
+  if (rc) return rc;
+  if (!x) return fail(NNC_ERR_ARG, "x is NULL");
+  if (r && !y) return fail(NNC_ERR_ARG, "y is NULL");
+  if ((H || grad) && !lambda) return fail(NNC_ERR_ARG, "lambda is NULL");
+  return eval_all(net, x, lambda, nullptr, J, H, grad, pick(net, stream), y, r);
 }
 
 int nnc_eval_batched(nnc_net* const* nets, int K, const double* const* x,

@@ -23,7 +23,7 @@ STATUS = {0: "NNC_OK", -1: "NNC_ERR_ARG", -2: "NNC_ERR_CUDA", -3: "NNC_ERR_NONFI
 # Every symbol that include/nnc.h declares.
 EXPORTS = ["nnc_load_weights", "nnc_eval", "nnc_residual", "nnc_jacobian", "nnc_hessian_lag",
            "nnc_eval_batched", "nnc_eval_dev", "nnc_residual_dev", "nnc_jacobian_dev",
-           "nnc_hessian_lag_dev", "nnc_eval_all_dev", "nnc_free", "nnc_last_error",
+           "nnc_hessian_lag_dev", "nnc_eval_all_dev", "nnc_eval_kkt_dev", "nnc_eval_kkt", "nnc_free", "nnc_last_error",
            "nnc_net_info", "nnc_launch_count", "nnc_profile", "nnc_profile_read",
            "nnc_ipm_default_options", "nnc_ipm_adversarial", "nnc_kkt_solve",
            "nnc_residual_noalloc", "nnc_batch_create", "nnc_batch_free", "nnc_batch_info",
@@ -99,6 +99,8 @@ def load_library(path: str = LIB_PATH):
     lib.nnc_jacobian_dev.argtypes = [_P, _P, _P, _P]
     lib.nnc_hessian_lag_dev.argtypes = [_P, _P, _P, _P, _P, _P]
     lib.nnc_eval_all_dev.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P]
+    lib.nnc_eval_kkt_dev.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _P]
+    lib.nnc_eval_kkt.argtypes = [_P, _DP, _DP, _DP, _DP, _DP, _DP, _DP]
     lib.nnc_free.argtypes = [_P]
     lib.nnc_free.restype = None
     lib.nnc_ipm_default_options.restype = None
@@ -258,6 +260,16 @@ class Net:
                                     _dp(g) if want_grad else None))
         return (H, g) if want_grad else H
 
+    def eval_kkt(self, x, y, lam):
+        """nnc_eval_kkt: (r = y - NN(x), J, H, grad = lambda^T J) at one iterate, one value pass."""
+        x, y, lam = _f64(x), _f64(y), _f64(lam)
+        r = np.empty(self.n_out)
+        J = np.empty((self.n_out, self.n_in))
+        H = np.empty((self.n_in, self.n_in))
+        g = np.empty(self.n_in)
+        _check(_lib.nnc_eval_kkt(self._h, _dp(x), _dp(y), _dp(lam), _dp(r), _dp(J), _dp(H), _dp(g)))
+        return r, J, H, g
+
     def autotune(self, cache_path=None, retune=False):
         """nnc_autotune: time the tile / split candidates and keep the fastest (JSON cache optional)."""
         _check(_lib.nnc_autotune(self._h, cache_path.encode() if cache_path else None, int(bool(retune))))
@@ -267,8 +279,14 @@ class Net:
         _check(_lib.nnc_tuning(self._h, int(layer), ctypes.byref(bn), ctypes.byref(sp)))
         return bn.value, sp.value
 
-    def profile(self, enable=True):
-        _check(_lib.nnc_profile(self._h, int(bool(enable))))
+    def profile(self, enable=True, kinds=None):
+        """Start (or stop) event timing of the library's launches; `kinds` (names of
+        PROFILE_KINDS) limits it to those kernel kinds."""
+        if enable and kinds:
+            mask = sum(1 << (PROFILE_KINDS.index(k) + 1) for k in kinds)
+            _check(_lib.nnc_profile(self._h, mask))
+        else:
+            _check(_lib.nnc_profile(self._h, int(bool(enable))))
 
     def profile_read(self):
         """{kind: (total ms, launches)} recorded since profile(True) (and clears the record)."""
@@ -296,6 +314,11 @@ class Net:
     def eval_all_dev(self, x, lam=None, y=None, J=None, H=None, grad=None, stream=None):
         _check(_lib.nnc_eval_all_dev(self._h, _tp(x), _tp(lam), _tp(y), _tp(J), _tp(H), _tp(grad),
                                      stream or _stream_ptr()))
+
+    def eval_kkt_dev(self, x, y=None, lam=None, r=None, J=None, H=None, grad=None, stream=None):
+        """nnc_eval_kkt_dev: r = y - NN(x), J, H, grad at one iterate from a single value pass."""
+        _check(_lib.nnc_eval_kkt_dev(self._h, _tp(x), _tp(y), _tp(lam), _tp(r), _tp(J), _tp(H),
+                                     _tp(grad), stream or _stream_ptr()))
 
 
 def eval_batched(nets, xs, lams=None, what=WANT_Y | WANT_J | WANT_H):

@@ -56,6 +56,10 @@ def _check_all(nnc, mlp, x, lam, prec, label=""):
     assert np.max(np.abs(r)) <= 1e-10 * max(1.0, np.max(np.abs(yo))), r
     y64 = net.eval(x, fp64_residual=True)
     assert rel(y64, yo) < 1e-12
+    # the fused iterate call: same derivatives, FP64-accurate residual from its one value pass
+    rk, Jk, Hk, gk = net.eval_kkt(x, yo, lam)
+    assert np.max(np.abs(rk)) <= 1e-10 * max(1.0, np.max(np.abs(yo))), rk
+    assert np.array_equal(Jk, J) and np.array_equal(Hk, H) and np.array_equal(gk, g)
     net.free()
     return e
 
