@@ -55,6 +55,63 @@ __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, int* err,
   }
 }
 
+// As mbar_wait, but gives up early once *abort_flag is set (by another thread of the CTA), and
+// sets it when the wait runs out.
+__device__ __forceinline__ bool mbar_wait_abort(uint32_t a, uint32_t parity, int* err, int code,
+                                                volatile int* abort_flag,
+                                                long long limit = kWaitCycles) {
+  if (mbar_try(a, parity)) return true;
+  const long long t0 = clock64();
+  while (true) {
+    if (mbar_try(a, parity)) return true;
+    if (*abort_flag) return false;
+    if (clock64() - t0 > limit) {
+      if (err) atomicCAS(err, 0, code);
+      *abort_flag = 1;
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+
+// 2-D tiled TMA load of one box at element coordinates (x = inner, y = outer) into `dst`.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* map, uint32_t mbar, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(mbar), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Barrier among the first `threads` threads of the CTA (named barrier `id`, 1..15).
+__device__ __forceinline__ void named_sync(int id, int threads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+// Thread-block clusters: rank of this CTA, a full cluster barrier (release / acquire: shared
+// memory written before it is visible to the other CTAs after it), and a load from the shared
+// memory of CTA `rank` of the cluster at the address that `local` has in this CTA.
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+__device__ __forceinline__ float ld_dsmem_f32(uint32_t local, uint32_t rank) {
+  uint32_t remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(rank));
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(remote) : "memory");
+  return v;
+}
+
 // `bytes` (a multiple of 16) from global `src` to shared `dst` (both 16-byte aligned); the
 // transaction count of mbarrier `mbar` is decremented as the bytes land.
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,

@@ -422,10 +422,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             float* hp = KIND == TC_SYRK
                             ? args.Hp + ((size_t)split * args.N + i) * args.N
                             : args.Hp + split * args.ldh_split + args.g_hoff[grp] + (size_t)i * n_valid;
+            // TC_SYRK: every (split, tile) has exactly one CTA and every split at least one K
+            // block, so the partial is stored (the buffer needs no clearing); the grouped form
+            // accumulates into a cleared buffer
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
               const int n = n0 + c0 + j;
-              if (n <= i) hp[n] += v[j];
+              if (n <= i) {
+                if (KIND == TC_SYRK) hp[n] = v[j];
+                else hp[n] += v[j];
+              }
             }
           }
         }

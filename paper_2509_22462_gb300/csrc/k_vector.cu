@@ -3,6 +3,7 @@
 // and the small reductions around them.  All read weights once, coalesced and vectorised.
 #include <type_traits>
 
+#include "async.cuh"
 #include "kernels.cuh"
 
 namespace nnc {
@@ -187,6 +188,7 @@ __global__ void k_rev_reduce(const TP* __restrict__ part, int chunks, int kcols,
                              int lam_col, int nJ, double* __restrict__ Zbar_out,
                              double* __restrict__ c_out, float* __restrict__ c_out_f,
                              double* __restrict__ J_out, double* __restrict__ g_out) {
+  async::griddep_launch();  // the next layer's streaming kernel may start fetching its weights
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= kcols * S) return;
   const int kk = idx / S, s = idx % S;
@@ -227,6 +229,7 @@ __global__ void k_rev_seed(int m, int S, int nJ, int lam_col, const double* __re
                            const double* __restrict__ s2, const double* __restrict__ lam,
                            double* __restrict__ Zbar, double* __restrict__ c_out,
                            float* __restrict__ c_out_f) {
+  async::griddep_launch();
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= m * S) return;
   const int i = idx / S, s = idx % S;
@@ -302,9 +305,89 @@ __global__ void k_first_tangent(const TW* __restrict__ W1, int ldw, int m_pad, i
   }
 }
 
+// BF16 forms: 64 rows of W_1 x 32 tangents per block through a shared tile; a thread converts 8
+// consecutive rows of one tangent and writes each output part as one 16-byte vector.
+template <bool X3>
+__global__ void __launch_bounds__(256) k_first_tangent_v(const float* __restrict__ W1, int ldw,
+                                                         int m_pad, int n,
+                                                         const double* __restrict__ s1,
+                                                         const double* __restrict__ c, TanBuf At,
+                                                         int lda, TanBuf Zt, TanBuf Yt, int ldz) {
+  __shared__ float tile[64][33];
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 32;
+  const int t = threadIdx.x, j = t / 8, q = t % 8;   // tangent n0 + j, rows m0 + 8q .. + 7
+  const int nn = n0 + j, mb = m0 + 8 * q;
+  // all global loads first (independent, so they are in flight together)
+  float wv[8], sv[8], cv[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int mm = m0 + t / 32 + 8 * i, nc = n0 + (t & 31);
+    wv[i] = (mm < m_pad && nc < n) ? __ldg(W1 + (size_t)mm * ldw + nc) : 0.f;
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const bool in = mb + i < m_pad;
+    sv[i] = in ? (float)__ldg(s1 + mb + i) : 0.f;
+    cv[i] = in ? (float)__ldg(c + mb + i) : 0.f;
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) tile[t / 32 + 8 * i][t & 31] = wv[i];
+  __syncthreads();
+  if (nn >= n || mb >= m_pad) return;
+  uint32_t ah[4], al[4], zh[4], zl[4], yh[4], yl[4];
+#pragma unroll
+  for (int e = 0; e < 8; e += 2) {
+    float a2[2], z2[2], y2[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const float w = tile[8 * q + e + u][j];
+      z2[u] = w;
+      a2[u] = sv[e + u] * w;
+      y2[u] = cv[e + u] * w;
+    }
+    auto pk = [](float v0, float v1, uint32_t& hi, uint32_t& lo) {
+      __nv_bfloat16 h0, l0, h1, l1;
+      split_bf16(v0, h0, l0);
+      split_bf16(v1, h1, l1);
+      hi = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+      lo = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+    };
+    pk(a2[0], a2[1], ah[e / 2], al[e / 2]);
+    pk(z2[0], z2[1], zh[e / 2], zl[e / 2]);
+    pk(y2[0], y2[1], yh[e / 2], yl[e / 2]);
+  }
+  auto st16 = [](void* base, size_t idx, const uint32_t (&v)[4]) {
+    *reinterpret_cast<uint4*>((__nv_bfloat16*)base + idx) = make_uint4(v[0], v[1], v[2], v[3]);
+  };
+  if (At.hi) {
+    st16(At.hi, (size_t)nn * lda + mb, ah);
+    if (X3) st16(At.lo, (size_t)nn * lda + mb, al);
+  }
+  if (Zt.hi) {
+    st16(Zt.hi, (size_t)nn * ldz + mb, zh);
+    st16(Yt.hi, (size_t)nn * ldz + mb, yh);
+    if (X3) {
+      st16(Zt.lo, (size_t)nn * ldz + mb, zl);
+      st16(Yt.lo, (size_t)nn * ldz + mb, yl);
+    }
+  }
+}
+
 cudaError_t launch_first_tangent(Elem e, const void* W1, int ldw, int m_pad, int n,
                                  const double* s1, const double* c, TanBuf At, int lda, TanBuf Zt,
                                  TanBuf Yt, int ldz, cudaStream_t st) {
+  if ((e == Elem::BF16 || e == Elem::BF16X3) && m_pad % 64 == 0 && lda % 8 == 0 && ldz % 8 == 0) {
+    // (Zt / Yt already point at the layer's column block, whose offset is a multiple of 128)
+    dim3 g((n + 31) / 32, m_pad / 64);
+    if (e == Elem::BF16X3)
+      k_first_tangent_v<true><<<g, 256, 0, st>>>((const float*)W1, ldw, m_pad, n, s1, c, At, lda,
+                                                 Zt, Yt, ldz);
+    else
+      k_first_tangent_v<false><<<g, 256, 0, st>>>((const float*)W1, ldw, m_pad, n, s1, c, At, lda,
+                                                  Zt, Yt, ldz);
+    note_launch();
+    return cudaGetLastError();
+  }
   dim3 grid((n + 31) / 32, (m_pad + 31) / 32), block(32, 8);
   const float* Wf = (const float*)W1;
   switch (e) {
@@ -357,13 +440,47 @@ __global__ void k_h_finish(const TP* __restrict__ Hp, int splits, int n, int ldp
   }
 }
 
+// FP32 partials (tensor-core forms): one block per lower 32 x 32 tile (bi >= bj) sums the splits
+// in FP32 (GB300's FP64 rate is a small fraction of FP32's; the partials carry FP32 accuracy
+// anyway), then writes the tile and its mirror, each coalesced.  Only R >= C entries of the
+// partials are read (the upper triangle of a diagonal tile is not written by the product).
+__global__ void __launch_bounds__(1024) k_h_finish_f32(const float* __restrict__ Hp, int splits,
+                                                       int n, int ldp, double* __restrict__ H) {
+  __shared__ float t[32][33];
+  int b = blockIdx.x, bi = 0;
+  while (b > bi) b -= ++bi;          // lower-tile index -> (bi, bj), bj = b <= bi
+  const int bj = b;
+  const int i0 = bi * 32, j0 = bj * 32, rr = threadIdx.y, x = threadIdx.x;
+  {
+    const int r = i0 + rr, c = j0 + x;
+    float v = 0.f;
+    if (r < n && c < n) {
+      const int R = r >= c ? r : c, C = r >= c ? c : r;
+      const float* p = Hp + (size_t)R * ldp + C;
+      const size_t plane = (size_t)n * ldp;
+#pragma unroll 8
+      for (int s = 0; s < splits; ++s) v += __ldg(p + s * plane);
+    }
+    t[rr][x] = v;
+  }
+  __syncthreads();
+  const int i = i0 + rr, j = j0 + x;
+  if (i < n && j < n) H[(size_t)i * n + j] = (double)t[rr][x];
+  if (bi != bj) {
+    const int i2 = j0 + rr, j2 = i0 + x;   // mirror tile H[j0..][i0..]
+    if (i2 < n && j2 < n) H[(size_t)i2 * n + j2] = (double)t[x][rr];
+  }
+}
+
 cudaError_t launch_h_finish(bool part_f32, const void* Hp, int splits, int n, int ldp, double* H,
                             cudaStream_t st) {
-  dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
-  if (part_f32)
-    k_h_finish<float><<<grid, block, 0, st>>>((const float*)Hp, splits, n, ldp, H);
-  else
+  const int T = (n + 31) / 32;
+  if (part_f32) {
+    k_h_finish_f32<<<T * (T + 1) / 2, dim3(32, 32), 0, st>>>((const float*)Hp, splits, n, ldp, H);
+  } else {
+    dim3 grid(T, T), block(32, 8);
     k_h_finish<double><<<grid, block, 0, st>>>((const double*)Hp, splits, n, ldp, H);
+  }
   note_launch();
   return cudaGetLastError();
 }

@@ -1,6 +1,8 @@
 // Launch wrappers of libnnc's kernels (host side).  Every wrapper queues work on `st` and
 // returns the cudaError_t of the launch.
 #pragma once
+#include <cuda.h>
+
 #include "common.cuh"
 
 namespace nnc {
@@ -87,6 +89,34 @@ namespace nnc {
 cudaError_t launch_gemv_stream_df(const void* W2, int ldw, int m, const double* b, const void* a_in2,
                                   int act, double* a_out, void* a_df, double* s1, double* s2,
                                   int* err, int sm_count, cudaStream_t st);
+}  // namespace nnc
+
+namespace nnc {
+// Streaming FP32 reverse sweep (k_rev.cu), up to 16 seed columns, programmatic dependent launch,
+// thread-block clusters along the row blocks.  Seeds are FP32 with SM = rev_stream_sm(S) columns
+// per row (zero past S).  One launch per layer: Abar[k][s] = sum_r W[r][k] Zf[r][s] (W through
+// `map`, from rev_stream_map of the FP32 weights, mp x kp, kp a multiple of 128), then either the
+// next seeds Zf_out[k][s] = s1n[k] Abar[k][s] and c = s2n * Abar[:, lam_col] (c_out / c_f_out may
+// be NULL), or, with s1n NULL (first layer), J_out[s][k] (s < nJ) and g_out[k] (s = lam_col) for
+// k < kvalid.  Geometry from rev_stream_geom (S: the most seeds of any call of the net); part holds
+// (splits / cl) x kp x 16 floats, counters kp / 128 ints, zero before the first launch (each launch
+// leaves them zero).
+struct RevGeom {
+  int rows = 0;     // rows per CTA (multiple of 32)
+  int splits = 0;   // row blocks (CTAs per column strip), a multiple of cl
+  int cl = 1;       // cluster size along the row blocks
+};
+int rev_stream_sm(int S);
+bool rev_stream_map(CUtensorMap* map, const float* W, int mp, int kp);
+RevGeom rev_stream_geom(int m, int kp, int S, int sm_count);
+cudaError_t launch_rev_seed_f(int m, int S, int nJ, int lam_col, const double* s1, const double* s2,
+                              const double* lam, float* Zf, double* c_out, float* c_f,
+                              cudaStream_t st);
+cudaError_t launch_rev_stream(const CUtensorMap& map, int m, int kp, const float* Zf, int S,
+                              const RevGeom& g, float* part, int* counters, int nJ, int lam_col,
+                              int kvalid, const double* s1n, const double* s2n, float* Zf_out,
+                              double* c_out, float* c_f_out, double* J_out, double* g_out, int* err,
+                              cudaStream_t st);
 }  // namespace nnc
 
 namespace nnc {

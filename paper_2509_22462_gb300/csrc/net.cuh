@@ -39,6 +39,9 @@ struct LayerDev {
   void* W2 = nullptr;             // double-float (hi, lo) pairs of W [mp][kp] (float2)
   void* a2 = nullptr;             // double-float (hi, lo) pairs of a_l [mp] (float2)
   nnc::TcPlan plan_tan;                // tensor-core plan of this layer's tangent GEMM
+  CUtensorMap rev_map;            // TMA map of W32 for the streaming reverse layer
+  nnc::RevGeom rev_geom;          // its launch geometry
+  int rev_cnt_off = 0;            // offset of its strip counters in nnc_net::rev_cnt
   int zy_off = -1;                // column offset of this layer's Zdot / Ydot block (-1: none)
 };
 
@@ -71,6 +74,9 @@ struct nnc_net {
   void* Zb[2][3] = {};  // reverse seeds^T [48][mp_max], ping-pong x three BF16 parts
   float* Prev = nullptr;             // split partials of the tensor-core reverse step
   bool tc_rev = false;               // reverse sweep on the tensor cores
+  bool rev_stream = false;           // streaming FP32 reverse sweep (k_rev.cu)
+  float* Zf[2] = {nullptr, nullptr}; // its FP32 seeds [mp_max][16], ping-pong
+  int* rev_cnt = nullptr;            // its per-strip arrival counters
   unsigned char* A8 = nullptr;       // FP8 form: e4m3 copy of the current tangent operand
   float* tsc = nullptr;              // FP8 form: its per-row (per-tangent) scales
   nnc::TcPlan plan_syrk;                  // tensor-core plan of the one symmetric product

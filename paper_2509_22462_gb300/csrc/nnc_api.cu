@@ -211,6 +211,30 @@ int run_reverse(nnc_net* net, bool fp64, int nJ, bool with_lam, const double* la
     }
     return NNC_OK;
   }
+  if (net->rev_stream) {
+    // FP32 weights streamed by TMA, one launch per layer (the layer boundary is fused in)
+    CK(launch_rev_seed_f(Lo.m, S, nJ, lam_col, Lo.s1, Lo.s2, lam, net->Zf[0],
+                         with_lam ? Lo.c : nullptr, (with_lam && tc) ? Lo.c_f : nullptr, st));
+    int cur = 0;
+    for (int l = net->L - 1; l >= 0; --l) {
+      LayerDev& Ly = net->layers[l];
+      PROF(PK_REV);
+      if (l > 0) {
+        LayerDev& Lp = net->layers[l - 1];
+        CK(launch_rev_stream(Ly.rev_map, Ly.m, Ly.kp, net->Zf[cur], S, Ly.rev_geom,
+                             (float*)net->part, net->rev_cnt + Ly.rev_cnt_off, nJ, lam_col, Ly.k,
+                             Lp.s1, Lp.s2, net->Zf[1 - cur], with_lam ? Lp.c : nullptr,
+                             (with_lam && tc) ? Lp.c_f : nullptr, nullptr, nullptr, net->dev_err,
+                             st));
+      } else {
+        CK(launch_rev_stream(Ly.rev_map, Ly.m, Ly.kp, net->Zf[cur], S, Ly.rev_geom,
+                             (float*)net->part, net->rev_cnt + Ly.rev_cnt_off, nJ, lam_col, Ly.k,
+                             nullptr, nullptr, nullptr, nullptr, nullptr, J, g, net->dev_err, st));
+      }
+      cur = 1 - cur;
+    }
+    return NNC_OK;
+  }
   CK(launch_rev_seed(Lo.m, S, nJ, lam_col, Lo.s1, Lo.s2, lam, net->Zbar[0],
                      with_lam ? Lo.c : nullptr, (with_lam && tc) ? Lo.c_f : nullptr, st));
   int cur = 0;
@@ -289,8 +313,8 @@ int run_hessian(nnc_net* net, double* H, cudaStream_t st) {
   }
   {
     PROF(PK_SYRK);
-    const size_t hp_bytes = (size_t)net->h_splits * n * n * (net->hp_f32 ? 4 : 8);
-    CK(cudaMemsetAsync(net->Hp, 0, hp_bytes, st));
+    if (!tc)  // the tensor-core product stores its partials; the CUDA-core one adds to them
+      CK(cudaMemsetAsync(net->Hp, 0, (size_t)net->h_splits * n * n * 8, st));
     if (tc)
       CK(tc_syrk(net->plan_syrk, (float*)net->Hp, net->dev_err, st));
     else
@@ -458,6 +482,7 @@ static int load_impl(nnc_net* net, int n_layers, const int* widths, const int* a
   net->layers.resize(n_layers);
   int mp_max = net->n_in_pad;
   size_t part_max = 1;
+  int rev_cnt_total = 0;
   for (int l = 0; l < n_layers; ++l) {
     LayerDev& Ly = net->layers[l];
     Ly.m = widths[l + 1];
@@ -476,7 +501,9 @@ static int load_impl(nnc_net* net, int n_layers, const int* widths, const int* a
       if (prec == NNC_BF16X3) AL(Ly.Wlo, nw);
     }
     CK(launch_pack(Ly.W64, nw, Ly.W32, Ly.Whi, Ly.Wlo, net->stream));
-    if (tc) {
+    // W^T in three BF16 parts for the tensor-core reverse sweep (nets with more than 15
+    // outputs; the others stream the FP32 weights)
+    if (tc && net->S_max > 16 && net->S_max <= 48) {
       AL(Ly.WThi, nw);
       AL(Ly.WTlo, nw);
       AL(Ly.WTp2, nw);
@@ -510,6 +537,15 @@ static int load_impl(nnc_net* net, int n_layers, const int* widths, const int* a
     if (tc) AL(Ly.c_f, Ly.mp);
     const int chunks = rev_chunks(Ly.m, Ly.kp, net->sm_count);
     part_max = std::max(part_max, (size_t)chunks * Ly.kp * net->S_max);
+    if (prec != NNC_FP64 && net->S_max <= 16) {
+      if (!rev_stream_map(&Ly.rev_map, Ly.W32, Ly.mp, Ly.kp))
+        return fail(NNC_ERR_CUDA, "tensor map of the reverse sweep failed");
+      Ly.rev_geom = rev_stream_geom(Ly.m, Ly.kp, net->S_max, net->sm_count);
+      part_max = std::max(part_max, (size_t)(Ly.rev_geom.splits / Ly.rev_geom.cl) * Ly.kp * 16);
+      Ly.rev_cnt_off = rev_cnt_total;
+      rev_cnt_total += Ly.kp / kPad;
+      net->rev_stream = true;
+    }
   }
   net->mp_max = mp_max;
   AL(net->x, net->n_in_pad);
@@ -532,6 +568,11 @@ static int load_impl(nnc_net* net, int n_layers, const int* widths, const int* a
   AL(net->Zbar[0], (size_t)mp_max * net->S_max);
   AL(net->Zbar[1], (size_t)mp_max * net->S_max);
   AL(net->part, part_max);
+  if (net->rev_stream) {
+    AL(net->Zf[0], (size_t)mp_max * 16);
+    AL(net->Zf[1], (size_t)mp_max * 16);
+    AL(net->rev_cnt, rev_cnt_total);
+  }
   AL(net->Jdev, (size_t)net->n_out * net->n_in);
   AL(net->gdev, net->n_in_pad);
   AL(net->Hdev, (size_t)net->n_in * net->n_in);
@@ -581,7 +622,7 @@ static int load_impl(nnc_net* net, int n_layers, const int* widths, const int* a
       if (r != NNC_OK) return fail(r, "tensor-core tangent plan failed");
     }
     // reverse sweep on the tensor cores (seed columns padded to 16 or 48)
-    if (net->S_max <= 48) {
+    if (net->S_max > 16 && net->S_max <= 48) {
       size_t prev = 1;
       for (int pp = 0; pp < 2; ++pp)
         for (int part = 0; part < 3; ++part) {
