@@ -30,10 +30,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "hessian_lag_evals_per_s"
 
-# DRAM bytes (read + write) of one tangent-GEMM launch from the ncu capture summarised in
+# DRAM bytes (read + write) of one tangent-GEMM launch (M = 4096, N = 784, K = 4096) per form and
+# N tile: mean of two launches of the ncu captures summarised in
 # profiles/k_tc_gemm_tangent_784x4096x4096.md; an entry is valid only for the kernel version it
-# was taken on (none is recorded for the current one yet).
-TANGENT_TRAFFIC = {}
+# was taken on.
+TANGENT_TRAFFIC = {("bf16x3", 112): 90.57e6, ("bf16x3", 128): 91.92e6, ("bf16x3", 208): 82.05e6,
+                   ("bf16x3", 256): 82.16e6}
 UNIT = "evals/s"
 
 
@@ -470,6 +472,7 @@ def run_ours(args, rank, world, local_rank):
     dom_ms, dom_cnt = prof_timed[dom_name] if prof_timed.get(dom_name, (0, 0))[1] else prof[dom_name]
     roof = None
     if dom_name == "tangent_gemm" and dom_cnt > 0:
+        tangent_bn = net.tuning(1)[0] if len(spec.widths) > 3 else 0
         per = tangent_gemm_flops(spec)
         fl_per_launch = sum(per) / len(per)
         avg_s = dom_ms / dom_cnt / 1e3
@@ -478,7 +481,8 @@ def run_ours(args, rank, world, local_rank):
         roof = {"kernel": "k_tc_gemm (tangent: Zdot_l = W_l Adot_{l-1}, fused sigma' / sigma'' epilogue)"
                 if args.prec.startswith("bf16") else "k_simt_gemm (tangent)",
                 "bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                "traffic": TANGENT_TRAFFIC.get((args.workload, args.prec)),
+                "traffic": TANGENT_TRAFFIC.get((args.prec, tangent_bn)),
+                "tangent_bn": tangent_bn,
                 "peak_source": f"{peak_src} bf16 sustained",
                 "executed_frac": ach * (3 if args.prec == "bf16x3" else 1) / pk,
                 "avg_launch_us": avg_s * 1e6, "launches": dom_cnt,

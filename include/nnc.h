@@ -218,6 +218,11 @@ long long nnc_launch_count(void);
  * return NNC_OK at once.  nnc_tuning reports the current choice for one layer. */
 int nnc_autotune(nnc_net* net, const char* cache_path, int retune);
 int nnc_tuning(const nnc_net* net, int layer, int* tangent_bn, int* syrk_splits);
+/* Pin the tensor-core tiling instead of tuning it (reproducible profiles): tangent_bn = the N tile
+ * of every tangent GEMM (112, 128, 208 or 256; 0 keeps the current one), syrk_splits = the split-K
+ * count of the symmetric product (1 .. the count chosen at load; 0 keeps it).  No effect on the
+ * CUDA-core forms; NNC_ERR_ARG for other values. */
+int nnc_tune_set(nnc_net* net, int tangent_bn, int syrk_splits);
 
 /* Per-kernel timing with CUDA events on the net's launch streams (no effect on results).
  * nnc_profile(net, 1) starts recording a pair of events around every launch (and clears what

@@ -1,6 +1,7 @@
 // Autotuner for the tensor-core GEMMs of a net: for every tangent-GEMM shape it times the N-tile
-// widths the kernel supports, for the symmetric product the split-K counts, on the net's own
-// buffers with CUDA events, and keeps the fastest.  Results can be kept in a small JSON file
+// widths the kernel supports (over the chain of that shape's layers, as a step runs them), for
+// the symmetric product the split-K counts, on the net's own buffers with CUDA events, and keeps
+// the fastest.  Results can be kept in a small JSON file
 // ({"<key>": [choice, microseconds], ...}, one key per device, kind, precision and shape) so that
 // later loads reuse them without timing.
 #include <algorithm>
@@ -9,6 +10,7 @@
 #include <map>
 #include <sstream>
 #include <string>
+#include <vector>
 
 #include "net.cuh"
 
@@ -94,46 +96,53 @@ extern "C" int nnc_autotune(nnc_net* net, const char* cache_path, int retune) {
   cudaStream_t st = net->stream;
   const int n = net->n_in;
   const int bns[4] = {112, 128, 208, 256};
-  // tangent GEMMs
-  for (int l = 1; l < net->L; ++l) {
+  // tangent GEMMs: layers of one shape share a choice, timed over the chain of those layers as a
+  // step runs them (different weights each launch), so that a layer's weights are not timed out
+  // of L2, which one repeated launch would do
+  std::map<std::string, std::vector<int>> groups;
+  for (int l = 1; l < net->L; ++l)
+    if (net->layers[l].plan_tan.ready)
+      groups[key_of(net, "tangent", net->layers[l].mp, n, net->layers[l].kp)].push_back(l);
+  auto make_plan = [&](TcPlan& p, int l, int bn) {
     LayerDev& Ly = net->layers[l];
-    if (!Ly.plan_tan.ready) continue;
-    const std::string key = key_of(net, "tangent", Ly.mp, n, Ly.kp);
-    int best = Ly.plan_tan.bn;
-    auto it = cache.find(key);
+    const int cur = (l - 1) % 2;
+    return prec == NNC_FP8
+               ? tc_plan_make(p, TC_TANGENT, prec, Ly.W8, nullptr, Ly.mp, Ly.kp, net->A8, nullptr, n,
+                              Ly.kp, Ly.mp, n, Ly.kp, net->sm_count, bn)
+               : tc_plan_make(p, TC_TANGENT, prec, Ly.Whi, Ly.Wlo, Ly.mp, Ly.kp, net->At[cur][0],
+                              net->At[cur][1], n, Ly.kp, Ly.mp, n, Ly.kp, net->sm_count, bn);
+  };
+  for (auto& g : groups) {
+    const std::vector<int>& ls = g.second;
+    int best = net->layers[ls[0]].plan_tan.bn;
+    auto it = cache.find(g.first);
     if (it != cache.end() && !retune) {
       best = it->second.first;
     } else {
       double best_us = 1e30;
-      const int cur = (l - 1) % 2;
       for (int bn : bns) {
-        TcPlan p;
-        const int r = prec == NNC_FP8
-                          ? tc_plan_make(p, TC_TANGENT, prec, Ly.W8, nullptr, Ly.mp, Ly.kp, net->A8, nullptr,
-                                         n, Ly.kp, Ly.mp, n, Ly.kp, net->sm_count, bn)
-                          : tc_plan_make(p, TC_TANGENT, prec, Ly.Whi, Ly.Wlo, Ly.mp, Ly.kp, net->At[cur][0],
-                                         net->At[cur][1], n, Ly.kp, Ly.mp, n, Ly.kp, net->sm_count, bn);
-        if (r != NNC_OK) continue;
+        std::vector<TcPlan> plans(ls.size());
+        bool okp = true;
+        for (size_t i = 0; i < ls.size() && okp; ++i) okp = make_plan(plans[i], ls[i], bn) == NNC_OK;
+        if (!okp) continue;
         const double us = time_us(st, 3, [&] {
-          tc_tangent(p, Ly.s1, Ly.c_f, net->At[1 - cur][0], net->At[1 - cur][1], Ly.mp, net->Zt[0],
-                     net->Zt[1], net->Yt[0], net->Yt[1], net->K_total, net->dev_err, st, Ly.w8s, net->tsc);
-        });
+          for (size_t i = 0; i < ls.size(); ++i) {
+            LayerDev& Ly = net->layers[ls[i]];
+            const int cur = (ls[i] - 1) % 2;
+            tc_tangent(plans[i], Ly.s1, Ly.c_f, net->At[1 - cur][0], net->At[1 - cur][1], Ly.mp,
+                       net->Zt[0], net->Zt[1], net->Yt[0], net->Yt[1], net->K_total, net->dev_err, st,
+                       Ly.w8s, net->tsc);
+          }
+        }) / ls.size();
         if (us < best_us) {
           best_us = us;
           best = bn;
         }
       }
-      cache[key] = {best, best_us};
+      cache[g.first] = {best, best_us};
     }
-    if (best != Ly.plan_tan.bn) {
-      const int cur = (l - 1) % 2;
-      if (prec == NNC_FP8)
-        tc_plan_make(Ly.plan_tan, TC_TANGENT, prec, Ly.W8, nullptr, Ly.mp, Ly.kp, net->A8, nullptr, n,
-                     Ly.kp, Ly.mp, n, Ly.kp, net->sm_count, best);
-      else
-        tc_plan_make(Ly.plan_tan, TC_TANGENT, prec, Ly.Whi, Ly.Wlo, Ly.mp, Ly.kp, net->At[cur][0],
-                     net->At[cur][1], n, Ly.kp, Ly.mp, n, Ly.kp, net->sm_count, best);
-    }
+    for (int l : ls)
+      if (best != net->layers[l].plan_tan.bn) make_plan(net->layers[l].plan_tan, l, best);
   }
   // symmetric product: split-K count (bounded by the partial-sum buffer allocated at load)
   if (net->K_total > 0 && net->plan_syrk.ready) {
@@ -176,6 +185,54 @@ extern "C" int nnc_autotune(nnc_net* net, const char* cache_path, int retune) {
   }
   write_cache(cache_path, cache);
   return cudaGetLastError() == cudaSuccess ? NNC_OK : NNC_ERR_CUDA;
+}
+
+extern "C" int nnc_tune_set(nnc_net* net, int tangent_bn, int syrk_splits) {
+  if (!net) {
+    set_last_error("net is NULL");
+    return NNC_ERR_ARG;
+  }
+  const int prec = net->prec;
+  if (!(prec == NNC_BF16 || prec == NNC_BF16X3 || prec == NNC_FP8)) return NNC_OK;  // CUDA-core forms
+  if (tangent_bn && tangent_bn != 112 && tangent_bn != 128 && tangent_bn != 208 && tangent_bn != 256) {
+    set_last_error("tangent N tile must be 112, 128, 208 or 256");
+    return NNC_ERR_ARG;
+  }
+  if (syrk_splits < 0 || syrk_splits > net->h_splits) {
+    set_last_error("symmetric-product splits out of range");
+    return NNC_ERR_ARG;
+  }
+  cudaSetDevice(net->device);
+  const int n = net->n_in;
+  for (int l = 1; l < net->L && tangent_bn; ++l) {
+    LayerDev& Ly = net->layers[l];
+    if (!Ly.plan_tan.ready) continue;
+    const int cur = (l - 1) % 2;
+    TcPlan p;
+    const int r = prec == NNC_FP8
+                      ? tc_plan_make(p, TC_TANGENT, prec, Ly.W8, nullptr, Ly.mp, Ly.kp, net->A8, nullptr,
+                                     n, Ly.kp, Ly.mp, n, Ly.kp, net->sm_count, tangent_bn)
+                      : tc_plan_make(p, TC_TANGENT, prec, Ly.Whi, Ly.Wlo, Ly.mp, Ly.kp, net->At[cur][0],
+                                     net->At[cur][1], n, Ly.kp, Ly.mp, n, Ly.kp, net->sm_count,
+                                     tangent_bn);
+    if (r != NNC_OK) {
+      set_last_error("tangent plan failed");
+      return r;
+    }
+    Ly.plan_tan = p;
+  }
+  if (syrk_splits && net->K_total > 0 && net->plan_syrk.ready) {
+    TcPlan p;
+    const int r = tc_plan_make(p, TC_SYRK, prec, net->Zt[0], net->Zt[1], n, net->K_total, net->Yt[0],
+                               net->Yt[1], n, net->K_total, n, n, net->K_total, net->sm_count, 0,
+                               syrk_splits);
+    if (r != NNC_OK || p.splits > net->h_splits) {
+      set_last_error("symmetric-product plan failed");
+      return r != NNC_OK ? r : NNC_ERR_ARG;
+    }
+    net->plan_syrk = p;
+  }
+  return NNC_OK;
 }
 
 extern "C" int nnc_tuning(const nnc_net* net, int layer, int* tangent_bn, int* syrk_splits) {

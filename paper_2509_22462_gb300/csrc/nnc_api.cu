@@ -323,7 +323,9 @@ int run_hessian(nnc_net* net, double* H, cudaStream_t st) {
   }
   {
     PROF(PK_OTHER);
-    CK(launch_h_finish(net->hp_f32, net->Hp, net->h_splits, n, n, H, st));
+    // the tensor-core product writes exactly plan_syrk.splits planes (tuning may lower the count)
+    const int planes = tc ? net->plan_syrk.splits : net->h_splits;
+    CK(launch_h_finish(net->hp_f32, net->Hp, planes, n, n, H, st));
   }
   return NNC_OK;
 }

@@ -30,7 +30,7 @@ EXPORTS = ["nnc_load_weights", "nnc_eval", "nnc_residual", "nnc_jacobian", "nnc_
            "nnc_batch_set_bias", "nnc_batch_use_graph", "nnc_batch_eval_dev", "nnc_batch_residual_dev",
            "nnc_batch_eval", "nnc_batch_residual", "nnc_ipm_scopf", "nnc_ws_create", "nnc_ws_free",
            "nnc_ws_set_scaling", "nnc_ws_loss_grad", "nnc_ws_adam_step", "nnc_ws_train",
-           "nnc_ws_predict", "nnc_ws_get_params", "nnc_ipm_scopf_warm", "nnc_autotune", "nnc_tuning"]
+           "nnc_ws_predict", "nnc_ws_get_params", "nnc_ipm_scopf_warm", "nnc_autotune", "nnc_tuning", "nnc_tune_set"]
 IPM_STATUS = {0: "optimal", 1: "max_iter", 2: "linesearch_failed", 3: "nonfinite",
               4: "inertia_failed", 5: "eval_error"}
 
@@ -125,6 +125,7 @@ def load_library(path: str = LIB_PATH):
                                   ctypes.POINTER(IpmOptions), _DP, _DP, ctypes.POINTER(IpmResult)]
     lib.nnc_autotune.argtypes = [_P, ctypes.c_char_p, ctypes.c_int]
     lib.nnc_tuning.argtypes = [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.nnc_tune_set.argtypes = [_P, ctypes.c_int, ctypes.c_int]
     lib.nnc_ipm_scopf_warm.argtypes = [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_int), _DP, ctypes.c_double, _DP, _DP, _DP,
                                        ctypes.POINTER(IpmOptions), _DP, _DP, ctypes.POINTER(IpmResult)]
@@ -273,6 +274,10 @@ class Net:
     def autotune(self, cache_path=None, retune=False):
         """nnc_autotune: time the tile / split candidates and keep the fastest (JSON cache optional)."""
         _check(_lib.nnc_autotune(self._h, cache_path.encode() if cache_path else None, int(bool(retune))))
+
+    def tune_set(self, tangent_bn=0, syrk_splits=0):
+        """nnc_tune_set: pin the tangent N tile and / or the symmetric-product splits."""
+        _check(_lib.nnc_tune_set(self._h, int(tangent_bn), int(syrk_splits)))
 
     def tuning(self, layer):
         bn, sp = ctypes.c_int(), ctypes.c_int()

@@ -22,6 +22,7 @@ def main():
     ap.add_argument("--act", default="tanh")
     ap.add_argument("--prec", default="bf16x3")
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--bn", type=int, default=0, help="pin the tangent N tile (0: the load-time plan)")
     a = ap.parse_args()
     import torch
     import synth
@@ -37,6 +38,8 @@ def main():
     st = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(st)
     net = nnc.Net.from_mlp(mlp, precision=a.prec)
+    if a.bn:
+        net.tune_set(tangent_bn=a.bn)
     n, m = widths[0], widths[-1]
     x = torch.tensor(d.x0, device=dev)
     lam = torch.tensor(d.lam, device=dev)

@@ -40,3 +40,29 @@ def test_autotune_keeps_results_and_caches(tmp_path):
     assert os.path.getsize(path) > 0
     net.free()
     net2.free()
+
+
+def test_tune_set_pins_tiles_and_keeps_results():
+    """nnc_tune_set: every candidate N tile gives the same tangents (the K order of one output is
+    the same in every tile), so H changes only through the symmetric product's splits."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_22462_gb300 import build, nnc
+    build.build()
+    mlp = make_mlp(MLPSpec([300, 512, 512, 7], ["tanh", "sigmoid", "identity"]), seed=5)
+    x = synth.uniform01(synth.derive_key(5, "tune-x"), 300)
+    lam = synth.normal(synth.derive_key(5, "tune-lam"), 7)
+    net = nnc.Net.from_mlp(mlp, precision="bf16x3")
+    H0 = net.hessian_lag(x, lam)
+    for bn in (112, 128, 208, 256):
+        net.tune_set(tangent_bn=bn)
+        assert net.tuning(1)[0] == bn
+        assert np.array_equal(net.hessian_lag(x, lam), H0), bn
+    net.tune_set(syrk_splits=1)
+    assert net.tuning(0)[1] == 1
+    H1 = net.hessian_lag(x, lam)
+    assert np.linalg.norm(H1 - H0) <= 1e-4 * np.linalg.norm(H0)
+    with pytest.raises(nnc.NNCError):
+        net.tune_set(tangent_bn=100)
+    net.free()
