@@ -46,7 +46,7 @@ def _args():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--prec", default="bf16x3", choices=["bf16x3", "bf16", "fp32", "fp64"])
-    p.add_argument("--workload", default="104m", choices=["104m", "87m", "tiny", "scopf"])
+    p.add_argument("--workload", default="104m", choices=["104m", "87m", "tiny", "scopf68m", "scopf"])
     p.add_argument("--scopf-k", type=int, default=256)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64-form", action="store_true")
@@ -64,9 +64,11 @@ def _workload(name):
 
 
 def _workload_config(spec, name, prec):
-    return {"workload": f"mnist_{name}_{'x'.join(map(str, spec.widths))}_tanh",
+    kind = "scopf_single" if name.startswith("scopf") else "mnist"
+    return {"workload": f"{kind}_{name}_{'x'.join(map(str, spec.widths))}_tanh",
             "n_params": spec.n_params, "n_in": spec.n_in, "n_out": spec.n_out,
-            "precision_form": prec, "inputs": "x0~U[0,1]^784, lambda~N(0,1), weights N(0,1/fan_in) seed 0",
+            "precision_form": prec,
+            "inputs": f"x0~U[0,1]^{spec.n_in}, lambda~N(0,1), weights N(0,1/fan_in) seed 0",
             "l2": "weights exceed L2 (no flush needed)"}
 
 

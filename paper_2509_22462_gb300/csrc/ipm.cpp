@@ -39,6 +39,7 @@ double secs(Clock::time_point a, Clock::time_point b) {
 // Row-major n x n, lower triangle.  Returns false if the matrix is not positive definite.
 bool cholesky(int n, double* A) {
   const int NB = 64;
+  std::vector<double> Pt;   // L21^T of the current block column, rows padded to a multiple of 4
   for (int kb = 0; kb < n; kb += NB) {
     const int nb = std::min(NB, n - kb);
     // diagonal block (unblocked, right-looking)
@@ -54,6 +55,8 @@ bool cholesky(int n, double* A) {
       }
     }
     const int r0 = kb + nb;
+    const int rem = n - r0;
+    if (rem <= 0) break;
     // panel below: L21 = A21 L11^-T (row by row)
 #pragma omp parallel for schedule(static)
     for (int i = r0; i < n; ++i) {
@@ -65,16 +68,35 @@ bool cholesky(int n, double* A) {
         ai[j] = s / aj[j];
       }
     }
-    // trailing update A22 -= L21 L21^T (lower triangle)
-#pragma omp parallel for schedule(dynamic, 8)
-    for (int i = r0; i < n; ++i) {
-      double* ai = A + (size_t)i * n;
-      const double* li = ai + kb;
-      for (int p = r0; p <= i; ++p) {
-        const double* lp = A + (size_t)p * n + kb;
-        double s = 0.0;
-        for (int q = 0; q < nb; ++q) s += li[q] * lp[q];
-        ai[p] -= s;
+    // trailing update A22 -= L21 L21^T (lower triangle) in 4 x 4 tiles: the panel is transposed
+    // so that each step of the K loop is an outer product of two contiguous 4-vectors (16
+    // independent accumulators, which the compiler keeps in vector registers)
+    const int rp = (rem + 3) / 4 * 4;
+    Pt.assign((size_t)nb * rp, 0.0);
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < rem; ++i)
+      for (int q = 0; q < nb; ++q) Pt[(size_t)q * rp + i] = A[(size_t)(r0 + i) * n + kb + q];
+    const int nt = rp / 4;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int ti = nt - 1; ti >= 0; --ti) {   // long rows first
+      const int i0 = ti * 4;
+      for (int tp = 0; tp <= ti; ++tp) {
+        const int p0 = tp * 4;
+        double acc[4][4] = {};
+        for (int q = 0; q < nb; ++q) {
+          const double* c = Pt.data() + (size_t)q * rp;
+          double a[4], b[4];
+          for (int u = 0; u < 4; ++u) {
+            a[u] = c[i0 + u];
+            b[u] = c[p0 + u];
+          }
+          for (int u = 0; u < 4; ++u)
+            for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+        }
+        for (int u = 0; u < 4 && i0 + u < rem; ++u) {
+          double* ai = A + (size_t)(r0 + i0 + u) * n + r0;
+          for (int v = 0; v < 4 && p0 + v <= i0 + u; ++v) ai[p0 + v] -= acc[u][v];
+        }
       }
     }
   }

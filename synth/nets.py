@@ -88,8 +88,15 @@ PAPER_104M = mnist_like_spec(4096, 7)          # 784 -> 4096 x 7 -> 10, 103,944,
 PAPER_87M = mnist_like_spec(4096, 6)           # literal "6 hidden layers" reading, 87,162,890 params
 
 
+# SCOPF-shaped single network (Section 4.2): 117 inputs (generator setpoints and loads), 37 outputs
+# (stability margins), deep tanh; [117, 4096 x 5, 37] has 67.7M parameters, the size of the
+# paper's 68M SCOPF net.  Its Jacobian has 37 seed rows and its Hessian 117 tangents.
+SCOPF_68M = MLPSpec([117] + [4096] * 5 + [37], ["tanh"] * 5 + ["identity"],
+                    name="scopf_117_4096x5_37_tanh")
+
+
 def spec_by_name(name: str) -> Optional[MLPSpec]:
-    return {"tiny": TINY, "104m": PAPER_104M, "87m": PAPER_87M}.get(name)
+    return {"tiny": TINY, "104m": PAPER_104M, "87m": PAPER_87M, "scopf68m": SCOPF_68M}.get(name)
 
 
 def warmstart_params(n_in: int, h1: int, h2: int, n_out: int, seed: int = 0):

@@ -154,3 +154,37 @@ def test_full_size_104m_sampled(lib, prec):
     r = net.residual(d.x0, yo)
     assert np.max(np.abs(r)) <= 1e-10 * max(1.0, np.max(np.abs(yo)))
     net.free()
+
+
+def test_scopf_shaped_single_net(lib):
+    """SCOPF-shaped single network (117 inputs, 37 outputs, deep tanh; Section 4.2): 37 Jacobian
+    seeds take the tensor-core reverse sweep (more than 15 outputs), 117 tangents one N tile.
+    A reduced-width copy of the 68M shape, checked in full."""
+    mlp = make_mlp(MLPSpec([117, 512, 512, 512, 37], ["tanh"] * 3 + ["identity"]), seed=11, tag="scopf1")
+    x = synth.uniform01(synth.derive_key(11, "scopf1-x"), 117)
+    lam = synth.normal(synth.derive_key(11, "scopf1-lam"), 37)
+    for prec in ["fp64", "fp32", "bf16x3", "bf16"]:
+        _check_all(lib, mlp, x, lam, prec, "scopf1")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_scopf_68m_sampled(lib, prec):
+    """[117, 4096 x 5, 37] tanh (67.7M parameters): value, Jacobian, gradient in full and sampled
+    Hessian columns against the oracle."""
+    mlp = make_mlp(synth.SCOPF_68M, seed=0)
+    d = synth.adversarial_data(n_in=117, n_out=37, seed=0)
+    net = lib.Net.from_mlp(mlp, precision=prec)
+    y = net.eval(d.x0)
+    J = net.jacobian(d.x0)
+    H, g = net.hessian_lag(d.x0, d.lam, want_grad=True)
+    yo = onn.value(mlp, d.x0)
+    Jo = onn.jacobian(mlp, d.x0)
+    go = onn.vjp(mlp, d.x0, d.lam)
+    cols = [0, 1, 58, 116]
+    Hc = onn.hessian_lag_columns(mlp, d.x0, d.lam, cols)
+    e = dict(y=rel(y, yo), J=rel(J, Jo), H=rel(H[:, cols], Hc), g=rel(g, go))
+    print(f"[scopf68m {prec}] rel err y={e['y']:.2e} J={e['J']:.2e} Hcols={e['H']:.2e} g={e['g']:.2e}")
+    t = TOL[prec]
+    assert e["y"] < t["y"] and e["J"] < t["J"] and e["H"] < t["H"] and e["g"] < t["J"], e
+    assert np.array_equal(H, H.T)
+    net.free()
