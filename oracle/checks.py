@@ -16,6 +16,9 @@ import numpy as np
 def _act_complex(name, z):
     if name == "identity":
         return z
+    if name == "softmax":
+        e = np.exp(z)
+        return e / np.sum(e)
     if name == "tanh":
         e = np.exp(2.0 * z)
         return (e - 1.0) / (e + 1.0)
@@ -106,6 +109,10 @@ class HyperDual:
 def _act_hd(name, u):
     if name == "identity":
         return u
+    if name == "softmax":
+        e = u.exp()
+        total = HyperDual(np.sum(e.a), np.sum(e.b), np.sum(e.c), np.sum(e.d))
+        return e * total.recip()
     if name == "tanh":
         e = (u * 2.0).exp()
         return (e - 1.0) / (e + 1.0)

@@ -17,6 +17,9 @@ import numpy as np
 def act_value(name, z):
     if name == "identity":
         return z.copy()
+    if name == "softmax":
+        e = np.exp(z - np.max(z))
+        return e / np.sum(e)
     if name == "tanh":
         return np.tanh(z)
     if name == "sigmoid":
@@ -65,6 +68,50 @@ def act_d2(name, z):
     raise ValueError(name)
 
 
+# Layer maps as operators.  An elementwise activation has the Jacobian diag(sigma'(z)) and, for
+# an adjoint abar, the curvature matrix grad_z^2 (abar^T sigma(z)) = diag(sigma''(z) * abar).  The
+# softmax output layer (Section 4.1's classifiers), p_i = exp(z_i) / sum_j exp(z_j), couples its
+# outputs: dp_i/dz_j = p_i (delta_ij - p_j), and
+#   d2 p_i / dz_j dz_k = p_i [(delta_ij - p_j)(delta_ik - p_k) - p_j (delta_jk - p_k)],
+# so both are full matrices, written out below from these definitions.
+
+
+def softmax_second(p):
+    """The tensor D[i, j, k] = d2 p_i / dz_j dz_k of the softmax at probabilities p."""
+    n = p.size
+    I = np.eye(n)
+    A = I - p[None, :]                                   # A[i, j] = delta_ij - p_j
+    return p[:, None, None] * (A[:, :, None] * A[:, None, :] -
+                               p[None, :, None] * (I - p[None, None, :]))
+
+
+def jac_apply(name, z, M):
+    """D sigma(z) @ M for a matrix (or vector) M."""
+    if name == "softmax":
+        p = act_value(name, z)
+        return p[:, None] * M - np.outer(p, p @ M) if M.ndim == 2 else p * M - p * (p @ M)
+    d1 = act_d1(name, z)
+    return d1[:, None] * M if M.ndim == 2 else d1 * M
+
+
+def jacT_apply(name, z, M):
+    """D sigma(z)^T @ M (the softmax Jacobian is symmetric; elementwise ones are diagonal)."""
+    return jac_apply(name, z, M)
+
+
+def curvature(name, z, abar):
+    """The matrix grad_z^2 (abar^T sigma(z)), or for an elementwise activation its diagonal."""
+    if name == "softmax":
+        return np.einsum("i,ijk->jk", abar, softmax_second(act_value(name, z)))
+    return act_d2(name, z) * abar
+
+
+def curv_apply(name, z, abar, Zdot):
+    """grad_z^2 (abar^T sigma(z)) @ Zdot."""
+    c = curvature(name, z, abar)
+    return c @ Zdot if c.ndim == 2 else c[:, None] * Zdot
+
+
 # ---------------------------------------------------------------- Eq. 3
 
 
@@ -92,14 +139,14 @@ def jacobian(net, x):
     """dNN/dx, shape (n_out, n_in), by reverse mode with one seed per output.
 
     Seeds abar_L = e_i for every output i at once (columns of the identity); then
-    zbar_l = sigma_l'(z_l) * abar_l and abar_{l-1} = W_l^T zbar_l.  Row i of J is abar_0 of
-    seed i.
+    zbar_l = D sigma_l(z_l)^T abar_l (sigma_l'(z_l) * abar_l for an elementwise activation) and
+    abar_{l-1} = W_l^T zbar_l.  Row i of J is abar_0 of seed i.
     """
     zs, _ = forward(net, x)
     L = len(net.W)
     Abar = np.eye(net.spec.n_out)                       # columns are seeds
     for l in range(L, 0, -1):
-        Zbar = act_d1(net.spec.acts[l - 1], zs[l - 1])[:, None] * Abar
+        Zbar = jacT_apply(net.spec.acts[l - 1], zs[l - 1], Abar)
         Abar = net.W[l - 1].T @ Zbar
     return Abar.T.copy()
 
@@ -109,7 +156,7 @@ def vjp(net, x, lam):
     zs, _ = forward(net, x)
     abar = np.asarray(lam, dtype=np.float64)
     for l in range(len(net.W), 0, -1):
-        abar = net.W[l - 1].T @ (act_d1(net.spec.acts[l - 1], zs[l - 1]) * abar)
+        abar = net.W[l - 1].T @ jacT_apply(net.spec.acts[l - 1], zs[l - 1], abar)
     return abar
 
 
@@ -119,7 +166,7 @@ def adjoints(net, zs, lam):
     abars = [None] * (L + 1)
     abars[L] = np.asarray(lam, dtype=np.float64)
     for l in range(L, 0, -1):
-        abars[l - 1] = net.W[l - 1].T @ (act_d1(net.spec.acts[l - 1], zs[l - 1]) * abars[l])
+        abars[l - 1] = net.W[l - 1].T @ jacT_apply(net.spec.acts[l - 1], zs[l - 1], abars[l])
     return abars
 
 
@@ -132,11 +179,12 @@ def hessian_lag_for(net, x, lam):
     The reverse sweep of `adjoints` computes grad(lambda^T NN)(x) = abar_0.  Differentiating
     every step of it in the n_in directions e_1..e_n at once (forward mode, tangents carried
     as matrix columns) gives the Hessian:
-      forward tangents:  Adot_0 = I,  Zdot_l = W_l Adot_{l-1},  Adot_l = sigma_l'(z_l) * Zdot_l
+      forward tangents:  Adot_0 = I,  Zdot_l = W_l Adot_{l-1},  Adot_l = D sigma_l(z_l) Zdot_l
       reverse tangents:  dabar_L = 0 (lambda is constant),
-                         dzbar_l = sigma_l'(z_l) * dabar_l + (sigma_l''(z_l) * abar_l) * Zdot_l,
+                         dzbar_l = D sigma_l(z_l)^T dabar_l + M_l(abar_l) Zdot_l,
                          dabar_{l-1} = W_l^T dzbar_l
-    and H = dabar_0.  The result is returned as computed (no symmetrisation).
+    with M_l(abar) = grad_z^2 (abar^T sigma_l(z_l)) (diag(sigma_l'' * abar) when elementwise), and
+    H = dabar_0.  The result is returned as computed (no symmetrisation).
     """
     zs, _ = forward(net, x)
     abars = adjoints(net, zs, lam)
@@ -146,20 +194,19 @@ def hessian_lag_for(net, x, lam):
     Zdots = []
     for l in range(1, L + 1):
         Zdot = net.W[l - 1] @ Adot
-        Adot = act_d1(net.spec.acts[l - 1], zs[l - 1])[:, None] * Zdot
+        Adot = jac_apply(net.spec.acts[l - 1], zs[l - 1], Zdot)
         Zdots.append(Zdot)
     dabar = np.zeros((net.spec.n_out, n))
     for l in range(L, 0, -1):
         act = net.spec.acts[l - 1]
-        d1 = act_d1(act, zs[l - 1])
-        d2 = act_d2(act, zs[l - 1])
-        dzbar = d1[:, None] * dabar + (d2 * abars[l])[:, None] * Zdots[l - 1]
+        dzbar = jacT_apply(act, zs[l - 1], dabar) + curv_apply(act, zs[l - 1], abars[l], Zdots[l - 1])
         dabar = net.W[l - 1].T @ dzbar
     return dabar
 
 
 def hessian_lag_layers(net, x, lam):
-    """The same Hessian as a sum over layers: H = sum_l Zdot_l^T diag(sigma_l''(z_l) * abar_l) Zdot_l.
+    """The same Hessian as a sum over layers: H = sum_l Zdot_l^T M_l(abar_l) Zdot_l, where
+    M_l(abar_l) = diag(sigma_l''(z_l) * abar_l) for an elementwise activation.
 
     Unrolling the reverse-tangent recursion of `hessian_lag_for` (the affine maps add no
     curvature) leaves one term per layer, where Zdot_l = dz_l/dx and abar_l is the adjoint of
@@ -175,9 +222,8 @@ def hessian_lag_layers(net, x, lam):
     for l in range(1, L + 1):
         act = net.spec.acts[l - 1]
         Zdot = net.W[l - 1] @ Adot
-        c = act_d2(act, zs[l - 1]) * abars[l]
-        H += Zdot.T @ (c[:, None] * Zdot)
-        Adot = act_d1(act, zs[l - 1])[:, None] * Zdot
+        H += Zdot.T @ curv_apply(act, zs[l - 1], abars[l], Zdot)
+        Adot = jac_apply(act, zs[l - 1], Zdot)
     return H
 
 
@@ -204,12 +250,11 @@ def hessian_lag_columns(net, x, lam, cols):
     Zdots = []
     for l in range(1, L + 1):
         Zdot = net.W[l - 1] @ Adot
-        Adot = act_d1(net.spec.acts[l - 1], zs[l - 1])[:, None] * Zdot
+        Adot = jac_apply(net.spec.acts[l - 1], zs[l - 1], Zdot)
         Zdots.append(Zdot)
     dabar = np.zeros((net.spec.n_out, cols.size))
     for l in range(L, 0, -1):
         act = net.spec.acts[l - 1]
-        dzbar = act_d1(act, zs[l - 1])[:, None] * dabar + \
-            (act_d2(act, zs[l - 1]) * abars[l])[:, None] * Zdots[l - 1]
+        dzbar = jacT_apply(act, zs[l - 1], dabar) + curv_apply(act, zs[l - 1], abars[l], Zdots[l - 1])
         dabar = net.W[l - 1].T @ dzbar
     return dabar

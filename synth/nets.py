@@ -10,7 +10,7 @@ import numpy as np
 
 from .rng import derive_key, normal
 
-ACTIVATIONS = ("identity", "tanh", "sigmoid", "softplus", "gelu")
+ACTIVATIONS = ("identity", "tanh", "sigmoid", "softplus", "gelu", "softmax")
 
 
 @dataclass
@@ -24,6 +24,7 @@ class MLPSpec:
         assert len(self.acts) == len(self.widths) - 1
         for a in self.acts:
             assert a in ACTIVATIONS, a
+        assert "softmax" not in self.acts[:-1], "softmax is an output-layer activation"
 
     @property
     def n_layers(self) -> int:

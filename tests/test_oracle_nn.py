@@ -176,3 +176,48 @@ def test_hessian_columns_match_full_sweep():
     x, lam = _x(11), _lam(3)
     cols = [0, 4, 10]
     assert _rel(nn.hessian_lag_columns(net, x, lam, cols), nn.hessian_lag_for(net, x, lam)[:, cols]) < 1e-15
+
+
+# ---------------------------------------------------------------- softmax output layer
+SOFTMAX_NETS = [([4, 5, 3], ["tanh", "softmax"]),
+                ([3, 6, 4, 5], ["sigmoid", "softplus", "softmax"]),
+                ([5, 4], ["softmax"])]
+
+
+@pytest.mark.parametrize("case", range(len(SOFTMAX_NETS)))
+def test_softmax_output_against_complex_step_and_hyperdual(case):
+    """Softmax output layer (Section 4.1's classifiers): J by complex step, H by hyper-dual
+    numbers (both from exp only), the literal sweep equal to the per-layer sum."""
+    widths, acts = SOFTMAX_NETS[case]
+    net = _net(widths, acts, seed=case)
+    x, lam = _x(widths[0], seed=case + 3), _lam(widths[-1], seed=case + 4)
+    p = nn.value(net, x)
+    assert abs(p.sum() - 1.0) < 1e-14 and np.all(p > 0)
+    J = nn.jacobian(net, x)
+    assert np.max(np.abs(J - checks.jacobian_complex_step(net, x))) < 1e-13 * max(1.0, np.abs(J).max())
+    assert np.allclose(nn.vjp(net, x, lam), lam @ J, rtol=0, atol=1e-14)
+    H = nn.hessian_lag_for(net, x, lam)
+    Hh = checks.hessian_hyperdual(net, x, lam)
+    assert np.max(np.abs(H - Hh)) < 1e-12 * max(1.0, np.abs(Hh).max())
+    assert np.max(np.abs(nn.hessian_lag_layers(net, x, lam) - Hh)) < 1e-12 * max(1.0, np.abs(Hh).max())
+
+
+def test_softmax_invariants():
+    """Probabilities sum to one, so the Jacobian's columns sum to zero and a multiplier vector
+    proportional to (1, ..., 1) sees no curvature."""
+    net = _net([6, 8, 5], ["tanh", "softmax"], seed=9)
+    x = _x(6, seed=10)
+    J = nn.jacobian(net, x)
+    assert np.max(np.abs(J.sum(axis=0))) < 1e-15
+    H = nn.hessian_lag(net, x, 2.5 * np.ones(5))
+    assert np.max(np.abs(H)) < 1e-14
+    # the softmax second-derivative tensor against central differences of its Jacobian
+    z = synth.normal(synth.derive_key(11, "sm-z"), 5)
+    D = nn.softmax_second(nn.act_value("softmax", z))
+    h = 1e-5
+    for k in range(5):
+        e = np.zeros(5); e[k] = h
+        pp, pm = nn.act_value("softmax", z + e), nn.act_value("softmax", z - e)
+        Jp = np.diag(pp) - np.outer(pp, pp)
+        Jm = np.diag(pm) - np.outer(pm, pm)
+        assert np.max(np.abs((Jp - Jm) / (2 * h) - D[:, :, k])) < 1e-9
