@@ -61,7 +61,11 @@ typedef enum {
 typedef enum { NNC_FP64 = 0, NNC_FP32 = 1, NNC_BF16 = 2, NNC_BF16X3 = 3, NNC_FP8 = 4 } nnc_precision;
 
 /* sigma_l of Eq. 3.  All are C^2, as interior-point methods require (Section 2). */
-typedef enum { NNC_IDENTITY = 0, NNC_TANH = 1, NNC_SIGMOID = 2, NNC_SOFTPLUS = 3, NNC_GELU = 4 } nnc_act;
+/* NNC_SOFTMAX: output layer only (n_out <= 64): p = softmax(z_L), the classifiers of Section 4.1.
+ * Its second derivative couples the outputs; the library adds that coupling to H exactly. */
+typedef enum {
+  NNC_IDENTITY = 0, NNC_TANH = 1, NNC_SIGMOID = 2, NNC_SOFTPLUS = 3, NNC_GELU = 4, NNC_SOFTMAX = 5
+} nnc_act;
 
 /* Bits of `what` in nnc_eval_batched. */
 #define NNC_WANT_Y 1u    /* value NN(x) */

@@ -214,6 +214,7 @@ int build(nnc_batch* b, nnc_net* const* nets, int K) {
   b->device = n0->device;
   b->sm_count = n0->sm_count;
   if (!is_tc_prec(b->prec)) return bfail(NNC_ERR_UNSUPPORTED, "batch needs a BF16 or BF16x3 net");
+  if (nets[0]->softmax) return bfail(NNC_ERR_UNSUPPORTED, "batch members need an elementwise output layer");
   for (int k = 0; k < K; ++k) {
     nnc_net* n = nets[k];
     if (!n || n->L != b->L || n->n_out != b->n_out || n->prec != b->prec || n->device != b->device)

@@ -59,6 +59,34 @@ __device__ __forceinline__ void act_eval(int act, double z, double& a, double& d
   }
 }
 
+// Output-layer seed of the reverse sweep and the output layer's curvature for the Hessian.
+// Seed column s is abar_L = e_s (s < nJ) or lambda (s = lam_col); zbar_L = D sigma_L(z_L)^T abar_L.
+// Elementwise sigma_L: zbar_L[i] = sigma'_i abar_L[i] and the curvature grad_z^2(lambda^T a_L) is
+// diag(sigma''_i lambda_i).  Softmax (p = the probabilities; D sigma = diag(p) - p p^T): zbar_L[i] =
+// p_i (abar_L[i] - p^T abar_L), and the curvature is diag(p_i (lambda_i - lambar)) plus a rank-two
+// part (handled by the caller), lambar = p^T lambda.  Returns zbar_L[i] of column s; *c = the
+// diagonal curvature of row i (used with the lambda column).
+__device__ __forceinline__ double out_seed(int i, int s, int m, int nJ, int lam_col,
+                                           const double* s1, const double* s2, const double* lam,
+                                           const double* p, double* c) {
+  if (!p) {
+    double ab = 0.0;
+    if (s == lam_col) ab = lam[i];
+    else if (s < nJ) ab = (s == i) ? 1.0 : 0.0;
+    *c = s2[i] * (s == lam_col ? ab : 0.0);
+    return s1[i] * ab;
+  }
+  if (s == lam_col) {
+    double lb = 0.0;
+    for (int j = 0; j < m; ++j) lb += lam[j] * p[j];
+    *c = p[i] * (lam[i] - lb);
+    return *c;
+  }
+  *c = 0.0;
+  if (s < nJ) return p[i] * ((s == i ? 1.0 : 0.0) - p[s]);
+  return 0.0;
+}
+
 // v ~ hi + lo with hi = bf16(v) and lo = bf16(v - hi): the split of the BF16x3 scheme
 // (Henry, Tang & Heinecke 2019).  hi carries 8 significant bits, hi + lo about 16.
 __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {

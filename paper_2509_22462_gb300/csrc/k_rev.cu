@@ -232,24 +232,22 @@ __global__ void __launch_bounds__(kRvThreads, SM <= 12 ? 2 : 1) k_rev_stream(con
   if (threadIdx.x == 0) a.counters[blockIdx.x] = 0;  // ready for the next launch
 }
 
-// Output-layer seeds for the streaming sweep: Zf[i][s] = sigma_L'(z_i) * abar_L[i][s] in FP32 with
-// SM columns per row (zero past S), abar_L = e_s (s < nJ) or lambda (s = lam_col); c_L = sigma_L'' *
-// lambda.
+// Output-layer seeds for the streaming sweep (out_seed): Zf[i][s] = zbar_L[i][s] in FP32 with SM
+// columns per row (zero past S); c_L of the lambda column.  p: softmax probabilities or NULL.
 __global__ void k_rev_seed_f(int m, int S, int SM, int nJ, int lam_col, const double* __restrict__ s1,
                              const double* __restrict__ s2, const double* __restrict__ lam,
-                             float* __restrict__ Zf, double* __restrict__ c_out,
-                             float* __restrict__ c_f) {
+                             const double* __restrict__ p, float* __restrict__ Zf,
+                             double* __restrict__ c_out, float* __restrict__ c_f) {
   griddep_launch();
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= m * SM) return;
   const int i = idx / SM, s = idx % SM;
-  double ab = 0.0;
-  if (s == lam_col) ab = lam[i];
-  else if (s < nJ) ab = (s == i) ? 1.0 : 0.0;
-  Zf[idx] = s < S ? (float)(s1[i] * ab) : 0.f;
+  double c = 0.0;
+  const double zb = s < S ? out_seed(i, s, m, nJ, lam_col, s1, s2, lam, p, &c) : 0.0;
+  Zf[idx] = (float)zb;
   if (s == lam_col) {
-    if (c_out) c_out[i] = s2[i] * ab;
-    if (c_f) c_f[i] = (float)(s2[i] * ab);
+    if (c_out) c_out[i] = c;
+    if (c_f) c_f[i] = (float)c;
   }
 }
 
@@ -329,11 +327,11 @@ RevGeom rev_stream_geom(int m, int kp, int S, int sm_count) {
 }
 
 cudaError_t launch_rev_seed_f(int m, int S, int nJ, int lam_col, const double* s1, const double* s2,
-                              const double* lam, float* Zf, double* c_out, float* c_f,
-                              cudaStream_t st) {
+                              const double* lam, const double* p, float* Zf, double* c_out,
+                              float* c_f, cudaStream_t st) {
   const int SM = rev_stream_sm(S);
-  k_rev_seed_f<<<(m * SM + 255) / 256, 256, 0, st>>>(m, S, SM, nJ, lam_col, s1, s2, lam, Zf, c_out,
-                                                     c_f);
+  k_rev_seed_f<<<(m * SM + 255) / 256, 256, 0, st>>>(m, S, SM, nJ, lam_col, s1, s2, lam, p, Zf,
+                                                     c_out, c_f);
   note_launch();
   return cudaGetLastError();
 }

@@ -223,31 +223,29 @@ cudaError_t launch_rev_reduce(bool fp64, const void* part, int chunks, int kcols
   return cudaGetLastError();
 }
 
-// Seeds at the output layer: abar_L = e_s for the Jacobian columns s < nJ and abar_L = lambda
-// for column lam_col; zbar_L = sigma_L' * abar_L, and c_L = sigma_L'' * lambda.
+// Seeds at the output layer (out_seed): zbar_L of every seed column, and the output layer's
+// diagonal curvature c_L (the lambda column).  p: softmax probabilities, or NULL.
 __global__ void k_rev_seed(int m, int S, int nJ, int lam_col, const double* __restrict__ s1,
                            const double* __restrict__ s2, const double* __restrict__ lam,
-                           double* __restrict__ Zbar, double* __restrict__ c_out,
-                           float* __restrict__ c_out_f) {
+                           const double* __restrict__ p, double* __restrict__ Zbar,
+                           double* __restrict__ c_out, float* __restrict__ c_out_f) {
   async::griddep_launch();
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= m * S) return;
   const int i = idx / S, s = idx % S;
-  double ab = 0.0;
-  if (s == lam_col) ab = lam[i];
-  else if (s < nJ) ab = (s == i) ? 1.0 : 0.0;
-  Zbar[idx] = s1[i] * ab;
+  double c;
+  Zbar[idx] = out_seed(i, s, m, nJ, lam_col, s1, s2, lam, p, &c);
   if (s == lam_col) {
-    if (c_out) c_out[i] = s2[i] * ab;
-    if (c_out_f) c_out_f[i] = (float)(s2[i] * ab);
+    if (c_out) c_out[i] = c;
+    if (c_out_f) c_out_f[i] = (float)c;
   }
 }
 
 cudaError_t launch_rev_seed(int m, int S, int nJ, int lam_col, const double* s1, const double* s2,
-                            const double* lam, double* Zbar, double* c_out, float* c_out_f,
-                            cudaStream_t st) {
+                            const double* lam, const double* p, double* Zbar, double* c_out,
+                            float* c_out_f, cudaStream_t st) {
   const int total = m * S;
-  k_rev_seed<<<(total + 255) / 256, 256, 0, st>>>(m, S, nJ, lam_col, s1, s2, lam, Zbar, c_out,
+  k_rev_seed<<<(total + 255) / 256, 256, 0, st>>>(m, S, nJ, lam_col, s1, s2, lam, p, Zbar, c_out,
                                                   c_out_f);
   note_launch();
   return cudaGetLastError();
@@ -269,6 +267,90 @@ __device__ __forceinline__ void put_tan(TanBuf b, size_t i, float v) {
     ((__nv_bfloat16*)b.hi)[i] = h;
     ((__nv_bfloat16*)b.lo)[i] = l;
   }
+}
+
+// ------------------------------------------------------------------ softmax output layer
+// p = softmax(z) in place (the value pass computed the logits z = W_L a_{L-1} + b_L), with the
+// maximum subtracted before exp.  m <= 64; one warp.
+__global__ void k_softmax_head(int m, double* __restrict__ z) {
+  const int lane = threadIdx.x;
+  double v0 = lane < m ? z[lane] : -INFINITY, v1 = lane + 32 < m ? z[lane + 32] : -INFINITY;
+  double mx = fmax(v0, v1);
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const double e0 = lane < m ? exp(v0 - mx) : 0.0, e1 = lane + 32 < m ? exp(v1 - mx) : 0.0;
+  const double sum = warp_sum(e0 + e1);
+  if (lane < m) z[lane] = e0 / sum;
+  if (lane + 32 < m) z[lane + 32] = e1 / sum;
+}
+
+cudaError_t launch_softmax_head(int m, double* z, cudaStream_t st) {
+  if (m > 64) return cudaErrorInvalidValue;
+  k_softmax_head<<<1, 32, 0, st>>>(m, z);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// The softmax layer's curvature grad_z^2(lambda^T p) = diag(p (lambda - lambar)) + U C U^T with
+// U = [p, p lambda], C = [[2 lambar, -1], [-1, 0]], lambar = p^T lambda.  The diagonal part goes
+// through the tangent epilogue like any layer; the rank-two part is written as two extra columns
+// of the symmetric product's operands: with C's eigenvalues g_k = lambar +- sqrt(lambar^2 + 1)
+// and u_k = p + (2 lambar - g_k) p lambda, U C U^T = sum_k g'_k u_k u_k^T,
+// g'_k = g_k / (1 + (2 lambar - g_k)^2); column k of Zdot^T is w_k = Zdot_L^T u_k, of the scaled
+// operand g'_k w_k, so the product adds sum_k g'_k w_k w_k^T to H.
+template <Elem E>
+__device__ __forceinline__ double get_tan(TanBuf b, size_t i) {
+  if constexpr (E == Elem::F64) return ((const double*)b.hi)[i];
+  else if constexpr (E == Elem::F32) return ((const float*)b.hi)[i];
+  else if constexpr (E == Elem::BF16) return __bfloat162float(((const __nv_bfloat16*)b.hi)[i]);
+  else
+    return (double)__bfloat162float(((const __nv_bfloat16*)b.hi)[i]) +
+           (double)__bfloat162float(((const __nv_bfloat16*)b.lo)[i]);
+}
+
+template <Elem E>
+__device__ __forceinline__ void set_tan(TanBuf b, size_t i, double v) {
+  if constexpr (E == Elem::F64) ((double*)b.hi)[i] = v;
+  else put_tan<E>(b, i, (float)v);
+}
+
+template <Elem E>
+__global__ void k_softmax_ext(int n, int m, const double* __restrict__ p, const double* __restrict__ lam,
+                              TanBuf ZL, TanBuf Zx, TanBuf Yx, int ldz) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;   // tangent (row of Zdot^T)
+  if (j >= n) return;
+  double lb = 0.0;
+  for (int i = 0; i < m; ++i) lb += lam[i] * p[i];
+  const double r = sqrt(lb * lb + 1.0);
+  const double g[2] = {lb + r, lb - r};
+  double w[2] = {0.0, 0.0};
+  for (int i = 0; i < m; ++i) {
+    const double z = get_tan<E>(ZL, (size_t)j * ldz + i);
+    const double pl = p[i] * lam[i];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) w[k] += z * (p[i] + (2.0 * lb - g[k]) * pl);
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const double t = 2.0 * lb - g[k];
+    const size_t o = (size_t)j * ldz + k;
+    set_tan<E>(Zx, o, w[k]);
+    set_tan<E>(Yx, o, g[k] / (1.0 + t * t) * w[k]);
+  }
+}
+
+cudaError_t launch_softmax_ext(Elem e, int n, int m, const double* p, const double* lam, TanBuf ZL,
+                               TanBuf Zx, TanBuf Yx, int ldz, cudaStream_t st) {
+  const int blocks = (n + 127) / 128;
+  switch (e) {
+    case Elem::F64: k_softmax_ext<Elem::F64><<<blocks, 128, 0, st>>>(n, m, p, lam, ZL, Zx, Yx, ldz); break;
+    case Elem::F32: k_softmax_ext<Elem::F32><<<blocks, 128, 0, st>>>(n, m, p, lam, ZL, Zx, Yx, ldz); break;
+    case Elem::BF16: k_softmax_ext<Elem::BF16><<<blocks, 128, 0, st>>>(n, m, p, lam, ZL, Zx, Yx, ldz); break;
+    case Elem::BF16X3:
+      k_softmax_ext<Elem::BF16X3><<<blocks, 128, 0, st>>>(n, m, p, lam, ZL, Zx, Yx, ldz);
+      break;
+  }
+  note_launch();
+  return cudaGetLastError();
 }
 
 template <Elem E, typename TW>
@@ -647,36 +729,34 @@ cudaError_t launch_pack_t(const double* W, int mp, int kp, __nv_bfloat16* p0, __
   return cudaGetLastError();
 }
 
-// Output-layer seeds, transposed for the reverse GEMM: Zb[s][i] = s1[i] * abar_L[i][s] as three
-// BF16 parts z0/z1/z2 (row stride ld), abar_L = e_s (s < nJ) or lambda (s = lam_col);
-// c_L = s2 * lambda.
+// Output-layer seeds (out_seed), transposed for the reverse GEMM: Zb[s][i] = zbar_L[i][s] as three
+// BF16 parts z0/z1/z2 (row stride ld); c_L of the lambda column.
 __global__ void k_rev_seed_t(int m, int S, int nJ, int lam_col, const double* __restrict__ s1,
                              const double* __restrict__ s2, const double* __restrict__ lam,
-                             __nv_bfloat16* __restrict__ z0, __nv_bfloat16* __restrict__ z1,
-                             __nv_bfloat16* __restrict__ z2, int ld, double* __restrict__ c_out,
-                             float* __restrict__ c_f) {
+                             const double* __restrict__ p, __nv_bfloat16* __restrict__ z0,
+                             __nv_bfloat16* __restrict__ z1, __nv_bfloat16* __restrict__ z2, int ld,
+                             double* __restrict__ c_out, float* __restrict__ c_f) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= m * S) return;
   const int i = idx / S, s = idx % S;
-  double ab = 0.0;
-  if (s == lam_col) ab = lam[i];
-  else if (s < nJ) ab = (s == i) ? 1.0 : 0.0;
+  double cv;
+  const double zb = out_seed(i, s, m, nJ, lam_col, s1, s2, lam, p, &cv);
   __nv_bfloat16 a, b, c;
-  split3_bf16(s1[i] * ab, a, b, c);
+  split3_bf16(zb, a, b, c);
   const size_t o = (size_t)s * ld + i;
   z0[o] = a;
   z1[o] = b;
   z2[o] = c;
   if (s == lam_col) {
-    if (c_out) c_out[i] = s2[i] * ab;
-    if (c_f) c_f[i] = (float)(s2[i] * ab);
+    if (c_out) c_out[i] = cv;
+    if (c_f) c_f[i] = (float)cv;
   }
 }
 
 cudaError_t launch_rev_seed_t(int m, int S, int nJ, int lam_col, const double* s1, const double* s2,
-                              const double* lam, void* const z[3], int ld, double* c_out, float* c_f,
-                              cudaStream_t st) {
-  k_rev_seed_t<<<(m * S + 255) / 256, 256, 0, st>>>(m, S, nJ, lam_col, s1, s2, lam,
+                              const double* lam, const double* p, void* const z[3], int ld,
+                              double* c_out, float* c_f, cudaStream_t st) {
+  k_rev_seed_t<<<(m * S + 255) / 256, 256, 0, st>>>(m, S, nJ, lam_col, s1, s2, lam, p,
                                                     (__nv_bfloat16*)z[0], (__nv_bfloat16*)z[1],
                                                     (__nv_bfloat16*)z[2], ld, c_out, c_f);
   note_launch();

@@ -34,10 +34,17 @@ cudaError_t launch_rev_reduce(bool fp64, const void* part, int chunks, int kcols
                               const double* s1, const double* s2, int lam_col, int nJ,
                               double* Zbar_out, double* c_out, float* c_out_f, double* J_out,
                               double* g_out, cudaStream_t st);
+// Softmax output layer (k_vector.cu): p = softmax(z) in place (m <= 64); and the rank-two part of
+// its curvature as two extra columns of the symmetric product's operands: Zx[j][k] = w_k[j],
+// Yx[j][k] = g'_k w_k[j] (k = 0, 1; row stride ldz), w_k = ZL^T u_k from the layer's tangent
+// block ZL (element type e).
+cudaError_t launch_softmax_head(int m, double* z, cudaStream_t st);
+cudaError_t launch_softmax_ext(Elem e, int n, int m, const double* p, const double* lam, TanBuf ZL,
+                               TanBuf Zx, TanBuf Yx, int ldz, cudaStream_t st);
 // Seeds of the reverse sweep at the output layer (see k_vector.cu).
 cudaError_t launch_rev_seed(int m, int S, int nJ, int lam_col, const double* s1, const double* s2,
-                            const double* lam, double* Zbar, double* c_out, float* c_out_f,
-                            cudaStream_t st);
+                            const double* lam, const double* p, double* Zbar, double* c_out,
+                            float* c_out_f, cudaStream_t st);
 // First-layer tangents: Zdot_1 = W_1, so At[n][m] = s1[m] W1[m][n] (row stride lda), and
 // Zt = W1^T, Yt[n][m] = c[m] W1[m][n] (row stride ldz; skipped if Zt.hi is NULL).  W1 is the
 // FP32 copy of the first layer (the FP64 copy for the FP64 form).
@@ -110,8 +117,8 @@ int rev_stream_sm(int S);
 bool rev_stream_map(CUtensorMap* map, const float* W, int mp, int kp);
 RevGeom rev_stream_geom(int m, int kp, int S, int sm_count);
 cudaError_t launch_rev_seed_f(int m, int S, int nJ, int lam_col, const double* s1, const double* s2,
-                              const double* lam, float* Zf, double* c_out, float* c_f,
-                              cudaStream_t st);
+                              const double* lam, const double* p, float* Zf, double* c_out,
+                              float* c_f, cudaStream_t st);
 cudaError_t launch_rev_stream(const CUtensorMap& map, int m, int kp, const float* Zf, int S,
                               const RevGeom& g, float* part, int* counters, int nJ, int lam_col,
                               int kvalid, const double* s1n, const double* s2n, float* Zf_out,
@@ -125,8 +132,8 @@ namespace nnc {
 cudaError_t launch_pack_t(const double* W, int mp, int kp, __nv_bfloat16* p0, __nv_bfloat16* p1,
                           __nv_bfloat16* p2, cudaStream_t st);
 cudaError_t launch_rev_seed_t(int m, int S, int nJ, int lam_col, const double* s1, const double* s2,
-                              const double* lam, void* const z[3], int ld, double* c_out, float* c_f,
-                              cudaStream_t st);
+                              const double* lam, const double* p, void* const z[3], int ld,
+                              double* c_out, float* c_f, cudaStream_t st);
 cudaError_t launch_rev_reduce_t(const float* P, int splits, int kcols, int bn, int S, int kvalid,
                                 const double* s1, const double* s2, int lam_col, int nJ,
                                 void* const z[3], int ld, double* c_out, float* c_f, double* J_out,

@@ -70,7 +70,9 @@ struct nnc_net {
   void* At[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [ping-pong][hi, lo]
   void* Zt[2] = {nullptr, nullptr};  // [hi, lo]: Zdot_l^T of all curved layers, n x K_total
   void* Yt[2] = {nullptr, nullptr};  // [hi, lo]: (c_l * Zdot_l)^T, n x K_total
-  int K_total = 0;                   // sum of mp_l over layers with sigma'' != 0
+  int K_total = 0;                   // sum of mp_l over layers with sigma'' != 0 (+ 128: softmax)
+  bool softmax = false;              // softmax output layer
+  int ext_off = -1;                  // its two rank-two curvature columns in the Zdot / Ydot arrays
   void* Zb[2][3] = {};  // reverse seeds^T [48][mp_max], ping-pong x three BF16 parts
   float* Prev = nullptr;             // split partials of the tensor-core reverse step
   bool tc_rev = false;               // reverse sweep on the tensor cores

@@ -141,6 +141,7 @@ int run_forward(nnc_net* net, bool fp64, cudaStream_t st) {
                          Ly.s2, st));
       a_in = Ly.a;
     }
+    if (net->softmax) CK(launch_softmax_head(net->n_out, net->layers.back().a, st));
     return NNC_OK;
   }
   const void* a_in2 = net->x2;
@@ -150,6 +151,7 @@ int run_forward(nnc_net* net, bool fp64, cudaStream_t st) {
                              net->dev_err, net->sm_count, st));
     a_in2 = Ly.a2;
   }
+  if (net->softmax) CK(launch_softmax_head(net->n_out, net->layers.back().a, st));
   return NNC_OK;
 }
 
@@ -166,15 +168,16 @@ int run_forward_fp64_values(nnc_net* net, const double* x, cudaStream_t st) {
                          nullptr, nullptr, st));
       a_in = Ly.ra;
     }
-    return NNC_OK;
+  } else {
+    const void* a_in2 = net->xr2;
+    for (auto& Ly : net->layers) {
+      PROF(PK_FWD);
+      CK(launch_gemv_stream_df(Ly.W2, Ly.kp, Ly.m, Ly.b, a_in2, Ly.act, Ly.ra, Ly.ra2, nullptr,
+                               nullptr, net->dev_err, net->sm_count, st));
+      a_in2 = Ly.ra2;
+    }
   }
-  const void* a_in2 = net->xr2;
-  for (auto& Ly : net->layers) {
-    PROF(PK_FWD);
-    CK(launch_gemv_stream_df(Ly.W2, Ly.kp, Ly.m, Ly.b, a_in2, Ly.act, Ly.ra, Ly.ra2, nullptr,
-                             nullptr, net->dev_err, net->sm_count, st));
-    a_in2 = Ly.ra2;
-  }
+  if (net->softmax) CK(launch_softmax_head(net->n_out, net->layers.back().ra, st));
   return NNC_OK;
 }
 
@@ -188,10 +191,11 @@ int run_reverse(nnc_net* net, bool fp64, int nJ, bool with_lam, const double* la
   const int lam_col = with_lam ? nJ : -1;
   const bool tc = is_tc(net->prec);
   LayerDev& Lo = net->layers.back();
+  const double* soft_p = net->softmax ? Lo.a : nullptr;   // softmax probabilities (value pass)
   if (net->tc_rev) {
     // seeds^T in three BF16 parts, then per layer: split-K tensor-core product W_l^T Zbar and a reduce
     // that forms the next seeds (or J and the gradient on the first layer)
-    CK(launch_rev_seed_t(Lo.m, S, nJ, lam_col, Lo.s1, Lo.s2, lam, net->Zb[0], Lo.mp,
+    CK(launch_rev_seed_t(Lo.m, S, nJ, lam_col, Lo.s1, Lo.s2, lam, soft_p, net->Zb[0], Lo.mp,
                          with_lam ? Lo.c : nullptr, with_lam ? Lo.c_f : nullptr, st));
     for (int l = net->L - 1; l >= 0; --l) {
       LayerDev& Ly = net->layers[l];
@@ -213,7 +217,7 @@ int run_reverse(nnc_net* net, bool fp64, int nJ, bool with_lam, const double* la
   }
   if (net->rev_stream) {
     // FP32 weights streamed by TMA, one launch per layer (the layer boundary is fused in)
-    CK(launch_rev_seed_f(Lo.m, S, nJ, lam_col, Lo.s1, Lo.s2, lam, net->Zf[0],
+    CK(launch_rev_seed_f(Lo.m, S, nJ, lam_col, Lo.s1, Lo.s2, lam, soft_p, net->Zf[0],
                          with_lam ? Lo.c : nullptr, (with_lam && tc) ? Lo.c_f : nullptr, st));
     int cur = 0;
     for (int l = net->L - 1; l >= 0; --l) {
@@ -235,7 +239,7 @@ int run_reverse(nnc_net* net, bool fp64, int nJ, bool with_lam, const double* la
     }
     return NNC_OK;
   }
-  CK(launch_rev_seed(Lo.m, S, nJ, lam_col, Lo.s1, Lo.s2, lam, net->Zbar[0],
+  CK(launch_rev_seed(Lo.m, S, nJ, lam_col, Lo.s1, Lo.s2, lam, soft_p, net->Zbar[0],
                      with_lam ? Lo.c : nullptr, (with_lam && tc) ? Lo.c_f : nullptr, st));
   int cur = 0;
   for (int l = net->L - 1; l >= 0; --l) {
@@ -262,7 +266,7 @@ int run_reverse(nnc_net* net, bool fp64, int nJ, bool with_lam, const double* la
 // Forward tangents layer by layer (Zdot_1 = W_1 elementwise; Zdot_l = W_l Adot_{l-1} as a GEMM
 // with the n_in tangents as columns), each layer's Zdot_l and c_l * Zdot_l stored side by side
 // along K; then one symmetric product H = sum_l Zdot_l^T diag(c_l) Zdot_l.
-int run_hessian(nnc_net* net, double* H, cudaStream_t st) {
+int run_hessian(nnc_net* net, const double* lam, double* H, cudaStream_t st) {
   const int n = net->n_in;
   const int prec = net->prec;
   const bool tc = is_tc(prec);
@@ -307,6 +311,16 @@ int run_hessian(nnc_net* net, double* H, cudaStream_t st) {
     }
     cur = 1 - cur;
   }
+  if (net->softmax) {
+    // the rank-two part of the softmax layer's curvature as two extra operand columns
+    LayerDev& Lo = net->layers.back();
+    PROF(PK_OTHER);
+    CK(launch_softmax_ext(e, n, net->n_out, Lo.a, lam,
+                          TanBuf{zoff(net->Zt[0], Lo.zy_off), zoff(net->Zt[1], Lo.zy_off)},
+                          TanBuf{zoff(net->Zt[0], net->ext_off), zoff(net->Zt[1], net->ext_off)},
+                          TanBuf{zoff(net->Yt[0], net->ext_off), zoff(net->Yt[1], net->ext_off)},
+                          net->K_total, st));
+  }
   if (net->K_total == 0) {  // every layer is linear: H = 0
     CK(cudaMemsetAsync(H, 0, sizeof(double) * n * n, st));
     return NNC_OK;
@@ -348,7 +362,7 @@ int eval_all(nnc_net* net, const double* x, const double* lam, double* y, double
     if (r != NNC_OK) return r;
   }
   if (H) {
-    r = run_hessian(net, H, st);
+    r = run_hessian(net, lam, H, st);
     if (r != NNC_OK) return r;
   }
   return NNC_OK;
@@ -586,6 +600,12 @@ static int load_impl(nnc_net* net, int n_layers, const int* widths, const int* a
     Ly.zy_off = Ly.act == NNC_IDENTITY ? -1 : net->K_total;
     if (Ly.zy_off >= 0) net->K_total += Ly.mp;
   }
+  // softmax output: two more columns (one padded block) carry the rank-two part of its curvature
+  net->softmax = net->layers.back().act == NNC_SOFTMAX;
+  if (net->softmax) {
+    net->ext_off = net->K_total;
+    net->K_total += kPad;
+  }
   const size_t tan_elems = (size_t)n * mp_max;
   const size_t zy_elems = (size_t)n * std::max(net->K_total, kPad);
   const size_t es = elem_size(prec);
@@ -683,7 +703,9 @@ int nnc_load_weights(nnc_net** out, int n_layers, const int* widths, const int* 
   for (int l = 0; l <= n_layers; ++l)
     if (widths[l] < 1 || widths[l] > 65536) return fail(NNC_ERR_ARG, "width out of range [1, 65536]");
   for (int l = 0; l < n_layers; ++l) {
-    if (act[l] < NNC_IDENTITY || act[l] > NNC_GELU) return fail(NNC_ERR_ARG, "bad activation code");
+    if (act[l] < NNC_IDENTITY || act[l] > NNC_SOFTMAX) return fail(NNC_ERR_ARG, "bad activation code");
+    if (act[l] == NNC_SOFTMAX && (l != n_layers - 1 || widths[n_layers] > 64))
+      return fail(NNC_ERR_ARG, "softmax is an output-layer activation with at most 64 outputs");
     if (!W[l]) return fail(NNC_ERR_ARG, "W[l] is NULL");
   }
   if (prec < NNC_FP64 || prec > NNC_FP8) return fail(NNC_ERR_ARG, "bad precision code");

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "libnnc.so")
 
 FP64, FP32, BF16, BF16X3, FP8 = 0, 1, 2, 3, 4
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": BF16, "bf16x3": BF16X3, "fp8": FP8}
-ACTS = {"identity": 0, "tanh": 1, "sigmoid": 2, "softplus": 3, "gelu": 4}
+ACTS = {"identity": 0, "tanh": 1, "sigmoid": 2, "softplus": 3, "gelu": 4, "softmax": 5}
 WANT_Y, WANT_J, WANT_H, WANT_G = 1, 2, 4, 8
 STATUS = {0: "NNC_OK", -1: "NNC_ERR_ARG", -2: "NNC_ERR_CUDA", -3: "NNC_ERR_NONFINITE",
           -4: "NNC_ERR_TIMEOUT", -5: "NNC_ERR_OOM", -6: "NNC_ERR_UNSUPPORTED"}

@@ -188,3 +188,26 @@ def test_scopf_68m_sampled(lib, prec):
     assert e["y"] < t["y"] and e["J"] < t["J"] and e["H"] < t["H"] and e["g"] < t["J"], e
     assert np.array_equal(H, H.T)
     net.free()
+
+
+SOFTMAX = [
+    ([784, 128, 128, 10], ["tanh", "tanh", "softmax"]),          # the MNIST classifier shape
+    ([33, 130, 257, 10], ["sigmoid", "softplus", "softmax"]),
+    ([200, 129, 64, 37], ["gelu", "tanh", "softmax"]),            # > 15 outputs: tensor-core reverse
+    ([5, 4], ["softmax"]),                                         # single layer: first-layer tangents
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3", "bf16"])
+@pytest.mark.parametrize("case", range(len(SOFTMAX)))
+def test_softmax_output(lib, prec, case):
+    """Softmax output layer (Section 4.1's classifiers): value, Jacobian, gradient and the full
+    Hessian (diagonal curvature through the tangent epilogue, rank-two coupling as extra operand
+    columns) against the oracle."""
+    widths, acts = SOFTMAX[case]
+    mlp = make_mlp(MLPSpec(widths, acts), seed=case + 20, tag="softmax", bias_std=0.2)
+    x = synth.uniform01(synth.derive_key(case, "sm-x"), widths[0])
+    lam = synth.normal(synth.derive_key(case, "sm-lam"), widths[-1])
+    e = _check_all(lib, mlp, x, lam, prec, f"softmax{case}")
+    yo = onn.value(mlp, x)
+    assert abs(yo.sum() - 1.0) < 1e-12
