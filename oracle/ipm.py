@@ -31,8 +31,9 @@ terms -mu/(v - L) + mu/(U - v) plus the bound multipliers they replace.  The ste
 A warm start (a predicted point v, lambda) replaces the start: v pushed into the bounds as above,
 lambda as given, mu = warm_mu0 = 1e-3 and z = mu / slack, so every complementarity product starts
 at mu.
-The inertia here is the plain definition (signs of the eigenvalues, numpy eigvalsh); the
-solve is numpy's dense solver.  Iteration counts need not match IPOPT's (no filter, no
+The inertia here is the plain definition (signs of the eigenvalues, numpy eigvalsh, taken on a
+congruent diagonally scaled copy so that the zero test is scale-invariant); the solve is numpy's
+dense solver.  Iteration counts need not match IPOPT's (no filter, no
 second-order correction, no restoration phase).
 """
 from dataclasses import dataclass, field
@@ -113,7 +114,14 @@ def _errors(p, v, lam, zL, zU, mu, g, cval, A, hasL, hasU, s_max):
 
 
 def _inertia(K, tol=0.0):
-    ev = np.linalg.eigvalsh(K)
+    """(positive, negative, zero) eigenvalue counts of K.  The signs are taken after a symmetric
+    diagonal scaling D K D (D_ii = 1 / sqrt(max_j |K_ij|)): a congruence, so by Sylvester's law of
+    inertia the counts are those of K, while the zero test (relative to the largest eigenvalue)
+    no longer mistakes the small negative eigenvalues of a badly scaled KKT matrix (barrier terms
+    of order 1e10 next to constraint rows of order 1) for zeros."""
+    rmax = np.abs(K).max(axis=1)
+    d = 1.0 / np.sqrt(np.where(rmax > 0.0, rmax, 1.0))
+    ev = np.linalg.eigvalsh(K * d[:, None] * d[None, :])
     scale = max(1.0, np.abs(ev).max())
     zero = np.abs(ev) <= 1e-14 * scale
     return int(((ev > 0) & ~zero).sum()), int(((ev < 0) & ~zero).sum()), int(zero.sum())

@@ -2,8 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY.
 
-Adversarial problem (a synthetic variant of Eq. 7; the paper's L1 objective and softmax
-confidence threshold are replaced by an L2 objective and logit margins):
+Adversarial problems.  `adversarial_l1` is Eq. 7 itself (L1 objective through split variables,
+softmax confidence threshold); `adversarial` is a smooth variant (L2 objective, logit margins):
     variables v = (x in [0,1]^n_in, y in R^n_out, s in R^(n_out-1), s >= 0)
     min ||x - x0||^2
     s.t. y - NN(x) = 0                                   (the reduced-space constraint, Eq. 5)
@@ -67,6 +67,58 @@ def adversarial(mlp, x0, target=3, margin=0.1):
     p = Problem(nv, m, lb, ub, v0, f, grad_f, hess_f, c, jac_c, hess_c)
     p.blocks = dict(n_in=n_in, n_out=n_out, ns=ns, target=target, margin=margin)
     return p
+
+
+def adversarial_l1(mlp, x_ref, target, conf=0.6):
+    """Eq. 7: the smallest L1 change to a reference image that makes a softmax classifier give the
+    target class probability `conf` or more.  The L1 norm is written with split variables
+    x - x_ref = p - q, p, q >= 0, so the objective is linear and smooth:
+        variables v = (x in [0,1]^n, p >= 0, q >= 0, y with y_t >= conf)
+        min sum(p) + sum(q)
+        s.t. x - p + q - x_ref = 0,   y - NN(x) = 0.
+    Start: x = x_ref, p = q = 0, y = NN(x_ref) (the solver pushes them into their bounds)."""
+    n, n_out = mlp.spec.n_in, mlp.spec.n_out
+    nv = 3 * n + n_out
+    m = n + n_out
+    ix, ip, iq, iy = (slice(0, n), slice(n, 2 * n), slice(2 * n, 3 * n), slice(3 * n, nv))
+    lb = np.concatenate([np.zeros(3 * n), np.full(n_out, -np.inf)])
+    ub = np.concatenate([np.ones(n), np.full(2 * n + n_out, np.inf)])
+    lb[3 * n + target] = conf
+    x_ref = np.asarray(x_ref, dtype=np.float64)
+    v0 = np.concatenate([x_ref, np.zeros(2 * n), onn.value(mlp, x_ref)])
+
+    def f(v):
+        return float(np.sum(v[ip]) + np.sum(v[iq]))
+
+    def grad_f(v):
+        g = np.zeros(nv)
+        g[ip] = 1.0
+        g[iq] = 1.0
+        return g
+
+    def hess_f(v):
+        return np.zeros((nv, nv))
+
+    def c(v):
+        return np.concatenate([v[ix] - v[ip] + v[iq] - x_ref, v[iy] - onn.value(mlp, v[ix])])
+
+    def jac_c(v):
+        A = np.zeros((m, nv))
+        A[:n, ix] = np.eye(n)
+        A[:n, ip] = -np.eye(n)
+        A[:n, iq] = np.eye(n)
+        A[n:, ix] = -onn.jacobian(mlp, v[ix])
+        A[n:, iy] = np.eye(n_out)
+        return A
+
+    def hess_c(v, lam):
+        Hh = np.zeros((nv, nv))
+        Hh[ix, ix] = -onn.hessian_lag(mlp, v[ix], lam[n:])
+        return Hh
+
+    pr = Problem(nv, m, lb, ub, v0, f, grad_f, hess_f, c, jac_c, hess_c)
+    pr.blocks = dict(n_in=n, n_out=n_out, target=target, conf=conf)
+    return pr
 
 
 def box_projection(x0):

@@ -109,3 +109,52 @@ def test_status_codes():
     p = problems.box_projection(x0)
     p.f = lambda v: float("nan")
     assert ipm.solve(p).status == ipm.NONFINITE
+
+
+def _l1_instance(seed, n=20, scale=4.0):
+    """A small softmax classifier whose output layer is scaled so that its probabilities are as
+    peaked as a trained classifier's (the 0.6 threshold of Eq. 7 is then reachable)."""
+    mlp = make_mlp(MLPSpec([n, 16, 16, 5], ["tanh", "tanh", "softmax"]), seed=seed, tag="l1",
+                   bias_std=0.3)
+    mlp.W[-1] = mlp.W[-1] * scale
+    x = synth.uniform01(synth.derive_key(seed, "l1-x"), n)
+    p0 = onn.value(mlp, x)
+    return mlp, x, int(np.argsort(p0)[-2])
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_l1_adversarial_against_slsqp(seed):
+    """Eq. 7 with split variables: the IPM's optimum has p q = 0 componentwise, its objective is
+    ||x - x_ref||_1, the confidence constraint is active, and scipy's SLSQP on the same smooth
+    program from the same start reaches the same objective."""
+    from scipy.optimize import minimize
+    mlp, x_ref, t = _l1_instance(seed)
+    n = x_ref.size
+    pr = problems.adversarial_l1(mlp, x_ref, t, 0.6)
+    r = ipm.solve(pr)
+    assert r.status == ipm.OPTIMAL, r.status
+    x, p, q = r.v[:n], r.v[n:2 * n], r.v[2 * n:3 * n]
+    assert np.max(np.minimum(p, q)) < 1e-6
+    # at the barrier optimum both split variables of an unchanged pixel sit at ~1e-7 (complementarity
+    # mu <= tol / 10 with multipliers of order one), so sum(p + q) exceeds ||x - x_ref||_1 by
+    # 2 sum(min(p, q)) <= 2 n 1e-7
+    assert abs(r.obj - np.abs(x - x_ref).sum()) < 2e-7 * n + 1e-9
+    assert abs(onn.value(mlp, x)[t] - 0.6) < 1e-6
+    cons = [{"type": "eq", "fun": pr.c, "jac": pr.jac_c}]
+    bounds = list(zip(np.where(np.isfinite(pr.lb), pr.lb, None), np.where(np.isfinite(pr.ub), pr.ub, None)))
+    s = minimize(pr.f, pr.v0, jac=pr.grad_f, bounds=bounds, constraints=cons, method="SLSQP",
+                 options={"ftol": 1e-12, "maxiter": 500})
+    assert s.success, s.message
+    assert abs(s.fun - r.obj) < 1e-5 * max(1.0, r.obj), (s.fun, r.obj)
+
+
+def test_l1_adversarial_already_confident():
+    """If the reference image already has target probability >= 0.6 the answer is x = x_ref with
+    objective 0 (p = q = 0)."""
+    mlp, x_ref, _ = _l1_instance(3)
+    t = int(np.argmax(onn.value(mlp, x_ref)))
+    conf = 0.5 * onn.value(mlp, x_ref)[t]
+    r = ipm.solve(problems.adversarial_l1(mlp, x_ref, t, conf))
+    assert r.status == ipm.OPTIMAL
+    assert r.obj < 2e-7 * x_ref.size + 1e-9   # barrier floor of the split variables (see above)
+    assert np.max(np.abs(r.v[:x_ref.size] - x_ref)) < 1e-5
