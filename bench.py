@@ -46,7 +46,8 @@ def _args():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--prec", default="bf16x3", choices=["bf16x3", "bf16", "fp32", "fp64"])
-    p.add_argument("--workload", default="104m", choices=["104m", "87m", "tiny", "scopf68m", "scopf"])
+    p.add_argument("--workload", default="104m", choices=["104m", "87m", "tiny", "scopf68m", "scopf", "70m",
+                                                              "274m"])
     p.add_argument("--scopf-k", type=int, default=256)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64-form", action="store_true")
@@ -58,17 +59,21 @@ def _args():
 def _workload(name):
     import synth
     spec = synth.spec_by_name(name)
-    mlp = synth.make_mlp(spec, seed=0)
+    # the softmax classifiers (Eq. 7) use the trained-classifier stand-in; the rest plain N(0, 1/fan_in)
+    mlp = synth.make_classifier(spec, seed=0) if spec.acts[-1] == "softmax" else synth.make_mlp(spec, seed=0)
     d = synth.adversarial_data(n_in=spec.n_in, n_out=spec.n_out, seed=0)
     return spec, mlp, d
 
 
 def _workload_config(spec, name, prec):
     kind = "scopf_single" if name.startswith("scopf") else "mnist"
-    return {"workload": f"{kind}_{name}_{'x'.join(map(str, spec.widths))}_tanh",
+    acts = spec.acts[0] + ("+softmax" if spec.acts[-1] == "softmax" else "")
+    weights = ("N(0,16/fan_in) sigmoid / N(0,1/fan_in) tanh hidden, logits x3 (classifier stand-in)"
+               if spec.acts[-1] == "softmax" else "N(0,1/fan_in)")
+    return {"workload": f"{kind}_{name}_{'x'.join(map(str, spec.widths))}_{acts}",
             "n_params": spec.n_params, "n_in": spec.n_in, "n_out": spec.n_out,
             "precision_form": prec,
-            "inputs": f"x0~U[0,1]^{spec.n_in}, lambda~N(0,1), weights N(0,1/fan_in) seed 0",
+            "inputs": f"x0~U[0,1]^{spec.n_in}, lambda~N(0,1), weights {weights} seed 0",
             "l2": "weights exceed L2 (no flush needed)"}
 
 
@@ -518,10 +523,16 @@ def run_ours(args, rank, world, local_rank):
                "d2h_bytes_per_step": d2h}
 
     # IPM solve of the adversarial problem to KKT tolerance 1e-6 with this form
+    # (Eq. 7 with its L1 objective and 0.6 confidence for a softmax classifier, else the
+    # margin form of the adversarial problem)
+    def solve(nt):
+        if spec.acts[-1] == "softmax":
+            return nnc.ipm_adversarial_l1(nt, d.x0, d.target, 0.6)[0]
+        return nnc.ipm_adversarial(nt, d.x0, d.target, d.margin)[0]
+
     ipm = {}
     if rank == 0 and not args.no_ipm:
-        res, v, lam_ipm = nnc.ipm_adversarial(net, d.x0, d.target, d.margin)
-        ipm[args.prec] = res
+        ipm[args.prec] = solve(net)
 
     # the FP64 form on the same GPU, for the TC-vs-FP64 comparison of the metric
     forms = {args.prec: {"evals_per_s": value / world, "ms_per_eval": el_ms / args.steps}}
@@ -529,8 +540,7 @@ def run_ours(args, rank, world, local_rank):
         net.free()
         n64 = nnc.Net.from_mlp(mlp, precision="fp64")
         if not args.no_ipm:
-            res, v, lam_ipm = nnc.ipm_adversarial(n64, d.x0, d.target, d.margin)
-            ipm["fp64"] = res
+            ipm["fp64"] = solve(n64)
 
         def step64():
             n64.eval_kkt_dev(x, y_it, lam, r, J, H, g)

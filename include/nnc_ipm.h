@@ -74,12 +74,28 @@ void nnc_ipm_default_options(nnc_ipm_options* opt);
  *   rhs_sol : n + m doubles, the right-hand side on entry, the solution on return (left
  *             unchanged when K is singular);
  *   inertia : 4 ints (may be NULL): positive, negative and zero eigenvalue counts of K, and 1
- *             if the whole matrix had to be factorized (W_DD block not positive definite).
- * Factorization: blocked Cholesky of the first block and Bunch-Kaufman LDL^T of its Schur
- * complement, or Bunch-Kaufman of all of K; the inertia is exact either way (Sylvester). */
+ *             if the whole matrix had to be factorized (first block not positive definite and
+ *             a negative small-block diagonal entry), else 0.
+ * Factorization: rows that pin one dense variable through slack variables of their own (such
+ * as x_i - p_i + q_i = x_ref,i) are eliminated first; then blocked Cholesky of the first block
+ * and Bunch-Kaufman LDL^T of the reduced multiplier system, or, when the first block is
+ * indefinite, Bunch-Kaufman of the dense block, the zero-diagonal variables and the multipliers
+ * together (positive small-block diagonals eliminated), or of all of K.  The inertia is exact
+ * in every form (Sylvester / Haynsworth). */
 int nnc_kkt_solve(int nd, int ns, int m, const double* WDD, const double* WSS, const double* sigma,
                   const double* AD, const double* AS, double delta_w, double delta_c,
                   double* rhs_sol, int* inertia);
+
+/* Eq. 7 itself: the smallest L1 change to the reference image x_ref that makes the classifier's
+ * output t at least conf (a probability, for a softmax output layer: 0 < conf < 1).  Split
+ * variables carry the L1 norm: v = (x in [0,1]^n_in, p >= 0, q >= 0 in R^n_in, y in R^n_out with
+ * y_t >= conf),  min sum(p) + sum(q)  s.t.  x - p + q - x_ref = 0,  y - NN(x) = 0.
+ * Start: x = x_ref, p = q = 0, y = NN(x_ref) (pushed into the bounds by the solver).
+ *   v_out   : 3 n_in + n_out doubles (may be NULL);  lam_out : n_in + n_out doubles (may be NULL).
+ *   result  : may be NULL. */
+int nnc_ipm_adversarial_l1(nnc_net* net, const double* x_ref, int target, double conf,
+                           const nnc_ipm_options* opt, double* v_out, double* lam_out,
+                           nnc_ipm_result* result);
 
 /* The adversarial problem (a synthetic variant of Eq. 7): variables v = (x, y, s) with
  * x in [0,1]^n_in, y in R^n_out, s in R^(n_out-1), s >= 0;

@@ -299,12 +299,107 @@ struct BK {
 struct KktSolver {
   int nd = 0, ns = 0, m = 0, n = 0, r = 0;
   std::vector<double> K11, K12, Y, Sm, Kfull, tmp, Dinv, T, AS_;
-  BK bkS, bkF, bkT;
-  int mode = 0;  // 0: Schur of the small block (BK); 1: whole matrix (BK); 2: diagonal small block
+  BK bkS, bkF, bkT, bkR;
+  std::vector<int> zid;   // mode 3: small-block variables with a zero diagonal (free, no curvature)
+  std::vector<double> R;
+  // 0: Schur of the small block (BK); 1: whole matrix (BK); 2: diagonal small block; 3: diagonal
+  // small block with zero entries kept next to the multipliers; 4: indefinite dense block (BK of
+  // the dense block, the zero-diagonal variables and the multipliers)
+  int mode = 0;
   bool t_chol = false;
   int npos = 0, nneg = 0, nzero = 0;
+
+  // Rows eliminated before the rest ("pinning" rows, such as x_i - p_i + q_i = x_ref,i of the L1
+  // problem): at most one nonzero in A_D, and slack columns with a positive diagonal that no
+  // other row touches.  Eliminating the slacks leaves row j as a_j w_D[i_j] - e_j u_j = r~3_j with
+  // e_j = dc + sum_c A_S[j,c]^2 / D_c > 0, and eliminating u_j adds a_j^2 / e_j to K11[i_j, i_j];
+  // each such row adds one negative eigenvalue to the inertia (Haynsworth).
+  struct PinTerm { int row, col; double a; };
+  int m_all = 0, n_all = 0;
+  std::vector<int> prow, pcol, orow;        // pinning rows, their A_D column (-1: none), other rows
+  std::vector<double> palpha, pe, pD, r3t;
+  std::vector<PinTerm> pterm;               // slack entries of the pinning rows
+  std::vector<double> WDDp, ADo, ASo, core;
   void factor(int nd_, int ns_, int m_, const double* WDD, const double* WSS, const double* sig,
               const double* AD, const double* AS, double dw, double dc, double zero_tol) {
+    m_all = m_;
+    n_all = nd_ + ns_;
+    prow.clear(); pcol.clear(); orow.clear(); palpha.clear(); pe.clear(); pterm.clear();
+    pD.assign(ns_, 0.0);
+    std::vector<int> ccount(ns_, 0);
+    for (int j = 0; j < m_; ++j)
+      for (int c = 0; c < ns_; ++c)
+        if (AS[(size_t)j * ns_ + c] != 0.0) ++ccount[c];
+    for (int c = 0; c < ns_; ++c) pD[c] = WSS[c] + sig[nd_ + c] + dw;
+    for (int j = 0; j < m_; ++j) {
+      int col = -1, nnz = 0;
+      for (int i = 0; i < nd_ && nnz < 2; ++i)
+        if (AD[(size_t)j * nd_ + i] != 0.0) { col = i; ++nnz; }
+      bool pin = nnz <= 1;
+      double e = dc;
+      for (int c = 0; c < ns_ && pin; ++c) {
+        const double a = AS[(size_t)j * ns_ + c];
+        if (a == 0.0) continue;
+        pin = ccount[c] == 1 && pD[c] > 0.0;
+        e += a * a / pD[c];
+      }
+      if (pin && e > 0.0) {
+        prow.push_back(j);
+        pcol.push_back(col);
+        palpha.push_back(col >= 0 ? AD[(size_t)j * nd_ + col] : 0.0);
+        pe.push_back(e);
+        for (int c = 0; c < ns_; ++c)
+          if (AS[(size_t)j * ns_ + c] != 0.0) pterm.push_back({(int)prow.size() - 1, c, AS[(size_t)j * ns_ + c]});
+      } else {
+        orow.push_back(j);
+      }
+    }
+    if (prow.empty()) {
+      factor_core(nd_, ns_, m_, WDD, WSS, sig, AD, AS, dw, dc, zero_tol);
+      return;
+    }
+    WDDp.assign(WDD, WDD + (size_t)nd_ * nd_);
+    for (size_t k = 0; k < prow.size(); ++k)
+      if (pcol[k] >= 0) WDDp[(size_t)pcol[k] * nd_ + pcol[k]] += palpha[k] * palpha[k] / pe[k];
+    const int mo = (int)orow.size();
+    ADo.assign((size_t)mo * nd_, 0.0);
+    ASo.assign((size_t)mo * ns_, 0.0);
+    for (int k = 0; k < mo; ++k) {
+      std::memcpy(&ADo[(size_t)k * nd_], &AD[(size_t)orow[k] * nd_], sizeof(double) * nd_);
+      std::memcpy(&ASo[(size_t)k * ns_], &AS[(size_t)orow[k] * ns_], sizeof(double) * ns_);
+    }
+    factor_core(nd_, ns_, mo, WDDp.data(), WSS, sig, ADo.data(), ASo.data(), dw, dc, zero_tol);
+    nneg += (int)prow.size();
+  }
+
+  // rhs (n + m) -> solution, in place
+  void solve(double* rhs) {
+    if (prow.empty()) {
+      solve_core(rhs);
+      return;
+    }
+    const int np = (int)prow.size(), mo = (int)orow.size();
+    // r~3_j = r3_j - sum_c A_S[j,c] r2_c / D_c; r1 += a_j r~3_j / e_j
+    r3t.assign(np, 0.0);
+    for (int k = 0; k < np; ++k) r3t[k] = rhs[n_all + prow[k]];
+    for (const PinTerm& t : pterm) r3t[t.row] -= t.a * rhs[nd + t.col] / pD[t.col];
+    core.assign(rhs, rhs + n_all + mo);
+    for (int k = 0; k < np; ++k)
+      if (pcol[k] >= 0) core[pcol[k]] += palpha[k] * r3t[k] / pe[k];
+    for (int k = 0; k < mo; ++k) core[n_all + k] = rhs[n_all + orow[k]];
+    const std::vector<double> r2(rhs + nd, rhs + n_all);
+    solve_core(core.data());
+    std::vector<double> u(np);
+    for (int k = 0; k < np; ++k)
+      u[k] = ((pcol[k] >= 0 ? palpha[k] * core[pcol[k]] : 0.0) - r3t[k]) / pe[k];
+    for (const PinTerm& t : pterm) core[nd + t.col] = (r2[t.col] - t.a * u[t.row]) / pD[t.col];
+    std::copy(core.begin(), core.begin() + n_all, rhs);
+    for (int k = 0; k < mo; ++k) rhs[n_all + orow[k]] = core[n_all + k];
+    for (int k = 0; k < np; ++k) rhs[n_all + prow[k]] = u[k];
+  }
+
+  void factor_core(int nd_, int ns_, int m_, const double* WDD, const double* WSS, const double* sig,
+                   const double* AD, const double* AS, double dw, double dc, double zero_tol) {
     nd = nd_;
     ns = ns_;
     m = m_;
@@ -314,8 +409,59 @@ struct KktSolver {
     std::memcpy(K11.data(), WDD, sizeof(double) * nd * nd);
     for (int i = 0; i < nd; ++i) K11[(size_t)i * nd + i] += sig[i] + dw;
     const bool pd = nd == 0 || cholesky(nd, K11.data());
-    bool diag_pd = pd && ns > 0;
-    for (int a = 0; a < ns && diag_pd; ++a) diag_pd = WSS[a] + sig[nd + a] + dw > 0.0;
+    bool diag_ok = pd && ns > 0;
+    zid.clear();
+    for (int a = 0; a < ns && diag_ok; ++a) {
+      const double d = WSS[a] + sig[nd + a] + dw;
+      diag_ok = d >= 0.0;
+      if (d == 0.0) zid.push_back(a);
+    }
+    if (diag_ok && !zid.empty() && m == 0) diag_ok = false;
+    const bool diag_pd = diag_ok && zid.empty();
+    if (diag_ok && !zid.empty()) {
+      // Zero-diagonal variables w_Z (free, no curvature) stay beside the multipliers: with the
+      // dense block and the positive diagonal entries eliminated,
+      //   R = [[0, A_Z^T], [A_Z, -T]],  T = dc I + A_D K11^-1 A_D^T + A_P D_P^-1 A_P^T,
+      // and inertia(K) = (nd + |P|, 0, 0) + inertia(R).
+      mode = 3;
+      Dinv.assign(ns, 0.0);
+      for (int a = 0; a < ns; ++a) {
+        const double d = WSS[a] + sig[nd + a] + dw;
+        Dinv[a] = d > 0.0 ? 1.0 / d : 0.0;
+      }
+      AS_.assign(AS, AS + (size_t)m * ns);
+      Y.assign((size_t)nd * m, 0.0);
+      for (int i = 0; i < nd; ++i)
+        for (int j = 0; j < m; ++j) Y[(size_t)i * m + j] = AD[(size_t)j * nd + i];
+      if (nd) lower_solve(nd, K11.data(), m, Y.data());
+      const int nz = (int)zid.size(), nr = nz + m;
+      R.assign((size_t)nr * nr, 0.0);
+#pragma omp parallel for schedule(dynamic, 4) if (m >= 64)
+      for (int a = 0; a < m; ++a) {
+        for (int b = 0; b <= a; ++b) {
+          double s = 0;
+          for (int i = 0; i < nd; ++i) s += Y[(size_t)i * m + a] * Y[(size_t)i * m + b];
+          const double* ra = &AS_[(size_t)a * ns];
+          const double* rb = &AS_[(size_t)b * ns];
+          for (int c = 0; c < ns; ++c)
+            if (ra[c] != 0.0 && rb[c] != 0.0) s += ra[c] * rb[c] * Dinv[c];
+          const double t = -(s + (a == b ? dc : 0.0));
+          R[(size_t)(nz + a) * nr + nz + b] = t;
+          R[(size_t)(nz + b) * nr + nz + a] = t;
+        }
+      }
+      for (int q = 0; q < nz; ++q)
+        for (int j = 0; j < m; ++j) {
+          const double v = AS[(size_t)j * ns + zid[q]];
+          R[(size_t)q * nr + nz + j] = v;
+          R[(size_t)(nz + j) * nr + q] = v;
+        }
+      bkR.factor(nr, R.data(), zero_tol);
+      npos = nd + (ns - nz) + bkR.npos;
+      nneg = bkR.nneg;
+      nzero = bkR.nzero;
+      return;
+    }
     if (diag_pd) {
       // Eliminate the diagonal small block as well: T = -dc I - A_D K11^-1 A_D^T - A_S D^-1 A_S^T.
       // inertia(K) = (nd + ns, 0, 0) + inertia(T); T must be negative definite.
@@ -357,6 +503,14 @@ struct KktSolver {
         nzero = bkT.nzero;
       }
       return;
+    }
+    if (!pd && m > 0) {
+      bool nonneg = true;
+      for (int a = 0; a < ns && nonneg; ++a) nonneg = WSS[a] + sig[nd + a] + dw >= 0.0;
+      if (nonneg) {
+        factor_indefinite(WDD, WSS, sig, AD, AS, dw, dc, zero_tol);
+        return;
+      }
     }
     K12.assign((size_t)nd * r, 0.0);
     for (int i = 0; i < nd; ++i)
@@ -405,11 +559,126 @@ struct KktSolver {
       mode = 1;
     }
   }
+  // Mode 4: K11 is not positive definite but every small-block diagonal is >= 0.  The positive
+  // ones (P) are eliminated; the dense block, the zero-diagonal variables (Z) and the multipliers
+  // stay in one symmetric indefinite factorization of size nd + |Z| + m:
+  //   M = [[K11, 0, A_D^T], [0, 0, A_Z^T], [A_D, A_Z, -(dc I + A_P D_P^-1 A_P^T)]],
+  // inertia(K) = (|P|, 0, 0) + inertia(M).  Far smaller than the whole matrix when ns >> |Z|.
+  BK bkM;
+  void factor_indefinite(const double* WDD, const double* WSS, const double* sig, const double* AD,
+                         const double* AS, double dw, double dc, double zero_tol) {
+    mode = 4;
+    Dinv.assign(ns, 0.0);
+    zid.clear();
+    for (int a = 0; a < ns; ++a) {
+      const double d = WSS[a] + sig[nd + a] + dw;
+      if (d > 0.0) Dinv[a] = 1.0 / d;
+      else zid.push_back(a);
+    }
+    AS_.assign(AS, AS + (size_t)m * ns);
+    const int nz = (int)zid.size(), N = nd + nz + m;
+    std::vector<double> M((size_t)N * N, 0.0);
+    for (int i = 0; i < nd; ++i) {
+      std::memcpy(&M[(size_t)i * N], &WDD[(size_t)i * nd], sizeof(double) * nd);
+      M[(size_t)i * N + i] += sig[i] + dw;
+    }
+    const int u0 = nd + nz;
+    for (int j = 0; j < m; ++j)
+      for (int i = 0; i < nd; ++i)
+        M[(size_t)(u0 + j) * N + i] = M[(size_t)i * N + u0 + j] = AD[(size_t)j * nd + i];
+    for (int q = 0; q < nz; ++q)
+      for (int j = 0; j < m; ++j)
+        M[(size_t)(u0 + j) * N + nd + q] = M[(size_t)(nd + q) * N + u0 + j] = AS[(size_t)j * ns + zid[q]];
+    for (int j = 0; j < m; ++j)
+      for (int k = 0; k <= j; ++k) {
+        double t = j == k ? dc : 0.0;
+        const double* rj = &AS[(size_t)j * ns];
+        const double* rk = &AS[(size_t)k * ns];
+        for (int c = 0; c < ns; ++c)
+          if (rj[c] != 0.0 && rk[c] != 0.0) t += rj[c] * rk[c] * Dinv[c];
+        M[(size_t)(u0 + j) * N + u0 + k] = M[(size_t)(u0 + k) * N + u0 + j] = -t;
+      }
+    bkM.factor(N, M.data(), zero_tol);
+    npos = (ns - nz) + bkM.npos;
+    nneg = bkM.nneg;
+    nzero = bkM.nzero;
+  }
+  void solve_indefinite(double* rhs) {
+    // [w_D; w_Z; u] = M^-1 [r1; r2_Z; r3 - A_P D_P^-1 r2_P]; w_P = D_P^-1 (r2_P - A_P^T u)
+    const int nz = (int)zid.size(), N = nd + nz + m, u0 = nd + nz;
+    std::vector<double> q(N);
+    for (int i = 0; i < nd; ++i) q[i] = rhs[i];
+    for (int k = 0; k < nz; ++k) q[nd + k] = rhs[nd + zid[k]];
+    for (int j = 0; j < m; ++j) {
+      double s = rhs[n + j];
+      const double* ra = &AS_[(size_t)j * ns];
+      for (int c = 0; c < ns; ++c)
+        if (ra[c] != 0.0) s -= ra[c] * Dinv[c] * rhs[nd + c];
+      q[u0 + j] = s;
+    }
+    bkM.solve(q.data());
+    for (int c = 0; c < ns; ++c) {
+      if (Dinv[c] == 0.0) continue;
+      double s = rhs[nd + c];
+      for (int j = 0; j < m; ++j) s -= AS_[(size_t)j * ns + c] * q[u0 + j];
+      rhs[nd + c] = s * Dinv[c];
+    }
+    for (int k = 0; k < nz; ++k) rhs[nd + zid[k]] = q[nd + k];
+    for (int i = 0; i < nd; ++i) rhs[i] = q[i];
+    for (int j = 0; j < m; ++j) rhs[n + j] = q[u0 + j];
+  }
+
   bool full() const { return mode == 1; }
-  // rhs (n + m) -> solution, in place
-  void solve(double* rhs) {
+  void solve_core(double* rhs) {
+    if (mode == 4) {
+      solve_indefinite(rhs);
+      return;
+    }
     if (mode == 1) {
       bkF.solve(rhs);
+      return;
+    }
+    if (mode == 3) {
+      // [w_Z; z] = R^-1 [r2_Z; r3 - A_D K11^-1 r1 - A_P D_P^-1 r2_P]; then u and w_P as in mode 2
+      const int nz = (int)zid.size();
+      tmp.assign(rhs, rhs + nd);
+      if (nd) lower_solve1(nd, K11.data(), tmp.data());
+      std::vector<double> q(nz + m);
+      for (int k = 0; k < nz; ++k) q[k] = rhs[nd + zid[k]];
+      for (int j = 0; j < m; ++j) {
+        double s = rhs[n + j];
+        for (int i = 0; i < nd; ++i) s -= Y[(size_t)i * m + j] * tmp[i];
+        const double* ra = &AS_[(size_t)j * ns];
+        for (int c = 0; c < ns; ++c)
+          if (ra[c] != 0.0) s -= ra[c] * Dinv[c] * rhs[nd + c];
+        q[nz + j] = s;
+      }
+      bkR.solve(q.data());
+      const double* z = q.data() + nz;
+      std::vector<double> u(rhs, rhs + nd), yz(nd, 0.0);
+      for (int i = 0; i < nd; ++i) {
+        double s = 0;
+        for (int j = 0; j < m; ++j) s += Y[(size_t)i * m + j] * z[j];
+        yz[i] = s;
+      }
+      for (int i = nd - 1; i >= 0; --i) {   // A_D^T z = L (Y z)
+        double s = 0;
+        const double* li = &K11[(size_t)i * nd];
+        for (int j = 0; j <= i; ++j) s += li[j] * yz[j];
+        u[i] -= s;
+      }
+      if (nd) {
+        lower_solve1(nd, K11.data(), u.data());
+        upper_solve_lt(nd, K11.data(), u.data());
+      }
+      for (int c = 0; c < ns; ++c) {
+        double s = rhs[nd + c];
+        for (int j = 0; j < m; ++j) s -= AS_[(size_t)j * ns + c] * z[j];
+        rhs[nd + c] = s * Dinv[c];
+      }
+      for (int k = 0; k < nz; ++k) rhs[nd + zid[k]] = q[k];
+      for (int i = 0; i < nd; ++i) rhs[i] = u[i];
+      for (int j = 0; j < m; ++j) rhs[n + j] = z[j];
       return;
     }
     if (mode == 2) {
@@ -550,8 +819,20 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
   double E0 = INFINITY;
   std::vector<double> g(n), c(m), AD((size_t)m * nd), AS((size_t)m * ns), WDD((size_t)nd * nd),
       WSS(ns), vt(n), ct(m), rhs(n + m), sol(n + m), dv(n), dl(m), dzL(n), dzU(n), sL(n), sU(n),
-      SigL(n), SigU(n), sig(n), gphi(n);
+      SigL(n), SigU(n), sig(n), gphi(n), atl(n);
   KktSolver kkt;
+  // atl = A^T lam, row by row (contiguous reads of the dense Jacobian blocks)
+  auto update_atl = [&]() {
+    std::fill(atl.begin(), atl.end(), 0.0);
+    for (int j = 0; j < m; ++j) {
+      const double l = lam[j];
+      if (l == 0.0) continue;
+      const double* ad = &AD[(size_t)j * nd];
+      const double* as = &AS[(size_t)j * ns];
+      for (int i = 0; i < nd; ++i) atl[i] += ad[i] * l;
+      for (int i = 0; i < ns; ++i) atl[nd + i] += as[i] * l;
+    }
+  };
   (void)r;
   auto slackL = [&](const std::vector<double>& x, int i) { return hasL[i] ? x[i] - lb0[i] : 1.0; };
   auto slackU = [&](const std::vector<double>& x, int i) { return hasU[i] ? ub0[i] - x[i] : 1.0; };
@@ -574,8 +855,7 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
     const double s_c = std::max(o.s_max, sz / std::max(1, nb)) / o.s_max;
     double rd = 0, comp = 0, cinf = 0;
     for (int i = 0; i < n; ++i) {
-      double d = g[i] - zL[i] + zU[i];
-      for (int j = 0; j < m; ++j) d += (i < nd ? AD[(size_t)j * nd + i] : AS[(size_t)j * ns + i - nd]) * lam[j];
+      const double d = g[i] - zL[i] + zU[i] + atl[i];
       rd = std::max(rd, std::fabs(d));
       if (hasL[i]) comp = std::max(comp, std::fabs((v[i] - lb0[i]) * zL[i] - mu_));
       if (hasU[i]) comp = std::max(comp, std::fabs((ub0[i] - v[i]) * zU[i] - mu_));
@@ -615,6 +895,7 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
     for (double x : c) finite &= std::isfinite(x);
     for (double x : AD) finite &= std::isfinite(x);
     if (!finite) { status = NNC_IPM_NONFINITE; break; }
+    update_atl();
     E0 = errors(0.0);
     if (o.verbose)
       std::printf("iter %3d  f %.10e  inf_pr %.3e  E0 %.3e  mu %.1e\n", it, fv, m ? inf_norm(c) : 0.0, E0, mu);
@@ -635,11 +916,7 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
       SigU[i] = hasU[i] ? zU[i] / sU[i] : 0.0;
       gphi[i] = g[i] - (hasL[i] ? mu / sL[i] : 0.0) + (hasU[i] ? mu / sU[i] : 0.0);
     }
-    for (int i = 0; i < n; ++i) {
-      double d = gphi[i];
-      for (int j = 0; j < m; ++j) d += (i < nd ? AD[(size_t)j * nd + i] : AS[(size_t)j * ns + i - nd]) * lam[j];
-      rhs[i] = -d;
-    }
+    for (int i = 0; i < n; ++i) rhs[i] = -(gphi[i] + atl[i]);
     for (int j = 0; j < m; ++j) rhs[n + j] = -c[j];
     // --- inertia-corrected factorization
     double delta_w = 0.0, delta_c = 0.0;
@@ -653,7 +930,9 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
     for (double x : AD) scale = std::max(scale, std::fabs(x));
     for (double x : AS) scale = std::max(scale, std::fabs(x));
     const double zero_tol = 1e-14 * scale;
+    int tries = 0;
     while (true) {
+      ++tries;
       kkt.factor(nd, ns, m, WDD.data(), WSS.data(), sig.data(), AD.data(), AS.data(), delta_w,
                  delta_c, zero_tol);
       if (kkt.npos == n && kkt.nneg == m && kkt.nzero == 0) { ok = true; break; }
@@ -668,6 +947,9 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
     }
     if (!ok) { status = NNC_IPM_INERTIA_FAILED; T.solver += secs(t_lin, Clock::now()); break; }
     if (delta_w > 0.0) delta_w_last = delta_w;
+    if (o.verbose)
+      std::printf("          kkt mode %d, %d factorization(s), delta_w %.1e, %.1f ms\n", kkt.mode, tries,
+                  delta_w, 1e3 * secs(t_lin, Clock::now()));
     sol = rhs;
     kkt.solve(sol.data());
     for (int i = 0; i < n; ++i) dv[i] = sol[i];
@@ -833,6 +1115,82 @@ struct Adversarial : IpmProblem {
     if (rc) return rc;
     for (size_t i = 0; i < (size_t)nd * nd; ++i) WDD[i] = -H[i];
     for (int i = 0; i < nd; ++i) WDD[(size_t)i * nd + i] += 2.0;
+    std::fill(WSS, WSS + ns, 0.0);
+    return NNC_OK;
+  }
+};
+
+// ---------------------------------------------------------------- Eq. 7: the L1 adversarial problem
+// The smallest L1 change to a reference image that makes the classifier's (softmax) probability of
+// the target class at least conf.  The L1 norm through split variables x - x_ref = p - q:
+// variables v = (x in [0,1]^n | p >= 0, q >= 0 in R^n, y in R^n_out with y_t >= conf),
+//   min sum(p) + sum(q)  s.t.  x - p + q - x_ref = 0,  y - NN(x) = 0.
+// The dense block is x (the network's curvature); p, q and y are the diagonal block (p, q carry
+// only barrier terms, y is free except y_t, so its zero diagonal stays beside the multipliers).
+struct AdversarialL1 : IpmProblem {
+  nnc_net* net;
+  int n_in, n_out, t;
+  double conf;
+  std::vector<double> xr, J, H, r;
+  AdversarialL1(nnc_net* net_, const double* x_ref, int n_in_, int n_out_, int t_, double conf_)
+      : net(net_), n_in(n_in_), n_out(n_out_), t(t_), conf(conf_), xr(x_ref, x_ref + n_in_) {
+    nd = n_in;
+    ns = 2 * n_in + n_out;
+    m = n_in + n_out;
+    lb.assign(nd + ns, 0.0);
+    ub.assign(nd + ns, INFINITY);
+    for (int i = 0; i < n_in; ++i) ub[i] = 1.0;
+    for (int j = 0; j < n_out; ++j) lb[3 * n_in + j] = -INFINITY;
+    lb[3 * n_in + t] = conf;
+    J.resize((size_t)n_out * n_in);
+    H.resize((size_t)n_in * n_in);
+    r.resize(n_out);
+  }
+  int start() {
+    std::vector<double> y(n_out);
+    int rc = nnc_eval(net, xr.data(), y.data(), 1);
+    if (rc) return rc;
+    v0.assign(nd + ns, 0.0);
+    for (int i = 0; i < n_in; ++i) v0[i] = xr[i];
+    for (int j = 0; j < n_out; ++j) v0[3 * n_in + j] = y[j];
+    return NNC_OK;
+  }
+  double f(const double* v) override {
+    double s = 0;
+    for (int i = n_in; i < 3 * n_in; ++i) s += v[i];
+    return s;
+  }
+  void grad_f(const double* v, double* g) override {
+    for (int i = 0; i < nd + ns; ++i) g[i] = (i >= n_in && i < 3 * n_in) ? 1.0 : 0.0;
+  }
+  int cons(const double* v, double* c) override {
+    for (int i = 0; i < n_in; ++i) c[i] = v[i] - v[n_in + i] + v[2 * n_in + i] - xr[i];
+    int rc = nnc_residual(net, v, v + 3 * n_in, r.data());   // y - NN(x), FP64-accurate
+    if (rc) return rc;
+    for (int j = 0; j < n_out; ++j) c[n_in + j] = r[j];
+    return NNC_OK;
+  }
+  int jac(const double* v, double* AD, double* AS) override {
+    int rc = nnc_jacobian(net, v, J.data());
+    if (rc) return rc;
+    std::fill(AD, AD + (size_t)m * nd, 0.0);
+    std::fill(AS, AS + (size_t)m * ns, 0.0);
+    for (int i = 0; i < n_in; ++i) {
+      AD[(size_t)i * nd + i] = 1.0;
+      AS[(size_t)i * ns + i] = -1.0;            // p_i
+      AS[(size_t)i * ns + n_in + i] = 1.0;      // q_i
+    }
+    for (int j = 0; j < n_out; ++j) {
+      for (int i = 0; i < n_in; ++i) AD[(size_t)(n_in + j) * nd + i] = -J[(size_t)j * n_in + i];
+      AS[(size_t)(n_in + j) * ns + 2 * n_in + j] = 1.0;   // y_j
+    }
+    return NNC_OK;
+  }
+  int hess(const double* v, const double* lam, double* WDD, double* WSS) override {
+    // the objective is linear; sum_i lam_i grad^2 c_i = -sum_j lam_{n+j} grad^2 NN_j (Eq. 6)
+    int rc = nnc_hessian_lag(net, v, lam + n_in, H.data(), nullptr);
+    if (rc) return rc;
+    for (size_t i = 0; i < (size_t)nd * nd; ++i) WDD[i] = -H[i];
     std::fill(WSS, WSS + ns, 0.0);
     return NNC_OK;
   }
@@ -1052,6 +1410,27 @@ int nnc_ipm_adversarial(nnc_net* net, const double* x0, int target, double margi
   if (opt) o = *opt;
   else nnc_ipm_default_options(&o);
   Adversarial p(net, x0, n_in, n_out, target, margin);
+  rc = p.start();
+  if (rc) return rc;
+  std::vector<double> v, lam;
+  rc = ipm_solve(p, o, v, lam, res);
+  if (rc) return rc;
+  if (v_out) std::copy(v.begin(), v.end(), v_out);
+  if (lam_out) std::copy(lam.begin(), lam.end(), lam_out);
+  return NNC_OK;
+}
+
+int nnc_ipm_adversarial_l1(nnc_net* net, const double* x_ref, int target, double conf,
+                           const nnc_ipm_options* opt, double* v_out, double* lam_out,
+                           nnc_ipm_result* res) {
+  int L = 0, n_in = 0, n_out = 0, prec = 0;
+  int rc = nnc_net_info(net, &L, &n_in, &n_out, &prec);
+  if (rc) return rc;
+  if (!x_ref || target < 0 || target >= n_out || !(conf > 0.0 && conf < 1.0)) return NNC_ERR_ARG;
+  nnc_ipm_options o;
+  if (opt) o = *opt;
+  else nnc_ipm_default_options(&o);
+  AdversarialL1 p(net, x_ref, n_in, n_out, target, conf);
   rc = p.start();
   if (rc) return rc;
   std::vector<double> v, lam;

@@ -25,7 +25,7 @@ EXPORTS = ["nnc_load_weights", "nnc_eval", "nnc_residual", "nnc_jacobian", "nnc_
            "nnc_eval_batched", "nnc_eval_dev", "nnc_residual_dev", "nnc_jacobian_dev",
            "nnc_hessian_lag_dev", "nnc_eval_all_dev", "nnc_eval_kkt_dev", "nnc_eval_kkt", "nnc_free", "nnc_last_error",
            "nnc_net_info", "nnc_launch_count", "nnc_profile", "nnc_profile_read",
-           "nnc_ipm_default_options", "nnc_ipm_adversarial", "nnc_kkt_solve",
+           "nnc_ipm_default_options", "nnc_ipm_adversarial", "nnc_ipm_adversarial_l1", "nnc_kkt_solve",
            "nnc_residual_noalloc", "nnc_batch_create", "nnc_batch_free", "nnc_batch_info",
            "nnc_batch_set_bias", "nnc_batch_use_graph", "nnc_batch_eval_dev", "nnc_batch_residual_dev",
            "nnc_batch_eval", "nnc_batch_residual", "nnc_ipm_scopf", "nnc_ws_create", "nnc_ws_free",
@@ -148,6 +148,9 @@ def load_library(path: str = LIB_PATH):
     lib.nnc_ipm_adversarial.argtypes = [_P, _DP, ctypes.c_int, ctypes.c_double,
                                         ctypes.POINTER(IpmOptions), _DP, _DP,
                                         ctypes.POINTER(IpmResult)]
+    lib.nnc_ipm_adversarial_l1.argtypes = [_P, _DP, ctypes.c_int, ctypes.c_double,
+                                           ctypes.POINTER(IpmOptions), _DP, _DP,
+                                           ctypes.POINTER(IpmResult)]
     lib.nnc_profile_read.argtypes = [_P, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
     for name in EXPORTS:
@@ -361,6 +364,20 @@ def ipm_adversarial(net, x0, target=3, margin=0.1, **options):
     res = IpmResult()
     _check(lib.nnc_ipm_adversarial(net.handle, _dp(x0), int(target), float(margin), ctypes.byref(o),
                                    _dp(v), _dp(lam), ctypes.byref(res)))
+    return res.as_dict(), v, lam
+
+
+def ipm_adversarial_l1(net, x_ref, target, conf=0.6, **options):
+    """Eq. 7 (L1 objective by split variables, y_t >= conf) with the host interior-point driver.
+    Returns (result dict, v = (x, p, q, y), lambda)."""
+    lib = load_library()
+    x_ref = _f64(x_ref)
+    o = ipm_options(**options)
+    v = np.empty(3 * net.n_in + net.n_out)
+    lam = np.empty(net.n_in + net.n_out)
+    res = IpmResult()
+    _check(lib.nnc_ipm_adversarial_l1(net.handle, _dp(x_ref), int(target), float(conf), ctypes.byref(o),
+                                      _dp(v), _dp(lam), ctypes.byref(res)))
     return res.as_dict(), v, lam
 
 

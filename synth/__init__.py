@@ -12,7 +12,8 @@ uniforms).  Everything is vectorised numpy, so the draw is identical on every
 machine and library version.
 """
 from .rng import derive_key, uniform01, normal, randint, permutation  # noqa: F401
-from .nets import (MLP, MLPSpec, make_mlp, mnist_like_spec, surrogate_spec, spec_by_name, TINY,  # noqa: F401
-                   PAPER_104M, PAPER_87M, SCOPF_68M, warmstart_params)
+from .nets import (MLP, MLPSpec, make_mlp, make_classifier, mnist_like_spec, surrogate_spec, spec_by_name, TINY,  # noqa: F401
+                   PAPER_104M, PAPER_87M, PAPER_70M_SOFTMAX, PAPER_274M, SCOPF_68M,
+                   warmstart_params)
 from .problems import (AdversarialData, adversarial_data, ScopfData, scopf_data, load_vectors,  # noqa: F401
                        scopf_first_bias, scopf_demand)

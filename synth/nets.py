@@ -69,6 +69,22 @@ def make_mlp(spec: MLPSpec, seed: int = 0, tag: str = "mlp", bias_std: float = 0
     return MLP(spec, W, b, seed)
 
 
+def make_classifier(spec: MLPSpec, seed: int = 0, tag: str = "clf", out_scale: float = 3.0) -> MLP:
+    """A random stand-in for a trained softmax classifier (Section 4.1): hidden weights
+    N(0, g^2 / fan_in) with g = 4 for sigmoid layers (the reciprocal of sigmoid'(0), so the
+    layer gain stays near one through five wide layers) and g = 1 for tanh, sigmoid biases
+    -W 0.5 (centring inputs that average one half), and the output logits scaled by `out_scale`
+    so that the class probabilities are peaked as a trained classifier's are.  With these
+    settings a confidence of 0.6 on any class is reachable from x ~ U[0,1]^784 inside the box."""
+    mlp = make_mlp(spec, seed=seed, tag=tag)
+    for l in range(spec.n_layers - 1):
+        if spec.acts[l] == "sigmoid":
+            mlp.W[l] = 4.0 * mlp.W[l]
+            mlp.b[l] = -0.5 * mlp.W[l].sum(axis=1)
+    mlp.W[-1] = out_scale * mlp.W[-1]
+    return mlp
+
+
 def mnist_like_spec(hidden: int, n_hidden_layers: int, act: str = "tanh",
                     out_act: str = "identity", n_in: int = 784, n_out: int = 10) -> MLPSpec:
     """784 -> hidden x n_hidden_layers -> 10.  The output layer is linear (logits) by default."""
@@ -89,6 +105,12 @@ PAPER_104M = mnist_like_spec(4096, 7)          # 784 -> 4096 x 7 -> 10, 103,944,
 PAPER_87M = mnist_like_spec(4096, 6)           # literal "6 hidden layers" reading, 87,162,890 params
 
 
+# The paper's softmax classifiers (Table 1): seven layers in all, so five hidden layers; 4096 wide
+# tanh gives 70.4M parameters (the 70M row), 8192 wide sigmoid 275.0M (the 274M row).
+PAPER_70M_SOFTMAX = mnist_like_spec(4096, 5, out_act="softmax")
+PAPER_274M = mnist_like_spec(8192, 5, act="sigmoid", out_act="softmax")
+
+
 # SCOPF-shaped single network (Section 4.2): 117 inputs (generator setpoints and loads), 37 outputs
 # (stability margins), deep tanh; [117, 4096 x 5, 37] has 67.7M parameters, the size of the
 # paper's 68M SCOPF net.  Its Jacobian has 37 seed rows and its Hessian 117 tangents.
@@ -97,7 +119,8 @@ SCOPF_68M = MLPSpec([117] + [4096] * 5 + [37], ["tanh"] * 5 + ["identity"],
 
 
 def spec_by_name(name: str) -> Optional[MLPSpec]:
-    return {"tiny": TINY, "104m": PAPER_104M, "87m": PAPER_87M, "scopf68m": SCOPF_68M}.get(name)
+    return {"tiny": TINY, "104m": PAPER_104M, "87m": PAPER_87M, "scopf68m": SCOPF_68M,
+            "70m": PAPER_70M_SOFTMAX, "274m": PAPER_274M}.get(name)
 
 
 def warmstart_params(n_in: int, h1: int, h2: int, n_out: int, seed: int = 0):

@@ -97,3 +97,92 @@ def test_adversarial_104m_matches_oracle(nnc, m104_oracle_solution, prec):
     assert res["kkt_error"] <= 1e-6
     assert abs(res["obj"] - ro.obj) <= 1e-6 * abs(ro.obj)
     net.free()
+
+
+def _l1_instance(seed, n=20, scale=4.0):
+    """A small softmax classifier whose output layer is scaled so that its probabilities are as
+    peaked as a trained classifier's, so the 0.6 confidence of Eq. 7 is reachable."""
+    from oracle import nn as onn
+    mlp = make_mlp(MLPSpec([n, 16, 16, 5], ["tanh", "tanh", "softmax"]), seed=seed, tag="l1",
+                   bias_std=0.3)
+    mlp.W[-1] = mlp.W[-1] * scale
+    x = synth.uniform01(synth.derive_key(seed, "l1-x"), n)
+    p0 = onn.value(mlp, x)
+    return mlp, x, int(np.argsort(p0)[-2])
+
+
+@pytest.fixture(scope="module")
+def l1_oracle_solution():
+    mlp, x_ref, t = _l1_instance(0)
+    r = oipm.solve(problems.adversarial_l1(mlp, x_ref, t, 0.6))
+    assert r.status == oipm.OPTIMAL
+    return mlp, x_ref, t, r
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3"])
+def test_adversarial_l1_matches_oracle(nnc, l1_oracle_solution, prec):
+    """Eq. 7 (L1 objective by split variables, softmax output, y_t >= 0.6) on the GPU oracles:
+    with FP64 the iterates follow the oracle's; every form reaches its objective within 1e-6."""
+    mlp, x_ref, t, ro = l1_oracle_solution
+    n = x_ref.size
+    net = nnc.Net.from_mlp(mlp, precision=prec)
+    res, v, lam = nnc.ipm_adversarial_l1(net, x_ref, t, 0.6)
+    print(f"[ipm l1 {prec}] status={res['status_name']} iters={res['iters']} (oracle {ro.iters}) "
+          f"obj={res['obj']:.12g} (oracle {ro.obj:.12g}) kkt={res['kkt_error']:.2e}")
+    assert res["status"] == 0
+    assert res["kkt_error"] <= 1e-6
+    assert abs(res["obj"] - ro.obj) <= 1e-6 * abs(ro.obj)
+    assert v[3 * n + t] >= 0.6 - 1e-8
+    if prec == "fp64":
+        assert res["iters"] == ro.iters
+        assert np.max(np.abs(v - ro.v)) < 1e-6
+        assert np.max(np.abs(lam - ro.lam)) < 1e-5 * max(1.0, np.max(np.abs(ro.lam)))
+    net.free()
+
+
+def test_adversarial_l1_rejects_bad_confidence(nnc):
+    mlp, x_ref, t = _l1_instance(1)
+    net = nnc.Net.from_mlp(mlp, precision="fp64")
+    with pytest.raises(nnc.NNCError):
+        nnc.ipm_adversarial_l1(net, x_ref, t, 1.0)
+    with pytest.raises(nnc.NNCError):
+        nnc.ipm_adversarial_l1(net, x_ref, 7, 0.6)
+    net.free()
+
+
+def test_adversarial_l1_274m(nnc):
+    """Eq. 7 on the 274M-shaped sigmoid+softmax classifier: the tensor-core form reaches the FP64
+    form's objective within 1e-6, and at the tensor-core solution the oracle confirms
+    y_t = NN_t(x) >= 0.6 and the stationarity of x: for every pixel strictly
+    well inside its bounds, lambda_link,i = (J^T lambda_NN)_i, and |lambda_link| <= 1 (the bound
+    multipliers of the split variables, 1 - lambda_link and 1 + lambda_link, are nonnegative)."""
+    from oracle import nn as onn
+    mlp = synth.make_classifier(synth.PAPER_274M, seed=0)
+    d = synth.adversarial_data(seed=0)
+    n = d.x0.size
+    out = {}
+    for prec in ["fp64", "bf16x3"]:
+        net = nnc.Net.from_mlp(mlp, precision=prec)
+        res, v, lam = nnc.ipm_adversarial_l1(net, d.x0, d.target, 0.6)
+        print(f"[ipm l1 274m {prec}] status={res['status_name']} iters={res['iters']} "
+              f"obj={res['obj']:.12g} kkt={res['kkt_error']:.2e} t={res['solve_seconds']:.3f}s "
+              f"fn={res['t_function']:.3f} jac={res['t_jacobian']:.3f} hess={res['t_hessian']:.3f} "
+              f"solver={res['t_solver']:.3f}")
+        assert res["status"] == 0 and res["kkt_error"] <= 1e-6
+        out[prec] = (res, v, lam)
+        net.free()
+    r64, rtc = out["fp64"][0], out["bf16x3"][0]
+    assert abs(rtc["obj"] - r64["obj"]) <= 1e-6 * abs(r64["obj"])
+    _, v, lam = out["bf16x3"]
+    x = v[:n]
+    assert onn.value(mlp, x)[d.target] >= 0.6 - 1e-7
+    J = onn.jacobian(mlp, x)
+    lam_link, lam_nn = lam[:n], lam[n:]
+    assert np.max(np.abs(lam_link)) <= 1 + 1e-6
+    # pixels well inside [0, 1], where the barrier's bound multipliers mu / x and mu / (1 - x) are
+    # below 1e-6 at the final mu <= 1e-7
+    inner = (x > 0.1) & (x < 0.9)
+    assert inner.sum() > 0
+    resid = lam_link - J.T @ lam_nn
+    scale = max(1.0, np.max(np.abs(lam_nn)) * np.max(np.abs(J)))
+    assert np.max(np.abs(resid[inner])) <= 1e-5 * scale

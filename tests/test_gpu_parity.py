@@ -211,3 +211,32 @@ def test_softmax_output(lib, prec, case):
     e = _check_all(lib, mlp, x, lam, prec, f"softmax{case}")
     yo = onn.value(mlp, x)
     assert abs(yo.sum() - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("name,prec", [("274m", "fp64"), ("274m", "bf16x3"), ("274m", "bf16"),
+                                       ("70m", "bf16x3")])
+def test_softmax_classifier_full_size_sampled(lib, name, prec):
+    """The paper's softmax classifiers at full size (Table 1: [784, 8192 x 5, 10] sigmoid+softmax,
+    275.0M parameters; [784, 4096 x 5, 10] tanh+softmax, 70.4M): value, Jacobian and gradient in
+    full and sampled Hessian columns against the oracle, in the launch configuration the bench
+    times."""
+    spec = synth.spec_by_name(name)
+    mlp = synth.make_classifier(spec, seed=0)
+    d = synth.adversarial_data(seed=0)
+    net = lib.Net.from_mlp(mlp, precision=prec)
+    y = net.eval(d.x0)
+    J = net.jacobian(d.x0)
+    H, g = net.hessian_lag(d.x0, d.lam, want_grad=True)
+    yo = onn.value(mlp, d.x0)
+    Jo = onn.jacobian(mlp, d.x0)
+    go = onn.vjp(mlp, d.x0, d.lam)
+    cols = [0, 1, 391, 783]
+    Hc = onn.hessian_lag_columns(mlp, d.x0, d.lam, cols)
+    e = dict(y=rel(y, yo), J=rel(J, Jo), H=rel(H[:, cols], Hc), g=rel(g, go))
+    print(f"[{name} {prec}] rel err y={e['y']:.2e} J={e['J']:.2e} Hcols={e['H']:.2e} g={e['g']:.2e}")
+    t = TOL[prec]
+    assert e["y"] < t["y"] and e["J"] < t["J"] and e["H"] < t["H"] and e["g"] < t["J"], e
+    assert np.array_equal(H, H.T)
+    r = net.residual(d.x0, yo)
+    assert np.max(np.abs(r)) <= 1e-10 * max(1.0, np.max(np.abs(yo)))
+    net.free()
