@@ -34,8 +34,7 @@ METRIC = "hessian_lag_evals_per_s"
 # N tile: mean of two launches of the ncu captures summarised in
 # profiles/k_tc_gemm_tangent_784x4096x4096.md; an entry is valid only for the kernel version it
 # was taken on.
-TANGENT_TRAFFIC = {("bf16x3", 112): 90.57e6, ("bf16x3", 128): 91.92e6, ("bf16x3", 208): 82.05e6,
-                   ("bf16x3", 256): 82.16e6}
+TANGENT_TRAFFIC = {}
 UNIT = "evals/s"
 
 

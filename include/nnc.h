@@ -223,7 +223,7 @@ long long nnc_launch_count(void);
 int nnc_autotune(nnc_net* net, const char* cache_path, int retune);
 int nnc_tuning(const nnc_net* net, int layer, int* tangent_bn, int* syrk_splits);
 /* Pin the tensor-core tiling instead of tuning it (reproducible profiles): tangent_bn = the N tile
- * of every tangent GEMM (112, 128, 208 or 256; 0 keeps the current one), syrk_splits = the split-K
+ * of every tangent GEMM (112, 128, 176, 208 or 256; 0 keeps the current one), syrk_splits = the split-K
  * count of the symmetric product (1 .. the count chosen at load; 0 keeps it).  No effect on the
  * CUDA-core forms; NNC_ERR_ARG for other values. */
 int nnc_tune_set(nnc_net* net, int tangent_bn, int syrk_splits);

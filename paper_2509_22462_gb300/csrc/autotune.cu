@@ -95,7 +95,7 @@ extern "C" int nnc_autotune(nnc_net* net, const char* cache_path, int retune) {
   auto cache = read_cache(cache_path);
   cudaStream_t st = net->stream;
   const int n = net->n_in;
-  const int bns[4] = {112, 128, 208, 256};
+  const int bns[5] = {112, 128, 176, 208, 256};
   // tangent GEMMs: layers of one shape share a choice, timed over the chain of those layers as a
   // step runs them (different weights each launch), so that a layer's weights are not timed out
   // of L2, which one repeated launch would do
@@ -194,8 +194,9 @@ extern "C" int nnc_tune_set(nnc_net* net, int tangent_bn, int syrk_splits) {
   }
   const int prec = net->prec;
   if (!(prec == NNC_BF16 || prec == NNC_BF16X3 || prec == NNC_FP8)) return NNC_OK;  // CUDA-core forms
-  if (tangent_bn && tangent_bn != 112 && tangent_bn != 128 && tangent_bn != 208 && tangent_bn != 256) {
-    set_last_error("tangent N tile must be 112, 128, 208 or 256");
+  if (tangent_bn && tangent_bn != 112 && tangent_bn != 128 && tangent_bn != 176 && tangent_bn != 208 &&
+      tangent_bn != 256) {
+    set_last_error("tangent N tile must be 112, 128, 176, 208 or 256");
     return NNC_ERR_ARG;
   }
   if (syrk_splits < 0 || syrk_splits > net->h_splits) {

@@ -16,7 +16,9 @@
 // and returns.
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdio>
+#include <vector>
 
 #include "kernels.cuh"
 #include "tc.cuh"
@@ -234,12 +236,22 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int tm, tn, split, grp = 0, a_row0, b_row0, n_valid, n_eff = BN;
   if (KIND == TC_TANGENT) {
-    tn = blockIdx.x;
-    tm = blockIdx.y;
+    // 1-D grid, full-width column tiles first (row-major over (tm, tn)), then one narrow tile per
+    // row block for the N % BN remainder: the narrow tiles fill the SMs the wide ones leave idle
+    const int nfull = args.N / BN;
+    const int b = blockIdx.x;
+    if (b < args.ntm * nfull) {
+      tm = b / nfull;
+      tn = b % nfull;
+    } else {
+      tm = b - args.ntm * nfull;
+      tn = nfull;
+    }
     split = 0;
     a_row0 = tm * BM;
     b_row0 = tn * BN;
     n_valid = args.N;
+    n_eff = (min(BN, args.N - tn * BN) + 15) / 16 * 16;
   } else if (KIND == TC_SYRK) {
     tn = blockIdx.x % args.ntn;
     tm = blockIdx.x / args.ntn;
@@ -534,12 +546,31 @@ cudaError_t launch_any(const TcPlan& p, const TcArgs& a, dim3 grid, cudaStream_t
     return cudaErrorInvalidValue;
   }
   switch (p.bn) {
+    case 176:
+      if constexpr (KIND == TC_TANGENT) return launch_mode<KIND, 176>(p, a, grid, st);
+      return cudaErrorInvalidValue;
     case 112: return launch_mode<KIND, 112>(p, a, grid, st);
     case 128: return launch_mode<KIND, 128>(p, a, grid, st);
     case 208: return launch_mode<KIND, 208>(p, a, grid, st);
     case 256: return launch_mode<KIND, 256>(p, a, grid, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// Makespan model of one tangent launch: CTAs in launch order (full-width tiles, then the narrow
+// remainder tiles) go to the first free SM; a tile costs its MMA width plus a fixed 24 columns.
+double tangent_makespan(int ntm, int N, int bn, int sm_count) {
+  const int nfull = N / bn, rem = N - nfull * bn;
+  std::vector<double> t;
+  for (int i = 0; i < ntm * nfull; ++i) t.push_back(bn + 24.0);
+  if (rem > 0)
+    for (int i = 0; i < ntm; ++i) t.push_back((rem + 15) / 16 * 16 + 24.0);
+  std::vector<double> sm(std::max(1, sm_count), 0.0);
+  for (double c : t) {
+    auto it = std::min_element(sm.begin(), sm.end());
+    *it += c;
+  }
+  return *std::max_element(sm.begin(), sm.end());
 }
 
 int count_lower_tiles(int ntm, int ntn, int bn) {
@@ -604,13 +635,10 @@ int tc_plan_make(TcPlan& p, int kind, int prec, const void* a_hi, const void* a_
   } else if (kind == TC_TANGENT) {
     int best_bn = 208;
     double best = 1e30;
-    const int cands[4] = {256, 208, 128, 112};
+    const int cands[5] = {256, 208, 176, 128, 112};
     const int ntm = M / BM;
     for (int bn : cands) {
-      const int ntn = (N + bn - 1) / bn;
-      const int ctas = ntm * ntn;
-      const int waves = (ctas + sm_count - 1) / sm_count;
-      const double cost = (double)waves * (bn + 24);
+      const double cost = tangent_makespan(ntm, N, bn, sm_count);
       if (cost < best - 1e-9) {
         best = cost;
         best_bn = bn;
@@ -670,7 +698,7 @@ cudaError_t tc_tangent(const TcPlan& p, const double* s1, const float* c, void* 
   a.err = err;
   a.wscale = wscale;
   a.tscale = tscale;
-  return launch_any<TC_TANGENT>(p, a, dim3(p.ntn, p.ntm, 1), st);
+  return launch_any<TC_TANGENT>(p, a, dim3(p.ntn * p.ntm, 1, 1), st);
 }
 
 cudaError_t tc_tangent_grouped(const TcPlan& p, int groups, const int* g_n, const int* g_boff,

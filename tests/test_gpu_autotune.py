@@ -55,7 +55,7 @@ def test_tune_set_pins_tiles_and_keeps_results():
     lam = synth.normal(synth.derive_key(5, "tune-lam"), 7)
     net = nnc.Net.from_mlp(mlp, precision="bf16x3")
     H0 = net.hessian_lag(x, lam)
-    for bn in (112, 128, 208, 256):
+    for bn in (112, 128, 176, 208, 256):
         net.tune_set(tangent_bn=bn)
         assert net.tuning(1)[0] == bn
         assert np.array_equal(net.hessian_lag(x, lam), H0), bn
