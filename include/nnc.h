@@ -215,17 +215,21 @@ int nnc_net_info(const nnc_net* net, int* n_layers, int* n_in, int* n_out, int* 
 long long nnc_launch_count(void);
 
 /* Autotuner for the tensor-core forms (no effect on results): times every N-tile width of each
- * tangent-GEMM shape and every split-K count of the symmetric product on the net's own buffers
- * (CUDA events on its stream) and keeps the fastest.  cache_path (may be NULL) names a JSON file
- * of earlier choices, keyed by device, kind, precision and shape; existing entries are reused
- * unless retune != 0, and the file is rewritten with the current choices.  CUDA-core forms
- * return NNC_OK at once.  nnc_tuning reports the current choice for one layer. */
+ * tangent-GEMM shape, on one SM per tile and on SM pairs (tcgen05 cta_group::2, 256-row tiles;
+ * layers with a multiple of 256 rows, BF16 forms), and every split-K count of the symmetric
+ * product on the net's own buffers (CUDA events on its stream) and keeps the fastest.
+ * cache_path (may be NULL) names a JSON file of earlier choices, keyed by device, kind,
+ * precision and shape; existing entries are reused unless retune != 0, and the file is
+ * rewritten with the current choices.  CUDA-core forms return NNC_OK at once.  nnc_tuning
+ * reports the current choice for one layer (a negative tangent tile is an SM-pair tile). */
 int nnc_autotune(nnc_net* net, const char* cache_path, int retune);
 int nnc_tuning(const nnc_net* net, int layer, int* tangent_bn, int* syrk_splits);
 /* Pin the tensor-core tiling instead of tuning it (reproducible profiles): tangent_bn = the N tile
- * of every tangent GEMM (112, 128, 176, 208 or 256; 0 keeps the current one), syrk_splits = the split-K
- * count of the symmetric product (1 .. the count chosen at load; 0 keeps it).  No effect on the
- * CUDA-core forms; NNC_ERR_ARG for other values. */
+ * of every tangent GEMM (112, 128, 208 or 256 on one SM per tile; -128, -160, -208 or -256
+ * on SM pairs, applied to the layers whose row count is a multiple of 256, not in the FP8 form;
+ * 0 keeps the current one), syrk_splits = the split-K count of the symmetric product (1 .. the
+ * count chosen at load; 0 keeps it).  No effect on the CUDA-core forms; NNC_ERR_ARG for other
+ * values. */
 int nnc_tune_set(nnc_net* net, int tangent_bn, int syrk_splits);
 
 /* Per-kernel timing with CUDA events on the net's launch streams (no effect on results).

@@ -95,7 +95,8 @@ extern "C" int nnc_autotune(nnc_net* net, const char* cache_path, int retune) {
   auto cache = read_cache(cache_path);
   cudaStream_t st = net->stream;
   const int n = net->n_in;
-  const int bns[5] = {112, 128, 176, 208, 256};
+  // single-SM N tiles, then SM-pair tiles (negative codes)
+  const int bns[8] = {112, 128, 208, 256, -128, -160, -208, -256};
   // tangent GEMMs: layers of one shape share a choice, timed over the chain of those layers as a
   // step runs them (different weights each launch), so that a layer's weights are not timed out
   // of L2, which one repeated launch would do
@@ -114,7 +115,7 @@ extern "C" int nnc_autotune(nnc_net* net, const char* cache_path, int retune) {
   };
   for (auto& g : groups) {
     const std::vector<int>& ls = g.second;
-    int best = net->layers[ls[0]].plan_tan.bn;
+    int best = plan_code(net->layers[ls[0]].plan_tan);
     auto it = cache.find(g.first);
     if (it != cache.end() && !retune) {
       best = it->second.first;
@@ -142,7 +143,7 @@ extern "C" int nnc_autotune(nnc_net* net, const char* cache_path, int retune) {
       cache[g.first] = {best, best_us};
     }
     for (int l : ls)
-      if (best != net->layers[l].plan_tan.bn) make_plan(net->layers[l].plan_tan, l, best);
+      if (best != plan_code(net->layers[l].plan_tan)) make_plan(net->layers[l].plan_tan, l, best);
   }
   // symmetric product: split-K count (bounded by the partial-sum buffer allocated at load)
   if (net->K_total > 0 && net->plan_syrk.ready) {
@@ -194,10 +195,19 @@ extern "C" int nnc_tune_set(nnc_net* net, int tangent_bn, int syrk_splits) {
   }
   const int prec = net->prec;
   if (!(prec == NNC_BF16 || prec == NNC_BF16X3 || prec == NNC_FP8)) return NNC_OK;  // CUDA-core forms
-  if (tangent_bn && tangent_bn != 112 && tangent_bn != 128 && tangent_bn != 176 && tangent_bn != 208 &&
-      tangent_bn != 256) {
-    set_last_error("tangent N tile must be 112, 128, 176, 208 or 256");
-    return NNC_ERR_ARG;
+  {
+    const int t = tangent_bn;
+    const bool single = t == 112 || t == 128 || t == 208 || t == 256;
+    const bool pair = t == -128 || t == -160 || t == -208 || t == -256;
+    if (t && !single && !pair) {
+      set_last_error("tangent tile must be 112, 128, 208, 256 (one SM) or -128, -160, -208, -256 "
+                     "(SM pairs)");
+      return NNC_ERR_ARG;
+    }
+    if (pair && prec == NNC_FP8) {
+      set_last_error("the SM-pair tangent kernel has no FP8 form");
+      return NNC_ERR_ARG;
+    }
   }
   if (syrk_splits < 0 || syrk_splits > net->h_splits) {
     set_last_error("symmetric-product splits out of range");
@@ -208,6 +218,7 @@ extern "C" int nnc_tune_set(nnc_net* net, int tangent_bn, int syrk_splits) {
   for (int l = 1; l < net->L && tangent_bn; ++l) {
     LayerDev& Ly = net->layers[l];
     if (!Ly.plan_tan.ready) continue;
+    if (tangent_bn < 0 && Ly.mp % 256 != 0) continue;   // pairs need 256-row blocks
     const int cur = (l - 1) % 2;
     TcPlan p;
     const int r = prec == NNC_FP8
@@ -241,7 +252,7 @@ extern "C" int nnc_tuning(const nnc_net* net, int layer, int* tangent_bn, int* s
     set_last_error("bad arguments");
     return NNC_ERR_ARG;
   }
-  if (tangent_bn) *tangent_bn = net->layers[layer].plan_tan.ready ? net->layers[layer].plan_tan.bn : 0;
+  if (tangent_bn) *tangent_bn = net->layers[layer].plan_tan.ready ? plan_code(net->layers[layer].plan_tan) : 0;
   if (syrk_splits) *syrk_splits = net->plan_syrk.ready ? net->plan_syrk.splits : net->h_splits;
   return NNC_OK;
 }

@@ -16,9 +16,7 @@
 // and returns.
 #include <cudaTypedefs.h>
 
-#include <algorithm>
 #include <cstdio>
-#include <vector>
 
 #include "kernels.cuh"
 #include "tc.cuh"
@@ -137,6 +135,10 @@ __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, int* err,
   }
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t mbar,
                                             int x, int y) {
   asm volatile(
@@ -237,7 +239,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   int tm, tn, split, grp = 0, a_row0, b_row0, n_valid, n_eff = BN;
   if (KIND == TC_TANGENT) {
     // 1-D grid, full-width column tiles first (row-major over (tm, tn)), then one narrow tile per
-    // row block for the N % BN remainder: the narrow tiles fill the SMs the wide ones leave idle
+    // row block for the N % BN remainder, whose MMA N is the remainder rounded up to 16
     const int nfull = args.N / BN;
     const int b = blockIdx.x;
     if (b < args.ntm * nfull) {
@@ -478,6 +480,255 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// ---------------------------------------------------------------- SM-pair tangent GEMM
+// tcgen05 with cta_group::2: a cluster of two CTAs on two SMs computes a 256 x BNP tile.  Each
+// CTA copies its own 128 rows of A and its half of the B tile (n / 2 rows) into its own shared
+// memory; the copies of both CTAs complete on the even (leader) CTA's "full" barrier, whose
+// producer expects the bytes of both.  The leader's MMA thread issues
+// tcgen05.mma.cta_group::2 (M = 256): each SM's tensor core multiplies its own A rows by the
+// whole B tile, taking one half of B from each SM's shared memory, so each SM stages and reads
+// half of B instead of all of it (the single-SM kernel is bound by shared-memory traffic in the
+// split form).  Commits arrive on both CTAs' barriers (multicast); each CTA's epilogue reads
+// its own 128 accumulator lanes.  Waits are bounded as in k_tc_gemm; both CTAs reach the final
+// cluster barrier on every path, so neither frees shared or tensor memory the other still uses.
+template <int BNP, int MODE>
+struct PairCfg {
+  static constexpr bool X3 = MODE == MODE_BF16X3;
+  static constexpr int BKE = bk_for(MODE);
+  static constexpr int ROWB = BKE * 2;
+  static constexpr int SWZ = ROWB == 128 ? 2 : 4;
+  static constexpr int SBO = 8 * ROWB;
+  static constexpr int BH = BNP / 2;                    // B rows per CTA (box height)
+  static constexpr int BH_SLOT = (BH + 15) / 16 * 16;   // shared-memory rows, 1024-byte multiple
+  static constexpr int A_BYTES = BM * ROWB;
+  static constexpr int B_BYTES = BH_SLOT * ROWB;
+  static constexpr int NPARTS = X3 ? 2 : 1;
+  static constexpr int STAGE_BYTES = NPARTS * (A_BYTES + B_BYTES);
+  static constexpr int TX_PAIR = 2 * NPARTS * (BM + BH) * ROWB;   // both CTAs' boxes
+  static constexpr int SMEM_BUDGET = 227 * 1024 - 2048;
+  static constexpr int STAGES_FIT = SMEM_BUDGET / STAGE_BYTES;
+  static constexpr int STAGES = STAGES_FIT > 8 ? 8 : STAGES_FIT;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+  static constexpr int TMEM_COLS = BNP <= 32 ? 32 : BNP <= 64 ? 64 : BNP <= 128 ? 128 : 256;
+  // kind::f16, D = F32, A = B = BF16, K-major, M = 256 (M >> 4 at bit 24)
+  static constexpr uint32_t IDESC_NO_N =
+      (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(256 >> 4) << 24);
+  static_assert(MODE == MODE_BF16 || MODE == MODE_BF16X3, "pair kernel: BF16 forms");
+  static_assert(BNP % 16 == 0 && BNP >= 32 && BNP <= 256, "UMMA N for M = 256");
+  static_assert(A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0, "1024-byte aligned stage parts");
+  static_assert(STAGES >= 2, "at least two stages");
+};
+
+__device__ __forceinline__ uint32_t pair_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void pair_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+__device__ __forceinline__ uint32_t map_to_rank(uint32_t local, uint32_t rank) {
+  uint32_t remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(rank));
+  return remote;
+}
+// 2-D tiled load into this CTA's shared memory whose completion is counted on an mbarrier that
+// may sit in the peer CTA of the pair (the leader's "full" barrier).
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map,
+                                                 uint32_t mbar_cluster, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(mbar_cluster), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void umma_bf16_pair(uint32_t tmem_d, uint64_t a, uint64_t b,
+                                               uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Arrives once on the mbarrier at this shared-memory offset in both CTAs of the pair when every
+// MMA issued so far has completed.
+__device__ __forceinline__ void umma_commit_pair(uint32_t mbar) {
+  const uint16_t mask = 0x3;
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(mbar),
+      "h"(mask)
+      : "memory");
+}
+
+template <int BNP, int MODE>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
+    k_tc_pair(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
+              const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
+              const TcArgs args) {
+  using C = PairCfg<BNP, MODE>;
+  constexpr bool X3 = C::X3;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + C::STAGES * C::STAGE_BYTES);
+  uint64_t* empty = full + C::STAGES;
+  uint64_t* accf = empty + C::STAGES;
+  uint32_t* tmem_slot = (uint32_t*)(accf + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  volatile int* consumed_sh = (volatile int*)(tmem_slot + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = pair_rank();   // 0: leader (issues the MMAs)
+  // pair tiles: full-width column tiles first (row-major over (tm, tn)), then the remainder tile
+  const int pr = blockIdx.x >> 1;
+  const int nfull = args.N / BNP;
+  int tm, tn;
+  if (pr < args.ntm * nfull) {
+    tm = pr / nfull;
+    tn = pr % nfull;
+  } else {
+    tm = pr - args.ntm * nfull;
+    tn = nfull;
+  }
+  const int n0 = tn * BNP;
+  const int n_eff = (min(BNP, args.N - n0) + 15) / 16 * 16;   // MMA N of this pair
+  const int a_row0 = tm * 2 * BM + (int)rank * BM;
+  const int b_row0 = n0 + (int)rank * (n_eff / 2);
+  const uint32_t idesc = C::IDESC_NO_N | ((uint32_t)(n_eff >> 3) << 17);
+  const int nk = args.nkb;
+  if (nk <= 0) return;  // uniform over both CTAs, before any barrier exists
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(accf), 1);
+    *abort_flag = 0;
+    *consumed_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(C::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  pair_sync();   // barriers of both CTAs initialised, tensor memory allocated in both
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t full_leader = map_to_rank(smem_u32(full), 0);
+
+  int issued = 0;  // producer only
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % C::STAGES;
+        const uint32_t ph = (uint32_t)(i / C::STAGES) & 1u;
+        if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1u, args.err, 11, abort_flag)) break;
+        uint8_t* st = smem + s * C::STAGE_BYTES;
+        const uint32_t fb = full_leader + (uint32_t)(s * 8);
+        if (rank == 0) mbar_expect_tx(smem_u32(&full[s]), C::TX_PAIR);
+        const int kx = i * C::BKE;
+        tma_load_2d_pair(smem_u32(st), &ta_hi, fb, kx, a_row0);
+        if (X3) tma_load_2d_pair(smem_u32(st + C::A_BYTES), &ta_lo, fb, kx, a_row0);
+        tma_load_2d_pair(smem_u32(st + C::NPARTS * C::A_BYTES), &tb_hi, fb, kx, b_row0);
+        if (X3)
+          tma_load_2d_pair(smem_u32(st + C::NPARTS * C::A_BYTES + C::B_BYTES), &tb_lo, fb, kx,
+                           b_row0);
+        issued = i + 1;
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && rank == 0) {
+      int i = 0;
+      for (; i < nk; ++i) {
+        const int s = i % C::STAGES;
+        const uint32_t ph = (uint32_t)(i / C::STAGES) & 1u;
+        if (!mbar_wait(smem_u32(&full[s]), ph, args.err, 12, abort_flag)) break;
+        tc_fence_after();
+        const uint32_t st = smem_u32(smem + s * C::STAGE_BYTES);
+        const uint32_t a_hi = st, a_lo = st + C::A_BYTES;
+        const uint32_t b_hi = st + C::NPARTS * C::A_BYTES;
+        const uint32_t b_lo = b_hi + C::B_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < C::ROWB / 32; ++kk) {
+          const uint32_t off = kk * 32;   // one MMA consumes K = 16 (32 bytes)
+          constexpr int SW = C::SWZ, SB = C::SBO;
+          umma_bf16_pair(tmem, sdesc<SW, SB>(a_hi + off), sdesc<SW, SB>(b_hi + off), idesc,
+                         (i > 0 || kk > 0) ? 1u : 0u);
+          if (X3) {
+            umma_bf16_pair(tmem, sdesc<SW, SB>(a_hi + off), sdesc<SW, SB>(b_lo + off), idesc, 1u);
+            umma_bf16_pair(tmem, sdesc<SW, SB>(a_lo + off), sdesc<SW, SB>(b_hi + off), idesc, 1u);
+          }
+        }
+        umma_commit_pair(smem_u32(&empty[s]));
+      }
+      *consumed_sh = i;
+      umma_commit_pair(smem_u32(accf));   // both CTAs' epilogues start when every MMA is done
+    }
+  } else {
+    const int q = warp & 3;  // TMEM lanes 32q .. 32q+31 belong to this warp
+    const int row = q * 32 + lane;
+    const bool ok = mbar_wait(smem_u32(accf), 0, args.err, 13, abort_flag);
+    tc_fence_after();
+    if (ok) {
+      const int m = a_row0 + row;
+      const float sm = (float)args.s1[m];
+      const float cm = args.c[m];
+#pragma unroll 1
+      for (int c0 = 0; c0 < n_eff; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int n = n0 + c0 + j;
+          if (n < args.N) {
+            if (args.at_hi) put<X3>(args.at_hi, args.at_lo, (size_t)n * args.ldo + m, sm * v[j]);
+            if (args.zt_hi) {
+              const size_t oz = (size_t)n * args.ldz + m;
+              put<X3>(args.zt_hi, args.zt_lo, oz, v[j]);
+              put<X3>(args.yt_hi, args.yt_lo, oz, cm * v[j]);
+            }
+          }
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (*abort_flag) {
+    // Drain (bounded): the leader's producer waits for stages it expected but its MMA thread
+    // never consumed, the MMA thread for its outstanding MMAs.
+    if (rank == 0 && warp == 0 && lane == 0) {
+      for (int i = *consumed_sh; i < issued; ++i) {
+        const int s = i % C::STAGES;
+        const uint32_t ph = (uint32_t)(i / C::STAGES) & 1u;
+        volatile int no_abort = 0;
+        mbar_wait(smem_u32(&full[s]), ph, args.err, 14, &no_abort, kWaitCycles / 8);
+      }
+    }
+    if (rank == 0 && warp == 1 && lane == 0) {
+      volatile int no_abort = 0;
+      mbar_wait(smem_u32(accf), 0, args.err, 15, &no_abort, kWaitCycles / 8);
+    }
+    __syncthreads();
+  }
+  pair_sync();   // neither CTA releases memory the other's copies or MMAs may still use
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(C::TMEM_COLS)
+                 : "memory");
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -528,6 +779,40 @@ cudaError_t launch_t(const TcPlan& p, const TcArgs& a, dim3 grid, cudaStream_t s
   return cudaGetLastError();
 }
 
+template <int BNP, int MODE>
+cudaError_t launch_pair_t(const TcPlan& p, const TcArgs& a, int ctas, cudaStream_t st) {
+  using C = PairCfg<BNP, MODE>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_pair<BNP, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_tc_pair<BNP, MODE><<<ctas, kThreads, C::SMEM, st>>>(p.ta_hi, p.ta_lo, p.tb_hi, p.tb_lo, a);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <int BNP>
+cudaError_t launch_pair_mode(const TcPlan& p, const TcArgs& a, int ctas, cudaStream_t st) {
+  if (p.mode == MODE_BF16X3) return launch_pair_t<BNP, MODE_BF16X3>(p, a, ctas, st);
+  if (p.mode == MODE_BF16) return launch_pair_t<BNP, MODE_BF16>(p, a, ctas, st);
+  return cudaErrorInvalidValue;
+}
+
+constexpr int kPairTiles[4] = {128, 160, 208, 256};
+
+cudaError_t launch_pair(const TcPlan& p, const TcArgs& a, int ctas, cudaStream_t st) {
+  switch (p.bn) {
+    case 128: return launch_pair_mode<128>(p, a, ctas, st);
+    case 160: return launch_pair_mode<160>(p, a, ctas, st);
+    case 208: return launch_pair_mode<208>(p, a, ctas, st);
+    case 256: return launch_pair_mode<256>(p, a, ctas, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <int KIND, int BN>
 cudaError_t launch_mode(const TcPlan& p, const TcArgs& a, dim3 grid, cudaStream_t st) {
   if (p.mode == MODE_BF16X3) return launch_t<BN, MODE_BF16X3, KIND>(p, a, grid, st);
@@ -546,31 +831,12 @@ cudaError_t launch_any(const TcPlan& p, const TcArgs& a, dim3 grid, cudaStream_t
     return cudaErrorInvalidValue;
   }
   switch (p.bn) {
-    case 176:
-      if constexpr (KIND == TC_TANGENT) return launch_mode<KIND, 176>(p, a, grid, st);
-      return cudaErrorInvalidValue;
     case 112: return launch_mode<KIND, 112>(p, a, grid, st);
     case 128: return launch_mode<KIND, 128>(p, a, grid, st);
     case 208: return launch_mode<KIND, 208>(p, a, grid, st);
     case 256: return launch_mode<KIND, 256>(p, a, grid, st);
     default: return cudaErrorInvalidValue;
   }
-}
-
-// Makespan model of one tangent launch: CTAs in launch order (full-width tiles, then the narrow
-// remainder tiles) go to the first free SM; a tile costs its MMA width plus a fixed 24 columns.
-double tangent_makespan(int ntm, int N, int bn, int sm_count) {
-  const int nfull = N / bn, rem = N - nfull * bn;
-  std::vector<double> t;
-  for (int i = 0; i < ntm * nfull; ++i) t.push_back(bn + 24.0);
-  if (rem > 0)
-    for (int i = 0; i < ntm; ++i) t.push_back((rem + 15) / 16 * 16 + 24.0);
-  std::vector<double> sm(std::max(1, sm_count), 0.0);
-  for (double c : t) {
-    auto it = std::min_element(sm.begin(), sm.end());
-    *it += c;
-  }
-  return *std::max_element(sm.begin(), sm.end());
 }
 
 int count_lower_tiles(int ntm, int ntn, int bn) {
@@ -632,13 +898,27 @@ int tc_plan_make(TcPlan& p, int kind, int prec, const void* a_hi, const void* a_
     if (p.splits > nkb) p.splits = nkb;
     p.kb_per_split = (nkb + p.splits - 1) / p.splits;
     p.splits = (nkb + p.kb_per_split - 1) / p.kb_per_split;
+  } else if (kind == TC_TANGENT && force_bn < 0) {
+    // SM-pair kernel: 256-row tiles, N tile -force_bn
+    bool ok = M % (2 * BM) == 0 && (p.mode == MODE_BF16 || p.mode == MODE_BF16X3);
+    bool known = false;
+    for (int t : kPairTiles) known |= t == -force_bn;
+    if (!ok || !known) return NNC_ERR_ARG;
+    p.pair = 1;
+    p.bn = -force_bn;
+    p.ntm = M / (2 * BM);
+    p.ntn = (N + p.bn - 1) / p.bn;
+    p.splits = 1;
+    p.kb_per_split = nkb;
   } else if (kind == TC_TANGENT) {
     int best_bn = 208;
     double best = 1e30;
-    const int cands[5] = {256, 208, 176, 128, 112};
+    const int cands[4] = {256, 208, 128, 112};
     const int ntm = M / BM;
     for (int bn : cands) {
-      const double cost = tangent_makespan(ntm, N, bn, sm_count);
+      // waves of full tiles; the narrow remainder tile counts as a full one
+      const int ctas = ntm * ((N + bn - 1) / bn);
+      const double cost = (double)((ctas + sm_count - 1) / sm_count) * (bn + 24);
       if (cost < best - 1e-9) {
         best = cost;
         best_bn = bn;
@@ -660,7 +940,8 @@ int tc_plan_make(TcPlan& p, int kind, int prec, const void* a_hi, const void* a_
     p.splits = (nkb + p.kb_per_split - 1) / p.kb_per_split;
   }
   const int a_box = BM;
-  const int b_box = p.bn;   // REV: the seed rows of B beyond the plan's N read as zero
+  // REV: the seed rows of B beyond the plan's N read as zero; pair plans: each CTA's half of B
+  const int b_box = p.pair ? p.bn / 2 : p.bn;
   if (!make_map(&p.ta_hi, a_hi, a_rows, K, ld_a, a_box, p.bk, eb)) return NNC_ERR_CUDA;
   if (!make_map(&p.ta_lo, p.x3 ? a_lo : nullptr, a_rows, K, ld_a, a_box, p.bk, eb)) return NNC_ERR_CUDA;
   if (!make_map(&p.tb_hi, b_hi, b_rows, K, ld_b, b_box, p.bk, eb)) return NNC_ERR_CUDA;
@@ -698,6 +979,7 @@ cudaError_t tc_tangent(const TcPlan& p, const double* s1, const float* c, void* 
   a.err = err;
   a.wscale = wscale;
   a.tscale = tscale;
+  if (p.pair) return launch_pair(p, a, 2 * p.ntm * p.ntn, st);
   return launch_any<TC_TANGENT>(p, a, dim3(p.ntn * p.ntm, 1, 1), st);
 }
 

@@ -26,14 +26,19 @@ struct TcPlan {
   int bn = 0;           // N tile
   int bk = 64;          // K block (elements) of a pipeline stage
   int mode = 0;         // 0 BF16, 1 split-BF16x3, 2 FP8 e4m3 (tangent GEMM only)
-  int ntm = 0, ntn = 0; // tiles along M and N
+  int pair = 0;         // tangent GEMM on SM pairs (cta_group::2, 256-row tiles, bn = pair tile)
+  int ntm = 0, ntn = 0; // tiles along M and N (pair plans: 256-row blocks)
   int splits = 1, kb_per_split = 0;
   bool ready = false;
 };
 
+// Tile code of a tangent plan: the N tile, negative for the SM-pair kernel.
+inline int plan_code(const TcPlan& p) { return p.pair ? -p.bn : p.bn; }
+
 // Choose tiles and split-K for one GEMM and encode its tensor maps.  a_rows / b_rows are the
 // row counts of the A and B arrays (rows beyond them read as zero), ld_a / ld_b their row
-// strides in elements.  Returns NNC_OK or a negative status.
+// strides in elements.  Tangent GEMMs: force_bn > 0 pins a single-SM N tile, force_bn < 0 the
+// SM-pair kernel with N tile -force_bn.  Returns NNC_OK or a negative status.
 int tc_plan_make(TcPlan& p, int kind, int prec, const void* a_hi, const void* a_lo, int a_rows,
                  int ld_a, const void* b_hi, const void* b_lo, int b_rows, int ld_b, int M, int N,
                  int K, int sm_count, int force_bn = 0, int force_splits = 0,

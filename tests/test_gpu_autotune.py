@@ -55,14 +55,22 @@ def test_tune_set_pins_tiles_and_keeps_results():
     lam = synth.normal(synth.derive_key(5, "tune-lam"), 7)
     net = nnc.Net.from_mlp(mlp, precision="bf16x3")
     H0 = net.hessian_lag(x, lam)
-    for bn in (112, 128, 176, 208, 256):
+    for bn in (112, 128, 208, 256):
         net.tune_set(tangent_bn=bn)
         assert net.tuning(1)[0] == bn
         assert np.array_equal(net.hessian_lag(x, lam), H0), bn
+    # SM-pair tiles (cta_group::2, 256-row tiles): the same products in the same K order
+    for bn in (-128, -160, -208, -256):
+        net.tune_set(tangent_bn=bn)
+        assert net.tuning(1)[0] == bn
+        H = net.hessian_lag(x, lam)
+        assert np.linalg.norm(H - H0) <= 1e-6 * np.linalg.norm(H0), (bn, np.linalg.norm(H - H0))
     net.tune_set(syrk_splits=1)
     assert net.tuning(0)[1] == 1
     H1 = net.hessian_lag(x, lam)
     assert np.linalg.norm(H1 - H0) <= 1e-4 * np.linalg.norm(H0)
     with pytest.raises(nnc.NNCError):
         net.tune_set(tangent_bn=100)
+    with pytest.raises(nnc.NNCError):
+        net.tune_set(tangent_bn=-112)
     net.free()

@@ -240,3 +240,31 @@ def test_softmax_classifier_full_size_sampled(lib, name, prec):
     r = net.residual(d.x0, yo)
     assert np.max(np.abs(r)) <= 1e-10 * max(1.0, np.max(np.abs(yo)))
     net.free()
+
+
+PAIR_NETS = [
+    ([784, 512, 768, 10], ["tanh", "sigmoid", "identity"]),          # two pair-tiled layers
+    ([117, 1024, 512, 37], ["tanh", "softplus", "identity"]),        # one N tile (117 columns)
+    ([300, 256, 1280, 5], ["gelu", "tanh", "softmax"]),              # remainder N tile, softmax
+]
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+@pytest.mark.parametrize("case", range(len(PAIR_NETS)))
+def test_pair_tangent_kernel(lib, prec, case):
+    """Tangent GEMMs on SM pairs (tcgen05 cta_group::2, 256-row tiles) for every pair tile: the
+    full Hessian against the oracle."""
+    widths, acts = PAIR_NETS[case]
+    mlp = make_mlp(MLPSpec(widths, acts), seed=case + 40, tag="pair", bias_std=0.2)
+    x = synth.uniform01(synth.derive_key(case, "pair-x"), widths[0])
+    lam = synth.normal(synth.derive_key(case, "pair-lam"), widths[-1])
+    Ho = onn.hessian_lag(mlp, x, lam)
+    for bn in (-128, -160, -208, -256):
+        net = lib.Net.from_mlp(mlp, precision=prec)
+        net.tune_set(tangent_bn=bn)
+        H = net.hessian_lag(x, lam)
+        e = rel(H, Ho)
+        print(f"[pair {case} {prec} {bn}] H rel err {e:.2e}")
+        assert e < (1e-4 if prec == "bf16x3" else TOL[prec]["H"]), (bn, e)
+        assert np.array_equal(H, H.T)
+        net.free()
