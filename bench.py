@@ -484,8 +484,10 @@ def run_ours(args, rank, world, local_rank):
         avg_s = dom_ms / dom_cnt / 1e3
         ach = fl_per_launch / avg_s / 1e12
         pk = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
-        roof = {"kernel": "k_tc_gemm (tangent: Zdot_l = W_l Adot_{l-1}, fused sigma' / sigma'' epilogue)"
-                if args.prec.startswith("bf16") else "k_simt_gemm (tangent)",
+        kname = ("k_tc_pair (tangent on SM pairs, tcgen05 cta_group::2: Zdot_l = W_l Adot_{l-1}, "
+                 "fused sigma' / sigma'' epilogue)" if tangent_bn < 0 else
+                 "k_tc_gemm (tangent: Zdot_l = W_l Adot_{l-1}, fused sigma' / sigma'' epilogue)")
+        roof = {"kernel": kname if args.prec.startswith("bf16") else "k_simt_gemm (tangent)",
                 "bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
                 "traffic": TANGENT_TRAFFIC.get((args.prec, tangent_bn)),
                 "tangent_bn": tangent_bn,
