@@ -35,6 +35,24 @@ double secs(Clock::time_point a, Clock::time_point b) {
   return std::chrono::duration<double>(b - a).count();
 }
 
+// ---------------------------------------------------------------- dense helpers (OpenMP)
+double max_abs(const double* x, size_t n) {
+  double m = 0.0;
+#pragma omp parallel for reduction(max : m) schedule(static) if (n > 65536)
+  for (long long i = 0; i < (long long)n; ++i) m = std::max(m, std::fabs(x[i]));
+  return m;
+}
+bool all_finite(const double* x, size_t n) {
+  int ok = 1;
+#pragma omp parallel for reduction(&& : ok) schedule(static) if (n > 65536)
+  for (long long i = 0; i < (long long)n; ++i) ok = ok && std::isfinite(x[i]);
+  return ok != 0;
+}
+void par_zero(double* x, size_t n) {
+#pragma omp parallel for schedule(static) if (n > 65536)
+  for (long long i = 0; i < (long long)n; ++i) x[i] = 0.0;
+}
+
 // ---------------------------------------------------------------- dense linear algebra
 // Row-major n x n, lower triangle.  Returns false if the matrix is not positive definite.
 bool cholesky(int n, double* A) {
@@ -104,20 +122,34 @@ bool cholesky(int n, double* A) {
 }
 
 // L y = b in place (L lower, row-major n x n), for r right-hand sides stored row-major n x r.
+// Blocked by 64 rows: the diagonal block is solved row by row, then the rows below subtract its
+// contribution in parallel (the bulk of the n^2 r / 2 multiply-adds).
 void lower_solve(int n, const double* L, int r, double* B) {
-#pragma omp parallel for schedule(static) if (r >= 8)
-  for (int c0 = 0; c0 < r; c0 += 8) {
-    const int c1 = std::min(r, c0 + 8);
-    for (int i = 0; i < n; ++i) {
+  const int NB = 64;
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int k1 = std::min(n, k0 + NB);
+    for (int i = k0; i < k1; ++i) {
       const double* li = L + (size_t)i * n;
       double* bi = B + (size_t)i * r;
-      for (int j = 0; j < i; ++j) {
+      for (int j = k0; j < i; ++j) {
         const double l = li[j];
         if (l == 0.0) continue;
         const double* bj = B + (size_t)j * r;
-        for (int c = c0; c < c1; ++c) bi[c] -= l * bj[c];
+        for (int c = 0; c < r; ++c) bi[c] -= l * bj[c];
       }
-      for (int c = c0; c < c1; ++c) bi[c] /= li[i];
+      const double d = li[i];
+      for (int c = 0; c < r; ++c) bi[c] /= d;
+    }
+#pragma omp parallel for schedule(static) if ((size_t)(n - k1) * r > 4096)
+    for (int i = k1; i < n; ++i) {
+      const double* li = L + (size_t)i * n;
+      double* bi = B + (size_t)i * r;
+      for (int j = k0; j < k1; ++j) {
+        const double l = li[j];
+        if (l == 0.0) continue;
+        const double* bj = B + (size_t)j * r;
+        for (int c = 0; c < r; ++c) bi[c] -= l * bj[c];
+      }
     }
   }
 }
@@ -142,8 +174,9 @@ void lower_solve1(int n, const double* L, double* x) {
 }
 
 // Bunch-Kaufman symmetric indefinite factorization P A P^T = L D L^T (Golub & Van Loan,
-// "Matrix Computations", Sec. 4.4), full symmetric storage, row-major.  Records the pivot
-// sequence and the inertia of A (via Sylvester's law from the 1x1 / 2x2 blocks of D).
+// "Matrix Computations", Sec. 4.4), row-major, only the lower triangle is read and updated
+// (symmetric row / column interchanges act on it directly).  Records the pivot sequence and the
+// inertia of A (via Sylvester's law from the 1x1 / 2x2 blocks of D).
 struct BK {
   int n = 0;
   std::vector<double> A;     // factored in place: L below the diagonal, D on/near it
@@ -158,13 +191,18 @@ struct BK {
     for (int i = 0; i < n; ++i) perm[i] = i;
     npos = nneg = nzero = 0;
     const double alpha = (1.0 + std::sqrt(17.0)) / 8.0;
-    auto a = [&](int i, int j) -> double& { return A[(size_t)i * n + j]; };
+    auto a = [&](int i, int j) -> double& { return A[(size_t)i * n + j]; };   // i >= j
+    // interchange rows and columns r and s of the symmetric matrix held in the lower triangle
     auto swap_rc = [&](int r, int s) {
       if (r == s) return;
-      for (int j = 0; j < n; ++j) std::swap(a(r, j), a(s, j));
-      for (int i = 0; i < n; ++i) std::swap(a(i, r), a(i, s));
+      if (r > s) std::swap(r, s);
+      for (int j = 0; j < r; ++j) std::swap(a(r, j), a(s, j));
+      std::swap(a(r, r), a(s, s));
+      for (int j = r + 1; j < s; ++j) std::swap(a(j, r), a(s, j));
+      for (int j = s + 1; j < n; ++j) std::swap(a(j, r), a(j, s));
       std::swap(perm[r], perm[s]);
     };
+    std::vector<double> l1(n, 0.0), l2(n, 0.0);
     int k = 0;
     while (k < n) {
       const double absakk = std::fabs(a(k, k));
@@ -187,9 +225,9 @@ struct BK {
       if (absakk >= alpha * colmax) {
         kp = k;
       } else {
-        double rowmax = 0.0;
-        for (int j = k; j < n; ++j)
-          if (j != imax) rowmax = std::max(rowmax, std::fabs(a(imax, j)));
+        double rowmax = 0.0;   // largest off-diagonal of row imax inside the trailing block
+        for (int j = k; j < imax; ++j) rowmax = std::max(rowmax, std::fabs(a(imax, j)));
+        for (int j = imax + 1; j < n; ++j) rowmax = std::max(rowmax, std::fabs(a(j, imax)));
         if (absakk >= alpha * colmax * (colmax / rowmax)) {
           kp = k;
         } else if (std::fabs(a(imax, imax)) >= alpha * rowmax) {
@@ -208,15 +246,16 @@ struct BK {
         else if (d > 0) ++npos;
         else ++nneg;
         const double inv = d != 0.0 ? 1.0 / d : 0.0;
-        // trailing update A22 -= a21 a21^T / d (full symmetric storage)
-#pragma omp parallel for schedule(static) if (n - k > 256)
+        for (int i = k + 1; i < n; ++i) l1[i] = a(i, k);
+        // trailing update A22 -= a21 a21^T / d on the lower triangle
+#pragma omp parallel for schedule(dynamic, 16) if (n - k > 192)
         for (int i = k + 1; i < n; ++i) {
-          const double f = a(i, k) * inv;
+          const double f = l1[i] * inv;
           if (f == 0.0) continue;
           double* ai = &a(i, 0);
-          for (int j = k + 1; j < n; ++j) ai[j] -= f * A[(size_t)j * n + k];
+          for (int j = k + 1; j <= i; ++j) ai[j] -= f * l1[j];
         }
-        for (int i = k + 1; i < n; ++i) a(i, k) *= inv;
+        for (int i = k + 1; i < n; ++i) a(i, k) = l1[i] * inv;
       } else {
         const double d11 = a(k, k), d21 = a(k + 1, k), d22 = a(k + 1, k + 1);
         const double det = d11 * d22 - d21 * d21;
@@ -231,18 +270,19 @@ struct BK {
           nneg += 2;
         }
         const double i11 = d22 / det, i22 = d11 / det, i21 = -d21 / det;
-        // W = A(k+2:, k:k+2); L = W D^-1; A22 -= W D^-1 W^T
-        std::vector<double> l1(n, 0.0), l2(n, 0.0);
+        // W = A(k+2:, k:k+2); L = W D^-1; A22 -= W D^-1 W^T (lower triangle)
+        std::vector<double> w1(n, 0.0), w2(n, 0.0);
         for (int i = k + 2; i < n; ++i) {
-          const double w1 = a(i, k), w2 = a(i, k + 1);
-          l1[i] = w1 * i11 + w2 * i21;
-          l2[i] = w1 * i21 + w2 * i22;
+          w1[i] = a(i, k);
+          w2[i] = a(i, k + 1);
+          l1[i] = w1[i] * i11 + w2[i] * i21;
+          l2[i] = w1[i] * i21 + w2[i] * i22;
         }
-#pragma omp parallel for schedule(static) if (n - k > 256)
+#pragma omp parallel for schedule(dynamic, 16) if (n - k > 192)
         for (int i = k + 2; i < n; ++i) {
           double* ai = &a(i, 0);
           const double f1 = l1[i], f2 = l2[i];
-          for (int j = k + 2; j < n; ++j) ai[j] -= f1 * A[(size_t)j * n + k] + f2 * A[(size_t)j * n + k + 1];
+          for (int j = k + 2; j <= i; ++j) ai[j] -= f1 * w1[j] + f2 * w2[j];
         }
         for (int i = k + 2; i < n; ++i) {
           a(i, k) = l1[i];
@@ -327,10 +367,21 @@ struct KktSolver {
     prow.clear(); pcol.clear(); orow.clear(); palpha.clear(); pe.clear(); pterm.clear();
     pD.assign(ns_, 0.0);
     std::vector<int> ccount(ns_, 0);
-    for (int j = 0; j < m_; ++j)
-      for (int c = 0; c < ns_; ++c)
-        if (AS[(size_t)j * ns_ + c] != 0.0) ++ccount[c];
+    // column counts of A_S, in parallel over column blocks (each thread reads row segments)
+#pragma omp parallel for schedule(static) if ((size_t)m_ * ns_ > 65536)
+    for (int c0 = 0; c0 < ns_; c0 += 64) {
+      const int c1 = std::min(ns_, c0 + 64);
+      for (int j = 0; j < m_; ++j) {
+        const double* r = AS + (size_t)j * ns_;
+        for (int c = c0; c < c1; ++c) ccount[c] += r[c] != 0.0;
+      }
+    }
     for (int c = 0; c < ns_; ++c) pD[c] = WSS[c] + sig[nd_ + c] + dw;
+    // per-row classification in parallel, then an ordered compaction
+    std::vector<int> rcol(m_, -1);
+    std::vector<double> re(m_, 0.0);
+    std::vector<char> rpin(m_, 0);
+#pragma omp parallel for schedule(static) if ((size_t)m_ * (nd_ + ns_) > 65536)
     for (int j = 0; j < m_; ++j) {
       int col = -1, nnz = 0;
       for (int i = 0; i < nd_ && nnz < 2; ++i)
@@ -343,7 +394,14 @@ struct KktSolver {
         pin = ccount[c] == 1 && pD[c] > 0.0;
         e += a * a / pD[c];
       }
-      if (pin && e > 0.0) {
+      rpin[j] = pin && e > 0.0;
+      rcol[j] = col;
+      re[j] = e;
+    }
+    for (int j = 0; j < m_; ++j) {
+      const int col = rcol[j];
+      const double e = re[j];
+      if (rpin[j]) {
         prow.push_back(j);
         pcol.push_back(col);
         palpha.push_back(col >= 0 ? AD[(size_t)j * nd_ + col] : 0.0);
@@ -823,14 +881,16 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
   KktSolver kkt;
   // atl = A^T lam, row by row (contiguous reads of the dense Jacobian blocks)
   auto update_atl = [&]() {
-    std::fill(atl.begin(), atl.end(), 0.0);
-    for (int j = 0; j < m; ++j) {
-      const double l = lam[j];
-      if (l == 0.0) continue;
-      const double* ad = &AD[(size_t)j * nd];
-      const double* as = &AS[(size_t)j * ns];
-      for (int i = 0; i < nd; ++i) atl[i] += ad[i] * l;
-      for (int i = 0; i < ns; ++i) atl[nd + i] += as[i] * l;
+#pragma omp parallel for schedule(static) if ((size_t)m * n > 65536)
+    for (int i0 = 0; i0 < n; i0 += 64) {   // column blocks, rows streamed
+      const int i1 = std::min(n, i0 + 64);
+      for (int i = i0; i < i1; ++i) atl[i] = 0.0;
+      for (int j = 0; j < m; ++j) {
+        const double l = lam[j];
+        if (l == 0.0) continue;
+        for (int i = i0; i < i1; ++i)
+          atl[i] += (i < nd ? AD[(size_t)j * nd + i] : AS[(size_t)j * ns + i - nd]) * l;
+      }
     }
   };
   (void)r;
@@ -893,7 +953,7 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
     bool finite = std::isfinite(fv);
     for (double x : g) finite &= std::isfinite(x);
     for (double x : c) finite &= std::isfinite(x);
-    for (double x : AD) finite &= std::isfinite(x);
+    finite &= all_finite(AD.data(), AD.size());
     if (!finite) { status = NNC_IPM_NONFINITE; break; }
     update_atl();
     E0 = errors(0.0);
@@ -922,13 +982,13 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
     double delta_w = 0.0, delta_c = 0.0;
     bool first = true, ok = false;
     double scale = 1.0;
-    for (size_t i = 0; i < WDD.size(); ++i) scale = std::max(scale, std::fabs(WDD[i]));
+    scale = std::max(scale, max_abs(WDD.data(), WDD.size()));
     for (int i = 0; i < n; ++i) {
       sig[i] = SigL[i] + SigU[i];
       scale = std::max(scale, sig[i]);
     }
-    for (double x : AD) scale = std::max(scale, std::fabs(x));
-    for (double x : AS) scale = std::max(scale, std::fabs(x));
+    scale = std::max(scale, max_abs(AD.data(), AD.size()));
+    scale = std::max(scale, max_abs(AS.data(), AS.size()));
     const double zero_tol = 1e-14 * scale;
     int tries = 0;
     while (true) {
@@ -1096,8 +1156,8 @@ struct Adversarial : IpmProblem {
   int jac(const double* v, double* AD, double* AS) override {
     int rc = nnc_jacobian(net, v, J.data());
     if (rc) return rc;
-    std::fill(AD, AD + (size_t)m * nd, 0.0);
-    std::fill(AS, AS + (size_t)m * ns, 0.0);
+    par_zero(AD, (size_t)m * nd);
+    par_zero(AS, (size_t)m * ns);
     for (int j = 0; j < n_out; ++j) {
       for (int i = 0; i < n_in; ++i) AD[(size_t)j * nd + i] = -J[(size_t)j * n_in + i];
       AS[(size_t)j * ns + j] = 1.0;
@@ -1173,8 +1233,8 @@ struct AdversarialL1 : IpmProblem {
   int jac(const double* v, double* AD, double* AS) override {
     int rc = nnc_jacobian(net, v, J.data());
     if (rc) return rc;
-    std::fill(AD, AD + (size_t)m * nd, 0.0);
-    std::fill(AS, AS + (size_t)m * ns, 0.0);
+    par_zero(AD, (size_t)m * nd);
+    par_zero(AS, (size_t)m * ns);
     for (int i = 0; i < n_in; ++i) {
       AD[(size_t)i * nd + i] = 1.0;
       AS[(size_t)i * ns + i] = -1.0;            // p_i
@@ -1274,8 +1334,8 @@ struct Scopf : IpmProblem {
     gather(v);
     int r = nnc_batch_eval(b, xc.data(), nullptr, nullptr, Jc.data(), nullptr, nullptr);
     if (r) return r;
-    std::fill(AD, AD + (size_t)m * nd, 0.0);
-    std::fill(AS, AS + (size_t)m * ns, 0.0);
+    par_zero(AD, (size_t)m * nd);
+    par_zero(AS, (size_t)m * ns);
     for (int k = 0; k < K; ++k) {
       for (int j = 0; j < nk[k]; ++j) AD[(size_t)k * nd + sub[off[k] + j]] -= Jc[off[k] + j];
       AS[(size_t)k * ns + k] = 1.0;

@@ -170,3 +170,36 @@ def test_negative_small_block_diagonal_whole_matrix(nnc):
     assert (npos, nneg, nzero) == (int((ev > 0).sum()), int((ev < 0).sum()), 0)
     ref = np.linalg.solve(K, rhs)
     assert np.linalg.norm(x - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+def test_negative_small_block_diagonal_schur(nnc):
+    """A negative small-block diagonal entry with a definite dense block: Cholesky of the dense
+    block and Bunch-Kaufman of the whole reduced system of the small block and the multipliers."""
+    W, WSS, sig, AD, AS, K = _kkt(40, 9, 7, seed=23, indefinite=False)
+    WSS[[1, 4]] = [-6.0, -2.5]
+    n = 49
+    K[40 + 1, 40 + 1] = WSS[1] + sig[40 + 1]
+    K[40 + 4, 40 + 4] = WSS[4] + sig[40 + 4]
+    rhs = np.random.default_rng(8).standard_normal(n + 7)
+    x, (npos, nneg, nzero, full) = nnc.kkt_solve(W, WSS, sig, AD, AS, rhs)
+    assert full == 0
+    ev = np.linalg.eigvalsh(K)
+    assert (npos, nneg, nzero) == (int((ev > 0).sum()), int((ev < 0).sum()), 0)
+    ref = np.linalg.solve(K, rhs)
+    assert np.linalg.norm(x - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("n,seed", [(5, 1), (37, 2), (300, 3)])
+def test_bunch_kaufman_through_whole_matrix(nnc, n, seed):
+    """Indefinite matrices of every size class through the whole-matrix factorization (negative
+    small-block diagonal, indefinite dense block): inertia and solution."""
+    W, WSS, sig, AD, AS, K = _kkt(n, 6, 4, seed=seed, indefinite=True)
+    WSS[0] = -9.0
+    K[n, n] = WSS[0] + sig[n]
+    rhs = np.random.default_rng(seed).standard_normal(n + 10)
+    x, (npos, nneg, nzero, full) = nnc.kkt_solve(W, WSS, sig, AD, AS, rhs)
+    assert full == 1
+    ev = np.linalg.eigvalsh(K)
+    assert (npos, nneg, nzero) == (int((ev > 0).sum()), int((ev < 0).sum()), 0)
+    ref = np.linalg.solve(K, rhs)
+    assert np.linalg.norm(x - ref) <= 1e-8 * np.linalg.norm(ref)
