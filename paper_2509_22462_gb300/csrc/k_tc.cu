@@ -135,6 +135,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, int* err,
   }
 }
 
+// Programmatic dependent launch: wait until the preceding kernel of the stream has completed and
+// its writes are visible; allow the next one to be scheduled.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive(uint32_t a) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
 }
@@ -322,6 +329,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  // tangent chain (launched with programmatic dependent launch): the previous layer's outputs,
+  // this layer's B operand, are complete before any copy or store of this CTA
+  if (KIND == TC_TANGENT) griddep_wait();
 
   int issued = 0;  // producer only
   if (warp == 0) {
@@ -388,6 +398,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int row = q * 32 + lane;
     const bool ok = mbar_wait(smem_u32(accf), 0, args.err, 3, abort_flag);
     tc_fence_after();
+    // the next layer may be queued now: its CTAs take SMs as this grid's epilogues end
+    if (KIND == TC_TANGENT && threadIdx.x == 64) griddep_launch();
     if (ok && KIND == TC_REV) {
       // split-K partial of W_l^T Zbar: P[split][k][0..BN) for row k of this tile
       const int k = m0 + row;
@@ -418,11 +430,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (n < n_valid) {
               const size_t orow = (size_t)(KIND == TC_TANGENT_G ? b_row0 + n : n);
               if (args.at_hi) put<X3>(args.at_hi, args.at_lo, orow * args.ldo + m, sm * v[j]);
-              if (args.zt_hi) {
-                const size_t oz = orow * args.ldz + m;
-                put<X3>(args.zt_hi, args.zt_lo, oz, v[j]);
-                put<X3>(args.yt_hi, args.yt_lo, oz, cm * v[j]);
-              }
+              if (args.zt_hi) put<X3>(args.zt_hi, args.zt_lo, orow * args.ldz + m, v[j]);
+              if (args.yt_hi) put<X3>(args.yt_hi, args.yt_lo, orow * args.ldz + m, cm * v[j]);
             }
           }
         }
@@ -622,6 +631,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   pair_sync();   // barriers of both CTAs initialised, tensor memory allocated in both
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  griddep_wait();   // programmatic dependent launch: the previous layer's outputs are complete
   const uint32_t full_leader = map_to_rank(smem_u32(full), 0);
 
   int issued = 0;  // producer only
@@ -677,6 +687,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     const int row = q * 32 + lane;
     const bool ok = mbar_wait(smem_u32(accf), 0, args.err, 13, abort_flag);
     tc_fence_after();
+    if (threadIdx.x == 64) griddep_launch();
     if (ok) {
       const int m = a_row0 + row;
       const float sm = (float)args.s1[m];
@@ -690,11 +701,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
           const int n = n0 + c0 + j;
           if (n < args.N) {
             if (args.at_hi) put<X3>(args.at_hi, args.at_lo, (size_t)n * args.ldo + m, sm * v[j]);
-            if (args.zt_hi) {
-              const size_t oz = (size_t)n * args.ldz + m;
-              put<X3>(args.zt_hi, args.zt_lo, oz, v[j]);
-              put<X3>(args.yt_hi, args.yt_lo, oz, cm * v[j]);
-            }
+            if (args.zt_hi) put<X3>(args.zt_hi, args.zt_lo, (size_t)n * args.ldz + m, v[j]);
+            if (args.yt_hi) put<X3>(args.yt_hi, args.yt_lo, (size_t)n * args.ldz + m, cm * v[j]);
           }
         }
       }
@@ -773,6 +781,22 @@ cudaError_t launch_t(const TcPlan& p, const TcArgs& a, dim3 grid, cudaStream_t s
     if (e != cudaSuccess) return e;
     attr = true;
   }
+  if (KIND == TC_TANGENT) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_tc_gemm<BN, MODE, KIND>, p.ta_hi, p.ta_lo,
+                                             p.tb_hi, p.tb_lo, p.ta_p2, p.tb_p2, a);
+    note_launch();
+    return e;
+  }
   k_tc_gemm<BN, MODE, KIND><<<grid, kThreads, C::SMEM, st>>>(p.ta_hi, p.ta_lo, p.tb_hi, p.tb_lo, p.ta_p2,
                                                              p.tb_p2, a);
   note_launch();
@@ -789,9 +813,20 @@ cudaError_t launch_pair_t(const TcPlan& p, const TcArgs& a, int ctas, cudaStream
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_tc_pair<BNP, MODE><<<ctas, kThreads, C::SMEM, st>>>(p.ta_hi, p.ta_lo, p.tb_hi, p.tb_lo, a);
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(ctas);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = C::SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_tc_pair<BNP, MODE>, p.ta_hi, p.ta_lo, p.tb_hi,
+                                           p.tb_lo, a);
   note_launch();
-  return cudaGetLastError();
+  return e;
 }
 
 template <int BNP>

@@ -447,12 +447,78 @@ __global__ void __launch_bounds__(256) k_first_tangent_v(const float* __restrict
   }
   if (Zt.hi) {
     st16(Zt.hi, (size_t)nn * ldz + mb, zh);
-    st16(Yt.hi, (size_t)nn * ldz + mb, yh);
-    if (X3) {
-      st16(Zt.lo, (size_t)nn * ldz + mb, zl);
-      st16(Yt.lo, (size_t)nn * ldz + mb, yl);
-    }
+    if (X3) st16(Zt.lo, (size_t)nn * ldz + mb, zl);
   }
+  if (Yt.hi) {
+    st16(Yt.hi, (size_t)nn * ldz + mb, yh);
+    if (X3) st16(Yt.lo, (size_t)nn * ldz + mb, yl);
+  }
+}
+
+// Ydot = c * Zdot over the columns [k0, k1) of the n x ldz operand blocks of the symmetric
+// product, c[k] per column (the curvature weight c_l of the layer owning column k):
+// Y = split(c * (Z_hi + Z_lo)) in the split form, bf16(c * Z) otherwise.  Eight columns per
+// thread (16-byte loads and stores).
+template <bool X3>
+__global__ void __launch_bounds__(256) k_scale_y(const __nv_bfloat16* __restrict__ Zh,
+                                                 const __nv_bfloat16* __restrict__ Zl,
+                                                 __nv_bfloat16* __restrict__ Yh,
+                                                 __nv_bfloat16* __restrict__ Yl,
+                                                 const float* __restrict__ c, int n, int ldz,
+                                                 int k0, int k1) {
+  const int per_row = (k1 - k0) / 8;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n * per_row) return;
+  const int row = (int)(t / per_row);
+  const int k = k0 + 8 * (int)(t % per_row);
+  const size_t o = (size_t)row * ldz + k;
+  const uint4 zh = *reinterpret_cast<const uint4*>(Zh + o);
+  uint4 zl = make_uint4(0, 0, 0, 0);
+  if (X3) zl = *reinterpret_cast<const uint4*>(Zl + o);
+  const float4 c0 = *reinterpret_cast<const float4*>(c + k);
+  const float4 c1 = *reinterpret_cast<const float4*>(c + k + 4);
+  const float cv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+  const uint32_t zhw[4] = {zh.x, zh.y, zh.z, zh.w}, zlw[4] = {zl.x, zl.y, zl.z, zl.w};
+  uint32_t yh[4], yl[4];
+#pragma unroll
+  for (int w = 0; w < 4; ++w) {
+    uint32_t h2 = 0, l2 = 0;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const float z = __bfloat162float(__ushort_as_bfloat16((unsigned short)(zhw[w] >> (16 * u)))) +
+                      (X3 ? __bfloat162float(__ushort_as_bfloat16((unsigned short)(zlw[w] >> (16 * u)))) : 0.f);
+      const float y = cv[2 * w + u] * z;
+      __nv_bfloat16 hb, lb;
+      if (X3) {
+        split_bf16(y, hb, lb);
+      } else {
+        hb = __float2bfloat16_rn(y);
+        lb = __float2bfloat16_rn(0.f);
+      }
+      h2 |= (uint32_t)__bfloat16_as_ushort(hb) << (16 * u);
+      l2 |= (uint32_t)__bfloat16_as_ushort(lb) << (16 * u);
+    }
+    yh[w] = h2;
+    yl[w] = l2;
+  }
+  *reinterpret_cast<uint4*>(Yh + o) = make_uint4(yh[0], yh[1], yh[2], yh[3]);
+  if (X3) *reinterpret_cast<uint4*>(Yl + o) = make_uint4(yl[0], yl[1], yl[2], yl[3]);
+}
+
+cudaError_t launch_scale_y(bool x3, const void* Zh, const void* Zl, void* Yh, void* Yl,
+                           const float* c, int n, int ldz, int k0, int k1, cudaStream_t st) {
+  if (k1 <= k0) return cudaSuccess;
+  if ((k0 | k1 | ldz) % 8 != 0) return cudaErrorInvalidValue;
+  const long long threads = (long long)n * ((k1 - k0) / 8);
+  const int blocks = (int)((threads + 255) / 256);
+  if (x3)
+    k_scale_y<true><<<blocks, 256, 0, st>>>((const __nv_bfloat16*)Zh, (const __nv_bfloat16*)Zl,
+                                            (__nv_bfloat16*)Yh, (__nv_bfloat16*)Yl, c, n, ldz, k0, k1);
+  else
+    k_scale_y<false><<<blocks, 256, 0, st>>>((const __nv_bfloat16*)Zh, nullptr, (__nv_bfloat16*)Yh,
+                                             nullptr, c, n, ldz, k0, k1);
+  note_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t launch_first_tangent(Elem e, const void* W1, int ldw, int m_pad, int n,

@@ -48,6 +48,10 @@ cudaError_t launch_rev_seed(int m, int S, int nJ, int lam_col, const double* s1,
 // First-layer tangents: Zdot_1 = W_1, so At[n][m] = s1[m] W1[m][n] (row stride lda), and
 // Zt = W1^T, Yt[n][m] = c[m] W1[m][n] (row stride ldz; skipped if Zt.hi is NULL).  W1 is the
 // FP32 copy of the first layer (the FP64 copy for the FP64 form).
+// Ydot = c * Zdot over columns [k0, k1) of the n x ldz BF16 (hi, lo) operand blocks (k0, k1,
+// ldz multiples of 8).
+cudaError_t launch_scale_y(bool x3, const void* Zh, const void* Zl, void* Yh, void* Yl,
+                           const float* c, int n, int ldz, int k0, int k1, cudaStream_t st);
 cudaError_t launch_first_tangent(Elem e, const void* W1, int ldw, int m_pad, int n,
                                  const double* s1, const double* c, TanBuf At, int lda, TanBuf Zt,
                                  TanBuf Yt, int ldz, cudaStream_t st);

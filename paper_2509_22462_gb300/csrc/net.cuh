@@ -50,6 +50,12 @@ struct nnc_net {
   std::vector<LayerDev> layers;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // tensor-core forms: the reverse sweep runs on side_stream next to the tangent chain (which no
+  // longer needs its c_l); ev_fork / ev_join order it after the value pass and before the
+  // symmetric product.  cK holds c_l of every curvature layer at its Zdot column offset.
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  float* cK = nullptr;
   int device = 0, sm_count = 0;
   std::vector<void*> allocs;
   double* x = nullptr;       // a_0 [n_in_pad]

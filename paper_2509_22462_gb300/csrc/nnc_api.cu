@@ -266,7 +266,9 @@ int run_reverse(nnc_net* net, bool fp64, int nJ, bool with_lam, const double* la
 // Forward tangents layer by layer (Zdot_1 = W_1 elementwise; Zdot_l = W_l Adot_{l-1} as a GEMM
 // with the n_in tangents as columns), each layer's Zdot_l and c_l * Zdot_l stored side by side
 // along K; then one symmetric product H = sum_l Zdot_l^T diag(c_l) Zdot_l.
-int run_hessian(nnc_net* net, const double* lam, double* H, cudaStream_t st) {
+// deferred: the tangent chain writes Zdot_l only (it does not need c_l, so the reverse sweep that
+// produces c_l runs on the side stream meanwhile); after ev_join, one pass forms c_l * Zdot_l.
+int run_hessian(nnc_net* net, const double* lam, double* H, cudaStream_t st, bool deferred) {
   const int n = net->n_in;
   const int prec = net->prec;
   const bool tc = is_tc(prec);
@@ -280,7 +282,8 @@ int run_hessian(nnc_net* net, const double* lam, double* H, cudaStream_t st) {
     PROF(PK_OTHER);
     TanBuf At0{net->At[0][0], net->At[0][1]};
     TanBuf Zt{zoff(net->Zt[0], L1.zy_off), zoff(net->Zt[1], L1.zy_off)};
-    TanBuf Yt{zoff(net->Yt[0], L1.zy_off), zoff(net->Yt[1], L1.zy_off)};
+    TanBuf Yt{deferred ? nullptr : zoff(net->Yt[0], L1.zy_off),
+              deferred ? nullptr : zoff(net->Yt[1], L1.zy_off)};
     CK(launch_first_tangent(e, prec == NNC_FP64 ? (const void*)L1.W64 : (const void*)L1.W32, L1.kp,
                             L1.mp, n, L1.s1, L1.c, net->L > 1 ? At0 : TanBuf{}, L1.mp, Zt, Yt,
                             net->K_total, st));
@@ -300,7 +303,8 @@ int run_hessian(nnc_net* net, const double* lam, double* H, cudaStream_t st) {
     if (tc) {
       CK(tc_tangent(Ly.plan_tan, Ly.s1, Ly.c_f, Anext_hi, Anext_lo, Ly.mp,
                     zoff(net->Zt[0], Ly.zy_off), zoff(net->Zt[1], Ly.zy_off),
-                    zoff(net->Yt[0], Ly.zy_off), zoff(net->Yt[1], Ly.zy_off), net->K_total,
+                    deferred ? nullptr : zoff(net->Yt[0], Ly.zy_off),
+                    deferred ? nullptr : zoff(net->Yt[1], Ly.zy_off), net->K_total,
                     net->dev_err, st, Ly.w8s, net->tsc));
     } else {
       CK(launch_simt_tangent(prec == NNC_FP64,
@@ -324,6 +328,12 @@ int run_hessian(nnc_net* net, const double* lam, double* H, cudaStream_t st) {
   if (net->K_total == 0) {  // every layer is linear: H = 0
     CK(cudaMemsetAsync(H, 0, sizeof(double) * n * n, st));
     return NNC_OK;
+  }
+  if (deferred) {
+    CK(cudaStreamWaitEvent(st, net->ev_join, 0));   // c_l of every layer is written
+    PROF(PK_OTHER);
+    CK(launch_scale_y(prec == NNC_BF16X3, net->Zt[0], net->Zt[1], net->Yt[0], net->Yt[1], net->cK,
+                      n, net->K_total, 0, net->softmax ? net->ext_off : net->K_total, st));
   }
   {
     PROF(PK_SYRK);
@@ -357,12 +367,25 @@ int eval_all(nnc_net* net, const double* x, const double* lam, double* y, double
                        cudaMemcpyDeviceToDevice, st));
   if (rr) CK(launch_sub(yv, net->layers.back().a, rr, net->n_out, st));
   const bool need_lam = (H != nullptr) || (g != nullptr);
+  // tensor-core forms with the streaming reverse: the reverse sweep on the side stream, next to
+  // the tangent chain
+  const bool fork = H && is_tc(net->prec) && net->rev_stream && net->side_stream;
+  if (fork) {
+    CK(cudaEventRecord(net->ev_fork, st));
+    CK(cudaStreamWaitEvent(net->side_stream, net->ev_fork, 0));
+    r = run_reverse(net, fp64, J ? net->n_out : 0, true, lam, J, g, net->side_stream);
+    if (r != NNC_OK) return r;
+    CK(cudaEventRecord(net->ev_join, net->side_stream));
+    r = run_hessian(net, lam, H, st, true);
+    CK(cudaStreamWaitEvent(st, net->ev_join, 0));   // J and the gradient too, on every path
+    return r;
+  }
   if (J || need_lam) {
     r = run_reverse(net, fp64, J ? net->n_out : 0, need_lam, lam, J, g, st);
     if (r != NNC_OK) return r;
   }
   if (H) {
-    r = run_hessian(net, lam, H, st);
+    r = run_hessian(net, lam, H, st, false);
     if (r != NNC_OK) return r;
   }
   return NNC_OK;
@@ -474,6 +497,12 @@ void nnc_free(nnc_net* net) {
   for (void* p : net->allocs) cudaFree(p);
   for (cudaEvent_t e : net->ev_pool) cudaEventDestroy(e);
   if (net->h_stage) cudaFreeHost(net->h_stage);
+  if (net->side_stream) {
+    cudaStreamSynchronize(net->side_stream);
+    cudaStreamDestroy(net->side_stream);
+  }
+  if (net->ev_fork) cudaEventDestroy(net->ev_fork);
+  if (net->ev_join) cudaEventDestroy(net->ev_join);
   if (net->own_stream && net->stream) cudaStreamDestroy(net->stream);
   delete net;
 }
@@ -550,7 +579,7 @@ static int load_impl(nnc_net* net, int n_layers, const int* widths, const int* a
       AL(r2, Ly.mp);
       Ly.ra2 = r2;
     }
-    if (tc) AL(Ly.c_f, Ly.mp);
+    if (tc && Ly.act == NNC_IDENTITY) AL(Ly.c_f, Ly.mp);   // curvature layers: views of cK
     const int chunks = rev_chunks(Ly.m, Ly.kp, net->sm_count);
     part_max = std::max(part_max, (size_t)chunks * Ly.kp * net->S_max);
     if (prec != NNC_FP64 && net->S_max <= 16) {
@@ -605,6 +634,17 @@ static int load_impl(nnc_net* net, int n_layers, const int* widths, const int* a
   if (net->softmax) {
     net->ext_off = net->K_total;
     net->K_total += kPad;
+  }
+  if (tc) {
+    AL(net->cK, std::max(net->K_total, kPad));
+    for (auto& Ly : net->layers)
+      if (Ly.zy_off >= 0) Ly.c_f = net->cK + Ly.zy_off;
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (cudaStreamCreateWithPriority(&net->side_stream, cudaStreamNonBlocking, lo) != cudaSuccess ||
+        cudaEventCreateWithFlags(&net->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&net->ev_join, cudaEventDisableTiming) != cudaSuccess)
+      return fail(NNC_ERR_CUDA, "side stream or events could not be created");
   }
   const size_t tan_elems = (size_t)n * mp_max;
   const size_t zy_elems = (size_t)n * std::max(net->K_total, kPad);

@@ -45,7 +45,7 @@ int tc_plan_make(TcPlan& p, int kind, int prec, const void* a_hi, const void* a_
                  const void* a_p2 = nullptr, const void* b_p2 = nullptr);
 
 // at_* (row stride ldo) may be NULL on the last layer; zt_* / yt_* (row stride ldz) may be NULL
-// for a layer without curvature.
+// for a layer without curvature, yt_* alone when c_l * Zdot_l is formed later (launch_scale_y).
 // FP8 plans: A = W8 (e4m3, per-row scales wscale), B = tangents in e4m3 with per-row scales
 // tscale; the outputs are BF16.
 cudaError_t tc_tangent(const TcPlan& p, const double* s1, const float* c, void* at_hi, void* at_lo,
