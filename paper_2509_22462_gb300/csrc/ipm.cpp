@@ -823,6 +823,14 @@ struct IpmProblem {
   virtual int jac(const double* v, double* AD, double* AS) = 0;             // m x nd, m x ns
   // W_DD (nd x nd, full) and diag(W_SS) (ns) of grad^2 f + sum_i lam_i grad^2 c_i
   virtual int hess(const double* v, const double* lam, double* WDD, double* WSS) = 0;
+  // Jacobian and Hessian at one point from one network evaluation (problems that can); the driver
+  // then takes both at the top of an iteration.
+  virtual bool joint() const { return false; }
+  virtual int jac_hess(const double* v, const double* lam, double* AD, double* AS, double* WDD,
+                       double* WSS) {
+    const int rc = jac(v, AD, AS);
+    return rc ? rc : hess(v, lam, WDD, WSS);
+  }
 };
 
 struct Timers {
@@ -949,7 +957,13 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
     if (!have_c && m) {
       if (timed(T.fn, T.n_fn, [&] { return p.cons(v.data(), c.data()); })) { status = NNC_IPM_EVAL_ERROR; break; }
     }
-    if (m && timed(T.jac, T.n_jac, [&] { return p.jac(v.data(), AD.data(), AS.data()); })) { status = NNC_IPM_EVAL_ERROR; break; }
+    if (m && p.joint()) {
+      // J and the Hessian of the Lagrangian at (v, lam) in one evaluation (counted as both)
+      ++T.n_jac;
+      if (timed(T.hess, T.n_hess, [&] {
+            return p.jac_hess(v.data(), lam.data(), AD.data(), AS.data(), WDD.data(), WSS.data());
+          })) { status = NNC_IPM_EVAL_ERROR; break; }
+    } else if (m && timed(T.jac, T.n_jac, [&] { return p.jac(v.data(), AD.data(), AS.data()); })) { status = NNC_IPM_EVAL_ERROR; break; }
     bool finite = std::isfinite(fv);
     for (double x : g) finite &= std::isfinite(x);
     for (double x : c) finite &= std::isfinite(x);
@@ -967,7 +981,8 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
       tau = std::max(o.tau_min, 1.0 - mu);
       Emu = errors(mu);
     }
-    if (timed(T.hess, T.n_hess, [&] { return p.hess(v.data(), lam.data(), WDD.data(), WSS.data()); })) { status = NNC_IPM_EVAL_ERROR; break; }
+    if (!(m && p.joint()) &&
+        timed(T.hess, T.n_hess, [&] { return p.hess(v.data(), lam.data(), WDD.data(), WSS.data()); })) { status = NNC_IPM_EVAL_ERROR; break; }
     const auto t_lin = Clock::now();
     for (int i = 0; i < n; ++i) {
       sL[i] = slackL(v, i);
@@ -1156,6 +1171,22 @@ struct Adversarial : IpmProblem {
   int jac(const double* v, double* AD, double* AS) override {
     int rc = nnc_jacobian(net, v, J.data());
     if (rc) return rc;
+    fill_jac(AD, AS);
+    return NNC_OK;
+  }
+  int hess(const double* v, const double* lam, double* WDD, double* WSS) override {
+    // grad^2 f = 2 I on x; sum_i lam_i grad^2 c_i = -sum_{i < n_out} lam_i grad^2 NN_i (Eq. 6)
+    int rc = nnc_hessian_lag(net, v, lam, H.data(), nullptr);
+    if (rc) return rc;
+    fill_wdd(WDD, WSS);
+    return NNC_OK;
+  }
+  void fill_wdd(double* WDD, double* WSS) {
+    for (size_t i = 0; i < (size_t)nd * nd; ++i) WDD[i] = -H[i];
+    for (int i = 0; i < nd; ++i) WDD[(size_t)i * nd + i] += 2.0;
+    std::fill(WSS, WSS + ns, 0.0);
+  }
+  void fill_jac(double* AD, double* AS) {
     par_zero(AD, (size_t)m * nd);
     par_zero(AS, (size_t)m * ns);
     for (int j = 0; j < n_out; ++j) {
@@ -1167,15 +1198,14 @@ struct Adversarial : IpmProblem {
       AS[(size_t)(n_out + k) * ns + others[k]] = -1.0;
       AS[(size_t)(n_out + k) * ns + n_out + k] = -1.0;
     }
-    return NNC_OK;
   }
-  int hess(const double* v, const double* lam, double* WDD, double* WSS) override {
-    // grad^2 f = 2 I on x; sum_i lam_i grad^2 c_i = -sum_{i < n_out} lam_i grad^2 NN_i (Eq. 6)
-    int rc = nnc_hessian_lag(net, v, lam, H.data(), nullptr);
+  bool joint() const override { return true; }
+  int jac_hess(const double* v, const double* lam, double* AD, double* AS, double* WDD,
+               double* WSS) override {
+    int rc = nnc_eval_kkt(net, v, nullptr, lam, nullptr, J.data(), H.data(), nullptr);
     if (rc) return rc;
-    for (size_t i = 0; i < (size_t)nd * nd; ++i) WDD[i] = -H[i];
-    for (int i = 0; i < nd; ++i) WDD[(size_t)i * nd + i] += 2.0;
-    std::fill(WSS, WSS + ns, 0.0);
+    fill_jac(AD, AS);
+    fill_wdd(WDD, WSS);
     return NNC_OK;
   }
 };
@@ -1230,9 +1260,7 @@ struct AdversarialL1 : IpmProblem {
     for (int j = 0; j < n_out; ++j) c[n_in + j] = r[j];
     return NNC_OK;
   }
-  int jac(const double* v, double* AD, double* AS) override {
-    int rc = nnc_jacobian(net, v, J.data());
-    if (rc) return rc;
+  void fill_jac(double* AD, double* AS) {
     par_zero(AD, (size_t)m * nd);
     par_zero(AS, (size_t)m * ns);
     for (int i = 0; i < n_in; ++i) {
@@ -1244,14 +1272,31 @@ struct AdversarialL1 : IpmProblem {
       for (int i = 0; i < n_in; ++i) AD[(size_t)(n_in + j) * nd + i] = -J[(size_t)j * n_in + i];
       AS[(size_t)(n_in + j) * ns + 2 * n_in + j] = 1.0;   // y_j
     }
+  }
+  void fill_wdd(double* WDD, double* WSS) {
+    for (size_t i = 0; i < (size_t)nd * nd; ++i) WDD[i] = -H[i];
+    std::fill(WSS, WSS + ns, 0.0);
+  }
+  int jac(const double* v, double* AD, double* AS) override {
+    int rc = nnc_jacobian(net, v, J.data());
+    if (rc) return rc;
+    fill_jac(AD, AS);
     return NNC_OK;
   }
   int hess(const double* v, const double* lam, double* WDD, double* WSS) override {
     // the objective is linear; sum_i lam_i grad^2 c_i = -sum_j lam_{n+j} grad^2 NN_j (Eq. 6)
     int rc = nnc_hessian_lag(net, v, lam + n_in, H.data(), nullptr);
     if (rc) return rc;
-    for (size_t i = 0; i < (size_t)nd * nd; ++i) WDD[i] = -H[i];
-    std::fill(WSS, WSS + ns, 0.0);
+    fill_wdd(WDD, WSS);
+    return NNC_OK;
+  }
+  bool joint() const override { return true; }
+  int jac_hess(const double* v, const double* lam, double* AD, double* AS, double* WDD,
+               double* WSS) override {
+    int rc = nnc_eval_kkt(net, v, nullptr, lam + n_in, nullptr, J.data(), H.data(), nullptr);
+    if (rc) return rc;
+    fill_jac(AD, AS);
+    fill_wdd(WDD, WSS);
     return NNC_OK;
   }
 };
