@@ -367,9 +367,9 @@ int eval_all(nnc_net* net, const double* x, const double* lam, double* y, double
                        cudaMemcpyDeviceToDevice, st));
   if (rr) CK(launch_sub(yv, net->layers.back().a, rr, net->n_out, st));
   const bool need_lam = (H != nullptr) || (g != nullptr);
-  // tensor-core forms with the streaming reverse: the reverse sweep on the side stream, next to
-  // the tangent chain
-  const bool fork = H && is_tc(net->prec) && net->rev_stream && net->side_stream;
+  // tensor-core forms: the reverse sweep (streaming, or on the tensor cores for more than 15
+  // outputs) on the side stream, next to the tangent chain
+  const bool fork = H && is_tc(net->prec) && (net->rev_stream || net->tc_rev) && net->side_stream;
   if (fork) {
     CK(cudaEventRecord(net->ev_fork, st));
     CK(cudaStreamWaitEvent(net->side_stream, net->ev_fork, 0));
