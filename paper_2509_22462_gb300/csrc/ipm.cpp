@@ -16,6 +16,8 @@
 // host cores), Schur complement S = K22 - K12^T K11^-1 K12, Bunch-Kaufman LDL^T of S.  If K11 is
 // positive definite, inertia(K) = (n_D, 0, 0) + inertia(S) (Haynsworth); otherwise the whole K
 // is factorized by Bunch-Kaufman.  Either way the inertia is exact.
+#include <cuda_runtime.h>
+
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -34,6 +36,32 @@ using Clock = std::chrono::steady_clock;
 double secs(Clock::time_point a, Clock::time_point b) {
   return std::chrono::duration<double>(b - a).count();
 }
+
+// Page-locked host array (device-to-host copies of the Hessian at link speed); plain heap memory
+// if page-locked memory cannot be had.
+struct PinnedVec {
+  double* p = nullptr;
+  bool pinned = false;
+  PinnedVec() = default;
+  PinnedVec(const PinnedVec&) = delete;
+  PinnedVec& operator=(const PinnedVec&) = delete;
+  ~PinnedVec() { release(); }
+  void release() {
+    if (p && pinned) cudaFreeHost(p);
+    else delete[] p;
+    p = nullptr;
+  }
+  void resize(size_t n) {
+    release();
+    pinned = cudaMallocHost((void**)&p, n * sizeof(double)) == cudaSuccess;
+    if (!pinned) {
+      cudaGetLastError();
+      p = new double[n];
+    }
+  }
+  double* data() { return p; }
+  double& operator[](size_t i) { return p[i]; }
+};
 
 // ---------------------------------------------------------------- dense helpers (OpenMP)
 double max_abs(const double* x, size_t n) {
@@ -54,8 +82,9 @@ void par_zero(double* x, size_t n) {
 }
 
 // ---------------------------------------------------------------- dense linear algebra
-// Row-major n x n, lower triangle.  Returns false if the matrix is not positive definite.
-bool cholesky(int n, double* A) {
+// Row-major n x n, lower triangle.  Returns false if the matrix is not positive definite, or if a
+// pivot (before its square root) is not above min_pivot.
+bool cholesky(int n, double* A, double min_pivot = 0.0) {
   const int NB = 64;
   std::vector<double> Pt;   // L21^T of the current block column, rows padded to a multiple of 4
   for (int kb = 0; kb < n; kb += NB) {
@@ -63,7 +92,7 @@ bool cholesky(int n, double* A) {
     // diagonal block (unblocked, right-looking)
     for (int j = kb; j < kb + nb; ++j) {
       double d = A[(size_t)j * n + j];
-      if (!(d > 0.0) || !std::isfinite(d)) return false;
+      if (!(d > min_pivot) || !std::isfinite(d)) return false;
       d = std::sqrt(d);
       A[(size_t)j * n + j] = d;
       for (int i = j + 1; i < kb + nb; ++i) A[(size_t)i * n + j] /= d;
@@ -154,22 +183,48 @@ void lower_solve(int n, const double* L, int r, double* B) {
   }
 }
 
-// L^T x = y in place for one right-hand side.
+// L^T x = y in place for one right-hand side.  Blocked by 64 rows from the end: the diagonal
+// block is solved row by row, then the entries above it subtract its contribution in parallel.
 void upper_solve_lt(int n, const double* L, double* x) {
-  for (int i = n - 1; i >= 0; --i) {
-    x[i] /= L[(size_t)i * n + i];
-    const double xi = x[i];
-    const double* li = L + (size_t)i * n;
-    for (int j = 0; j < i; ++j) x[j] -= li[j] * xi;
+  const int NB = 64;
+  for (int k1 = n; k1 > 0; k1 -= NB) {
+    const int k0 = std::max(0, k1 - NB);
+    for (int i = k1 - 1; i >= k0; --i) {
+      x[i] /= L[(size_t)i * n + i];
+      const double xi = x[i];
+      const double* li = L + (size_t)i * n;
+      for (int j = k0; j < i; ++j) x[j] -= li[j] * xi;
+    }
+#pragma omp parallel for schedule(static) if (k0 >= 512)
+    for (int j0 = 0; j0 < k0; j0 += 64) {
+      const int j1 = std::min(k0, j0 + 64);
+      for (int i = k0; i < k1; ++i) {
+        const double xi = x[i];
+        const double* li = L + (size_t)i * n;
+        for (int j = j0; j < j1; ++j) x[j] -= li[j] * xi;
+      }
+    }
   }
 }
 
+// L x = b in place for one right-hand side, blocked like upper_solve_lt.
 void lower_solve1(int n, const double* L, double* x) {
-  for (int i = 0; i < n; ++i) {
-    const double* li = L + (size_t)i * n;
-    double s = x[i];
-    for (int j = 0; j < i; ++j) s -= li[j] * x[j];
-    x[i] = s / li[i];
+  const int NB = 64;
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int k1 = std::min(n, k0 + NB);
+    for (int i = k0; i < k1; ++i) {
+      const double* li = L + (size_t)i * n;
+      double s = x[i];
+      for (int j = k0; j < i; ++j) s -= li[j] * x[j];
+      x[i] = s / li[i];
+    }
+#pragma omp parallel for schedule(static) if (n - k1 >= 512)
+    for (int i = k1; i < n; ++i) {
+      const double* li = L + (size_t)i * n;
+      double s = 0.0;
+      for (int j = k0; j < k1; ++j) s += li[j] * x[j];
+      x[i] -= s;
+    }
   }
 }
 
@@ -416,7 +471,10 @@ struct KktSolver {
       factor_core(nd_, ns_, m_, WDD, WSS, sig, AD, AS, dw, dc, zero_tol);
       return;
     }
-    WDDp.assign(WDD, WDD + (size_t)nd_ * nd_);
+    WDDp.resize((size_t)nd_ * nd_);
+#pragma omp parallel for schedule(static) if (nd_ >= 256)
+    for (int i = 0; i < nd_; ++i)
+      std::memcpy(&WDDp[(size_t)i * nd_], &WDD[(size_t)i * nd_], sizeof(double) * nd_);
     for (size_t k = 0; k < prow.size(); ++k)
       if (pcol[k] >= 0) WDDp[(size_t)pcol[k] * nd_ + pcol[k]] += palpha[k] * palpha[k] / pe[k];
     const int mo = (int)orow.size();
@@ -463,9 +521,12 @@ struct KktSolver {
     m = m_;
     n = nd + ns;
     r = ns + m;
-    K11.assign((size_t)nd * nd, 0.0);
-    std::memcpy(K11.data(), WDD, sizeof(double) * nd * nd);
-    for (int i = 0; i < nd; ++i) K11[(size_t)i * nd + i] += sig[i] + dw;
+    K11.resize((size_t)nd * nd);
+#pragma omp parallel for schedule(static) if (nd >= 256)
+    for (int i = 0; i < nd; ++i) {
+      std::memcpy(&K11[(size_t)i * nd], &WDD[(size_t)i * nd], sizeof(double) * nd);
+      K11[(size_t)i * nd + i] += sig[i] + dw;
+    }
     const bool pd = nd == 0 || cholesky(nd, K11.data());
     bool diag_ok = pd && ns > 0;
     zid.clear();
@@ -547,7 +608,8 @@ struct KktSolver {
         }
       }
       std::vector<double> Tc(T);
-      t_chol = m == 0 || cholesky(m, Tc.data());
+      // a pivot within the zero tolerance is left to Bunch-Kaufman, which reports it as zero
+      t_chol = m == 0 || cholesky(m, Tc.data(), zero_tol);
       if (t_chol) {
         T.swap(Tc);
         npos = n;
@@ -1119,7 +1181,8 @@ struct Adversarial : IpmProblem {
   nnc_net* net;
   int n_in, n_out, t;
   double margin;
-  std::vector<double> x0, J, H, r;
+  std::vector<double> x0, J, r;
+  PinnedVec H;
   std::vector<int> others;
   Adversarial(nnc_net* net_, const double* x0_, int n_in_, int n_out_, int t_, double margin_)
       : net(net_), n_in(n_in_), n_out(n_out_), t(t_), margin(margin_), x0(x0_, x0_ + n_in_) {
@@ -1182,8 +1245,11 @@ struct Adversarial : IpmProblem {
     return NNC_OK;
   }
   void fill_wdd(double* WDD, double* WSS) {
-    for (size_t i = 0; i < (size_t)nd * nd; ++i) WDD[i] = -H[i];
-    for (int i = 0; i < nd; ++i) WDD[(size_t)i * nd + i] += 2.0;
+#pragma omp parallel for schedule(static) if (nd >= 256)
+    for (int i = 0; i < nd; ++i) {
+      for (int j = 0; j < nd; ++j) WDD[(size_t)i * nd + j] = -H[(size_t)i * nd + j];
+      WDD[(size_t)i * nd + i] += 2.0;
+    }
     std::fill(WSS, WSS + ns, 0.0);
   }
   void fill_jac(double* AD, double* AS) {
@@ -1221,7 +1287,8 @@ struct AdversarialL1 : IpmProblem {
   nnc_net* net;
   int n_in, n_out, t;
   double conf;
-  std::vector<double> xr, J, H, r;
+  std::vector<double> xr, J, r;
+  PinnedVec H;
   AdversarialL1(nnc_net* net_, const double* x_ref, int n_in_, int n_out_, int t_, double conf_)
       : net(net_), n_in(n_in_), n_out(n_out_), t(t_), conf(conf_), xr(x_ref, x_ref + n_in_) {
     nd = n_in;
@@ -1274,7 +1341,9 @@ struct AdversarialL1 : IpmProblem {
     }
   }
   void fill_wdd(double* WDD, double* WSS) {
-    for (size_t i = 0; i < (size_t)nd * nd; ++i) WDD[i] = -H[i];
+#pragma omp parallel for schedule(static) if (nd >= 256)
+    for (int i = 0; i < nd; ++i)
+      for (int j = 0; j < nd; ++j) WDD[(size_t)i * nd + j] = -H[(size_t)i * nd + j];
     std::fill(WSS, WSS + ns, 0.0);
   }
   int jac(const double* v, double* AD, double* AS) override {
