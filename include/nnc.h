@@ -211,6 +211,11 @@ const char* nnc_last_error(void);
 
 /* Query helpers (no device work). */
 int nnc_net_info(const nnc_net* net, int* n_layers, int* n_in, int* n_out, int* prec);
+/* Layer l (0-based) of the loaded net: its FP64 weights W (rows x cols, row-major, host, may be
+ * NULL), bias b (rows, host, may be NULL; zeros if none was given), activation code, and shape
+ * (rows = width of layer l+1, cols = width of layer l).  Synchronises the net's stream. */
+int nnc_layer_weights(const nnc_net* net, int layer, double* W, double* b, int* act, int* rows,
+                      int* cols);
 /* Number of kernel launches this library queued since load (all nets, this process). */
 long long nnc_launch_count(void);
 

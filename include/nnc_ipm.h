@@ -97,6 +97,19 @@ int nnc_ipm_adversarial_l1(nnc_net* net, const double* x_ref, int target, double
                            const nnc_ipm_options* opt, double* v_out, double* lam_out,
                            nnc_ipm_result* result);
 
+/* Eq. 7 with the network in the full space (Eq. 4): every layer's affine output z_l and
+ * activation output y_l are variables, tied by z_l - W_l y_{l-1} - b_l = 0 and
+ * y_l - sigma_l(z_l) = 0 (y_0 = x, y_L = y); objective, bounds and split variables as in
+ * nnc_ipm_adversarial_l1, so both forms have the same optima.  Functions are evaluated on the host
+ * from the net's FP64 weights and the KKT matrix is factorized densely: small nets only
+ * (NNC_ERR_UNSUPPORTED when variables + constraints exceed 6000).
+ *   v_out   : (x, p, q, z_1, y_1, ..., z_L, y_L): 3 n_in + 2 sum_l n_l doubles (may be NULL);
+ *   lam_out : (link rows, then per layer the affine and the activation rows):
+ *             n_in + 2 sum_l n_l doubles (may be NULL);  result : may be NULL. */
+int nnc_ipm_adversarial_l1_fullspace(nnc_net* net, const double* x_ref, int target, double conf,
+                                     const nnc_ipm_options* opt, double* v_out, double* lam_out,
+                                     nnc_ipm_result* res);
+
 /* The adversarial problem (a synthetic variant of Eq. 7): variables v = (x, y, s) with
  * x in [0,1]^n_in, y in R^n_out, s in R^(n_out-1), s >= 0;
  *   min ||x - x0||^2  s.t.  y - NN(x) = 0,  y_t - y_j - margin - s_j = 0 for j != t.

@@ -3,7 +3,9 @@
 TEST INFRASTRUCTURE ONLY.
 
 Adversarial problems.  `adversarial_l1` is Eq. 7 itself (L1 objective through split variables,
-softmax confidence threshold); `adversarial` is a smooth variant (L2 objective, logit margins):
+softmax confidence threshold) with the network in the reduced space (Eq. 5);
+`adversarial_l1_fullspace` the same problem with the network in the full space (Eq. 4);
+`adversarial` is a smooth variant (L2 objective, logit margins):
     variables v = (x in [0,1]^n_in, y in R^n_out, s in R^(n_out-1), s >= 0)
     min ||x - x0||^2
     s.t. y - NN(x) = 0                                   (the reduced-space constraint, Eq. 5)
@@ -118,6 +120,102 @@ def adversarial_l1(mlp, x_ref, target, conf=0.6):
 
     pr = Problem(nv, m, lb, ub, v0, f, grad_f, hess_f, c, jac_c, hess_c)
     pr.blocks = dict(n_in=n, n_out=n_out, target=target, conf=conf)
+    return pr
+
+
+def adversarial_l1_fullspace(mlp, x_ref, target, conf=0.6):
+    """Eq. 7 with the network in the full-space form of Eq. 4: every layer's affine output z_l and
+    activation output y_l are variables, tied by z_l - W_l y_{l-1} - b_l = 0 and
+    y_l - sigma_l(z_l) = 0 (y_0 = x, y_L = y).  Same objective, bounds and split variables as
+    `adversarial_l1`, so both forms have the same optima:
+        v = (x, p, q, z_1, y_1, ..., z_L, y_L),  min sum(p) + sum(q)
+        s.t. x - p + q - x_ref = 0,  z_l - W_l y_{l-1} - b_l = 0,  y_l - sigma_l(z_l) = 0.
+    Start: x = x_ref, p = q = 0, (z_l, y_l) from the forward pass at x_ref."""
+    n, L = mlp.spec.n_in, mlp.spec.n_layers
+    widths, acts = mlp.spec.widths, mlp.spec.acts
+    # variable offsets
+    off_z, off_y = [], []
+    k = 3 * n
+    for l in range(L):
+        off_z.append(k)
+        k += widths[l + 1]
+        off_y.append(k)
+        k += widths[l + 1]
+    nv = k
+    m = n + 2 * sum(widths[1:])
+    lb = np.full(nv, -np.inf)
+    ub = np.full(nv, np.inf)
+    lb[:3 * n] = 0.0
+    ub[:n] = 1.0
+    lb[off_y[-1] + target] = conf
+    x_ref = np.asarray(x_ref, dtype=np.float64)
+    zs, as_ = onn.forward(mlp, x_ref)
+    v0 = np.zeros(nv)
+    v0[:n] = x_ref
+    for l in range(L):
+        v0[off_z[l]:off_z[l] + widths[l + 1]] = zs[l]
+        v0[off_y[l]:off_y[l] + widths[l + 1]] = as_[l + 1]
+
+    def seg(v, off, l):
+        return v[off[l]:off[l] + widths[l + 1]]
+
+    def prev(v, l):
+        return v[:n] if l == 0 else seg(v, off_y, l - 1)
+
+    def f(v):
+        return float(np.sum(v[n:3 * n]))
+
+    def grad_f(v):
+        g = np.zeros(nv)
+        g[n:3 * n] = 1.0
+        return g
+
+    def hess_f(v):
+        return np.zeros((nv, nv))
+
+    def c(v):
+        out = [v[:n] - v[n:2 * n] + v[2 * n:3 * n] - x_ref]
+        for l in range(L):
+            z = seg(v, off_z, l)
+            out.append(z - mlp.W[l] @ prev(v, l) - mlp.b[l])
+            out.append(seg(v, off_y, l) - onn.act_value(acts[l], z))
+        return np.concatenate(out)
+
+    def jac_c(v):
+        A = np.zeros((m, nv))
+        A[:n, :n] = np.eye(n)
+        A[:n, n:2 * n] = -np.eye(n)
+        A[:n, 2 * n:3 * n] = np.eye(n)
+        r = n
+        for l in range(L):
+            w = widths[l + 1]
+            z = seg(v, off_z, l)
+            A[r:r + w, off_z[l]:off_z[l] + w] = np.eye(w)
+            cols = slice(0, n) if l == 0 else slice(off_y[l - 1], off_y[l - 1] + widths[l])
+            A[r:r + w, cols] = -mlp.W[l]
+            r += w
+            A[r:r + w, off_y[l]:off_y[l] + w] = np.eye(w)
+            A[r:r + w, off_z[l]:off_z[l] + w] = -onn.jac_apply(acts[l], z, np.eye(w))
+            r += w
+        return A
+
+    def hess_c(v, lam):
+        # only y_l - sigma_l(z_l) is nonlinear: its multipliers mu_l give -grad^2 (mu_l^T sigma_l)
+        Hh = np.zeros((nv, nv))
+        r = n
+        for l in range(L):
+            w = widths[l + 1]
+            r += w
+            mu = lam[r:r + w]
+            z = seg(v, off_z, l)
+            C = onn.curvature(acts[l], z, mu)
+            zz = slice(off_z[l], off_z[l] + w)
+            Hh[zz, zz] = -(C if C.ndim == 2 else np.diag(C))
+            r += w
+        return Hh
+
+    pr = Problem(nv, m, lb, ub, v0, f, grad_f, hess_f, c, jac_c, hess_c)
+    pr.blocks = dict(n_in=n, n_out=widths[-1], target=target, conf=conf, off_z=off_z, off_y=off_y)
     return pr
 
 

@@ -1370,6 +1370,273 @@ struct AdversarialL1 : IpmProblem {
   }
 };
 
+// ---------------------------------------------------------------- Eq. 7 in the full space (Eq. 4)
+// The network as per-layer variables and constraints: z_l - W_l y_{l-1} - b_l = 0 and
+// y_l - sigma_l(z_l) = 0 (y_0 = x, y_L = y), with the objective, bounds and split variables of
+// AdversarialL1.  Natural variable order v = (x, p, q, z_1, y_1, ..., z_L, y_L); constraints
+// (link, then per layer the affine rows and the activation rows).  The Hessian of the Lagrangian
+// is diagonal except for a softmax output (an n_out x n_out block on z_L), so z_L of a softmax
+// net forms the dense block and every other variable the diagonal block.  Functions are affine
+// maps and elementwise activations evaluated on the host (the paper evaluates its full-space
+// model on the CPU too); the KKT matrix is factorized densely, so this form is for small nets.
+namespace {
+void host_act(int act, double z, double& a, double& d1, double& d2) {
+  switch (act) {
+    case NNC_TANH: {
+      const double t = std::tanh(z);
+      a = t;
+      d1 = 1.0 - t * t;
+      d2 = -2.0 * t * d1;
+      return;
+    }
+    case NNC_SIGMOID: {
+      const double e = std::exp(-std::fabs(z));
+      const double sg = z >= 0 ? 1.0 / (1.0 + e) : e / (1.0 + e);
+      a = sg;
+      d1 = sg * (1.0 - sg);
+      d2 = d1 * (1.0 - 2.0 * sg);
+      return;
+    }
+    case NNC_SOFTPLUS: {
+      const double e = std::exp(-std::fabs(z));
+      a = (z > 0 ? z : 0.0) + std::log1p(e);
+      const double sg = z >= 0 ? 1.0 / (1.0 + e) : e / (1.0 + e);
+      d1 = sg;
+      d2 = sg * (1.0 - sg);
+      return;
+    }
+    case NNC_GELU: {
+      const double phi = std::exp(-0.5 * z * z) / std::sqrt(2.0 * M_PI);
+      const double Phi = 0.5 * (1.0 + std::erf(z / std::sqrt(2.0)));
+      a = z * Phi;
+      d1 = Phi + z * phi;
+      d2 = phi * (2.0 - z * z);
+      return;
+    }
+    default:
+      a = z;
+      d1 = 1.0;
+      d2 = 0.0;
+  }
+}
+void host_softmax(const double* z, int k, double* p) {
+  double mx = z[0];
+  for (int i = 1; i < k; ++i) mx = std::max(mx, z[i]);
+  double s = 0;
+  for (int i = 0; i < k; ++i) s += (p[i] = std::exp(z[i] - mx));
+  for (int i = 0; i < k; ++i) p[i] /= s;
+}
+}  // namespace
+
+struct AdversarialL1Full : IpmProblem {
+  int n = 0, L = 0, t = 0, nv = 0, dense = 0;
+  double conf = 0.6;
+  std::vector<int> w, act, off_z, off_y, perm, inv;   // perm: internal -> natural; inv: inverse
+  std::vector<std::vector<double>> W, b;
+  std::vector<double> xr, vn, tmp;
+  int load(nnc_net* net, const double* x_ref, int target, double conf_) {
+    int nl = 0, ni = 0, no = 0, prec = 0;
+    int rc = nnc_net_info(net, &nl, &ni, &no, &prec);
+    if (rc) return rc;
+    L = nl;
+    n = ni;
+    t = target;
+    conf = conf_;
+    w.assign(1, n);
+    act.resize(L);
+    W.resize(L);
+    b.resize(L);
+    for (int l = 0; l < L; ++l) {
+      int rows = 0, cols = 0;
+      rc = nnc_layer_weights(net, l, nullptr, nullptr, &act[l], &rows, &cols);
+      if (rc) return rc;
+      W[l].resize((size_t)rows * cols);
+      b[l].resize(rows);
+      rc = nnc_layer_weights(net, l, W[l].data(), b[l].data(), nullptr, nullptr, nullptr);
+      if (rc) return rc;
+      w.push_back(rows);
+    }
+    for (int l = 0; l + 1 < L; ++l)
+      if (act[l] == NNC_SOFTMAX) return NNC_ERR_UNSUPPORTED;
+    int k = 3 * n;
+    m = n;
+    for (int l = 0; l < L; ++l) {
+      off_z.push_back(k);
+      k += w[l + 1];
+      off_y.push_back(k);
+      k += w[l + 1];
+      m += 2 * w[l + 1];
+    }
+    nv = k;
+    if (nv + m > 6000) return NNC_ERR_UNSUPPORTED;   // dense KKT: small nets only
+    dense = act[L - 1] == NNC_SOFTMAX ? w[L] : 0;
+    nd = dense;
+    ns = nv - dense;
+    perm.clear();
+    for (int i = 0; i < dense; ++i) perm.push_back(off_z[L - 1] + i);
+    for (int i = 0; i < nv; ++i)
+      if (!(dense && i >= off_z[L - 1] && i < off_z[L - 1] + dense)) perm.push_back(i);
+    inv.assign(nv, 0);
+    for (int i = 0; i < nv; ++i) inv[perm[i]] = i;
+    std::vector<double> lbn(nv, -INFINITY), ubn(nv, INFINITY);
+    for (int i = 0; i < 3 * n; ++i) lbn[i] = 0.0;
+    for (int i = 0; i < n; ++i) ubn[i] = 1.0;
+    lbn[off_y[L - 1] + t] = conf;
+    lb.resize(nv);
+    ub.resize(nv);
+    for (int i = 0; i < nv; ++i) {
+      lb[i] = lbn[perm[i]];
+      ub[i] = ubn[perm[i]];
+    }
+    // start: x = x_ref, p = q = 0, (z_l, y_l) of the forward pass at x_ref
+    xr.assign(x_ref, x_ref + n);
+    vn.assign(nv, 0.0);
+    for (int i = 0; i < n; ++i) vn[i] = xr[i];
+    for (int l = 0; l < L; ++l) {
+      const double* yp = l == 0 ? vn.data() : &vn[off_y[l - 1]];
+      double* z = &vn[off_z[l]];
+      double* y = &vn[off_y[l]];
+      affine(l, yp, z);
+      activate(l, z, y);
+    }
+    v0.resize(nv);
+    to_internal(vn.data(), v0.data());
+    return NNC_OK;
+  }
+  void affine(int l, const double* yp, double* z) const {
+    const int rows = w[l + 1], cols = w[l];
+    for (int r = 0; r < rows; ++r) {
+      double s = b[l][r];
+      const double* wr = &W[l][(size_t)r * cols];
+      for (int c = 0; c < cols; ++c) s += wr[c] * yp[c];
+      z[r] = s;
+    }
+  }
+  void activate(int l, const double* z, double* y) const {
+    if (act[l] == NNC_SOFTMAX) {
+      host_softmax(z, w[l + 1], y);
+      return;
+    }
+    double d1, d2;
+    for (int r = 0; r < w[l + 1]; ++r) host_act(act[l], z[r], y[r], d1, d2);
+  }
+  void to_natural(const double* vi, double* vnat) const {
+    for (int i = 0; i < nv; ++i) vnat[perm[i]] = vi[i];
+  }
+  void to_internal(const double* vnat, double* vi) const {
+    for (int i = 0; i < nv; ++i) vi[i] = vnat[perm[i]];
+  }
+  double f(const double* v) override {
+    vn.resize(nv);
+    to_natural(v, vn.data());
+    double s = 0;
+    for (int i = n; i < 3 * n; ++i) s += vn[i];
+    return s;
+  }
+  void grad_f(const double* v, double* g) override {
+    for (int i = 0; i < nv; ++i) g[i] = (perm[i] >= n && perm[i] < 3 * n) ? 1.0 : 0.0;
+  }
+  int cons(const double* v, double* c) override {
+    vn.resize(nv);
+    to_natural(v, vn.data());
+    for (int i = 0; i < n; ++i) c[i] = vn[i] - vn[n + i] + vn[2 * n + i] - xr[i];
+    int r = n;
+    for (int l = 0; l < L; ++l) {
+      const int k = w[l + 1];
+      const double* yp = l == 0 ? vn.data() : &vn[off_y[l - 1]];
+      tmp.resize(k);
+      affine(l, yp, tmp.data());
+      for (int j = 0; j < k; ++j) c[r + j] = vn[off_z[l] + j] - tmp[j];
+      r += k;
+      activate(l, &vn[off_z[l]], tmp.data());
+      for (int j = 0; j < k; ++j) c[r + j] = vn[off_y[l] + j] - tmp[j];
+      r += k;
+    }
+    return NNC_OK;
+  }
+  int jac(const double* v, double* AD, double* AS) override {
+    vn.resize(nv);
+    to_natural(v, vn.data());
+    par_zero(AD, (size_t)m * nd);
+    par_zero(AS, (size_t)m * ns);
+    auto put = [&](int row, int col, double val) {
+      const int ic = inv[col];
+      if (ic < nd) AD[(size_t)row * nd + ic] = val;
+      else AS[(size_t)row * ns + ic - nd] = val;
+    };
+    for (int i = 0; i < n; ++i) {
+      put(i, i, 1.0);
+      put(i, n + i, -1.0);
+      put(i, 2 * n + i, 1.0);
+    }
+    int r = n;
+    for (int l = 0; l < L; ++l) {
+      const int k = w[l + 1], kin = w[l];
+      const int prev = l == 0 ? 0 : off_y[l - 1];
+      for (int j = 0; j < k; ++j) {
+        put(r + j, off_z[l] + j, 1.0);
+        for (int c = 0; c < kin; ++c) put(r + j, prev + c, -W[l][(size_t)j * kin + c]);
+      }
+      r += k;
+      const double* z = &vn[off_z[l]];
+      if (act[l] == NNC_SOFTMAX) {
+        tmp.resize(k);
+        host_softmax(z, k, tmp.data());
+        for (int j = 0; j < k; ++j) {
+          put(r + j, off_y[l] + j, 1.0);
+          for (int c = 0; c < k; ++c) put(r + j, off_z[l] + c, -(tmp[j] * ((j == c) - tmp[c])));
+        }
+      } else {
+        for (int j = 0; j < k; ++j) {
+          double a, d1, d2;
+          host_act(act[l], z[j], a, d1, d2);
+          put(r + j, off_y[l] + j, 1.0);
+          put(r + j, off_z[l] + j, -d1);
+        }
+      }
+      r += k;
+    }
+    return NNC_OK;
+  }
+  int hess(const double* v, const double* lam, double* WDD, double* WSS) override {
+    // only y_l - sigma_l(z_l) is nonlinear: its multipliers mu give -grad^2 (mu^T sigma_l(z_l))
+    vn.resize(nv);
+    to_natural(v, vn.data());
+    std::fill(WDD, WDD + (size_t)nd * nd, 0.0);
+    std::fill(WSS, WSS + ns, 0.0);
+    int r = n;
+    for (int l = 0; l < L; ++l) {
+      const int k = w[l + 1];
+      r += k;
+      const double* mu = lam + r;
+      const double* z = &vn[off_z[l]];
+      if (act[l] == NNC_SOFTMAX) {
+        // sum_i mu_i grad^2 p_i = diag(p (mu - mubar)) - p (p mu)^T - (p mu) p^T + 2 mubar p p^T
+        tmp.resize(k);
+        host_softmax(z, k, tmp.data());
+        double mb = 0;
+        for (int i = 0; i < k; ++i) mb += tmp[i] * mu[i];
+        for (int i = 0; i < k; ++i)
+          for (int j = 0; j < k; ++j) {
+            double cij = -tmp[i] * tmp[j] * mu[j] - tmp[i] * mu[i] * tmp[j] + 2.0 * mb * tmp[i] * tmp[j];
+            if (i == j) cij += tmp[i] * (mu[i] - mb);
+            WDD[(size_t)inv[off_z[l] + i] * nd + inv[off_z[l] + j]] = -cij;
+          }
+      } else {
+        for (int j = 0; j < k; ++j) {
+          double a, d1, d2;
+          host_act(act[l], z[j], a, d1, d2);
+          const int ic = inv[off_z[l] + j];
+          if (ic < nd) WDD[(size_t)ic * nd + ic] = -mu[j] * d2;
+          else WSS[ic - nd] = -mu[j] * d2;
+        }
+      }
+      r += k;
+    }
+    return NNC_OK;
+  }
+};
+
 // ---------------------------------------------------------------- SCOPF-shaped batch problem
 // Variables v = (x in [0,1]^G | y in R^K, y >= 0).
 // min sum_i c_i x_i^2  s.t.  y_k - (NN_k(x[S_k]) + shift_k) = 0,  sum_i x_i - D = 0.
@@ -1590,6 +1857,27 @@ int nnc_ipm_adversarial(nnc_net* net, const double* x0, int target, double margi
   rc = ipm_solve(p, o, v, lam, res);
   if (rc) return rc;
   if (v_out) std::copy(v.begin(), v.end(), v_out);
+  if (lam_out) std::copy(lam.begin(), lam.end(), lam_out);
+  return NNC_OK;
+}
+
+int nnc_ipm_adversarial_l1_fullspace(nnc_net* net, const double* x_ref, int target, double conf,
+                                     const nnc_ipm_options* opt, double* v_out, double* lam_out,
+                                     nnc_ipm_result* res) {
+  int L = 0, n_in = 0, n_out = 0, prec = 0;
+  int rc = nnc_net_info(net, &L, &n_in, &n_out, &prec);
+  if (rc) return rc;
+  if (!x_ref || target < 0 || target >= n_out || !(conf > 0.0 && conf < 1.0)) return NNC_ERR_ARG;
+  nnc_ipm_options o;
+  if (opt) o = *opt;
+  else nnc_ipm_default_options(&o);
+  AdversarialL1Full p;
+  rc = p.load(net, x_ref, target, conf);
+  if (rc) return rc;
+  std::vector<double> v, lam;
+  rc = ipm_solve(p, o, v, lam, res);
+  if (rc) return rc;
+  if (v_out) p.to_natural(v.data(), v_out);
   if (lam_out) std::copy(lam.begin(), lam.end(), lam_out);
   return NNC_OK;
 }

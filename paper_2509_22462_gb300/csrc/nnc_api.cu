@@ -489,6 +489,26 @@ int nnc_net_info(const nnc_net* net, int* n_layers, int* n_in, int* n_out, int* 
   return NNC_OK;
 }
 
+int nnc_layer_weights(const nnc_net* net, int layer, double* W, double* b, int* act, int* rows,
+                      int* cols) {
+  if (!net) return fail(NNC_ERR_ARG, "net is NULL");
+  if (layer < 0 || layer >= net->L) return fail(NNC_ERR_ARG, "layer out of range");
+  const LayerDev& Ly = net->layers[layer];
+  if (act) *act = Ly.act;
+  if (rows) *rows = Ly.m;
+  if (cols) *cols = Ly.k;
+  CK(cudaSetDevice(net->device));
+  CK(cudaStreamSynchronize(net->stream));
+  if (W)   // the padded rows of the FP64 master, unpadded on the host
+    CK(cudaMemcpy2D(W, sizeof(double) * Ly.k, Ly.W64, sizeof(double) * Ly.kp, sizeof(double) * Ly.k,
+                    Ly.m, cudaMemcpyDeviceToHost));
+  if (b) {
+    if (Ly.b) CK(cudaMemcpy(b, Ly.b, sizeof(double) * Ly.m, cudaMemcpyDeviceToHost));
+    else std::memset(b, 0, sizeof(double) * Ly.m);
+  }
+  return NNC_OK;
+}
+
 void nnc_free(nnc_net* net) {
   if (!net) return;
   batch_cache_forget(net);

@@ -25,7 +25,8 @@ EXPORTS = ["nnc_load_weights", "nnc_eval", "nnc_residual", "nnc_jacobian", "nnc_
            "nnc_eval_batched", "nnc_eval_dev", "nnc_residual_dev", "nnc_jacobian_dev",
            "nnc_hessian_lag_dev", "nnc_eval_all_dev", "nnc_eval_kkt_dev", "nnc_eval_kkt", "nnc_free", "nnc_last_error",
            "nnc_net_info", "nnc_launch_count", "nnc_profile", "nnc_profile_read",
-           "nnc_ipm_default_options", "nnc_ipm_adversarial", "nnc_ipm_adversarial_l1", "nnc_kkt_solve",
+           "nnc_ipm_default_options", "nnc_ipm_adversarial", "nnc_ipm_adversarial_l1",
+           "nnc_ipm_adversarial_l1_fullspace", "nnc_layer_weights", "nnc_kkt_solve",
            "nnc_residual_noalloc", "nnc_batch_create", "nnc_batch_free", "nnc_batch_info",
            "nnc_batch_set_bias", "nnc_batch_use_graph", "nnc_batch_eval_dev", "nnc_batch_residual_dev",
            "nnc_batch_eval", "nnc_batch_residual", "nnc_ipm_scopf", "nnc_ws_create", "nnc_ws_free",
@@ -151,6 +152,11 @@ def load_library(path: str = LIB_PATH):
     lib.nnc_ipm_adversarial_l1.argtypes = [_P, _DP, ctypes.c_int, ctypes.c_double,
                                            ctypes.POINTER(IpmOptions), _DP, _DP,
                                            ctypes.POINTER(IpmResult)]
+    lib.nnc_ipm_adversarial_l1_fullspace.argtypes = [_P, _DP, ctypes.c_int, ctypes.c_double,
+                                                     ctypes.POINTER(IpmOptions), _DP, _DP,
+                                                     ctypes.POINTER(IpmResult)]
+    lib.nnc_layer_weights.argtypes = [_P, ctypes.c_int, _DP, _DP, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.nnc_profile_read.argtypes = [_P, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
     for name in EXPORTS:
@@ -379,6 +385,33 @@ def ipm_adversarial_l1(net, x_ref, target, conf=0.6, **options):
     _check(lib.nnc_ipm_adversarial_l1(net.handle, _dp(x_ref), int(target), float(conf), ctypes.byref(o),
                                       _dp(v), _dp(lam), ctypes.byref(res)))
     return res.as_dict(), v, lam
+
+
+def ipm_adversarial_l1_fullspace(net, x_ref, target, conf=0.6, **options):
+    """Eq. 7 with the network in the full space (Eq. 4), host functions and a dense KKT (small
+    nets).  Returns (result dict, v = (x, p, q, z_1, y_1, ..., z_L, y_L), lambda)."""
+    lib = load_library()
+    x_ref = _f64(x_ref)
+    o = ipm_options(**options)
+    hidden = sum(net.widths[1:])
+    v = np.empty(3 * net.n_in + 2 * hidden)
+    lam = np.empty(net.n_in + 2 * hidden)
+    res = IpmResult()
+    _check(lib.nnc_ipm_adversarial_l1_fullspace(net.handle, _dp(x_ref), int(target), float(conf),
+                                                ctypes.byref(o), _dp(v), _dp(lam), ctypes.byref(res)))
+    return res.as_dict(), v, lam
+
+
+def layer_weights(net, layer):
+    """(W, b, activation code) of layer `layer` as loaded (FP64 master copy)."""
+    lib = load_library()
+    act, rows, cols = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib.nnc_layer_weights(net.handle, int(layer), None, None, ctypes.byref(act),
+                                 ctypes.byref(rows), ctypes.byref(cols)))
+    W = np.empty((rows.value, cols.value))
+    b = np.empty(rows.value)
+    _check(lib.nnc_layer_weights(net.handle, int(layer), _dp(W), _dp(b), None, None, None))
+    return W, b, act.value
 
 
 def kkt_solve(WDD, WSS, sigma, AD, AS, rhs, delta_w=0.0, delta_c=0.0):

@@ -111,12 +111,16 @@ def _l1_instance(seed, n=20, scale=4.0):
     return mlp, x, int(np.argsort(p0)[-2])
 
 
-@pytest.fixture(scope="module")
-def l1_oracle_solution():
+def l1_oracle_solution_data():
     mlp, x_ref, t = _l1_instance(0)
     r = oipm.solve(problems.adversarial_l1(mlp, x_ref, t, 0.6))
     assert r.status == oipm.OPTIMAL
     return mlp, x_ref, t, r
+
+
+@pytest.fixture(scope="module")
+def l1_oracle_solution():
+    return l1_oracle_solution_data()
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3"])
@@ -186,3 +190,54 @@ def test_adversarial_l1_274m(nnc):
     resid = lam_link - J.T @ lam_nn
     scale = max(1.0, np.max(np.abs(lam_nn)) * np.max(np.abs(J)))
     assert np.max(np.abs(resid[inner])) <= 1e-5 * scale
+
+
+def test_layer_weights_roundtrip(nnc):
+    mlp, x_ref, t = _l1_instance(2)
+    net = nnc.Net.from_mlp(mlp, precision="bf16x3")
+    for l in range(mlp.spec.n_layers):
+        W, b, act = nnc.layer_weights(net, l)
+        assert np.array_equal(W, mlp.W[l]) and np.array_equal(b, mlp.b[l])
+        assert act == nnc.ACTS[mlp.spec.acts[l]]
+    net.free()
+
+
+def test_adversarial_l1_fullspace_matches_oracle(nnc):
+    """Eq. 7 in the full space (Eq. 4) with the host driver against the oracle's full-space form
+    from the same start: the same converged point; and the same optimum as the reduced space."""
+    mlp, x_ref, t, ro = l1_oracle_solution_data()
+    n = x_ref.size
+    rf_o = oipm.solve(problems.adversarial_l1_fullspace(mlp, x_ref, t, 0.6))
+    assert rf_o.status == oipm.OPTIMAL
+    net = nnc.Net.from_mlp(mlp, precision="bf16x3")
+    res, v, lam = nnc.ipm_adversarial_l1_fullspace(net, x_ref, t, 0.6)
+    print(f"[ipm l1 full space] status={res['status_name']} iters={res['iters']} "
+          f"(oracle {rf_o.iters}) obj={res['obj']:.12g} (oracle {rf_o.obj:.12g}, reduced "
+          f"{ro.obj:.12g} in {ro.iters}) kkt={res['kkt_error']:.2e}")
+    assert res["status"] == 0 and res["kkt_error"] <= 1e-6
+    assert abs(res["obj"] - rf_o.obj) <= 1e-8 * max(1.0, abs(rf_o.obj))
+    assert np.max(np.abs(v - rf_o.v)) < 1e-6
+    assert abs(res["obj"] - ro.obj) <= 1e-6 * max(1.0, abs(ro.obj))
+    net.free()
+
+
+def test_adversarial_l1_fullspace_contrast(nnc):
+    """A deeper classifier ([100, 64 x 3, 10] tanh+softmax): both forms reach the same optimum;
+    the full-space KKT system is several times larger (Table 2's structural contrast)."""
+    from oracle import nn as onn
+    widths = [100, 64, 64, 64, 10]
+    mlp = make_mlp(MLPSpec(widths, ["tanh"] * 3 + ["softmax"]), seed=3, tag="fs", bias_std=0.3)
+    mlp.W[-1] = mlp.W[-1] * 4
+    x = synth.uniform01(synth.derive_key(3, "fs-x"), 100)
+    t = int(np.argsort(onn.value(mlp, x))[-2])
+    net = nnc.Net.from_mlp(mlp, precision="bf16x3")
+    rr, _, _ = nnc.ipm_adversarial_l1(net, x, t, 0.6)
+    rf, _, _ = nnc.ipm_adversarial_l1_fullspace(net, x, t, 0.6)
+    hidden = sum(widths[1:])
+    kkt_red = 3 * 100 + 10 + 100 + 10
+    kkt_full = 3 * 100 + 2 * hidden + 100 + 2 * hidden
+    print(f"[ipm l1 contrast] reduced: {rr['iters']} iterations, {rr['solve_seconds']:.3f} s, KKT "
+          f"{kkt_red}; full space: {rf['iters']} iterations, {rf['solve_seconds']:.3f} s, KKT {kkt_full}")
+    assert rr["status"] == 0 and rf["status"] == 0
+    assert abs(rf["obj"] - rr["obj"]) <= 1e-6 * max(1.0, abs(rr["obj"]))
+    net.free()

@@ -158,3 +158,43 @@ def test_l1_adversarial_already_confident():
     assert r.status == ipm.OPTIMAL
     assert r.obj < 2e-7 * x_ref.size + 1e-9   # barrier floor of the split variables (see above)
     assert np.max(np.abs(r.v[:x_ref.size] - x_ref)) < 1e-5
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_l1_fullspace_matches_reduced(seed):
+    """Eq. 7 with the network in the full space (Eq. 4: z_l and y_l as variables) is the same
+    program as the reduced-space form (Eq. 5): the same optimum, reached from the same start."""
+    mlp, x_ref, t = _l1_instance(seed)
+    n = x_ref.size
+    r = ipm.solve(problems.adversarial_l1(mlp, x_ref, t, 0.6))
+    rf = ipm.solve(problems.adversarial_l1_fullspace(mlp, x_ref, t, 0.6))
+    assert r.status == ipm.OPTIMAL and rf.status == ipm.OPTIMAL
+    print(f"[l1 {seed}] reduced {r.iters} iterations, full space {rf.iters}")
+    assert abs(rf.obj - r.obj) <= 1e-6 * max(1.0, abs(r.obj))
+    assert np.max(np.abs(rf.v[:n] - r.v[:n])) < 1e-5
+    pf = problems.adversarial_l1_fullspace(mlp, x_ref, t, 0.6)
+    off_y = pf.blocks["off_y"]
+    assert np.max(np.abs(rf.v[off_y[-1]:off_y[-1] + mlp.spec.n_out] - onn.value(mlp, rf.v[:n]))) < 1e-8
+
+
+def test_l1_fullspace_derivatives():
+    """The full-space constraint Jacobian against central differences of c, and the Hessian of
+    the Lagrangian against central differences of lambda^T J (tanh, sigmoid and softmax layers);
+    at the start point every layer constraint holds."""
+    mlp = make_mlp(MLPSpec([3, 4, 5, 3], ["tanh", "sigmoid", "softmax"]), seed=4, tag="fs-d",
+                   bias_std=0.3)
+    x = synth.uniform01(synth.derive_key(4, "fs-x"), 3)
+    pr = problems.adversarial_l1_fullspace(mlp, x, 1, 0.6)
+    assert np.max(np.abs(pr.c(pr.v0))) < 1e-15
+    v = pr.v0 + 0.05 * synth.normal(synth.derive_key(4, "fs-v"), pr.n)
+    lam = synth.normal(synth.derive_key(4, "fs-lam"), pr.m)
+    h = 1e-6
+    A = pr.jac_c(v)
+    Hl = pr.hess_c(v, lam)
+    for k in range(pr.n):
+        e = np.zeros(pr.n)
+        e[k] = h
+        fd = (pr.c(v + e) - pr.c(v - e)) / (2 * h)
+        assert np.max(np.abs(fd - A[:, k])) < 1e-8, k
+        fd2 = (pr.jac_c(v + e).T @ lam - pr.jac_c(v - e).T @ lam) / (2 * h)
+        assert np.max(np.abs(fd2 - Hl[:, k])) < 1e-7, k
