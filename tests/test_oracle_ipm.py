@@ -198,3 +198,29 @@ def test_l1_fullspace_derivatives():
         assert np.max(np.abs(fd - A[:, k])) < 1e-8, k
         fd2 = (pr.jac_c(v + e).T @ lam - pr.jac_c(v - e).T @ lam) / (2 * h)
         assert np.max(np.abs(fd2 - Hl[:, k])) < 1e-7, k
+
+
+def test_structure_of_both_forms_matches_table2():
+    """Table 2's structural counts for the 167k-parameter MNIST classifier ([784, 128 x 5, 10],
+    tanh + softmax): variables, constraints and Jacobian nonzeros of the full-space form (Eq. 4)
+    and the reduced-space form (Eq. 5) of Eq. 7, counted from the problems' own Jacobians and
+    Hessians at the start point (the table truncates to thousands)."""
+    import json
+    import os
+    from synth.nets import make_classifier
+    with open(os.path.join(os.path.dirname(__file__), "golden", "table2_structure_167k.json")) as f:
+        g = json.load(f)
+    w = g["widths"]
+    mlp = make_classifier(MLPSpec(w, ["tanh"] * (len(w) - 2) + ["softmax"]), seed=0)
+    assert 166_000 < mlp.spec.n_params < 168_000
+    x_ref = synth.uniform01(synth.derive_key(0, "t2-x"), w[0])
+    for form, build in (("full_space", problems.adversarial_l1_fullspace),
+                        ("reduced_space", problems.adversarial_l1)):
+        pr = build(mlp, x_ref, 3, 0.6)
+        A = pr.jac_c(pr.v0)
+        H = pr.hess_c(pr.v0, np.ones(pr.m)) + pr.hess_f(pr.v0)
+        counts = dict(n_var=pr.n, n_con=pr.m, jac_nnz=int(np.count_nonzero(A)),
+                      hess_nnz=int(np.count_nonzero(np.tril(H))))
+        print(form, counts)
+        for key, val in g[form].items():
+            assert counts[key.replace("_thousands", "")] // 1000 == val, (form, key, counts)
