@@ -86,7 +86,7 @@ void par_zero(double* x, size_t n) {
 // pivot (before its square root) is not above min_pivot.
 bool cholesky(int n, double* A, double min_pivot = 0.0) {
   const int NB = 64;
-  std::vector<double> Pt;   // L21^T of the current block column, rows padded to a multiple of 4
+  std::vector<double> Pt;   // L21^T of the current block column, rows padded to a multiple of 8
   for (int kb = 0; kb < n; kb += NB) {
     const int nb = std::min(NB, n - kb);
     // diagonal block (unblocked, right-looking)
@@ -104,45 +104,42 @@ bool cholesky(int n, double* A, double min_pivot = 0.0) {
     const int r0 = kb + nb;
     const int rem = n - r0;
     if (rem <= 0) break;
-    // panel below: L21 = A21 L11^-T (row by row)
-#pragma omp parallel for schedule(static)
-    for (int i = r0; i < n; ++i) {
-      double* ai = A + (size_t)i * n;
-      for (int j = kb; j < kb + nb; ++j) {
-        const double* aj = A + (size_t)j * n;
-        double s = ai[j];
-        for (int p = kb; p < j; ++p) s -= ai[p] * aj[p];
-        ai[j] = s / aj[j];
-      }
-    }
-    // trailing update A22 -= L21 L21^T (lower triangle) in 4 x 4 tiles: the panel is transposed
-    // so that each step of the K loop is an outer product of two contiguous 4-vectors (16
-    // independent accumulators, which the compiler keeps in vector registers)
-    const int rp = (rem + 3) / 4 * 4;
+    // panel below, L21 = A21 L11^-T row by row, copied transposed (rows padded to a multiple of 8)
+    // so that each step of the update's K loop is an outer product of contiguous vectors; then
+    // A22 -= L21 L21^T on the lower triangle in 8 x 4 tiles (32 accumulators in registers)
+    const int rp = (rem + 7) / 8 * 8;
     Pt.assign((size_t)nb * rp, 0.0);
-#pragma omp parallel for schedule(static)
-    for (int i = 0; i < rem; ++i)
-      for (int q = 0; q < nb; ++q) Pt[(size_t)q * rp + i] = A[(size_t)(r0 + i) * n + kb + q];
-    const int nt = rp / 4;
-#pragma omp parallel for schedule(dynamic, 1)
-    for (int ti = nt - 1; ti >= 0; --ti) {   // long rows first
-      const int i0 = ti * 4;
-      for (int tp = 0; tp <= ti; ++tp) {
-        const int p0 = tp * 4;
-        double acc[4][4] = {};
-        for (int q = 0; q < nb; ++q) {
-          const double* c = Pt.data() + (size_t)q * rp;
-          double a[4], b[4];
-          for (int u = 0; u < 4; ++u) {
-            a[u] = c[i0 + u];
-            b[u] = c[p0 + u];
-          }
-          for (int u = 0; u < 4; ++u)
-            for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+#pragma omp parallel
+    {
+#pragma omp for schedule(static)
+      for (int i = r0; i < n; ++i) {
+        double* ai = A + (size_t)i * n;
+        for (int j = kb; j < kb + nb; ++j) {
+          const double* aj = A + (size_t)j * n;
+          double s = ai[j];
+          for (int p = kb; p < j; ++p) s -= ai[p] * aj[p];
+          ai[j] = s / aj[j];
+          Pt[(size_t)(j - kb) * rp + (i - r0)] = ai[j];
         }
-        for (int u = 0; u < 4 && i0 + u < rem; ++u) {
-          double* ai = A + (size_t)(r0 + i0 + u) * n + r0;
-          for (int v = 0; v < 4 && p0 + v <= i0 + u; ++v) ai[p0 + v] -= acc[u][v];
+      }
+      const int nti = rp / 8;
+#pragma omp for schedule(dynamic, 1)
+      for (int ti = nti - 1; ti >= 0; --ti) {   // long rows first
+        const int i0 = ti * 8;
+        for (int p0 = 0; p0 < i0 + 8; p0 += 4) {
+          double acc[8][4] = {};
+          for (int q = 0; q < nb; ++q) {
+            const double* c = Pt.data() + (size_t)q * rp;
+            double a8[8], b4[4];
+            for (int u = 0; u < 8; ++u) a8[u] = c[i0 + u];
+            for (int v = 0; v < 4; ++v) b4[v] = c[p0 + v];
+            for (int u = 0; u < 8; ++u)
+              for (int v = 0; v < 4; ++v) acc[u][v] += a8[u] * b4[v];
+          }
+          for (int u = 0; u < 8 && i0 + u < rem; ++u) {
+            double* ai = A + (size_t)(r0 + i0 + u) * n + r0;
+            for (int v = 0; v < 4 && p0 + v <= i0 + u; ++v) ai[p0 + v] -= acc[u][v];
+          }
         }
       }
     }
@@ -257,94 +254,115 @@ struct BK {
       for (int j = s + 1; j < n; ++j) std::swap(a(j, r), a(j, s));
       std::swap(perm[r], perm[s]);
     };
-    std::vector<double> l1(n, 0.0), l2(n, 0.0);
-    int k = 0;
-    while (k < n) {
-      const double absakk = std::fabs(a(k, k));
-      int imax = k;
-      double colmax = 0.0;
-      for (int i = k + 1; i < n; ++i)
-        if (std::fabs(a(i, k)) > colmax) {
-          colmax = std::fabs(a(i, k));
-          imax = i;
+    std::vector<double> l1(n, 0.0), l2(n, 0.0), w1(n, 0.0), w2(n, 0.0);
+    int k = 0, kstep = 1;
+    bool zero_col = false;
+    double inv = 0.0;
+    // One parallel region for the whole factorization: the pivot choice and the interchanges run
+    // on one thread, the trailing updates are shared; the barriers of the single / for constructs
+    // order the steps (k, kstep and zero_col change only inside single blocks).
+#pragma omp parallel if (n > 256)
+    {
+      while (k < n) {
+#pragma omp single
+        {
+          const double absakk = std::fabs(a(k, k));
+          int imax = k;
+          double colmax = 0.0;
+          for (int i = k + 1; i < n; ++i)
+            if (std::fabs(a(i, k)) > colmax) {
+              colmax = std::fabs(a(i, k));
+              imax = i;
+            }
+          kstep = 1;
+          zero_col = std::max(absakk, colmax) <= zero_tol;
+          if (zero_col) {
+            ++nzero;
+            step[k] = 1;
+          } else {
+            int kp = k;
+            if (absakk < alpha * colmax) {
+              double rowmax = 0.0;   // largest off-diagonal of row imax inside the trailing block
+              for (int j = k; j < imax; ++j) rowmax = std::max(rowmax, std::fabs(a(imax, j)));
+              for (int j = imax + 1; j < n; ++j) rowmax = std::max(rowmax, std::fabs(a(j, imax)));
+              if (absakk >= alpha * colmax * (colmax / rowmax)) {
+                kp = k;
+              } else if (std::fabs(a(imax, imax)) >= alpha * rowmax) {
+                kp = imax;
+              } else {
+                kp = imax;
+                kstep = 2;
+              }
+            }
+            swap_rc(k + kstep - 1, kp);
+            step[k] = kstep;
+            if (kstep == 1) {
+              const double d = a(k, k);
+              if (std::fabs(d) <= zero_tol) ++nzero;
+              else if (d > 0) ++npos;
+              else ++nneg;
+              inv = d != 0.0 ? 1.0 / d : 0.0;
+              for (int i = k + 1; i < n; ++i) l1[i] = a(i, k);
+            } else {
+              const double d11 = a(k, k), d21 = a(k + 1, k), d22 = a(k + 1, k + 1);
+              const double det = d11 * d22 - d21 * d21;
+              if (det < 0) {
+                ++npos;
+                ++nneg;
+              } else if (std::fabs(det) <= zero_tol * zero_tol) {
+                nzero += 2;
+              } else if (d11 + d22 > 0) {
+                npos += 2;
+              } else {
+                nneg += 2;
+              }
+              const double i11 = d22 / det, i22 = d11 / det, i21 = -d21 / det;
+              // W = A(k+2:, k:k+2); L = W D^-1
+              for (int i = k + 2; i < n; ++i) {
+                w1[i] = a(i, k);
+                w2[i] = a(i, k + 1);
+                l1[i] = w1[i] * i11 + w2[i] * i21;
+                l2[i] = w1[i] * i21 + w2[i] * i22;
+              }
+            }
+          }
         }
-      int kstep = 1, kp = k;
-      if (std::max(absakk, colmax) <= zero_tol) {
-        ++nzero;
-        step[k] = 1;
-        a(k, k) = 0.0;
-        for (int i = k + 1; i < n; ++i) a(i, k) = 0.0;
-        ++k;
-        continue;
+        if (!zero_col && kstep == 1) {
+          // trailing update A22 -= a21 a21^T / d on the lower triangle
+#pragma omp for schedule(dynamic, 16)
+          for (int i = k + 1; i < n; ++i) {
+            const double f = l1[i] * inv;
+            if (f == 0.0) continue;
+            double* ai = &a(i, 0);
+            for (int j = k + 1; j <= i; ++j) ai[j] -= f * l1[j];
+          }
+        } else if (!zero_col) {
+          // A22 -= W D^-1 W^T (lower triangle)
+#pragma omp for schedule(dynamic, 16)
+          for (int i = k + 2; i < n; ++i) {
+            double* ai = &a(i, 0);
+            const double f1 = l1[i], f2 = l2[i];
+            for (int j = k + 2; j <= i; ++j) ai[j] -= f1 * w1[j] + f2 * w2[j];
+          }
+        }
+#pragma omp single
+        {
+          if (zero_col) {
+            a(k, k) = 0.0;
+            for (int i = k + 1; i < n; ++i) a(i, k) = 0.0;
+            k += 1;
+          } else if (kstep == 1) {
+            for (int i = k + 1; i < n; ++i) a(i, k) = l1[i] * inv;
+            k += 1;
+          } else {
+            for (int i = k + 2; i < n; ++i) {
+              a(i, k) = l1[i];
+              a(i, k + 1) = l2[i];
+            }
+            k += 2;
+          }
+        }
       }
-      if (absakk >= alpha * colmax) {
-        kp = k;
-      } else {
-        double rowmax = 0.0;   // largest off-diagonal of row imax inside the trailing block
-        for (int j = k; j < imax; ++j) rowmax = std::max(rowmax, std::fabs(a(imax, j)));
-        for (int j = imax + 1; j < n; ++j) rowmax = std::max(rowmax, std::fabs(a(j, imax)));
-        if (absakk >= alpha * colmax * (colmax / rowmax)) {
-          kp = k;
-        } else if (std::fabs(a(imax, imax)) >= alpha * rowmax) {
-          kp = imax;
-        } else {
-          kp = imax;
-          kstep = 2;
-        }
-      }
-      const int kk = k + kstep - 1;
-      swap_rc(kk, kp);
-      step[k] = kstep;
-      if (kstep == 1) {
-        const double d = a(k, k);
-        if (std::fabs(d) <= zero_tol) ++nzero;
-        else if (d > 0) ++npos;
-        else ++nneg;
-        const double inv = d != 0.0 ? 1.0 / d : 0.0;
-        for (int i = k + 1; i < n; ++i) l1[i] = a(i, k);
-        // trailing update A22 -= a21 a21^T / d on the lower triangle
-#pragma omp parallel for schedule(dynamic, 16) if (n - k > 192)
-        for (int i = k + 1; i < n; ++i) {
-          const double f = l1[i] * inv;
-          if (f == 0.0) continue;
-          double* ai = &a(i, 0);
-          for (int j = k + 1; j <= i; ++j) ai[j] -= f * l1[j];
-        }
-        for (int i = k + 1; i < n; ++i) a(i, k) = l1[i] * inv;
-      } else {
-        const double d11 = a(k, k), d21 = a(k + 1, k), d22 = a(k + 1, k + 1);
-        const double det = d11 * d22 - d21 * d21;
-        if (det < 0) {
-          ++npos;
-          ++nneg;
-        } else if (std::fabs(det) <= zero_tol * zero_tol) {
-          nzero += 2;
-        } else if (d11 + d22 > 0) {
-          npos += 2;
-        } else {
-          nneg += 2;
-        }
-        const double i11 = d22 / det, i22 = d11 / det, i21 = -d21 / det;
-        // W = A(k+2:, k:k+2); L = W D^-1; A22 -= W D^-1 W^T (lower triangle)
-        std::vector<double> w1(n, 0.0), w2(n, 0.0);
-        for (int i = k + 2; i < n; ++i) {
-          w1[i] = a(i, k);
-          w2[i] = a(i, k + 1);
-          l1[i] = w1[i] * i11 + w2[i] * i21;
-          l2[i] = w1[i] * i21 + w2[i] * i22;
-        }
-#pragma omp parallel for schedule(dynamic, 16) if (n - k > 192)
-        for (int i = k + 2; i < n; ++i) {
-          double* ai = &a(i, 0);
-          const double f1 = l1[i], f2 = l2[i];
-          for (int j = k + 2; j <= i; ++j) ai[j] -= f1 * w1[j] + f2 * w2[j];
-        }
-        for (int i = k + 2; i < n; ++i) {
-          a(i, k) = l1[i];
-          a(i, k + 1) = l2[i];
-        }
-      }
-      k += kstep;
     }
     return true;
   }
