@@ -216,6 +216,11 @@ int nnc_net_info(const nnc_net* net, int* n_layers, int* n_in, int* n_out, int* 
  * (rows = width of layer l+1, cols = width of layer l).  Synchronises the net's stream. */
 int nnc_layer_weights(const nnc_net* net, int layer, double* W, double* b, int* act, int* rows,
                       int* cols);
+/* Failure-detection self-test (no net): one CTA waits `cycles` clock cycles (1 .. 4e9) on an
+ * mbarrier that nothing arrives on, with the bounded wait of the streaming kernels (which = 0) or
+ * of the tensor-core kernels (which = 1, abort flag included).  The wait must give up: returns
+ * NNC_ERR_TIMEOUT with the recorded wait code in *code (may be NULL), and the device stays usable. */
+int nnc_selftest_bounded_wait(int which, long long cycles, int* code);
 /* Number of kernel launches this library queued since load (all nets, this process). */
 long long nnc_launch_count(void);
 

@@ -206,7 +206,26 @@ cudaError_t launch_sv(SvArgs a, int sm_count, cudaStream_t st) {
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
+// Self-test of the bounded wait: an mbarrier that nothing arrives on, waited for `limit` cycles;
+// the wait must give up and record `code` in *err.
+__global__ void k_wait_selftest(int* err, long long limit, int code) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait(smem_u32(&bar), 0, err, code, limit);
+  __syncthreads();
+}
+
 }  // namespace
+
+cudaError_t launch_wait_selftest_stream(int* err, long long limit, int code, cudaStream_t st) {
+  k_wait_selftest<<<1, 32, 0, st>>>(err, limit, code);
+  note_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t launch_gemv_stream_df(const void* W2, int ldw, int m, const double* b, const void* a_in2,
                                   int act, double* a_out, void* a_df, double* s1, double* s2,

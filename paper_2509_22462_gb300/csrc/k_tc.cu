@@ -737,6 +737,25 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   }
 }
 
+// Self-test of the tensor-core kernels' bounded wait (with the CTA abort flag): an mbarrier that
+// nothing arrives on; the wait gives up after `limit` cycles, records `code` and sets the flag,
+// which a second wait then sees at once.
+__global__ void k_tc_wait_selftest(int* err, long long limit, int code) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ volatile int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_wait(smem_u32(&bar), 0, err, code, &abort_flag, limit);
+    if (abort_flag) mbar_wait(smem_u32(&bar), 0, err, code + 1, &abort_flag, limit);
+  }
+  __syncthreads();
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -987,6 +1006,12 @@ int tc_plan_make(TcPlan& p, int kind, int prec, const void* a_hi, const void* a_
   if (!make_map(&p.tb_p2, x6 ? b_p2 : nullptr, b_rows, K, ld_b, b_box, p.bk, eb)) return NNC_ERR_CUDA;
   p.ready = true;
   return NNC_OK;
+}
+
+cudaError_t launch_wait_selftest_tc(int* err, long long limit, int code, cudaStream_t st) {
+  k_tc_wait_selftest<<<1, 32, 0, st>>>(err, limit, code);
+  note_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t tc_tangent(const TcPlan& p, const double* s1, const float* c, void* at_hi, void* at_lo,

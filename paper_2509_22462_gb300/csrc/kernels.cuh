@@ -93,6 +93,14 @@ cudaError_t launch_quant_fp8(const void* A, int rows, int ld, unsigned char* A8,
 }  // namespace nnc
 
 namespace nnc {
+// Bounded-wait self-tests: one CTA waits `limit` cycles on an mbarrier nothing arrives on and
+// records `code` in *err (the streaming kernels' wait, and the tensor-core kernels' wait with its
+// abort flag).
+cudaError_t launch_wait_selftest_stream(int* err, long long limit, int code, cudaStream_t st);
+cudaError_t launch_wait_selftest_tc(int* err, long long limit, int code, cudaStream_t st);
+}  // namespace nnc
+
+namespace nnc {
 // Streaming value-pass layer in double-float arithmetic (k_stream.cu), launched with
 // programmatic dependent launch: z = W a_in + b from (hi, lo) float2 weights and activations;
 // a_out = sigma(z), a_df its (hi, lo) float2 copy, s1 = sigma'(z), s2 = sigma''(z) (each may be

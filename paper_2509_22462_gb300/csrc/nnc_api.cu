@@ -489,6 +489,27 @@ int nnc_net_info(const nnc_net* net, int* n_layers, int* n_in, int* n_out, int* 
   return NNC_OK;
 }
 
+int nnc_selftest_bounded_wait(int which, long long cycles, int* code) {
+  if (code) *code = 0;
+  if (which < 0 || which > 1 || cycles < 1 || cycles > 4000000000LL)
+    return fail(NNC_ERR_ARG, "which must be 0 or 1, cycles in [1, 4e9]");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail(NNC_ERR_CUDA, "no CUDA device");
+  int* err = nullptr;
+  CK(cudaMalloc(&err, sizeof(int)));
+  cudaMemset(err, 0, sizeof(int));
+  cudaError_t e = which == 0 ? launch_wait_selftest_stream(err, cycles, 91, nullptr)
+                             : launch_wait_selftest_tc(err, cycles, 93, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(err);
+  if (e != cudaSuccess) return fail(NNC_ERR_CUDA, cudaGetErrorString(e));
+  if (code) *code = h;
+  if (h) return fail(NNC_ERR_TIMEOUT, "a bounded device-side wait ran out (code " + std::to_string(h) + ")");
+  return NNC_OK;
+}
+
 int nnc_layer_weights(const nnc_net* net, int layer, double* W, double* b, int* act, int* rows,
                       int* cols) {
   if (!net) return fail(NNC_ERR_ARG, "net is NULL");

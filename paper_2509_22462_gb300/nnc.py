@@ -26,7 +26,8 @@ EXPORTS = ["nnc_load_weights", "nnc_eval", "nnc_residual", "nnc_jacobian", "nnc_
            "nnc_hessian_lag_dev", "nnc_eval_all_dev", "nnc_eval_kkt_dev", "nnc_eval_kkt", "nnc_free", "nnc_last_error",
            "nnc_net_info", "nnc_launch_count", "nnc_profile", "nnc_profile_read",
            "nnc_ipm_default_options", "nnc_ipm_adversarial", "nnc_ipm_adversarial_l1",
-           "nnc_ipm_adversarial_l1_fullspace", "nnc_layer_weights", "nnc_kkt_solve",
+           "nnc_ipm_adversarial_l1_fullspace", "nnc_layer_weights", "nnc_selftest_bounded_wait",
+           "nnc_kkt_solve",
            "nnc_residual_noalloc", "nnc_batch_create", "nnc_batch_free", "nnc_batch_info",
            "nnc_batch_set_bias", "nnc_batch_use_graph", "nnc_batch_eval_dev", "nnc_batch_residual_dev",
            "nnc_batch_eval", "nnc_batch_residual", "nnc_ipm_scopf", "nnc_ws_create", "nnc_ws_free",
@@ -157,6 +158,7 @@ def load_library(path: str = LIB_PATH):
                                                      ctypes.POINTER(IpmResult)]
     lib.nnc_layer_weights.argtypes = [_P, ctypes.c_int, _DP, _DP, ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.nnc_selftest_bounded_wait.argtypes = [ctypes.c_int, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int)]
     lib.nnc_profile_read.argtypes = [_P, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
     for name in EXPORTS:
@@ -412,6 +414,14 @@ def layer_weights(net, layer):
     b = np.empty(rows.value)
     _check(lib.nnc_layer_weights(net.handle, int(layer), _dp(W), _dp(b), None, None, None))
     return W, b, act.value
+
+
+def selftest_bounded_wait(which, cycles):
+    """Runs the bounded-wait self-test; returns (status, recorded wait code)."""
+    lib = load_library()
+    code = ctypes.c_int()
+    st = lib.nnc_selftest_bounded_wait(int(which), int(cycles), ctypes.byref(code))
+    return st, code.value
 
 
 def kkt_solve(WDD, WSS, sigma, AD, AS, rhs, delta_w=0.0, delta_c=0.0):
