@@ -186,8 +186,9 @@ cudaError_t launch_sv(SvArgs a, int sm_count, cudaStream_t st) {
   }
   if (smem > kSvMaxWarps * 3 * kSvSlice || a.ns > kSvMaxStages || a.gw > kSvMaxGroups)
     return cudaErrorInvalidValue;
-  // CTAs per SM from shared memory (about 200 KB usable with the static part) and warps
-  const int per_sm = std::max(1, std::min({4, 200 * 1024 / smem, 48 / a.nw}));
+  // CTAs per SM from shared memory (about 200 KB usable with the static part) and warps: layers
+  // with short rows (few warps per CTA) get more CTAs per SM, so more copies are in flight
+  const int per_sm = std::max(1, std::min({12, 200 * 1024 / smem, 48 / a.nw}));
   const int grid = std::max(1, std::min(a.m, per_sm * sm_count));
   a.rows_per_cta = (a.m + grid - 1) / grid;
   const int used = (a.m + a.rows_per_cta - 1) / a.rows_per_cta;
