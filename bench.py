@@ -334,10 +334,12 @@ def run_ours_scopf(args, rank, world, local_rank):
     H = torch.empty(batch.h_sum, dtype=torch.float64, device=dev)
     g = torch.empty(batch.n_sum, dtype=torch.float64, device=dev)
     r = torch.empty(K, dtype=torch.float64, device=dev)
+    y_it = torch.zeros(K, dtype=torch.float64, device=dev)   # the iterate's margins y_k
 
     def step():
-        batch.eval_dev(xc, lc, y, J, H, g)
-        batch.residual_dev(xc, y, r)
+        # one interior-point iterate of every surrogate: FP64-accurate residual, J, H and
+        # gradient from one value pass
+        batch.eval_kkt_dev(xc, y_it, lc, r, J, H, g)
 
     for _ in range(args.warmup):
         step()

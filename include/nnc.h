@@ -164,9 +164,17 @@ int nnc_batch_use_graph(nnc_batch* batch, int enable);
 int nnc_batch_eval_dev(nnc_batch* batch, const double* x_cat, const double* lambda_cat,
                        double* y_cat, double* J_cat, double* H_cat, double* grad_cat,
                        void* stream);
-/* FP64 residual r_cat = y_cat - NN(x_cat) of every net (FP64 weights), device pointers. */
+/* FP64-accurate residual r_cat = y_cat - NN(x_cat) of every net (double-float value pass),
+ * device pointers. */
 int nnc_batch_residual_dev(nnc_batch* batch, const double* x_cat, const double* y_cat,
                            double* r_cat, void* stream);
+/* One interior-point iterate of every net from one value pass: the FP64-accurate residual
+ * r_cat = y_cat - NN(x_cat) (r_cat may be NULL, then y_cat too), J, H and the gradient as in
+ * nnc_batch_eval_dev (any may be NULL; lambda_cat needed for H or grad); captured in the CUDA
+ * graph like nnc_batch_eval_dev. */
+int nnc_batch_eval_kkt_dev(nnc_batch* batch, const double* x_cat, const double* y_cat,
+                           const double* lambda_cat, double* r_cat, double* J_cat, double* H_cat,
+                           double* grad_cat, void* stream);
 /* Host-pointer twins (copy, run, copy back, wait). */
 int nnc_batch_eval(nnc_batch* batch, const double* x_cat, const double* lambda_cat, double* y_cat,
                    double* J_cat, double* H_cat, double* grad_cat);

@@ -29,10 +29,12 @@ struct BLayer {
   int m = 0, k = 0, act = 0, mp = 0, kp = 0, zy_off = -1;
   double* W64 = nullptr;
   float* W32 = nullptr;
+  float2* W2 = nullptr;           // double-float (hi, lo) pairs of the weights (value passes)
   __nv_bfloat16 *Whi = nullptr, *Wlo = nullptr;
   double* b = nullptr;
   double *a = nullptr, *s1 = nullptr, *s2 = nullptr, *c = nullptr, *ra = nullptr;
-  float *af = nullptr, *c_f = nullptr;
+  float2 *a2 = nullptr, *ra2 = nullptr;   // double-float pairs of a and ra (next layer's input)
+  float* c_f = nullptr;
   TcPlan plan_tan;
 };
 
@@ -56,7 +58,7 @@ struct nnc_batch {
   int n_work = 0;
   std::vector<BLayer> layers;
   double *xs = nullptr, *lam = nullptr, *Zbar[2] = {nullptr, nullptr};
-  float* xf = nullptr;
+  float2* xs2 = nullptr;   // double-float pairs of the scattered inputs
   float* part = nullptr;
   void *At[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}}, *Zt[2] = {nullptr, nullptr},
        *Yt[2] = {nullptr, nullptr};
@@ -74,7 +76,8 @@ struct nnc_batch {
   // CUDA graph of one evaluation, keyed by its pointer arguments
   bool use_graph = false;
   cudaGraphExec_t gexec = nullptr;
-  const void* gkey[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  const void* gkey[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                         nullptr};
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 };
 
@@ -109,21 +112,34 @@ int balloc(nnc_batch* b, T** p, size_t n) {
 
 bool is_tc_prec(int p) { return p == NNC_BF16 || p == NNC_BF16X3; }
 
-int batch_eval(nnc_batch* b, const double* x, const double* lam, double* y, double* J, double* H,
-               double* g, cudaStream_t st) {
+// Value pass of every network in double-float arithmetic (one grouped streaming launch per layer):
+// a (FP64-accurate), its pairs for the next layer and, for an evaluation, sigma' and sigma''.
+int batch_value(nnc_batch* b, const double* x, bool residual, cudaStream_t st) {
   const int K = b->K;
-  const bool x3 = b->prec == NNC_BF16X3;
-  BCK(launch_bx_scatter(x, b->d_gn, b->d_goff, b->kp0, K, b->xs, b->xf, st));
-  const void* a_in = b->xf;
+  BCK(launch_bx_scatter(x, b->d_gn, b->d_goff, b->kp0, K, b->xs, nullptr, st));
+  BCK(launch_split_df(b->xs, (size_t)K * b->kp0, b->xs2, st));
+  const void* a_in = b->xs2;
   int ld_in = b->kp0;
   for (auto& Ly : b->layers) {
-    BCK(launch_bgemv_fwd(false, Ly.W32, Ly.kp, Ly.mp, Ly.m, K, Ly.b, a_in, ld_in, Ly.act, Ly.a, Ly.af,
-                         Ly.s1, Ly.s2, st));
-    a_in = Ly.af;
+    BCK(launch_gemv_stream_df_grouped(Ly.W2, Ly.kp, K, Ly.mp, Ly.m, Ly.b, a_in, ld_in, Ly.act,
+                                      residual ? Ly.ra : Ly.a, residual ? Ly.ra2 : Ly.a2,
+                                      residual ? nullptr : Ly.s1, residual ? nullptr : Ly.s2,
+                                      b->dev_err, b->sm_count, st));
+    a_in = residual ? Ly.ra2 : Ly.a2;
     ld_in = Ly.mp;
   }
+  return NNC_OK;
+}
+
+int batch_eval(nnc_batch* b, const double* x, const double* lam, double* y, double* J, double* H,
+               double* g, cudaStream_t st, const double* yv = nullptr, double* rr = nullptr) {
+  const int K = b->K;
+  const bool x3 = b->prec == NNC_BF16X3;
+  int rv = batch_value(b, x, false, st);
+  if (rv != NNC_OK) return rv;
   BLayer& Lo = b->layers.back();
   if (y) BCK(launch_bgather(Lo.a, b->n_out, Lo.mp, K, y, st));
+  if (rr) BCK(launch_bsub(yv, Lo.a, b->n_out, Lo.mp, K, rr, st));   // y - NN(x), FP64-accurate
   if (!J && !H && !g) return NNC_OK;
   const int nJ = J ? b->n_out : 0;
   const bool with_lam = H || g;
@@ -179,17 +195,9 @@ int batch_eval(nnc_batch* b, const double* x, const double* lam, double* y, doub
 }
 
 int batch_residual(nnc_batch* b, const double* x, const double* y, double* r, cudaStream_t st) {
-  const int K = b->K;
-  BCK(launch_bx_scatter(x, b->d_gn, b->d_goff, b->kp0, K, b->xs, nullptr, st));
-  const void* a_in = b->xs;
-  int ld_in = b->kp0;
-  for (auto& Ly : b->layers) {
-    BCK(launch_bgemv_fwd(true, Ly.W64, Ly.kp, Ly.mp, Ly.m, K, Ly.b, a_in, ld_in, Ly.act, Ly.ra,
-                         nullptr, nullptr, nullptr, st));
-    a_in = Ly.ra;
-    ld_in = Ly.mp;
-  }
-  BCK(launch_bsub(y, b->layers.back().ra, b->n_out, b->layers.back().mp, K, r, st));
+  int rv = batch_value(b, x, true, st);
+  if (rv != NNC_OK) return rv;
+  BCK(launch_bsub(y, b->layers.back().ra, b->n_out, b->layers.back().mp, b->K, r, st));
   return NNC_OK;
 }
 
@@ -268,6 +276,7 @@ int build(nnc_batch* b, nnc_net* const* nets, int K) {
     const size_t per = (size_t)Ly.mp * Ly.kp;
     BAL(Ly.W64, per * K);
     BAL(Ly.W32, per * K);
+    BAL(Ly.W2, per * K);
     if (l > 0) {
       BAL(Ly.Whi, per * K);
       if (x3) BAL(Ly.Wlo, per * K);
@@ -281,8 +290,10 @@ int build(nnc_batch* b, nnc_net* const* nets, int K) {
                           cudaMemcpyDeviceToDevice, b->stream));
     }
     BCK(launch_pack(Ly.W64, per * K, Ly.W32, Ly.Whi, Ly.Wlo, b->stream));
+    BCK(launch_split_df(Ly.W64, per * K, Ly.W2, b->stream));
     BAL(Ly.a, (size_t)Ly.mp * K);
-    BAL(Ly.af, (size_t)Ly.mp * K);
+    BAL(Ly.a2, (size_t)Ly.mp * K);
+    BAL(Ly.ra2, (size_t)Ly.mp * K);
     BAL(Ly.s1, (size_t)Ly.mp * K);
     BAL(Ly.s2, (size_t)Ly.mp * K);
     BAL(Ly.c, (size_t)Ly.mp * K);
@@ -291,7 +302,7 @@ int build(nnc_batch* b, nnc_net* const* nets, int K) {
     part_max = std::max(part_max, (size_t)K * bgemv_rev_chunks(Ly.m) * Ly.kp * b->S);
   }
   BAL(b->xs, (size_t)K * b->kp0);
-  BAL(b->xf, (size_t)K * b->kp0);
+  BAL(b->xs2, (size_t)K * b->kp0);
   BAL(b->Zbar[0], (size_t)K * mp_max * b->S);
   BAL(b->Zbar[1], (size_t)K * mp_max * b->S);
   BAL(b->part, part_max);
@@ -434,13 +445,12 @@ int nnc_batch_use_graph(nnc_batch* b, int enable) {
   return NNC_OK;
 }
 
-int nnc_batch_eval_dev(nnc_batch* b, const double* x, const double* lambda, double* y, double* J,
-                       double* H, double* grad, void* stream) {
-  if (!b || !x || ((H || grad) && !lambda)) return bfail(NNC_ERR_ARG, "nnc_batch_eval_dev: bad arguments");
+static int batch_eval_dev(nnc_batch* b, const double* x, const double* yv, const double* lambda,
+                          double* rr, double* y, double* J, double* H, double* grad, void* stream) {
   cudaStream_t st = stream ? (cudaStream_t)stream : b->stream;
-  if (!b->use_graph) return batch_eval(b, x, lambda, y, J, H, grad, st);
+  if (!b->use_graph) return batch_eval(b, x, lambda, y, J, H, grad, st, yv, rr);
   // Graph mode: capture once on the batch's own stream, replay while the pointers match.
-  const void* key[7] = {x, lambda, y, J, H, grad, nullptr};
+  const void* key[9] = {x, lambda, y, J, H, grad, yv, rr, nullptr};
   if (b->gexec && std::memcmp(key, b->gkey, sizeof(key)) != 0) {
     cudaGraphExecDestroy(b->gexec);
     b->gexec = nullptr;
@@ -448,7 +458,7 @@ int nnc_batch_eval_dev(nnc_batch* b, const double* x, const double* lambda, doub
   if (!b->gexec) {
     cudaGraph_t graph;
     BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-    int r = batch_eval(b, x, lambda, y, J, H, grad, b->stream);
+    int r = batch_eval(b, x, lambda, y, J, H, grad, b->stream, yv, rr);
     cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
     if (r != NNC_OK) return r;
     BCK(e);
@@ -468,6 +478,19 @@ int nnc_batch_eval_dev(nnc_batch* b, const double* x, const double* lambda, doub
     BCK(cudaStreamWaitEvent(st, b->ev_out, 0));
   }
   return NNC_OK;
+}
+
+int nnc_batch_eval_dev(nnc_batch* b, const double* x, const double* lambda, double* y, double* J,
+                       double* H, double* grad, void* stream) {
+  if (!b || !x || ((H || grad) && !lambda)) return bfail(NNC_ERR_ARG, "nnc_batch_eval_dev: bad arguments");
+  return batch_eval_dev(b, x, nullptr, lambda, nullptr, y, J, H, grad, stream);
+}
+
+int nnc_batch_eval_kkt_dev(nnc_batch* b, const double* x, const double* y, const double* lambda,
+                           double* r, double* J, double* H, double* grad, void* stream) {
+  if (!b || !x || (r && !y) || ((H || grad) && !lambda))
+    return bfail(NNC_ERR_ARG, "nnc_batch_eval_kkt_dev: bad arguments");
+  return batch_eval_dev(b, x, y, lambda, r, nullptr, J, H, grad, stream);
 }
 
 int nnc_batch_residual_dev(nnc_batch* b, const double* x, const double* y, double* r, void* stream) {

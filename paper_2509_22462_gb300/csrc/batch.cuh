@@ -7,9 +7,6 @@ namespace nnc {
 
 cudaError_t launch_bx_scatter(const double* xcat, const int* gn, const int* goff, int kp, int groups,
                               double* xs, float* xf, cudaStream_t st);
-cudaError_t launch_bgemv_fwd(bool fp64, const void* W, int ldw, int mp, int m, int groups,
-                             const double* b, const void* a_in, int ld_in, int act, double* a_out,
-                             float* a_out_f, double* s1, double* s2, cudaStream_t st);
 cudaError_t launch_bgemv_rev(const float* W, int ldw, int mp, int m, int groups, const double* Zbar,
                              int S, float* part, cudaStream_t st);
 int bgemv_rev_chunks(int m);

@@ -35,74 +35,6 @@ cudaError_t launch_bx_scatter(const double* xcat, const int* gn, const int* goff
   return cudaGetLastError();
 }
 
-// One warp per output row of every group: z = W a + b, a = sigma(z), sigma', sigma''.
-template <typename TW>
-__global__ void __launch_bounds__(256) k_bgemv_fwd(const TW* __restrict__ W, int ldw, int mp,
-                                                   int m, const double* __restrict__ bias,
-                                                   const void* __restrict__ a_in_v, int ld_in,
-                                                   int act, double* __restrict__ a_out,
-                                                   float* __restrict__ a_out_f,
-                                                   double* __restrict__ s1,
-                                                   double* __restrict__ s2) {
-  const int g = blockIdx.y;
-  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (row >= m) return;
-  const size_t grow = (size_t)g * mp + row;
-  double acc;
-  if constexpr (std::is_same<TW, float>::value) {
-    const float4* r4 = reinterpret_cast<const float4*>(W + grow * ldw);
-    const float4* a4 = reinterpret_cast<const float4*>((const float*)a_in_v + (size_t)g * ld_in);
-    const int nk4 = ldw >> 2;
-    float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
-#pragma unroll 8
-    for (int j = lane; j < nk4; j += 32) {
-      const float4 w = __ldg(r4 + j);
-      const float4 a = a4[j];
-      p0 = fmaf(w.x, a.x, p0);
-      p1 = fmaf(w.y, a.y, p1);
-      p2 = fmaf(w.z, a.z, p2);
-      p3 = fmaf(w.w, a.w, p3);
-    }
-    acc = ((double)p0 + (double)p1) + ((double)p2 + (double)p3);
-  } else {
-    const double2* r2 = reinterpret_cast<const double2*>(W + grow * ldw);
-    const double2* a2 = reinterpret_cast<const double2*>((const double*)a_in_v + (size_t)g * ld_in);
-    const int nk2 = ldw >> 1;
-    double q0 = 0.0, q1 = 0.0;
-#pragma unroll 4
-    for (int j = lane; j < nk2; j += 32) {
-      const double2 w = __ldg(r2 + j);
-      const double2 a = a2[j];
-      q0 = fma(w.x, a.x, q0);
-      q1 = fma(w.y, a.y, q1);
-    }
-    acc = q0 + q1;
-  }
-  acc = bwarp_sum(acc);
-  if (lane == 0) {
-    double a, d1, d2;
-    act_eval(act, acc + (bias ? bias[grow] : 0.0), a, d1, d2);
-    a_out[grow] = a;
-    if (a_out_f) a_out_f[grow] = (float)a;
-    if (s1) s1[grow] = d1;
-    if (s2) s2[grow] = d2;
-  }
-}
-
-cudaError_t launch_bgemv_fwd(bool fp64, const void* W, int ldw, int mp, int m, int groups,
-                             const double* b, const void* a_in, int ld_in, int act, double* a_out,
-                             float* a_out_f, double* s1, double* s2, cudaStream_t st) {
-  dim3 grid((m * 32 + 255) / 256, groups);
-  if (fp64)
-    k_bgemv_fwd<double><<<grid, 256, 0, st>>>((const double*)W, ldw, mp, m, b, a_in, ld_in, act,
-                                              a_out, a_out_f, s1, s2);
-  else
-    k_bgemv_fwd<float><<<grid, 256, 0, st>>>((const float*)W, ldw, mp, m, b, a_in, ld_in, act,
-                                             a_out, a_out_f, s1, s2);
-  note_launch();
-  return cudaGetLastError();
-}
 
 // Reverse step of every group: part[g][c][kk][s] = sum_{r in chunk c} W_g[r][kk] Zbar_g[r][s]
 // (FP32 weights, FP32 seeds), 256 threads x 4 columns per block, kBRows rows per chunk.

@@ -52,6 +52,10 @@ struct SvArgs {
   int gw;               // 512-byte groups per warp slice (<= kSvMaxGroups)
   int ns;               // ring stages per warp (<= kSvMaxStages)
   int rows_per_cta;
+  // grouped rows (a batch of networks stacked by rows): rows [g group_rows, (g + 1) group_rows)
+  // belong to group g, whose first group_m are valid and whose activation vector starts at
+  // a_in + g ld_in (float2 elements); group_rows = 0: one vector for all rows
+  int group_rows, group_m, ld_in;
 };
 
 __global__ void __launch_bounds__(kSvMaxWarps * 32) k_gemv_stream(const SvArgs p) {
@@ -67,7 +71,9 @@ __global__ void __launch_bounds__(kSvMaxWarps * 32) k_gemv_stream(const SvArgs p
   const int ng = max(0, min(groups, g0 + p.gw) - g0);  // this warp's groups
   const int slice_bytes = ng * kSvGroup;
   const int r0 = blockIdx.x * p.rows_per_cta;
-  const int nrows = max(0, min(p.m, r0 + p.rows_per_cta) - r0);
+  int nrows = max(0, min(p.m, r0 + p.rows_per_cta) - r0);
+  const int grp = p.group_rows ? r0 / p.group_rows : 0;   // rows_per_cta divides group_rows
+  if (p.group_rows) nrows = max(0, min(nrows, p.group_m - (r0 - grp * p.group_rows)));
   unsigned char* ring = sv_smem + warp * (p.ns * kSvSlice);
   if (p.ns < 1 || p.ns > kSvMaxStages || p.nw * 32 != (int)blockDim.x || p.nw > kSvMaxWarps ||
       p.gw < 1 || p.gw > kSvMaxGroups)
@@ -96,7 +102,8 @@ __global__ void __launch_bounds__(kSvMaxWarps * 32) k_gemv_stream(const SvArgs p
   griddep_launch();  // the next kernel in the stream may start issuing its own copies
 
   float4 act[kSvMaxGroups];
-  const float4* a4 = reinterpret_cast<const float4*>(p.a_in) + (size_t)g0 * 32 + lane;
+  const float4* a4 = reinterpret_cast<const float4*>(p.a_in) + (size_t)grp * (p.ld_in / 2) +
+                     (size_t)g0 * 32 + lane;
 #pragma unroll
   for (int g = 0; g < kSvMaxGroups; ++g)
     act[g] = g < ng ? __ldg(a4 + g * 32) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -189,9 +196,30 @@ cudaError_t launch_sv(SvArgs a, int sm_count, cudaStream_t st) {
   // CTAs per SM from shared memory (about 200 KB usable with the static part) and warps: layers
   // with short rows (few warps per CTA) get more CTAs per SM, so more copies are in flight
   const int per_sm = std::max(1, std::min({12, 200 * 1024 / smem, 48 / a.nw}));
-  const int grid = std::max(1, std::min(a.m, per_sm * sm_count));
-  a.rows_per_cta = (a.m + grid - 1) / grid;
-  const int used = (a.m + a.rows_per_cta - 1) / a.rows_per_cta;
+  int used;
+  if (a.group_rows > 0) {
+    // grouped: rows per CTA a power of two dividing group_rows (a multiple of 128), chosen so
+    // that the CTAs holding valid rows fill whole waves of resident CTAs best (larger on ties)
+    const int groups = a.m / a.group_rows;
+    const long long slots = (long long)per_sm * sm_count;
+    int best = a.group_rows;
+    double best_eff = -1.0;
+    for (int p2 = a.group_rows; p2 >= 8; p2 /= 2) {
+      const long long ctas = (long long)groups * ((a.group_m + p2 - 1) / p2);
+      const long long waves = (ctas + slots - 1) / slots;
+      const double eff = (double)ctas / (double)(waves * slots);
+      if (eff > best_eff + 1e-9) {
+        best_eff = eff;
+        best = p2;
+      }
+    }
+    a.rows_per_cta = best;
+    used = a.m / best;
+  } else {
+    const int grid = std::max(1, std::min(a.m, per_sm * sm_count));
+    a.rows_per_cta = (a.m + grid - 1) / grid;
+    used = (a.m + a.rows_per_cta - 1) / a.rows_per_cta;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(used);
   cfg.blockDim = dim3(a.nw * 32);
@@ -232,7 +260,18 @@ cudaError_t launch_gemv_stream_df(const void* W2, int ldw, int m, const double* 
                                   int act, double* a_out, void* a_df, double* s1, double* s2,
                                   int* err, int sm_count, cudaStream_t st) {
   if (ldw % kPad) return cudaErrorInvalidValue;
-  SvArgs a{W2, ldw, m, b, a_in2, act, a_out, (float2*)a_df, s1, s2, err, 0, 0, 0, 0};
+  SvArgs a{W2, ldw, m, b, a_in2, act, a_out, (float2*)a_df, s1, s2, err, 0, 0, 0, 0, 0, 0, 0};
+  return launch_sv(a, sm_count, st);
+}
+
+cudaError_t launch_gemv_stream_df_grouped(const void* W2, int ldw, int groups, int mp, int m,
+                                          const double* b, const void* a_in2, int ld_in, int act,
+                                          double* a_out, void* a_df, double* s1, double* s2,
+                                          int* err, int sm_count, cudaStream_t st) {
+  if (ldw % kPad || mp % kPad || ld_in % kPad || groups < 1 || m < 1 || m > mp)
+    return cudaErrorInvalidValue;
+  SvArgs a{W2, ldw, groups * mp, b, a_in2, act, a_out, (float2*)a_df, s1, s2, err, 0, 0, 0, 0,
+           mp, m, ld_in};
   return launch_sv(a, sm_count, st);
 }
 

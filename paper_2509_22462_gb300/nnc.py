@@ -29,7 +29,7 @@ EXPORTS = ["nnc_load_weights", "nnc_eval", "nnc_residual", "nnc_jacobian", "nnc_
            "nnc_ipm_adversarial_l1_fullspace", "nnc_layer_weights", "nnc_selftest_bounded_wait",
            "nnc_kkt_solve",
            "nnc_residual_noalloc", "nnc_batch_create", "nnc_batch_free", "nnc_batch_info",
-           "nnc_batch_set_bias", "nnc_batch_use_graph", "nnc_batch_eval_dev", "nnc_batch_residual_dev",
+           "nnc_batch_set_bias", "nnc_batch_use_graph", "nnc_batch_eval_dev", "nnc_batch_residual_dev", "nnc_batch_eval_kkt_dev",
            "nnc_batch_eval", "nnc_batch_residual", "nnc_ipm_scopf", "nnc_ws_create", "nnc_ws_free",
            "nnc_ws_set_scaling", "nnc_ws_loss_grad", "nnc_ws_adam_step", "nnc_ws_train",
            "nnc_ws_predict", "nnc_ws_get_params", "nnc_ipm_scopf_warm", "nnc_autotune", "nnc_tuning", "nnc_tune_set"]
@@ -120,6 +120,7 @@ def load_library(path: str = LIB_PATH):
     lib.nnc_batch_use_graph.argtypes = [_P, ctypes.c_int]
     lib.nnc_batch_eval_dev.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P]
     lib.nnc_batch_residual_dev.argtypes = [_P, _P, _P, _P, _P]
+    lib.nnc_batch_eval_kkt_dev.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _P]
     lib.nnc_batch_eval.argtypes = [_P, _DP, _DP, _DP, _DP, _DP, _DP]
     lib.nnc_batch_residual.argtypes = [_P, _DP, _DP, _DP]
     lib.nnc_ipm_scopf.argtypes = [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -528,6 +529,11 @@ class Batch:
 
     def residual_dev(self, x, y, r, stream=None):
         _check(_lib.nnc_batch_residual_dev(self._h, _tp(x), _tp(y), _tp(r), stream or _stream_ptr()))
+
+    def eval_kkt_dev(self, x, y, lam, r=None, J=None, H=None, g=None, stream=None):
+        """Residual y - NN(x), J, H and gradient of every net from one value pass."""
+        _check(_lib.nnc_batch_eval_kkt_dev(self._h, _tp(x), _tp(y), _tp(lam), _tp(r), _tp(J), _tp(H),
+                                           _tp(g), stream or _stream_ptr()))
 
 
 def ipm_scopf(batch, G, subsets, cost, demand, delta, v_start=None, lam_start=None, **options):

@@ -128,3 +128,42 @@ def test_scopf_ipm_matches_oracle(nnc):
     b.free()
     for n in nets:
         n.free()
+
+
+def test_fused_residual_matches_separate_calls(nnc, small_batch):
+    """nnc_batch_eval_kkt_dev: the FP64-accurate residual, J, H and gradient of every net from one
+    value pass, equal to the separate calls, with and without the CUDA graph."""
+    import torch
+    data, raw, nets = small_batch
+    b = nnc.Batch(nets)
+    dev = torch.device("cuda:0")
+    x = synth.uniform01(synth.derive_key(4, "bx"), data.G)
+    xs = [x[S] for S in data.subsets]
+    lams = [np.array([0.3 + 0.05 * k]) for k in range(len(raw))]
+    yv = np.array([0.1 * k - 0.4 for k in range(len(raw))])
+    xc = torch.tensor(b.concat(xs), device=dev)
+    lc = torch.tensor(b.concat(lams), device=dev)
+    yc = torch.tensor(yv, device=dev)
+
+    def bufs():
+        return (torch.empty(b.K, dtype=torch.float64, device=dev),
+                torch.empty(b.n_sum, dtype=torch.float64, device=dev),
+                torch.empty(b.h_sum, dtype=torch.float64, device=dev),
+                torch.empty(b.n_sum, dtype=torch.float64, device=dev))
+    y, J, H, g = bufs()
+    r_sep = torch.empty(b.K, dtype=torch.float64, device=dev)
+    b.use_graph(False)
+    b.eval_dev(xc, lc, y, J, H, g)
+    b.residual_dev(xc, yc, r_sep)
+    torch.cuda.synchronize()
+    ref = [t.cpu().numpy() for t in (r_sep, J, H, g)]
+    yo = np.concatenate([onn.value(raw[k], xs[k]) for k in range(len(raw))])
+    assert np.max(np.abs(ref[0] - (yv - yo))) <= 1e-10 * max(1.0, np.max(np.abs(yo)))
+    for graph in (False, True, True):
+        b.use_graph(graph)
+        r, J2, H2, g2 = bufs()
+        b.eval_kkt_dev(xc, yc, lc, r, J2, H2, g2)
+        torch.cuda.synchronize()
+        for a, c in zip([t.cpu().numpy() for t in (r, J2, H2, g2)], ref):
+            assert np.array_equal(a, c)
+    b.free()
