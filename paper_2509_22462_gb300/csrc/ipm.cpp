@@ -1733,6 +1733,10 @@ struct Scopf : IpmProblem {
     gather(v);
     int r = nnc_batch_eval(b, xc.data(), nullptr, nullptr, Jc.data(), nullptr, nullptr);
     if (r) return r;
+    fill_jac(AD, AS);
+    return NNC_OK;
+  }
+  void fill_jac(double* AD, double* AS) {
     par_zero(AD, (size_t)m * nd);
     par_zero(AS, (size_t)m * ns);
     for (int k = 0; k < K; ++k) {
@@ -1740,13 +1744,27 @@ struct Scopf : IpmProblem {
       AS[(size_t)k * ns + k] = 1.0;
     }
     for (int i = 0; i < G; ++i) AD[(size_t)K * nd + i] = 1.0;
-    return NNC_OK;
   }
   int hess(const double* v, const double* lam, double* WDD, double* WSS) override {
     gather(v);
     for (int k = 0; k < K; ++k) lc[k] = lam[k];
     int r = nnc_batch_eval(b, xc.data(), lc.data(), nullptr, nullptr, Hc.data(), nullptr);
     if (r) return r;
+    fill_wdd(WDD, WSS);
+    return NNC_OK;
+  }
+  bool joint() const override { return true; }
+  int jac_hess(const double* v, const double* lam, double* AD, double* AS, double* WDD,
+               double* WSS) override {
+    gather(v);
+    for (int k = 0; k < K; ++k) lc[k] = lam[k];
+    int r = nnc_batch_eval(b, xc.data(), lc.data(), nullptr, Jc.data(), Hc.data(), nullptr);
+    if (r) return r;
+    fill_jac(AD, AS);
+    fill_wdd(WDD, WSS);
+    return NNC_OK;
+  }
+  void fill_wdd(double* WDD, double* WSS) {
     std::fill(WDD, WDD + (size_t)nd * nd, 0.0);
     for (int i = 0; i < G; ++i) WDD[(size_t)i * nd + i] = 2.0 * cost[i];
     long long h = 0;
@@ -1758,7 +1776,6 @@ struct Scopf : IpmProblem {
       h += (long long)n * n;
     }
     std::fill(WSS, WSS + ns, 0.0);
-    return NNC_OK;
   }
 };
 
