@@ -16,6 +16,7 @@
 // and returns.
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdio>
 
 #include "kernels.cuh"
@@ -737,6 +738,196 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   }
 }
 
+// ---------------------------------------------------------------- persistent grouped tangent GEMM
+// The grouped tangent GEMM of a batch (many networks, each with its own W_l and its own tangent
+// count) as a persistent kernel: one CTA per SM takes the (network, 128-row block) tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...; the copy ring runs on across tiles, and two TMEM
+// accumulators (2 x 256 columns) let the epilogue of one tile run while the MMAs of the next
+// accumulate, so the short tiles of a batch (K = a hidden width) do not each pay a prologue and
+// an unoverlapped epilogue.  Same operands and outputs as TC_TANGENT_G.
+template <int BN, int MODE>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tc_gtan(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
+              const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
+              const TcArgs args, int groups) {
+  using C = Cfg<BN, MODE>;
+  constexpr bool X3 = C::X3;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + C::STAGES * C::STAGE_BYTES);
+  uint64_t* empty = full + C::STAGES;
+  uint64_t* accf = empty + C::STAGES;   // [2]: accumulator b holds a finished tile
+  uint64_t* tfree = accf + 2;           // [2]: the epilogue has read accumulator b
+  uint64_t* mdone = tfree + 2;          // every MMA issued has completed
+  uint32_t* tmem_slot = (uint32_t*)(mdone + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  volatile int* consumed_sh = (volatile int*)(tmem_slot + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tiles = groups * args.ntm;
+  const int nkb = args.nkb;
+  if (nkb <= 0 || (int)blockIdx.x >= tiles) return;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&accf[b]), 1);
+      mbar_init(smem_u32(&tfree[b]), 4);   // one arrival per epilogue warp
+    }
+    mbar_init(smem_u32(mdone), 1);
+    *abort_flag = 0;
+    *consumed_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  int issued = 0;  // producer only
+  if (warp == 0) {
+    if (lane == 0) {
+      int i = 0;
+      bool stop = false;
+      for (int t = blockIdx.x; t < tiles && !stop; t += gridDim.x) {
+        const int grp = t / args.ntm, tm = t % args.ntm;
+        const int a_row0 = grp * args.a_group_rows + tm * BM;
+        const int b_row0 = args.g_boff[grp];
+        for (int kb = 0; kb < nkb; ++kb, ++i) {
+          const int s = i % C::STAGES;
+          const uint32_t ph = (uint32_t)(i / C::STAGES) & 1u;
+          if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1u, args.err, 41, abort_flag)) {
+            stop = true;
+            break;
+          }
+          uint8_t* st = smem + s * C::STAGE_BYTES;
+          const uint32_t fb = smem_u32(&full[s]);
+          mbar_expect_tx(fb, C::TX_BYTES);
+          const int kx = kb * C::BKE;
+          tma_load_2d(smem_u32(st), &ta_hi, fb, kx, a_row0);
+          if (X3) tma_load_2d(smem_u32(st + C::A_BYTES), &ta_lo, fb, kx, a_row0);
+          tma_load_2d(smem_u32(st + C::NPARTS * C::A_BYTES), &tb_hi, fb, kx, b_row0);
+          if (X3) tma_load_2d(smem_u32(st + C::NPARTS * C::A_BYTES + C::B_BYTES), &tb_lo, fb, kx, b_row0);
+          issued = i + 1;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int i = 0, pi = 0;
+      bool stop = false;
+      for (int t = blockIdx.x; t < tiles && !stop; t += gridDim.x, ++pi) {
+        const int grp = t / args.ntm;
+        const int b = pi & 1;
+        if (pi >= 2 &&
+            !mbar_wait(smem_u32(&tfree[b]), (uint32_t)((pi - 2) >> 1) & 1u, args.err, 42, abort_flag))
+          break;
+        tc_fence_after();
+        const int n_eff = (min(BN, args.g_n[grp]) + 15) / 16 * 16;
+        const uint32_t idesc = C::IDESC_NO_N | ((uint32_t)(n_eff >> 3) << 17);
+        const uint32_t d = tmem + (uint32_t)(b * 256);
+        for (int kb = 0; kb < nkb; ++kb, ++i) {
+          const int s = i % C::STAGES;
+          const uint32_t ph = (uint32_t)(i / C::STAGES) & 1u;
+          if (!mbar_wait(smem_u32(&full[s]), ph, args.err, 43, abort_flag)) {
+            stop = true;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = smem_u32(smem + s * C::STAGE_BYTES);
+          const uint32_t a_hi = st, a_lo = st + C::A_BYTES;
+          const uint32_t b_hi = st + C::NPARTS * C::A_BYTES;
+          const uint32_t b_lo = b_hi + C::B_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < C::ROWB / 32; ++kk) {
+            const uint32_t off = kk * 32;
+            constexpr int SW = C::SWZ, SB = C::SBO;
+            umma_bf16(d, sdesc<SW, SB>(a_hi + off), sdesc<SW, SB>(b_hi + off), idesc,
+                      (kb > 0 || kk > 0) ? 1u : 0u);
+            if (X3) {
+              umma_bf16(d, sdesc<SW, SB>(a_hi + off), sdesc<SW, SB>(b_lo + off), idesc, 1u);
+              umma_bf16(d, sdesc<SW, SB>(a_lo + off), sdesc<SW, SB>(b_hi + off), idesc, 1u);
+            }
+          }
+          umma_commit(smem_u32(&empty[s]));
+        }
+        if (!stop) umma_commit(smem_u32(&accf[b]));
+      }
+      *consumed_sh = i;
+      umma_commit(smem_u32(mdone));
+    }
+  } else {
+    const int q = warp & 3;  // TMEM lanes 32q .. 32q+31 belong to this warp
+    const int row = q * 32 + lane;
+    int pi = 0;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++pi) {
+      const int grp = t / args.ntm, tm = t % args.ntm;
+      const int b = pi & 1;
+      if (!mbar_wait(smem_u32(&accf[b]), (uint32_t)(pi >> 1) & 1u, args.err, 44, abort_flag)) break;
+      tc_fence_after();
+      const int n_valid = args.g_n[grp];
+      const int n_eff = (min(BN, n_valid) + 15) / 16 * 16;
+      const int b_row0 = args.g_boff[grp];
+      const int m = tm * BM + row;                   // row of W_l inside the group
+      const int ms = grp * args.a_group_rows + m;    // stacked row
+      const float sm = (float)args.s1[ms];
+      const float cm = args.c ? args.c[ms] : 0.f;
+      const uint32_t dt = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 256);
+#pragma unroll 1
+      for (int c0 = 0; c0 < n_eff; c0 += 16) {
+        float v[16];
+        tmem_ld16(dt + (uint32_t)c0, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int n = c0 + j;
+          if (n < n_valid) {
+            const size_t orow = (size_t)(b_row0 + n);
+            if (args.at_hi) put<X3>(args.at_hi, args.at_lo, orow * args.ldo + m, sm * v[j]);
+            if (args.zt_hi) put<X3>(args.zt_hi, args.zt_lo, orow * args.ldz + m, v[j]);
+            if (args.yt_hi) put<X3>(args.yt_hi, args.yt_lo, orow * args.ldz + m, cm * v[j]);
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&tfree[b]));
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1 && lane == 0) {
+    // every MMA this CTA issued has completed before its memory goes away (bounded)
+    volatile int no_abort = 0;
+    mbar_wait(smem_u32(mdone), 0, args.err, 45, &no_abort, *abort_flag ? kWaitCycles / 8 : kWaitCycles);
+  }
+  if (*abort_flag && warp == 0 && lane == 0) {
+    for (int i = *consumed_sh; i < issued; ++i) {
+      const int s = i % C::STAGES;
+      const uint32_t ph = (uint32_t)(i / C::STAGES) & 1u;
+      volatile int no_abort = 0;
+      mbar_wait(smem_u32(&full[s]), ph, args.err, 46, &no_abort, kWaitCycles / 8);
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512)
+                 : "memory");
+  }
+}
+
 // Self-test of the tensor-core kernels' bounded wait (with the CTA abort flag): an mbarrier that
 // nothing arrives on; the wait gives up after `limit` cycles, records `code` and sets the flag,
 // which a second wait then sees at once.
@@ -947,6 +1138,9 @@ int tc_plan_make(TcPlan& p, int kind, int prec, const void* a_hi, const void* a_
     if (bn > 256) return NNC_ERR_UNSUPPORTED;
     p.bn = kind == TC_SYRK_G ? 128 : pick;
     p.ntm = kind == TC_TANGENT_G ? M / BM : 0;
+    // grouped tangent GEMMs in the BF16 forms run persistently (one CTA per SM over the tiles)
+    p.persistent = kind == TC_TANGENT_G && (p.mode == MODE_BF16 || p.mode == MODE_BF16X3);
+    p.sm_count = sm_count;
     p.ntn = 1;
     p.splits = force_splits ? force_splits : 1;
     if (p.splits > nkb) p.splits = nkb;
@@ -1043,6 +1237,28 @@ cudaError_t tc_tangent(const TcPlan& p, const double* s1, const float* c, void* 
   return launch_any<TC_TANGENT>(p, a, dim3(p.ntn * p.ntm, 1, 1), st);
 }
 
+template <int BN, int MODE>
+cudaError_t launch_gtan_t(const TcPlan& p, const TcArgs& a, int groups, int grid, cudaStream_t st) {
+  using C = Cfg<BN, MODE>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gtan<BN, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_tc_gtan<BN, MODE><<<grid, kThreads, C::SMEM, st>>>(p.ta_hi, p.ta_lo, p.tb_hi, p.tb_lo, a, groups);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <int BN>
+cudaError_t launch_gtan_mode(const TcPlan& p, const TcArgs& a, int groups, int grid, cudaStream_t st) {
+  if (p.mode == MODE_BF16X3) return launch_gtan_t<BN, MODE_BF16X3>(p, a, groups, grid, st);
+  if (p.mode == MODE_BF16) return launch_gtan_t<BN, MODE_BF16>(p, a, groups, grid, st);
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t tc_tangent_grouped(const TcPlan& p, int groups, const int* g_n, const int* g_boff,
                                const double* s1, const float* c, void* at_hi, void* at_lo, int ldo,
                                void* zt_hi, void* zt_lo, void* yt_hi, void* yt_lo, int ldz,
@@ -1070,6 +1286,16 @@ cudaError_t tc_tangent_grouped(const TcPlan& p, int groups, const int* g_n, cons
   a.g_n = g_n;
   a.g_boff = g_boff;
   a.a_group_rows = p.M;
+  if (p.persistent) {
+    const int grid = std::min(p.sm_count, groups * p.ntm);
+    switch (p.bn) {
+      case 112: return launch_gtan_mode<112>(p, a, groups, grid, st);
+      case 128: return launch_gtan_mode<128>(p, a, groups, grid, st);
+      case 208: return launch_gtan_mode<208>(p, a, groups, grid, st);
+      case 256: return launch_gtan_mode<256>(p, a, groups, grid, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   return launch_any<TC_TANGENT_G>(p, a, dim3(p.ntm, groups, 1), st);
 }
 

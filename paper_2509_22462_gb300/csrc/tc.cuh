@@ -27,6 +27,8 @@ struct TcPlan {
   int bk = 64;          // K block (elements) of a pipeline stage
   int mode = 0;         // 0 BF16, 1 split-BF16x3, 2 FP8 e4m3 (tangent GEMM only)
   int pair = 0;         // tangent GEMM on SM pairs (cta_group::2, 256-row tiles, bn = pair tile)
+  int persistent = 0;   // grouped tangent GEMM: one CTA per SM over all (network, row block) tiles
+  int sm_count = 0;
   int ntm = 0, ntn = 0; // tiles along M and N (pair plans: 256-row blocks)
   int splits = 1, kb_per_split = 0;
   bool ready = false;
