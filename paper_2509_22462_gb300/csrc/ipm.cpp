@@ -17,6 +17,7 @@
 // positive definite, inertia(K) = (n_D, 0, 0) + inertia(S) (Haynsworth); otherwise the whole K
 // is factorized by Bunch-Kaufman.  Either way the inertia is exact.
 #include <cuda_runtime.h>
+#include <omp.h>
 
 #include <algorithm>
 #include <chrono>
@@ -82,49 +83,117 @@ void par_zero(double* x, size_t n) {
 }
 
 // ---------------------------------------------------------------- dense linear algebra
+// Diagonal block of the blocked Cholesky (rows and columns kb .. kb + nb of A, fully updated),
+// factorized transposed so that every update is a contiguous axpy: Dt[j * nb + c] = L[c][j]
+// (c >= j), dinv[j] = 1 / L[j][j]; L is written back into A.  False on a pivot (before its square
+// root) not above min_pivot.
+bool chol_diag(int n, double* A, int kb, int nb, double* Dt, double* dinv, double min_pivot) {
+  for (int i = 0; i < nb; ++i)
+    for (int j = 0; j <= i; ++j) Dt[(size_t)j * nb + i] = A[(size_t)(kb + i) * n + kb + j];
+  for (int j = 0; j < nb; ++j) {
+    double* cj = Dt + (size_t)j * nb;
+    double d = cj[j];
+    if (!(d > min_pivot) || !std::isfinite(d)) return false;
+    d = std::sqrt(d);
+    cj[j] = d;
+    const double inv = 1.0 / d;
+    dinv[j] = inv;
+    for (int i = j + 1; i < nb; ++i) cj[i] *= inv;
+    for (int c = j + 1; c < nb; ++c) {
+      const double f = cj[c];
+      double* cc = Dt + (size_t)c * nb;
+      for (int i = c; i < nb; ++i) cc[i] -= f * cj[i];
+    }
+  }
+  for (int i = 0; i < nb; ++i)
+    for (int j = 0; j <= i; ++j) A[(size_t)(kb + i) * n + kb + j] = Dt[(size_t)j * nb + i];
+  return true;
+}
+
 // Row-major n x n, lower triangle.  Returns false if the matrix is not positive definite, or if a
-// pivot (before its square root) is not above min_pivot.
+// pivot (before its square root) is not above min_pivot.  Right-looking, blocks of NB columns; per
+// block, in one parallel region:
+//  - panel L21 = A21 L11^-T, solved transposed (Pt[j][i] = L21[i][j], rows padded to a multiple of
+//    8) in chunks of CH rows: 16 columns at a time by axpys, the later columns updated by a
+//    4 x 8 register-tiled product;
+//  - trailing update A22 -= L21 L21^T on the lower triangle in 8 x 4 tiles (32 accumulators); the
+//    row tiles of the next diagonal block go first to one thread, which then factorizes that block
+//    while the others update the rest (the diagonal factorization leaves the critical path).
 bool cholesky(int n, double* A, double min_pivot = 0.0) {
-  const int NB = 64;
-  std::vector<double> Pt;   // L21^T of the current block column, rows padded to a multiple of 8
+  constexpr int NB = 32, CH = 32;
+  std::vector<double> Dbuf[2] = {std::vector<double>((size_t)NB * NB), std::vector<double>((size_t)NB * NB)};
+  std::vector<double> ibuf[2] = {std::vector<double>(NB), std::vector<double>(NB)};
+  std::vector<double> Pt;
+  int cur = 0;
+  if (n > 0 && !chol_diag(n, A, 0, std::min(NB, n), Dbuf[0].data(), ibuf[0].data(), min_pivot))
+    return false;
   for (int kb = 0; kb < n; kb += NB) {
     const int nb = std::min(NB, n - kb);
-    // diagonal block (unblocked, right-looking)
-    for (int j = kb; j < kb + nb; ++j) {
-      double d = A[(size_t)j * n + j];
-      if (!(d > min_pivot) || !std::isfinite(d)) return false;
-      d = std::sqrt(d);
-      A[(size_t)j * n + j] = d;
-      for (int i = j + 1; i < kb + nb; ++i) A[(size_t)i * n + j] /= d;
-      for (int i = j + 1; i < kb + nb; ++i) {
-        const double lij = A[(size_t)i * n + j];
-        for (int p = j + 1; p <= i; ++p) A[(size_t)i * n + p] -= lij * A[(size_t)p * n + j];
-      }
-    }
     const int r0 = kb + nb;
     const int rem = n - r0;
     if (rem <= 0) break;
-    // panel below, L21 = A21 L11^-T row by row, copied transposed (rows padded to a multiple of 8)
-    // so that each step of the update's K loop is an outer product of contiguous vectors; then
-    // A22 -= L21 L21^T on the lower triangle in 8 x 4 tiles (32 accumulators in registers)
+    const double* Dt = Dbuf[cur].data();
+    const double* dinv = ibuf[cur].data();
+    double* Dn = Dbuf[1 - cur].data();
+    double* in = ibuf[1 - cur].data();
+    const int nb2 = std::min(NB, rem);
+    bool ok2 = true;
     const int rp = (rem + 7) / 8 * 8;
-    Pt.assign((size_t)nb * rp, 0.0);
+    Pt.resize((size_t)nb * rp);
+    const int nch = (rp + CH - 1) / CH;
 #pragma omp parallel
     {
-#pragma omp for schedule(static)
-      for (int i = r0; i < n; ++i) {
-        double* ai = A + (size_t)i * n;
-        for (int j = kb; j < kb + nb; ++j) {
-          const double* aj = A + (size_t)j * n;
-          double s = ai[j];
-          for (int p = kb; p < j; ++p) s -= ai[p] * aj[p];
-          ai[j] = s / aj[j];
-          Pt[(size_t)(j - kb) * rp + (i - r0)] = ai[j];
+#pragma omp for schedule(dynamic, 1)
+      for (int ch = 0; ch < nch; ++ch) {
+        const int i0 = ch * CH, i1 = std::min(rp, i0 + CH);
+        for (int i = i0; i < i1; ++i) {
+          if (i < rem) {
+            const double* ai = A + (size_t)(r0 + i) * n + kb;
+            for (int j = 0; j < nb; ++j) Pt[(size_t)j * rp + i] = ai[j];
+          } else {
+            for (int j = 0; j < nb; ++j) Pt[(size_t)j * rp + i] = 0.0;
+          }
+        }
+        for (int jb = 0; jb < nb; jb += 16) {
+          const int je = std::min(nb, jb + 16);
+          for (int j = jb; j < je; ++j) {
+            double* pj = &Pt[(size_t)j * rp];
+            const double inv = dinv[j];
+            for (int i = i0; i < i1; ++i) pj[i] *= inv;
+            const double* lj = Dt + (size_t)j * nb;
+            for (int c = j + 1; c < je; ++c) {
+              const double f = lj[c];
+              double* pc = &Pt[(size_t)c * rp];
+              for (int i = i0; i < i1; ++i) pc[i] -= f * pj[i];
+            }
+          }
+          for (int c0 = je; c0 < nb; c0 += 4) {
+            const int cn = std::min(4, nb - c0);
+            for (int i = i0; i < i1; i += 8) {
+              double acc[4][8] = {};
+              for (int j = jb; j < je; ++j) {
+                const double* pj = &Pt[(size_t)j * rp + i];
+                const double* lj = Dt + (size_t)j * nb + c0;
+                double lv[4];
+                for (int v = 0; v < 4; ++v) lv[v] = v < cn ? lj[v] : 0.0;
+                for (int v = 0; v < 4; ++v)
+                  for (int u = 0; u < 8; ++u) acc[v][u] += lv[v] * pj[u];
+              }
+              for (int v = 0; v < cn; ++v) {
+                double* pc = &Pt[(size_t)(c0 + v) * rp + i];
+                for (int u = 0; u < 8; ++u) pc[u] -= acc[v][u];
+              }
+            }
+          }
+        }
+        for (int i = i0; i < std::min(i1, rem); ++i) {
+          double* ai = A + (size_t)(r0 + i) * n + kb;
+          for (int j = 0; j < nb; ++j) ai[j] = Pt[(size_t)j * rp + i];
         }
       }
       const int nti = rp / 8;
-#pragma omp for schedule(dynamic, 1)
-      for (int ti = nti - 1; ti >= 0; --ti) {   // long rows first
+      const int nd8 = (nb2 + 7) / 8;   // row tiles that hold the next diagonal block
+      auto tile_row = [&](int ti) {
         const int i0 = ti * 8;
         for (int p0 = 0; p0 < i0 + 8; p0 += 4) {
           double acc[8][4] = {};
@@ -141,8 +210,17 @@ bool cholesky(int n, double* A, double min_pivot = 0.0) {
             for (int v = 0; v < 4 && p0 + v <= i0 + u; ++v) ai[p0 + v] -= acc[u][v];
           }
         }
+      };
+#pragma omp single nowait
+      {
+        for (int ti = 0; ti < nd8; ++ti) tile_row(ti);
+        ok2 = chol_diag(n, A, r0, nb2, Dn, in, min_pivot);
       }
+#pragma omp for schedule(dynamic, 1)
+      for (int ti = nti - 1; ti >= nd8; --ti) tile_row(ti);   // long rows first
     }
+    if (!ok2) return false;
+    cur = 1 - cur;
   }
   return true;
 }
@@ -204,6 +282,31 @@ void upper_solve_lt(int n, const double* L, double* x) {
   }
 }
 
+// Dot product with four partial sums (four independent multiply-add chains).
+inline double dot4(const double* a, const double* b, int len) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int j = 0;
+  for (; j + 4 <= len; j += 4) {
+    s0 += a[j] * b[j];
+    s1 += a[j + 1] * b[j + 1];
+    s2 += a[j + 2] * b[j + 2];
+    s3 += a[j + 3] * b[j + 3];
+  }
+  for (; j < len; ++j) s0 += a[j] * b[j];
+  return (s0 + s1) + (s2 + s3);
+}
+
+// Y^T t for Y row-major nd x r: the rows of Y are added in order (contiguous, vectorizable).
+inline std::vector<double> ytmul(int nd, int r, const double* Y, const double* t) {
+  std::vector<double> out(r, 0.0);
+  for (int i = 0; i < nd; ++i) {
+    const double ti = t[i];
+    const double* yi = Y + (size_t)i * r;
+    for (int a = 0; a < r; ++a) out[a] += yi[a] * ti;
+  }
+  return out;
+}
+
 // L x = b in place for one right-hand side, blocked like upper_solve_lt.
 void lower_solve1(int n, const double* L, double* x) {
   const int NB = 64;
@@ -211,24 +314,19 @@ void lower_solve1(int n, const double* L, double* x) {
     const int k1 = std::min(n, k0 + NB);
     for (int i = k0; i < k1; ++i) {
       const double* li = L + (size_t)i * n;
-      double s = x[i];
-      for (int j = k0; j < i; ++j) s -= li[j] * x[j];
-      x[i] = s / li[i];
+      x[i] = (x[i] - dot4(li + k0, x + k0, i - k0)) / li[i];
     }
 #pragma omp parallel for schedule(static) if (n - k1 >= 512)
-    for (int i = k1; i < n; ++i) {
-      const double* li = L + (size_t)i * n;
-      double s = 0.0;
-      for (int j = k0; j < k1; ++j) s += li[j] * x[j];
-      x[i] -= s;
-    }
+    for (int i = k1; i < n; ++i) x[i] -= dot4(L + (size_t)i * n + k0, x + k0, k1 - k0);
   }
 }
 
 // Bunch-Kaufman symmetric indefinite factorization P A P^T = L D L^T (Golub & Van Loan,
-// "Matrix Computations", Sec. 4.4), row-major, only the lower triangle is read and updated
-// (symmetric row / column interchanges act on it directly).  Records the pivot sequence and the
-// inertia of A (via Sylvester's law from the 1x1 / 2x2 blocks of D).
+// "Matrix Computations", Sec. 4.4), row-major.  The lower triangle of the input is read; the
+// factorization keeps the whole symmetric matrix, so that the pivot column (= row k), the row of
+// a candidate pivot and both rows of an interchange are contiguous.  On return the lower triangle
+// holds L below the diagonal and D on it (and at (k + 1, k) for a 2 x 2 block); the pivot sequence
+// and the inertia of A (Sylvester's law on the 1 x 1 / 2 x 2 blocks of D) are recorded.
 struct BK {
   int n = 0;
   std::vector<double> A;     // factored in place: L below the diagonal, D on/near it
@@ -237,74 +335,94 @@ struct BK {
   int npos = 0, nneg = 0, nzero = 0;
   bool factor(int n_, const double* src, double zero_tol) {
     n = n_;
-    A.assign(src, src + (size_t)n * n);
+    A.resize((size_t)n * n);
+    for (int i = 0; i < n; ++i) {
+      std::memcpy(&A[(size_t)i * n], src + (size_t)i * n, sizeof(double) * (i + 1));
+      for (int j = 0; j < i; ++j) A[(size_t)j * n + i] = src[(size_t)i * n + j];
+    }
     perm.resize(n);
     step.assign(n, 0);
     for (int i = 0; i < n; ++i) perm[i] = i;
     npos = nneg = nzero = 0;
     const double alpha = (1.0 + std::sqrt(17.0)) / 8.0;
-    auto a = [&](int i, int j) -> double& { return A[(size_t)i * n + j]; };   // i >= j
-    // interchange rows and columns r and s of the symmetric matrix held in the lower triangle
-    auto swap_rc = [&](int r, int s) {
-      if (r == s) return;
-      if (r > s) std::swap(r, s);
-      for (int j = 0; j < r; ++j) std::swap(a(r, j), a(s, j));
-      std::swap(a(r, r), a(s, s));
-      for (int j = r + 1; j < s; ++j) std::swap(a(j, r), a(s, j));
-      for (int j = s + 1; j < n; ++j) std::swap(a(j, r), a(j, s));
-      std::swap(perm[r], perm[s]);
-    };
-    std::vector<double> l1(n, 0.0), l2(n, 0.0), w1(n, 0.0), w2(n, 0.0);
-    int k = 0, kstep = 1;
-    bool zero_col = false;
-    double inv = 0.0;
-    // One parallel region for the whole factorization: the pivot choice and the interchanges run
-    // on one thread, the trailing updates are shared; the barriers of the single / for constructs
-    // order the steps (k, kstep and zero_col change only inside single blocks).
+    std::vector<double> w1(n, 0.0), w2(n, 0.0);
+    // Shared state of the current step, written by the single thread that chooses the pivot:
+    // kc the pivot index, ks its block size, zc a zero column, (sr, ss) the interchange (ss < 0:
+    // none), the inverse of D's block (i11, i21, i22; 1 x 1: i11).  It is read only between the
+    // single's barrier and the step's closing barrier; each thread advances its own copy k of the
+    // pivot index there, so no thread can see a later step's value in the loop test.
+    int kc = 0, ks = 1, sr = 0, ss = -1;
+    bool zc = false;
+    double i11 = 0.0, i21 = 0.0, i22 = 0.0;
+    constexpr int kRows = 8;   // rows per ownership chunk: chunk c belongs to thread c % threads
+    // One parallel region: per step the pivot choice and the interchange run on one thread (rows
+    // only), then every thread applies the interchange's column swap to its own rows and updates
+    // them; each row stays with one thread for the whole factorization (its cache).
 #pragma omp parallel if (n > 256)
     {
+      const int tid = omp_get_thread_num(), nt = omp_get_num_threads();
+      int k = 0;
       while (k < n) {
 #pragma omp single
         {
-          const double absakk = std::fabs(a(k, k));
+          kc = k;
+          double* rk = &A[(size_t)k * n];
+          const double absakk = std::fabs(rk[k]);
           int imax = k;
           double colmax = 0.0;
-          for (int i = k + 1; i < n; ++i)
-            if (std::fabs(a(i, k)) > colmax) {
-              colmax = std::fabs(a(i, k));
-              imax = i;
+          for (int j = k + 1; j < n; ++j)
+            if (std::fabs(rk[j]) > colmax) {
+              colmax = std::fabs(rk[j]);
+              imax = j;
             }
-          kstep = 1;
-          zero_col = std::max(absakk, colmax) <= zero_tol;
-          if (zero_col) {
+          ks = 1;
+          ss = -1;
+          zc = std::max(absakk, colmax) <= zero_tol;
+          if (zc) {
             ++nzero;
             step[k] = 1;
+            rk[k] = 0.0;
           } else {
             int kp = k;
             if (absakk < alpha * colmax) {
+              const double* ri = &A[(size_t)imax * n];
               double rowmax = 0.0;   // largest off-diagonal of row imax inside the trailing block
-              for (int j = k; j < imax; ++j) rowmax = std::max(rowmax, std::fabs(a(imax, j)));
-              for (int j = imax + 1; j < n; ++j) rowmax = std::max(rowmax, std::fabs(a(j, imax)));
+              for (int j = k; j < n; ++j)
+                if (j != imax) rowmax = std::max(rowmax, std::fabs(ri[j]));
               if (absakk >= alpha * colmax * (colmax / rowmax)) {
                 kp = k;
-              } else if (std::fabs(a(imax, imax)) >= alpha * rowmax) {
+              } else if (std::fabs(ri[imax]) >= alpha * rowmax) {
                 kp = imax;
               } else {
                 kp = imax;
-                kstep = 2;
+                ks = 2;
               }
             }
-            swap_rc(k + kstep - 1, kp);
-            step[k] = kstep;
-            if (kstep == 1) {
-              const double d = a(k, k);
+            const int r = k + ks - 1;
+            if (kp != r) {
+              // symmetric interchange of r and kp: the two rows here (with their column swap),
+              // the column swap of every other trailing row by its owner
+              double* ar = &A[(size_t)r * n];
+              double* as = &A[(size_t)kp * n];
+              for (int j = 0; j < n; ++j) std::swap(ar[j], as[j]);
+              std::swap(ar[r], ar[kp]);
+              std::swap(as[r], as[kp]);
+              if (ks == 2) std::swap(rk[r], rk[kp]);
+              std::swap(perm[r], perm[kp]);
+              sr = r;
+              ss = kp;
+            }
+            step[k] = ks;
+            if (ks == 1) {
+              const double d = rk[k];
               if (std::fabs(d) <= zero_tol) ++nzero;
               else if (d > 0) ++npos;
               else ++nneg;
-              inv = d != 0.0 ? 1.0 / d : 0.0;
-              for (int i = k + 1; i < n; ++i) l1[i] = a(i, k);
+              i11 = d != 0.0 ? 1.0 / d : 0.0;
+              std::memcpy(&w1[k + 1], &rk[k + 1], sizeof(double) * (n - k - 1));
             } else {
-              const double d11 = a(k, k), d21 = a(k + 1, k), d22 = a(k + 1, k + 1);
+              const double* rk1 = &A[(size_t)(k + 1) * n];
+              const double d11 = rk[k], d21 = rk1[k], d22 = rk1[k + 1];
               const double det = d11 * d22 - d21 * d21;
               if (det < 0) {
                 ++npos;
@@ -316,52 +434,40 @@ struct BK {
               } else {
                 nneg += 2;
               }
-              const double i11 = d22 / det, i22 = d11 / det, i21 = -d21 / det;
-              // W = A(k+2:, k:k+2); L = W D^-1
-              for (int i = k + 2; i < n; ++i) {
-                w1[i] = a(i, k);
-                w2[i] = a(i, k + 1);
-                l1[i] = w1[i] * i11 + w2[i] * i21;
-                l2[i] = w1[i] * i21 + w2[i] * i22;
-              }
+              i11 = d22 / det;
+              i22 = d11 / det;
+              i21 = -d21 / det;
+              std::memcpy(&w1[k + 2], &rk[k + 2], sizeof(double) * (n - k - 2));
+              std::memcpy(&w2[k + 2], &rk1[k + 2], sizeof(double) * (n - k - 2));
             }
           }
         }
-        if (!zero_col && kstep == 1) {
-          // trailing update A22 -= a21 a21^T / d on the lower triangle
-#pragma omp for schedule(dynamic, 16)
-          for (int i = k + 1; i < n; ++i) {
-            const double f = l1[i] * inv;
-            if (f == 0.0) continue;
-            double* ai = &a(i, 0);
-            for (int j = k + 1; j <= i; ++j) ai[j] -= f * l1[j];
-          }
-        } else if (!zero_col) {
-          // A22 -= W D^-1 W^T (lower triangle)
-#pragma omp for schedule(dynamic, 16)
-          for (int i = k + 2; i < n; ++i) {
-            double* ai = &a(i, 0);
-            const double f1 = l1[i], f2 = l2[i];
-            for (int j = k + 2; j <= i; ++j) ai[j] -= f1 * w1[j] + f2 * w2[j];
-          }
-        }
-#pragma omp single
-        {
-          if (zero_col) {
-            a(k, k) = 0.0;
-            for (int i = k + 1; i < n; ++i) a(i, k) = 0.0;
-            k += 1;
-          } else if (kstep == 1) {
-            for (int i = k + 1; i < n; ++i) a(i, k) = l1[i] * inv;
-            k += 1;
-          } else {
-            for (int i = k + 2; i < n; ++i) {
-              a(i, k) = l1[i];
-              a(i, k + 1) = l2[i];
+        // rows below the pivot block: pending column swap, multipliers L = a D^-1 (stored in the
+        // pivot columns) and the trailing update of the whole row
+        const int i_lo = kc + ks;
+        for (int c = tid; c * kRows < n; c += nt) {
+          const int c0 = std::max(c * kRows, i_lo), c1 = std::min(n, (c + 1) * kRows);
+          for (int i = c0; i < c1; ++i) {
+            double* ai = &A[(size_t)i * n];
+            if (ss >= 0 && i != ss) std::swap(ai[sr], ai[ss]);
+            if (zc) {
+              ai[kc] = 0.0;
+            } else if (ks == 1) {
+              const double f = ai[kc] * i11;
+              ai[kc] = f;
+              if (f != 0.0)
+                for (int j = kc + 1; j < n; ++j) ai[j] -= f * w1[j];
+            } else {
+              const double f1 = ai[kc] * i11 + ai[kc + 1] * i21;
+              const double f2 = ai[kc] * i21 + ai[kc + 1] * i22;
+              ai[kc] = f1;
+              ai[kc + 1] = f2;
+              for (int j = kc + 2; j < n; ++j) ai[j] -= f1 * w1[j] + f2 * w2[j];
             }
-            k += 2;
           }
         }
+        k = kc + ks;
+#pragma omp barrier
       }
     }
     return true;
@@ -783,9 +889,9 @@ struct KktSolver {
       if (nd) lower_solve1(nd, K11.data(), tmp.data());
       std::vector<double> q(nz + m);
       for (int k = 0; k < nz; ++k) q[k] = rhs[nd + zid[k]];
+      const std::vector<double> yt = ytmul(nd, m, Y.data(), tmp.data());   // A_D K11^-1 r1 = Y^T t
       for (int j = 0; j < m; ++j) {
-        double s = rhs[n + j];
-        for (int i = 0; i < nd; ++i) s -= Y[(size_t)i * m + j] * tmp[i];
+        double s = rhs[n + j] - yt[j];
         const double* ra = &AS_[(size_t)j * ns];
         for (int c = 0; c < ns; ++c)
           if (ra[c] != 0.0) s -= ra[c] * Dinv[c] * rhs[nd + c];
@@ -793,22 +899,10 @@ struct KktSolver {
       }
       bkR.solve(q.data());
       const double* z = q.data() + nz;
-      std::vector<double> u(rhs, rhs + nd), yz(nd, 0.0);
-      for (int i = 0; i < nd; ++i) {
-        double s = 0;
-        for (int j = 0; j < m; ++j) s += Y[(size_t)i * m + j] * z[j];
-        yz[i] = s;
-      }
-      for (int i = nd - 1; i >= 0; --i) {   // A_D^T z = L (Y z)
-        double s = 0;
-        const double* li = &K11[(size_t)i * nd];
-        for (int j = 0; j <= i; ++j) s += li[j] * yz[j];
-        u[i] -= s;
-      }
-      if (nd) {
-        lower_solve1(nd, K11.data(), u.data());
-        upper_solve_lt(nd, K11.data(), u.data());
-      }
+      // u = K11^-1 (r1 - A_D^T z) with L^-1 (r1 - A_D^T z) = t - Y z: one backward solve
+      std::vector<double> u(nd);
+      for (int i = 0; i < nd; ++i) u[i] = tmp[i] - dot4(&Y[(size_t)i * m], z, m);
+      if (nd) upper_solve_lt(nd, K11.data(), u.data());
       for (int c = 0; c < ns; ++c) {
         double s = rhs[nd + c];
         for (int j = 0; j < m; ++j) s -= AS_[(size_t)j * ns + c] * z[j];
@@ -824,9 +918,9 @@ struct KktSolver {
       tmp.assign(rhs, rhs + nd);
       if (nd) lower_solve1(nd, K11.data(), tmp.data());     // t = L^-1 r1; A_D K11^-1 r1 = Y^T t
       std::vector<double> z(m);
+      const std::vector<double> yt = ytmul(nd, m, Y.data(), tmp.data());
       for (int j = 0; j < m; ++j) {
-        double s = rhs[n + j];
-        for (int i = 0; i < nd; ++i) s -= Y[(size_t)i * m + j] * tmp[i];
+        double s = rhs[n + j] - yt[j];
         const double* ra = &AS_[(size_t)j * ns];
         for (int c = 0; c < ns; ++c)
           if (ra[c] != 0.0) s -= ra[c] * Dinv[c] * rhs[nd + c];
@@ -839,25 +933,10 @@ struct KktSolver {
       } else {
         bkT.solve(z.data());
       }
-      std::vector<double> u(rhs, rhs + nd);
-      // r1 - A_D^T z, with A_D^T = L Y (Y = L^-1 A_D^T is stored): A_D^T z = L (Y z)
-      std::vector<double> yz(nd, 0.0);
-      for (int i = 0; i < nd; ++i) {
-        double s = 0;
-        for (int j = 0; j < m; ++j) s += Y[(size_t)i * m + j] * z[j];
-        yz[i] = s;
-      }
-      // L yz
-      for (int i = nd - 1; i >= 0; --i) {
-        double s = 0;
-        const double* li = &K11[(size_t)i * nd];
-        for (int j = 0; j <= i; ++j) s += li[j] * yz[j];
-        u[i] -= s;
-      }
-      if (nd) {
-        lower_solve1(nd, K11.data(), u.data());
-        upper_solve_lt(nd, K11.data(), u.data());
-      }
+      // u = K11^-1 (r1 - A_D^T z) with L^-1 (r1 - A_D^T z) = t - Y z (Y = L^-1 A_D^T is stored)
+      std::vector<double> u(nd);
+      for (int i = 0; i < nd; ++i) u[i] = tmp[i] - dot4(&Y[(size_t)i * m], z.data(), m);
+      if (nd) upper_solve_lt(nd, K11.data(), u.data());
       for (int c = 0; c < ns; ++c) {
         double s = rhs[nd + c];
         for (int j = 0; j < m; ++j) s -= AS_[(size_t)j * ns + c] * z[j];
@@ -871,21 +950,12 @@ struct KktSolver {
     tmp.assign(rhs, rhs + nd);
     if (nd) lower_solve1(nd, K11.data(), tmp.data());
     std::vector<double> w(r);
-    for (int a = 0; a < r; ++a) {
-      double s = 0;
-      for (int i = 0; i < nd; ++i) s += Y[(size_t)i * r + a] * tmp[i];
-      w[a] = rhs[nd + a] - s;
-    }
+    const std::vector<double> yt = ytmul(nd, r, Y.data(), tmp.data());
+    for (int a = 0; a < r; ++a) w[a] = rhs[nd + a] - yt[a];
     bkS.solve(w.data());
-    for (int i = 0; i < nd; ++i) {
-      double s = rhs[i];
-      for (int a = 0; a < r; ++a) s -= K12[(size_t)i * r + a] * w[a];
-      tmp[i] = s;
-    }
-    if (nd) {
-      lower_solve1(nd, K11.data(), tmp.data());
-      upper_solve_lt(nd, K11.data(), tmp.data());
-    }
+    // u = K11^-1 (r1 - K12 w) with L^-1 (r1 - K12 w) = t - Y w (Y = L^-1 K12)
+    for (int i = 0; i < nd; ++i) tmp[i] -= dot4(&Y[(size_t)i * r], w.data(), r);
+    if (nd) upper_solve_lt(nd, K11.data(), tmp.data());
     for (int i = 0; i < nd; ++i) rhs[i] = tmp[i];
     for (int a = 0; a < r; ++a) rhs[nd + a] = w[a];
   }
