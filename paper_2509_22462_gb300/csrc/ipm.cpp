@@ -83,7 +83,8 @@ void par_zero(double* x, size_t n) {
 }
 
 // ---------------------------------------------------------------- dense linear algebra
-// Diagonal block of the blocked Cholesky (rows and columns kb .. kb + nb of A, fully updated),
+// Diagonal block of the blocked Cholesky (rows and columns kb .. kb + nb of A, row stride n,
+// fully updated),
 // factorized transposed so that every update is a contiguous axpy: Dt[j * nb + c] = L[c][j]
 // (c >= j), dinv[j] = 1 / L[j][j]; L is written back into A.  False on a pivot (before its square
 // root) not above min_pivot.
@@ -110,33 +111,36 @@ bool chol_diag(int n, double* A, int kb, int nb, double* Dt, double* dinv, doubl
   return true;
 }
 
-// Row-major n x n, lower triangle.  Returns false if the matrix is not positive definite, or if a
-// pivot (before its square root) is not above min_pivot.  Right-looking, blocks of NB columns; per
-// block, in one parallel region:
+// Partial Cholesky of a bordered matrix: A is N x N, row-major with row stride ld, lower triangle;
+// its leading nc columns are factorized (the leading nc x nc block becomes L11, the rows below it
+// L21 = A21 L11^-T) and the trailing block becomes A22 - L21 L21^T (nc = N: the plain Cholesky
+// factor).  Returns false if the leading block is not positive definite, or if a pivot (before its
+// square root) is not above min_pivot.  Right-looking, blocks of NB columns; per block, in one
+// parallel region:
 //  - panel L21 = A21 L11^-T, solved transposed (Pt[j][i] = L21[i][j], rows padded to a multiple of
 //    8) in chunks of CH rows: 16 columns at a time by axpys, the later columns updated by a
 //    4 x 8 register-tiled product;
 //  - trailing update A22 -= L21 L21^T on the lower triangle in 8 x 4 tiles (32 accumulators); the
 //    row tiles of the next diagonal block go first to one thread, which then factorizes that block
 //    while the others update the rest (the diagonal factorization leaves the critical path).
-bool cholesky(int n, double* A, double min_pivot = 0.0) {
+bool cholesky_bordered(int N, int nc, int ld, double* A, double min_pivot) {
   constexpr int NB = 32, CH = 32;
   std::vector<double> Dbuf[2] = {std::vector<double>((size_t)NB * NB), std::vector<double>((size_t)NB * NB)};
   std::vector<double> ibuf[2] = {std::vector<double>(NB), std::vector<double>(NB)};
   std::vector<double> Pt;
   int cur = 0;
-  if (n > 0 && !chol_diag(n, A, 0, std::min(NB, n), Dbuf[0].data(), ibuf[0].data(), min_pivot))
+  if (nc > 0 && !chol_diag(ld, A, 0, std::min(NB, nc), Dbuf[0].data(), ibuf[0].data(), min_pivot))
     return false;
-  for (int kb = 0; kb < n; kb += NB) {
-    const int nb = std::min(NB, n - kb);
+  for (int kb = 0; kb < nc; kb += NB) {
+    const int nb = std::min(NB, nc - kb);
     const int r0 = kb + nb;
-    const int rem = n - r0;
+    const int rem = N - r0;
     if (rem <= 0) break;
     const double* Dt = Dbuf[cur].data();
     const double* dinv = ibuf[cur].data();
     double* Dn = Dbuf[1 - cur].data();
     double* in = ibuf[1 - cur].data();
-    const int nb2 = std::min(NB, rem);
+    const int nb2 = std::max(0, std::min(NB, nc - r0));   // next diagonal block (0: none)
     bool ok2 = true;
     const int rp = (rem + 7) / 8 * 8;
     Pt.resize((size_t)nb * rp);
@@ -148,7 +152,7 @@ bool cholesky(int n, double* A, double min_pivot = 0.0) {
         const int i0 = ch * CH, i1 = std::min(rp, i0 + CH);
         for (int i = i0; i < i1; ++i) {
           if (i < rem) {
-            const double* ai = A + (size_t)(r0 + i) * n + kb;
+            const double* ai = A + (size_t)(r0 + i) * ld + kb;
             for (int j = 0; j < nb; ++j) Pt[(size_t)j * rp + i] = ai[j];
           } else {
             for (int j = 0; j < nb; ++j) Pt[(size_t)j * rp + i] = 0.0;
@@ -187,7 +191,7 @@ bool cholesky(int n, double* A, double min_pivot = 0.0) {
           }
         }
         for (int i = i0; i < std::min(i1, rem); ++i) {
-          double* ai = A + (size_t)(r0 + i) * n + kb;
+          double* ai = A + (size_t)(r0 + i) * ld + kb;
           for (int j = 0; j < nb; ++j) ai[j] = Pt[(size_t)j * rp + i];
         }
       }
@@ -206,15 +210,15 @@ bool cholesky(int n, double* A, double min_pivot = 0.0) {
               for (int v = 0; v < 4; ++v) acc[u][v] += a8[u] * b4[v];
           }
           for (int u = 0; u < 8 && i0 + u < rem; ++u) {
-            double* ai = A + (size_t)(r0 + i0 + u) * n + r0;
+            double* ai = A + (size_t)(r0 + i0 + u) * ld + r0;
             for (int v = 0; v < 4 && p0 + v <= i0 + u; ++v) ai[p0 + v] -= acc[u][v];
           }
         }
       };
 #pragma omp single nowait
-      {
+      if (nb2 > 0) {
         for (int ti = 0; ti < nd8; ++ti) tile_row(ti);
-        ok2 = chol_diag(n, A, r0, nb2, Dn, in, min_pivot);
+        ok2 = chol_diag(ld, A, r0, nb2, Dn, in, min_pivot);
       }
 #pragma omp for schedule(dynamic, 1)
       for (int ti = nti - 1; ti >= nd8; --ti) tile_row(ti);   // long rows first
@@ -225,49 +229,22 @@ bool cholesky(int n, double* A, double min_pivot = 0.0) {
   return true;
 }
 
-// L y = b in place (L lower, row-major n x n), for r right-hand sides stored row-major n x r.
-// Blocked by 64 rows: the diagonal block is solved row by row, then the rows below subtract its
-// contribution in parallel (the bulk of the n^2 r / 2 multiply-adds).
-void lower_solve(int n, const double* L, int r, double* B) {
-  const int NB = 64;
-  for (int k0 = 0; k0 < n; k0 += NB) {
-    const int k1 = std::min(n, k0 + NB);
-    for (int i = k0; i < k1; ++i) {
-      const double* li = L + (size_t)i * n;
-      double* bi = B + (size_t)i * r;
-      for (int j = k0; j < i; ++j) {
-        const double l = li[j];
-        if (l == 0.0) continue;
-        const double* bj = B + (size_t)j * r;
-        for (int c = 0; c < r; ++c) bi[c] -= l * bj[c];
-      }
-      const double d = li[i];
-      for (int c = 0; c < r; ++c) bi[c] /= d;
-    }
-#pragma omp parallel for schedule(static) if ((size_t)(n - k1) * r > 4096)
-    for (int i = k1; i < n; ++i) {
-      const double* li = L + (size_t)i * n;
-      double* bi = B + (size_t)i * r;
-      for (int j = k0; j < k1; ++j) {
-        const double l = li[j];
-        if (l == 0.0) continue;
-        const double* bj = B + (size_t)j * r;
-        for (int c = 0; c < r; ++c) bi[c] -= l * bj[c];
-      }
-    }
-  }
+// Plain Cholesky (row-major n x n, lower triangle), as above with no border.
+bool cholesky(int n, double* A, double min_pivot = 0.0) {
+  return cholesky_bordered(n, n, n, A, min_pivot);
 }
 
 // L^T x = y in place for one right-hand side.  Blocked by 64 rows from the end: the diagonal
 // block is solved row by row, then the entries above it subtract its contribution in parallel.
-void upper_solve_lt(int n, const double* L, double* x) {
+void upper_solve_lt(int n, const double* L, double* x, int ld = 0) {
+  if (ld == 0) ld = n;
   const int NB = 64;
   for (int k1 = n; k1 > 0; k1 -= NB) {
     const int k0 = std::max(0, k1 - NB);
     for (int i = k1 - 1; i >= k0; --i) {
-      x[i] /= L[(size_t)i * n + i];
+      x[i] /= L[(size_t)i * ld + i];
       const double xi = x[i];
-      const double* li = L + (size_t)i * n;
+      const double* li = L + (size_t)i * ld;
       for (int j = k0; j < i; ++j) x[j] -= li[j] * xi;
     }
 #pragma omp parallel for schedule(static) if (k0 >= 512)
@@ -275,7 +252,7 @@ void upper_solve_lt(int n, const double* L, double* x) {
       const int j1 = std::min(k0, j0 + 64);
       for (int i = k0; i < k1; ++i) {
         const double xi = x[i];
-        const double* li = L + (size_t)i * n;
+        const double* li = L + (size_t)i * ld;
         for (int j = j0; j < j1; ++j) x[j] -= li[j] * xi;
       }
     }
@@ -308,23 +285,27 @@ inline std::vector<double> ytmul(int nd, int r, const double* Y, const double* t
 }
 
 // L x = b in place for one right-hand side, blocked like upper_solve_lt.
-void lower_solve1(int n, const double* L, double* x) {
+void lower_solve1(int n, const double* L, double* x, int ld = 0) {
+  if (ld == 0) ld = n;
   const int NB = 64;
   for (int k0 = 0; k0 < n; k0 += NB) {
     const int k1 = std::min(n, k0 + NB);
     for (int i = k0; i < k1; ++i) {
-      const double* li = L + (size_t)i * n;
+      const double* li = L + (size_t)i * ld;
       x[i] = (x[i] - dot4(li + k0, x + k0, i - k0)) / li[i];
     }
 #pragma omp parallel for schedule(static) if (n - k1 >= 512)
-    for (int i = k1; i < n; ++i) x[i] -= dot4(L + (size_t)i * n + k0, x + k0, k1 - k0);
+    for (int i = k1; i < n; ++i) x[i] -= dot4(L + (size_t)i * ld + k0, x + k0, k1 - k0);
   }
 }
 
 // Bunch-Kaufman symmetric indefinite factorization P A P^T = L D L^T (Golub & Van Loan,
 // "Matrix Computations", Sec. 4.4), row-major.  The lower triangle of the input is read; the
 // factorization keeps the whole symmetric matrix, so that the pivot column (= row k), the row of
-// a candidate pivot and both rows of an interchange are contiguous.  On return the lower triangle
+// a candidate pivot and both rows of an interchange are contiguous.  Both triangles are updated
+// with the same operand pairs (entry (i, j) and entry (j, i) take the same products), so the
+// matrix stays exactly symmetric and the lower triangle follows the lower-triangle-only
+// recurrence bit for bit.  On return the lower triangle
 // holds L below the diagonal and D on it (and at (k + 1, k) for a 2 x 2 block); the pivot sequence
 // and the inertia of A (Sylvester's law on the 1 x 1 / 2 x 2 blocks of D) are recorded.
 struct BK {
@@ -345,7 +326,8 @@ struct BK {
     for (int i = 0; i < n; ++i) perm[i] = i;
     npos = nneg = nzero = 0;
     const double alpha = (1.0 + std::sqrt(17.0)) / 8.0;
-    std::vector<double> w1(n, 0.0), w2(n, 0.0);
+    // w1, w2: the pivot row(s); g1, g2: the multipliers a D^-1 of every trailing index
+    std::vector<double> w1(n, 0.0), w2(n, 0.0), g1(n, 0.0), g2(n, 0.0);
     // Shared state of the current step, written by the single thread that chooses the pivot:
     // kc the pivot index, ks its block size, zc a zero column, (sr, ss) the interchange (ss < 0:
     // none), the inverse of D's block (i11, i21, i22; 1 x 1: i11).  It is read only between the
@@ -420,6 +402,7 @@ struct BK {
               else ++nneg;
               i11 = d != 0.0 ? 1.0 / d : 0.0;
               std::memcpy(&w1[k + 1], &rk[k + 1], sizeof(double) * (n - k - 1));
+              for (int j = k + 1; j < n; ++j) g1[j] = w1[j] * i11;
             } else {
               const double* rk1 = &A[(size_t)(k + 1) * n];
               const double d11 = rk[k], d21 = rk1[k], d22 = rk1[k + 1];
@@ -439,6 +422,10 @@ struct BK {
               i21 = -d21 / det;
               std::memcpy(&w1[k + 2], &rk[k + 2], sizeof(double) * (n - k - 2));
               std::memcpy(&w2[k + 2], &rk1[k + 2], sizeof(double) * (n - k - 2));
+              for (int j = k + 2; j < n; ++j) {
+                g1[j] = w1[j] * i11 + w2[j] * i21;
+                g2[j] = w1[j] * i21 + w2[j] * i22;
+              }
             }
           }
         }
@@ -453,16 +440,19 @@ struct BK {
             if (zc) {
               ai[kc] = 0.0;
             } else if (ks == 1) {
-              const double f = ai[kc] * i11;
+              // (i, j), j <= i: a_ij -= g_i w_j;  (i, j), j > i: a_ij -= g_j w_i (= entry (j, i))
+              const double f = g1[i], wi = ai[kc];
               ai[kc] = f;
-              if (f != 0.0)
-                for (int j = kc + 1; j < n; ++j) ai[j] -= f * w1[j];
+              if (f != 0.0) {
+                for (int j = kc + 1; j <= i; ++j) ai[j] -= f * w1[j];
+                for (int j = i + 1; j < n; ++j) ai[j] -= g1[j] * wi;
+              }
             } else {
-              const double f1 = ai[kc] * i11 + ai[kc + 1] * i21;
-              const double f2 = ai[kc] * i21 + ai[kc + 1] * i22;
+              const double f1 = g1[i], f2 = g2[i], wi1 = ai[kc], wi2 = ai[kc + 1];
               ai[kc] = f1;
               ai[kc + 1] = f2;
-              for (int j = kc + 2; j < n; ++j) ai[j] -= f1 * w1[j] + f2 * w2[j];
+              for (int j = kc + 2; j <= i; ++j) ai[j] -= f1 * w1[j] + f2 * w2[j];
+              for (int j = i + 1; j < n; ++j) ai[j] -= g1[j] * wi1 + g2[j] * wi2;
             }
           }
         }
@@ -516,8 +506,8 @@ struct BK {
 // K = [[W_DD + diag(sig_D) + dw I, 0, A_D^T], [0, diag(W_SS + sig_S) + dw I, A_S^T],
 //      [A_D, A_S, -dc I]], n = nd + ns primal rows and m constraint rows.
 struct KktSolver {
-  int nd = 0, ns = 0, m = 0, n = 0, r = 0;
-  std::vector<double> K11, K12, Y, Sm, Kfull, tmp, Dinv, T, AS_;
+  int nd = 0, ns = 0, m = 0, n = 0, r = 0, ldk = 0;
+  std::vector<double> K11, Y, Sm, Kfull, tmp, Dinv, T, AS_;
   BK bkS, bkF, bkT, bkR;
   std::vector<int> zid;   // mode 3: small-block variables with a zero diagonal (free, no curvature)
   std::vector<double> R;
@@ -645,13 +635,32 @@ struct KktSolver {
     m = m_;
     n = nd + ns;
     r = ns + m;
-    K11.resize((size_t)nd * nd);
+    // K11 with the constraint rows A_D below it (row stride ldk = nd + m): the partial Cholesky
+    // of its leading nd columns leaves L, the rows Y^T = A_D L^-T and, in the bottom m x m block,
+    // G = -A_D K11^-1 A_D^T
+    ldk = nd + m;
+    K11.resize((size_t)ldk * ldk);
 #pragma omp parallel for schedule(static) if (nd >= 256)
-    for (int i = 0; i < nd; ++i) {
-      std::memcpy(&K11[(size_t)i * nd], &WDD[(size_t)i * nd], sizeof(double) * nd);
-      K11[(size_t)i * nd + i] += sig[i] + dw;
+    for (int i = 0; i < ldk; ++i) {
+      double* ki = &K11[(size_t)i * ldk];
+      if (i < nd) {
+        std::memcpy(ki, &WDD[(size_t)i * nd], sizeof(double) * nd);
+        ki[i] += sig[i] + dw;
+      } else {
+        std::memcpy(ki, &AD[(size_t)(i - nd) * nd], sizeof(double) * nd);
+        std::memset(ki + nd, 0, sizeof(double) * (i - nd + 1));
+      }
     }
-    const bool pd = nd == 0 || cholesky(nd, K11.data());
+    const bool pd = nd == 0 || cholesky_bordered(ldk, nd, ldk, K11.data(), 0.0);
+    auto G = [&](int a, int b) { return K11[(size_t)(nd + std::max(a, b)) * ldk + nd + std::min(a, b)]; };
+    // Y = L^-1 A_D^T (nd x m) from the rows below L
+    auto fill_y = [&](int cols, int off) {
+      Y.assign((size_t)nd * cols, 0.0);
+      for (int j = 0; j < m; ++j) {
+        const double* yj = &K11[(size_t)(nd + j) * ldk];
+        for (int i = 0; i < nd; ++i) Y[(size_t)i * cols + off + j] = yj[i];
+      }
+    };
     bool diag_ok = pd && ns > 0;
     zid.clear();
     for (int a = 0; a < ns && diag_ok; ++a) {
@@ -673,17 +682,13 @@ struct KktSolver {
         Dinv[a] = d > 0.0 ? 1.0 / d : 0.0;
       }
       AS_.assign(AS, AS + (size_t)m * ns);
-      Y.assign((size_t)nd * m, 0.0);
-      for (int i = 0; i < nd; ++i)
-        for (int j = 0; j < m; ++j) Y[(size_t)i * m + j] = AD[(size_t)j * nd + i];
-      if (nd) lower_solve(nd, K11.data(), m, Y.data());
+      fill_y(m, 0);
       const int nz = (int)zid.size(), nr = nz + m;
       R.assign((size_t)nr * nr, 0.0);
 #pragma omp parallel for schedule(dynamic, 4) if (m >= 64)
       for (int a = 0; a < m; ++a) {
         for (int b = 0; b <= a; ++b) {
-          double s = 0;
-          for (int i = 0; i < nd; ++i) s += Y[(size_t)i * m + a] * Y[(size_t)i * m + b];
+          double s = nd ? -G(a, b) : 0.0;   // (A_D K11^-1 A_D^T)[a][b]
           const double* ra = &AS_[(size_t)a * ns];
           const double* rb = &AS_[(size_t)b * ns];
           for (int c = 0; c < ns; ++c)
@@ -712,16 +717,12 @@ struct KktSolver {
       Dinv.resize(ns);
       for (int a = 0; a < ns; ++a) Dinv[a] = 1.0 / (WSS[a] + sig[nd + a] + dw);
       AS_.assign(AS, AS + (size_t)m * ns);
-      Y.assign((size_t)nd * m, 0.0);
-      for (int i = 0; i < nd; ++i)
-        for (int j = 0; j < m; ++j) Y[(size_t)i * m + j] = AD[(size_t)j * nd + i];
-      if (nd) lower_solve(nd, K11.data(), m, Y.data());
+      fill_y(m, 0);
       T.assign((size_t)m * m, 0.0);
 #pragma omp parallel for schedule(dynamic, 4) if (m >= 64)
       for (int a = 0; a < m; ++a) {
         for (int b = 0; b <= a; ++b) {
-          double s = 0;
-          for (int i = 0; i < nd; ++i) s += Y[(size_t)i * m + a] * Y[(size_t)i * m + b];
+          double s = nd ? -G(a, b) : 0.0;
           const double* ra = &AS_[(size_t)a * ns];
           const double* rb = &AS_[(size_t)b * ns];
           for (int c = 0; c < ns; ++c)
@@ -756,12 +757,8 @@ struct KktSolver {
         return;
       }
     }
-    K12.assign((size_t)nd * r, 0.0);
-    for (int i = 0; i < nd; ++i)
-      for (int j = 0; j < m; ++j) K12[(size_t)i * r + ns + j] = AD[(size_t)j * nd + i];
     if (pd) {
-      Y = K12;
-      if (nd) lower_solve(nd, K11.data(), r, Y.data());
+      fill_y(r, ns);   // Y = L^-1 K12, K12 = [0 | A_D^T] (nd x r)
       Sm.assign((size_t)r * r, 0.0);
       for (int a = 0; a < ns; ++a) Sm[(size_t)a * r + a] = WSS[a] + sig[nd + a] + dw;
       for (int j = 0; j < m; ++j)
@@ -770,14 +767,13 @@ struct KktSolver {
           Sm[(size_t)a * r + ns + j] = AS[(size_t)j * ns + a];
         }
       for (int j = 0; j < m; ++j) Sm[(size_t)(ns + j) * r + ns + j] = -dc;
-#pragma omp parallel for schedule(dynamic, 4) if (r >= 64)
-      for (int a = 0; a < r; ++a)
-        for (int b = 0; b <= a; ++b) {
-          double s = 0;
-          for (int i = 0; i < nd; ++i) s += Y[(size_t)i * r + a] * Y[(size_t)i * r + b];
-          Sm[(size_t)a * r + b] -= s;
-          if (b != a) Sm[(size_t)b * r + a] -= s;
-        }
+      // the rows and columns of the multipliers take G = -A_D K11^-1 A_D^T
+      if (nd)
+        for (int a = 0; a < m; ++a)
+          for (int b = 0; b <= a; ++b) {
+            Sm[(size_t)(ns + a) * r + ns + b] += G(a, b);
+            if (b != a) Sm[(size_t)(ns + b) * r + ns + a] += G(a, b);
+          }
       bkS.factor(r, Sm.data(), zero_tol);
       npos = nd + bkS.npos;
       nneg = bkS.nneg;
@@ -886,7 +882,7 @@ struct KktSolver {
       // [w_Z; z] = R^-1 [r2_Z; r3 - A_D K11^-1 r1 - A_P D_P^-1 r2_P]; then u and w_P as in mode 2
       const int nz = (int)zid.size();
       tmp.assign(rhs, rhs + nd);
-      if (nd) lower_solve1(nd, K11.data(), tmp.data());
+      if (nd) lower_solve1(nd, K11.data(), tmp.data(), ldk);
       std::vector<double> q(nz + m);
       for (int k = 0; k < nz; ++k) q[k] = rhs[nd + zid[k]];
       const std::vector<double> yt = ytmul(nd, m, Y.data(), tmp.data());   // A_D K11^-1 r1 = Y^T t
@@ -902,7 +898,7 @@ struct KktSolver {
       // u = K11^-1 (r1 - A_D^T z) with L^-1 (r1 - A_D^T z) = t - Y z: one backward solve
       std::vector<double> u(nd);
       for (int i = 0; i < nd; ++i) u[i] = tmp[i] - dot4(&Y[(size_t)i * m], z, m);
-      if (nd) upper_solve_lt(nd, K11.data(), u.data());
+      if (nd) upper_solve_lt(nd, K11.data(), u.data(), ldk);
       for (int c = 0; c < ns; ++c) {
         double s = rhs[nd + c];
         for (int j = 0; j < m; ++j) s -= AS_[(size_t)j * ns + c] * z[j];
@@ -916,7 +912,7 @@ struct KktSolver {
     if (mode == 2) {
       // z = T^-1 (r3 - A_D K11^-1 r1 - A_S D^-1 r2); u = K11^-1 (r1 - A_D^T z); w = D^-1 (r2 - A_S^T z)
       tmp.assign(rhs, rhs + nd);
-      if (nd) lower_solve1(nd, K11.data(), tmp.data());     // t = L^-1 r1; A_D K11^-1 r1 = Y^T t
+      if (nd) lower_solve1(nd, K11.data(), tmp.data(), ldk);     // t = L^-1 r1; A_D K11^-1 r1 = Y^T t
       std::vector<double> z(m);
       const std::vector<double> yt = ytmul(nd, m, Y.data(), tmp.data());
       for (int j = 0; j < m; ++j) {
@@ -936,7 +932,7 @@ struct KktSolver {
       // u = K11^-1 (r1 - A_D^T z) with L^-1 (r1 - A_D^T z) = t - Y z (Y = L^-1 A_D^T is stored)
       std::vector<double> u(nd);
       for (int i = 0; i < nd; ++i) u[i] = tmp[i] - dot4(&Y[(size_t)i * m], z.data(), m);
-      if (nd) upper_solve_lt(nd, K11.data(), u.data());
+      if (nd) upper_solve_lt(nd, K11.data(), u.data(), ldk);
       for (int c = 0; c < ns; ++c) {
         double s = rhs[nd + c];
         for (int j = 0; j < m; ++j) s -= AS_[(size_t)j * ns + c] * z[j];
@@ -948,14 +944,14 @@ struct KktSolver {
     }
     // [K11 K12; K12^T K22] [u; w] = [r1; r2]: w = S^-1 (r2 - Y^T L^-1 r1), u = K11^-1 (r1 - K12 w)
     tmp.assign(rhs, rhs + nd);
-    if (nd) lower_solve1(nd, K11.data(), tmp.data());
+    if (nd) lower_solve1(nd, K11.data(), tmp.data(), ldk);
     std::vector<double> w(r);
     const std::vector<double> yt = ytmul(nd, r, Y.data(), tmp.data());
     for (int a = 0; a < r; ++a) w[a] = rhs[nd + a] - yt[a];
     bkS.solve(w.data());
     // u = K11^-1 (r1 - K12 w) with L^-1 (r1 - K12 w) = t - Y w (Y = L^-1 K12)
     for (int i = 0; i < nd; ++i) tmp[i] -= dot4(&Y[(size_t)i * r], w.data(), r);
-    if (nd) upper_solve_lt(nd, K11.data(), tmp.data());
+    if (nd) upper_solve_lt(nd, K11.data(), tmp.data(), ldk);
     for (int i = 0; i < nd; ++i) rhs[i] = tmp[i];
     for (int a = 0; a < r; ++a) rhs[nd + a] = w[a];
   }
