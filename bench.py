@@ -30,11 +30,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "hessian_lag_evals_per_s"
 
-# DRAM bytes (read + write) of one tangent-GEMM launch (M = 4096, N = 784, K = 4096) per form and
-# N tile: mean of two launches of the ncu captures summarised in
-# profiles/k_tc_gemm_tangent_784x4096x4096.md; an entry is valid only for the kernel version it
-# was taken on.
-TANGENT_TRAFFIC = {("bf16x3", 208): 81.66e6, ("bf16x3", -208): 81.57e6}
+# DRAM bytes (read + write) of one tangent-GEMM launch per (M, N, K) shape, form and N tile: mean
+# of two launches of the ncu captures summarised in profiles/k_tc_gemm_tangent_784x4096x4096.md
+# (M = 4096, N = 784, K = 4096); an entry is valid only for the shape and kernel version it was
+# taken on, other shapes report null.
+TANGENT_TRAFFIC = {((4096, 784, 4096), "bf16x3", 208): 81.66e6,
+                   ((4096, 784, 4096), "bf16x3", -208): 81.57e6}
 UNIT = "evals/s"
 
 
@@ -77,6 +78,14 @@ def _workload_config(spec, name, prec):
 
 
 # ------------------------------------------------------------------ algorithmic work
+def tangent_shape(spec):
+    """(M, N, K) of the tangent GEMMs Zdot_l = W_l Adot_{l-1} (hidden layers 2 .. L-1, N = n_in),
+    or None when the layers differ in shape."""
+    w = spec.widths
+    shapes = {(w[l], w[0], w[l - 1]) for l in range(2, len(w) - 1)}
+    return shapes.pop() if len(shapes) == 1 else None
+
+
 def hessian_flops(spec):
     """Algorithmic FLOPs of one Hessian by the per-layer sum form that the GPU runs, counted once
     (no padding, no x3): forward tangents 2 n m_l k_l for l >= 2, plus the lower triangle of each
@@ -286,6 +295,17 @@ def scopf_flops(n_in, hidden=1024, depth=5):
     return f
 
 
+def scopf_weight_bytes(raw):
+    """Algorithmic DRAM bytes of one batched step: every weight is read by the double-float value
+    pass (8 B: hi, lo FP32 pair), the FP32 reverse sweep (4 B) and the tangent sweep (4 B: the FP32
+    first layer, BF16 hi + lo for the hidden layers; a linear output layer takes no tangent)."""
+    b = 0
+    for m in raw:
+        P = sum(w.size for w in m.W)
+        b += 8 * P + 4 * P + 4 * (P - m.W[-1].size)
+    return b
+
+
 def run_ours_scopf(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -378,6 +398,7 @@ def run_ours_scopf(args, rank, world, local_rank):
                                     data.delta)
         ipm[args.prec] = res
     fl = scopf_flops(n_in)
+    wb = scopf_weight_bytes(raw)
     if rank == 0:
         out = {"metric": "batched_hessian_lag_evals_per_s", "value": value, "unit": UNIT, "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": el_ms / args.steps,
@@ -387,11 +408,13 @@ def run_ours_scopf(args, rank, world, local_rank):
                    sum(w.size + b.size for w, b in zip(m.W, m.b)) for m in raw)), "G": data.G,
                    "n_in_range": [min(n_in), max(n_in)], "precision_form": args.prec,
                    "l2": "weights exceed L2 (no flush needed)", "cuda_graph": True},
-               "roofline": {"kernel": "grouped k_tc_gemm + all other grouped launches (whole step)",
-                            "bound": "tensor", "achieved": fl / (el_ms / args.steps / 1e3) / 1e12,
-                            "peak": _peaks()[0].get("bf16_tflops_sustained"), "unit": "TFLOP/s",
-                            "frac": fl / (el_ms / args.steps / 1e3) / 1e12 / _peaks()[0].get("bf16_tflops_sustained"),
-                            "traffic": None},
+               "roofline": {"kernel": "whole step (grouped value pass, reverse sweep, persistent "
+                                      "grouped tangent GEMM, symmetric product)",
+                            "bound": "hbm", "achieved": wb / (el_ms / args.steps / 1e3) / 1e9,
+                            "peak": _peaks()[0].get("hbm_gbs"), "unit": "GB/s",
+                            "frac": wb / (el_ms / args.steps / 1e3) / 1e9 / _peaks()[0].get("hbm_gbs"),
+                            "traffic": None, "algorithmic_bytes_per_step": wb,
+                            "tensor_tflops_algorithmic": fl / (el_ms / args.steps / 1e3) / 1e12},
                "cpu_baseline": cpu_baseline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
                "ipm_solve": ipm, "hessian_algorithmic_gflop": fl / 1e9}
         print(json.dumps(out), flush=True)
@@ -491,7 +514,7 @@ def run_ours(args, rank, world, local_rank):
                  "k_tc_gemm (tangent: Zdot_l = W_l Adot_{l-1}, fused sigma' / sigma'' epilogue)")
         roof = {"kernel": kname if args.prec.startswith("bf16") else "k_simt_gemm (tangent)",
                 "bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                "traffic": TANGENT_TRAFFIC.get((args.prec, tangent_bn)),
+                "traffic": TANGENT_TRAFFIC.get((tangent_shape(spec), args.prec, tangent_bn)),
                 "tangent_bn": tangent_bn,
                 "peak_source": f"{peak_src} bf16 sustained",
                 "executed_frac": ach * (3 if args.prec == "bf16x3" else 1) / pk,

@@ -157,6 +157,13 @@ int nnc_batch_info(const nnc_batch* batch, int* K, int* n_out, int* n_sum, long 
 /* Replace the biases of one layer of every net: bias = K x d_{layer+1} host doubles (problem
  * data such as loads entering the first layer; the nets themselves are not changed). */
 int nnc_batch_set_bias(nnc_batch* batch, int layer, const double* bias);
+/* Split-K count of the batch's symmetric product (1..32; the CTAs of each lower-triangle tile
+ * of sum_l Zdot_l^T diag(c_l) Zdot_l share its K = sum of the hidden widths; partial sums in FP32
+ * planes, added in split order).  Pins the plan (reproducible profiles, tuning); drops a
+ * captured graph.  NNC_ERR_ARG outside the range; the plan is unchanged on any error. */
+int nnc_batch_tune_set(nnc_batch* batch, int syrk_splits);
+/* The split-K count in use (0 when no layer has curvature). */
+int nnc_batch_tuning(const nnc_batch* batch, int* syrk_splits);
 /* Capture one evaluation in a CUDA graph on first use and replay it while the device pointers
  * passed to nnc_batch_eval_dev stay the same (enable = 0 drops the graph). */
 int nnc_batch_use_graph(nnc_batch* batch, int enable);

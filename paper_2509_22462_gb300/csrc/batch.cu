@@ -63,6 +63,7 @@ struct nnc_batch {
   void *At[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}}, *Zt[2] = {nullptr, nullptr},
        *Yt[2] = {nullptr, nullptr};
   float* Hp = nullptr;
+  int hp_planes = 0;   // split-K planes Hp holds
   TcPlan plan_syrk;
   int* dev_err = nullptr;
   // device staging for the host-pointer calls
@@ -76,6 +77,7 @@ struct nnc_batch {
   // CUDA graph of one evaluation, keyed by its pointer arguments
   bool use_graph = false;
   cudaGraphExec_t gexec = nullptr;
+  int g_kernels = 0;   // kernel nodes of the captured evaluation
   const void* gkey[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                          nullptr};
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -151,7 +153,7 @@ int batch_eval(nnc_batch* b, const double* x, const double* lam, double* y, doub
   for (int l = b->L - 1; l >= 0; --l) {
     BLayer& Ly = b->layers[l];
     BCK(launch_bgemv_rev(Ly.W32, Ly.kp, Ly.mp, Ly.m, K, b->Zbar[cur], S, b->part, st));
-    const int chunks = bgemv_rev_chunks(Ly.m);
+    const int chunks = bgemv_rev_chunks(Ly.m, Ly.kp);
     if (l > 0) {
       BLayer& Lp = b->layers[l - 1];
       BCK(launch_brev_reduce(b->part, chunks, Ly.kp, Lp.mp, K, S, Lp.s1, Lp.s2, lam_col, nJ,
@@ -299,7 +301,7 @@ int build(nnc_batch* b, nnc_net* const* nets, int K) {
     BAL(Ly.c, (size_t)Ly.mp * K);
     BAL(Ly.c_f, (size_t)Ly.mp * K);
     BAL(Ly.ra, (size_t)Ly.mp * K);
-    part_max = std::max(part_max, (size_t)K * bgemv_rev_chunks(Ly.m) * Ly.kp * b->S);
+    part_max = std::max(part_max, (size_t)K * bgemv_rev_chunks(Ly.m, Ly.kp) * Ly.kp * b->S);
   }
   BAL(b->xs, (size_t)K * b->kp0);
   BAL(b->xs2, (size_t)K * b->kp0);
@@ -342,6 +344,7 @@ int build(nnc_batch* b, nnc_net* const* nets, int K) {
                          b->sm_count);
     if (r != NNC_OK) return bfail(r, "grouped symmetric-product plan failed");
     BAL(b->Hp, (size_t)b->h_sum * b->plan_syrk.splits);
+    b->hp_planes = b->plan_syrk.splits;
   }
   BAL(b->lam, (size_t)K * b->n_out);
   BAL(b->x_in, b->n_sum);
@@ -435,6 +438,37 @@ int nnc_batch_set_bias(nnc_batch* b, int layer, const double* bias) {
   return NNC_OK;
 }
 
+int nnc_batch_tune_set(nnc_batch* b, int syrk_splits) {
+  if (!b || syrk_splits < 1 || syrk_splits > 32) return bfail(NNC_ERR_ARG, "nnc_batch_tune_set: splits in [1, 32]");
+  if (b->K_total == 0) return NNC_OK;
+  BCK(cudaSetDevice(b->device));
+  BCK(cudaStreamSynchronize(b->stream));
+  TcPlan p;
+  int r = tc_plan_make(p, TC_SYRK_G, b->prec, b->Zt[0], b->Zt[1], b->n_sum, b->K_total, b->Yt[0],
+                       b->Yt[1], b->n_sum, b->K_total, b->n_max, b->n_max, b->K_total, b->sm_count,
+                       0, syrk_splits);
+  if (r != NNC_OK) return bfail(r, "grouped symmetric-product plan failed");
+  if (p.splits > b->hp_planes) {
+    float* hp = nullptr;
+    BCK(cudaMalloc(&hp, sizeof(float) * (size_t)b->h_sum * p.splits));
+    b->allocs.push_back(hp);   // the smaller buffer stays allocated until nnc_batch_free
+    b->Hp = hp;
+    b->hp_planes = p.splits;
+  }
+  b->plan_syrk = p;
+  if (b->gexec) {   // the captured graph holds the old plan
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+  }
+  return NNC_OK;
+}
+
+int nnc_batch_tuning(const nnc_batch* b, int* syrk_splits) {
+  if (!b) return bfail(NNC_ERR_ARG, "batch is NULL");
+  if (syrk_splits) *syrk_splits = b->K_total > 0 ? b->plan_syrk.splits : 0;
+  return NNC_OK;
+}
+
 int nnc_batch_use_graph(nnc_batch* b, int enable) {
   if (!b) return bfail(NNC_ERR_ARG, "batch is NULL");
   b->use_graph = enable != 0;
@@ -462,6 +496,16 @@ static int batch_eval_dev(nnc_batch* b, const double* x, const double* yv, const
     cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
     if (r != NNC_OK) return r;
     BCK(e);
+    size_t nn = 0;
+    b->g_kernels = 0;
+    if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess && nn) {
+      std::vector<cudaGraphNode_t> nodes(nn);
+      if (cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess)
+        for (size_t i = 0; i < nn; ++i) {
+          cudaGraphNodeType t;
+          if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++b->g_kernels;
+        }
+    }
     e = cudaGraphInstantiate(&b->gexec, graph, 0);
     cudaGraphDestroy(graph);
     BCK(e);
@@ -472,7 +516,7 @@ static int batch_eval_dev(nnc_batch* b, const double* x, const double* yv, const
     BCK(cudaStreamWaitEvent(b->stream, b->ev_in, 0));
   }
   BCK(cudaGraphLaunch(b->gexec, b->stream));
-  note_launch(1);
+  note_launch(b->g_kernels);
   if (st != b->stream) {
     BCK(cudaEventRecord(b->ev_out, b->stream));
     BCK(cudaStreamWaitEvent(st, b->ev_out, 0));

@@ -9,7 +9,7 @@ cudaError_t launch_bx_scatter(const double* xcat, const int* gn, const int* goff
                               double* xs, float* xf, cudaStream_t st);
 cudaError_t launch_bgemv_rev(const float* W, int ldw, int mp, int m, int groups, const double* Zbar,
                              int S, float* part, cudaStream_t st);
-int bgemv_rev_chunks(int m);
+int bgemv_rev_chunks(int m, int ldw);   // row chunks of a reverse step (ldw: columns)
 cudaError_t launch_brev_reduce(const float* part, int chunks, int kcols, int mp_out, int groups,
                                int S, const double* s1, const double* s2, int lam_col, int nJ,
                                double* Zbar_out, double* c_out, float* c_f, const int* gn,

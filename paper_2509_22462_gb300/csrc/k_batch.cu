@@ -3,6 +3,7 @@
 // Every network's arrays are stacked: group g's rows of layer l start at g * mp_l; its input
 // sits in row g of an n_max-padded block; its tangent rows start at boff[g] (n_g of them).
 // One launch covers the same step of every network.
+#include <algorithm>
 #include <type_traits>
 
 #include "batch.cuh"
@@ -37,19 +38,23 @@ cudaError_t launch_bx_scatter(const double* xcat, const int* gn, const int* goff
 
 
 // Reverse step of every group: part[g][c][kk][s] = sum_{r in chunk c} W_g[r][kk] Zbar_g[r][s]
-// (FP32 weights, FP32 seeds), 256 threads x 4 columns per block, kBRows rows per chunk.
-constexpr int kBRows = 64;
+// (FP32 weights, FP32 seeds), up to 256 threads x 4 columns per block (fewer for short rows, so
+// that no thread of a block is idle), 64 rows per chunk.  Larger chunks cut the partial-sum
+// traffic but leave too few blocks to stream the weights at full rate.
+constexpr int kBRowsMax = 64;
+__host__ __device__ constexpr int brev_rows(int) { return 64; }
 template <int SMAX>
 __global__ void __launch_bounds__(256) k_bgemv_rev(const float* __restrict__ W, int ldw, int mp,
                                                    int m, const double* __restrict__ Zbar, int S,
                                                    int chunks, float* __restrict__ part) {
-  __shared__ float zs[kBRows][SMAX];
+  __shared__ float zs[kBRowsMax][SMAX];
+  const int rows = brev_rows(ldw);
   const int g = blockIdx.z;
-  const int c0 = (blockIdx.x * 256 + threadIdx.x) * 4;
-  const int r0 = blockIdx.y * kBRows;
-  const int nr = min(kBRows, m - r0);
+  const int c0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  const int r0 = blockIdx.y * rows;
+  const int nr = min(rows, m - r0);
   const double* zg = Zbar + (size_t)g * mp * S;
-  for (int i = threadIdx.x; i < kBRows * SMAX; i += 256) {
+  for (int i = threadIdx.x; i < rows * SMAX; i += blockDim.x) {
     const int r = i / SMAX, s = i % SMAX;
     zs[r][s] = (r < nr && s < S) ? (float)zg[(size_t)(r0 + r) * S + s] : 0.f;
   }
@@ -83,19 +88,21 @@ __global__ void __launch_bounds__(256) k_bgemv_rev(const float* __restrict__ W, 
 
 cudaError_t launch_bgemv_rev(const float* W, int ldw, int mp, int m, int groups, const double* Zbar,
                              int S, float* part, cudaStream_t st) {
-  const int chunks = (m + kBRows - 1) / kBRows;
-  dim3 grid((ldw + 1023) / 1024, chunks, groups);
+  const int chunks = bgemv_rev_chunks(m, ldw);
+  // threads: the row's 4-column groups, rounded up to whole warps, at most 256
+  const int threads = std::min(256, (ldw / 4 + 31) / 32 * 32);
+  dim3 grid((ldw + 4 * threads - 1) / (4 * threads), chunks, groups);
   if (S <= 2)
-    k_bgemv_rev<2><<<grid, 256, 0, st>>>(W, ldw, mp, m, Zbar, S, chunks, part);
+    k_bgemv_rev<2><<<grid, threads, 0, st>>>(W, ldw, mp, m, Zbar, S, chunks, part);
   else if (S <= 4)
-    k_bgemv_rev<4><<<grid, 256, 0, st>>>(W, ldw, mp, m, Zbar, S, chunks, part);
+    k_bgemv_rev<4><<<grid, threads, 0, st>>>(W, ldw, mp, m, Zbar, S, chunks, part);
   else
     return cudaErrorInvalidValue;
   note_launch();
   return cudaGetLastError();
 }
 
-int bgemv_rev_chunks(int m) { return (m + kBRows - 1) / kBRows; }
+int bgemv_rev_chunks(int m, int ldw) { return (m + brev_rows(ldw) - 1) / brev_rows(ldw); }
 
 // Sum the chunks of every group; Zbar_out = s1 * Abar (next seeds), c = s2 * Abar[:, lam_col];
 // on the first layer (s1 == NULL): J_cat[goff*nJ + s*n_g + kk] and grad_cat[goff + kk], kk < n_g.
@@ -110,9 +117,12 @@ __global__ void k_brev_reduce(const float* __restrict__ part, int chunks, int kc
   if (idx >= kcols * S) return;
   const int kk = idx / S, s = idx % S;
   const float* pp = part + (size_t)g * chunks * kcols * S + idx;
-  double v = 0.0;
+  // FP32 sums like the products (the reverse sweep is an FP32 recurrence); FP64 only for the
+  // boundary products below, once per output
+  float vf = 0.f;
 #pragma unroll 8
-  for (int c = 0; c < chunks; ++c) v += (double)pp[(size_t)c * kcols * S];
+  for (int c = 0; c < chunks; ++c) vf += pp[(size_t)c * kcols * S];
+  const double v = (double)vf;
   if (s1) {
     const size_t gi = (size_t)g * mp_out + kk;
     if (kk < mp_out) Zbar_out[(size_t)g * mp_out * S + idx] = s1[gi] * v;

@@ -177,7 +177,8 @@ cudaError_t launch_sv(SvArgs a, int sm_count, cudaStream_t st) {
   if (a.nw < 1 || a.nw > kSvMaxWarps || a.m < 1) return cudaErrorInvalidValue;
   a.gw = (groups + a.nw - 1) / a.nw;
   // Two stages per warp suffice; what brings the stream to HBM speed is enough warps per SM
-  // (3-4 CTAs): measured at 6.3 TB/s on a 1 GB matrix (6.6 TB/s with FP32 weights).
+  // (3-4 CTAs): measured at 6.3 TB/s on a 1 GB matrix (6.6 TB/s with FP32 weights).  (Four stages
+  // for one-warp CTAs, the 2 KB rows of a batch's first layer, measured slower: 216 against 154 us.)
   a.ns = 2;
   const int smem = a.nw * a.ns * kSvSlice;
   static bool attr = false;

@@ -167,3 +167,38 @@ def test_fused_residual_matches_separate_calls(nnc, small_batch):
         for a, c in zip([t.cpu().numpy() for t in (r, J2, H2, g2)], ref):
             assert np.array_equal(a, c)
     b.free()
+
+
+def test_syrk_splits_keep_results(nnc, small_batch):
+    """nnc_batch_tune_set: split-K of the symmetric product changes only the FP32 summation order
+    of H (relative change at FP32 rounding level); J and the gradient are untouched.  A graph
+    replay counts its kernel nodes as launches."""
+    import torch
+    data, raw, nets = small_batch
+    b = nnc.Batch(nets)
+    dev = torch.device("cuda:0")
+    x = synth.uniform01(synth.derive_key(5, "bx"), data.G)
+    xc = torch.tensor(b.concat([x[S] for S in data.subsets]), device=dev)
+    lc = torch.tensor(b.concat([np.array([0.5 + 0.1 * k]) for k in range(len(raw))]), device=dev)
+    assert b.tuning() == 1
+    outs = []
+    for splits in (1, 3):
+        b.tune_set(splits)
+        assert b.tuning() == splits
+        b.use_graph(True)
+        y = torch.empty(b.K, dtype=torch.float64, device=dev)
+        J = torch.empty(b.n_sum, dtype=torch.float64, device=dev)
+        H = torch.empty(b.h_sum, dtype=torch.float64, device=dev)
+        g = torch.empty(b.n_sum, dtype=torch.float64, device=dev)
+        b.eval_dev(xc, lc, y, J, H, g)
+        c0 = nnc.launch_count()
+        b.eval_dev(xc, lc, y, J, H, g)
+        torch.cuda.synchronize()
+        assert nnc.launch_count() - c0 > 5
+        outs.append([t.cpu().numpy() for t in (y, J, H, g)])
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    assert rel(outs[1][2], outs[0][2]) <= 1e-5
+    with pytest.raises(nnc.NNCError):
+        b.tune_set(0)
+    assert b.tuning() == 3
+    b.free()
