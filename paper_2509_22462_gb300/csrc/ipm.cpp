@@ -989,6 +989,35 @@ struct IpmProblem {
     const int rc = jac(v, AD, AS);
     return rc ? rc : hess(v, lam, WDD, WSS);
   }
+  // Trial points (joint problems that can): the constraint values at v together with the
+  // Jacobian and Hessian there for the multipliers lam_t that v gets if the step is accepted, from
+  // one network evaluation; jac_hess at exactly (v, lam_t) then reuses them.
+  virtual bool speculative() const { return false; }
+  virtual int cons_spec(const double* v, const double* lam_t, double* c) {
+    (void)lam_t;
+    return cons(v, c);
+  }
+  // true when jac_hess(v, lam) will reuse the derivatives of the last cons_spec
+  virtual bool has_derivs(const double* v, const double* lam) const {
+    (void)v;
+    (void)lam;
+    return false;
+  }
+};
+
+// Derivatives kept from a trial-point evaluation, keyed by the point and the multipliers.
+struct SpecCache {
+  std::vector<double> v, lam;
+  bool valid = false;
+  void store(const double* v_, size_t nv, const double* lam_, size_t nl) {
+    v.assign(v_, v_ + nv);
+    lam.assign(lam_, lam_ + nl);
+    valid = true;
+  }
+  bool match(const double* v_, const double* lam_) const {
+    return valid && std::memcmp(v.data(), v_, sizeof(double) * v.size()) == 0 &&
+           std::memcmp(lam.data(), lam_, sizeof(double) * lam.size()) == 0;
+  }
 };
 
 struct Timers {
@@ -1042,7 +1071,7 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
   int ls_fail = 0, status = NNC_IPM_MAX_ITER, it = 0;
   double E0 = INFINITY;
   std::vector<double> g(n), c(m), AD((size_t)m * nd), AS((size_t)m * ns), WDD((size_t)nd * nd),
-      WSS(ns), vt(n), ct(m), rhs(n + m), sol(n + m), dv(n), dl(m), dzL(n), dzU(n), sL(n), sU(n),
+      WSS(ns), vt(n), ct(m), lam_t(m), rhs(n + m), sol(n + m), dv(n), dl(m), dzL(n), dzU(n), sL(n), sU(n),
       SigL(n), SigU(n), sig(n), gphi(n), atl(n);
   KktSolver kkt;
   // atl = A^T lam, row by row (contiguous reads of the dense Jacobian blocks)
@@ -1115,7 +1144,13 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
     if (!have_c && m) {
       if (timed(T.fn, T.n_fn, [&] { return p.cons(v.data(), c.data()); })) { status = NNC_IPM_EVAL_ERROR; break; }
     }
-    if (m && p.joint()) {
+    if (m && p.joint() && p.has_derivs(v.data(), lam.data())) {
+      // taken with the residual at the accepted trial point (counted there)
+      if (p.jac_hess(v.data(), lam.data(), AD.data(), AS.data(), WDD.data(), WSS.data())) {
+        status = NNC_IPM_EVAL_ERROR;
+        break;
+      }
+    } else if (m && p.joint()) {
       // J and the Hessian of the Lagrangian at (v, lam) in one evaluation (counted as both)
       ++T.n_jac;
       if (timed(T.hess, T.n_hess, [&] {
@@ -1223,12 +1258,30 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
     const double phi0 = merit(v, fv, c, nu);
     double alpha = a_max;
     bool accepted = false;
+    bool spec_taken = false;   // the accepted point is the first trial, evaluated with lam_t
     for (int bt = 0; bt < o.max_backtracks; ++bt) {
       for (int i = 0; i < n; ++i) vt[i] = v[i] + alpha * dv[i];
       const double ft = p.f(vt.data());
-      if (m && timed(T.fn, T.n_fn, [&] { return p.cons(vt.data(), ct.data()); })) { status = NNC_IPM_EVAL_ERROR; break; }
+      if (m && bt == 0 && p.speculative()) {
+        // the first trial is usually accepted: evaluate it with its derivatives (one network
+        // evaluation instead of a residual now and a full evaluation at the next iteration)
+        for (int j = 0; j < m; ++j) lam_t[j] = lam[j] + alpha * dl[j];
+        ++T.n_fn;
+        ++T.n_jac;
+        if (timed(T.hess, T.n_hess, [&] { return p.cons_spec(vt.data(), lam_t.data(), ct.data()); })) {
+          status = NNC_IPM_EVAL_ERROR;
+          break;
+        }
+      } else if (m && timed(T.fn, T.n_fn, [&] { return p.cons(vt.data(), ct.data()); })) {
+        status = NNC_IPM_EVAL_ERROR;
+        break;
+      }
       const double phit = merit(vt, ft, ct, nu);
-      if (std::isfinite(phit) && phit <= phi0 + o.eta * alpha * D) { accepted = true; break; }
+      if (std::isfinite(phit) && phit <= phi0 + o.eta * alpha * D) {
+        accepted = true;
+        spec_taken = bt == 0 && p.speculative();
+        break;
+      }
       alpha *= 0.5;
     }
     if (status == NNC_IPM_EVAL_ERROR) break;
@@ -1242,7 +1295,9 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
     v = vt;
     c = ct;
     have_c = true;
-    for (int j = 0; j < m; ++j) lam[j] += alpha * dl[j];
+    if (spec_taken) lam = lam_t;   // bit for bit the multipliers the trial was evaluated with
+    else
+      for (int j = 0; j < m; ++j) lam[j] += alpha * dl[j];
     for (int i = 0; i < n; ++i) {
       zL[i] += a_z * dzL[i];
       zU[i] += a_z * dzU[i];
@@ -1317,16 +1372,30 @@ struct Adversarial : IpmProblem {
   void grad_f(const double* v, double* g) override {
     for (int i = 0; i < nd + ns; ++i) g[i] = i < n_in ? 2.0 * (v[i] - x0[i]) : 0.0;
   }
-  int cons(const double* v, double* c) override {
-    // y - NN(x) with the FP64 weights (the FP64 residual at step acceptance)
-    int rc = nnc_residual(net, v, v + n_in, r.data());
-    if (rc) return rc;
+  SpecCache spec;
+  void fill_cons(const double* v, double* c) {
     for (int j = 0; j < n_out; ++j) c[j] = r[j];
     const double* y = v + n_in;
     const double* s = v + n_in + n_out;
     for (int k = 0; k < n_out - 1; ++k) c[n_out + k] = y[t] - y[others[k]] - margin - s[k];
+  }
+  int cons(const double* v, double* c) override {
+    // y - NN(x) with the FP64 weights (the FP64 residual at step acceptance)
+    int rc = nnc_residual(net, v, v + n_in, r.data());
+    if (rc) return rc;
+    fill_cons(v, c);
     return NNC_OK;
   }
+  bool speculative() const override { return true; }
+  int cons_spec(const double* v, const double* lam_t, double* c) override {
+    spec.valid = false;
+    int rc = nnc_eval_kkt(net, v, v + n_in, lam_t, r.data(), J.data(), H.data(), nullptr);
+    if (rc) return rc;
+    spec.store(v, nd + ns, lam_t, m);
+    fill_cons(v, c);
+    return NNC_OK;
+  }
+  bool has_derivs(const double* v, const double* lam) const override { return spec.match(v, lam); }
   int jac(const double* v, double* AD, double* AS) override {
     int rc = nnc_jacobian(net, v, J.data());
     if (rc) return rc;
@@ -1364,8 +1433,11 @@ struct Adversarial : IpmProblem {
   bool joint() const override { return true; }
   int jac_hess(const double* v, const double* lam, double* AD, double* AS, double* WDD,
                double* WSS) override {
-    int rc = nnc_eval_kkt(net, v, nullptr, lam, nullptr, J.data(), H.data(), nullptr);
-    if (rc) return rc;
+    if (!spec.match(v, lam)) {   // else J and H are those of the accepted trial point
+      int rc = nnc_eval_kkt(net, v, nullptr, lam, nullptr, J.data(), H.data(), nullptr);
+      if (rc) return rc;
+    }
+    spec.valid = false;
     fill_jac(AD, AS);
     fill_wdd(WDD, WSS);
     return NNC_OK;
@@ -1416,6 +1488,7 @@ struct AdversarialL1 : IpmProblem {
   void grad_f(const double* v, double* g) override {
     for (int i = 0; i < nd + ns; ++i) g[i] = (i >= n_in && i < 3 * n_in) ? 1.0 : 0.0;
   }
+  SpecCache spec;
   int cons(const double* v, double* c) override {
     for (int i = 0; i < n_in; ++i) c[i] = v[i] - v[n_in + i] + v[2 * n_in + i] - xr[i];
     int rc = nnc_residual(net, v, v + 3 * n_in, r.data());   // y - NN(x), FP64-accurate
@@ -1423,6 +1496,17 @@ struct AdversarialL1 : IpmProblem {
     for (int j = 0; j < n_out; ++j) c[n_in + j] = r[j];
     return NNC_OK;
   }
+  bool speculative() const override { return true; }
+  int cons_spec(const double* v, const double* lam_t, double* c) override {
+    spec.valid = false;
+    for (int i = 0; i < n_in; ++i) c[i] = v[i] - v[n_in + i] + v[2 * n_in + i] - xr[i];
+    int rc = nnc_eval_kkt(net, v, v + 3 * n_in, lam_t + n_in, r.data(), J.data(), H.data(), nullptr);
+    if (rc) return rc;
+    for (int j = 0; j < n_out; ++j) c[n_in + j] = r[j];
+    spec.store(v, nd + ns, lam_t, m);
+    return NNC_OK;
+  }
+  bool has_derivs(const double* v, const double* lam) const override { return spec.match(v, lam); }
   void fill_jac(double* AD, double* AS) {
     par_zero(AD, (size_t)m * nd);
     par_zero(AS, (size_t)m * ns);
@@ -1458,8 +1542,11 @@ struct AdversarialL1 : IpmProblem {
   bool joint() const override { return true; }
   int jac_hess(const double* v, const double* lam, double* AD, double* AS, double* WDD,
                double* WSS) override {
-    int rc = nnc_eval_kkt(net, v, nullptr, lam + n_in, nullptr, J.data(), H.data(), nullptr);
-    if (rc) return rc;
+    if (!spec.match(v, lam)) {   // else J and H are those of the accepted trial point
+      int rc = nnc_eval_kkt(net, v, nullptr, lam + n_in, nullptr, J.data(), H.data(), nullptr);
+      if (rc) return rc;
+    }
+    spec.valid = false;
     fill_jac(AD, AS);
     fill_wdd(WDD, WSS);
     return NNC_OK;
