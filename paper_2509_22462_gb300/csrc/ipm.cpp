@@ -12,10 +12,14 @@
 // The network constraint makes the variables split into a dense block D (the network inputs x,
 // whose Hessian block is the dense n_in x n_in matrix of Eq. 6) and a small block S (outputs,
 // slacks) with diagonal Hessian.  The KKT matrix K = [[K11, K12], [K12^T, K22]] with
-// K11 = W_DD + Sigma_D + delta_w I is factorized as: blocked Cholesky of K11 (parallel on the
-// host cores), Schur complement S = K22 - K12^T K11^-1 K12, Bunch-Kaufman LDL^T of S.  If K11 is
-// positive definite, inertia(K) = (n_D, 0, 0) + inertia(S) (Haynsworth); otherwise the whole K
-// is factorized by Bunch-Kaufman.  Either way the inertia is exact.
+// K11 = W_DD + Sigma_D + delta_w I is factorized as: rows that pin one dense variable through
+// slacks of their own eliminated first; a bordered blocked Cholesky of K11 (parallel on the host
+// cores) that also leaves A_D L^-T and the Schur block -A_D K11^-1 A_D^T; Bunch-Kaufman LDL^T of
+// the reduced multiplier system.  If K11 is positive definite, inertia(K) = (n_D, 0, 0) +
+// inertia(Schur complement) (Haynsworth); otherwise Bunch-Kaufman of the dense block with the
+// multipliers (positive small-block diagonals eliminated), or of the whole K.  Either way the
+// inertia is exact.  The first trial point of each line search is evaluated together with its
+// derivatives (problems that can), which the next iteration reuses when the step is accepted.
 #include <cuda_runtime.h>
 #include <omp.h>
 
