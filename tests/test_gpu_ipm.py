@@ -50,6 +50,41 @@ def test_adversarial_tiny_matches_oracle(nnc, tiny_oracle_solution, prec):
     net.free()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_backtracking_step_matches_oracle(nnc, prec):
+    """An instance whose line search backtracks once (x0 seed 2, target 3, margin 3 on the
+    784-128-128-10 net: the oracle evaluates the constraints 2 iters + 2 times): the driver
+    evaluates the first trial of every line search with its derivatives, so here one such
+    evaluation is rejected and the backtracked point is evaluated afresh.  The FP64 form must
+    follow the oracle's iterates (same iteration count, point within 1e-6) with one extra
+    function evaluation; the tensor-core form must reach the same objective."""
+    mlp = make_mlp(synth.TINY, seed=0)
+    d = synth.adversarial_data(seed=2)
+    p = problems.adversarial(mlp, d.x0, 3, 3.0)
+    calls = [0]
+    c_plain = p.c
+
+    def c_counted(v):
+        calls[0] += 1
+        return c_plain(v)
+
+    p.c = c_counted
+    ro = oipm.solve(p)
+    assert ro.status == oipm.OPTIMAL
+    assert calls[0] == 2 * ro.iters + 2          # one backtracking step in the oracle
+    net = nnc.Net.from_mlp(mlp, precision=prec)
+    res, v, lam = nnc.ipm_adversarial(net, d.x0, 3, 3.0)
+    print(f"[ipm backtrack {prec}] iters={res['iters']} (oracle {ro.iters}) obj={res['obj']:.12g} "
+          f"(oracle {ro.obj:.12g}) n_function={res['n_function']} n_hessian={res['n_hessian']}")
+    assert res["status"] == 0 and res["kkt_error"] <= 1e-6
+    assert abs(res["obj"] - ro.obj) <= 1e-6 * abs(ro.obj)
+    if prec == "fp64":
+        assert res["iters"] == ro.iters
+        assert np.max(np.abs(v - ro.v)) < 1e-6
+        assert res["n_function"] == res["iters"] + 2   # the start, one trial per iteration, one backtrack
+    net.free()
+
+
 def test_box_only_network_with_slack_margin(nnc):
     """A net whose margins hold with slack at the start: the solution is x = x0 (objective 0)."""
     spec = MLPSpec([20, 16, 3], ["tanh", "identity"])
