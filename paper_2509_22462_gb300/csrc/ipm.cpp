@@ -1203,6 +1203,7 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
     scale = std::max(scale, max_abs(AS.data(), AS.size()));
     const double zero_tol = 1e-14 * scale;
     int tries = 0;
+    const auto t_fac = Clock::now();
     while (true) {
       ++tries;
       kkt.factor(nd, ns, m, WDD.data(), WSS.data(), sig.data(), AD.data(), AS.data(), delta_w,
@@ -1219,11 +1220,10 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
     }
     if (!ok) { status = NNC_IPM_INERTIA_FAILED; T.solver += secs(t_lin, Clock::now()); break; }
     if (delta_w > 0.0) delta_w_last = delta_w;
-    if (o.verbose)
-      std::printf("          kkt mode %d, %d factorization(s), delta_w %.1e, %.1f ms\n", kkt.mode, tries,
-                  delta_w, 1e3 * secs(t_lin, Clock::now()));
+    const auto t_sol = Clock::now();
     sol = rhs;
     kkt.solve(sol.data());
+    const auto t_sol_end = Clock::now();
     for (int i = 0; i < n; ++i) dv[i] = sol[i];
     for (int j = 0; j < m; ++j) dl[j] = sol[n + j];
     for (int i = 0; i < n; ++i) {
@@ -1259,6 +1259,11 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
     }
     const double D = dphi - nu * c1;
     T.solver += secs(t_lin, Clock::now());
+    if (o.verbose)
+      std::printf("          kkt mode %d, %d factorization(s), delta_w %.1e: factor %.2f ms, solve %.2f ms, "
+                  "step set-up %.2f ms\n", kkt.mode, tries, delta_w, 1e3 * secs(t_fac, t_sol),
+                  1e3 * secs(t_sol, t_sol_end),
+                  1e3 * (secs(t_lin, Clock::now()) - secs(t_fac, t_sol) - secs(t_sol, t_sol_end)));
     const double phi0 = merit(v, fv, c, nu);
     double alpha = a_max;
     bool accepted = false;
