@@ -221,6 +221,20 @@ def time_oracle(mlp, d, budget_s=12.0, max_steps=20):
                       f"Hessian, FP64 residual) in {el:.1f} s, numpy FP64 with multithreaded BLAS"}
 
 
+def time_oracle_ipm(mlp, d):
+    """The oracle interior-point method (numpy FP64, eigenvalue inertia) on the adversarial
+    problem, solved to KKT 1e-6 on the host cores: the CPU column of the IPM comparison."""
+    from oracle import ipm as oipm, problems as oproblems
+    t0 = time.perf_counter()
+    r = oipm.solve(oproblems.adversarial(mlp, d.x0, d.target, d.margin))
+    el = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"status": int(r.status), "iters": int(r.iters), "obj": float(r.obj),
+            "kkt_error": float(r.kkt_error), "solve_seconds": el, "cores": cores,
+            "kind": "oracle (numpy FP64 on the host cores: forward-over-reverse Hessian, "
+                    "eigenvalue inertia)"}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -431,8 +445,11 @@ def run_ours(args, rank, world, local_rank):
 
     spec, mlp, d = _workload(args.workload)
     cpu_baseline = None
+    oracle_ipm = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu_baseline = time_oracle(mlp, d)  # before the first GPU call
+        if not args.no_ipm and spec.acts[-1] != "softmax":
+            oracle_ipm = time_oracle_ipm(mlp, d)
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -559,6 +576,8 @@ def run_ours(args, rank, world, local_rank):
     ipm = {}
     if rank == 0 and not args.no_ipm:
         ipm[args.prec] = solve(net)
+    if oracle_ipm is not None:
+        ipm["oracle"] = oracle_ipm
 
     # the FP64 form on the same GPU, for the TC-vs-FP64 comparison of the metric
     forms = {args.prec: {"evals_per_s": value / world, "ms_per_eval": el_ms / args.steps}}
