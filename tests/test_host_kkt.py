@@ -203,3 +203,65 @@ def test_bunch_kaufman_through_whole_matrix(nnc, n, seed):
     assert (npos, nneg, nzero) == (int((ev > 0).sum()), int((ev < 0).sum()), 0)
     ref = np.linalg.solve(K, rhs)
     assert np.linalg.norm(x - ref) <= 1e-8 * np.linalg.norm(ref)
+
+
+def _check(nnc, W, WSS, sig, AD, AS, K, rhs, dw=0.0, dc=0.0, tol=1e-8):
+    x, (npos, nneg, nzero, full) = nnc.kkt_solve(W, WSS, sig, AD, AS, rhs, delta_w=dw, delta_c=dc)
+    ev = np.linalg.eigvalsh(K)
+    assert (npos, nneg, nzero) == (int((ev > 0).sum()), int((ev < 0).sum()), 0)
+    ref = np.linalg.solve(K, rhs)
+    assert np.linalg.norm(x - ref) <= tol * np.linalg.norm(ref)
+    return full
+
+
+@pytest.mark.parametrize("nd,ns,m", [(97, 11, 7), (600, 19, 19), (785, 9, 30)])
+def test_bordered_cholesky_many_blocks(nnc, nd, ns, m):
+    """Definite dense blocks spanning many column blocks with a ragged last block (the
+    constraint rows below the block are carried through the same factorization): inertia
+    (n, m, 0) and the solution against the plain definitions."""
+    W, WSS, sig, AD, AS, K = _kkt(nd, ns, m, seed=nd + 3, indefinite=False, dw=0.05, dc=1e-6)
+    rhs = np.random.default_rng(nd).standard_normal(nd + ns + m)
+    assert _check(nnc, W, WSS, sig, AD, AS, K, rhs, dw=0.05, dc=1e-6) == 0
+
+
+@pytest.mark.parametrize("nd,ns,m", [(400, 20, 15), (700, 12, 40)])
+def test_indefinite_dense_block_parallel_path(nnc, nd, ns, m):
+    """Indefinite dense blocks large enough for the multithreaded symmetric indefinite
+    factorization (more than 256 rows with the multipliers): inertia and solution."""
+    W, WSS, sig, AD, AS, K = _kkt(nd, ns, m, seed=nd + 5, indefinite=True, dw=0.0, dc=1e-6)
+    WSS[:] = np.abs(WSS)
+    K[nd:nd + ns, nd:nd + ns] = np.diag(WSS + sig[nd:])
+    rhs = np.random.default_rng(nd + 1).standard_normal(nd + ns + m)
+    assert _check(nnc, W, WSS, sig, AD, AS, K, rhs, dc=1e-6) == 0
+
+
+@pytest.mark.parametrize("indef", [False, True])
+def test_pinning_rows_l1_structure_large(nnc, indef):
+    """The L1 structure (Eq. 7 with split variables) at 300 pixels: pinning-row elimination, then
+    the bordered Cholesky or, with an indefinite dense block, the multithreaded indefinite
+    factorization."""
+    W, WSS, sig, AD, AS, K = _l1_kkt(300, 10, seed=301, indefinite=indef, dc=1e-8)
+    rhs = np.random.default_rng(6).standard_normal(K.shape[0])
+    assert _check(nnc, W, WSS, sig, AD, AS, K, rhs, dc=1e-8) == 0
+
+
+def test_no_dense_block_and_no_constraints(nnc):
+    """Degenerate shapes: no dense-block variables (nd = 0), and no constraints (m = 0, the KKT
+    matrix is the positive definite Hessian block alone)."""
+    W = np.zeros((0, 0))
+    rng = np.random.default_rng(13)
+    ns, m = 10, 5
+    WSS = rng.uniform(0.1, 1.0, ns)
+    sig = rng.uniform(0.1, 1.0, ns)
+    AS = rng.standard_normal((m, ns))
+    AD = np.zeros((m, 0))
+    K = np.zeros((ns + m, ns + m))
+    K[:ns, :ns] = np.diag(WSS + sig)
+    K[ns:, :ns] = AS
+    K[:ns, ns:] = AS.T
+    K[ns:, ns:] = -1e-6 * np.eye(m)
+    rhs = rng.standard_normal(ns + m)
+    _check(nnc, W, WSS, sig, AD, AS, K, rhs, dc=1e-6)
+    W, WSS, sig, AD, AS, K = _kkt(330, 4, 0, seed=17, indefinite=False)
+    rhs = np.random.default_rng(17).standard_normal(334)
+    _check(nnc, W, WSS, sig, AD, AS, K, rhs)
