@@ -186,6 +186,13 @@ int nnc_batch_eval_kkt_dev(nnc_batch* batch, const double* x_cat, const double* 
 int nnc_batch_eval(nnc_batch* batch, const double* x_cat, const double* lambda_cat, double* y_cat,
                    double* J_cat, double* H_cat, double* grad_cat);
 int nnc_batch_residual(nnc_batch* batch, const double* x_cat, const double* y_cat, double* r_cat);
+/* Host-pointer twin of nnc_batch_eval_kkt_dev: copies x_cat (and y_cat, lambda_cat) in, returns
+ * r_cat = y_cat - NN(x_cat), J_cat, H_cat and grad_cat (any output may be NULL; y_cat needed for
+ * r_cat, lambda_cat for H_cat or grad_cat) from one value pass, and waits.  The same results as
+ * nnc_batch_residual and nnc_batch_eval, bit for bit. */
+int nnc_batch_eval_kkt(nnc_batch* batch, const double* x_cat, const double* y_cat,
+                       const double* lambda_cat, double* r_cat, double* J_cat, double* H_cat,
+                       double* grad_cat);
 
 /* ---- Learned warm start ---------------------------------------------------------------------
  * An MLP n_in -> h1 -> h2 -> n_out with GELU hidden layers (GELU(z) = z Phi(z)) and a linear

@@ -565,6 +565,38 @@ int nnc_batch_eval(nnc_batch* b, const double* x, const double* lambda, double* 
   return check_dev_err(b);
 }
 
+int nnc_batch_eval_kkt(nnc_batch* b, const double* x, const double* y, const double* lambda, double* r,
+                       double* J, double* H, double* grad) {
+  if (!b || !x || (r && !y) || ((H || grad) && !lambda))
+    return bfail(NNC_ERR_ARG, "nnc_batch_eval_kkt: bad arguments");
+  BCK(cudaSetDevice(b->device));
+  cudaStream_t st = b->stream;
+  const size_t nl = (size_t)b->K * b->n_out;
+  double* hx = b->h_stage;
+  double* hy = hx + b->n_sum;
+  double* hl = hy + nl;
+  std::memcpy(hx, x, sizeof(double) * b->n_sum);
+  BCK(cudaMemcpyAsync(b->x_in, hx, sizeof(double) * b->n_sum, cudaMemcpyHostToDevice, st));
+  if (r) {
+    std::memcpy(hy, y, sizeof(double) * nl);
+    BCK(cudaMemcpyAsync(b->y_in, hy, sizeof(double) * nl, cudaMemcpyHostToDevice, st));
+  }
+  if (lambda) {
+    std::memcpy(hl, lambda, sizeof(double) * nl);
+    BCK(cudaMemcpyAsync(b->lam_in, hl, sizeof(double) * nl, cudaMemcpyHostToDevice, st));
+  }
+  int rc = nnc_batch_eval_kkt_dev(b, b->x_in, r ? b->y_in : nullptr, lambda ? b->lam_in : nullptr,
+                                  r ? b->r_out : nullptr, J ? b->J_out : nullptr,
+                                  H ? b->H_out : nullptr, grad ? b->g_out : nullptr, st);
+  if (rc) return rc;
+  if (r) BCK(cudaMemcpyAsync(r, b->r_out, sizeof(double) * nl, cudaMemcpyDeviceToHost, st));
+  if (J) BCK(cudaMemcpyAsync(J, b->J_out, sizeof(double) * b->n_sum * b->n_out, cudaMemcpyDeviceToHost, st));
+  if (H) BCK(cudaMemcpyAsync(H, b->H_out, sizeof(double) * b->h_sum, cudaMemcpyDeviceToHost, st));
+  if (grad) BCK(cudaMemcpyAsync(grad, b->g_out, sizeof(double) * b->n_sum, cudaMemcpyDeviceToHost, st));
+  BCK(cudaStreamSynchronize(st));
+  return check_dev_err(b);
+}
+
 int nnc_batch_residual(nnc_batch* b, const double* x, const double* y, double* r) {
   if (!b || !x || !y || !r) return bfail(NNC_ERR_ARG, "nnc_batch_residual: bad arguments");
   BCK(cudaSetDevice(b->device));

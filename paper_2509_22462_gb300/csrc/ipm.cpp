@@ -1892,17 +1892,36 @@ struct Scopf : IpmProblem {
   void grad_f(const double* v, double* g) override {
     for (int i = 0; i < nd + ns; ++i) g[i] = i < G ? 2.0 * cost[i] * v[i] : 0.0;
   }
+  SpecCache spec;
+  void fill_cons(const double* v, double* c) {
+    double sx = 0;
+    for (int i = 0; i < G; ++i) sx += v[i];
+    for (int k = 0; k < K; ++k) c[k] = rc[k];
+    c[K] = sx - D;
+  }
   int cons(const double* v, double* c) override {
     gather(v);
     for (int k = 0; k < K; ++k) yc[k] = v[G + k] - shift[k];
     int r = nnc_batch_residual(b, xc.data(), yc.data(), rc.data());
     if (r) return r;
-    double sx = 0;
-    for (int i = 0; i < G; ++i) sx += v[i];
-    for (int k = 0; k < K; ++k) c[k] = rc[k];
-    c[K] = sx - D;
+    fill_cons(v, c);
     return NNC_OK;
   }
+  bool speculative() const override { return true; }
+  int cons_spec(const double* v, const double* lam_t, double* c) override {
+    spec.valid = false;
+    gather(v);
+    for (int k = 0; k < K; ++k) {
+      yc[k] = v[G + k] - shift[k];
+      lc[k] = lam_t[k];
+    }
+    int r = nnc_batch_eval_kkt(b, xc.data(), yc.data(), lc.data(), rc.data(), Jc.data(), Hc.data(), nullptr);
+    if (r) return r;
+    fill_cons(v, c);
+    spec.store(v, nd + ns, lam_t, m);
+    return NNC_OK;
+  }
+  bool has_derivs(const double* v, const double* lam) const override { return spec.match(v, lam); }
   int jac(const double* v, double* AD, double* AS) override {
     gather(v);
     int r = nnc_batch_eval(b, xc.data(), nullptr, nullptr, Jc.data(), nullptr, nullptr);
@@ -1930,10 +1949,13 @@ struct Scopf : IpmProblem {
   bool joint() const override { return true; }
   int jac_hess(const double* v, const double* lam, double* AD, double* AS, double* WDD,
                double* WSS) override {
-    gather(v);
-    for (int k = 0; k < K; ++k) lc[k] = lam[k];
-    int r = nnc_batch_eval(b, xc.data(), lc.data(), nullptr, Jc.data(), Hc.data(), nullptr);
-    if (r) return r;
+    if (!spec.match(v, lam)) {   // else J and H are those of the accepted trial point
+      gather(v);
+      for (int k = 0; k < K; ++k) lc[k] = lam[k];
+      int r = nnc_batch_eval(b, xc.data(), lc.data(), nullptr, Jc.data(), Hc.data(), nullptr);
+      if (r) return r;
+    }
+    spec.valid = false;
     fill_jac(AD, AS);
     fill_wdd(WDD, WSS);
     return NNC_OK;

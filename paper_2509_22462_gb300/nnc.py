@@ -30,7 +30,7 @@ EXPORTS = ["nnc_load_weights", "nnc_eval", "nnc_residual", "nnc_jacobian", "nnc_
            "nnc_kkt_solve",
            "nnc_residual_noalloc", "nnc_batch_create", "nnc_batch_free", "nnc_batch_info",
            "nnc_batch_set_bias", "nnc_batch_use_graph", "nnc_batch_tune_set", "nnc_batch_tuning", "nnc_batch_eval_dev", "nnc_batch_residual_dev", "nnc_batch_eval_kkt_dev",
-           "nnc_batch_eval", "nnc_batch_residual", "nnc_ipm_scopf", "nnc_ws_create", "nnc_ws_free",
+           "nnc_batch_eval", "nnc_batch_residual", "nnc_batch_eval_kkt", "nnc_ipm_scopf", "nnc_ws_create", "nnc_ws_free",
            "nnc_ws_set_scaling", "nnc_ws_loss_grad", "nnc_ws_adam_step", "nnc_ws_train",
            "nnc_ws_predict", "nnc_ws_get_params", "nnc_ipm_scopf_warm", "nnc_autotune", "nnc_tuning", "nnc_tune_set"]
 IPM_STATUS = {0: "optimal", 1: "max_iter", 2: "linesearch_failed", 3: "nonfinite",
@@ -125,6 +125,7 @@ def load_library(path: str = LIB_PATH):
     lib.nnc_batch_eval_kkt_dev.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _P]
     lib.nnc_batch_eval.argtypes = [_P, _DP, _DP, _DP, _DP, _DP, _DP]
     lib.nnc_batch_residual.argtypes = [_P, _DP, _DP, _DP]
+    lib.nnc_batch_eval_kkt.argtypes = [_P, _DP, _DP, _DP, _DP, _DP, _DP, _DP]
     lib.nnc_ipm_scopf.argtypes = [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                   ctypes.POINTER(ctypes.c_int), _DP, ctypes.c_double, _DP,
                                   ctypes.POINTER(IpmOptions), _DP, _DP, ctypes.POINTER(IpmResult)]
@@ -534,6 +535,17 @@ class Batch:
         r = np.empty(self.K * self.n_out)
         _check(_lib.nnc_batch_residual(self._h, _dp(x), _dp(y), _dp(r)))
         return [r[k * self.n_out:(k + 1) * self.n_out] for k in range(self.K)]
+
+    def eval_kkt(self, xs, ys, lams):
+        """nnc_batch_eval_kkt (host arrays): per net the residual y - NN(x), J, H and the gradient
+        lambda^T J from one value pass; returns concatenated (r, J, H, g)."""
+        x, y, lam = self.concat(xs), self.concat(ys), self.concat(lams)
+        r = np.empty(self.K * self.n_out)
+        J = np.empty(self.n_sum * self.n_out)
+        H = np.empty(self.h_sum)
+        g = np.empty(self.n_sum)
+        _check(_lib.nnc_batch_eval_kkt(self._h, _dp(x), _dp(y), _dp(lam), _dp(r), _dp(J), _dp(H), _dp(g)))
+        return r, J, H, g
 
     def eval_dev(self, x, lam=None, y=None, J=None, H=None, g=None, stream=None):
         _check(_lib.nnc_batch_eval_dev(self._h, _tp(x), _tp(lam), _tp(y), _tp(J), _tp(H), _tp(g),

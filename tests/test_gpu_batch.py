@@ -202,3 +202,24 @@ def test_syrk_splits_keep_results(nnc, small_batch):
         b.tune_set(0)
     assert b.tuning() == 3
     b.free()
+
+
+def test_host_eval_kkt_matches_separate_calls(nnc, small_batch):
+    """nnc_batch_eval_kkt (host arrays): the residual, J, H and gradient from one value pass equal
+    nnc_batch_residual and nnc_batch_eval bit for bit, and the residual matches the oracle."""
+    data, raw, nets = small_batch
+    b = nnc.Batch(nets)
+    x = synth.uniform01(synth.derive_key(6, "bx"), data.G)
+    xs = [x[S] for S in data.subsets]
+    lams = [np.array([0.2 + 0.03 * k]) for k in range(len(raw))]
+    ys = [np.array([0.05 * k - 0.3]) for k in range(len(raw))]
+    r, J, H, g = b.eval_kkt(xs, ys, lams)
+    _, Js, Hs, gs = b.eval(xs, lams)        # per-net views of the concatenated outputs
+    r_ref = np.concatenate(b.residual(xs, ys))
+    _, J2, H2, g2 = b.split_outputs(None, J, H, g)
+    assert np.array_equal(r, r_ref)
+    for k in range(len(raw)):
+        assert np.array_equal(J2[k], Js[k]) and np.array_equal(H2[k], Hs[k]) and np.array_equal(g2[k], gs[k])
+    yo = np.concatenate([onn.value(raw[k], xs[k]) for k in range(len(raw))])
+    assert np.max(np.abs(r - (np.concatenate(ys) - yo))) <= 1e-10 * max(1.0, np.max(np.abs(yo)))
+    b.free()
