@@ -6,7 +6,7 @@
    library's forward / backward / Adam kernels (nnc_ws_*).
 3. On held-out loads, predict (x, y, lambda), solve warm-started (nnc_ipm_scopf_warm); if the
    warm solve fails or needs more iterations than the cold cap, fall back to a cold solve and
-   count both.  The cold solve of the same instance is the judge.
+   count both.  The cold solve of the same instance is the reference it is measured against.
 
   python -m paper_2509_22462_gb300.warmstart_experiment --K 256 --train 512 --test 64
 """
