@@ -142,24 +142,32 @@ class Clocks:
         except Exception:
             self.p.kill()
         self.f.flush()
-        rows = []
         with open(self.f.name) as fh:
-            for line in fh:
-                parts = [x.strip() for x in line.split(",")]
-                if len(parts) < 9:
-                    continue
-                try:
-                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
-                except ValueError:
-                    continue
+            out = parse_clock_samples(fh)
         os.unlink(self.f.name)
-        if not rows:
-            return None
-        sm = sorted(r[0] for r in rows)
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[2][i].lower().startswith("active")})
-        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
-                "samples": len(rows)}
+        return out
+
+
+def parse_clock_samples(lines):
+    """nvidia-smi samples (csv, noheader, nounits, the Clocks.FIELDS order) -> the median SM clock
+    under load, the maximum SM clock and the throttle reasons active in any sample; None without
+    samples.  Malformed lines are skipped."""
+    rows = []
+    for line in lines:
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+        except ValueError:
+            continue
+    if not rows:
+        return None
+    sm = sorted(r[0] for r in rows)
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for r in rows for i in range(4) if r[2][i].lower().startswith("active")})
+    return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+            "samples": len(rows)}
 
 
 def _gpu_index(local_rank):

@@ -59,3 +59,20 @@ def test_scopf_weight_bytes():
     n_k = [len(s) for s in data.subsets]
     assert P == sum(n * 1024 + 4 * 1024 * 1024 + 1024 for n in n_k)
     assert bench.scopf_weight_bytes(raw) == 16 * P - 4 * 1024 * len(raw)
+
+
+def test_clock_samples():
+    """The clocks record of a bench line: median SM clock, its maximum, and every throttle reason
+    seen active in any sample (sw_power_cap kept, hardware slowdowns reported)."""
+    lines = [
+        "0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1390.5, 0x4, Not Active, Not Active, Not Active, Active",
+        "garbage line",
+        "0, 2070, 2070, 1100.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, N/A, 2070, 1100.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ]
+    out = bench.parse_clock_samples(lines)
+    assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    hot = bench.parse_clock_samples([lines[0], "0, 1200, 2070, 1400, 0x48, Active, Active, Not Active, Active"])
+    assert hot["reasons"] == ["hw_slowdown", "hw_thermal_slowdown", "sw_power_cap"]
+    assert bench.parse_clock_samples(["garbage"]) is None
