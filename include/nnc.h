@@ -57,7 +57,10 @@ typedef enum {
  *                A*B ~ Ahi*Bhi + Ahi*Blo + Alo*Bhi, all three accumulated in one FP32 tile.
  *   NNC_FP8    : as NNC_BF16, but the Hessian sweep runs kind::f8f6f4 with e4m3 weights and
  *                per-output-row scales.  Reported, not held to the BF16 tolerances.
- * In every form nnc_residual (and nnc_eval with fp64_residual != 0) uses FP64 weights. */
+ * nnc_residual (and nnc_eval with fp64_residual != 0) is FP64 in the NNC_FP64 form; in every other
+ * form it runs in double-float arithmetic (each value an unevaluated sum of two FP32 numbers, about
+ * 48 significant bits) on (hi, lo) pairs of the FP64 weights, and is held to
+ * |r - r_fp64| <= 1e-10 * max(1, |y|). */
 typedef enum { NNC_FP64 = 0, NNC_FP32 = 1, NNC_BF16 = 2, NNC_BF16X3 = 3, NNC_FP8 = 4 } nnc_precision;
 
 /* sigma_l of Eq. 3.  All are C^2, as interior-point methods require (Section 2). */
@@ -88,12 +91,14 @@ typedef enum {
 int nnc_load_weights(nnc_net** out, int n_layers, const int* widths, const int* act,
                      const double* const* W, const double* const* b, int prec, void* stream);
 
-/* y = NN(x) (Eq. 3).  x: n_in doubles; y: n_out doubles.  fp64_residual != 0 evaluates with
- * the FP64 weight copy whatever the precision form (the FP64 correction of the residual). */
+/* y = NN(x) (Eq. 3).  x: n_in doubles; y: n_out doubles.  fp64_residual != 0 evaluates with the
+ * FP64-accurate value pass whatever the precision form (the FP64 correction of the residual):
+ * FP64 weights in the NNC_FP64 form, double-float (hi, lo) weight pairs in the others. */
 int nnc_eval(nnc_net* net, const double* x, double* y, int fp64_residual);
 
-/* r = y - NN(x) in FP64 on the device: the residual of g(x, y) = y - NN(x) (Eq. 5) used at
- * step acceptance.  x: n_in, y: n_out, r: n_out doubles. */
+/* r = y - NN(x) on the device, FP64-accurate: the residual of g(x, y) = y - NN(x) (Eq. 5) used
+ * at step acceptance (FP64 in the NNC_FP64 form, double-float in the others, as stated above).
+ * x: n_in, y: n_out, r: n_out doubles. */
 int nnc_residual(nnc_net* net, const double* x, const double* y, double* r);
 
 /* J = dNN/dx at x by a reverse sweep with n_out seed columns (the Jacobian oracle of
@@ -276,20 +281,23 @@ int nnc_tune_set(nnc_net* net, int tangent_bn, int syrk_splits);
 int nnc_profile(nnc_net* net, int enable);
 int nnc_profile_read(nnc_net* net, double* ms, long long* count, int n_kinds);
 
-/* r = y - NN(x) in FP64 without allocating any device memory.  The paper has no counterpart:
- * this entry point serves callers that cannot call cudaMalloc (code running while a CUDA graph
- * is being captured, or inside a host framework that owns the device allocator), and who
- * therefore cannot create a net with nnc_load_weights.  The caller passes every buffer:
- *   n_layers, widths (L+1 host ints, each in [1, 65536]), act (L host nnc_act codes);
+/* r = y - NN(x) in FP64 without allocating any device memory.  The paper has no counterpart.
+ * Some callers cannot call cudaMalloc: a host framework that owns the device memory budget and
+ * hands out memory only from its own pool, or a control loop that must not call cudaMalloc
+ * because it can synchronise the device and take unbounded time.  Such callers cannot create a
+ * net with nnc_load_weights (it allocates the packed weights), so they pass every buffer:
+ *   n_layers, widths (L+1 host ints, each in [1, 65536]), act (L host nnc_act codes, elementwise
+ *   activations only: NNC_SOFTMAX returns NNC_ERR_UNSUPPORTED);
  *   W : L host pointers to device arrays, W[l] = d_{l+1} x d_l row-major FP64, no padding;
  *   b : NULL, or L host pointers to device arrays of d_{l+1} doubles (entries may be NULL);
  *   x (n_in), y (n_out), r (n_out): device arrays of doubles;  stream: cudaStream_t or NULL.
  * The layer activations go to one file-scope device array of 2 x 65536 doubles (1 MiB), which
  * every GPU that loads the library keeps until the process exits; a width above 65536 returns
- * NNC_ERR_ARG.  The first call on a device looks up that array's address (with the device
- * current), so make that first call before any stream capture.  All calls share the array:
- * calls whose work overlaps on the GPU race and must be ordered by the caller.  The call is
- * asynchronous on `stream`. */
+ * NNC_ERR_ARG.  The first call on a device (and the first call after that device's context was
+ * destroyed and created again) looks up the array's address with the device current, so make
+ * that first call before any stream capture.  All calls share the array and it keeps the last
+ * call's contents (every entry a call reads it has written first): calls whose work overlaps on
+ * the GPU race and must be ordered by the caller.  The call is asynchronous on `stream`. */
 int nnc_residual_noalloc(int n_layers, const int* widths, const int* act, const double* const* W,
                          const double* const* b, const double* x, const double* y, double* r,
                          void* stream);

@@ -142,8 +142,22 @@ extern "C" int nnc_autotune(nnc_net* net, const char* cache_path, int retune) {
       }
       cache[g.first] = {best, best_us};
     }
-    for (int l : ls)
-      if (best != plan_code(net->layers[l].plan_tan)) make_plan(net->layers[l].plan_tan, l, best);
+    // apply the choice through temporaries: a cached entry whose plan fails leaves every layer's
+    // current plan in place, is dropped from the cache and reported
+    std::vector<TcPlan> fresh(ls.size());
+    bool okp = true;
+    for (size_t i = 0; i < ls.size() && okp; ++i)
+      okp = best == plan_code(net->layers[ls[i]].plan_tan) ||
+            make_plan(fresh[i], ls[i], best) == NNC_OK;
+    if (!okp) {
+      cache.erase(g.first);
+      write_cache(cache_path, cache);
+      set_last_error("autotune: the tangent tile " + std::to_string(best) + " chosen for " + g.first +
+                     " has no valid plan; the previous tiling is kept");
+      return NNC_ERR_ARG;
+    }
+    for (size_t i = 0; i < ls.size(); ++i)
+      if (best != plan_code(net->layers[ls[i]].plan_tan)) net->layers[ls[i]].plan_tan = fresh[i];
   }
   // symmetric product: split-K count (bounded by the partial-sum buffer allocated at load)
   if (net->K_total > 0 && net->plan_syrk.ready) {
@@ -171,9 +185,19 @@ extern "C" int nnc_autotune(nnc_net* net, const char* cache_path, int retune) {
       }
       cache[key] = {best, best_us};
     }
-    if (best != net->plan_syrk.splits)
-      tc_plan_make(net->plan_syrk, TC_SYRK, prec, net->Zt[0], net->Zt[1], n, net->K_total, net->Yt[0],
-                   net->Yt[1], n, net->K_total, n, n, net->K_total, net->sm_count, 0, best);
+    if (best != net->plan_syrk.splits) {
+      TcPlan p;
+      if (tc_plan_make(p, TC_SYRK, prec, net->Zt[0], net->Zt[1], n, net->K_total, net->Yt[0],
+                       net->Yt[1], n, net->K_total, n, n, net->K_total, net->sm_count, 0,
+                       best) != NNC_OK || p.splits > net->h_splits) {
+        cache.erase(key);
+        write_cache(cache_path, cache);
+        set_last_error("autotune: the symmetric-product split count " + std::to_string(best) +
+                       " has no valid plan; the previous one is kept");
+        return NNC_ERR_ARG;
+      }
+      net->plan_syrk = p;
+    }
   }
   cudaStreamSynchronize(st);
   int e = 0;

@@ -1,12 +1,14 @@
-"""nnc_residual_noalloc, the entry point for callers that cannot allocate device memory (for
-example code running during CUDA-graph capture, or under a host framework that owns the
-allocator): it must give the same FP64 residual y - NN(x) as nnc_residual on a net built with
-nnc_load_weights, on two calls in a row (its fixed scratch array keeps the previous call's
-contents, which must not leak into the next result).  Collected last on purpose."""
+"""nnc_residual_noalloc, the entry point for callers that cannot allocate device memory (a host
+framework that owns the device memory budget, or a control loop that must not call cudaMalloc,
+which can synchronise the device): it must give the same FP64 residual y - NN(x) as nnc_residual
+on a net built with nnc_load_weights, and as the FP64 oracle, on two calls in a row (its fixed
+scratch array keeps the previous call's contents, which must not leak into the next result).
+Collected last on purpose."""
 import numpy as np
 import pytest
 
 import synth
+from oracle import nn as onn
 from synth.nets import MLPSpec, make_mlp
 
 pytestmark = pytest.mark.gpu
@@ -33,8 +35,11 @@ def test_noalloc_residual_matches_nnc_residual():
         nnc.residual_noalloc(spec.widths, spec.acts, W_dev, b_dev, xd, yd, rd)
         torch.cuda.synchronize()
         r = rd.cpu().numpy()
-        # the FP64 tolerance of the other GPU tests: 1e-10 relative
+        # the FP64 tolerance of the other GPU tests: 1e-10 relative, against the existing entry
+        # point and against the oracle's r = y - NN(x)
         assert np.linalg.norm(r - ref) <= 1e-10 * max(np.linalg.norm(ref), 1.0), (call, r, ref)
+        r_or = y - onn.value(mlp, x)
+        assert np.linalg.norm(r - r_or) <= 1e-10 * max(np.linalg.norm(r_or), 1.0), (call, r, r_or)
     net.free()
 
 
@@ -48,3 +53,15 @@ def test_noalloc_rejects_widths_beyond_its_array():
     Wp = (ctypes.c_void_p * 1)(fake)
     assert lib.nnc_residual_noalloc(1, wid, act, Wp, None, fake, fake, fake, None) == -1
     assert b"65536" in lib.nnc_last_error()
+
+
+def test_noalloc_rejects_softmax_output():
+    from paper_2509_22462_gb300 import nnc
+    lib = nnc.load_library()
+    import ctypes
+    wid = (ctypes.c_int * 2)(4, 3)
+    act = (ctypes.c_int * 1)(5)         # NNC_SOFTMAX
+    fake = ctypes.c_void_p(16)          # never dereferenced: the activation check comes first
+    Wp = (ctypes.c_void_p * 1)(fake)
+    assert lib.nnc_residual_noalloc(1, wid, act, Wp, None, fake, fake, fake, None) == -6
+    assert b"softmax" in lib.nnc_last_error()
