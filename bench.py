@@ -37,6 +37,7 @@ METRIC = "hessian_lag_evals_per_s"
 TANGENT_TRAFFIC = {((4096, 784, 4096), "bf16x3", 208): 81.66e6,
                    ((4096, 784, 4096), "bf16x3", -208): 81.57e6}
 UNIT = "evals/s"
+FP64_NOMINAL_TFLOPS = 1.25   # GB300's nominal dense FP64 rate
 
 
 def _args():
@@ -53,6 +54,8 @@ def _args():
     p.add_argument("--no-fp64-form", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-ipm", action="store_true")
+    p.add_argument("--no-forms", action="store_true", help="skip the other tensor-core forms")
+    p.add_argument("--oracle-step-probe", action="store_true", help=argparse.SUPPRESS)
     return p.parse_args()
 
 
@@ -214,6 +217,50 @@ def oracle_step(mlp, x, lam, cols=None):
     _ = y - onn.value(mlp, x)  # the residual y - NN(x) in FP64
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or None."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
+def time_oracle_single_thread(workload):
+    """One full oracle step with every BLAS / OpenMP pool limited to one thread, in a child
+    process (the thread limits must be set before numpy loads).  Returns seconds or None."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT"):
+        env.pop(k, None)
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-step-probe",
+                            "--workload", workload], capture_output=True, text=True, env=env,
+                           timeout=600)
+        return float(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
+    except Exception:
+        return None
+
+
+def _oracle_step_probe(args):
+    spec, mlp, d = _workload(args.workload)
+    t0 = time.perf_counter()
+    oracle_step(mlp, d.x0, d.lam)
+    print(time.perf_counter() - t0, flush=True)
+    return 0
+
+
 def time_oracle(mlp, d, budget_s=12.0, max_steps=20):
     """Bounded sample: full oracle steps until `budget_s` seconds (at least one)."""
     n_done, t0 = 0, time.perf_counter()
@@ -226,7 +273,8 @@ def time_oracle(mlp, d, budget_s=12.0, max_steps=20):
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     return {"value": n_done / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n_done} full oracle step(s) (value, Jacobian, gradient, forward-over-reverse "
-                      f"Hessian, FP64 residual) in {el:.1f} s, numpy FP64 with multithreaded BLAS"}
+                      f"Hessian, FP64 residual) in {el:.1f} s, numpy FP64 with multithreaded BLAS",
+            "cpu_model": cpu_model()}
 
 
 def time_oracle_ipm(mlp, d):
@@ -444,6 +492,58 @@ def run_ours_scopf(args, rank, world, local_rank):
     return 0
 
 
+def timed_kernel_pass(net, step, steps, torch):
+    """K steps with events around the tangent-GEMM launches only; returns {kind: (ms, count)} and
+    the pass's wall time per step in ms under "_ms_per_step"."""
+    net.profile(True, kinds=["tangent_gemm"])
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record()
+    for _ in range(steps):
+        step()
+    a1.record()
+    torch.cuda.synchronize()
+    out = net.profile_read()
+    net.profile(False)
+    out["_ms_per_step"] = (a0.elapsed_time(a1) / steps, steps)
+    return out
+
+
+def tangent_roofline(net, spec, prec, roof_pass, prof, peaks, peak_src):
+    """Roofline of the dominant kernel, the tangent GEMM (the largest single kernel of a step):
+    algorithmic FLOPs per launch over the average launch time of the timed kernel pass."""
+    dom_name = "tangent_gemm" if prof.get("tangent_gemm", (0, 0))[1] > 0 else \
+        max(prof.items(), key=lambda kv: kv[1][0])[0]
+    dom_ms, dom_cnt = roof_pass[dom_name] if roof_pass.get(dom_name, (0, 0))[1] else prof[dom_name]
+    if dom_name == "tangent_gemm" and dom_cnt > 0:
+        tangent_bn = net.tuning(1)[0] if len(spec.widths) > 3 else 0
+        per = tangent_gemm_flops(spec)
+        fl_per_launch = sum(per) / len(per)
+        avg_s = dom_ms / dom_cnt / 1e3
+        ach = fl_per_launch / avg_s / 1e12
+        # the kernel is timed inside a step of well under a second: the burst peak applies
+        # (for FP8 operands the measured BF16 peak times the nominal 2x of e4m3)
+        pk = peaks.get("bf16_tflops") * (2.0 if prec == "fp8" else 1.0)
+        kname = ("k_tc_pair (tangent on SM pairs, tcgen05 cta_group::2: Zdot_l = W_l Adot_{l-1}, "
+                 "fused sigma' / sigma'' epilogue)" if tangent_bn < 0 else
+                 "k_tc_gemm (tangent: Zdot_l = W_l Adot_{l-1}, fused sigma' / sigma'' epilogue)")
+        mult = {"bf16x3": 3, "bf16": 1, "fp8": 1}.get(prec, 1)
+        return {"kernel": kname if prec in ("bf16", "bf16x3", "fp8") else "k_simt_gemm (tangent)",
+                "bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                "traffic": TANGENT_TRAFFIC.get((tangent_shape(spec), prec, tangent_bn)),
+                "tangent_bn": tangent_bn,
+                "peak_source": f"{peak_src} bf16 burst" + (" x 2 (e4m3 nominal ratio)" if prec == "fp8" else ""),
+                "executed_frac": ach * mult / pk, "products_per_tile": mult,
+                "avg_launch_us": avg_s * 1e6, "launches": dom_cnt,
+                "algorithmic_flops_per_launch": fl_per_launch,
+                "timed_pass_ms_per_step": roof_pass.get("_ms_per_step", (None,))[0]}
+    if dom_cnt > 0:
+        avg_s = dom_ms / dom_cnt / 1e3
+        return {"kernel": dom_name, "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"),
+                "unit": "GB/s", "frac": None, "traffic": None, "avg_launch_us": avg_s * 1e6}
+    return None
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -456,6 +556,10 @@ def run_ours(args, rank, world, local_rank):
     oracle_ipm = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu_baseline = time_oracle(mlp, d)  # before the first GPU call
+        t1 = time_oracle_single_thread(args.workload)
+        cpu_baseline["single_thread"] = ({"value": 1.0 / t1, "unit": UNIT, "cores": 1,
+                                          "sample": "1 full oracle step, BLAS and OpenMP limited to "
+                                                    "one thread"} if t1 else None)
         if not args.no_ipm and spec.acts[-1] != "softmax":
             oracle_ipm = time_oracle_ipm(mlp, d)
 
@@ -492,9 +596,7 @@ def run_ours(args, rank, world, local_rank):
 
     clocks = Clocks(_gpu_index(local_rank)) if rank == 0 else None
     time.sleep(0.3 if clocks else 0)
-    # events bracket only the tangent GEMM (the roofline kernel) inside the timed region; the
-    # per-kind breakdown comes from a separate profiled pass below
-    net.profile(True, kinds=["tangent_gemm"])
+    # the headline: K steps with no event inside the timed region
     launches0 = nnc.launch_count()
     if world > 1:
         dist.barrier()
@@ -508,9 +610,11 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         dist.barrier()
     launches = nnc.launch_count() - launches0
-    prof_timed = net.profile_read()
-    clk = clocks.stop() if clocks else None
     value, el_ms = aggregate(e0.elapsed_time(e1), args.steps, world, dev)
+    # the roofline kernel's launch time: a second timed pass of K steps with the library's events
+    # around each tangent-GEMM launch only, on the stream the kernel runs on
+    roof_pass = timed_kernel_pass(net, step, args.steps, torch)
+    clk = clocks.stop() if clocks else None
     # per-kind breakdown (events around every launch, outside the timed region)
     net.profile(True)
     for _ in range(min(args.steps, 10)):
@@ -520,35 +624,8 @@ def run_ours(args, rank, world, local_rank):
     net.profile(False)
     n_prof = min(args.steps, 10)
 
-    # roofline of the dominant kernel: the tangent GEMM (the largest single kernel of a step;
-    # the value pass and the FP64 residual are 16 smaller launches of two different kernels)
     peaks, peak_src = _peaks()
-    dom_name = "tangent_gemm" if prof.get("tangent_gemm", (0, 0))[1] > 0 else \
-        max(prof.items(), key=lambda kv: kv[1][0])[0]
-    dom_ms, dom_cnt = prof_timed[dom_name] if prof_timed.get(dom_name, (0, 0))[1] else prof[dom_name]
-    roof = None
-    if dom_name == "tangent_gemm" and dom_cnt > 0:
-        tangent_bn = net.tuning(1)[0] if len(spec.widths) > 3 else 0
-        per = tangent_gemm_flops(spec)
-        fl_per_launch = sum(per) / len(per)
-        avg_s = dom_ms / dom_cnt / 1e3
-        ach = fl_per_launch / avg_s / 1e12
-        pk = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
-        kname = ("k_tc_pair (tangent on SM pairs, tcgen05 cta_group::2: Zdot_l = W_l Adot_{l-1}, "
-                 "fused sigma' / sigma'' epilogue)" if tangent_bn < 0 else
-                 "k_tc_gemm (tangent: Zdot_l = W_l Adot_{l-1}, fused sigma' / sigma'' epilogue)")
-        roof = {"kernel": kname if args.prec.startswith("bf16") else "k_simt_gemm (tangent)",
-                "bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                "traffic": TANGENT_TRAFFIC.get((tangent_shape(spec), args.prec, tangent_bn)),
-                "tangent_bn": tangent_bn,
-                "peak_source": f"{peak_src} bf16 sustained",
-                "executed_frac": ach * (3 if args.prec == "bf16x3" else 1) / pk,
-                "avg_launch_us": avg_s * 1e6, "launches": dom_cnt,
-                "algorithmic_flops_per_launch": fl_per_launch}
-    elif dom_cnt > 0:
-        avg_s = dom_ms / dom_cnt / 1e3
-        roof = {"kernel": dom_name, "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"),
-                "unit": "GB/s", "frac": None, "traffic": None, "avg_launch_us": avg_s * 1e6}
+    roof = tangent_roofline(net, spec, args.prec, roof_pass, prof, peaks, peak_src)
     kernel_ms = {k: {"ms_per_step": v[0] / n_prof, "launches_per_step": v[1] / n_prof}
                  for k, v in prof.items()}
 
@@ -587,10 +664,44 @@ def run_ours(args, rank, world, local_rank):
     if oracle_ipm is not None:
         ipm["oracle"] = oracle_ipm
 
-    # the FP64 form on the same GPU, for the TC-vs-FP64 comparison of the metric
-    forms = {args.prec: {"evals_per_s": value / world, "ms_per_eval": el_ms / args.steps}}
+    # the other tensor-core forms, each timed like the headline (K steps, no events) plus its
+    # own tangent-kernel pass, and solved with the same interior-point driver
+    hf = hessian_flops(spec)
+    forms = {args.prec: {"evals_per_s": value / world, "ms_per_eval": el_ms / args.steps,
+                         "tangent_roofline_frac": roof.get("frac") if roof else None}}
+    others = [] if (args.no_forms or rank != 0) else \
+        [f for f in ("bf16x3", "bf16", "fp8") if f != args.prec and args.prec in ("bf16x3", "bf16", "fp8")]
+    net.free()
+    for f in others:
+        nf = nnc.Net.from_mlp(mlp, precision=f)
+        nf.autotune(os.environ.get("NNC_TUNE_CACHE"))
+
+        def stepf(nf=nf):
+            nf.eval_kkt_dev(x, y_it, lam, r, J, H, g)
+
+        for _ in range(args.warmup):
+            stepf()
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record()
+        for _ in range(args.steps):
+            stepf()
+        a1.record()
+        torch.cuda.synchronize()
+        msf = a0.elapsed_time(a1) / args.steps
+        rp = timed_kernel_pass(nf, stepf, args.steps, torch)
+        rf = tangent_roofline(nf, spec, f, rp, rp, peaks, peak_src)
+        forms[f] = {"evals_per_s": 1e3 / msf, "ms_per_eval": msf,
+                    "tangent_roofline_frac": rf.get("frac") if rf else None,
+                    "tangent_avg_launch_us": rf.get("avg_launch_us") if rf else None,
+                    "tangent_bn": rf.get("tangent_bn") if rf else None}
+        if not args.no_ipm:
+            ipm[f] = solve(nf)
+        nf.free()
+
+    # the FP64 form on the same GPU, for the TC-vs-FP64 comparison of the metric; its Hessian runs
+    # on FP64 CUDA cores, reported against the nominal FP64 rate (no measured FP64 peak exists)
     if rank == 0 and not args.no_fp64_form and args.prec != "fp64":
-        net.free()
         n64 = nnc.Net.from_mlp(mlp, precision="fp64")
         if not args.no_ipm:
             ipm["fp64"] = solve(n64)
@@ -608,7 +719,12 @@ def run_ours(args, rank, world, local_rank):
         a1.record()
         torch.cuda.synchronize()
         ms64 = a0.elapsed_time(a1) / k64
-        forms["fp64"] = {"evals_per_s": 1e3 / ms64, "ms_per_eval": ms64, "steps": k64}
+        fp64_tflops = hf / (ms64 / 1e3) / 1e12
+        forms["fp64"] = {"evals_per_s": 1e3 / ms64, "ms_per_eval": ms64, "steps": k64,
+                         "hessian_tflops_algorithmic": fp64_tflops,
+                         "fp64_peak_frac": fp64_tflops / FP64_NOMINAL_TFLOPS,
+                         "fp64_peak": FP64_NOMINAL_TFLOPS,
+                         "fp64_peak_source": "nominal GB300 FP64 rate (not measured)"}
         n64.free()
 
     if rank == 0:
@@ -626,6 +742,8 @@ def run_ours(args, rank, world, local_rank):
 
 def main():
     args = _args()
+    if args.oracle_step_probe:
+        return _oracle_step_probe(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

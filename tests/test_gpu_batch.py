@@ -223,3 +223,61 @@ def test_host_eval_kkt_matches_separate_calls(nnc, small_batch):
     yo = np.concatenate([onn.value(raw[k], xs[k]) for k in range(len(raw))])
     assert np.max(np.abs(r - (np.concatenate(ys) - yo))) <= 1e-10 * max(1.0, np.max(np.abs(yo)))
     b.free()
+
+
+def test_batch_bench_size_matches_oracle(nnc):
+    """The batch the bench times: 256 surrogates n_k -> 1024 x 5 sigmoid -> 1 with n_k ~ U{20..200}
+    (seed 0, loads d = 1), one fused evaluation per iterate replayed from the CUDA graph.  Nets
+    with 128 < n_k <= 200 take three lower-triangle tiles of the grouped symmetric product and the
+    persistent grouped tangent GEMM runs more than 13 tiles per CTA.  Every net's FP64 residual and
+    the value are checked; J, gradient and the full H of 45 nets (the 16 with n_k > 190 and every
+    eighth one) against the oracle, at the stated tolerances."""
+    import torch
+    data = scopf_data(K=256, G=200, n_bus=512, seed=0)
+    d = np.ones(512)
+    raw = _raw_nets(data, d)
+    nets = [nnc.Net.from_mlp(m, precision="bf16x3") for m in raw]
+    b = nnc.Batch(nets)
+    for n in nets:
+        n.free()
+    b.use_graph(True)
+    dev = torch.device("cuda:0")
+    x = synth.uniform01(synth.derive_key(9, "bench-bx"), data.G)
+    xs = [x[S] for S in data.subsets]
+    lams = [synth.normal(synth.derive_key(k, "bench-blam"), 1) for k in range(len(raw))]
+    yo = np.concatenate([onn.value(raw[k], xs[k]) for k in range(len(raw))])
+    xc = torch.tensor(b.concat(xs), device=dev)
+    lc = torch.tensor(b.concat(lams), device=dev)
+    yi = torch.tensor(yo, device=dev)
+    outs = []
+    for _ in range(2):          # capture, then replay
+        r = torch.empty(b.K, dtype=torch.float64, device=dev)
+        J = torch.empty(b.n_sum, dtype=torch.float64, device=dev)
+        H = torch.empty(b.h_sum, dtype=torch.float64, device=dev)
+        g = torch.empty(b.n_sum, dtype=torch.float64, device=dev)
+        b.eval_kkt_dev(xc, yi, lc, r, J, H, g)
+        torch.cuda.synchronize()
+        outs.append([t.cpu().numpy() for t in (r, J, H, g)])
+    for a, c in zip(outs[0], outs[1]):
+        assert np.array_equal(a, c)
+    r, J, H, g = outs[1]
+    assert np.max(np.abs(r)) <= 1e-10 * max(1.0, np.max(np.abs(yo))), np.max(np.abs(r))
+    ys, _, _, _ = b.eval(xs, None, want=("y",))
+    assert rel(np.concatenate(ys), yo) < 1e-6
+    _, Js, Hs, gs = b.split_outputs(None, J, H, g)
+    n_in = np.array([len(S) for S in data.subsets])
+    assert n_in.max() > 190 and (n_in > 128).sum() > 32
+    sample = sorted(set(np.flatnonzero(n_in > 190).tolist()) | set(range(0, 256, 8)))
+    worst = dict(J=0.0, H=0.0, g=0.0)
+    for k in sample:
+        Jo = onn.jacobian(raw[k], xs[k])
+        Ho = onn.hessian_lag(raw[k], xs[k], lams[k])
+        go = onn.vjp(raw[k], xs[k], lams[k])
+        worst["J"] = max(worst["J"], rel(Js[k], Jo))
+        worst["H"] = max(worst["H"], rel(Hs[k], Ho))
+        worst["g"] = max(worst["g"], rel(gs[k], go))
+        assert np.array_equal(Hs[k], Hs[k].T)
+    print(f"[batch bench size, {len(sample)} nets] worst rel err J={worst['J']:.2e} "
+          f"H={worst['H']:.2e} g={worst['g']:.2e}")
+    assert worst["J"] < 1e-3 and worst["H"] < 1e-2 and worst["g"] < 1e-3
+    b.free()

@@ -131,28 +131,38 @@ def test_device_pointer_calls_match_host_calls(lib):
         net.free()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "bf16x3", "bf16", "fp8"])
-def test_full_size_104m_sampled(lib, prec):
-    """The ~104M-parameter net (784 -> 4096 x 7 -> 10 tanh) in the launch configuration the
-    bench times: full value and Jacobian, and sampled Hessian columns against the oracle."""
+@pytest.fixture(scope="module")
+def oracle_104m():
+    """The ~104M-parameter net and the oracle's value, Jacobian, full 784 x 784 Hessian and
+    gradient at (x0, lambda) of seed 0 (computed once for every form)."""
     mlp = make_mlp(synth.PAPER_104M, seed=0)
     d = synth.adversarial_data(seed=0)
+    return mlp, d, onn.all_outputs(mlp, d.x0, d.lam)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3", "bf16", "fp8"])
+def test_full_size_104m(lib, oracle_104m, prec):
+    """The ~104M-parameter net (784 -> 4096 x 7 -> 10 tanh) in the launch configuration the
+    bench times (autotuned tiles): value, Jacobian, gradient and the full 784 x 784 Hessian
+    against the oracle, element by element through the relative Frobenius norm."""
+    mlp, d, (yo, Jo, Ho, go) = oracle_104m
     net = lib.Net.from_mlp(mlp, precision=prec)
+    net.autotune()
     y = net.eval(d.x0)
     J = net.jacobian(d.x0)
     H, g = net.hessian_lag(d.x0, d.lam, want_grad=True)
-    yo = onn.value(mlp, d.x0)
-    Jo = onn.jacobian(mlp, d.x0)
-    go = onn.vjp(mlp, d.x0, d.lam)
-    cols = [0, 1, 391, 392, 783]
-    Hc = onn.hessian_lag_columns(mlp, d.x0, d.lam, cols)
-    e = dict(y=rel(y, yo), J=rel(J, Jo), H=rel(H[:, cols], Hc), g=rel(g, go))
-    print(f"[104m {prec}] rel err y={e['y']:.2e} J={e['J']:.2e} Hcols={e['H']:.2e} g={e['g']:.2e}")
+    e = dict(y=rel(y, yo), J=rel(J, Jo), H=rel(H, Ho), g=rel(g, go))
+    print(f"[104m {prec}] rel err y={e['y']:.2e} J={e['J']:.2e} H={e['H']:.2e} g={e['g']:.2e} "
+          f"max|dH|/max|H| {np.max(np.abs(H - Ho)) / np.max(np.abs(Ho)):.2e}")
     t = TOL[prec]
     assert e["y"] < t["y"] and e["J"] < t["J"] and e["H"] < t["H"] and e["g"] < t["J"], e
     assert np.array_equal(H, H.T)
     r = net.residual(d.x0, yo)
     assert np.max(np.abs(r)) <= 1e-10 * max(1.0, np.max(np.abs(yo)))
+    # the fused iterate call the bench times: the same outputs from one value pass
+    rk, Jk, Hk, gk = net.eval_kkt(d.x0, yo, d.lam)
+    assert np.array_equal(Jk, J) and np.array_equal(Hk, H) and np.array_equal(gk, g)
+    assert np.max(np.abs(rk)) <= 1e-10 * max(1.0, np.max(np.abs(yo)))
     net.free()
 
 
