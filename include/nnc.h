@@ -274,10 +274,13 @@ int nnc_tune_set(nnc_net* net, int tangent_bn, int syrk_splits);
  * was recorded); nnc_profile_read waits for the recorded work, then fills ms[k] (total
  * milliseconds) and count[k] (launches) for kernel kind k < n_kinds and clears the record:
  *   0 tangent GEMM, 1 symmetric product (Hessian accumulation), 2 forward layer,
- *   3 reverse layer, 4 other.
- * enable = 0 stops recording; enable > 1 records only the kinds whose bit (k + 1) is set, so that
- * events do not sit between the forward layers, which overlap through programmatic dependent
- * launch. */
+ *   3 reverse layer, 4 other,
+ *   5 tangent chain: one pair of events around all tangent GEMMs of an evaluation, counted as
+ *     that many launches (its ms / count is the average launch time with the launches overlapping
+ *     as they do unprofiled; recorded only when its own bit is set).
+ * enable = 0 stops recording; enable = 1 records kinds 0 to 4; enable > 1 records only the kinds
+ * whose bit (k + 1) is set, so that events do not sit between launches that overlap through
+ * programmatic dependent launch. */
 int nnc_profile(nnc_net* net, int enable);
 int nnc_profile_read(nnc_net* net, double* ms, long long* count, int n_kinds);
 

@@ -6,9 +6,10 @@
  * The method is a primal-dual barrier method for Eq. 1 whose Newton system is Eq. 2 with the
  * unstated terms alpha, beta read as IPOPT's barrier terms (Waechter & Biegler 2006): inertia
  * correction delta_w, barrier parameter mu with monotone decrease, fraction to the boundary,
- * backtracking on an exact-penalty merit function.  The KKT factorization, the merit checks
- * and all optimizer state stay in FP64 on the host; the constraint residual y - NN(x) is
- * always evaluated with the FP64 weights (nnc_residual), whatever the net's precision form.
+ * backtracking on an exact-penalty merit function.  The merit checks and all optimizer state stay
+ * in FP64 on the host; so does the KKT factorization, except the dense block of the tensor-core
+ * forms (opt->kkt_on_device).  The constraint residual y - NN(x) is always FP64-accurate
+ * (nnc_residual), whatever the net's precision form.
  *
  * Ownership: all pointers are host memory owned by the caller.  Errors: negative nnc_status
  * for bad arguments or a failing oracle call; the solver's own outcome is in result->status.
@@ -48,6 +49,14 @@ typedef struct {
   int max_ls_failures;     /* 5 */
   int verbose;             /* print one line per iteration */
   double warm_mu0;         /* 1e-3: barrier parameter of a warm start (z = warm_mu0 / slack) */
+  int kkt_on_device;       /* 1 (default): for the single-network problems in the tensor-core forms
+                            * (NNC_BF16, NNC_BF16X3, NNC_FP8) the Hessian stays in device memory and
+                            * the dense block of the KKT matrix is assembled and factorized on the
+                            * GPU (Jacobi-scaled FP32 blocked Cholesky of the bordered matrix, the
+                            * factor widened to FP64 for the host's solves; an indefinite or nearly
+                            * singular block, pivot <= 1e-5 of the unit diagonal, goes to the FP64
+                            * host path).  0: everything on the host.  The FP64 and FP32 forms and
+                            * the SCOPF-shaped problem always factorize on the host. */
 } nnc_ipm_options;
 
 typedef struct {

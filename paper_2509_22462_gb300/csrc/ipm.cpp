@@ -35,6 +35,17 @@
 #include "../../include/nnc.h"
 #include "../../include/nnc_ipm.h"
 
+// the dense block of the KKT matrix on the device (kkt_gpu.cu)
+namespace nnc {
+struct DenseKktDev;
+DenseKktDev* dkkt_create(int nd, int mmax, cudaStream_t st);
+void dkkt_free(DenseKktDev* d);
+int dkkt_maxabs(DenseKktDev* d, const double* H, double s, const double* hf, double* out);
+int dkkt_matvec(DenseKktDev* d, const double* H, const double* x, double* u);
+int dkkt_factor(DenseKktDev* d, const double* H, double s, const double* dvec, const double* AD,
+                int m, bool* pd, const double** result);
+}  // namespace nnc
+
 namespace {
 
 using Clock = std::chrono::steady_clock;
@@ -518,12 +529,31 @@ struct BK {
 };
 
 
+// ---------------------------------------------------------------- dense block on the device
+
+// W_DD = s H + diag(hf) with H (nd x nd FP64) in device memory: the KKT solver assembles and
+// factorizes the dense block there; host_wdd materializes W_DD on the host for the rare
+// indefinite iterations.
+struct DenseOnDevice {
+  nnc::DenseKktDev* dk = nullptr;
+  const double* H = nullptr;
+  double s = 1.0;
+  const double* hf = nullptr;
+  std::function<const double*()> host_wdd;
+};
+
 // ---------------------------------------------------------------- structured KKT solver
 // K = [[W_DD + diag(sig_D) + dw I, 0, A_D^T], [0, diag(W_SS + sig_S) + dw I, A_S^T],
 //      [A_D, A_S, -dc I]], n = nd + ns primal rows and m constraint rows.
 struct KktSolver {
   int nd = 0, ns = 0, m = 0, n = 0, r = 0, ldk = 0;
   std::vector<double> K11, Y, Sm, Kfull, tmp, Dinv, T, AS_;
+  // the factored bordered matrix (row stride ldk): K11's storage, or the pinned copy of the
+  // device factorization
+  const double* Kp = nullptr;
+  DenseOnDevice* dev = nullptr;   // dense block on the device (null: host)
+  int dev_error = 0;              // nnc_status of a failed device factorization
+  std::vector<double> dvec, pinadd;
   BK bkS, bkF, bkT, bkR;
   std::vector<int> zid;   // mode 3: small-block variables with a zero diagonal (free, no curvature)
   std::vector<double> R;
@@ -547,6 +577,7 @@ struct KktSolver {
   std::vector<double> WDDp, ADo, ASo, core;
   void factor(int nd_, int ns_, int m_, const double* WDD, const double* WSS, const double* sig,
               const double* AD, const double* AS, double dw, double dc, double zero_tol) {
+    dev_error = 0;
     m_all = m_;
     n_all = nd_ + ns_;
     prow.clear(); pcol.clear(); orow.clear(); palpha.clear(); pe.clear(); pterm.clear();
@@ -598,15 +629,13 @@ struct KktSolver {
       }
     }
     if (prow.empty()) {
+      pinadd.assign(nd_, 0.0);
       factor_core(nd_, ns_, m_, WDD, WSS, sig, AD, AS, dw, dc, zero_tol);
       return;
     }
-    WDDp.resize((size_t)nd_ * nd_);
-#pragma omp parallel for schedule(static) if (nd_ >= 256)
-    for (int i = 0; i < nd_; ++i)
-      std::memcpy(&WDDp[(size_t)i * nd_], &WDD[(size_t)i * nd_], sizeof(double) * nd_);
+    pinadd.assign(nd_, 0.0);
     for (size_t k = 0; k < prow.size(); ++k)
-      if (pcol[k] >= 0) WDDp[(size_t)pcol[k] * nd_ + pcol[k]] += palpha[k] * palpha[k] / pe[k];
+      if (pcol[k] >= 0) pinadd[pcol[k]] += palpha[k] * palpha[k] / pe[k];
     const int mo = (int)orow.size();
     ADo.assign((size_t)mo * nd_, 0.0);
     ASo.assign((size_t)mo * ns_, 0.0);
@@ -614,6 +643,18 @@ struct KktSolver {
       std::memcpy(&ADo[(size_t)k * nd_], &AD[(size_t)orow[k] * nd_], sizeof(double) * nd_);
       std::memcpy(&ASo[(size_t)k * ns_], &AS[(size_t)orow[k] * ns_], sizeof(double) * ns_);
     }
+    if (dev) {
+      // the pinning terms enter the device assembly through pinadd; W_DD + pinadd is formed on the
+      // host only if the device finds the dense block indefinite
+      factor_core(nd_, ns_, mo, nullptr, WSS, sig, ADo.data(), ASo.data(), dw, dc, zero_tol);
+      nneg += (int)prow.size();
+      return;
+    }
+    WDDp.resize((size_t)nd_ * nd_);
+#pragma omp parallel for schedule(static) if (nd_ >= 256)
+    for (int i = 0; i < nd_; ++i)
+      std::memcpy(&WDDp[(size_t)i * nd_], &WDD[(size_t)i * nd_], sizeof(double) * nd_);
+    for (int i = 0; i < nd_; ++i) WDDp[(size_t)i * nd_ + i] += pinadd[i];
     factor_core(nd_, ns_, mo, WDDp.data(), WSS, sig, ADo.data(), ASo.data(), dw, dc, zero_tol);
     nneg += (int)prow.size();
   }
@@ -655,25 +696,58 @@ struct KktSolver {
     // of its leading nd columns leaves L, the rows Y^T = A_D L^-T and, in the bottom m x m block,
     // G = -A_D K11^-1 A_D^T
     ldk = nd + m;
-    K11.resize((size_t)ldk * ldk);
-#pragma omp parallel for schedule(static) if (nd >= 256)
-    for (int i = 0; i < ldk; ++i) {
-      double* ki = &K11[(size_t)i * ldk];
-      if (i < nd) {
-        std::memcpy(ki, &WDD[(size_t)i * nd], sizeof(double) * nd);
-        ki[i] += sig[i] + dw;
+    bool pd = nd == 0;
+    bool host_factor = !dev || nd == 0;
+    if (dev && nd > 0) {
+      // assembly and partial Cholesky of the bordered matrix on the device (H stays there)
+      dvec.resize(nd);
+      for (int i = 0; i < nd; ++i) dvec[i] = dev->hf[i] + sig[i] + dw + pinadd[i];
+      const double* res = nullptr;
+      const int rc = nnc::dkkt_factor(dev->dk, dev->H, dev->s, dvec.data(), AD, m, &pd, &res);
+      if (rc) {
+        dev_error = rc;
+        npos = nneg = nzero = 0;
+        return;
+      }
+      if (pd) {
+        Kp = res;
       } else {
-        std::memcpy(ki, &AD[(size_t)(i - nd) * nd], sizeof(double) * nd);
-        std::memset(ki + nd, 0, sizeof(double) * (i - nd + 1));
+        // not positive definite in FP32 (or nearly singular): the FP64 host path decides, with
+        // W_DD (+ the pinning terms) on the host
+        const double* W = dev->host_wdd();
+        if (!W) {
+          dev_error = NNC_ERR_CUDA;
+          npos = nneg = nzero = 0;
+          return;
+        }
+        WDDp.assign(W, W + (size_t)nd * nd);
+        for (int i = 0; i < nd; ++i) WDDp[(size_t)i * nd + i] += pinadd[i];
+        WDD = WDDp.data();
+        host_factor = true;
       }
     }
-    const bool pd = nd == 0 || cholesky_bordered(ldk, nd, ldk, K11.data(), 0.0);
-    auto G = [&](int a, int b) { return K11[(size_t)(nd + std::max(a, b)) * ldk + nd + std::min(a, b)]; };
+    if (host_factor) {
+      K11.resize((size_t)ldk * ldk);
+#pragma omp parallel for schedule(static) if (nd >= 256)
+      for (int i = 0; i < ldk; ++i) {
+        double* ki = &K11[(size_t)i * ldk];
+        if (i < nd) {
+          std::memcpy(ki, &WDD[(size_t)i * nd], sizeof(double) * nd);
+          ki[i] += sig[i] + dw;
+        } else {
+          std::memcpy(ki, &AD[(size_t)(i - nd) * nd], sizeof(double) * nd);
+          std::memset(ki + nd, 0, sizeof(double) * (i - nd + 1));
+        }
+      }
+      pd = nd == 0 || cholesky_bordered(ldk, nd, ldk, K11.data(), 0.0);
+      Kp = K11.data();
+    }
+    auto G = [&](int a, int b) { return Kp[(size_t)(nd + std::max(a, b)) * ldk + nd + std::min(a, b)]; };
     // Y = L^-1 A_D^T (nd x m) from the rows below L
     auto fill_y = [&](int cols, int off) {
       Y.assign((size_t)nd * cols, 0.0);
       for (int j = 0; j < m; ++j) {
-        const double* yj = &K11[(size_t)(nd + j) * ldk];
+        const double* yj = &Kp[(size_t)(nd + j) * ldk];
         for (int i = 0; i < nd; ++i) Y[(size_t)i * cols + off + j] = yj[i];
       }
     };
@@ -898,7 +972,7 @@ struct KktSolver {
       // [w_Z; z] = R^-1 [r2_Z; r3 - A_D K11^-1 r1 - A_P D_P^-1 r2_P]; then u and w_P as in mode 2
       const int nz = (int)zid.size();
       tmp.assign(rhs, rhs + nd);
-      if (nd) lower_solve1(nd, K11.data(), tmp.data(), ldk);
+      if (nd) lower_solve1(nd, Kp, tmp.data(), ldk);
       std::vector<double> q(nz + m);
       for (int k = 0; k < nz; ++k) q[k] = rhs[nd + zid[k]];
       const std::vector<double> yt = ytmul(nd, m, Y.data(), tmp.data());   // A_D K11^-1 r1 = Y^T t
@@ -914,7 +988,7 @@ struct KktSolver {
       // u = K11^-1 (r1 - A_D^T z) with L^-1 (r1 - A_D^T z) = t - Y z: one backward solve
       std::vector<double> u(nd);
       for (int i = 0; i < nd; ++i) u[i] = tmp[i] - dot4(&Y[(size_t)i * m], z, m);
-      if (nd) upper_solve_lt(nd, K11.data(), u.data(), ldk);
+      if (nd) upper_solve_lt(nd, Kp, u.data(), ldk);
       for (int c = 0; c < ns; ++c) {
         double s = rhs[nd + c];
         for (int j = 0; j < m; ++j) s -= AS_[(size_t)j * ns + c] * z[j];
@@ -928,7 +1002,7 @@ struct KktSolver {
     if (mode == 2) {
       // z = T^-1 (r3 - A_D K11^-1 r1 - A_S D^-1 r2); u = K11^-1 (r1 - A_D^T z); w = D^-1 (r2 - A_S^T z)
       tmp.assign(rhs, rhs + nd);
-      if (nd) lower_solve1(nd, K11.data(), tmp.data(), ldk);     // t = L^-1 r1; A_D K11^-1 r1 = Y^T t
+      if (nd) lower_solve1(nd, Kp, tmp.data(), ldk);     // t = L^-1 r1; A_D K11^-1 r1 = Y^T t
       std::vector<double> z(m);
       const std::vector<double> yt = ytmul(nd, m, Y.data(), tmp.data());
       for (int j = 0; j < m; ++j) {
@@ -948,7 +1022,7 @@ struct KktSolver {
       // u = K11^-1 (r1 - A_D^T z) with L^-1 (r1 - A_D^T z) = t - Y z (Y = L^-1 A_D^T is stored)
       std::vector<double> u(nd);
       for (int i = 0; i < nd; ++i) u[i] = tmp[i] - dot4(&Y[(size_t)i * m], z.data(), m);
-      if (nd) upper_solve_lt(nd, K11.data(), u.data(), ldk);
+      if (nd) upper_solve_lt(nd, Kp, u.data(), ldk);
       for (int c = 0; c < ns; ++c) {
         double s = rhs[nd + c];
         for (int j = 0; j < m; ++j) s -= AS_[(size_t)j * ns + c] * z[j];
@@ -960,14 +1034,14 @@ struct KktSolver {
     }
     // [K11 K12; K12^T K22] [u; w] = [r1; r2]: w = S^-1 (r2 - Y^T L^-1 r1), u = K11^-1 (r1 - K12 w)
     tmp.assign(rhs, rhs + nd);
-    if (nd) lower_solve1(nd, K11.data(), tmp.data(), ldk);
+    if (nd) lower_solve1(nd, Kp, tmp.data(), ldk);
     std::vector<double> w(r);
     const std::vector<double> yt = ytmul(nd, r, Y.data(), tmp.data());
     for (int a = 0; a < r; ++a) w[a] = rhs[nd + a] - yt[a];
     bkS.solve(w.data());
     // u = K11^-1 (r1 - K12 w) with L^-1 (r1 - K12 w) = t - Y w (Y = L^-1 K12)
     for (int i = 0; i < nd; ++i) tmp[i] -= dot4(&Y[(size_t)i * r], w.data(), r);
-    if (nd) upper_solve_lt(nd, K11.data(), tmp.data(), ldk);
+    if (nd) upper_solve_lt(nd, Kp, tmp.data(), ldk);
     for (int i = 0; i < nd; ++i) rhs[i] = tmp[i];
     for (int a = 0; a < r; ++a) rhs[nd + a] = w[a];
   }
@@ -1007,6 +1081,17 @@ struct IpmProblem {
     (void)lam;
     return false;
   }
+  // Problems whose network Hessian can stay in device memory: W_DD = dense_scale() H +
+  // diag(dense_diag()) with H = dense_dev() (nd x nd FP64, valid after jac_hess), on the CUDA
+  // stream dense_stream().  After set_dense_on_device(true) their jac_hess leaves WDD unwritten,
+  // and host_wdd() copies H back and forms W_DD on the host (null on failure).
+  virtual bool dense_capable() const { return false; }
+  virtual bool set_dense_on_device(bool on) { return !on; }
+  virtual const double* dense_dev() const { return nullptr; }
+  virtual double dense_scale() const { return 1.0; }
+  virtual const double* dense_diag() const { return nullptr; }
+  virtual cudaStream_t dense_stream() const { return nullptr; }
+  virtual const double* host_wdd() { return nullptr; }
 };
 
 // Derivatives kept from a trial-point evaluation, keyed by the point and the multipliers.
@@ -1078,6 +1163,29 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
       WSS(ns), vt(n), ct(m), lam_t(m), rhs(n + m), sol(n + m), dv(n), dl(m), dzL(n), dzU(n), sL(n), sU(n),
       SigL(n), SigU(n), sig(n), gphi(n), atl(n);
   KktSolver kkt;
+  // the dense block on the device (tensor-core forms of the single-network problems)
+  DenseOnDevice dense;
+  const bool dev_kkt = o.kkt_on_device && nd > 0 && p.dense_capable() && p.set_dense_on_device(true);
+  if (dev_kkt) {
+    dense.dk = nnc::dkkt_create(nd, m, p.dense_stream());
+    if (!dense.dk) {
+      p.set_dense_on_device(false);
+      return NNC_ERR_CUDA;
+    }
+    dense.s = p.dense_scale();
+    dense.hf = p.dense_diag();
+    dense.host_wdd = [&p]() { return p.host_wdd(); };
+    kkt.dev = &dense;
+  }
+  struct DenseGuard {
+    DenseOnDevice& d;
+    IpmProblem& p;
+    bool on;
+    ~DenseGuard() {
+      if (d.dk) nnc::dkkt_free(d.dk);
+      if (on) p.set_dense_on_device(false);
+    }
+  } dense_guard{dense, p, dev_kkt};
   // atl = A^T lam, row by row (contiguous reads of the dense Jacobian blocks)
   auto update_atl = [&]() {
 #pragma omp parallel for schedule(static) if ((size_t)m * n > 65536)
@@ -1194,7 +1302,14 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
     double delta_w = 0.0, delta_c = 0.0;
     bool first = true, ok = false;
     double scale = 1.0;
-    scale = std::max(scale, max_abs(WDD.data(), WDD.size()));
+    if (dev_kkt) {
+      dense.H = p.dense_dev();
+      double mx = 0.0;
+      if (nnc::dkkt_maxabs(dense.dk, dense.H, dense.s, dense.hf, &mx)) { status = NNC_IPM_EVAL_ERROR; break; }
+      scale = std::max(scale, mx);
+    } else {
+      scale = std::max(scale, max_abs(WDD.data(), WDD.size()));
+    }
     for (int i = 0; i < n; ++i) {
       sig[i] = SigL[i] + SigU[i];
       scale = std::max(scale, sig[i]);
@@ -1208,6 +1323,7 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
       ++tries;
       kkt.factor(nd, ns, m, WDD.data(), WSS.data(), sig.data(), AD.data(), AS.data(), delta_w,
                  delta_c, zero_tol);
+      if (kkt.dev_error) break;
       if (kkt.npos == n && kkt.nneg == m && kkt.nzero == 0) { ok = true; break; }
       if (kkt.nzero > 0 && delta_c == 0.0 && m) delta_c = 1e-8 * std::pow(mu, 0.25);
       if (first) {
@@ -1218,6 +1334,7 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
       }
       if (delta_w > o.delta_w_max) break;
     }
+    if (kkt.dev_error) { status = NNC_IPM_EVAL_ERROR; T.solver += secs(t_lin, Clock::now()); break; }
     if (!ok) { status = NNC_IPM_INERTIA_FAILED; T.solver += secs(t_lin, Clock::now()); break; }
     if (delta_w > 0.0) delta_w_last = delta_w;
     const auto t_sol = Clock::now();
@@ -1245,11 +1362,18 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
     if (m && c1 > 0) {
       // curvature dv^T (W + Sigma + delta_w I) dv
       double curv = 0;
+      if (dev_kkt) {
+        // dv_D^T W_DD dv_D = s dv^T (H dv) + sum_i hf_i dv_i^2, H dv on the device
+        std::vector<double> hv(nd);
+        if (nnc::dkkt_matvec(dense.dk, dense.H, dv.data(), hv.data())) { status = NNC_IPM_EVAL_ERROR; break; }
+        for (int i = 0; i < nd; ++i) curv += dv[i] * (dense.s * hv[i] + dense.hf[i] * dv[i]);
+      } else {
 #pragma omp parallel for reduction(+ : curv) schedule(static)
-      for (int i = 0; i < nd; ++i) {
-        double s = 0;
-        for (int j = 0; j < nd; ++j) s += WDD[(size_t)i * nd + j] * dv[j];
-        curv += dv[i] * s;
+        for (int i = 0; i < nd; ++i) {
+          double s = 0;
+          for (int j = 0; j < nd; ++j) s += WDD[(size_t)i * nd + j] * dv[j];
+          curv += dv[i] * s;
+        }
       }
       for (int i = 0; i < n; ++i) curv += (SigL[i] + SigU[i] + delta_w + (i >= nd ? WSS[i - nd] : 0.0)) * dv[i] * dv[i];
       double lmax = 0;
@@ -1334,6 +1458,84 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
   return NNC_OK;
 }
 
+// ---------------------------------------------------------------- device-resident evaluation
+// One network evaluation at an iterate whose Hessian of lambda^T NN stays in device memory (for
+// the device factorization of the KKT dense block): x, y, lambda go in through one pinned staging
+// buffer, the residual r = y - NN(x) and J come back, H stays in `H`.  Its own stream orders the
+// evaluation before the factorization.
+struct DevEval {
+  nnc_net* net = nullptr;
+  int n_in = 0, n_out = 0;
+  cudaStream_t st = nullptr;
+  double* d = nullptr;          // x | y | lam | r | J | H
+  PinnedVec stage;              // x | y | lam | r | J
+  PinnedVec hh;                 // host copy of H (indefinite iterations only)
+  double *x = nullptr, *y = nullptr, *lam = nullptr, *r = nullptr, *J = nullptr, *H = nullptr;
+  ~DevEval() { release(); }
+  void release() {
+    if (st) cudaStreamSynchronize(st);
+    if (d) cudaFree(d);
+    if (st) cudaStreamDestroy(st);
+    d = nullptr;
+    st = nullptr;
+  }
+  bool init(nnc_net* net_, int n_in_, int n_out_) {
+    net = net_;
+    n_in = n_in_;
+    n_out = n_out_;
+    const size_t nstage = (size_t)n_in + 3 * n_out + (size_t)n_out * n_in;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return false;
+    if (cudaMalloc(&d, sizeof(double) * (nstage + (size_t)n_in * n_in)) != cudaSuccess) {
+      cudaGetLastError();
+      release();
+      return false;
+    }
+    x = d;
+    y = x + n_in;
+    lam = y + n_out;
+    r = lam + n_out;
+    J = r + n_out;
+    H = J + (size_t)n_out * n_in;
+    stage.resize(nstage);
+    return true;
+  }
+  // r (when yh is given) and J at (xh, lamh); H on the device
+  int eval(const double* xh, const double* yh, const double* lamh, double* rh, double* Jh) {
+    double* s = stage.data();
+    std::memcpy(s, xh, sizeof(double) * n_in);
+    if (yh) std::memcpy(s + n_in, yh, sizeof(double) * n_out);
+    std::memcpy(s + n_in + n_out, lamh, sizeof(double) * n_out);
+    if (cudaMemcpyAsync(x, s, sizeof(double) * (n_in + 2 * n_out), cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return NNC_ERR_CUDA;
+    int rc = nnc_eval_kkt_dev(net, x, yh ? y : nullptr, lam, yh ? r : nullptr, J, H, nullptr, st);
+    if (rc) return rc;
+    double* back = s + n_in + 2 * n_out;
+    const size_t nb = (size_t)n_out + (size_t)n_out * n_in;
+    if (cudaMemcpyAsync(back, r, sizeof(double) * nb, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return NNC_ERR_CUDA;
+    if (yh && rh) std::memcpy(rh, back, sizeof(double) * n_out);
+    std::memcpy(Jh, back + n_out, sizeof(double) * (size_t)n_out * n_in);
+    return NNC_OK;
+  }
+  const double* hess_host() {
+    if (!hh.data()) hh.resize((size_t)n_in * n_in);
+    if (cudaMemcpyAsync(hh.data(), H, sizeof(double) * (size_t)n_in * n_in, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return nullptr;
+    return hh.data();
+  }
+};
+
+// Tensor-core forms only: the FP64 and FP32 forms keep the host factorization (their Hessian is
+// as exact as the FP64 factorization, and the FP64 form is the reference path).
+bool tensor_core_form(nnc_net* net) {
+  int L = 0, ni = 0, no = 0, prec = 0;
+  return nnc_net_info(net, &L, &ni, &no, &prec) == NNC_OK &&
+         (prec == NNC_BF16 || prec == NNC_BF16X3 || prec == NNC_FP8);
+}
+
 // ---------------------------------------------------------------- adversarial problem
 // Variables v = (x in [0,1]^n_in | y free in R^n_out, s >= 0 in R^(n_out-1)).
 // min ||x - x0||^2  s.t.  y - NN(x) = 0,  y_t - y_j - margin - s_j = 0 (j != t).
@@ -1398,11 +1600,39 @@ struct Adversarial : IpmProblem {
   bool speculative() const override { return true; }
   int cons_spec(const double* v, const double* lam_t, double* c) override {
     spec.valid = false;
-    int rc = nnc_eval_kkt(net, v, v + n_in, lam_t, r.data(), J.data(), H.data(), nullptr);
+    int rc = dense_on ? de.eval(v, v + n_in, lam_t, r.data(), J.data())
+                      : nnc_eval_kkt(net, v, v + n_in, lam_t, r.data(), J.data(), H.data(), nullptr);
     if (rc) return rc;
     spec.store(v, nd + ns, lam_t, m);
     fill_cons(v, c);
     return NNC_OK;
+  }
+  // device-resident Hessian: W_DD = -H + 2 I
+  DevEval de;
+  bool dense_on = false;
+  std::vector<double> hf, wdd;
+  bool dense_capable() const override { return tensor_core_form(net); }
+  bool set_dense_on_device(bool on) override {
+    if (on && !de.d && !de.init(net, n_in, n_out)) return false;
+    dense_on = on;
+    spec.valid = false;
+    hf.assign(n_in, 2.0);
+    return true;
+  }
+  const double* dense_dev() const override { return de.H; }
+  double dense_scale() const override { return -1.0; }
+  const double* dense_diag() const override { return hf.data(); }
+  cudaStream_t dense_stream() const override { return de.st; }
+  const double* host_wdd() override {
+    const double* Hh = de.hess_host();
+    if (!Hh) return nullptr;
+    wdd.resize((size_t)nd * nd);
+#pragma omp parallel for schedule(static) if (nd >= 256)
+    for (int i = 0; i < nd; ++i) {
+      for (int j = 0; j < nd; ++j) wdd[(size_t)i * nd + j] = -Hh[(size_t)i * nd + j];
+      wdd[(size_t)i * nd + i] += 2.0;
+    }
+    return wdd.data();
   }
   bool has_derivs(const double* v, const double* lam) const override { return spec.match(v, lam); }
   int jac(const double* v, double* AD, double* AS) override {
@@ -1443,12 +1673,14 @@ struct Adversarial : IpmProblem {
   int jac_hess(const double* v, const double* lam, double* AD, double* AS, double* WDD,
                double* WSS) override {
     if (!spec.match(v, lam)) {   // else J and H are those of the accepted trial point
-      int rc = nnc_eval_kkt(net, v, nullptr, lam, nullptr, J.data(), H.data(), nullptr);
+      int rc = dense_on ? de.eval(v, nullptr, lam, nullptr, J.data())
+                        : nnc_eval_kkt(net, v, nullptr, lam, nullptr, J.data(), H.data(), nullptr);
       if (rc) return rc;
     }
     spec.valid = false;
     fill_jac(AD, AS);
-    fill_wdd(WDD, WSS);
+    if (dense_on) std::fill(WSS, WSS + ns, 0.0);
+    else fill_wdd(WDD, WSS);
     return NNC_OK;
   }
 };
@@ -1509,11 +1741,37 @@ struct AdversarialL1 : IpmProblem {
   int cons_spec(const double* v, const double* lam_t, double* c) override {
     spec.valid = false;
     for (int i = 0; i < n_in; ++i) c[i] = v[i] - v[n_in + i] + v[2 * n_in + i] - xr[i];
-    int rc = nnc_eval_kkt(net, v, v + 3 * n_in, lam_t + n_in, r.data(), J.data(), H.data(), nullptr);
+    int rc = dense_on ? de.eval(v, v + 3 * n_in, lam_t + n_in, r.data(), J.data())
+                      : nnc_eval_kkt(net, v, v + 3 * n_in, lam_t + n_in, r.data(), J.data(), H.data(), nullptr);
     if (rc) return rc;
     for (int j = 0; j < n_out; ++j) c[n_in + j] = r[j];
     spec.store(v, nd + ns, lam_t, m);
     return NNC_OK;
+  }
+  // device-resident Hessian: W_DD = -H (the objective is linear)
+  DevEval de;
+  bool dense_on = false;
+  std::vector<double> hf, wdd;
+  bool dense_capable() const override { return tensor_core_form(net); }
+  bool set_dense_on_device(bool on) override {
+    if (on && !de.d && !de.init(net, n_in, n_out)) return false;
+    dense_on = on;
+    spec.valid = false;
+    hf.assign(n_in, 0.0);
+    return true;
+  }
+  const double* dense_dev() const override { return de.H; }
+  double dense_scale() const override { return -1.0; }
+  const double* dense_diag() const override { return hf.data(); }
+  cudaStream_t dense_stream() const override { return de.st; }
+  const double* host_wdd() override {
+    const double* Hh = de.hess_host();
+    if (!Hh) return nullptr;
+    wdd.resize((size_t)nd * nd);
+#pragma omp parallel for schedule(static) if (nd >= 256)
+    for (int i = 0; i < nd; ++i)
+      for (int j = 0; j < nd; ++j) wdd[(size_t)i * nd + j] = -Hh[(size_t)i * nd + j];
+    return wdd.data();
   }
   bool has_derivs(const double* v, const double* lam) const override { return spec.match(v, lam); }
   void fill_jac(double* AD, double* AS) {
@@ -1552,12 +1810,14 @@ struct AdversarialL1 : IpmProblem {
   int jac_hess(const double* v, const double* lam, double* AD, double* AS, double* WDD,
                double* WSS) override {
     if (!spec.match(v, lam)) {   // else J and H are those of the accepted trial point
-      int rc = nnc_eval_kkt(net, v, nullptr, lam + n_in, nullptr, J.data(), H.data(), nullptr);
+      int rc = dense_on ? de.eval(v, nullptr, lam + n_in, nullptr, J.data())
+                        : nnc_eval_kkt(net, v, nullptr, lam + n_in, nullptr, J.data(), H.data(), nullptr);
       if (rc) return rc;
     }
     spec.valid = false;
     fill_jac(AD, AS);
-    fill_wdd(WDD, WSS);
+    if (dense_on) std::fill(WSS, WSS + ns, 0.0);
+    else fill_wdd(WDD, WSS);
     return NNC_OK;
   }
 };
@@ -2069,6 +2329,7 @@ void nnc_ipm_default_options(nnc_ipm_options* o) {
   o->max_ls_failures = 5;
   o->verbose = 0;
   o->warm_mu0 = 1e-3;
+  o->kkt_on_device = 1;
 }
 
 int nnc_ipm_adversarial(nnc_net* net, const double* x0, int target, double margin,

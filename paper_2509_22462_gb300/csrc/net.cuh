@@ -100,5 +100,6 @@ struct nnc_net {
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   std::vector<int> ev_kind;
+  std::vector<int> ev_weight;   // launches each recorded event pair stands for
 };
 

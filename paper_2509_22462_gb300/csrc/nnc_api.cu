@@ -98,7 +98,10 @@ int check_dev_err(nnc_net* net) {
 cudaStream_t pick(nnc_net* net, void* st) { return st ? (cudaStream_t)st : net->stream; }
 
 // Kernel kinds of nnc_profile_read.
-enum { PK_TANGENT = 0, PK_SYRK = 1, PK_FWD = 2, PK_REV = 3, PK_OTHER = 4, PK_N = 5 };
+// PK_TAN_SPAN: one pair of events around the whole chain of tangent GEMMs of an evaluation (from
+// before the first to after the last), counted as that many launches; recorded only when asked
+// for by its own bit, so that no event sits between the chain's launches.
+enum { PK_TANGENT = 0, PK_SYRK = 1, PK_FWD = 2, PK_REV = 3, PK_OTHER = 4, PK_TAN_SPAN = 5, PK_N = 6 };
 
 // Brackets one launch with a pair of events on its stream when profiling is on.
 struct ProfScope {
@@ -120,6 +123,7 @@ struct ProfScope {
     idx = net->ev_used;
     net->ev_used += 2;
     net->ev_kind.push_back(kind);
+    net->ev_weight.push_back(1);
     cudaEventRecord(net->ev_pool[idx], st);
   }
   ~ProfScope() {
@@ -289,10 +293,14 @@ int run_hessian(nnc_net* net, const double* lam, double* H, cudaStream_t st, boo
                             net->K_total, st));
   }
   int cur = 0;
+  // span of the whole tangent chain (PK_TAN_SPAN), counted as its number of tangent GEMMs
+  ProfScope span(net, PK_TAN_SPAN, st);
+  int span_launches = 0;
   for (int l = 1; l < net->L; ++l) {
     LayerDev& Ly = net->layers[l];
     const bool last = (l == net->L - 1);
     if (last && Ly.zy_off < 0) break;  // a linear output layer adds nothing to H
+    ++span_launches;
     void* Anext_hi = last ? nullptr : net->At[1 - cur][0];
     void* Anext_lo = last ? nullptr : net->At[1 - cur][1];
     if (prec == NNC_FP8) {
@@ -314,6 +322,17 @@ int run_hessian(nnc_net* net, const double* lam, double* H, cudaStream_t st, boo
                              net->K_total, st));
     }
     cur = 1 - cur;
+  }
+  if (span.on) {
+    if (span_launches) {
+      cudaEventRecord(net->ev_pool[span.idx + 1], st);
+      net->ev_weight[net->ev_weight.size() - 1] = span_launches;
+    } else {     // no tangent GEMM: drop the pair
+      net->ev_used -= 2;
+      net->ev_kind.pop_back();
+      net->ev_weight.pop_back();
+    }
+    span.on = false;
   }
   if (net->softmax) {
     // the rank-two part of the softmax layer's curvature as two extra operand columns
@@ -451,9 +470,10 @@ int nnc_profile(nnc_net* net, int enable) {
   int r = check_net(net);
   if (r) return r;
   // 1: every kind; other nonzero values: a mask of kinds, bit (k + 1) for kind k
-  net->prof_mask = enable == 0 ? 0u : enable == 1 ? ~0u : (unsigned)enable >> 1;
+  net->prof_mask = enable == 0 ? 0u : enable == 1 ? ~(1u << PK_TAN_SPAN) : (unsigned)enable >> 1;
   net->ev_used = 0;
   net->ev_kind.clear();
+  net->ev_weight.clear();
   return NNC_OK;
 }
 
@@ -472,11 +492,12 @@ int nnc_profile_read(nnc_net* net, double* ms, long long* count, int n_kinds) {
     const int k = net->ev_kind[i];
     if (k < n_kinds) {
       ms[k] += t;
-      count[k] += 1;
+      count[k] += net->ev_weight[i];
     }
   }
   net->ev_used = 0;
   net->ev_kind.clear();
+  net->ev_weight.clear();
   return NNC_OK;
 }
 

@@ -47,7 +47,8 @@ class IpmOptions(ctypes.Structure):
                 ("kappa_w_plus", ctypes.c_double), ("kappa_w_plus_bar", ctypes.c_double),
                 ("kappa_w_minus", ctypes.c_double), ("kappa_sigma", ctypes.c_double),
                 ("max_backtracks", ctypes.c_int), ("max_ls_failures", ctypes.c_int),
-                ("verbose", ctypes.c_int), ("warm_mu0", ctypes.c_double)]
+                ("verbose", ctypes.c_int), ("warm_mu0", ctypes.c_double),
+                ("kkt_on_device", ctypes.c_int)]
 
 
 class IpmResult(ctypes.Structure):
@@ -62,7 +63,7 @@ class IpmResult(ctypes.Structure):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["status_name"] = IPM_STATUS.get(self.status, str(self.status))
         return d
-PROFILE_KINDS = ["tangent_gemm", "syrk", "forward", "reverse", "other"]
+PROFILE_KINDS = ["tangent_gemm", "syrk", "forward", "reverse", "other", "tangent_chain"]
 
 
 class NNCError(RuntimeError):

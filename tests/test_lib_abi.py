@@ -39,9 +39,10 @@ def test_ipm_option_defaults_match_oracle():
     o = nnc.ipm_options()
     ref = ipm.Options()
     for name, _ in nnc.IpmOptions._fields_:
-        if name == "verbose":
+        if name in ("verbose", "kkt_on_device"):    # not part of the method: output, placement
             continue
         assert getattr(o, name) == getattr(ref, name), name
+    assert o.kkt_on_device == 1
 
 
 def test_status_codes_match_header():
