@@ -519,8 +519,8 @@ def timed_kernel_pass(net, step, steps, torch):
 def tangent_roofline(net, spec, prec, roof_pass, prof, peaks, peak_src):
     """Roofline of the dominant kernel, the tangent GEMM (the largest single kernel of a step):
     algorithmic FLOPs per launch over the average launch time of the timed kernel pass."""
-    dom_name = "tangent_gemm" if prof.get("tangent_gemm", (0, 0))[1] > 0 else \
-        max(prof.items(), key=lambda kv: kv[1][0])[0]
+    has_tan = prof.get("tangent_gemm", (0, 0))[1] > 0 or roof_pass.get("tangent_chain", (0, 0))[1] > 0
+    dom_name = "tangent_gemm" if has_tan else max(prof.items(), key=lambda kv: kv[1][0])[0]
     if dom_name == "tangent_gemm" and roof_pass.get("tangent_chain", (0, 0))[1]:
         dom_ms, dom_cnt = roof_pass["tangent_chain"]
     else:
