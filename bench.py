@@ -534,7 +534,9 @@ def tangent_roofline(net, spec, prec, roof_pass, prof, peaks, peak_src):
         # the kernel is timed inside a step of well under a second: the burst peak applies
         # (for FP8 operands the measured BF16 peak times the nominal 2x of e4m3)
         pk = peaks.get("bf16_tflops") * (2.0 if prec == "fp8" else 1.0)
-        kname = ("k_tc_pair (tangent on SM pairs, tcgen05 cta_group::2: Zdot_l = W_l Adot_{l-1}, "
+        kname = ("k_tc_chain (every tangent GEMM Zdot_l = W_l Adot_{l-1} of the step in one persistent "
+                 "tcgen05 launch, fused sigma' / sigma'' epilogue; per-layer average)" if tangent_bn == 1 else
+                 "k_tc_pair (tangent on SM pairs, tcgen05 cta_group::2: Zdot_l = W_l Adot_{l-1}, "
                  "fused sigma' / sigma'' epilogue)" if tangent_bn < 0 else
                  "k_tc_gemm (tangent: Zdot_l = W_l Adot_{l-1}, fused sigma' / sigma'' epilogue)")
         mult = {"bf16x3": 3, "bf16": 1, "fp8": 1}.get(prec, 1)

@@ -159,6 +159,45 @@ extern "C" int nnc_autotune(nnc_net* net, const char* cache_path, int retune) {
     for (size_t i = 0; i < ls.size(); ++i)
       if (best != plan_code(net->layers[ls[i]].plan_tan)) net->layers[ls[i]].plan_tan = fresh[i];
   }
+  // the persistent chain (one launch for every tangent GEMM) against the per-layer launches just
+  // chosen, over the same layers and buffers
+  if (net->chain_nl > 0) {
+    const std::string key = key_of(net, "chain", net->chain_plans[0].M, n, net->chain_nl);
+    auto it = cache.find(key);
+    int use = 1;
+    if (it != cache.end() && !retune) {
+      use = it->second.first;
+    } else {
+      std::vector<ChainOut> outs(net->chain_nl);
+      for (int i = 0; i < net->chain_nl; ++i) {
+        LayerDev& Ly = net->layers[i + 1];
+        const bool last = i + 1 == net->L - 1;
+        const int cur = i % 2;
+        auto zo = [&](void* base) {
+          return (base && Ly.zy_off >= 0) ? (void*)((char*)base + (size_t)Ly.zy_off * 2) : nullptr;
+        };
+        outs[i] = ChainOut{Ly.s1, Ly.c_f, last ? nullptr : net->At[1 - cur][0],
+                           last ? nullptr : net->At[1 - cur][1], Ly.mp, zo(net->Zt[0]), zo(net->Zt[1]),
+                           nullptr, nullptr};
+      }
+      const size_t cb = sizeof(unsigned) * (size_t)net->chain_nl * net->chain_plans[0].ntn;
+      const double us_chain = time_us(st, 3, [&] {
+        cudaMemsetAsync(net->chain_cnt, 0, cb, st);
+        tc_tangent_chain(net->chain_plans.data(), outs.data(), net->chain_nl, net->chain_cnt,
+                         net->K_total, net->dev_err, st);
+      });
+      const double us_layers = time_us(st, 3, [&] {
+        for (int i = 0; i < net->chain_nl; ++i) {
+          LayerDev& Ly = net->layers[i + 1];
+          tc_tangent(Ly.plan_tan, Ly.s1, Ly.c_f, outs[i].at_hi, outs[i].at_lo, Ly.mp, outs[i].zt_hi,
+                     outs[i].zt_lo, nullptr, nullptr, net->K_total, net->dev_err, st, Ly.w8s, net->tsc);
+        }
+      });
+      use = us_chain < us_layers ? 1 : 0;
+      cache[key] = {use, use ? us_chain : us_layers};
+    }
+    net->use_chain = use != 0;
+  }
   // symmetric product: split-K count (bounded by the partial-sum buffer allocated at load)
   if (net->K_total > 0 && net->plan_syrk.ready) {
     const std::string key = key_of(net, "syrk", n, n, net->K_total);
@@ -223,10 +262,23 @@ extern "C" int nnc_tune_set(nnc_net* net, int tangent_bn, int syrk_splits) {
     const int t = tangent_bn;
     const bool single = t == 112 || t == 128 || t == 208 || t == 256;
     const bool pair = t == -128 || t == -160 || t == -208 || t == -256;
-    if (t && !single && !pair) {
-      set_last_error("tangent tile must be 112, 128, 208, 256 (one SM) or -128, -160, -208, -256 "
-                     "(SM pairs)");
+    if (t == 1) {   // the persistent chain
+      if (net->chain_nl <= 0) {
+        set_last_error("this net has no persistent tangent chain (FP8 form, or too many layers)");
+        return NNC_ERR_ARG;
+      }
+      if (syrk_splits < 0 || syrk_splits > net->h_splits) {
+        set_last_error("symmetric-product splits out of range");
+        return NNC_ERR_ARG;
+      }
+      net->use_chain = true;
+      tangent_bn = 0;
+    } else if (t && !single && !pair) {
+      set_last_error("tangent tile must be 112, 128, 208, 256 (one SM), -128, -160, -208, -256 "
+                     "(SM pairs) or 1 (the persistent chain)");
       return NNC_ERR_ARG;
+    } else if (t) {
+      net->use_chain = false;
     }
     if (pair && prec == NNC_FP8) {
       set_last_error("the SM-pair tangent kernel has no FP8 form");
@@ -276,7 +328,10 @@ extern "C" int nnc_tuning(const nnc_net* net, int layer, int* tangent_bn, int* s
     set_last_error("bad arguments");
     return NNC_ERR_ARG;
   }
-  if (tangent_bn) *tangent_bn = net->layers[layer].plan_tan.ready ? plan_code(net->layers[layer].plan_tan) : 0;
+  if (tangent_bn)
+    *tangent_bn = !net->layers[layer].plan_tan.ready ? 0
+                  : (net->use_chain && layer >= 1 && layer <= net->chain_nl) ? 1
+                  : plan_code(net->layers[layer].plan_tan);
   if (syrk_splits) *syrk_splits = net->plan_syrk.ready ? net->plan_syrk.splits : net->h_splits;
   return NNC_OK;
 }

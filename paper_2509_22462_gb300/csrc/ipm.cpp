@@ -44,6 +44,7 @@ int dkkt_maxabs(DenseKktDev* d, const double* H, double s, const double* hf, dou
 int dkkt_matvec(DenseKktDev* d, const double* H, const double* x, double* u);
 int dkkt_factor(DenseKktDev* d, const double* H, double s, const double* dvec, const double* AD,
                 int m, bool* pd, const double** result);
+int dkkt_solve(DenseKktDev* d, double* x, int lower);
 }  // namespace nnc
 
 namespace {
@@ -552,7 +553,8 @@ struct KktSolver {
   // device factorization
   const double* Kp = nullptr;
   DenseOnDevice* dev = nullptr;   // dense block on the device (null: host)
-  int dev_error = 0;              // nnc_status of a failed device factorization
+  bool dev_factor = false;        // L of the current factorization is on the device
+  int dev_error = 0;              // nnc_status of a failed device factorization or solve
   std::vector<double> dvec, pinadd;
   BK bkS, bkF, bkT, bkR;
   std::vector<int> zid;   // mode 3: small-block variables with a zero diagonal (free, no curvature)
@@ -698,6 +700,7 @@ struct KktSolver {
     ldk = nd + m;
     bool pd = nd == 0;
     bool host_factor = !dev || nd == 0;
+    dev_factor = false;
     if (dev && nd > 0) {
       // assembly and partial Cholesky of the bordered matrix on the device (H stays there)
       dvec.resize(nd);
@@ -710,7 +713,8 @@ struct KktSolver {
         return;
       }
       if (pd) {
-        Kp = res;
+        Kp = res;   // border rows only; L stays on the device
+        dev_factor = true;
       } else {
         // not positive definite in FP32 (or nearly singular): the FP64 host path decides, with
         // W_DD (+ the pinning terms) on the host
@@ -958,6 +962,23 @@ struct KktSolver {
     for (int j = 0; j < m; ++j) rhs[n + j] = q[u0 + j];
   }
 
+  // L^-1 x and L^-T x with the current factorization's L (on the device or in Kp)
+  void lsolve(double* x) {
+    if (dev_factor) {
+      const int rc = nnc::dkkt_solve(dev->dk, x, 1);
+      if (rc) dev_error = rc;
+    } else {
+      lower_solve1(nd, Kp, x, ldk);
+    }
+  }
+  void usolve(double* x) {
+    if (dev_factor) {
+      const int rc = nnc::dkkt_solve(dev->dk, x, 0);
+      if (rc) dev_error = rc;
+    } else {
+      upper_solve_lt(nd, Kp, x, ldk);
+    }
+  }
   bool full() const { return mode == 1; }
   void solve_core(double* rhs) {
     if (mode == 4) {
@@ -972,7 +993,7 @@ struct KktSolver {
       // [w_Z; z] = R^-1 [r2_Z; r3 - A_D K11^-1 r1 - A_P D_P^-1 r2_P]; then u and w_P as in mode 2
       const int nz = (int)zid.size();
       tmp.assign(rhs, rhs + nd);
-      if (nd) lower_solve1(nd, Kp, tmp.data(), ldk);
+      if (nd) lsolve(tmp.data());
       std::vector<double> q(nz + m);
       for (int k = 0; k < nz; ++k) q[k] = rhs[nd + zid[k]];
       const std::vector<double> yt = ytmul(nd, m, Y.data(), tmp.data());   // A_D K11^-1 r1 = Y^T t
@@ -988,7 +1009,7 @@ struct KktSolver {
       // u = K11^-1 (r1 - A_D^T z) with L^-1 (r1 - A_D^T z) = t - Y z: one backward solve
       std::vector<double> u(nd);
       for (int i = 0; i < nd; ++i) u[i] = tmp[i] - dot4(&Y[(size_t)i * m], z, m);
-      if (nd) upper_solve_lt(nd, Kp, u.data(), ldk);
+      if (nd) usolve(u.data());
       for (int c = 0; c < ns; ++c) {
         double s = rhs[nd + c];
         for (int j = 0; j < m; ++j) s -= AS_[(size_t)j * ns + c] * z[j];
@@ -1002,7 +1023,7 @@ struct KktSolver {
     if (mode == 2) {
       // z = T^-1 (r3 - A_D K11^-1 r1 - A_S D^-1 r2); u = K11^-1 (r1 - A_D^T z); w = D^-1 (r2 - A_S^T z)
       tmp.assign(rhs, rhs + nd);
-      if (nd) lower_solve1(nd, Kp, tmp.data(), ldk);     // t = L^-1 r1; A_D K11^-1 r1 = Y^T t
+      if (nd) lsolve(tmp.data());     // t = L^-1 r1; A_D K11^-1 r1 = Y^T t
       std::vector<double> z(m);
       const std::vector<double> yt = ytmul(nd, m, Y.data(), tmp.data());
       for (int j = 0; j < m; ++j) {
@@ -1022,7 +1043,7 @@ struct KktSolver {
       // u = K11^-1 (r1 - A_D^T z) with L^-1 (r1 - A_D^T z) = t - Y z (Y = L^-1 A_D^T is stored)
       std::vector<double> u(nd);
       for (int i = 0; i < nd; ++i) u[i] = tmp[i] - dot4(&Y[(size_t)i * m], z.data(), m);
-      if (nd) upper_solve_lt(nd, Kp, u.data(), ldk);
+      if (nd) usolve(u.data());
       for (int c = 0; c < ns; ++c) {
         double s = rhs[nd + c];
         for (int j = 0; j < m; ++j) s -= AS_[(size_t)j * ns + c] * z[j];
@@ -1034,14 +1055,14 @@ struct KktSolver {
     }
     // [K11 K12; K12^T K22] [u; w] = [r1; r2]: w = S^-1 (r2 - Y^T L^-1 r1), u = K11^-1 (r1 - K12 w)
     tmp.assign(rhs, rhs + nd);
-    if (nd) lower_solve1(nd, Kp, tmp.data(), ldk);
+    if (nd) lsolve(tmp.data());
     std::vector<double> w(r);
     const std::vector<double> yt = ytmul(nd, r, Y.data(), tmp.data());
     for (int a = 0; a < r; ++a) w[a] = rhs[nd + a] - yt[a];
     bkS.solve(w.data());
     // u = K11^-1 (r1 - K12 w) with L^-1 (r1 - K12 w) = t - Y w (Y = L^-1 K12)
     for (int i = 0; i < nd; ++i) tmp[i] -= dot4(&Y[(size_t)i * r], w.data(), r);
-    if (nd) upper_solve_lt(nd, Kp, tmp.data(), ldk);
+    if (nd) usolve(tmp.data());
     for (int i = 0; i < nd; ++i) rhs[i] = tmp[i];
     for (int a = 0; a < r; ++a) rhs[nd + a] = w[a];
   }
@@ -1340,6 +1361,7 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
     const auto t_sol = Clock::now();
     sol = rhs;
     kkt.solve(sol.data());
+    if (kkt.dev_error) { status = NNC_IPM_EVAL_ERROR; T.solver += secs(t_lin, Clock::now()); break; }
     const auto t_sol_end = Clock::now();
     for (int i = 0; i < n; ++i) dv[i] = sol[i];
     for (int j = 0; j < m; ++j) dl[j] = sol[n + j];

@@ -51,6 +51,23 @@ struct TcArgs {
   long long ldh_split;
 };
 
+// Per-layer description of the persistent tangent chain (k_tc_chain).
+struct ChainLayer {
+  int ntm, nkb, tile0;   // row blocks, K blocks, index of the layer's first tile
+  const double* s1;
+  const float* c;
+  __nv_bfloat16 *at_hi, *at_lo;   // Adot_l^T (row stride ldo), NULL on the last layer
+  int ldo;
+  __nv_bfloat16 *zt_hi, *zt_lo, *yt_hi, *yt_lo;   // at the layer's column offset (row stride ldz)
+};
+struct ChainArgs {
+  CUtensorMap ta_hi[kMaxChain], ta_lo[kMaxChain], tb_hi[kMaxChain], tb_lo[kMaxChain];
+  ChainLayer L[kMaxChain];
+  int nl, N, ntn, ldz, tiles;
+  unsigned* cnt;   // [nl][ntn] arrival counters, zero at launch
+  int* err;
+};
+
 // K-block of one pipeline stage, in elements: 64 (one 128-byte swizzled row) for single BF16; 32
 // (64-byte swizzle) for split-BF16x3, whose stages carry four operand tiles, so that five stages
 // fit in shared memory instead of two.
@@ -928,6 +945,243 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// ---------------------------------------------------------------- persistent tangent chain
+// The whole chain of tangent GEMMs of one evaluation (Zdot_l = W_l Adot_{l-1} for every hidden
+// layer, with the fused epilogue of TC_TANGENT) in one persistent launch: one CTA per SM takes the
+// (layer, column block, row block) tiles blockIdx.x, blockIdx.x + gridDim.x, ... in that order.
+// Layer l + 1's tiles of column block tn read Adot_l^T rows tn * BN .. (all of layer l's rows
+// along K), so they wait (bounded) for an arrival counter that the epilogues of layer l's tiles
+// of that column block advance: four arrivals (one per epilogue warp) per row block, released
+// after the warp's stores, acquired by the producer before its first copy of the tile, with a
+// proxy fence so that the tensor copies see the stores.  The same dependency covers the reuse of
+// the ping-pong buffers: the writer of Adot_{l+1}^T rows tn waits for every reader of those rows
+// (layer l's tiles of block tn).  A CTA only waits for tiles of a smaller index, which CTAs that
+// are resident or finished hold, so the chain cannot dead-lock; the copy ring runs on across
+// tiles and layers, and two TMEM accumulators overlap each epilogue with the next tile's MMAs.
+// Programmatic dependent launch: the first layer's operand is complete after griddepcontrol.wait.
+template <int BN, int MODE>
+__global__ void __launch_bounds__(kThreads, 1) k_tc_chain(const __grid_constant__ ChainArgs args) {
+  using C = Cfg<BN, MODE>;
+  constexpr bool X3 = C::X3;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + C::STAGES * C::STAGE_BYTES);
+  uint64_t* empty = full + C::STAGES;
+  uint64_t* accf = empty + C::STAGES;   // [2]: accumulator b holds a finished tile
+  uint64_t* tfree = accf + 2;           // [2]: the epilogue has read accumulator b
+  uint64_t* mdone = tfree + 2;          // every MMA issued has completed
+  uint32_t* tmem_slot = (uint32_t*)(mdone + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  volatile int* consumed_sh = (volatile int*)(tmem_slot + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tiles = args.tiles;
+  if ((int)blockIdx.x >= tiles) return;
+  // tile t -> (layer, column block, row block); layers in order, column blocks, then rows
+  auto decode = [&](int t, int& li, int& tn, int& tm) {
+    li = 0;
+    while (li + 1 < args.nl && t >= args.L[li + 1].tile0) ++li;
+    const int local = t - args.L[li].tile0;
+    tn = local / args.L[li].ntm;
+    tm = local % args.L[li].ntm;
+  };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&accf[b]), 1);
+      mbar_init(smem_u32(&tfree[b]), 4);   // one arrival per epilogue warp
+    }
+    mbar_init(smem_u32(mdone), 1);
+    *abort_flag = 0;
+    *consumed_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  griddep_wait();   // the first layer's operand and the cleared counters are complete
+
+  int issued = 0;  // producer only
+  if (warp == 0) {
+    if (lane == 0) {
+      int i = 0;
+      bool stop = false;
+      for (int t = blockIdx.x; t < tiles && !stop; t += gridDim.x) {
+        int li, tn, tm;
+        decode(t, li, tn, tm);
+        const ChainLayer& Ly = args.L[li];
+        if (li > 0) {
+          // every row block of the previous layer's column block tn is written (acquire)
+          const unsigned* cnt = args.cnt + (size_t)(li - 1) * args.ntn + tn;
+          const unsigned need = 4u * (unsigned)args.L[li - 1].ntm;
+          unsigned v;
+          asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(cnt) : "memory");
+          if (v < need) {
+            const long long t0 = clock64();
+            while (true) {
+              asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(cnt) : "memory");
+              if (v >= need) break;
+              if (*abort_flag) {
+                stop = true;
+                break;
+              }
+              if (clock64() - t0 > kWaitCycles) {
+                atomicCAS(args.err, 0, 51);
+                *abort_flag = 1;
+                stop = true;
+                break;
+              }
+            }
+            if (stop) break;
+          }
+          asm volatile("fence.proxy.async.global;" ::: "memory");
+        }
+        const int a_row0 = tm * BM, b_row0 = tn * BN;
+        for (int kb = 0; kb < Ly.nkb; ++kb, ++i) {
+          const int s = i % C::STAGES;
+          const uint32_t ph = (uint32_t)(i / C::STAGES) & 1u;
+          if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1u, args.err, 52, abort_flag)) {
+            stop = true;
+            break;
+          }
+          uint8_t* st = smem + s * C::STAGE_BYTES;
+          const uint32_t fb = smem_u32(&full[s]);
+          mbar_expect_tx(fb, C::TX_BYTES);
+          const int kx = kb * C::BKE;
+          tma_load_2d(smem_u32(st), &args.ta_hi[li], fb, kx, a_row0);
+          if (X3) tma_load_2d(smem_u32(st + C::A_BYTES), &args.ta_lo[li], fb, kx, a_row0);
+          tma_load_2d(smem_u32(st + C::NPARTS * C::A_BYTES), &args.tb_hi[li], fb, kx, b_row0);
+          if (X3)
+            tma_load_2d(smem_u32(st + C::NPARTS * C::A_BYTES + C::B_BYTES), &args.tb_lo[li], fb, kx, b_row0);
+          issued = i + 1;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int i = 0, pi = 0;
+      bool stop = false;
+      for (int t = blockIdx.x; t < tiles && !stop; t += gridDim.x, ++pi) {
+        int li, tn, tm;
+        decode(t, li, tn, tm);
+        const int b = pi & 1;
+        if (pi >= 2 &&
+            !mbar_wait(smem_u32(&tfree[b]), (uint32_t)((pi - 2) >> 1) & 1u, args.err, 53, abort_flag))
+          break;
+        tc_fence_after();
+        const int n_eff = (min(BN, args.N - tn * BN) + 15) / 16 * 16;
+        const uint32_t idesc = C::IDESC_NO_N | ((uint32_t)(n_eff >> 3) << 17);
+        const uint32_t d = tmem + (uint32_t)(b * 256);
+        const int nkb = args.L[li].nkb;
+        for (int kb = 0; kb < nkb; ++kb, ++i) {
+          const int s = i % C::STAGES;
+          const uint32_t ph = (uint32_t)(i / C::STAGES) & 1u;
+          if (!mbar_wait(smem_u32(&full[s]), ph, args.err, 54, abort_flag)) {
+            stop = true;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = smem_u32(smem + s * C::STAGE_BYTES);
+          const uint32_t a_hi = st, a_lo = st + C::A_BYTES;
+          const uint32_t b_hi = st + C::NPARTS * C::A_BYTES;
+          const uint32_t b_lo = b_hi + C::B_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < C::ROWB / 32; ++kk) {
+            const uint32_t off = kk * 32;
+            constexpr int SW = C::SWZ, SB = C::SBO;
+            umma_bf16(d, sdesc<SW, SB>(a_hi + off), sdesc<SW, SB>(b_hi + off), idesc,
+                      (kb > 0 || kk > 0) ? 1u : 0u);
+            if (X3) {
+              umma_bf16(d, sdesc<SW, SB>(a_hi + off), sdesc<SW, SB>(b_lo + off), idesc, 1u);
+              umma_bf16(d, sdesc<SW, SB>(a_lo + off), sdesc<SW, SB>(b_hi + off), idesc, 1u);
+            }
+          }
+          umma_commit(smem_u32(&empty[s]));
+        }
+        if (!stop) umma_commit(smem_u32(&accf[b]));
+      }
+      *consumed_sh = i;
+      umma_commit(smem_u32(mdone));
+    }
+  } else {
+    const int q = warp & 3;  // TMEM lanes 32q .. 32q+31 belong to this warp
+    const int row = q * 32 + lane;
+    int pi = 0;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++pi) {
+      int li, tn, tm;
+      decode(t, li, tn, tm);
+      const ChainLayer& Ly = args.L[li];
+      const int b = pi & 1;
+      if (!mbar_wait(smem_u32(&accf[b]), (uint32_t)(pi >> 1) & 1u, args.err, 55, abort_flag)) break;
+      tc_fence_after();
+      // the kernel after the chain may be queued once this CTA's last tile is in its epilogue
+      if (t + (int)gridDim.x >= tiles && threadIdx.x == 64) griddep_launch();
+      const int n0 = tn * BN;
+      const int n_eff = (min(BN, args.N - n0) + 15) / 16 * 16;
+      const int m = tm * BM + row;   // row of W_l
+      const float sm = (float)Ly.s1[m];
+      const float cm = Ly.c ? Ly.c[m] : 0.f;
+      const uint32_t dt = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 256);
+#pragma unroll 1
+      for (int c0 = 0; c0 < n_eff; c0 += 16) {
+        float v[16];
+        tmem_ld16(dt + (uint32_t)c0, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int n = n0 + c0 + j;
+          if (n < args.N) {
+            if (Ly.at_hi) put<X3>(Ly.at_hi, Ly.at_lo, (size_t)n * Ly.ldo + m, sm * v[j]);
+            if (Ly.zt_hi) put<X3>(Ly.zt_hi, Ly.zt_lo, (size_t)n * args.ldz + m, v[j]);
+            if (Ly.yt_hi) put<X3>(Ly.yt_hi, Ly.yt_lo, (size_t)n * args.ldz + m, cm * v[j]);
+          }
+        }
+      }
+      tc_fence_before();
+      // release this warp's stores to the next layer's producers, then free the accumulator
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) {
+        atomicAdd(args.cnt + (size_t)li * args.ntn + tn, 1u);
+        mbar_arrive(smem_u32(&tfree[b]));
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1 && lane == 0) {
+    volatile int no_abort = 0;
+    mbar_wait(smem_u32(mdone), 0, args.err, 56, &no_abort, *abort_flag ? kWaitCycles / 8 : kWaitCycles);
+  }
+  if (*abort_flag && warp == 0 && lane == 0) {
+    for (int i = *consumed_sh; i < issued; ++i) {
+      const int s = i % C::STAGES;
+      const uint32_t ph = (uint32_t)(i / C::STAGES) & 1u;
+      volatile int no_abort = 0;
+      mbar_wait(smem_u32(&full[s]), ph, args.err, 57, &no_abort, kWaitCycles / 8);
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512)
+                 : "memory");
+  }
+}
+
 // Self-test of the tensor-core kernels' bounded wait (with the CTA abort flag): an mbarrier that
 // nothing arrives on; the wait gives up after `limit` cycles, records `code` and sets the flag,
 // which a second wait then sees at once.
@@ -1257,6 +1511,85 @@ cudaError_t launch_gtan_mode(const TcPlan& p, const TcArgs& a, int groups, int g
   if (p.mode == MODE_BF16X3) return launch_gtan_t<BN, MODE_BF16X3>(p, a, groups, grid, st);
   if (p.mode == MODE_BF16) return launch_gtan_t<BN, MODE_BF16>(p, a, groups, grid, st);
   return cudaErrorInvalidValue;
+}
+
+template <int BN, int MODE>
+cudaError_t launch_chain_t(const ChainArgs& a, int grid, cudaStream_t st) {
+  using C = Cfg<BN, MODE>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_chain<BN, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = C::SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_tc_chain<BN, MODE>, a);
+  note_launch();
+  return e;
+}
+
+template <int BN>
+cudaError_t launch_chain_mode(int mode, const ChainArgs& a, int grid, cudaStream_t st) {
+  if (mode == MODE_BF16X3) return launch_chain_t<BN, MODE_BF16X3>(a, grid, st);
+  if (mode == MODE_BF16) return launch_chain_t<BN, MODE_BF16>(a, grid, st);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t tc_tangent_chain(const TcPlan* plans, const ChainOut* outs, int nl, unsigned* cnt,
+                             int ldz, int* err, cudaStream_t st) {
+  if (nl < 1 || nl > kMaxChain || !cnt) return cudaErrorInvalidValue;
+  ChainArgs a{};
+  const TcPlan& p0 = plans[0];
+  int tiles = 0;
+  for (int l = 0; l < nl; ++l) {
+    const TcPlan& p = plans[l];
+    if (!p.ready || p.kind != TC_TANGENT || p.pair || p.bn != p0.bn || p.mode != p0.mode ||
+        p.N != p0.N || p.splits != 1)
+      return cudaErrorInvalidValue;
+    a.ta_hi[l] = p.ta_hi;
+    a.ta_lo[l] = p.ta_lo;
+    a.tb_hi[l] = p.tb_hi;
+    a.tb_lo[l] = p.tb_lo;
+    ChainLayer& L = a.L[l];
+    L.ntm = p.ntm;
+    L.nkb = p.K / p.bk;
+    L.tile0 = tiles;
+    L.s1 = outs[l].s1;
+    L.c = outs[l].c;
+    L.at_hi = (__nv_bfloat16*)outs[l].at_hi;
+    L.at_lo = (__nv_bfloat16*)outs[l].at_lo;
+    L.ldo = outs[l].ldo;
+    L.zt_hi = (__nv_bfloat16*)outs[l].zt_hi;
+    L.zt_lo = (__nv_bfloat16*)outs[l].zt_lo;
+    L.yt_hi = (__nv_bfloat16*)outs[l].yt_hi;
+    L.yt_lo = (__nv_bfloat16*)outs[l].yt_lo;
+    tiles += p.ntm * p.ntn;
+  }
+  a.nl = nl;
+  a.N = p0.N;
+  a.ntn = p0.ntn;
+  a.ldz = ldz;
+  a.tiles = tiles;
+  a.cnt = cnt;
+  a.err = err;
+  const int grid = std::min(p0.sm_count > 0 ? p0.sm_count : 148, tiles);
+  switch (p0.bn) {
+    case 112: return launch_chain_mode<112>(p0.mode, a, grid, st);
+    case 128: return launch_chain_mode<128>(p0.mode, a, grid, st);
+    case 208: return launch_chain_mode<208>(p0.mode, a, grid, st);
+    case 256: return launch_chain_mode<256>(p0.mode, a, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t tc_tangent_grouped(const TcPlan& p, int groups, const int* g_n, const int* g_boff,

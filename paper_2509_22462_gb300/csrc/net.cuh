@@ -77,6 +77,13 @@ struct nnc_net {
   void* Zt[2] = {nullptr, nullptr};  // [hi, lo]: Zdot_l^T of all curved layers, n x K_total
   void* Yt[2] = {nullptr, nullptr};  // [hi, lo]: (c_l * Zdot_l)^T, n x K_total
   int K_total = 0;                   // sum of mp_l over layers with sigma'' != 0 (+ 128: softmax)
+  // persistent chain of tangent GEMMs (BF16 and split-BF16x3 forms; k_tc_chain): plans of layers
+  // 1 .. chain_nl with one N tile, the chain's arrival counters, and whether evaluations use it
+  // (chosen by the autotuner or nnc_tune_set)
+  std::vector<nnc::TcPlan> chain_plans;
+  int chain_nl = 0;
+  unsigned* chain_cnt = nullptr;
+  bool use_chain = false;
   bool softmax = false;              // softmax output layer
   int ext_off = -1;                  // its two rank-two curvature columns in the Zdot / Ydot arrays
   void* Zb[2][3] = {};  // reverse seeds^T [48][mp_max], ping-pong x three BF16 parts

@@ -282,6 +282,9 @@ int run_hessian(nnc_net* net, const double* lam, double* H, cudaStream_t st, boo
     return (base && off >= 0) ? (void*)((char*)base + (size_t)off * es) : nullptr;
   };
   LayerDev& L1 = net->layers[0];
+  if (tc && net->use_chain && net->chain_nl > 0)
+    CK(cudaMemsetAsync(net->chain_cnt, 0,
+                       sizeof(unsigned) * (size_t)net->chain_nl * net->chain_plans[0].ntn, st));
   {
     PROF(PK_OTHER);
     TanBuf At0{net->At[0][0], net->At[0][1]};
@@ -292,6 +295,28 @@ int run_hessian(nnc_net* net, const double* lam, double* H, cudaStream_t st, boo
                             L1.mp, n, L1.s1, L1.c, net->L > 1 ? At0 : TanBuf{}, L1.mp, Zt, Yt,
                             net->K_total, st));
   }
+  if (tc && net->use_chain && net->chain_nl > 0) {
+    // every tangent GEMM in one persistent launch; its counters are cleared before the first
+    // layer's kernel so that the chain still follows it by programmatic dependent launch
+    std::vector<ChainOut> outs(net->chain_nl);
+    for (int i = 0; i < net->chain_nl; ++i) {
+      LayerDev& Ly = net->layers[i + 1];
+      const bool last = i + 1 == net->L - 1;
+      const int cur = i % 2;
+      outs[i] = ChainOut{Ly.s1, Ly.c_f, last ? nullptr : net->At[1 - cur][0],
+                         last ? nullptr : net->At[1 - cur][1], Ly.mp,
+                         zoff(net->Zt[0], Ly.zy_off), zoff(net->Zt[1], Ly.zy_off),
+                         deferred ? nullptr : zoff(net->Yt[0], Ly.zy_off),
+                         deferred ? nullptr : zoff(net->Yt[1], Ly.zy_off)};
+    }
+    {
+      ProfScope span(net, PK_TAN_SPAN, st);
+      if (span.on) net->ev_weight.back() = net->chain_nl;
+      PROF(PK_TANGENT);
+      CK(tc_tangent_chain(net->chain_plans.data(), outs.data(), net->chain_nl, net->chain_cnt,
+                          net->K_total, net->dev_err, st));
+    }
+  } else {
   int cur = 0;
   // span of the whole tangent chain (PK_TAN_SPAN), counted as its number of tangent GEMMs
   ProfScope span(net, PK_TAN_SPAN, st);
@@ -333,6 +358,7 @@ int run_hessian(nnc_net* net, const double* lam, double* H, cudaStream_t st, boo
       net->ev_weight.pop_back();
     }
     span.on = false;
+  }
   }
   if (net->softmax) {
     // the rank-two part of the softmax layer's curvature as two extra operand columns
@@ -744,6 +770,36 @@ static int load_impl(nnc_net* net, int n_layers, const int* widths, const int* a
                                  net->At[cur][0], net->At[cur][1], n, Ly.kp, Ly.mp, n, Ly.kp,
                                  net->sm_count);
       if (r != NNC_OK) return fail(r, "tensor-core tangent plan failed");
+    }
+    // the persistent chain: every tangent GEMM of an evaluation in one launch (not FP8, whose
+    // tangent operand is re-quantized between layers)
+    if (prec == NNC_BF16 || prec == NNC_BF16X3) {
+      int nl = 0;
+      for (int l = 1; l < n_layers; ++l) {
+        if (l == n_layers - 1 && net->layers[l].zy_off < 0) break;
+        ++nl;
+      }
+      if (nl >= 1 && nl <= kMaxChain) {
+        net->chain_plans.assign(nl, TcPlan());
+        const int bn = net->layers[1].plan_tan.pair ? 208 : net->layers[1].plan_tan.bn;
+        bool ok = true;
+        for (int i = 0; i < nl && ok; ++i) {
+          LayerDev& Ly = net->layers[i + 1];
+          const int cur = i % 2;
+          ok = tc_plan_make(net->chain_plans[i], TC_TANGENT, prec, Ly.Whi, Ly.Wlo, Ly.mp, Ly.kp,
+                            net->At[cur][0], net->At[cur][1], n, Ly.kp, Ly.mp, n, Ly.kp,
+                            net->sm_count, bn) == NNC_OK;
+        }
+        if (ok) {
+          unsigned* cnt;
+          AL(cnt, (size_t)nl * net->chain_plans[0].ntn);
+          net->chain_cnt = cnt;
+          net->chain_nl = nl;
+          net->use_chain = true;
+        } else {
+          net->chain_plans.clear();
+        }
+      }
     }
     // reverse sweep on the tensor cores (seed columns padded to 16 or 48)
     if (net->S_max > 16 && net->S_max <= 48) {

@@ -55,6 +55,20 @@ cudaError_t tc_tangent(const TcPlan& p, const double* s1, const float* c, void* 
                        int* err, cudaStream_t st, const float* wscale = nullptr,
                        const float* tscale = nullptr);
 
+// The whole tangent chain of an evaluation in one persistent launch (BF16 and split-BF16x3 forms):
+// plans[l] is layer l's single-SM tangent plan (every plan with the same N tile, mode and N),
+// outs[l] its outputs as for tc_tangent; cnt: nl * ntn unsigned counters, zero at launch.
+constexpr int kMaxChain = 12;
+struct ChainOut {
+  const double* s1;
+  const float* c;
+  void *at_hi, *at_lo;
+  int ldo;
+  void *zt_hi, *zt_lo, *yt_hi, *yt_lo;
+};
+cudaError_t tc_tangent_chain(const TcPlan* plans, const ChainOut* outs, int nl, unsigned* cnt,
+                             int ldz, int* err, cudaStream_t st);
+
 // Reverse sweep W_l^T Zbar with three-way split BF16 operands (six products, ~FP32 accuracy):
 // A = W_l^T (parts 0/1/2, kp x mp, K-major), B = Zbar^T (parts, seeds x mp); writes
 // part[split][k][0..bn) (FP32, bn = 16 or 48).

@@ -278,3 +278,37 @@ def test_pair_tangent_kernel(lib, prec, case):
         assert e < (1e-4 if prec == "bf16x3" else TOL[prec]["H"]), (bn, e)
         assert np.array_equal(H, H.T)
         net.free()
+
+
+CHAIN_NETS = [
+    ([784, 512, 384, 256, 10], ["tanh", "sigmoid", "tanh", "identity"]),   # three chain layers
+    ([117, 1024, 512, 37], ["tanh", "softplus", "identity"]),               # one column block
+    ([300, 256, 1280, 5], ["gelu", "tanh", "softmax"]),                     # curved output layer
+    ([33, 130, 257, 10], ["tanh", "softplus", "tanh"]),                      # ragged widths
+]
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("case", range(len(CHAIN_NETS)))
+def test_tangent_chain_matches_per_layer_launches(lib, prec, case):
+    """The persistent chain kernel (every tangent GEMM of an evaluation in one launch, layers
+    ordered by arrival counters) issues the same MMAs per tile as the per-layer launches, so the
+    Hessian is identical bit for bit; and both match the oracle."""
+    widths, acts = CHAIN_NETS[case]
+    mlp = make_mlp(MLPSpec(widths, acts), seed=case + 60, tag="chain", bias_std=0.2)
+    x = synth.uniform01(synth.derive_key(case, "chain-x"), widths[0])
+    lam = synth.normal(synth.derive_key(case, "chain-lam"), widths[-1])
+    Ho = onn.hessian_lag(mlp, x, lam)
+    net = lib.Net.from_mlp(mlp, precision=prec)
+    net.tune_set(tangent_bn=1)
+    assert net.tuning(1)[0] == 1
+    Hc, gc = net.hessian_lag(x, lam, want_grad=True)
+    Hc2 = net.hessian_lag(x, lam)           # counters cleared between evaluations
+    net.tune_set(tangent_bn=208)
+    assert net.tuning(1)[0] == 208
+    Hl, gl = net.hessian_lag(x, lam, want_grad=True)
+    net.free()
+    print(f"[chain {case} {prec}] H rel err {rel(Hc, Ho):.2e}")
+    assert np.array_equal(Hc, Hc2)
+    assert np.array_equal(Hc, Hl) and np.array_equal(gc, gl)
+    assert rel(Hc, Ho) < (1e-4 if prec == "bf16x3" else TOL[prec]["H"])
