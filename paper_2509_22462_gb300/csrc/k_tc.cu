@@ -1182,6 +1182,166 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_chain(const __grid_constant_
   }
 }
 
+// ---------------------------------------------------------------- plain BF16 GEMM
+// C = A B^T for the learned warm start's small dense layers (forward Z = X W^T, backward
+// dH = dZ W and dW = dZ^T X with transposed operand copies): one 128 x BN tile per CTA, the
+// producer / MMA / epilogue warps of k_tc_gemm, single BF16 product into an FP32 TMEM tile.
+// Epilogue: C[m][n] = acc + bias[n] for m < M, n < N (FP32, row stride ldc); with gelu also
+// Hf = GELU(C) (FP32), Hl = GELU(C) (BF16, row stride ldc) and, when Ht is given, the transposed
+// BF16 copy Ht[n][m] (row stride ldt), the operand layout of the next backward product.
+struct PlainArgs {
+  int M, N, nkb, ntn;
+  const float* bias;
+  float* C;
+  int ldc;
+  int gelu;
+  float* Hf;
+  __nv_bfloat16* Hl;
+  __nv_bfloat16* Ht;
+  int ldt;
+  int* err;
+};
+
+template <int BN>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tc_plain(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
+               const PlainArgs args) {
+  using C = Cfg<BN, MODE_BF16>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + C::STAGES * C::STAGE_BYTES);
+  uint64_t* empty = full + C::STAGES;
+  uint64_t* accf = empty + C::STAGES;
+  uint32_t* tmem_slot = (uint32_t*)(accf + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  volatile int* consumed_sh = (volatile int*)(tmem_slot + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tm = blockIdx.x / args.ntn, tn = blockIdx.x % args.ntn;
+  const int m0 = tm * BM, n0 = tn * BN;
+  const int n_eff = (min(BN, args.N - n0) + 15) / 16 * 16;
+  const uint32_t idesc = C::IDESC_NO_N | ((uint32_t)(n_eff >> 3) << 17);
+  const int nk = args.nkb;
+  if (nk <= 0 || n_eff <= 0) return;   // uniform over the CTA, before any barrier exists
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(accf), 1);
+    *abort_flag = 0;
+    *consumed_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(C::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  int issued = 0;
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % C::STAGES;
+        const uint32_t ph = (uint32_t)(i / C::STAGES) & 1u;
+        if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1u, args.err, 61, abort_flag)) break;
+        uint8_t* st = smem + s * C::STAGE_BYTES;
+        const uint32_t fb = smem_u32(&full[s]);
+        mbar_expect_tx(fb, C::TX_BYTES);
+        const int kx = i * C::BKE;
+        tma_load_2d(smem_u32(st), &ta, fb, kx, m0);
+        tma_load_2d(smem_u32(st + C::A_BYTES), &tb, fb, kx, n0);
+        issued = i + 1;
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int i = 0;
+      for (; i < nk; ++i) {
+        const int s = i % C::STAGES;
+        const uint32_t ph = (uint32_t)(i / C::STAGES) & 1u;
+        if (!mbar_wait(smem_u32(&full[s]), ph, args.err, 62, abort_flag)) break;
+        tc_fence_after();
+        const uint32_t st = smem_u32(smem + s * C::STAGE_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < C::ROWB / 32; ++kk) {
+          const uint32_t off = kk * 32;
+          constexpr int SW = C::SWZ, SB = C::SBO;
+          umma_bf16(tmem, sdesc<SW, SB>(st + off), sdesc<SW, SB>(st + C::A_BYTES + off), idesc,
+                    (i > 0 || kk > 0) ? 1u : 0u);
+        }
+        umma_commit(smem_u32(&empty[s]));
+      }
+      *consumed_sh = i;
+      umma_commit(smem_u32(accf));
+    }
+  } else {
+    const int q = warp & 3;
+    const int m = m0 + q * 32 + lane;
+    const bool ok = mbar_wait(smem_u32(accf), 0, args.err, 63, abort_flag);
+    tc_fence_after();
+    if (ok) {
+#pragma unroll 1
+      for (int c0 = 0; c0 < n_eff; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+        if (m < args.M) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int n = n0 + c0 + j;
+            if (n < args.N) {
+              const float z = v[j] + (args.bias ? args.bias[n] : 0.f);
+              const size_t o = (size_t)m * args.ldc + n;
+              args.C[o] = z;
+              if (args.gelu) {
+                double a, d1, d2;
+                act_eval(NNC_GELU, (double)z, a, d1, d2);
+                args.Hf[o] = (float)a;
+                const __nv_bfloat16 hb = __float2bfloat16_rn((float)a);
+                args.Hl[o] = hb;
+                if (args.Ht) args.Ht[(size_t)n * args.ldt + m] = hb;
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (*abort_flag) {
+    if (warp == 0 && lane == 0) {
+      for (int i = *consumed_sh; i < issued; ++i) {
+        const int s = i % C::STAGES;
+        const uint32_t ph = (uint32_t)(i / C::STAGES) & 1u;
+        volatile int no_abort = 0;
+        mbar_wait(smem_u32(&full[s]), ph, args.err, 64, &no_abort, kWaitCycles / 8);
+      }
+    }
+    if (warp == 1 && lane == 0) {
+      volatile int no_abort = 0;
+      mbar_wait(smem_u32(accf), 0, args.err, 65, &no_abort, kWaitCycles / 8);
+    }
+    __syncthreads();
+  }
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(C::TMEM_COLS)
+                 : "memory");
+  }
+}
+
 // Self-test of the tensor-core kernels' bounded wait (with the CTA abort flag): an mbarrier that
 // nothing arrives on; the wait gives up after `limit` cycles, records `code` and sets the flag,
 // which a second wait then sees at once.
@@ -1511,6 +1671,45 @@ cudaError_t launch_gtan_mode(const TcPlan& p, const TcArgs& a, int groups, int g
   if (p.mode == MODE_BF16X3) return launch_gtan_t<BN, MODE_BF16X3>(p, a, groups, grid, st);
   if (p.mode == MODE_BF16) return launch_gtan_t<BN, MODE_BF16>(p, a, groups, grid, st);
   return cudaErrorInvalidValue;
+}
+
+int tc_plain_plan(PlainPlan& p, const void* A, int a_rows, int lda, const void* B, int b_rows,
+                  int ldb, int M, int N, int K) {
+  p = PlainPlan();
+  if (M <= 0 || N <= 0 || K <= 0 || K % 64 != 0 || lda % 8 != 0 || ldb % 8 != 0 || !A || !B)
+    return NNC_ERR_ARG;
+  p.M = M;
+  p.N = N;
+  p.K = K;
+  p.bn = N <= 128 ? 128 : 256;
+  p.ntm = (M + BM - 1) / BM;
+  p.ntn = (N + p.bn - 1) / p.bn;
+  if (!make_map(&p.ta, A, a_rows, K, lda, BM, 64) || !make_map(&p.tb, B, b_rows, K, ldb, p.bn, 64))
+    return NNC_ERR_CUDA;
+  p.ready = true;
+  return NNC_OK;
+}
+
+template <int BN>
+cudaError_t launch_plain_t(const PlainPlan& p, const PlainArgs& a, cudaStream_t st) {
+  using C = Cfg<BN, MODE_BF16>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_plain<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_tc_plain<BN><<<p.ntm * p.ntn, kThreads, C::SMEM, st>>>(p.ta, p.tb, a);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t tc_plain(const PlainPlan& p, const float* bias, float* Cout, int ldc, bool gelu, float* Hf,
+                     void* Hl, void* Ht, int ldt, int* err, cudaStream_t st) {
+  if (!p.ready || !Cout || (gelu && (!Hf || !Hl))) return cudaErrorInvalidValue;
+  PlainArgs a{p.M, p.N, p.K / 64, p.ntn, bias, Cout, ldc, gelu ? 1 : 0, Hf, (__nv_bfloat16*)Hl,
+              (__nv_bfloat16*)Ht, ldt, err};
+  return p.bn == 128 ? launch_plain_t<128>(p, a, st) : launch_plain_t<256>(p, a, st);
 }
 
 template <int BN, int MODE>

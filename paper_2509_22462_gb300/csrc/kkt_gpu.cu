@@ -44,7 +44,7 @@ constexpr int kNB = 32;          // panel width
 constexpr int kTile = 64;        // trailing-update tile
 constexpr int kThreads = 256;
 constexpr int kMaxGrid = 96;     // CTAs of the factorization (fewer CTAs: cheaper barriers)
-constexpr int kSolveThreads = 1024;
+constexpr int kSolveThreads = 512;
 constexpr float kPivotMin = 1e-5f;
 constexpr long long kBarrierCycles = 4000000000LL;   // about two seconds at GB300 clocks
 
@@ -64,22 +64,22 @@ struct KktArgs {
 // Grid barrier (generation counter): every CTA arrives once; the last one resets the arrival
 // count and advances the generation.  Bounded: on expiry the CTA records the timeout and the
 // caller returns.
-__device__ bool grid_barrier(const KktArgs& a, volatile int* abort_sh) {
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* flags, volatile int* abort_sh) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* gen = a.bar + 1;
+    volatile unsigned* gen = bar + 1;
     const unsigned g = *gen;
     __threadfence();
-    const unsigned arrived = atomicAdd(a.bar, 1u);
+    const unsigned arrived = atomicAdd(bar, 1u);
     if (arrived == gridDim.x - 1) {
-      atomicExch(a.bar, 0u);
+      atomicExch(bar, 0u);
       __threadfence();
-      atomicAdd(a.bar + 1, 1u);
+      atomicAdd(bar + 1, 1u);
     } else {
       const long long t0 = clock64();
       while (*gen == g) {
         if (clock64() - t0 > kBarrierCycles) {
-          atomicExch(a.flags + 1, 1);
+          atomicExch(flags + 1, 1);
           *abort_sh = 1;
           break;
         }
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kThreads) k_kkt_chol(const KktArgs a) {
     const double d = a.s * __ldcg(a.H + (size_t)i * nd + i) + __ldcg(a.dvec + i);
     __stcg(a.sc + i, d > 0.0 ? 1.0 / sqrt(d) : 1.0);
   }
-  if (!grid_barrier(a, &abort_sh)) return;
+  if (!grid_barrier(a.bar, a.flags, &abort_sh)) return;
   // 1. assembly of the scaled bordered matrix (lower triangle), a row per warp
   {
     const int warp = gtid >> 5, lane = threadIdx.x & 31, nwarps = gthreads >> 5;
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kThreads) k_kkt_chol(const KktArgs a) {
       }
     }
   }
-  if (!grid_barrier(a, &abort_sh)) return;
+  if (!grid_barrier(a.bar, a.flags, &abort_sh)) return;
 
   for (int kb = 0; kb < nd; kb += kNB) {
     const int nb = min(kNB, nd - kb);
@@ -144,22 +144,24 @@ __global__ void __launch_bounds__(kThreads) k_kkt_chol(const KktArgs a) {
       for (int c = 0; c < kNB; ++c)
         v[c] = (r < nb && c <= r) ? __ldcg(a.A + (size_t)(kb + r) * ldp + kb + c) : (c == r ? 1.f : 0.f);
       int fail = 0;
-#pragma unroll
+      float mydiag = 1.f;   // L_rr (no dynamic index into v: it stays in registers)
+#pragma unroll 32
       for (int j = 0; j < kNB; ++j) {
         const float piv = __shfl_sync(0xffffffffu, v[j], j);
         if (j < nb && !fail && !(piv > kPivotMin)) fail = kb + j + 1;
         const float d = sqrtf(fmaxf(piv, kPivotMin));
+        if (r == j) mydiag = d;
         const float l = (r > j) ? v[j] / d : (r == j ? d : 0.f);
         v[j] = l;
-#pragma unroll
+#pragma unroll 31
         for (int k = j + 1; k < kNB; ++k) {
           const float lk = __shfl_sync(0xffffffffu, l, k);
-          if (r >= k) v[k] -= l * lk;
+          v[k] = (r >= k) ? v[k] - l * lk : v[k];
         }
       }
 #pragma unroll
       for (int c = 0; c < kNB; ++c) Ls[r][c] = v[c];
-      dinv[r] = 1.f / v[r];
+      dinv[r] = 1.f / mydiag;
       if (r == 0) fail_sh = fail;
     }
     __syncthreads();
@@ -183,7 +185,7 @@ __global__ void __launch_bounds__(kThreads) k_kkt_chol(const KktArgs a) {
       for (int k = 0; k < kNB; ++k)
         if (k < nb) __stcg(row + k, x[k]);
     }
-    if (!grid_barrier(a, &abort_sh)) return;
+    if (!grid_barrier(a.bar, a.flags, &abort_sh)) return;
     // the factored diagonal block goes back now that no CTA reads it any more (every CTA loaded
     // it before the barrier; the trailing update reads only rows >= k1)
     if (blockIdx.x == 0)
@@ -222,21 +224,28 @@ __global__ void __launch_bounds__(kThreads) k_kkt_chol(const KktArgs a) {
 #pragma unroll
           for (int w = 0; w < 4; ++w) acc[u][w] += p[u] * q[w];
       }
+      // all loads of the tile's old values first, then the stores (no load waits behind a store)
+      float old[4][4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int i = r0 + ty * 4 + u;
-        if (i >= N) continue;
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
           const int j = c0 + tx * 4 + w;
-          if (j <= i) {
-            float* p = a.A + (size_t)i * ldp + j;
-            __stcg(p, __ldcg(p) - acc[u][w]);
-          }
+          old[u][w] = (i < N && j <= i) ? __ldcg(a.A + (size_t)i * ldp + j) : 0.f;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = r0 + ty * 4 + u;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          const int j = c0 + tx * 4 + w;
+          if (i < N && j <= i) __stcg(a.A + (size_t)i * ldp + j, old[u][w] - acc[u][w]);
         }
       }
     }
-    if (!grid_barrier(a, &abort_sh)) return;
+    if (!grid_barrier(a.bar, a.flags, &abort_sh)) return;
   }
   // 3. the border rows as FP64 (Y^T in the first nd columns, the bottom block after them)
   for (int e = gtid; e < a.m * N; e += gthreads) {
@@ -249,7 +258,7 @@ __global__ void __launch_bounds__(kThreads) k_kkt_chol(const KktArgs a) {
 // Triangular solves with L = D^-1 Lhat (Lhat: the FP32 factor in A, row stride ldp), one CTA of
 // kSolveThreads: lower: x = L^-1 b = Lhat^-1 (D b); upper: x = L^-T b = D (Lhat^-T b).  By 32-row
 // blocks: warp 0 solves the diagonal block with shuffles, then every thread updates its rows.
-__global__ void __launch_bounds__(kSolveThreads) k_kkt_lower(const float* __restrict__ A, int ldp,
+__global__ void __launch_bounds__(kSolveThreads, 1) k_kkt_lower(const float* __restrict__ A, int ldp,
                                                              int n, const double* __restrict__ sc,
                                                              double* __restrict__ xio) {
   extern __shared__ float xs[];   // n
@@ -266,12 +275,11 @@ __global__ void __launch_bounds__(kSolveThreads) k_kkt_lower(const float* __rest
       for (int c = 0; c < kNB; ++c)
         lrow[c] = (r < nb && c <= r) ? A[(size_t)(kb + r) * ldp + kb + c] : (c == r ? 1.f : 0.f);
       float t = r < nb ? xs[kb + r] : 0.f;
-#pragma unroll
+#pragma unroll 32
       for (int j = 0; j < kNB; ++j) {
         if (j < nb) {   // uniform over the warp
           const float xj = __shfl_sync(0xffffffffu, t / lrow[j], j);   // lane j: t_j / L_jj
-          if (r == j) t = xj;
-          else if (r > j) t -= lrow[j] * xj;
+          t = (r == j) ? xj : (r > j) ? t - lrow[j] * xj : t;
         }
       }
       if (r < nb) {
@@ -292,7 +300,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_kkt_lower(const float* __rest
   for (int i = threadIdx.x; i < n; i += blockDim.x) xio[i] = (double)xs[i];
 }
 
-__global__ void __launch_bounds__(kSolveThreads) k_kkt_upper(const float* __restrict__ A, int ldp,
+__global__ void __launch_bounds__(kSolveThreads, 1) k_kkt_upper(const float* __restrict__ A, int ldp,
                                                              int n, const double* __restrict__ sc,
                                                              double* __restrict__ xio) {
   extern __shared__ float xs[];   // n
@@ -311,12 +319,11 @@ __global__ void __launch_bounds__(kSolveThreads) k_kkt_upper(const float* __rest
       for (int j = 0; j < kNB; ++j)
         lcol[j] = (r < nb && j < nb && j >= r) ? A[(size_t)(kb + j) * ldp + kb + r] : (j == r ? 1.f : 0.f);
       float t = r < nb ? xs[kb + r] : 0.f;
-#pragma unroll
+#pragma unroll 32
       for (int j = kNB - 1; j >= 0; --j) {
         if (j < nb) {   // uniform over the warp
           const float xj = __shfl_sync(0xffffffffu, t / lcol[j], j);   // lane j: t_j / L_jj
-          if (r == j) t = xj;
-          else if (r < j) t -= lcol[j] * xj;
+          t = (r == j) ? xj : (r < j) ? t - lcol[j] * xj : t;
         }
       }
       if (r < nb) {

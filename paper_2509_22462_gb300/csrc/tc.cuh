@@ -69,6 +69,21 @@ struct ChainOut {
 cudaError_t tc_tangent_chain(const TcPlan* plans, const ChainOut* outs, int nl, unsigned* cnt,
                              int ldz, int* err, cudaStream_t st);
 
+// Plain BF16 GEMM on the tensor cores (the learned warm start's layers): C[m][n] =
+// sum_k A[m][k] B[n][k] (+ bias[n]) for m < M, n < N, A (a_rows x K, row stride lda) and B
+// (b_rows x K, row stride ldb) K-major BF16, K a multiple of 64, strides multiples of 8; rows
+// beyond a_rows / b_rows read as zero.  With gelu: Hf = GELU(C) (FP32, row stride ldc), Hl (BF16,
+// row stride ldc) and, if Ht is not NULL, Ht[n][m] = GELU(C) (BF16, row stride ldt).
+struct PlainPlan {
+  CUtensorMap ta, tb;
+  int M = 0, N = 0, K = 0, bn = 0, ntm = 0, ntn = 0;
+  bool ready = false;
+};
+int tc_plain_plan(PlainPlan& p, const void* A, int a_rows, int lda, const void* B, int b_rows,
+                  int ldb, int M, int N, int K);
+cudaError_t tc_plain(const PlainPlan& p, const float* bias, float* C, int ldc, bool gelu, float* Hf,
+                     void* Hl, void* Ht, int ldt, int* err, cudaStream_t st);
+
 // Reverse sweep W_l^T Zbar with three-way split BF16 operands (six products, ~FP32 accuracy):
 // A = W_l^T (parts 0/1/2, kp x mp, K-major), B = Zbar^T (parts, seeds x mp); writes
 // part[split][k][0..bn) (FP32, bn = 16 or 48).

@@ -7,8 +7,13 @@
 //   backward  dP = 2 (P - T) / (B n_out); dW_l = dZ_l^T H_{l-1}; db_l = column sums of dZ_l;
 //             dH_{l-1} = dZ_l W_l; dZ = dH * GELU'(Z)
 //   Adam      (Kingma & Ba) on FP32 master weights, FP32 moments, BF16 operand copies.
-// The GEMMs are a shared-memory tiled CUDA-core kernel: the network has ~0.4M parameters, so a
-// training step is a few hundred MFLOP and launch/latency bound; tensor cores buy nothing here.
+// GEMMs: in the BF16 form the products run on the tcgen05 tensor cores (tc_plain: TMA-fed BF16
+// operands, FP32 accumulation in tensor memory, bias / GELU fused into the epilogue, which also
+// writes the transposed BF16 copy of each activation that the weight gradient dW = dZ^T H reads);
+// the backward products take transposed operand copies written by the loss, GELU-derivative and
+// Adam kernels.  Shapes the tensor cores cannot take (a batch that is not a multiple of 64 in the
+// weight-gradient products, widths that are not multiples of 64) and the FP32 form use a
+// shared-memory tiled CUDA-core kernel.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -19,6 +24,7 @@
 
 #include "../../include/nnc.h"
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace nnc {
 void set_last_error(const std::string& msg);
@@ -105,7 +111,8 @@ void gemm(const T* A, long sam, long sak, const T* B, long sbk, long sbn, int M,
 // dZ = dH * GELU'(Z), stored in FP32 and in the operand type.
 template <typename T>
 __global__ void k_ws_gelu_back(const float* __restrict__ dH, const float* __restrict__ Z, int n,
-                               float* __restrict__ dZ, T* __restrict__ dZl) {
+                               float* __restrict__ dZ, T* __restrict__ dZl, int cols,
+                               __nv_bfloat16* __restrict__ dZt, int ldt) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double a, d1, d2;
@@ -114,13 +121,15 @@ __global__ void k_ws_gelu_back(const float* __restrict__ dH, const float* __rest
   dZ[i] = v;
   if constexpr (std::is_same<T, float>::value) dZl[i] = v;
   else dZl[i] = __float2bfloat16_rn(v);
+  if (dZt) dZt[(size_t)(i % cols) * ldt + i / cols] = __float2bfloat16_rn(v);   // transposed copy
 }
 
 // dP = 2 (P - T) / (B n_out); loss partial sums per block into part[blockIdx.x].
 template <typename T>
 __global__ void k_ws_loss(const float* __restrict__ P, const float* __restrict__ Tt, int n,
                           float scale, float* __restrict__ dP, T* __restrict__ dPl,
-                          double* __restrict__ part) {
+                          double* __restrict__ part, int cols, __nv_bfloat16* __restrict__ dPp,
+                          int ldp, __nv_bfloat16* __restrict__ dPt, int ldt) {
   __shared__ double red[256];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double s = 0.0;
@@ -131,6 +140,11 @@ __global__ void k_ws_loss(const float* __restrict__ P, const float* __restrict__
     dP[i] = g;
     if constexpr (std::is_same<T, float>::value) dPl[i] = g;
     else dPl[i] = __float2bfloat16_rn(g);
+    // tensor-core operands: dP with its row stride padded to a multiple of 64 (the padding stays
+    // zero) and dP^T
+    const int r = i / cols, c = i % cols;
+    if (dPp) dPp[(size_t)r * ldp + c] = __float2bfloat16_rn(g);
+    if (dPt) dPt[(size_t)c * ldt + r] = __float2bfloat16_rn(g);
   }
   red[threadIdx.x] = s;
   __syncthreads();
@@ -150,11 +164,13 @@ __global__ void k_ws_colsum(const float* __restrict__ dZ, int B, int N, float* _
   db[j] = s;
 }
 
-// Adam on one flat parameter array; refreshes the operand copy.
+// Adam on one flat parameter array; refreshes the operand copy (and, for a weight matrix of
+// `cols` columns with wt given, its transposed BF16 copy, row stride ldt).
 template <typename T>
 __global__ void k_ws_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
                           float* __restrict__ v, T* __restrict__ wl, int n, float lr, float b1,
-                          float b2, float eps, float c1, float c2) {
+                          float b2, float eps, float c1, float c2, int cols,
+                          __nv_bfloat16* __restrict__ wt, int ldt) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float gi = g[i];
@@ -168,11 +184,13 @@ __global__ void k_ws_adam(float* __restrict__ w, const float* __restrict__ g, fl
     if constexpr (std::is_same<T, float>::value) wl[i] = wi;
     else wl[i] = __float2bfloat16_rn(wi);
   }
+  if (wt) wt[(size_t)(i % cols) * ldt + i / cols] = __float2bfloat16_rn(wi);
 }
 
 template <typename T>
 __global__ void k_ws_gather(const float* __restrict__ src, const int* __restrict__ idx, int rows,
-                            int cols, float* __restrict__ dst, T* __restrict__ dstl) {
+                            int cols, float* __restrict__ dst, T* __restrict__ dstl,
+                            __nv_bfloat16* __restrict__ dstt = nullptr, int ldt = 0) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows * cols) return;
   const int r = i / cols, c = i % cols;
@@ -182,14 +200,18 @@ __global__ void k_ws_gather(const float* __restrict__ src, const int* __restrict
     if constexpr (std::is_same<T, float>::value) dstl[i] = v;
     else dstl[i] = __float2bfloat16_rn(v);
   }
+  if (dstt) dstt[(size_t)c * ldt + r] = __float2bfloat16_rn(v);
 }
 
+// dst = src in the operand type; with dstt also the transposed BF16 copy of a rows x cols matrix
 template <typename T>
-__global__ void k_ws_cast(const float* __restrict__ src, int n, T* __restrict__ dst) {
+__global__ void k_ws_cast(const float* __restrict__ src, int n, T* __restrict__ dst, int cols = 1,
+                          __nv_bfloat16* __restrict__ dstt = nullptr, int ldt = 0) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if constexpr (std::is_same<T, float>::value) dst[i] = src[i];
   else dst[i] = __float2bfloat16_rn(src[i]);
+  if (dstt) dstt[(size_t)(i % cols) * ldt + i / cols] = __float2bfloat16_rn(src[i]);
 }
 
 int wfail(int code, const std::string& m) {
@@ -223,6 +245,16 @@ struct nnc_ws {
   int* idx = nullptr;
   float *Ud = nullptr, *Td = nullptr;   // standardized dataset on the device
   int nd = 0;
+  // tensor-core path (BF16 form with n_in, h1, h2 multiples of 64): transposed BF16 operand copies
+  // (row stride cap), dP with its row stride padded to n_out_p, W2^T and W3^T, and the plans of
+  // the eight products (built for `plan_rows` batch rows)
+  bool tc = false;
+  int n_out_p = 0;
+  __nv_bfloat16 *Ut = nullptr, *H1t = nullptr, *H2t = nullptr, *dPt = nullptr, *dZt = nullptr,
+                *dPp = nullptr, *W2t = nullptr, *W3t = nullptr;
+  int* d_err = nullptr;
+  nnc::PlainPlan pl[8];
+  int plan_rows = -1;
 };
 
 namespace {
@@ -246,6 +278,7 @@ size_t esz(const nnc_ws* s) { return s->prec == NNC_FP32 ? 4 : 2; }
 
 int ensure_cap(nnc_ws* s, int B) {
   if (B <= s->cap) return NNC_OK;
+  if (s->tc) B = (B + 63) / 64 * 64;   // the transposed copies' row stride: a multiple of 64
   const int wmax = std::max(std::max(s->h1, s->h2), std::max(s->n_in, s->n_out));
   const size_t big = (size_t)B * wmax;
   WAL(s->U, big);
@@ -266,14 +299,61 @@ int ensure_cap(nnc_ws* s, int B) {
   WAL(q, big * esz(s)); s->dZl = q;
   WAL(s->part, (big + 255) / 256 + 1);
   WAL(s->idx, B);
+  if (s->tc) {
+    WAL(s->Ut, (size_t)s->n_in * B);
+    WAL(s->H1t, (size_t)s->h1 * B);
+    WAL(s->H2t, (size_t)s->h2 * B);
+    WAL(s->dPt, (size_t)s->n_out * B);
+    WAL(s->dZt, (size_t)std::max(s->h1, s->h2) * B);
+    WAL(s->dPp, (size_t)B * s->n_out_p);
+  }
   s->cap = B;
+  s->plan_rows = -1;
   return NNC_OK;
 }
 
+// the eight tensor-core products for batches of B rows (tensor maps of the current buffers)
+int make_plans(nnc_ws* s, int B) {
+  if (s->plan_rows == B) return NNC_OK;
+  using nnc::tc_plain_plan;
+  const int cap = s->cap;
+  const __nv_bfloat16* w1 = (const __nv_bfloat16*)s->wl[0];
+  const __nv_bfloat16* w2 = (const __nv_bfloat16*)s->wl[2];
+  const __nv_bfloat16* w3 = (const __nv_bfloat16*)s->wl[4];
+  int r = tc_plain_plan(s->pl[0], s->Ul, B, s->n_in, w1, s->h1, s->n_in, B, s->h1, s->n_in);
+  if (!r) r = tc_plain_plan(s->pl[1], s->H1l, B, s->h1, w2, s->h2, s->h1, B, s->h2, s->h1);
+  if (!r) r = tc_plain_plan(s->pl[2], s->H2l, B, s->h2, w3, s->n_out, s->h2, B, s->n_out, s->h2);
+  if (!r && B % 64 == 0) {
+    r = tc_plain_plan(s->pl[3], s->dPt, s->n_out, cap, s->H2t, s->h2, cap, s->n_out, s->h2, B);
+    if (!r) r = tc_plain_plan(s->pl[4], s->dPp, B, s->n_out_p, s->W3t, s->h2, s->n_out_p, B, s->h2, s->n_out_p);
+    if (!r) r = tc_plain_plan(s->pl[5], s->dZt, s->h2, cap, s->H1t, s->h1, cap, s->h2, s->h1, B);
+    if (!r) r = tc_plain_plan(s->pl[6], s->dZl, B, s->h2, s->W2t, s->h1, s->h2, B, s->h1, s->h2);
+    if (!r) r = tc_plain_plan(s->pl[7], s->dZt, s->h1, cap, s->Ut, s->n_in, cap, s->h1, s->n_in, B);
+  }
+  if (r) return wfail(r, "warm start: tensor-core plan failed");
+  s->plan_rows = B;
+  return NNC_OK;
+}
+#define TCK(expr)                                                                            \
+  do {                                                                                       \
+    cudaError_t e_ = (expr);                                                                 \
+    if (e_ != cudaSuccess) return wfail(NNC_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
 // forward on the first B rows of s->U (FP32) / s->Ul (operand type): P = net(U)
 template <typename T>
-void forward(nnc_ws* s, int B) {
+int forward(nnc_ws* s, int B) {
   cudaStream_t st = s->stream;
+  if constexpr (!std::is_same<T, float>::value) {
+    if (s->tc) {
+      int r = make_plans(s, B);
+      if (r) return r;
+      TCK(nnc::tc_plain(s->pl[0], s->w[1], s->Z1, s->h1, true, s->H1, s->H1l, s->H1t, s->cap, s->d_err, st));
+      TCK(nnc::tc_plain(s->pl[1], s->w[3], s->Z2, s->h2, true, s->H2, s->H2l, s->H2t, s->cap, s->d_err, st));
+      TCK(nnc::tc_plain(s->pl[2], s->w[5], s->P, s->n_out, false, nullptr, nullptr, nullptr, 0, s->d_err, st));
+      return NNC_OK;
+    }
+  }
   T* Ul = (T*)s->Ul;
   gemm<T>(Ul, s->n_in, 1, (const T*)s->wl[0], 1, s->n_in, B, s->h1, s->n_in, s->w[1], s->Z1, s->h1,
           true, s->H1, (T*)s->H1l, st);
@@ -281,36 +361,63 @@ void forward(nnc_ws* s, int B) {
           s->h2, true, s->H2, (T*)s->H2l, st);
   gemm<T>((const T*)s->H2l, s->h2, 1, (const T*)s->wl[4], 1, s->h2, B, s->n_out, s->h2, s->w[5], s->P,
           s->n_out, false, nullptr, (T*)nullptr, st);
+  return NNC_OK;
 }
 
 // loss and gradients on the first B rows (targets in s->Tt); returns the loss through *loss
 template <typename T>
 int loss_grad(nnc_ws* s, int B, double* loss) {
   cudaStream_t st = s->stream;
-  forward<T>(s, B);
+  int rf = forward<T>(s, B);
+  if (rf) return rf;
   const int nP = B * s->n_out;
   const int nb = (nP + 255) / 256;
-  k_ws_loss<T><<<nb, 256, 0, st>>>(s->P, s->Tt, nP, 1.f / (float)nP, s->dP, (T*)s->dPl, s->part);
+  // tensor-core backward products need the batch (their K) to be a multiple of 64
+  const bool tcb = !std::is_same<T, float>::value && s->tc && B % 64 == 0;
+  k_ws_loss<T><<<nb, 256, 0, st>>>(s->P, s->Tt, nP, 1.f / (float)nP, s->dP, (T*)s->dPl, s->part,
+                                   s->n_out, tcb ? s->dPp : nullptr, s->n_out_p,
+                                   tcb ? s->dPt : nullptr, s->cap);
   note_launch();
+  if (tcb) {
+    // layer 3: dW3 = dP^T H2, db3 = colsum dP, dH2 = dP W3
+    TCK(nnc::tc_plain(s->pl[3], nullptr, s->g[4], s->h2, false, nullptr, nullptr, nullptr, 0, s->d_err, st));
+    k_ws_colsum<<<(s->n_out + 255) / 256, 256, 0, st>>>(s->dP, B, s->n_out, s->g[5]);
+    TCK(nnc::tc_plain(s->pl[4], nullptr, s->dH, s->h2, false, nullptr, nullptr, nullptr, 0, s->d_err, st));
+    k_ws_gelu_back<T><<<(B * s->h2 + 255) / 256, 256, 0, st>>>(s->dH, s->Z2, B * s->h2, s->dZ, (T*)s->dZl,
+                                                              s->h2, s->dZt, s->cap);
+    // layer 2
+    TCK(nnc::tc_plain(s->pl[5], nullptr, s->g[2], s->h1, false, nullptr, nullptr, nullptr, 0, s->d_err, st));
+    k_ws_colsum<<<(s->h2 + 255) / 256, 256, 0, st>>>(s->dZ, B, s->h2, s->g[3]);
+    TCK(nnc::tc_plain(s->pl[6], nullptr, s->dH, s->h1, false, nullptr, nullptr, nullptr, 0, s->d_err, st));
+    k_ws_gelu_back<T><<<(B * s->h1 + 255) / 256, 256, 0, st>>>(s->dH, s->Z1, B * s->h1, s->dZ, (T*)s->dZl,
+                                                              s->h1, s->dZt, s->cap);
+    // layer 1
+    TCK(nnc::tc_plain(s->pl[7], nullptr, s->g[0], s->n_in, false, nullptr, nullptr, nullptr, 0, s->d_err, st));
+    k_ws_colsum<<<(s->h1 + 255) / 256, 256, 0, st>>>(s->dZ, B, s->h1, s->g[1]);
+    note_launch(5);
+  } else {
   // layer 3: dW3 = dP^T H2, db3 = colsum dP, dH2 = dP W3
   gemm<T>((const T*)s->dPl, 1, s->n_out, (const T*)s->H2l, s->h2, 1, s->n_out, s->h2, B, nullptr,
           s->g[4], s->h2, false, nullptr, (T*)nullptr, st);
   k_ws_colsum<<<(s->n_out + 255) / 256, 256, 0, st>>>(s->dP, B, s->n_out, s->g[5]);
   gemm<T>((const T*)s->dPl, s->n_out, 1, (const T*)s->wl[4], s->h2, 1, B, s->h2, s->n_out, nullptr,
           s->dH, s->h2, false, nullptr, (T*)nullptr, st);
-  k_ws_gelu_back<T><<<(B * s->h2 + 255) / 256, 256, 0, st>>>(s->dH, s->Z2, B * s->h2, s->dZ, (T*)s->dZl);
+  k_ws_gelu_back<T><<<(B * s->h2 + 255) / 256, 256, 0, st>>>(s->dH, s->Z2, B * s->h2, s->dZ, (T*)s->dZl,
+                                                            s->h2, nullptr, 0);
   // layer 2
   gemm<T>((const T*)s->dZl, 1, s->h2, (const T*)s->H1l, s->h1, 1, s->h2, s->h1, B, nullptr, s->g[2],
           s->h1, false, nullptr, (T*)nullptr, st);
   k_ws_colsum<<<(s->h2 + 255) / 256, 256, 0, st>>>(s->dZ, B, s->h2, s->g[3]);
   gemm<T>((const T*)s->dZl, s->h2, 1, (const T*)s->wl[2], s->h1, 1, B, s->h1, s->h2, nullptr, s->dH,
           s->h1, false, nullptr, (T*)nullptr, st);
-  k_ws_gelu_back<T><<<(B * s->h1 + 255) / 256, 256, 0, st>>>(s->dH, s->Z1, B * s->h1, s->dZ, (T*)s->dZl);
+  k_ws_gelu_back<T><<<(B * s->h1 + 255) / 256, 256, 0, st>>>(s->dH, s->Z1, B * s->h1, s->dZ, (T*)s->dZl,
+                                                            s->h1, nullptr, 0);
   // layer 1
   gemm<T>((const T*)s->dZl, 1, s->h1, (const T*)s->Ul, s->n_in, 1, s->h1, s->n_in, B, nullptr, s->g[0],
           s->n_in, false, nullptr, (T*)nullptr, st);
   k_ws_colsum<<<(s->h1 + 255) / 256, 256, 0, st>>>(s->dZ, B, s->h1, s->g[1]);
   note_launch(5);
+  }
   if (loss) {
     std::vector<double> h(nb);
     WCK(cudaMemcpyAsync(h.data(), s->part, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
@@ -327,9 +434,13 @@ void adam(nnc_ws* s, float lr, float b1, float b2, float eps) {
   s->step += 1;
   const float c1 = 1.f - std::pow(b1, (float)s->step), c2 = 1.f - std::pow(b2, (float)s->step);
   for (int i = 0; i < 6; ++i) {
+    // W2^T and W3^T feed the tensor-core backward products
+    __nv_bfloat16* wt = !s->tc ? nullptr : i == 2 ? s->W2t : i == 4 ? s->W3t : nullptr;
+    const int cols = i == 2 ? s->h1 : i == 4 ? s->h2 : 1;
+    const int ldt = i == 2 ? s->h2 : i == 4 ? s->n_out_p : 0;
     k_ws_adam<T><<<(s->sizes[i] + 255) / 256, 256, 0, s->stream>>>(
         s->w[i], s->g[i], s->m[i], s->v[i], (i % 2 == 0) ? (T*)s->wl[i] : (T*)nullptr, s->sizes[i], lr,
-        b1, b2, eps, c1, c2);
+        b1, b2, eps, c1, c2, cols, wt, ldt);
   }
   note_launch(6);
 }
@@ -340,7 +451,8 @@ void stage_rows(nnc_ws* s, const float* U, const float* Tt, int B) {
   if (U != s->U) cudaMemcpyAsync(s->U, U, sizeof(float) * B * s->n_in, cudaMemcpyDeviceToDevice, s->stream);
   if (Tt && Tt != s->Tt)
     cudaMemcpyAsync(s->Tt, Tt, sizeof(float) * B * s->n_out, cudaMemcpyDeviceToDevice, s->stream);
-  k_ws_cast<T><<<(B * s->n_in + 255) / 256, 256, 0, s->stream>>>(s->U, B * s->n_in, (T*)s->Ul);
+  k_ws_cast<T><<<(B * s->n_in + 255) / 256, 256, 0, s->stream>>>(s->U, B * s->n_in, (T*)s->Ul, s->n_in,
+                                                                  s->tc ? s->Ut : nullptr, s->cap);
   note_launch();
 }
 
@@ -359,6 +471,19 @@ int upload_std(nnc_ws* s, const double* U, const double* Tt, int N, bool with_t)
   if (with_t)
     WCK(cudaMemcpyAsync(s->Tt, ht.data(), sizeof(float) * ht.size(), cudaMemcpyHostToDevice, s->stream));
   WCK(cudaStreamSynchronize(s->stream));
+  return NNC_OK;
+}
+
+// the tensor-core kernels' bounded waits record an error word; a set word fails the call
+int check_ws_err(nnc_ws* s) {
+  if (!s->d_err) return NNC_OK;
+  int e = 0;
+  WCK(cudaMemcpyAsync(&e, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  WCK(cudaStreamSynchronize(s->stream));
+  if (e) {
+    cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream);
+    return wfail(NNC_ERR_TIMEOUT, "warm start: a bounded device-side wait ran out");
+  }
   return NNC_OK;
 }
 
@@ -386,6 +511,17 @@ int nnc_ws_create(nnc_ws** out, int n_in, int h1, int h2, int n_out, const doubl
     s->own_stream = true;
   }
   const int sz[6] = {h1 * n_in, h1, h2 * h1, h2, n_out * h2, n_out};
+  s->tc = prec == NNC_BF16 && n_in % 64 == 0 && h1 % 64 == 0 && h2 % 64 == 0;
+  s->n_out_p = (n_out + 63) / 64 * 64;
+  if (s->tc) {
+    int r = walloc(s, &s->W2t, (size_t)h1 * h2);
+    if (!r) r = walloc(s, &s->W3t, (size_t)h2 * s->n_out_p);
+    if (!r) r = walloc(s, &s->d_err, 1);
+    if (r) {
+      nnc_ws_free(s);
+      return r;
+    }
+  }
   for (int i = 0; i < 6; ++i) {
     s->sizes[i] = sz[i];
     if (!params[i]) {
@@ -406,7 +542,12 @@ int nnc_ws_create(nnc_ws** out, int n_in, int h1, int h2, int n_out, const doubl
     std::vector<float> h(params[i], params[i] + sz[i]);
     cudaMemcpyAsync(s->w[i], h.data(), sizeof(float) * sz[i], cudaMemcpyHostToDevice, s->stream);
     if (prec == NNC_FP32) k_ws_cast<float><<<(sz[i] + 255) / 256, 256, 0, s->stream>>>(s->w[i], sz[i], (float*)q);
-    else k_ws_cast<__nv_bfloat16><<<(sz[i] + 255) / 256, 256, 0, s->stream>>>(s->w[i], sz[i], (__nv_bfloat16*)q);
+    else {
+      __nv_bfloat16* wt = !s->tc ? nullptr : i == 2 ? s->W2t : i == 4 ? s->W3t : nullptr;
+      k_ws_cast<__nv_bfloat16><<<(sz[i] + 255) / 256, 256, 0, s->stream>>>(
+          s->w[i], sz[i], (__nv_bfloat16*)q, i == 2 ? h1 : i == 4 ? h2 : 1, wt,
+          i == 2 ? h2 : i == 4 ? s->n_out_p : 0);
+    }
     note_launch();
     cudaStreamSynchronize(s->stream);
   }
@@ -452,6 +593,8 @@ int nnc_ws_loss_grad(nnc_ws* s, const double* U, const double* Tt, int B, double
     stage_rows<__nv_bfloat16>(s, s->U, s->Tt, B);
     r = loss_grad<__nv_bfloat16>(s, B, loss);
   }
+  if (r) return r;
+  r = check_ws_err(s);
   if (r) return r;
   if (grads) {
     for (int i = 0; i < 6; ++i) {
@@ -529,7 +672,8 @@ int nnc_ws_train(nnc_ws* s, const double* U, const double* Tt, int N, int epochs
         r = loss_grad<float>(s, B, want ? &last : nullptr);
         adam<float>(s, (float)lr, (float)beta1, (float)beta2, (float)eps);
       } else {
-        k_ws_gather<__nv_bfloat16><<<(B * s->n_in + 255) / 256, 256, 0, s->stream>>>(s->Ud, s->idx, B, s->n_in, s->U, (__nv_bfloat16*)s->Ul);
+        k_ws_gather<__nv_bfloat16><<<(B * s->n_in + 255) / 256, 256, 0, s->stream>>>(
+            s->Ud, s->idx, B, s->n_in, s->U, (__nv_bfloat16*)s->Ul, s->tc ? s->Ut : nullptr, s->cap);
         k_ws_gather<__nv_bfloat16><<<(B * s->n_out + 255) / 256, 256, 0, s->stream>>>(s->Td, s->idx, B, s->n_out, s->Tt, (__nv_bfloat16*)nullptr);
         note_launch(2);
         r = loss_grad<__nv_bfloat16>(s, B, want ? &last : nullptr);
@@ -540,6 +684,8 @@ int nnc_ws_train(nnc_ws* s, const double* U, const double* Tt, int N, int epochs
   }
   WCK(cudaStreamSynchronize(s->stream));
   WCK(cudaGetLastError());
+  r = check_ws_err(s);
+  if (r) return r;
   if (final_loss) *final_loss = last;
   return NNC_OK;
 }
@@ -550,11 +696,14 @@ int nnc_ws_predict(nnc_ws* s, const double* U, int N, double* P) {
   if (r) return r;
   if (s->prec == NNC_FP32) {
     stage_rows<float>(s, s->U, nullptr, N);
-    forward<float>(s, N);
+    r = forward<float>(s, N);
   } else {
     stage_rows<__nv_bfloat16>(s, s->U, nullptr, N);
-    forward<__nv_bfloat16>(s, N);
+    r = forward<__nv_bfloat16>(s, N);
   }
+  if (r) return r;
+  r = check_ws_err(s);
+  if (r) return r;
   std::vector<float> h((size_t)N * s->n_out);
   WCK(cudaMemcpyAsync(h.data(), s->P, sizeof(float) * h.size(), cudaMemcpyDeviceToHost, s->stream));
   WCK(cudaStreamSynchronize(s->stream));

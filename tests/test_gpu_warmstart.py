@@ -52,6 +52,35 @@ def test_gradients_match_oracle(nnc, prec, tol):
     ws.free()
 
 
+@pytest.mark.parametrize("shape", [(128, 128, 64, 23, 64),     # every product on the tensor cores
+                                   (512, 256, 256, 713, 128),  # the warm-start network of the bench
+                                   (128, 64, 64, 10, 48)])     # batch not a multiple of 64:
+                                                               # tensor-core forward, CUDA-core backward
+def test_tensor_core_gradients_match_oracle(nnc, shape):
+    """The BF16 form on the tcgen05 path (widths multiples of 64): loss and every gradient against
+    the FP64 oracle, and the prediction of the forward pass."""
+    n_in, h1, h2, n_out, B = shape
+    p = synth.warmstart_params(n_in, h1, h2, n_out, seed=5)
+    rng = np.random.default_rng(5)
+    for i in (1, 3, 5):
+        p[i] = 0.1 * rng.standard_normal(p[i].shape)
+    p = [np.float32(x).astype(np.float64) for x in p]
+    U = np.float32(rng.standard_normal((B, n_in))).astype(np.float64)
+    T = np.float32(rng.standard_normal((B, n_out))).astype(np.float64)
+    ws = nnc.WarmStart(p, precision="bf16")
+    loss, g = ws.loss_grad(U, T)
+    lo = ows.loss(p, U, T)
+    go = ows.grad(p, U, T)
+    errs = [rel(a, b) for a, b in zip(g, go)]
+    print(f"[warmstart tc {shape}] loss rel err {abs(loss - lo) / lo:.2e}, gradient rel errs "
+          + " ".join(f"{e:.1e}" for e in errs))
+    assert abs(loss - lo) <= 3e-2 * lo
+    assert max(errs) < 3e-2
+    P = ws.predict(U)
+    assert rel(P, ows.forward(p, U)[0]) < 3e-2
+    ws.free()
+
+
 def test_adam_step_matches_oracle(nnc):
     p, U, T = _data(seed=1)
     ws = nnc.WarmStart(p, precision="fp32")
