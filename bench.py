@@ -53,8 +53,11 @@ def _args():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--prec", default="bf16", choices=["bf16", "bf16x3", "fp8", "fp32", "fp64"])
     p.add_argument("--workload", default="104m", choices=["104m", "87m", "tiny", "scopf68m", "scopf", "70m",
-                                                              "274m"])
+                                                              "274m", "warmstart"])
     p.add_argument("--scopf-k", type=int, default=256)
+    p.add_argument("--ws-train", type=int, default=10000, help="warmstart: training loads (cold solves)")
+    p.add_argument("--ws-test", type=int, default=1000, help="warmstart: held-out loads")
+    p.add_argument("--ws-epochs", type=int, default=100)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64-form", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -558,12 +561,42 @@ def tangent_roofline(net, spec, prec, roof_pass, prof, peaks, peak_src):
     return None
 
 
+def run_ours_warmstart(args, rank, world, local_rank):
+    """The learned warm start on the SCOPF-shaped batch (256 surrogates): cold interior-point solves
+    of --ws-train loads d ~ N(1, 0.1^2) per bus give the training data, the warm-start MLP
+    (512 -> 256 -> 256 -> 713, GELU, BF16 on the tensor cores) is trained on the GPU, and
+    --ws-test held-out loads are solved warm-started and cold to KKT 1e-6.  The metric is the mean
+    warm-started solve time (fallbacks to a cold solve included); the cold mean sits beside it."""
+    import torch
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local_rank)
+    from paper_2509_22462_gb300 import build as B
+    B.build()
+    from paper_2509_22462_gb300 import warmstart_experiment as wse
+    t0 = time.perf_counter()
+    rep, _ = wse.run(K=args.scopf_k, n_train=args.ws_train, n_test=args.ws_test, epochs=args.ws_epochs,
+                     prec=args.prec if args.prec in ("bf16", "bf16x3") else "bf16x3", log=lambda *a: None)
+    wall = time.perf_counter() - t0
+    out = {"metric": "warm_started_ipm_solve_s", "value": rep["warm_seconds_mean"], "unit": "s",
+           "n_gpus": 1, "steps": args.ws_test, "warmup": 0, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+           "config": {"workload": f"scopf_{args.scopf_k}x(n_k->1024x5->1)_warmstart_512x256x256x713_gelu",
+                      "train_loads": args.ws_train, "test_loads": args.ws_test, "epochs": args.ws_epochs,
+                      "loads": "d ~ N(1, 0.1^2) per bus, 512 buses"},
+           "cold_seconds_mean": rep["cold_seconds_mean"], "warm_start": rep, "wall_seconds": wall}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
 
     if args.workload == "scopf":
         return run_ours_scopf(args, rank, world, local_rank)
+    if args.workload == "warmstart":
+        return run_ours_warmstart(args, rank, world, local_rank)
 
     spec, mlp, d = _workload(args.workload)
     cpu_baseline = None

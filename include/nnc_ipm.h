@@ -49,14 +49,16 @@ typedef struct {
   int max_ls_failures;     /* 5 */
   int verbose;             /* print one line per iteration */
   double warm_mu0;         /* 1e-3: barrier parameter of a warm start (z = warm_mu0 / slack) */
-  int kkt_on_device;       /* 1 (default): for the single-network problems in the tensor-core forms
-                            * (NNC_BF16, NNC_BF16X3, NNC_FP8) the Hessian stays in device memory and
-                            * the dense block of the KKT matrix is assembled and factorized on the
-                            * GPU (Jacobi-scaled FP32 blocked Cholesky of the bordered matrix, the
-                            * factor widened to FP64 for the host's solves; an indefinite or nearly
-                            * singular block, pivot <= 1e-5 of the unit diagonal, goes to the FP64
-                            * host path).  0: everything on the host.  The FP64 and FP32 forms and
-                            * the SCOPF-shaped problem always factorize on the host. */
+  int kkt_on_device;       /* 1: for the single-network problems in the tensor-core forms (NNC_BF16,
+                            * NNC_BF16X3, NNC_FP8) the Hessian stays in device memory and the dense
+                            * block of the KKT matrix is assembled, factorized and solved on the GPU
+                            * (Jacobi-scaled FP32 blocked Cholesky of the bordered matrix in one
+                            * cooperative launch, triangular solves on the device, only the border
+                            * rows go to the host; an indefinite or nearly singular block, pivot
+                            * <= 1e-5 of the unit diagonal, goes to the FP64 host path).  0 (default):
+                            * everything on the host, which is faster at n_in = 784 on a 16-core
+                            * host (the device factorization is latency-bound).  The FP64 and FP32
+                            * forms and the SCOPF-shaped problem always factorize on the host. */
 } nnc_ipm_options;
 
 typedef struct {

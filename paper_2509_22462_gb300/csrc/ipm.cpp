@@ -2351,7 +2351,7 @@ void nnc_ipm_default_options(nnc_ipm_options* o) {
   o->max_ls_failures = 5;
   o->verbose = 0;
   o->warm_mu0 = 1e-3;
-  o->kkt_on_device = 1;
+  o->kkt_on_device = 0;
 }
 
 int nnc_ipm_adversarial(nnc_net* net, const double* x0, int target, double margin,

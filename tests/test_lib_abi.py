@@ -42,7 +42,7 @@ def test_ipm_option_defaults_match_oracle():
         if name in ("verbose", "kkt_on_device"):    # not part of the method: output, placement
             continue
         assert getattr(o, name) == getattr(ref, name), name
-    assert o.kkt_on_device == 1
+    assert o.kkt_on_device == 0
 
 
 def test_status_codes_match_header():
