@@ -423,6 +423,7 @@ def run_ours_scopf(args, rank, world, local_rank):
     batch = nnc.Batch(nets)
     for n in nets:
         n.free()      # the batch keeps its own stacked copy
+    batch_tiling = batch.autotune(os.environ.get("NNC_BATCH_TUNE_CACHE"))
     batch.use_graph(True)
     x = np.full(data.G, synth.scopf_demand(data, d) / data.G)
     xc = torch.tensor(batch.concat([x[s] for s in data.subsets]), device=dev)
@@ -485,7 +486,8 @@ def run_ours_scopf(args, rank, world, local_rank):
                "config": {"workload": f"scopf_{K}x(n_k->1024x5->1)_sigmoid", "n_params": int(sum(
                    sum(w.size + b.size for w, b in zip(m.W, m.b)) for m in raw)), "G": data.G,
                    "n_in_range": [min(n_in), max(n_in)], "precision_form": args.prec,
-                   "l2": "weights exceed L2 (no flush needed)", "cuda_graph": True},
+                   "l2": "weights exceed L2 (no flush needed)", "cuda_graph": True,
+                   "autotuned": {"tangent_bn": batch_tiling[0], "syrk_splits": batch_tiling[1]}},
                "roofline": {"kernel": "whole step (grouped value pass, reverse sweep, persistent "
                                       "grouped tangent GEMM, symmetric product)",
                             "bound": "hbm", "achieved": wb / (el_ms / args.steps / 1e3) / 1e9,

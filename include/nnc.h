@@ -169,6 +169,15 @@ int nnc_batch_set_bias(nnc_batch* batch, int layer, const double* bias);
 int nnc_batch_tune_set(nnc_batch* batch, int syrk_splits);
 /* The split-K count in use (0 when no layer has curvature). */
 int nnc_batch_tuning(const nnc_batch* batch, int* syrk_splits);
+/* Autotuner of a batch (no effect on results): times whole evaluations on the batch's own buffers
+ * (CUDA events, no graph) for every grouped-tangent N tile that covers the widest network (112,
+ * 128, 208, 256) and split-K counts 1 .. 3 of the symmetric product, and keeps the fastest.
+ * cache_path (may be NULL) names a text file of earlier choices (one line per batch shape and
+ * device: key, N tile, splits, microseconds), reused unless retune != 0 and appended to.  Reports
+ * the choice in *tangent_bn, *syrk_splits (either may be NULL); drops a captured graph.  CUDA-core
+ * forms and batches without curvature return NNC_OK with the current plan. */
+int nnc_batch_autotune(nnc_batch* batch, const char* cache_path, int retune, int* tangent_bn,
+                       int* syrk_splits);
 /* Capture one evaluation in a CUDA graph on first use and replay it while the device pointers
  * passed to nnc_batch_eval_dev stay the same (enable = 0 drops the graph). */
 int nnc_batch_use_graph(nnc_batch* batch, int enable);

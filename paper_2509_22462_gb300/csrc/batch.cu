@@ -9,6 +9,7 @@
 // every network's Hessian, and the grouped finish.  The whole sequence can be captured once in
 // a CUDA graph and replayed with fixed device buffers.
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -460,6 +461,107 @@ int nnc_batch_tune_set(nnc_batch* b, int syrk_splits) {
     cudaGraphExecDestroy(b->gexec);
     b->gexec = nullptr;
   }
+  return NNC_OK;
+}
+
+// Autotuner of a batch: times whole evaluations (value pass, reverse sweep, grouped tangent GEMMs,
+// grouped symmetric product; CUDA events on the batch's stream, its own buffers, no graph) for
+// every grouped-tangent N tile that covers the widest network and split-K counts 1 .. 3 of the
+// symmetric product, and keeps the fastest; choices are cached in a text file (one line per
+// batch shape: key, N tile, splits, microseconds).
+int nnc_batch_autotune(nnc_batch* b, const char* cache_path, int retune, int* tangent_bn,
+                       int* syrk_splits) {
+  if (!b) return bfail(NNC_ERR_ARG, "batch is NULL");
+  if (!(b->prec == NNC_BF16 || b->prec == NNC_BF16X3) || b->L < 2 || b->K_total == 0) {
+    if (tangent_bn) *tangent_bn = b->L > 1 ? b->layers[1].plan_tan.bn : 0;
+    if (syrk_splits) *syrk_splits = b->K_total > 0 ? b->plan_syrk.splits : 0;
+    return NNC_OK;
+  }
+  BCK(cudaSetDevice(b->device));
+  cudaDeviceProp prop;
+  BCK(cudaGetDeviceProperties(&prop, b->device));
+  char kb[256];
+  std::snprintf(kb, sizeof kb, "batch-sm%d%d-%dsm-prec%d-K%d-nmax%d-hidden%d-depth%d", prop.major, prop.minor,
+                prop.multiProcessorCount, b->prec, b->K, b->n_max, b->layers[1].mp, b->L);
+  const std::string key = kb;
+  int best_bn = 0, best_sp = 0;
+  if (cache_path && !retune) {
+    FILE* f = std::fopen(cache_path, "r");
+    if (f) {
+      char k[256];
+      int bn = 0, sp = 0;
+      double us = 0;
+      while (std::fscanf(f, "%255s %d %d %lf", k, &bn, &sp, &us) == 4)
+        if (key == k) {
+          best_bn = bn;
+          best_sp = sp;
+        }
+      std::fclose(f);
+    }
+  }
+  auto apply = [&](int bn, int sp) -> int {
+    for (int l = 1; l < b->L; ++l) {
+      BLayer& Ly = b->layers[l];
+      const int cur = (l - 1) % 2;
+      TcPlan p;
+      int r = tc_plan_make(p, TC_TANGENT_G, b->prec, Ly.Whi, Ly.Wlo, Ly.mp * b->K, Ly.kp, b->At[cur][0],
+                           b->At[cur][1], b->n_sum, Ly.kp, Ly.mp, b->n_max, Ly.kp, b->sm_count, bn);
+      if (r != NNC_OK) return r;
+      Ly.plan_tan = p;
+    }
+    return nnc_batch_tune_set(b, sp);
+  };
+  double best_us = 1e30;
+  if (!best_bn) {
+    const int cands[4] = {112, 128, 208, 256};
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0));
+    BCK(cudaEventCreate(&e1));
+    for (int bn : cands) {
+      if (bn < (b->n_max + 15) / 16 * 16) continue;   // one column tile per network
+      for (int sp = 1; sp <= 3; ++sp) {
+        if (apply(bn, sp) != NNC_OK) continue;
+        auto run = [&] {
+          return batch_eval(b, b->x_in, b->lam_in, nullptr, b->J_out, b->H_out, b->g_out, b->stream,
+                            b->y_in, b->r_out);
+        };
+        if (run() != NNC_OK) continue;
+        cudaEventRecord(e0, b->stream);
+        bool ok = true;
+        for (int i = 0; i < 3 && ok; ++i) ok = run() == NNC_OK;
+        cudaEventRecord(e1, b->stream);
+        if (!ok || cudaEventSynchronize(e1) != cudaSuccess) continue;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double us = 1e3 * ms / 3;
+        if (us < best_us) {
+          best_us = us;
+          best_bn = bn;
+          best_sp = sp;
+        }
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int r = check_dev_err(b);
+    if (r) return r;
+    if (!best_bn) return bfail(NNC_ERR_CUDA, "batch autotune: no candidate ran");
+    if (cache_path) {
+      FILE* f = std::fopen(cache_path, "a");
+      if (f) {
+        std::fprintf(f, "%s %d %d %.3f\n", key.c_str(), best_bn, best_sp, best_us);
+        std::fclose(f);
+      }
+    }
+  }
+  int r = apply(best_bn, best_sp);
+  if (r) return bfail(r, "batch autotune: the chosen tiling has no valid plan");
+  if (b->gexec) {
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+  }
+  if (tangent_bn) *tangent_bn = best_bn;
+  if (syrk_splits) *syrk_splits = best_sp;
   return NNC_OK;
 }
 

@@ -29,7 +29,7 @@ EXPORTS = ["nnc_load_weights", "nnc_eval", "nnc_residual", "nnc_jacobian", "nnc_
            "nnc_ipm_adversarial_l1_fullspace", "nnc_layer_weights", "nnc_selftest_bounded_wait",
            "nnc_kkt_solve",
            "nnc_residual_noalloc", "nnc_batch_create", "nnc_batch_free", "nnc_batch_info",
-           "nnc_batch_set_bias", "nnc_batch_use_graph", "nnc_batch_tune_set", "nnc_batch_tuning", "nnc_batch_eval_dev", "nnc_batch_residual_dev", "nnc_batch_eval_kkt_dev",
+           "nnc_batch_set_bias", "nnc_batch_use_graph", "nnc_batch_tune_set", "nnc_batch_tuning", "nnc_batch_autotune", "nnc_batch_eval_dev", "nnc_batch_residual_dev", "nnc_batch_eval_kkt_dev",
            "nnc_batch_eval", "nnc_batch_residual", "nnc_batch_eval_kkt", "nnc_ipm_scopf", "nnc_ws_create", "nnc_ws_free",
            "nnc_ws_set_scaling", "nnc_ws_loss_grad", "nnc_ws_adam_step", "nnc_ws_train",
            "nnc_ws_predict", "nnc_ws_get_params", "nnc_ipm_scopf_warm", "nnc_autotune", "nnc_tuning", "nnc_tune_set"]
@@ -121,6 +121,8 @@ def load_library(path: str = LIB_PATH):
     lib.nnc_batch_use_graph.argtypes = [_P, ctypes.c_int]
     lib.nnc_batch_tune_set.argtypes = [_P, ctypes.c_int]
     lib.nnc_batch_tuning.argtypes = [_P, ctypes.POINTER(ctypes.c_int)]
+    lib.nnc_batch_autotune.argtypes = [_P, ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int)]
     lib.nnc_batch_eval_dev.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P]
     lib.nnc_batch_residual_dev.argtypes = [_P, _P, _P, _P, _P]
     lib.nnc_batch_eval_kkt_dev.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _P]
@@ -497,6 +499,13 @@ class Batch:
     def tune_set(self, syrk_splits):
         """nnc_batch_tune_set: pin the symmetric product's split-K count."""
         _check(_lib.nnc_batch_tune_set(self._h, int(syrk_splits)))
+
+    def autotune(self, cache_path=None, retune=False):
+        """nnc_batch_autotune: (grouped-tangent N tile, symmetric-product splits) chosen by timing."""
+        bn, sp = ctypes.c_int(), ctypes.c_int()
+        cp = cache_path.encode() if cache_path else None
+        _check(_lib.nnc_batch_autotune(self._h, cp, int(bool(retune)), ctypes.byref(bn), ctypes.byref(sp)))
+        return bn.value, sp.value
 
     def tuning(self):
         """nnc_batch_tuning: the symmetric product's split-K count in use."""

@@ -1,12 +1,16 @@
 """A small, self-contained workload for kernel profiling (ncu) and quick timing.
 
   python -m paper_2509_22462_gb300.profile_case --widths 784,4096,4096,4096,10 --prec bf16x3 --reps 2
+  python -m paper_2509_22462_gb300.profile_case --widths 784,128,128,10 --prec bf16 --ipm --kkt-device 1
 
 Builds a tanh MLP with N(0, 1/fan_in) weights (seed 0) and runs `reps` full oracle calls
 (value, Jacobian, gradient and Hessian of lambda^T NN, then the FP64 residual) on device-resident
 inputs, then prints
 the per-kernel-kind times of the last call.  With the default widths every tangent GEMM has the
-shape of the 104M network's (M = 4096, N = 784, K = 4096).
+shape of the 104M network's (M = 4096, N = 784, K = 4096).  --bn pins the tangent tiling (1: the
+persistent chain).  --ipm instead solves the adversarial problem (x0 ~ U[0,1]^n_in, target 3,
+margin 0.1) with the host interior-point driver, the KKT dense block on the device with
+--kkt-device 1, and prints the per-iteration timing.
 """
 import argparse
 import os
@@ -23,6 +27,8 @@ def main():
     ap.add_argument("--prec", default="bf16x3")
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--bn", type=int, default=0, help="pin the tangent N tile (0: the load-time plan)")
+    ap.add_argument("--ipm", action="store_true", help="solve the adversarial problem instead")
+    ap.add_argument("--kkt-device", type=int, default=0)
     a = ap.parse_args()
     import torch
     import synth
@@ -40,6 +46,11 @@ def main():
     net = nnc.Net.from_mlp(mlp, precision=a.prec)
     if a.bn:
         net.tune_set(tangent_bn=a.bn)
+    if a.ipm:
+        res, _, _ = nnc.ipm_adversarial(net, d.x0, 3, 0.1, kkt_on_device=a.kkt_device, verbose=1)
+        print({k: res[k] for k in ("status_name", "iters", "obj", "solve_seconds", "t_solver", "t_hessian")})
+        net.free()
+        return
     n, m = widths[0], widths[-1]
     x = torch.tensor(d.x0, device=dev)
     lam = torch.tensor(d.lam, device=dev)

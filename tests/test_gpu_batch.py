@@ -227,7 +227,8 @@ def test_host_eval_kkt_matches_separate_calls(nnc, small_batch):
 
 def test_batch_bench_size_matches_oracle(nnc):
     """The batch the bench times: 256 surrogates n_k -> 1024 x 5 sigmoid -> 1 with n_k ~ U{20..200}
-    (seed 0, loads d = 1), one fused evaluation per iterate replayed from the CUDA graph.  Nets
+    (seed 0, loads d = 1), autotuned tiles, one fused evaluation per iterate replayed from the CUDA
+    graph.  Nets
     with 128 < n_k <= 200 take three lower-triangle tiles of the grouped symmetric product and the
     persistent grouped tangent GEMM runs more than 13 tiles per CTA.  Every net's FP64 residual and
     the value are checked; J, gradient and the full H of 45 nets (the 16 with n_k > 190 and every
@@ -240,6 +241,9 @@ def test_batch_bench_size_matches_oracle(nnc):
     b = nnc.Batch(nets)
     for n in nets:
         n.free()
+    bn, sp = b.autotune()                     # the tiling the bench runs with
+    print(f"[batch bench size] autotuned tangent N tile {bn}, symmetric-product splits {sp}")
+    assert bn >= 208 and 1 <= sp <= 3
     b.use_graph(True)
     dev = torch.device("cuda:0")
     x = synth.uniform01(synth.derive_key(9, "bench-bx"), data.G)
