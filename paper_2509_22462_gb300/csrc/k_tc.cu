@@ -124,13 +124,6 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
                : "memory");
 }
 
-// Adds expected transaction bytes to the current phase without an arrival (the arrival comes
-// later from the same thread).
-__device__ __forceinline__ void mbar_expect_tx_only(uint32_t a, uint32_t bytes) {
-  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(bytes)
-               : "memory");
-}
-
 __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -236,25 +229,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// 32 consecutive accumulator columns of this warp's 32 lanes with one wait (the tangent epilogue
-// takes a 208-wide tile in seven loads instead of thirteen).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 template <bool X3>
@@ -375,21 +349,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem = *tmem_slot;
   // tangent chain (launched with programmatic dependent launch): the previous layer's outputs,
   // this layer's B operand, are complete before any copy or store of this CTA
-  // tangent chain: the weight tiles (A) of the first stages do not depend on the previous layer,
-  // so their copies start before the programmatic-dependent-launch wait (expected bytes only; the
-  // stage's arrival comes with its tangent-tile copy)
-  int pre = 0;  // producer only
-  if (KIND == TC_TANGENT && warp == 0 && lane == 0) {
-    pre = min(C::STAGES, nk);
-    for (int i = 0; i < pre; ++i) {
-      uint8_t* st = smem + i * C::STAGE_BYTES;
-      const uint32_t fb = smem_u32(&full[i]);
-      mbar_expect_tx_only(fb, C::NPARTS * C::A_BYTES);
-      const int kx = (kb0 + i) * C::BKE;
-      tma_load_2d(smem_u32(st), &ta_hi, fb, kx, a_row0);
-      if (X3) tma_load_2d(smem_u32(st + C::A_BYTES), &ta_lo, fb, kx, a_row0);
-    }
-  }
   if (KIND == TC_TANGENT) griddep_wait();
 
   int issued = 0;  // producer only
@@ -398,17 +357,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int i = 0; i < nk; ++i) {
         const int s = i % C::STAGES;
         const uint32_t ph = (uint32_t)(i / C::STAGES) & 1u;
+        if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1u, args.err, 1, abort_flag)) break;
         uint8_t* st = smem + s * C::STAGE_BYTES;
         const uint32_t fb = smem_u32(&full[s]);
+        mbar_expect_tx(fb, C::TX_BYTES);
         const int kx = (kb0 + i) * C::BKE;
-        if (i < pre) {
-          mbar_expect_tx(fb, C::NPARTS * C::B_BYTES);   // the arrival, with the B bytes
-        } else {
-          if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1u, args.err, 1, abort_flag)) break;
-          mbar_expect_tx(fb, C::TX_BYTES);
-          tma_load_2d(smem_u32(st), &ta_hi, fb, kx, a_row0);
-          if (X3) tma_load_2d(smem_u32(st + C::A_BYTES), &ta_lo, fb, kx, a_row0);
-        }
+        tma_load_2d(smem_u32(st), &ta_hi, fb, kx, a_row0);
+        if (X3) tma_load_2d(smem_u32(st + C::A_BYTES), &ta_lo, fb, kx, a_row0);
         tma_load_2d(smem_u32(st + C::NPARTS * C::A_BYTES), &tb_hi, fb, kx, b_row0);
         if (X3) tma_load_2d(smem_u32(st + C::NPARTS * C::A_BYTES + C::B_BYTES), &tb_lo, fb, kx, b_row0);
         if (C::X6) {
@@ -417,10 +372,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         issued = i + 1;
       }
-      // stopped before every prefetched stage got its arrival (abort): arrive now, so that the
-      // drain below can wait for the weight copies already in flight
-      for (int i = issued; i < pre; ++i) mbar_arrive(smem_u32(&full[i]));
-      issued = max(issued, pre);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -487,23 +438,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float cm = args.c[ms];
         const float wsc = C::F8 ? args.wscale[ms] : 1.f;   // FP8: per-row weight scale
 #pragma unroll 1
-        for (int c0 = 0; c0 < n_eff; c0 += 32) {
-          // 32 columns per load; n_eff is a multiple of 16, so the last load may take 16
-          const int w = min(32, n_eff - c0);
-          float v[32];
-          if (w == 32) {
-            tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
-          } else {
-            float h[16];
-            tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, h);
+        for (int c0 = 0; c0 < n_eff; c0 += 16) {
+          float v[16];
+          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] = h[j];
-          }
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
+          for (int j = 0; j < 16; ++j) {
             const int n = n0 + c0 + j;
-            if (j < w && n < n_valid) {
-              if (C::F8) v[j] *= wsc * args.tscale[n];   // undo both FP8 scalings
+            if (C::F8 && n < n_valid) v[j] *= wsc * args.tscale[n];   // undo both FP8 scalings
+            if (n < n_valid) {
               const size_t orow = (size_t)(KIND == TC_TANGENT_G ? b_row0 + n : n);
               if (args.at_hi) put<X3>(args.at_hi, args.at_lo, orow * args.ldo + m, sm * v[j]);
               if (args.zt_hi) put<X3>(args.zt_hi, args.zt_lo, orow * args.ldz + m, v[j]);
