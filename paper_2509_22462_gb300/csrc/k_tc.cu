@@ -1123,7 +1123,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_chain(const __grid_constant_
     for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++pi) {
       int li, tn, tm;
       decode(t, li, tn, tm);
-      const ChainLayer& Ly = args.L[li];
+      // the layer's fields in registers: a reference into the kernel parameters at a run-time
+      // index would be re-read from memory at every store of the epilogue
+      const ChainLayer Ly = args.L[li];
       const int b = pi & 1;
       if (!mbar_wait(smem_u32(&accf[b]), (uint32_t)(pi >> 1) & 1u, args.err, 55, abort_flag)) break;
       tc_fence_after();
