@@ -97,6 +97,25 @@ int nnc_kkt_solve(int nd, int ns, int m, const double* WDD, const double* WSS, c
                   const double* AD, const double* AS, double delta_w, double delta_c,
                   double* rhs_sol, int* inertia);
 
+/* The sparse KKT solve of the full-space problems (host, FP64): K = [[W + diag(sigma) + delta_w I,
+ * A^T], [A, -delta_c I]] with W (n x n, symmetric) given by its lower-triangle triplets
+ * (wr[k] >= wc[k], values wv, repeated entries add up) and A (m x n) by triplets (constraint jr[k],
+ * variable jc[k], values jv).  Every variable i has a stage var_stage[i] >= 0 and every constraint
+ * j a stage con_stage[j]; every nonzero of W and A must couple a stage with itself or with the
+ * next or previous one (K block tridiagonal over the stages).  K is factorized as L diag(F_s) L^T
+ * with F_s = K_ss - K_{s,s-1} F_{s-1}^{-1} K_{s-1,s} (dense, Bunch-Kaufman with 1 x 1 and 2 x 2
+ * pivots), so inertia(K) = sum_s inertia(F_s) exactly.  rhs_sol (n + m): the right-hand side,
+ * overwritten by the solution when inertia[2] == 0 (else unchanged).  inertia (3 ints, may be
+ * NULL): (positive, negative, zero) eigenvalue counts.  Each F_s is equilibrated (R F_s R with
+ * R = diag(1 / sqrt(largest entry of each row)), which keeps its inertia) and a pivot of at most
+ * 1e-14 there counts as zero; a zero is also reported when a leading block F_s is singular
+ * although K is not (this solver pivots within stages only).  NNC_ERR_ARG for bad sizes, pointers or indices,
+ * NNC_ERR_UNSUPPORTED when a nonzero couples stages that are not neighbours. */
+int nnc_stage_kkt_solve(int n, int m, const int* var_stage, const int* con_stage, int nw,
+                        const int* wr, const int* wc, const double* wv, int nj, const int* jr,
+                        const int* jc, const double* jv, const double* sigma, double delta_w,
+                        double delta_c, double* rhs_sol, int* inertia);
+
 /* Eq. 7 itself: the smallest L1 change to the reference image x_ref that makes the classifier's
  * output t at least conf (a probability, for a softmax output layer: 0 < conf < 1).  Split
  * variables carry the L1 norm: v = (x in [0,1]^n_in, p >= 0, q >= 0 in R^n_in, y in R^n_out with
@@ -112,8 +131,11 @@ int nnc_ipm_adversarial_l1(nnc_net* net, const double* x_ref, int target, double
  * activation output y_l are variables, tied by z_l - W_l y_{l-1} - b_l = 0 and
  * y_l - sigma_l(z_l) = 0 (y_0 = x, y_L = y); objective, bounds and split variables as in
  * nnc_ipm_adversarial_l1, so both forms have the same optima.  Functions are evaluated on the host
- * from the net's FP64 weights and the KKT matrix is factorized densely: small nets only
- * (NNC_ERR_UNSUPPORTED when variables + constraints exceed 6000).
+ * from the net's FP64 weights; the Jacobian and the Hessian of the Lagrangian are kept sparse and
+ * the KKT matrix is factorized stage by stage (nnc_stage_kkt_solve) over the chain
+ * (p, q) | link multipliers | x | per layer: (affine multipliers, z_l) | (activation
+ * multipliers, y_l), so memory and work grow with the sum over layers of (layer width)^3, not
+ * with (variables + constraints)^3.
  *   v_out   : (x, p, q, z_1, y_1, ..., z_L, y_L): 3 n_in + 2 sum_l n_l doubles (may be NULL);
  *   lam_out : (link rows, then per layer the affine and the activation rows):
  *             n_in + 2 sum_l n_l doubles (may be NULL);  result : may be NULL. */

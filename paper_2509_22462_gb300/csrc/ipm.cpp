@@ -490,6 +490,70 @@ struct BK {
     }
     return true;
   }
+  // Solve A X = B for r right-hand sides at once (B: n x r row-major, overwritten by X): the same
+  // three sweeps as solve, with every step a contiguous row operation on a block of columns of B;
+  // in parallel over column blocks.
+  void solve_multi(double* B, int r) const {
+    if (r <= 0 || n == 0) return;
+    std::vector<int> start(n);   // first index of each row's pivot block
+    for (int k = 0; k < n;) {
+      for (int c = k; c < k + step[k]; ++c) start[c] = k;
+      k += step[k];
+    }
+    constexpr int kCols = 32;
+#pragma omp parallel for schedule(dynamic, 1) if ((double)n * n * r > 1e6)
+    for (int c0 = 0; c0 < r; c0 += kCols) {
+      const int w = std::min(r, c0 + kCols) - c0;
+      std::vector<double> Y((size_t)n * w);
+      for (int i = 0; i < n; ++i)
+        std::memcpy(&Y[(size_t)i * w], &B[(size_t)perm[i] * r + c0], sizeof(double) * w);
+      // L y' = y: row i takes the columns of the pivot blocks before its own
+      for (int i = 0; i < n; ++i) {
+        const double* ai = &A[(size_t)i * n];
+        double* yi = &Y[(size_t)i * w];
+        for (int c = 0; c < start[i]; ++c) {
+          const double l = ai[c];
+          if (l == 0.0) continue;
+          const double* yc = &Y[(size_t)c * w];
+          for (int j = 0; j < w; ++j) yi[j] -= l * yc[j];
+        }
+      }
+      // D z = y'
+      for (int k = 0; k < n;) {
+        double* y1 = &Y[(size_t)k * w];
+        if (step[k] == 1) {
+          const double d = A[(size_t)k * n + k];
+          const double id = d != 0.0 ? 1.0 / d : 0.0;
+          for (int j = 0; j < w; ++j) y1[j] *= id;
+          k += 1;
+        } else {
+          double* y2 = &Y[(size_t)(k + 1) * w];
+          const double d11 = A[(size_t)k * n + k], d21 = A[(size_t)(k + 1) * n + k],
+                       d22 = A[(size_t)(k + 1) * n + k + 1];
+          const double det = d11 * d22 - d21 * d21;
+          for (int j = 0; j < w; ++j) {
+            const double a = y1[j], b = y2[j];
+            y1[j] = (d22 * a - d21 * b) / det;
+            y2[j] = (-d21 * a + d11 * b) / det;
+          }
+          k += 2;
+        }
+      }
+      // L^T x = z: rows from the last, each final row scattered into the earlier blocks' rows
+      for (int i = n - 1; i >= 0; --i) {
+        const double* ai = &A[(size_t)i * n];
+        const double* yi = &Y[(size_t)i * w];
+        for (int c = 0; c < start[i]; ++c) {
+          const double l = ai[c];
+          if (l == 0.0) continue;
+          double* yc = &Y[(size_t)c * w];
+          for (int j = 0; j < w; ++j) yc[j] -= l * yi[j];
+        }
+      }
+      for (int i = 0; i < n; ++i)
+        std::memcpy(&B[(size_t)perm[i] * r + c0], &Y[(size_t)i * w], sizeof(double) * w);
+    }
+  }
   // Solve A x = b (b overwritten by x).
   void solve(double* b) const {
     std::vector<double> y(n);
@@ -529,6 +593,194 @@ struct BK {
   }
 };
 
+
+// ---------------------------------------------------------------- block-tridiagonal sparse KKT
+// LDL^T of the KKT matrix K = [[W + Sigma + dw I, A^T], [A, -dc I]] of a sparse problem whose
+// unknowns (variables, then multipliers) are split into stages 0 .. S-1 such that every nonzero of
+// W and A couples a stage with itself or with a neighbour (the full-space form of Eq. 4: per layer
+// the affine multipliers, z_l, the activation multipliers, y_l, in a chain).  With F_0 = K_00 and
+//   F_s = K_ss - C_s F_{s-1}^{-1} C_s^T,   C_s = K_{s,s-1},
+// K = L diag(F_0, ..., F_{S-1}) L^T with L block unit lower bidiagonal, L_{s,s-1} = C_s F_{s-1}^{-1}.
+// Each F_s (dense, the size of one layer) is factorized by Bunch-Kaufman with 1 x 1 and 2 x 2
+// pivots, so zero diagonals (free variables without curvature, multipliers without dc) need no
+// regularization, and inertia(K) = sum_s inertia(F_s) exactly (Sylvester's law on the block
+// diagonal).  Only the nonzero rows of each coupling are solved for: X_s = F_{s-1}^{-1} C_s^T over
+// those rows is kept for the solves.  A zero pivot of some F_s is reported through nzero (the
+// driver then regularizes), as is a singular leading block of a nonsingular K, which this fixed
+// stage order cannot pivot around.
+struct StageKkt {
+  int n = 0, m = 0, S = 0;
+  std::vector<int> size;                  // unknowns per stage
+  std::vector<int> ustage, ulocal;        // stage and local index of every unknown
+  // destinations of the pattern entries: F_s(a, b) (b <= a, mirrored) or C_s(a, b)
+  struct Dst { int s, a, b; bool coupling; };
+  std::vector<Dst> wdst, jdst;            // for the W (lower) and A patterns
+  std::vector<std::vector<int>> crow;     // per stage: local rows with a nonzero coupling
+  std::vector<std::vector<int>> crow_of;  // per stage: local row -> index in crow, or -1
+  std::vector<std::vector<double>> C, X;  // per stage: C_s rows (crow x size[s-1]), X_s (size[s-1] x crow)
+  std::vector<std::vector<double>> F, R;  // F_s, then its equilibration R_s F_s R_s in place
+  std::vector<BK> bk;
+  int npos = 0, nneg = 0, nzero = 0;
+  // F_s^{-1} B for r right-hand sides (B: size[s] x r row-major, overwritten)
+  void apply_inv(int s, double* B, int r) const {
+    const int k = size[s];
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < r; ++j) B[(size_t)i * r + j] *= R[s][i];
+    bk[s].solve_multi(B, r);
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < r; ++j) B[(size_t)i * r + j] *= R[s][i];
+  }
+
+  // n variables with stages vstage, m constraints with stages cstage; W pattern (wr >= wc) and A
+  // pattern (ar: constraint, ac: variable).  False if a nonzero couples non-neighbouring stages.
+  bool setup(int n_, int m_, const int* vstage, const int* cstage, const std::vector<int>& wr,
+             const std::vector<int>& wc, const std::vector<int>& ar, const std::vector<int>& ac) {
+    n = n_;
+    m = m_;
+    S = 0;
+    ustage.resize(n + m);
+    ulocal.resize(n + m);
+    for (int i = 0; i < n + m; ++i) {
+      ustage[i] = i < n ? vstage[i] : cstage[i - n];
+      if (ustage[i] < 0) return false;
+      S = std::max(S, ustage[i] + 1);
+    }
+    size.assign(S, 0);
+    for (int i = 0; i < n + m; ++i) ulocal[i] = size[ustage[i]]++;
+    crow.assign(S, {});
+    crow_of.assign(S, {});
+    for (int s = 0; s < S; ++s) crow_of[s].assign(size[s], -1);
+    auto place = [&](int u, int w, Dst& d) {
+      const int su = ustage[u], sw = ustage[w];
+      if (su == sw) {
+        d = {su, std::max(ulocal[u], ulocal[w]), std::min(ulocal[u], ulocal[w]), false};
+        return true;
+      }
+      if (std::abs(su - sw) != 1) return false;
+      const int hi = su > sw ? u : w, lo = su > sw ? w : u;
+      const int s = ustage[hi], a = ulocal[hi];
+      if (crow_of[s][a] < 0) {
+        crow_of[s][a] = (int)crow[s].size();
+        crow[s].push_back(a);
+      }
+      d = {s, crow_of[s][a], ulocal[lo], true};
+      return true;
+    };
+    wdst.resize(wr.size());
+    for (size_t k = 0; k < wr.size(); ++k)
+      if (!place(wr[k], wc[k], wdst[k])) return false;
+    jdst.resize(ar.size());
+    for (size_t k = 0; k < ar.size(); ++k)
+      if (!place(n + ar[k], ac[k], jdst[k])) return false;
+    C.assign(S, {});
+    X.assign(S, {});
+    F.assign(S, {});
+    R.assign(S, {});
+    bk.assign(S, BK{});
+    return true;
+  }
+
+  // Each F_s is equilibrated (R_s F_s R_s, R_s = diag(1 / sqrt(max_j |F_s(i, j)|)), a congruence,
+  // so the inertia is unchanged) before Bunch-Kaufman, whose zero test is then relative:
+  // |pivot| <= rel_tol on rows of largest entry 1.  (An absolute test against the whole matrix's
+  // scale would call the tiny but regular Schur complements of strongly active bounds zero.)
+  void factor(const double* wv, const double* sig, const double* jv, double dw, double dc,
+              double rel_tol) {
+    npos = nneg = nzero = 0;
+    for (int s = 0; s < S; ++s) {
+      F[s].assign((size_t)size[s] * size[s], 0.0);
+      C[s].assign(s > 0 ? crow[s].size() * (size_t)size[s - 1] : 0, 0.0);
+    }
+    for (int i = 0; i < n + m; ++i) {
+      const int s = ustage[i], a = ulocal[i];
+      F[s][(size_t)a * size[s] + a] += i < n ? sig[i] + dw : -dc;
+    }
+    auto add = [&](const Dst& d, double v) {
+      if (d.coupling) {
+        C[d.s][(size_t)d.a * size[d.s - 1] + d.b] += v;
+      } else {
+        F[d.s][(size_t)d.a * size[d.s] + d.b] += v;
+        if (d.a != d.b) F[d.s][(size_t)d.b * size[d.s] + d.a] += v;
+      }
+    };
+    for (size_t k = 0; k < wdst.size(); ++k) add(wdst[k], wv[k]);
+    for (size_t k = 0; k < jdst.size(); ++k) add(jdst[k], jv[k]);
+    for (int s = 0; s < S; ++s) {
+      const int ns_ = size[s];
+      if (s > 0 && !crow[s].empty()) {
+        // X_s = F_{s-1}^{-1} C_s^T over the coupled rows, then F_s(rows) -= C_s X_s
+        const int np = size[s - 1], r = (int)crow[s].size();
+        std::vector<double>& Xs = X[s];
+        Xs.assign((size_t)np * r, 0.0);
+        for (int b = 0; b < r; ++b)
+          for (int k = 0; k < np; ++k) Xs[(size_t)k * r + b] = C[s][(size_t)b * np + k];
+        apply_inv(s - 1, Xs.data(), r);
+        std::vector<double>& Fs = F[s];
+        const std::vector<int>& rows = crow[s];
+#pragma omp parallel for schedule(static) if ((double)r * r * np > 1e6)
+        for (int a = 0; a < r; ++a) {
+          const double* ca = &C[s][(size_t)a * np];
+          std::vector<double> acc(r, 0.0);
+          for (int k = 0; k < np; ++k) {
+            const double c = ca[k];
+            if (c == 0.0) continue;
+            const double* xk = &Xs[(size_t)k * r];
+            for (int b = 0; b < r; ++b) acc[b] += c * xk[b];
+          }
+          double* fa = &Fs[(size_t)rows[a] * ns_];
+          for (int b = 0; b < r; ++b) fa[rows[b]] -= acc[b];
+        }
+      }
+      std::vector<double>& Rs = R[s];
+      Rs.assign(ns_, 1.0);
+      for (int i = 0; i < ns_; ++i) {
+        double mx = 0.0;
+        const double* fi = &F[s][(size_t)i * ns_];
+        for (int j = 0; j < ns_; ++j) mx = std::max(mx, std::fabs(fi[j]));
+        if (mx > 0.0) Rs[i] = 1.0 / std::sqrt(mx);
+      }
+      for (int i = 0; i < ns_; ++i)
+        for (int j = 0; j < ns_; ++j) F[s][(size_t)i * ns_ + j] *= Rs[i] * Rs[j];
+      bk[s].factor(ns_, F[s].data(), rel_tol);
+      npos += bk[s].npos;
+      nneg += bk[s].nneg;
+      nzero += bk[s].nzero;
+    }
+  }
+
+  // x = K^{-1} b (b: variables, then multipliers; overwritten)
+  void solve(double* b) const {
+    std::vector<std::vector<double>> z(S);
+    for (int s = 0; s < S; ++s) z[s].assign(size[s], 0.0);
+    for (int i = 0; i < n + m; ++i) z[ustage[i]][ulocal[i]] = b[i];
+    // forward: z_s -= X_s^T z_{s-1} on the coupled rows (z_{s-1} already final)
+    for (int s = 1; s < S; ++s) {
+      const int np = size[s - 1], r = (int)crow[s].size();
+      for (int a = 0; a < r; ++a) {
+        double t = 0.0;
+        for (int k = 0; k < np; ++k) t += X[s][(size_t)k * r + a] * z[s - 1][k];
+        z[s][crow[s][a]] -= t;
+      }
+    }
+    for (int s = 0; s < S; ++s) {
+      for (int i = 0; i < size[s]; ++i) z[s][i] *= R[s][i];
+      bk[s].solve(z[s].data());
+      for (int i = 0; i < size[s]; ++i) z[s][i] *= R[s][i];
+    }
+    // backward: x_s = w_s - X_{s+1} x_{s+1}(coupled rows)
+    for (int s = S - 2; s >= 0; --s) {
+      const int r = (int)crow[s + 1].size(), np = size[s];
+      if (r == 0) continue;
+      for (int k = 0; k < np; ++k) {
+        double t = 0.0;
+        const double* xk = &X[s + 1][(size_t)k * r];
+        for (int a = 0; a < r; ++a) t += xk[a] * z[s + 1][crow[s + 1][a]];
+        z[s][k] -= t;
+      }
+    }
+    for (int i = 0; i < n + m; ++i) b[i] = z[ustage[i]][ulocal[i]];
+  }
+};
 
 // ---------------------------------------------------------------- dense block on the device
 
@@ -1113,6 +1365,24 @@ struct IpmProblem {
   virtual const double* dense_diag() const { return nullptr; }
   virtual cudaStream_t dense_stream() const { return nullptr; }
   virtual const double* host_wdd() { return nullptr; }
+  // Sparse problems (the full-space form): nd = 0, ns = n; fixed patterns of the Jacobian
+  // (constraint jr[k], variable jc[k]) and of the lower triangle of the Lagrangian Hessian
+  // (hr[k] >= hc[k]), values from jac_sp / hess_sp in pattern order, and the stage of every
+  // variable and constraint for the block-tridiagonal KKT factorization (StageKkt).  jac, hess
+  // and jac_hess are not called for them.
+  virtual bool sparse() const { return false; }
+  std::vector<int> jr, jc, hr, hc, var_stage, con_stage;
+  virtual int jac_sp(const double* v, double* vals) {
+    (void)v;
+    (void)vals;
+    return NNC_ERR_UNSUPPORTED;
+  }
+  virtual int hess_sp(const double* v, const double* lam, double* vals) {
+    (void)v;
+    (void)lam;
+    (void)vals;
+    return NNC_ERR_UNSUPPORTED;
+  }
 };
 
 // Derivatives kept from a trial-point evaluation, keyed by the point and the multipliers.
@@ -1180,10 +1450,19 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
   double tau = std::max(o.tau_min, 1.0 - mu), nu = 1.0, delta_w_last = 0.0;
   int ls_fail = 0, status = NNC_IPM_MAX_ITER, it = 0;
   double E0 = INFINITY;
-  std::vector<double> g(n), c(m), AD((size_t)m * nd), AS((size_t)m * ns), WDD((size_t)nd * nd),
-      WSS(ns), vt(n), ct(m), lam_t(m), rhs(n + m), sol(n + m), dv(n), dl(m), dzL(n), dzU(n), sL(n), sU(n),
+  // sparse problems: Jacobian and Hessian values in their patterns, the block-tridiagonal KKT
+  // factorization over the problem's stages; no dense Jacobian blocks
+  const bool sp = p.sparse();
+  std::vector<double> g(n), c(m), AD(sp ? 0 : (size_t)m * nd), AS(sp ? 0 : (size_t)m * ns),
+      WDD((size_t)nd * nd), WSS(sp ? 0 : ns), Jv(sp ? p.jr.size() : 0), Hv(sp ? p.hr.size() : 0),
+      vt(n), ct(m), lam_t(m), rhs(n + m), sol(n + m), dv(n), dl(m), dzL(n), dzU(n), sL(n), sU(n),
       SigL(n), SigU(n), sig(n), gphi(n), atl(n);
   KktSolver kkt;
+  StageKkt skkt;
+  if (sp && (nd != 0 || (int)p.var_stage.size() != n || (int)p.con_stage.size() != m ||
+             p.jc.size() != p.jr.size() || p.hc.size() != p.hr.size() ||
+             !skkt.setup(n, m, p.var_stage.data(), p.con_stage.data(), p.hr, p.hc, p.jr, p.jc)))
+    return NNC_ERR_UNSUPPORTED;
   // the dense block on the device (tensor-core forms of the single-network problems)
   DenseOnDevice dense;
   const bool dev_kkt = o.kkt_on_device && nd > 0 && p.dense_capable() && p.set_dense_on_device(true);
@@ -1209,6 +1488,11 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
   } dense_guard{dense, p, dev_kkt};
   // atl = A^T lam, row by row (contiguous reads of the dense Jacobian blocks)
   auto update_atl = [&]() {
+    if (sp) {
+      std::fill(atl.begin(), atl.end(), 0.0);
+      for (size_t k = 0; k < Jv.size(); ++k) atl[p.jc[k]] += Jv[k] * lam[p.jr[k]];
+      return;
+    }
 #pragma omp parallel for schedule(static) if ((size_t)m * n > 65536)
     for (int i0 = 0; i0 < n; i0 += 64) {   // column blocks, rows streamed
       const int i1 = std::min(n, i0 + 64);
@@ -1277,7 +1561,9 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
     if (!have_c && m) {
       if (timed(T.fn, T.n_fn, [&] { return p.cons(v.data(), c.data()); })) { status = NNC_IPM_EVAL_ERROR; break; }
     }
-    if (m && p.joint() && p.has_derivs(v.data(), lam.data())) {
+    if (sp) {
+      if (m && timed(T.jac, T.n_jac, [&] { return p.jac_sp(v.data(), Jv.data()); })) { status = NNC_IPM_EVAL_ERROR; break; }
+    } else if (m && p.joint() && p.has_derivs(v.data(), lam.data())) {
       // taken with the residual at the accepted trial point (counted there)
       if (p.jac_hess(v.data(), lam.data(), AD.data(), AS.data(), WDD.data(), WSS.data())) {
         status = NNC_IPM_EVAL_ERROR;
@@ -1293,7 +1579,7 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
     bool finite = std::isfinite(fv);
     for (double x : g) finite &= std::isfinite(x);
     for (double x : c) finite &= std::isfinite(x);
-    finite &= all_finite(AD.data(), AD.size());
+    finite &= all_finite(AD.data(), AD.size()) && all_finite(Jv.data(), Jv.size());
     if (!finite) { status = NNC_IPM_NONFINITE; break; }
     update_atl();
     E0 = errors(0.0);
@@ -1307,7 +1593,9 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
       tau = std::max(o.tau_min, 1.0 - mu);
       Emu = errors(mu);
     }
-    if (!(m && p.joint()) &&
+    if (sp) {
+      if (timed(T.hess, T.n_hess, [&] { return p.hess_sp(v.data(), lam.data(), Hv.data()); })) { status = NNC_IPM_EVAL_ERROR; break; }
+    } else if (!(m && p.joint()) &&
         timed(T.hess, T.n_hess, [&] { return p.hess(v.data(), lam.data(), WDD.data(), WSS.data()); })) { status = NNC_IPM_EVAL_ERROR; break; }
     const auto t_lin = Clock::now();
     for (int i = 0; i < n; ++i) {
@@ -1337,16 +1625,23 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
     }
     scale = std::max(scale, max_abs(AD.data(), AD.size()));
     scale = std::max(scale, max_abs(AS.data(), AS.size()));
+    scale = std::max(scale, max_abs(Jv.data(), Jv.size()));
+    scale = std::max(scale, max_abs(Hv.data(), Hv.size()));
     const double zero_tol = 1e-14 * scale;
     int tries = 0;
     const auto t_fac = Clock::now();
     while (true) {
       ++tries;
-      kkt.factor(nd, ns, m, WDD.data(), WSS.data(), sig.data(), AD.data(), AS.data(), delta_w,
-                 delta_c, zero_tol);
+      if (sp)
+        skkt.factor(Hv.data(), sig.data(), Jv.data(), delta_w, delta_c, 1e-14);
+      else
+        kkt.factor(nd, ns, m, WDD.data(), WSS.data(), sig.data(), AD.data(), AS.data(), delta_w,
+                   delta_c, zero_tol);
       if (kkt.dev_error) break;
-      if (kkt.npos == n && kkt.nneg == m && kkt.nzero == 0) { ok = true; break; }
-      if (kkt.nzero > 0 && delta_c == 0.0 && m) delta_c = 1e-8 * std::pow(mu, 0.25);
+      const int npos = sp ? skkt.npos : kkt.npos, nneg = sp ? skkt.nneg : kkt.nneg,
+                nzero = sp ? skkt.nzero : kkt.nzero;
+      if (npos == n && nneg == m && nzero == 0) { ok = true; break; }
+      if (nzero > 0 && delta_c == 0.0 && m) delta_c = 1e-8 * std::pow(mu, 0.25);
       if (first) {
         delta_w = delta_w_last == 0.0 ? o.delta_w0 : std::max(o.delta_w_min, o.kappa_w_minus * delta_w_last);
         first = false;
@@ -1360,7 +1655,8 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
     if (delta_w > 0.0) delta_w_last = delta_w;
     const auto t_sol = Clock::now();
     sol = rhs;
-    kkt.solve(sol.data());
+    if (sp) skkt.solve(sol.data());
+    else kkt.solve(sol.data());
     if (kkt.dev_error) { status = NNC_IPM_EVAL_ERROR; T.solver += secs(t_lin, Clock::now()); break; }
     const auto t_sol_end = Clock::now();
     for (int i = 0; i < n; ++i) dv[i] = sol[i];
@@ -1389,6 +1685,9 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
         std::vector<double> hv(nd);
         if (nnc::dkkt_matvec(dense.dk, dense.H, dv.data(), hv.data())) { status = NNC_IPM_EVAL_ERROR; break; }
         for (int i = 0; i < nd; ++i) curv += dv[i] * (dense.s * hv[i] + dense.hf[i] * dv[i]);
+      } else if (sp) {
+        for (size_t k = 0; k < Hv.size(); ++k)
+          curv += (p.hr[k] == p.hc[k] ? 1.0 : 2.0) * Hv[k] * dv[p.hr[k]] * dv[p.hc[k]];
       } else {
 #pragma omp parallel for reduction(+ : curv) schedule(static)
         for (int i = 0; i < nd; ++i) {
@@ -1397,7 +1696,8 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
           curv += dv[i] * s;
         }
       }
-      for (int i = 0; i < n; ++i) curv += (SigL[i] + SigU[i] + delta_w + (i >= nd ? WSS[i - nd] : 0.0)) * dv[i] * dv[i];
+      for (int i = 0; i < n; ++i)
+        curv += (SigL[i] + SigU[i] + delta_w + (!sp && i >= nd ? WSS[i - nd] : 0.0)) * dv[i] * dv[i];
       double lmax = 0;
       for (int j = 0; j < m; ++j) lmax = std::max(lmax, std::fabs(lam[j] + dl[j]));
       const double nu_req = (dphi + 0.5 * std::max(curv, 0.0)) / (0.9 * c1);
@@ -1407,7 +1707,7 @@ int ipm_solve(IpmProblem& p, const nnc_ipm_options& o, std::vector<double>& v_ou
     T.solver += secs(t_lin, Clock::now());
     if (o.verbose)
       std::printf("          kkt mode %d, %d factorization(s), delta_w %.1e: factor %.2f ms, solve %.2f ms, "
-                  "step set-up %.2f ms\n", kkt.mode, tries, delta_w, 1e3 * secs(t_fac, t_sol),
+                  "step set-up %.2f ms\n", sp ? 5 : kkt.mode, tries, delta_w, 1e3 * secs(t_fac, t_sol),
                   1e3 * secs(t_sol, t_sol_end),
                   1e3 * (secs(t_lin, Clock::now()) - secs(t_fac, t_sol) - secs(t_sol, t_sol_end)));
     const double phi0 = merit(v, fv, c, nu);
@@ -1849,10 +2149,12 @@ struct AdversarialL1 : IpmProblem {
 // y_l - sigma_l(z_l) = 0 (y_0 = x, y_L = y), with the objective, bounds and split variables of
 // AdversarialL1.  Natural variable order v = (x, p, q, z_1, y_1, ..., z_L, y_L); constraints
 // (link, then per layer the affine rows and the activation rows).  The Hessian of the Lagrangian
-// is diagonal except for a softmax output (an n_out x n_out block on z_L), so z_L of a softmax
-// net forms the dense block and every other variable the diagonal block.  Functions are affine
+// is diagonal except for a softmax output (an n_out x n_out block on z_L).  Functions are affine
 // maps and elementwise activations evaluated on the host (the paper evaluates its full-space
-// model on the CPU too); the KKT matrix is factorized densely, so this form is for small nets.
+// model on the CPU too).  The Jacobian (the weights, sigma' and the identity links) and the
+// Hessian stay sparse, and the KKT matrix, block tridiagonal over the chain of stages
+// (p, q) | link multipliers | x | (affine multipliers, z_1) | (activation multipliers, y_1) | ...,
+// is factorized stage by stage (StageKkt), where the paper uses a general sparse LDL^T (MA57).
 namespace {
 void host_act(int act, double z, double& a, double& d1, double& d2) {
   switch (act) {
@@ -1903,11 +2205,14 @@ void host_softmax(const double* z, int k, double* p) {
 }  // namespace
 
 struct AdversarialL1Full : IpmProblem {
-  int n = 0, L = 0, t = 0, nv = 0, dense = 0;
+  int n = 0, L = 0, t = 0, nv = 0;
   double conf = 0.6;
-  std::vector<int> w, act, off_z, off_y, perm, inv;   // perm: internal -> natural; inv: inverse
+  std::vector<int> w, act, off_z, off_y, off_aff, off_act;
   std::vector<std::vector<double>> W, b;
-  std::vector<double> xr, vn, tmp;
+  std::vector<double> xr, tmp;
+  // Jacobian entries whose values change with v: act rows (sigma' or the softmax block)
+  size_t j_act0 = 0;
+  bool sparse() const override { return true; }
   int load(nnc_net* net, const double* x_ref, int target, double conf_) {
     int nl = 0, ni = 0, no = 0, prec = 0;
     int rc = nnc_net_info(net, &nl, &ni, &no, &prec);
@@ -1932,53 +2237,113 @@ struct AdversarialL1Full : IpmProblem {
     }
     for (int l = 0; l + 1 < L; ++l)
       if (act[l] == NNC_SOFTMAX) return NNC_ERR_UNSUPPORTED;
-    int k = 3 * n;
+    // variables (x, p, q, z_1, y_1, ..., z_L, y_L); constraints (link rows, then per layer the
+    // affine and the activation rows)
+    int k = 3 * n, r = n;
     m = n;
+    off_z.clear();
+    off_y.clear();
+    off_aff.clear();
+    off_act.clear();
     for (int l = 0; l < L; ++l) {
       off_z.push_back(k);
       k += w[l + 1];
       off_y.push_back(k);
       k += w[l + 1];
-      m += 2 * w[l + 1];
+      off_aff.push_back(r);
+      r += w[l + 1];
+      off_act.push_back(r);
+      r += w[l + 1];
     }
+    m = r;
     nv = k;
-    if (nv + m > 6000) return NNC_ERR_UNSUPPORTED;   // dense KKT: small nets only
-    dense = act[L - 1] == NNC_SOFTMAX ? w[L] : 0;
-    nd = dense;
-    ns = nv - dense;
-    perm.clear();
-    for (int i = 0; i < dense; ++i) perm.push_back(off_z[L - 1] + i);
-    for (int i = 0; i < nv; ++i)
-      if (!(dense && i >= off_z[L - 1] && i < off_z[L - 1] + dense)) perm.push_back(i);
-    inv.assign(nv, 0);
-    for (int i = 0; i < nv; ++i) inv[perm[i]] = i;
+    nd = 0;
+    ns = nv;
+    // stages of the block-tridiagonal KKT factorization: (p, q) | link multipliers | x | then per
+    // layer: (affine multipliers, z_l) | (activation multipliers, y_l).  Every nonzero couples a
+    // stage with itself or a neighbour.  Each multiplier shares its stage with the variable it
+    // links by an identity (z_l, y_l): alone, the affine multipliers of a layer wider than the one
+    // before would form a singular block (W_l F^-1 W_l^T has the rank of the narrower layer).
+    var_stage.assign(nv, 0);
+    con_stage.assign(m, 0);
+    for (int i = 0; i < n; ++i) var_stage[i] = 2;
+    for (int l = 0; l < L; ++l) {
+      const int s0 = 3 + 2 * l;
+      for (int j = 0; j < w[l + 1]; ++j) {
+        con_stage[off_aff[l] + j] = s0;
+        var_stage[off_z[l] + j] = s0;
+        con_stage[off_act[l] + j] = s0 + 1;
+        var_stage[off_y[l] + j] = s0 + 1;
+      }
+    }
+    for (int i = 0; i < n; ++i) con_stage[i] = 1;
+    // Jacobian pattern: constant entries first, then the activation rows' entries
+    jr.clear();
+    jc.clear();
+    auto ent = [&](int row, int col) {
+      jr.push_back(row);
+      jc.push_back(col);
+    };
+    for (int i = 0; i < n; ++i) {
+      ent(i, i);
+      ent(i, n + i);
+      ent(i, 2 * n + i);
+    }
+    for (int l = 0; l < L; ++l) {
+      const int kk = w[l + 1], kin = w[l], prev = l == 0 ? 0 : off_y[l - 1];
+      for (int j = 0; j < kk; ++j) {
+        ent(off_aff[l] + j, off_z[l] + j);
+        for (int c = 0; c < kin; ++c) ent(off_aff[l] + j, prev + c);
+      }
+      for (int j = 0; j < kk; ++j) ent(off_act[l] + j, off_y[l] + j);
+    }
+    j_act0 = jr.size();
+    for (int l = 0; l < L; ++l) {
+      const int kk = w[l + 1];
+      for (int j = 0; j < kk; ++j) {
+        if (act[l] == NNC_SOFTMAX)
+          for (int c = 0; c < kk; ++c) ent(off_act[l] + j, off_z[l] + c);
+        else
+          ent(off_act[l] + j, off_z[l] + j);
+      }
+    }
+    // Hessian pattern (lower triangle): sigma'' on each z_l, the softmax block of z_L
+    hr.clear();
+    hc.clear();
+    for (int l = 0; l < L; ++l) {
+      const int kk = w[l + 1];
+      for (int i = 0; i < kk; ++i) {
+        if (act[l] == NNC_SOFTMAX) {
+          for (int j = 0; j <= i; ++j) {
+            hr.push_back(off_z[l] + i);
+            hc.push_back(off_z[l] + j);
+          }
+        } else {
+          hr.push_back(off_z[l] + i);
+          hc.push_back(off_z[l] + i);
+        }
+      }
+    }
     std::vector<double> lbn(nv, -INFINITY), ubn(nv, INFINITY);
     for (int i = 0; i < 3 * n; ++i) lbn[i] = 0.0;
     for (int i = 0; i < n; ++i) ubn[i] = 1.0;
     lbn[off_y[L - 1] + t] = conf;
-    lb.resize(nv);
-    ub.resize(nv);
-    for (int i = 0; i < nv; ++i) {
-      lb[i] = lbn[perm[i]];
-      ub[i] = ubn[perm[i]];
-    }
+    lb = lbn;
+    ub = ubn;
     // start: x = x_ref, p = q = 0, (z_l, y_l) of the forward pass at x_ref
     xr.assign(x_ref, x_ref + n);
-    vn.assign(nv, 0.0);
-    for (int i = 0; i < n; ++i) vn[i] = xr[i];
+    v0.assign(nv, 0.0);
+    for (int i = 0; i < n; ++i) v0[i] = xr[i];
     for (int l = 0; l < L; ++l) {
-      const double* yp = l == 0 ? vn.data() : &vn[off_y[l - 1]];
-      double* z = &vn[off_z[l]];
-      double* y = &vn[off_y[l]];
-      affine(l, yp, z);
-      activate(l, z, y);
+      const double* yp = l == 0 ? v0.data() : &v0[off_y[l - 1]];
+      affine(l, yp, &v0[off_z[l]]);
+      activate(l, &v0[off_z[l]], &v0[off_y[l]]);
     }
-    v0.resize(nv);
-    to_internal(vn.data(), v0.data());
     return NNC_OK;
   }
   void affine(int l, const double* yp, double* z) const {
     const int rows = w[l + 1], cols = w[l];
+#pragma omp parallel for schedule(static) if ((size_t)rows * cols > 65536)
     for (int r = 0; r < rows; ++r) {
       double s = b[l][r];
       const double* wr = &W[l][(size_t)r * cols];
@@ -1994,120 +2359,92 @@ struct AdversarialL1Full : IpmProblem {
     double d1, d2;
     for (int r = 0; r < w[l + 1]; ++r) host_act(act[l], z[r], y[r], d1, d2);
   }
-  void to_natural(const double* vi, double* vnat) const {
-    for (int i = 0; i < nv; ++i) vnat[perm[i]] = vi[i];
-  }
-  void to_internal(const double* vnat, double* vi) const {
-    for (int i = 0; i < nv; ++i) vi[i] = vnat[perm[i]];
-  }
   double f(const double* v) override {
-    vn.resize(nv);
-    to_natural(v, vn.data());
     double s = 0;
-    for (int i = n; i < 3 * n; ++i) s += vn[i];
+    for (int i = n; i < 3 * n; ++i) s += v[i];
     return s;
   }
   void grad_f(const double* v, double* g) override {
-    for (int i = 0; i < nv; ++i) g[i] = (perm[i] >= n && perm[i] < 3 * n) ? 1.0 : 0.0;
+    (void)v;
+    for (int i = 0; i < nv; ++i) g[i] = (i >= n && i < 3 * n) ? 1.0 : 0.0;
   }
   int cons(const double* v, double* c) override {
-    vn.resize(nv);
-    to_natural(v, vn.data());
-    for (int i = 0; i < n; ++i) c[i] = vn[i] - vn[n + i] + vn[2 * n + i] - xr[i];
-    int r = n;
+    for (int i = 0; i < n; ++i) c[i] = v[i] - v[n + i] + v[2 * n + i] - xr[i];
     for (int l = 0; l < L; ++l) {
       const int k = w[l + 1];
-      const double* yp = l == 0 ? vn.data() : &vn[off_y[l - 1]];
+      const double* yp = l == 0 ? v : &v[off_y[l - 1]];
       tmp.resize(k);
       affine(l, yp, tmp.data());
-      for (int j = 0; j < k; ++j) c[r + j] = vn[off_z[l] + j] - tmp[j];
-      r += k;
-      activate(l, &vn[off_z[l]], tmp.data());
-      for (int j = 0; j < k; ++j) c[r + j] = vn[off_y[l] + j] - tmp[j];
-      r += k;
+      for (int j = 0; j < k; ++j) c[off_aff[l] + j] = v[off_z[l] + j] - tmp[j];
+      activate(l, &v[off_z[l]], tmp.data());
+      for (int j = 0; j < k; ++j) c[off_act[l] + j] = v[off_y[l] + j] - tmp[j];
     }
     return NNC_OK;
   }
-  int jac(const double* v, double* AD, double* AS) override {
-    vn.resize(nv);
-    to_natural(v, vn.data());
-    par_zero(AD, (size_t)m * nd);
-    par_zero(AS, (size_t)m * ns);
-    auto put = [&](int row, int col, double val) {
-      const int ic = inv[col];
-      if (ic < nd) AD[(size_t)row * nd + ic] = val;
-      else AS[(size_t)row * ns + ic - nd] = val;
-    };
+  int jac(const double*, double*, double*) override { return NNC_ERR_UNSUPPORTED; }
+  int hess(const double*, const double*, double*, double*) override { return NNC_ERR_UNSUPPORTED; }
+  int jac_sp(const double* v, double* vals) override {
+    size_t k = 0;
     for (int i = 0; i < n; ++i) {
-      put(i, i, 1.0);
-      put(i, n + i, -1.0);
-      put(i, 2 * n + i, 1.0);
+      vals[k++] = 1.0;
+      vals[k++] = -1.0;
+      vals[k++] = 1.0;
     }
-    int r = n;
     for (int l = 0; l < L; ++l) {
-      const int k = w[l + 1], kin = w[l];
-      const int prev = l == 0 ? 0 : off_y[l - 1];
-      for (int j = 0; j < k; ++j) {
-        put(r + j, off_z[l] + j, 1.0);
-        for (int c = 0; c < kin; ++c) put(r + j, prev + c, -W[l][(size_t)j * kin + c]);
+      const int kk = w[l + 1], kin = w[l];
+      for (int j = 0; j < kk; ++j) {
+        vals[k++] = 1.0;
+        const double* wr = &W[l][(size_t)j * kin];
+        for (int c = 0; c < kin; ++c) vals[k++] = -wr[c];
       }
-      r += k;
-      const double* z = &vn[off_z[l]];
+      for (int j = 0; j < kk; ++j) vals[k++] = 1.0;
+    }
+    for (int l = 0; l < L; ++l) {
+      const int kk = w[l + 1];
+      const double* z = &v[off_z[l]];
       if (act[l] == NNC_SOFTMAX) {
-        tmp.resize(k);
-        host_softmax(z, k, tmp.data());
-        for (int j = 0; j < k; ++j) {
-          put(r + j, off_y[l] + j, 1.0);
-          for (int c = 0; c < k; ++c) put(r + j, off_z[l] + c, -(tmp[j] * ((j == c) - tmp[c])));
-        }
+        tmp.resize(kk);
+        host_softmax(z, kk, tmp.data());
+        for (int j = 0; j < kk; ++j)
+          for (int c = 0; c < kk; ++c) vals[k++] = -(tmp[j] * ((j == c) - tmp[c]));
       } else {
-        for (int j = 0; j < k; ++j) {
+        for (int j = 0; j < kk; ++j) {
           double a, d1, d2;
           host_act(act[l], z[j], a, d1, d2);
-          put(r + j, off_y[l] + j, 1.0);
-          put(r + j, off_z[l] + j, -d1);
+          vals[k++] = -d1;
         }
       }
-      r += k;
     }
-    return NNC_OK;
+    return k == jr.size() ? NNC_OK : NNC_ERR_ARG;
   }
-  int hess(const double* v, const double* lam, double* WDD, double* WSS) override {
+  int hess_sp(const double* v, const double* lam, double* vals) override {
     // only y_l - sigma_l(z_l) is nonlinear: its multipliers mu give -grad^2 (mu^T sigma_l(z_l))
-    vn.resize(nv);
-    to_natural(v, vn.data());
-    std::fill(WDD, WDD + (size_t)nd * nd, 0.0);
-    std::fill(WSS, WSS + ns, 0.0);
-    int r = n;
+    size_t k = 0;
     for (int l = 0; l < L; ++l) {
-      const int k = w[l + 1];
-      r += k;
-      const double* mu = lam + r;
-      const double* z = &vn[off_z[l]];
+      const int kk = w[l + 1];
+      const double* mu = lam + off_act[l];
+      const double* z = &v[off_z[l]];
       if (act[l] == NNC_SOFTMAX) {
         // sum_i mu_i grad^2 p_i = diag(p (mu - mubar)) - p (p mu)^T - (p mu) p^T + 2 mubar p p^T
-        tmp.resize(k);
-        host_softmax(z, k, tmp.data());
+        tmp.resize(kk);
+        host_softmax(z, kk, tmp.data());
         double mb = 0;
-        for (int i = 0; i < k; ++i) mb += tmp[i] * mu[i];
-        for (int i = 0; i < k; ++i)
-          for (int j = 0; j < k; ++j) {
+        for (int i = 0; i < kk; ++i) mb += tmp[i] * mu[i];
+        for (int i = 0; i < kk; ++i)
+          for (int j = 0; j <= i; ++j) {
             double cij = -tmp[i] * tmp[j] * mu[j] - tmp[i] * mu[i] * tmp[j] + 2.0 * mb * tmp[i] * tmp[j];
             if (i == j) cij += tmp[i] * (mu[i] - mb);
-            WDD[(size_t)inv[off_z[l] + i] * nd + inv[off_z[l] + j]] = -cij;
+            vals[k++] = -cij;
           }
       } else {
-        for (int j = 0; j < k; ++j) {
+        for (int j = 0; j < kk; ++j) {
           double a, d1, d2;
           host_act(act[l], z[j], a, d1, d2);
-          const int ic = inv[off_z[l] + j];
-          if (ic < nd) WDD[(size_t)ic * nd + ic] = -mu[j] * d2;
-          else WSS[ic - nd] = -mu[j] * d2;
+          vals[k++] = -mu[j] * d2;
         }
       }
-      r += k;
     }
-    return NNC_OK;
+    return k == hr.size() ? NNC_OK : NNC_ERR_ARG;
   }
 };
 
@@ -2327,6 +2664,30 @@ int nnc_kkt_solve(int nd, int ns, int m, const double* WDD, const double* WSS, c
   return NNC_OK;
 }
 
+int nnc_stage_kkt_solve(int n, int m, const int* var_stage, const int* con_stage, int nw,
+                        const int* wr, const int* wc, const double* wv, int nj, const int* jr,
+                        const int* jc, const double* jv, const double* sigma, double delta_w,
+                        double delta_c, double* rhs_sol, int* inertia) {
+  if (n < 0 || m < 0 || nw < 0 || nj < 0 || !var_stage || (m && !con_stage) || !sigma || !rhs_sol ||
+      (nw && (!wr || !wc || !wv)) || (nj && (!jr || !jc || !jv)))
+    return NNC_ERR_ARG;
+  for (int k = 0; k < nw; ++k)
+    if (wr[k] < 0 || wr[k] >= n || wc[k] < 0 || wc[k] > wr[k]) return NNC_ERR_ARG;
+  for (int k = 0; k < nj; ++k)
+    if (jr[k] < 0 || jr[k] >= m || jc[k] < 0 || jc[k] >= n) return NNC_ERR_ARG;
+  std::vector<int> hr(wr, wr + nw), hc(wc, wc + nw), ar(jr, jr + nj), ac(jc, jc + nj);
+  StageKkt k;
+  if (!k.setup(n, m, var_stage, con_stage, hr, hc, ar, ac)) return NNC_ERR_UNSUPPORTED;
+  k.factor(wv, sigma, jv, delta_w, delta_c, 1e-14);
+  if (inertia) {
+    inertia[0] = k.npos;
+    inertia[1] = k.nneg;
+    inertia[2] = k.nzero;
+  }
+  if (k.nzero == 0) k.solve(rhs_sol);
+  return NNC_OK;
+}
+
 void nnc_ipm_default_options(nnc_ipm_options* o) {
   if (!o) return;
   o->tol = 1e-6;
@@ -2391,7 +2752,7 @@ int nnc_ipm_adversarial_l1_fullspace(nnc_net* net, const double* x_ref, int targ
   std::vector<double> v, lam;
   rc = ipm_solve(p, o, v, lam, res);
   if (rc) return rc;
-  if (v_out) p.to_natural(v.data(), v_out);
+  if (v_out) std::copy(v.begin(), v.end(), v_out);
   if (lam_out) std::copy(lam.begin(), lam.end(), lam_out);
   return NNC_OK;
 }

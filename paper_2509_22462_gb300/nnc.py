@@ -27,7 +27,7 @@ EXPORTS = ["nnc_load_weights", "nnc_eval", "nnc_residual", "nnc_jacobian", "nnc_
            "nnc_net_info", "nnc_launch_count", "nnc_profile", "nnc_profile_read",
            "nnc_ipm_default_options", "nnc_ipm_adversarial", "nnc_ipm_adversarial_l1",
            "nnc_ipm_adversarial_l1_fullspace", "nnc_layer_weights", "nnc_selftest_bounded_wait",
-           "nnc_kkt_solve",
+           "nnc_kkt_solve", "nnc_stage_kkt_solve",
            "nnc_residual_noalloc", "nnc_batch_create", "nnc_batch_free", "nnc_batch_info",
            "nnc_batch_set_bias", "nnc_batch_use_graph", "nnc_batch_tune_set", "nnc_batch_tuning", "nnc_batch_autotune", "nnc_batch_eval_dev", "nnc_batch_residual_dev", "nnc_batch_eval_kkt_dev",
            "nnc_batch_eval", "nnc_batch_residual", "nnc_batch_eval_kkt", "nnc_ipm_scopf", "nnc_ws_create", "nnc_ws_free",
@@ -75,6 +75,7 @@ class NNCError(RuntimeError):
 _lib = None
 _P = ctypes.c_void_p
 _DP = ctypes.POINTER(ctypes.c_double)
+_IP = ctypes.POINTER(ctypes.c_int)
 
 
 def load_library(path: str = LIB_PATH):
@@ -154,6 +155,9 @@ def load_library(path: str = LIB_PATH):
                                          ctypes.POINTER(_P), _P, _P, _P, _P]
     lib.nnc_kkt_solve.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _DP, _DP, _DP, _DP, _DP,
                                   ctypes.c_double, ctypes.c_double, _DP, ctypes.POINTER(ctypes.c_int)]
+    lib.nnc_stage_kkt_solve.argtypes = [ctypes.c_int, ctypes.c_int, _IP, _IP, ctypes.c_int, _IP, _IP, _DP,
+                                        ctypes.c_int, _IP, _IP, _DP, _DP, ctypes.c_double,
+                                        ctypes.c_double, _DP, _IP]
     lib.nnc_ipm_adversarial.argtypes = [_P, _DP, ctypes.c_int, ctypes.c_double,
                                         ctypes.POINTER(IpmOptions), _DP, _DP,
                                         ctypes.POINTER(IpmResult)]
@@ -397,8 +401,9 @@ def ipm_adversarial_l1(net, x_ref, target, conf=0.6, **options):
 
 
 def ipm_adversarial_l1_fullspace(net, x_ref, target, conf=0.6, **options):
-    """Eq. 7 with the network in the full space (Eq. 4), host functions and a dense KKT (small
-    nets).  Returns (result dict, v = (x, p, q, z_1, y_1, ..., z_L, y_L), lambda)."""
+    """Eq. 7 with the network in the full space (Eq. 4), host functions, sparse derivatives and the
+    stage-by-stage KKT factorization.  Returns (result dict, v = (x, p, q, z_1, y_1, ..., z_L, y_L),
+    lambda)."""
     lib = load_library()
     x_ref = _f64(x_ref)
     o = ipm_options(**options)
@@ -445,6 +450,25 @@ def kkt_solve(WDD, WSS, sigma, AD, AS, rhs, delta_w=0.0, delta_c=0.0):
     _check(lib.nnc_kkt_solve(nd, ns, m, _dp(WDD), _dp(WSS), _dp(sigma), _dp(AD), _dp(AS),
                              float(delta_w), float(delta_c), _dp(x), inert))
     return x, tuple(inert)
+
+
+def stage_kkt_solve(n, m, var_stage, con_stage, W_trip, A_trip, sigma, rhs, delta_w=0.0,
+                    delta_c=0.0):
+    """nnc_stage_kkt_solve (host FP64): W_trip = (rows, cols, values) of W's lower triangle,
+    A_trip = (constraint rows, variable columns, values); returns (solution or None, (npos, nneg,
+    nzero))."""
+    lib = load_library()
+    iv = lambda a: np.ascontiguousarray(a, dtype=np.int32)
+    vs, cs = iv(var_stage), iv(con_stage)
+    wr, wc, wv = iv(W_trip[0]), iv(W_trip[1]), _f64(W_trip[2])
+    jr, jc, jv = iv(A_trip[0]), iv(A_trip[1]), _f64(A_trip[2])
+    ip = lambda a: a.ctypes.data_as(_IP)
+    x = _f64(rhs).copy()
+    inert = (ctypes.c_int * 3)()
+    _check(lib.nnc_stage_kkt_solve(int(n), int(m), ip(vs), ip(cs), len(wv), ip(wr), ip(wc), _dp(wv),
+                                   len(jv), ip(jr), ip(jc), _dp(jv), _dp(_f64(sigma)),
+                                   float(delta_w), float(delta_c), _dp(x), inert))
+    return (x if inert[2] == 0 else None), tuple(inert)
 
 
 def residual_noalloc(widths, acts, W_dev, b_dev, x, y, r, stream=None):

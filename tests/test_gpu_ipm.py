@@ -280,6 +280,33 @@ def test_adversarial_l1_fullspace_matches_oracle(nnc):
     net.free()
 
 
+def test_adversarial_l1_fullspace_beyond_dense_sizes(nnc):
+    """A classifier whose full-space KKT system (6248 unknowns) exceeds what a dense factorization
+    would hold comfortably ([784, 256 x 3, 10] tanh+softmax): the sparse stage-by-stage solve
+    reaches the reduced space's optimum from the same start, each with its KKT certificate."""
+    from oracle import nn as onn
+    widths = [784, 256, 256, 256, 10]
+    mlp = make_mlp(MLPSpec(widths, ["tanh"] * 3 + ["softmax"]), seed=5, tag="fs-big", bias_std=0.3)
+    mlp.W[-1] = mlp.W[-1] * 4
+    x = synth.uniform01(synth.derive_key(5, "fs-big-x"), 784)
+    t = int(np.argsort(onn.value(mlp, x))[-2])
+    net = nnc.Net.from_mlp(mlp, precision="fp64")
+    rr, _, _ = nnc.ipm_adversarial_l1(net, x, t, 0.6)
+    rf, v, lam = nnc.ipm_adversarial_l1_fullspace(net, x, t, 0.6, max_iter=1000)
+    nv = 3 * 784 + 2 * sum(widths[1:])
+    assert v.size == nv and lam.size == 784 + 2 * sum(widths[1:])
+    print(f"[ipm l1 full space {nv + lam.size} unknowns] reduced: {rr['iters']} iterations, "
+          f"{rr['solve_seconds']:.3f} s; full space: {rf['iters']} iterations, {rf['solve_seconds']:.3f} s "
+          f"(solver {rf['t_solver']:.3f} s), obj {rf['obj']:.10g} vs {rr['obj']:.10g}")
+    assert rr["status"] == 0 and rr["kkt_error"] <= 1e-6
+    assert rf["status"] == 0 and rf["kkt_error"] <= 1e-6
+    assert abs(rf["obj"] - rr["obj"]) <= 1e-6 * max(1.0, abs(rr["obj"]))
+    # the link rows x - p + q = x_ref hold at the full-space point
+    xs, p, q = v[:784], v[784:1568], v[1568:2352]
+    assert np.max(np.abs(xs - p + q - x)) < 1e-6
+    net.free()
+
+
 def test_adversarial_l1_fullspace_contrast(nnc):
     """A deeper classifier ([100, 64 x 3, 10] tanh+softmax): both forms reach the same optimum;
     the full-space KKT system is several times larger (Table 2's structural contrast)."""
