@@ -53,11 +53,13 @@ def _args():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--prec", default="bf16", choices=["bf16", "bf16x3", "fp8", "fp32", "fp64"])
     p.add_argument("--workload", default="104m", choices=["104m", "87m", "tiny", "scopf68m", "scopf", "70m",
-                                                              "274m", "warmstart"])
+                                                              "274m", "warmstart", "fullspace"])
     p.add_argument("--scopf-k", type=int, default=256)
     p.add_argument("--ws-train", type=int, default=10000, help="warmstart: training loads (cold solves)")
     p.add_argument("--ws-test", type=int, default=1000, help="warmstart: held-out loads")
     p.add_argument("--ws-epochs", type=int, default=100)
+    p.add_argument("--fs-widths", default="128,512,1024",
+                   help="fullspace: hidden widths of the 784 -> w x 5 -> 10 classifiers")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64-form", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -591,6 +593,58 @@ def run_ours_warmstart(args, rank, world, local_rank):
     return 0
 
 
+def run_ours_fullspace(args, rank, world, local_rank):
+    """Tables 2-3's contrast on the MNIST-shaped classifiers 784 -> w x 5 -> 10 (tanh, softmax
+    output; w = 128, 512, 1024 give the 167k, 1.46M and 5.0M parameter rows): Eq. 7 (L1 change
+    of an image, target class at probability >= 0.6) solved to KKT 1e-6 in the reduced space (the
+    network on the GPU, BF16 and FP64 forms) and in the full space of Eq. 4 (host functions, the
+    sparse stage-by-stage KKT factorization), from the same start.  Weights N(0, 1/fan_in) with
+    the output layer scaled by 4 (so that 0.6 is reachable, as for a trained classifier), x ~
+    U[0,1]^784, target = the second most likely class.  The metric is the full-space solve time of
+    the widest net; iterations, times and objectives of every form are beside it."""
+    import torch
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local_rank)
+    from paper_2509_22462_gb300 import build as B, nnc
+    B.build()
+    import synth
+    from synth.nets import MLPSpec
+    rows = []
+    for w in [int(v) for v in args.fs_widths.split(",") if v]:
+        widths = [784] + [w] * 5 + [10]
+        mlp = synth.make_mlp(MLPSpec(widths, ["tanh"] * 5 + ["softmax"]), seed=1, tag="table3",
+                             bias_std=0.3)
+        mlp.W[-1] = mlp.W[-1] * 4
+        x = synth.uniform01(synth.derive_key(1, "table3-x"), 784)
+        net = nnc.Net.from_mlp(mlp, precision="fp64")
+        p0 = net.eval(x)
+        t = int(np.argsort(p0)[-2])
+        row = {"widths": widths, "n_params": int(sum(a.size for a in mlp.W) + sum(b.size for b in mlp.b)),
+               "full_space_variables": 3 * 784 + 2 * (5 * w + 10),
+               "full_space_constraints": 784 + 2 * (5 * w + 10)}
+        keys = ("status_name", "iters", "obj", "kkt_error", "solve_seconds", "t_solver", "t_hessian")
+        for prec in ("bf16", "fp64"):
+            nr = net if prec == "fp64" else nnc.Net.from_mlp(mlp, precision=prec)
+            r, _, _ = nnc.ipm_adversarial_l1(nr, x, t, 0.6)
+            row["reduced_" + prec] = {k: r[k] for k in keys}
+            if nr is not net:
+                nr.free()
+        r, _, _ = nnc.ipm_adversarial_l1_fullspace(net, x, t, 0.6, max_iter=3000)
+        row["full_space"] = {k: r[k] for k in keys}
+        net.free()
+        rows.append(row)
+    last = rows[-1]
+    out = {"metric": "full_space_ipm_solve_s", "value": last["full_space"]["solve_seconds"], "unit": "s",
+           "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "mnist_784_wx5_10_tanh_softmax_eq7_full_vs_reduced",
+                      "widths": args.fs_widths, "target": "second most likely class, p >= 0.6"},
+           "rows": rows}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -599,6 +653,8 @@ def run_ours(args, rank, world, local_rank):
         return run_ours_scopf(args, rank, world, local_rank)
     if args.workload == "warmstart":
         return run_ours_warmstart(args, rank, world, local_rank)
+    if args.workload == "fullspace":
+        return run_ours_fullspace(args, rank, world, local_rank)
 
     spec, mlp, d = _workload(args.workload)
     cpu_baseline = None
