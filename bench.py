@@ -461,18 +461,20 @@ def run_ours_scopf(args, rank, world, local_rank):
     launches = nnc.launch_count() - launches0
     clk = clocks.stop() if clocks else None
     value, el_ms = aggregate(e0.elapsed_time(e1), args.steps, world, dev)
-    # end to end through the host-pointer batch call
-    xs = [x[s] for s in data.subsets]
-    lams = [np.ones(1)] * K
-    batch.eval(xs, lams)
+    # end to end through the host-pointer batch call (the fused iterate call of the device step),
+    # inputs and outputs in pinned host memory
+    pin = lambda k: torch.empty(k, dtype=torch.float64, pin_memory=True).numpy()  # noqa: E731
+    xh, yh, lh = pin(batch.n_sum), pin(K), pin(K)
+    xh[:], yh[:], lh[:] = batch.concat([x[s] for s in data.subsets]), 0.0, 1.0
+    outs = (pin(K), pin(batch.n_sum), pin(batch.h_sum), pin(batch.n_sum))
+    batch.eval_kkt(xh, yh, lh, out=outs)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        ys, Js, Hs, gs = batch.eval(xs, lams)
-        batch.residual(xs, ys)
+        batch.eval_kkt(xh, yh, lh, out=outs)
     el = time.perf_counter() - t0
     e2e = {"value": world * args.steps / el, "unit": UNIT,
-           "h2d_bytes_per_step": 8 * (batch.n_sum + K) + 8 * (batch.n_sum + K),
-           "d2h_bytes_per_step": 8 * (K + batch.n_sum + batch.h_sum + batch.n_sum) + 8 * K}
+           "h2d_bytes_per_step": 8 * (batch.n_sum + K + K),
+           "d2h_bytes_per_step": 8 * (K + batch.n_sum + batch.h_sum + batch.n_sum)}
     ipm = {}
     if rank == 0 and not args.no_ipm:
         res, v, lam = nnc.ipm_scopf(batch, data.G, data.subsets, data.cost, synth.scopf_demand(data, d),
@@ -737,14 +739,18 @@ def run_ours(args, rank, world, local_rank):
     # end to end through the host-pointer C ABI (copies inside the timed region)
     e2e = None
     if not args.no_e2e:
-        xh, lh, yh = d.x0.copy(), d.lam.copy(), np.zeros(m)
+        # inputs and outputs in pinned host memory
+        pin = lambda *shape: torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+        xh, lh, yh = pin(n), pin(m), pin(m)
+        xh[:], lh[:], yh[:] = d.x0, d.lam, 0.0
+        outs = (pin(m), pin(m, n), pin(n, n), pin(n))
         for _ in range(2):
-            net.eval_kkt(xh, yh, lh)
+            net.eval_kkt(xh, yh, lh, out=outs)
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            net.eval_kkt(xh, yh, lh)
+            net.eval_kkt(xh, yh, lh, out=outs)
         el = time.perf_counter() - t0
         if world > 1:
             t = torch.tensor([el], device=dev)

@@ -283,13 +283,20 @@ class Net:
                                     _dp(g) if want_grad else None))
         return (H, g) if want_grad else H
 
-    def eval_kkt(self, x, y, lam):
-        """nnc_eval_kkt: (r = y - NN(x), J, H, grad = lambda^T J) at one iterate, one value pass."""
+    def eval_kkt(self, x, y, lam, out=None):
+        """nnc_eval_kkt: (r = y - NN(x), J, H, grad = lambda^T J) at one iterate, one value pass.
+        out: optional (r, J, H, grad) float64 C-contiguous arrays to fill (for example views of
+        pinned host memory), else new arrays."""
         x, y, lam = _f64(x), _f64(y), _f64(lam)
-        r = np.empty(self.n_out)
-        J = np.empty((self.n_out, self.n_in))
-        H = np.empty((self.n_in, self.n_in))
-        g = np.empty(self.n_in)
+        if out is None:
+            out = (np.empty(self.n_out), np.empty((self.n_out, self.n_in)),
+                   np.empty((self.n_in, self.n_in)), np.empty(self.n_in))
+        r, J, H, g = out
+        for a, shape in zip(out, ((self.n_out,), (self.n_out, self.n_in), (self.n_in, self.n_in),
+                                  (self.n_in,))):
+            if a.dtype != np.float64 or a.shape != shape or not a.flags.c_contiguous:
+                raise ValueError("eval_kkt: out arrays must be C-contiguous float64 of shapes "
+                                 "(n_out,), (n_out, n_in), (n_in, n_in), (n_in,)")
         _check(_lib.nnc_eval_kkt(self._h, _dp(x), _dp(y), _dp(lam), _dp(r), _dp(J), _dp(H), _dp(g)))
         return r, J, H, g
 
@@ -570,14 +577,23 @@ class Batch:
         _check(_lib.nnc_batch_residual(self._h, _dp(x), _dp(y), _dp(r)))
         return [r[k * self.n_out:(k + 1) * self.n_out] for k in range(self.K)]
 
-    def eval_kkt(self, xs, ys, lams):
+    def eval_kkt(self, xs, ys, lams, out=None):
         """nnc_batch_eval_kkt (host arrays): per net the residual y - NN(x), J, H and the gradient
-        lambda^T J from one value pass; returns concatenated (r, J, H, g)."""
-        x, y, lam = self.concat(xs), self.concat(ys), self.concat(lams)
-        r = np.empty(self.K * self.n_out)
-        J = np.empty(self.n_sum * self.n_out)
-        H = np.empty(self.h_sum)
-        g = np.empty(self.n_sum)
+        lambda^T J from one value pass; returns concatenated (r, J, H, g).  xs, ys, lams: lists
+        per net, or arrays already concatenated; out: optional concatenated (r, J, H, g) float64
+        arrays to fill (for example in pinned host memory)."""
+        cat = lambda v: v if isinstance(v, np.ndarray) and v.dtype == np.float64 and v.flags.c_contiguous \
+            else self.concat(v)  # noqa: E731
+        x, y, lam = cat(xs), cat(ys), cat(lams)
+        sizes = (self.K * self.n_out, self.n_sum * self.n_out, self.h_sum, self.n_sum)
+        if x.size != self.n_sum or y.size != self.K * self.n_out or lam.size != self.K * self.n_out:
+            raise ValueError("eval_kkt: concatenated inputs of the wrong size")
+        if out is None:
+            out = tuple(np.empty(k) for k in sizes)
+        for a, k in zip(out, sizes):
+            if a.dtype != np.float64 or a.size != k or not a.flags.c_contiguous:
+                raise ValueError("eval_kkt: out arrays must be C-contiguous float64 of the concatenated sizes")
+        r, J, H, g = out
         _check(_lib.nnc_batch_eval_kkt(self._h, _dp(x), _dp(y), _dp(lam), _dp(r), _dp(J), _dp(H), _dp(g)))
         return r, J, H, g
 
