@@ -375,14 +375,18 @@ def scopf_flops(n_in, hidden=1024, depth=5):
     return f
 
 
-def scopf_weight_bytes(raw):
+def scopf_weight_bytes(raw, prec):
     """Algorithmic DRAM bytes of one batched step: every weight is read by the double-float value
-    pass (8 B: hi, lo FP32 pair), the FP32 reverse sweep (4 B) and the tangent sweep (4 B: the FP32
-    first layer, BF16 hi + lo for the hidden layers; a linear output layer takes no tangent)."""
+    pass (8 B: hi, lo FP32 pair), the FP32 reverse sweep (4 B) and the tangent sweep (the FP32
+    first layer, 4 B; the hidden layers' tangent operand: BF16 hi + lo in the split form, 4 B,
+    BF16 hi in the BF16 form, 2 B, e4m3 in the FP8 form, 1 B; a linear output layer takes no
+    tangent)."""
+    tb = {"bf16x3": 4, "bf16": 2, "fp8": 1}.get(prec, 4)
     b = 0
     for m in raw:
         P = sum(w.size for w in m.W)
-        b += 8 * P + 4 * P + 4 * (P - m.W[-1].size)
+        P1 = m.W[0].size
+        b += 8 * P + 4 * P + 4 * P1 + tb * (P - P1 - m.W[-1].size)
     return b
 
 
@@ -481,7 +485,7 @@ def run_ours_scopf(args, rank, world, local_rank):
                                     data.delta)
         ipm[args.prec] = res
     fl = scopf_flops(n_in)
-    wb = scopf_weight_bytes(raw)
+    wb = scopf_weight_bytes(raw, args.prec)
     if rank == 0:
         out = {"metric": "batched_hessian_lag_evals_per_s", "value": value, "unit": UNIT, "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": el_ms / args.steps,
