@@ -1783,7 +1783,7 @@ cudaError_t tc_tangent_chain(const TcPlan* plans, const ChainOut* outs, int nl, 
   a.tiles = tiles;
   a.cnt = cnt;
   a.err = err;
-  const int grid = std::min(p0.sm_count > 0 ? p0.sm_count : 148, tiles);
+  const int grid = std::min({p0.sm_count > 0 ? p0.sm_count : 148, tiles, p0.ntm * p0.ntn});
   switch (p0.bn) {
     case 112: return launch_chain_mode<112>(p0.mode, a, grid, st);
     case 128: return launch_chain_mode<128>(p0.mode, a, grid, st);
