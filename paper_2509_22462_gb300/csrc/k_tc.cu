@@ -947,8 +947,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // ---------------------------------------------------------------- persistent tangent chain
 // The whole chain of tangent GEMMs of one evaluation (Zdot_l = W_l Adot_{l-1} for every hidden
-// layer, with the fused epilogue of TC_TANGENT) in one persistent launch: one CTA per SM takes the
-// (layer, column block, row block) tiles blockIdx.x, blockIdx.x + gridDim.x, ... in that order.
+// layer, with the fused epilogue of TC_TANGENT) in one persistent launch: as many CTAs as one
+// layer has tiles (at most one per SM; the remaining SMs stay free for the reverse sweep that runs
+// next to the chain), CTA b taking the (layer, column block, row block) tiles b, b + gridDim.x, ...
+// in that order.
 // Layer l + 1's tiles of column block tn read Adot_l^T rows tn * BN .. (all of layer l's rows
 // along K), so they wait (bounded) for an arrival counter that the epilogues of layer l's tiles
 // of that column block advance: four arrivals (one per epilogue warp) per row block, released
