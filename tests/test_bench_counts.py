@@ -41,24 +41,30 @@ def test_tangent_shape_key():
 
 
 def test_scopf_weight_bytes():
-    """8 B (double-float value pass) + 4 B (FP32 reverse) + 4 B (BF16 hi + lo tangents) per
-    weight, except the linear output layer, which takes no tangent."""
+    """8 B (double-float value pass) + 4 B (FP32 reverse) per weight, plus the tangent operand: the
+    FP32 first layer (4 B) and the hidden layers' BF16 hi + lo (4 B, split form), BF16 hi (2 B) or
+    e4m3 (1 B); the linear output layer takes no tangent."""
     rng = np.random.default_rng(0)
     nets = []
     for n_k in (20, 137, 200):
-        shapes = [(16, n_k), (16, 16), (1, 16)]
+        shapes = [(16, n_k), (16, 16), (16, 16), (1, 16)]
         nets.append(types.SimpleNamespace(W=[rng.standard_normal(s) for s in shapes]))
-    expect = 0
-    for net in nets:
-        P = sum(w.size for w in net.W)
-        expect += 8 * P + 4 * P + 4 * (P - net.W[-1].size)
-    assert bench.scopf_weight_bytes(nets) == expect
+    for prec, tb in (("bf16x3", 4), ("bf16", 2), ("fp8", 1)):
+        expect = 0
+        for net in nets:
+            P = sum(w.size for w in net.W)
+            first, hidden = net.W[0].size, net.W[1].size + net.W[2].size
+            assert P == first + hidden + net.W[-1].size
+            expect += 12 * P + 4 * first + tb * hidden
+        assert bench.scopf_weight_bytes(nets, prec) == expect, prec
     # the bench's own surrogates (8 of them here; the bench runs 256): n_k -> 1024 x 5 -> 1
     data, d, raw = bench._scopf_workload(8)
     P = sum(sum(w.size for w in m.W) for m in raw)
     n_k = [len(s) for s in data.subsets]
     assert P == sum(n * 1024 + 4 * 1024 * 1024 + 1024 for n in n_k)
-    assert bench.scopf_weight_bytes(raw) == 16 * P - 4 * 1024 * len(raw)
+    assert bench.scopf_weight_bytes(raw, "bf16x3") == 16 * P - 4 * 1024 * len(raw)
+    hidden = 4 * 1024 * 1024 * len(raw)
+    assert bench.scopf_weight_bytes(raw, "bf16") == 16 * P - 4 * 1024 * len(raw) - 2 * hidden
 
 
 def test_clock_samples():
