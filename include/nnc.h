@@ -263,7 +263,8 @@ long long nnc_launch_count(void);
 /* Autotuner for the tensor-core forms (no effect on results): times every N-tile width of each
  * tangent-GEMM shape, on one SM per tile and on SM pairs (tcgen05 cta_group::2, 256-row tiles;
  * layers with a multiple of 256 rows, BF16 forms), and every split-K count of the symmetric
- * product on the net's own buffers (CUDA events on its stream) and keeps the fastest.
+ * product with 128- and 256-column tiles on the net's own buffers (CUDA events on its stream)
+ * and keeps the fastest.
  * cache_path (may be NULL) names a JSON file of earlier choices, keyed by device, kind,
  * precision and shape; existing entries are reused unless retune != 0, and the file is
  * rewritten with the current choices.  CUDA-core forms return NNC_OK at once.  nnc_tuning

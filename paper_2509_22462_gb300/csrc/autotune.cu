@@ -198,40 +198,45 @@ extern "C" int nnc_autotune(nnc_net* net, const char* cache_path, int retune) {
     }
     net->use_chain = use != 0;
   }
-  // symmetric product: split-K count (bounded by the partial-sum buffer allocated at load)
+  // symmetric product: N tile (128 or 256 columns; lower-triangle tiles only) and split-K count
+  // (bounded by the partial-sum buffer allocated at load); the cache keeps bn * 1000 + splits
   if (net->K_total > 0 && net->plan_syrk.ready) {
     const std::string key = key_of(net, "syrk", n, n, net->K_total);
-    int best = net->plan_syrk.splits;
+    int best = net->plan_syrk.bn * 1000 + net->plan_syrk.splits;
     auto it = cache.find(key);
-    if (it != cache.end() && !retune && it->second.first <= net->h_splits) {
+    auto valid = [&](int code) {
+      return (code / 1000 == 128 || code / 1000 == 256) && code % 1000 >= 1 &&
+             code % 1000 <= net->h_splits;
+    };
+    if (it != cache.end() && !retune && valid(it->second.first)) {
       best = it->second.first;
     } else {
       double best_us = 1e30;
-      for (int sp = 1; sp <= net->h_splits; ++sp) {
-        TcPlan p;
-        if (tc_plan_make(p, TC_SYRK, prec, net->Zt[0], net->Zt[1], n, net->K_total, net->Yt[0],
-                         net->Yt[1], n, net->K_total, n, n, net->K_total, net->sm_count, 0, sp) != NNC_OK)
-          continue;
-        if (p.splits != sp) continue;
-        const double us = time_us(st, 3, [&] {
-          cudaMemsetAsync(net->Hp, 0, sizeof(float) * (size_t)net->h_splits * n * n, st);
-          tc_syrk(p, (float*)net->Hp, net->dev_err, st);
-        });
-        if (us < best_us) {
-          best_us = us;
-          best = sp;
+      for (int bn : {128, 256})
+        for (int sp = 1; sp <= net->h_splits; ++sp) {
+          TcPlan p;
+          if (tc_plan_make(p, TC_SYRK, prec, net->Zt[0], net->Zt[1], n, net->K_total, net->Yt[0],
+                           net->Yt[1], n, net->K_total, n, n, net->K_total, net->sm_count, bn,
+                           sp) != NNC_OK)
+            continue;
+          if (p.splits != sp) continue;
+          const double us = time_us(st, 3, [&] { tc_syrk(p, (float*)net->Hp, net->dev_err, st); });
+          if (us < best_us) {
+            best_us = us;
+            best = bn * 1000 + sp;
+          }
         }
-      }
       cache[key] = {best, best_us};
     }
-    if (best != net->plan_syrk.splits) {
+    if (best != net->plan_syrk.bn * 1000 + net->plan_syrk.splits) {
       TcPlan p;
-      if (tc_plan_make(p, TC_SYRK, prec, net->Zt[0], net->Zt[1], n, net->K_total, net->Yt[0],
-                       net->Yt[1], n, net->K_total, n, n, net->K_total, net->sm_count, 0,
-                       best) != NNC_OK || p.splits > net->h_splits) {
+      if (!valid(best) ||
+          tc_plan_make(p, TC_SYRK, prec, net->Zt[0], net->Zt[1], n, net->K_total, net->Yt[0],
+                       net->Yt[1], n, net->K_total, n, n, net->K_total, net->sm_count, best / 1000,
+                       best % 1000) != NNC_OK || p.splits > net->h_splits) {
         cache.erase(key);
         write_cache(cache_path, cache);
-        set_last_error("autotune: the symmetric-product split count " + std::to_string(best) +
+        set_last_error("autotune: the symmetric-product tiling " + std::to_string(best) +
                        " has no valid plan; the previous one is kept");
         return NNC_ERR_ARG;
       }

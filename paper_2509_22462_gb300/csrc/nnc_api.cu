@@ -829,6 +829,11 @@ static int load_impl(nnc_net* net, int n_layers, const int* widths, const int* a
                            net->sm_count);
       if (r != NNC_OK) return fail(r, "tensor-core symmetric-product plan failed");
       splits = net->plan_syrk.splits;
+      // room for the split partials of the 256-column tile too (the autotuner may pick it)
+      TcPlan p256;
+      if (tc_plan_make(p256, TC_SYRK, prec, net->Zt[0], net->Zt[1], n, net->K_total, net->Yt[0],
+                       net->Yt[1], n, net->K_total, n, n, net->K_total, net->sm_count, 256) == NNC_OK)
+        splits = std::max(splits, p256.splits);
     }
     net->h_splits = splits;
     float* hp;
