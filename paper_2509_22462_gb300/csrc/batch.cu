@@ -124,10 +124,12 @@ int batch_value(nnc_batch* b, const double* x, bool residual, cudaStream_t st) {
   const void* a_in = b->xs2;
   int ld_in = b->kp0;
   for (auto& Ly : b->layers) {
+    // the first layer's rows hold each net's n_k inputs, padded to the widest: skip the padding
     BCK(launch_gemv_stream_df_grouped(Ly.W2, Ly.kp, K, Ly.mp, Ly.m, Ly.b, a_in, ld_in, Ly.act,
                                       residual ? Ly.ra : Ly.a, residual ? Ly.ra2 : Ly.a2,
                                       residual ? nullptr : Ly.s1, residual ? nullptr : Ly.s2,
-                                      b->dev_err, b->sm_count, st));
+                                      b->dev_err, b->sm_count, st,
+                                      &Ly == &b->layers[0] ? b->d_gn : nullptr));
     a_in = residual ? Ly.ra2 : Ly.a2;
     ld_in = Ly.mp;
   }
@@ -153,7 +155,8 @@ int batch_eval(nnc_batch* b, const double* x, const double* lam, double* y, doub
   int cur = 0;
   for (int l = b->L - 1; l >= 0; --l) {
     BLayer& Ly = b->layers[l];
-    BCK(launch_bgemv_rev(Ly.W32, Ly.kp, Ly.mp, Ly.m, K, b->Zbar[cur], S, b->part, st));
+    BCK(launch_bgemv_rev(Ly.W32, Ly.kp, Ly.mp, Ly.m, K, b->Zbar[cur], S, b->part, st,
+                         l == 0 ? b->d_gn : nullptr));
     const int chunks = bgemv_rev_chunks(Ly.m, Ly.kp);
     if (l > 0) {
       BLayer& Lp = b->layers[l - 1];

@@ -7,8 +7,10 @@ namespace nnc {
 
 cudaError_t launch_bx_scatter(const double* xcat, const int* gn, const int* goff, int kp, int groups,
                               double* xs, float* xf, cudaStream_t st);
+// gcols (device, may be NULL): group g's valid columns; the partials of the columns past them
+// (a first layer's zero padding) are written as zero without reading the weights.
 cudaError_t launch_bgemv_rev(const float* W, int ldw, int mp, int m, int groups, const double* Zbar,
-                             int S, float* part, cudaStream_t st);
+                             int S, float* part, cudaStream_t st, const int* gcols = nullptr);
 int bgemv_rev_chunks(int m, int ldw);   // row chunks of a reverse step (ldw: columns)
 cudaError_t launch_brev_reduce(const float* part, int chunks, int kcols, int mp_out, int groups,
                                int S, const double* s1, const double* s2, int lam_col, int nJ,

@@ -46,7 +46,8 @@ __host__ __device__ constexpr int brev_rows(int) { return 64; }
 template <int SMAX>
 __global__ void __launch_bounds__(256) k_bgemv_rev(const float* __restrict__ W, int ldw, int mp,
                                                    int m, const double* __restrict__ Zbar, int S,
-                                                   int chunks, float* __restrict__ part) {
+                                                   int chunks, float* __restrict__ part,
+                                                   const int* __restrict__ gcols) {
   __shared__ float zs[kBRowsMax][SMAX];
   const int rows = brev_rows(ldw);
   const int g = blockIdx.z;
@@ -59,7 +60,13 @@ __global__ void __launch_bounds__(256) k_bgemv_rev(const float* __restrict__ W, 
     zs[r][s] = (r < nr && s < S) ? (float)zg[(size_t)(r0 + r) * S + s] : 0.f;
   }
   __syncthreads();
-  if (c0 >= ldw || nr <= 0) return;
+  if (c0 >= ldw) return;
+  float* out = part + (((size_t)g * chunks + blockIdx.y) * ldw + c0) * S;
+  // columns past the net's own (zero padding of a first layer): zero partials, no weight reads
+  if (nr <= 0 || (gcols && c0 >= gcols[g])) {
+    for (int i = 0; i < 4 * S; ++i) out[i] = 0.f;
+    return;
+  }
   float acc[4][SMAX];
 #pragma unroll
   for (int v = 0; v < 4; ++v)
@@ -78,7 +85,6 @@ __global__ void __launch_bounds__(256) k_bgemv_rev(const float* __restrict__ W, 
       acc[3][s] = fmaf(w.w, z, acc[3][s]);
     }
   }
-  float* out = part + (((size_t)g * chunks + blockIdx.y) * ldw + c0) * S;
 #pragma unroll
   for (int v = 0; v < 4; ++v)
 #pragma unroll
@@ -87,15 +93,15 @@ __global__ void __launch_bounds__(256) k_bgemv_rev(const float* __restrict__ W, 
 }
 
 cudaError_t launch_bgemv_rev(const float* W, int ldw, int mp, int m, int groups, const double* Zbar,
-                             int S, float* part, cudaStream_t st) {
+                             int S, float* part, cudaStream_t st, const int* gcols) {
   const int chunks = bgemv_rev_chunks(m, ldw);
   // threads: the row's 4-column groups, rounded up to whole warps, at most 256
   const int threads = std::min(256, (ldw / 4 + 31) / 32 * 32);
   dim3 grid((ldw + 4 * threads - 1) / (4 * threads), chunks, groups);
   if (S <= 2)
-    k_bgemv_rev<2><<<grid, threads, 0, st>>>(W, ldw, mp, m, Zbar, S, chunks, part);
+    k_bgemv_rev<2><<<grid, threads, 0, st>>>(W, ldw, mp, m, Zbar, S, chunks, part, gcols);
   else if (S <= 4)
-    k_bgemv_rev<4><<<grid, threads, 0, st>>>(W, ldw, mp, m, Zbar, S, chunks, part);
+    k_bgemv_rev<4><<<grid, threads, 0, st>>>(W, ldw, mp, m, Zbar, S, chunks, part, gcols);
   else
     return cudaErrorInvalidValue;
   note_launch();
@@ -180,46 +186,71 @@ cudaError_t launch_brev_seed(int m, int mp, int groups, int S, int nJ, int lam_c
 }
 
 // First-layer tangents of every group: At[boff+n][m] = s1[m] W1_g[m][n], Zt/Yt likewise at
-// column offset 0 of the side-by-side array (row stride ldz), n < n_g.
-__global__ void k_bfirst_tangent(const float* __restrict__ W1, int ldw, int mp,
-                                 const int* __restrict__ gn, const int* __restrict__ goff,
-                                 const double* __restrict__ s1, const double* __restrict__ c,
-                                 __nv_bfloat16* at_hi, __nv_bfloat16* at_lo, int lda,
-                                 __nv_bfloat16* zt_hi, __nv_bfloat16* zt_lo,
-                                 __nv_bfloat16* yt_hi, __nv_bfloat16* yt_lo, int ldz, int x3) {
-  __shared__ float tile[32][33];
+// column offset 0 of the side-by-side array (row stride ldz), n < n_g.  A CTA transposes a
+// 64-row x 32-column tile of W1_g through shared memory; a thread then owns one tangent column
+// and eight consecutive rows, so every output is one 16-byte store of eight BF16 values (row
+// strides and offsets are multiples of 8 elements, rows padded to a multiple of 64).
+__global__ void __launch_bounds__(256) k_bfirst_tangent(const float* __restrict__ W1, int ldw, int mp,
+                                                        const int* __restrict__ gn,
+                                                        const int* __restrict__ goff,
+                                                        const double* __restrict__ s1,
+                                                        const double* __restrict__ c,
+                                                        __nv_bfloat16* at_hi, __nv_bfloat16* at_lo,
+                                                        int lda, __nv_bfloat16* zt_hi,
+                                                        __nv_bfloat16* zt_lo, __nv_bfloat16* yt_hi,
+                                                        __nv_bfloat16* yt_lo, int ldz, int x3) {
+  __shared__ float tile[64][33];
   const int g = blockIdx.z;
   const int n_g = gn[g];
-  const int m0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
-  if (n0 >= n_g) return;
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 32;
+  if (n0 >= n_g) return;   // the same for the whole CTA
   const float* Wg = W1 + (size_t)g * mp * ldw;
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const int mm = m0 + r, nn = n0 + threadIdx.x;
-    tile[r][threadIdx.x] = (mm < mp && nn < n_g) ? Wg[(size_t)mm * ldw + nn] : 0.f;
+  const int t = threadIdx.x, j = t / 8, q = t % 8;   // tangent n0 + j, rows m0 + 8q .. + 7
+  const int nn = n0 + j, mb = m0 + 8 * q;
+  float wv[8], sv[8], cv[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int mm = m0 + t / 32 + 8 * i, nc = n0 + (t & 31);
+    wv[i] = (mm < mp && nc < n_g) ? __ldg(Wg + (size_t)mm * ldw + nc) : 0.f;
   }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const bool in = mb + i < mp;
+    sv[i] = in ? (float)__ldg(s1 + (size_t)g * mp + mb + i) : 0.f;
+    cv[i] = in ? (float)__ldg(c + (size_t)g * mp + mb + i) : 0.f;
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) tile[t / 32 + 8 * i][t & 31] = wv[i];
   __syncthreads();
-  const int mm = m0 + threadIdx.x;
-  if (mm >= mp) return;
-  const float sm = (float)s1[(size_t)g * mp + mm], cm = (float)c[(size_t)g * mp + mm];
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const int nn = n0 + r;
-    if (nn >= n_g) continue;
-    const float w = tile[threadIdx.x][r];
-    const size_t row = (size_t)goff[g] + nn;
-    __nv_bfloat16 h, l;
-    if (at_hi) {
-      split_bf16(sm * w, h, l);
-      at_hi[row * lda + mm] = h;
-      if (x3) at_lo[row * lda + mm] = l;
-    }
-    if (zt_hi) {
-      split_bf16(w, h, l);
-      zt_hi[row * ldz + mm] = h;
-      if (x3) zt_lo[row * ldz + mm] = l;
-      split_bf16(cm * w, h, l);
-      yt_hi[row * ldz + mm] = h;
-      if (x3) yt_lo[row * ldz + mm] = l;
-    }
+  if (nn >= n_g || mb >= mp) return;
+  uint32_t ah[4], al[4], zh[4], zl[4], yh[4], yl[4];
+  auto pk = [](float v0, float v1, uint32_t& hi, uint32_t& lo) {
+    __nv_bfloat16 h0, l0, h1, l1;
+    split_bf16(v0, h0, l0);
+    split_bf16(v1, h1, l1);
+    hi = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+    lo = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+  };
+#pragma unroll
+  for (int e = 0; e < 8; e += 2) {
+    const float w0 = tile[8 * q + e][j], w1 = tile[8 * q + e + 1][j];
+    pk(sv[e] * w0, sv[e + 1] * w1, ah[e / 2], al[e / 2]);
+    pk(w0, w1, zh[e / 2], zl[e / 2]);
+    pk(cv[e] * w0, cv[e + 1] * w1, yh[e / 2], yl[e / 2]);
+  }
+  auto st16 = [](__nv_bfloat16* base, size_t idx, const uint32_t (&v)[4]) {
+    *reinterpret_cast<uint4*>(base + idx) = make_uint4(v[0], v[1], v[2], v[3]);
+  };
+  const size_t row = (size_t)goff[g] + nn;
+  if (at_hi) {
+    st16(at_hi, row * lda + mb, ah);
+    if (x3) st16(at_lo, row * lda + mb, al);
+  }
+  if (zt_hi) {
+    st16(zt_hi, row * ldz + mb, zh);
+    if (x3) st16(zt_lo, row * ldz + mb, zl);
+    st16(yt_hi, row * ldz + mb, yh);
+    if (x3) st16(yt_lo, row * ldz + mb, yl);
   }
 }
 
@@ -227,8 +258,13 @@ cudaError_t launch_bfirst_tangent(const float* W1, int ldw, int mp, int groups, 
                                   const int* gn, const int* goff, const double* s1, const double* c,
                                   void* at_hi, void* at_lo, int lda, void* zt_hi, void* zt_lo,
                                   void* yt_hi, void* yt_lo, int ldz, bool x3, cudaStream_t st) {
-  dim3 grid((n_max + 31) / 32, (mp + 31) / 32, groups), block(32, 8);
-  k_bfirst_tangent<<<grid, block, 0, st>>>(
+  // 16-byte stores: row strides and the outputs' element offsets must be multiples of 8
+  auto al8 = [](const void* p) { return ((uintptr_t)p % 16) == 0; };
+  if (mp % 64 || lda % 8 || ldz % 8 || !al8(at_hi) || !al8(at_lo) || !al8(zt_hi) || !al8(zt_lo) ||
+      !al8(yt_hi) || !al8(yt_lo) || (zt_hi && !yt_hi))
+    return cudaErrorInvalidValue;
+  dim3 grid((n_max + 31) / 32, mp / 64, groups);
+  k_bfirst_tangent<<<grid, 256, 0, st>>>(
       W1, ldw, mp, gn, goff, s1, c, (__nv_bfloat16*)at_hi, (__nv_bfloat16*)at_lo, lda,
       (__nv_bfloat16*)zt_hi, (__nv_bfloat16*)zt_lo, (__nv_bfloat16*)yt_hi, (__nv_bfloat16*)yt_lo, ldz,
       x3 ? 1 : 0);

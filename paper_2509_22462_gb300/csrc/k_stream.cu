@@ -56,6 +56,9 @@ struct SvArgs {
   // belong to group g, whose first group_m are valid and whose activation vector starts at
   // a_in + g ld_in (float2 elements); group_rows = 0: one vector for all rows
   int group_rows, group_m, ld_in;
+  // grouped rows: valid columns of each group's weights (the rest of a row is zero padding and is
+  // neither copied nor multiplied), or NULL (every row's ldw columns)
+  const int* gcols;
 };
 
 __global__ void __launch_bounds__(kSvMaxWarps * 32) k_gemv_stream(const SvArgs p) {
@@ -68,12 +71,15 @@ __global__ void __launch_bounds__(kSvMaxWarps * 32) k_gemv_stream(const SvArgs p
   const int row_bytes = p.ldw * EB;
   const int groups = row_bytes / kSvGroup;
   const int g0 = warp * p.gw;
-  const int ng = max(0, min(groups, g0 + p.gw) - g0);  // this warp's groups
-  const int slice_bytes = ng * kSvGroup;
   const int r0 = blockIdx.x * p.rows_per_cta;
   int nrows = max(0, min(p.m, r0 + p.rows_per_cta) - r0);
   const int grp = p.group_rows ? r0 / p.group_rows : 0;   // rows_per_cta divides group_rows
   if (p.group_rows) nrows = max(0, min(nrows, p.group_m - (r0 - grp * p.group_rows)));
+  // a group's rows end at its last 512-byte group holding a valid column
+  const int groups_used =
+      (p.group_rows && p.gcols) ? min(groups, (p.gcols[grp] * EB + kSvGroup - 1) / kSvGroup) : groups;
+  const int ng = max(0, min(groups_used, g0 + p.gw) - g0);  // this warp's groups
+  const int slice_bytes = ng * kSvGroup;
   unsigned char* ring = sv_smem + warp * (p.ns * kSvSlice);
   if (p.ns < 1 || p.ns > kSvMaxStages || p.nw * 32 != (int)blockDim.x || p.nw > kSvMaxWarps ||
       p.gw < 1 || p.gw > kSvMaxGroups)
@@ -261,18 +267,19 @@ cudaError_t launch_gemv_stream_df(const void* W2, int ldw, int m, const double* 
                                   int act, double* a_out, void* a_df, double* s1, double* s2,
                                   int* err, int sm_count, cudaStream_t st) {
   if (ldw % kPad) return cudaErrorInvalidValue;
-  SvArgs a{W2, ldw, m, b, a_in2, act, a_out, (float2*)a_df, s1, s2, err, 0, 0, 0, 0, 0, 0, 0};
+  SvArgs a{W2, ldw, m, b, a_in2, act, a_out, (float2*)a_df, s1, s2, err, 0, 0, 0, 0, 0, 0, 0,
+           nullptr};
   return launch_sv(a, sm_count, st);
 }
 
 cudaError_t launch_gemv_stream_df_grouped(const void* W2, int ldw, int groups, int mp, int m,
                                           const double* b, const void* a_in2, int ld_in, int act,
                                           double* a_out, void* a_df, double* s1, double* s2,
-                                          int* err, int sm_count, cudaStream_t st) {
+                                          int* err, int sm_count, cudaStream_t st, const int* gcols) {
   if (ldw % kPad || mp % kPad || ld_in % kPad || groups < 1 || m < 1 || m > mp)
     return cudaErrorInvalidValue;
   SvArgs a{W2, ldw, groups * mp, b, a_in2, act, a_out, (float2*)a_df, s1, s2, err, 0, 0, 0, 0,
-           mp, m, ld_in};
+           mp, m, ld_in, gcols};
   return launch_sv(a, sm_count, st);
 }
 

@@ -110,11 +110,14 @@ cudaError_t launch_gemv_stream_df(const void* W2, int ldw, int m, const double* 
                                   int* err, int sm_count, cudaStream_t st);
 // The same over `groups` networks stacked by rows (W2 [groups * mp][ldw], bias and outputs
 // [groups * mp]): group g multiplies its own activations a_in2 + g * ld_in (float2 elements) and
-// only its first m rows are computed (the padding rows' outputs are left as they are).
+// only its first m rows are computed (the padding rows' outputs are left as they are).  gcols
+// (device, may be NULL): group g's weights have gcols[g] valid columns, the rest zero padding that
+// is skipped in whole 512-byte groups.
 cudaError_t launch_gemv_stream_df_grouped(const void* W2, int ldw, int groups, int mp, int m,
                                           const double* b, const void* a_in2, int ld_in, int act,
                                           double* a_out, void* a_df, double* s1, double* s2,
-                                          int* err, int sm_count, cudaStream_t st);
+                                          int* err, int sm_count, cudaStream_t st,
+                                          const int* gcols = nullptr);
 }  // namespace nnc
 
 namespace nnc {
