@@ -510,12 +510,12 @@ def run_ours_scopf(args, rank, world, local_rank):
     return 0
 
 
-def timed_kernel_pass(net, step, steps, torch):
+def timed_kernel_pass(net, step, steps, torch, kind="tangent_chain"):
     """K steps with one pair of events per step around the chain of tangent GEMMs (the library's
     "tangent_chain" span, counted as its launches, so that no event sits between launches that
-    overlap through programmatic dependent launch); returns {kind: (ms, count)} and the pass's
-    time per step in ms under "_ms_per_step"."""
-    net.profile(True, kinds=["tangent_chain"])
+    overlap through programmatic dependent launch; or another span kind); returns {kind: (ms,
+    count)} and the pass's time per step in ms under "_ms_per_step"."""
+    net.profile(True, kinds=[kind])
     torch.cuda.synchronize()
     a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a0.record()
@@ -725,6 +725,9 @@ def run_ours(args, rank, world, local_rank):
     # the roofline kernel's launch time: a second timed pass of K steps with the library's events
     # around each tangent-GEMM launch only, on the stream the kernel runs on
     roof_pass = timed_kernel_pass(net, step, args.steps, torch)
+    # the double-float value pass (the step's HBM-bound part on its critical path), the same way
+    value_pass = timed_kernel_pass(net, step, args.steps, torch, kind="value_pass") \
+        if args.prec != "fp64" else None
     clk = clocks.stop() if clocks else None
     # per-kind breakdown (events around every launch, outside the timed region)
     net.profile(True)
@@ -843,12 +846,24 @@ def run_ours(args, rank, world, local_rank):
         n64.free()
 
     if rank == 0:
+        roof_value = None
+        if value_pass and value_pass.get("value_pass", (0, 0))[1] > 0:
+            vms, vcnt = value_pass["value_pass"]
+            vbytes = 8 * sum(a * b for a, b in zip(spec.widths[1:], spec.widths[:-1]))
+            vgbs = vbytes / (vms / 1e3 / (vcnt / (len(spec.widths) - 1))) / 1e9
+            roof_value = {"kernel": "k_gemv_stream (double-float value pass, every layer)", "bound": "hbm",
+                          "achieved": vgbs, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                          "frac": vgbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
+                          "traffic": None, "algorithmic_bytes_per_pass": vbytes,
+                          "ms_per_pass": vms / (vcnt / (len(spec.widths) - 1)),
+                          "timing": "one event pair per step around the pass's layers, on the launch stream"}
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if args.prec.startswith("bf16") else
                {"fp32": "f32", "fp8": "e4m3"}.get(args.prec, "f64"),
                "data": "synthetic", "config": _workload_config(spec, args.workload, args.prec),
-               "roofline": roof, "cpu_baseline": cpu_baseline, "e2e": e2e, "gpu_launches": launches,
+               "roofline": roof, "roofline_value_pass": roof_value, "cpu_baseline": cpu_baseline,
+               "e2e": e2e, "gpu_launches": launches,
                "clocks": clk, "kernels": kernel_ms, "forms": forms, "ipm_solve": ipm,
                "hessian_algorithmic_gflop": hessian_flops(spec) / 1e9}
         print(json.dumps(out), flush=True)

@@ -287,7 +287,9 @@ int nnc_tune_set(nnc_net* net, int tangent_bn, int syrk_splits);
  *   3 reverse layer, 4 other,
  *   5 tangent chain: one pair of events around all tangent GEMMs of an evaluation, counted as
  *     that many launches (its ms / count is the average launch time with the launches overlapping
- *     as they do unprofiled; recorded only when its own bit is set).
+ *     as they do unprofiled; recorded only when its own bit is set),
+ *   6 value pass: likewise around the layers of the double-float value pass of an evaluation
+ *     (non-FP64 forms), counted as its layers.
  * enable = 0 stops recording; enable = 1 records kinds 0 to 4; enable > 1 records only the kinds
  * whose bit (k + 1) is set, so that events do not sit between launches that overlap through
  * programmatic dependent launch. */

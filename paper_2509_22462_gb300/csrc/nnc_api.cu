@@ -99,9 +99,11 @@ cudaStream_t pick(nnc_net* net, void* st) { return st ? (cudaStream_t)st : net->
 
 // Kernel kinds of nnc_profile_read.
 // PK_TAN_SPAN: one pair of events around the whole chain of tangent GEMMs of an evaluation (from
-// before the first to after the last), counted as that many launches; recorded only when asked
-// for by its own bit, so that no event sits between the chain's launches.
-enum { PK_TANGENT = 0, PK_SYRK = 1, PK_FWD = 2, PK_REV = 3, PK_OTHER = 4, PK_TAN_SPAN = 5, PK_N = 6 };
+// before the first to after the last), counted as that many launches; PK_FWD_SPAN likewise around
+// the layers of the value pass.  Both are recorded only when asked for by their own bits, so that
+// no event sits between launches that overlap through programmatic dependent launch.
+enum { PK_TANGENT = 0, PK_SYRK = 1, PK_FWD = 2, PK_REV = 3, PK_OTHER = 4, PK_TAN_SPAN = 5,
+       PK_FWD_SPAN = 6, PK_N = 7 };
 
 // Brackets one launch with a pair of events on its stream when profiling is on.
 struct ProfScope {
@@ -149,11 +151,15 @@ int run_forward(nnc_net* net, bool fp64, cudaStream_t st) {
     return NNC_OK;
   }
   const void* a_in2 = net->x2;
-  for (auto& Ly : net->layers) {
-    PROF(PK_FWD);
-    CK(launch_gemv_stream_df(Ly.W2, Ly.kp, Ly.m, Ly.b, a_in2, Ly.act, Ly.a, Ly.a2, Ly.s1, Ly.s2,
-                             net->dev_err, net->sm_count, st));
-    a_in2 = Ly.a2;
+  {
+    ProfScope span(net, PK_FWD_SPAN, st);   // the whole value pass, counted as its layers
+    if (span.on) net->ev_weight.back() = (int)net->layers.size();
+    for (auto& Ly : net->layers) {
+      PROF(PK_FWD);
+      CK(launch_gemv_stream_df(Ly.W2, Ly.kp, Ly.m, Ly.b, a_in2, Ly.act, Ly.a, Ly.a2, Ly.s1, Ly.s2,
+                               net->dev_err, net->sm_count, st));
+      a_in2 = Ly.a2;
+    }
   }
   if (net->softmax) CK(launch_softmax_head(net->n_out, net->layers.back().a, st));
   return NNC_OK;
@@ -496,7 +502,9 @@ int nnc_profile(nnc_net* net, int enable) {
   int r = check_net(net);
   if (r) return r;
   // 1: every kind; other nonzero values: a mask of kinds, bit (k + 1) for kind k
-  net->prof_mask = enable == 0 ? 0u : enable == 1 ? ~(1u << PK_TAN_SPAN) : (unsigned)enable >> 1;
+  net->prof_mask = enable == 0                ? 0u
+                   : enable == 1              ? ~((1u << PK_TAN_SPAN) | (1u << PK_FWD_SPAN))
+                                              : (unsigned)enable >> 1;
   net->ev_used = 0;
   net->ev_kind.clear();
   net->ev_weight.clear();

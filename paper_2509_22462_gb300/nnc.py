@@ -63,7 +63,8 @@ class IpmResult(ctypes.Structure):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["status_name"] = IPM_STATUS.get(self.status, str(self.status))
         return d
-PROFILE_KINDS = ["tangent_gemm", "syrk", "forward", "reverse", "other", "tangent_chain"]
+PROFILE_KINDS = ["tangent_gemm", "syrk", "forward", "reverse", "other", "tangent_chain",
+                 "value_pass"]
 
 
 class NNCError(RuntimeError):
