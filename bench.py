@@ -40,7 +40,8 @@ METRIC = "hessian_lag_evals_per_s"
 # (M = 4096, N = 784, K = 4096); an entry is valid only for the shape and kernel version it was
 # taken on, other shapes report null.
 TANGENT_TRAFFIC = {((4096, 784, 4096), "bf16x3", 208): 81.66e6,
-                   ((4096, 784, 4096), "bf16x3", -208): 81.57e6}
+                   ((4096, 784, 4096), "bf16x3", -208): 81.57e6,
+                   ((4096, 784, 4096), "bf16", 208): 40.20e6}
 UNIT = "evals/s"
 FP64_NOMINAL_TFLOPS = 1.25   # GB300's nominal dense FP64 rate
 
