@@ -49,6 +49,7 @@ struct TcArgs {
   const int4* work;
   int a_group_rows;
   long long ldh_split;
+  int vec_ok;   // tangent outputs: 16-byte aligned bases and row strides (staged epilogue)
 };
 
 // Per-layer description of the persistent tangent chain (k_tc_chain).
@@ -231,6 +232,23 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// True on every thread of the four epilogue warps (named barrier 1, 128 threads) only if p is
+// true on all of them, so that the barriers of the staged epilogue are reached by all or none.
+__device__ __forceinline__ bool epi_all(bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred q;\n\t"
+      "setp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.and.pred q, 1, 128, q;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)p)
+      : "memory");
+  return r != 0;
+}
+
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
 template <bool X3>
 __device__ __forceinline__ void put(__nv_bfloat16* hi, __nv_bfloat16* lo, size_t o, float v) {
   if (X3) {
@@ -240,6 +258,92 @@ __device__ __forceinline__ void put(__nv_bfloat16* hi, __nv_bfloat16* lo, size_t
     lo[o] = l;
   } else {
     hi[o] = __float2bfloat16_rn(v);
+  }
+}
+
+// Shared memory of the staged tangent epilogue: two buffers of [output][16 columns][128 rows] BF16
+// for the outputs at_hi, zt_hi, yt_hi (and at_lo, zt_lo, yt_lo in the split form).
+template <bool X3>
+constexpr int staged_epi_bytes() {
+  return 2 * (X3 ? 6 : 3) * 16 * BM * 2;
+}
+
+// Tangent epilogue of one 128-row tile, 16 accumulator columns at a time.  The four epilogue
+// warps (thread `row` holds TMEM lane `row`) scale their row's values, write them as BF16 into
+// shared memory as [output][column][row] (the pipeline stages are idle once every MMA has
+// completed), meet at a named barrier, and store each output's 16 x 128 block as whole 256-byte
+// row segments with 16-byte stores.  Stored one element per thread, the same outputs go out as
+// 64-byte pieces, two store instructions per element, and their issue, not their bytes, set the
+// epilogue's time.  Slices alternate between two buffers, so one barrier per slice suffices: a
+// buffer is written again only after every thread has passed the barrier that follows its reads.
+// Output row of column n: n, or b_row0 + n for a group of a batch; the column inside the row is
+// m0 + row.  Needs args.vec_ok (16-byte aligned outputs and strides).
+template <int MODE, int KIND>
+__device__ __forceinline__ void tangent_epilogue_staged(const TcArgs& args, uint8_t* smem,
+                                                        uint32_t tmem_q, int row, int m0, int n0,
+                                                        int n_eff, int n_valid, int b_row0,
+                                                        float sm, float cm, float wsc) {
+  constexpr bool X3 = MODE == MODE_BF16X3;
+  constexpr bool F8 = MODE == MODE_FP8;
+  constexpr int NS = X3 ? 6 : 3;                 // output slots
+  constexpr int SLOT = 16 * BM;                  // elements of one output's block
+  __nv_bfloat16* stg = reinterpret_cast<__nv_bfloat16*>(smem);
+  __nv_bfloat16* const outp[6] = {args.at_hi, args.zt_hi, args.yt_hi,
+                                  args.at_lo, args.zt_lo, args.yt_lo};
+  const bool has_a = args.at_hi != nullptr, has_z = args.zt_hi != nullptr,
+             has_y = args.yt_hi != nullptr;
+  int it = 0;
+#pragma unroll 1
+  for (int c0 = 0; c0 < n_eff; c0 += 16, ++it) {
+    float v[16];
+    tmem_ld16(tmem_q + (uint32_t)c0, v);
+    __nv_bfloat16* buf = stg + (it & 1) * NS * SLOT;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      float x = v[j];
+      if (F8) {
+        const int n = n0 + c0 + j;
+        x *= n < n_valid ? wsc * args.tscale[n] : 0.f;   // undo both FP8 scalings
+      }
+      const int o = j * BM + row;
+      if (X3) {
+        __nv_bfloat16 h, l;
+        if (has_a) {
+          split_bf16(sm * x, h, l);
+          buf[0 * SLOT + o] = h;
+          buf[3 * SLOT + o] = l;
+        }
+        if (has_z) {
+          split_bf16(x, h, l);
+          buf[1 * SLOT + o] = h;
+          buf[4 * SLOT + o] = l;
+        }
+        if (has_y) {
+          split_bf16(cm * x, h, l);
+          buf[2 * SLOT + o] = h;
+          buf[5 * SLOT + o] = l;
+        }
+      } else {
+        if (has_a) buf[0 * SLOT + o] = __float2bfloat16_rn(sm * x);
+        if (has_z) buf[1 * SLOT + o] = __float2bfloat16_rn(x);
+        if (has_y) buf[2 * SLOT + o] = __float2bfloat16_rn(cm * x);
+      }
+    }
+    epi_sync();
+    // chunk c = row + 128 i of the slice: output i / 2, column (c / 16) % 16, 16-byte piece c % 16
+#pragma unroll
+    for (int i = 0; i < 2 * NS; ++i) {
+      const int s = i >> 1;
+      if ((s % 3 == 0 && !has_a) || (s % 3 == 1 && !has_z) || (s % 3 == 2 && !has_y)) continue;
+      const int j = (row >> 4) + 8 * (i & 1), pc = row & 15;
+      const int n = n0 + c0 + j;
+      if (n < n_valid) {
+        const size_t orow = (size_t)(KIND == TC_TANGENT_G ? b_row0 + n : n);
+        const int ld = s % 3 == 0 ? args.ldo : args.ldz;
+        *reinterpret_cast<uint4*>(outp[s] + orow * ld + m0 + pc * 8) =
+            *reinterpret_cast<const uint4*>(buf + s * SLOT + j * BM + pc * 8);
+      }
+    }
   }
 }
 
@@ -414,7 +518,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     const int q = warp & 3;  // TMEM lanes 32q .. 32q+31 belong to this warp
     const int row = q * 32 + lane;
-    const bool ok = mbar_wait(smem_u32(accf), 0, args.err, 3, abort_flag);
+    const bool ok = epi_all(mbar_wait(smem_u32(accf), 0, args.err, 3, abort_flag));
     tc_fence_after();
     // the next layer may be queued now: its CTAs take SMs as this grid's epilogues end
     if (KIND == TC_TANGENT && threadIdx.x == 64) griddep_launch();
@@ -437,19 +541,26 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float sm = (float)args.s1[ms];
         const float cm = args.c[ms];
         const float wsc = C::F8 ? args.wscale[ms] : 1.f;   // FP8: per-row weight scale
+        if (args.vec_ok) {
+          static_assert(C::STAGES * C::STAGE_BYTES >= staged_epi_bytes<X3>(),
+                        "staged epilogue fits in the pipeline stages");
+          tangent_epilogue_staged<MODE, KIND>(args, smem, tmem + ((uint32_t)(q * 32) << 16), row,
+                                              m0, n0, n_eff, n_valid, b_row0, sm, cm, wsc);
+        } else {
 #pragma unroll 1
-        for (int c0 = 0; c0 < n_eff; c0 += 16) {
-          float v[16];
-          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+          for (int c0 = 0; c0 < n_eff; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int n = n0 + c0 + j;
-            if (C::F8 && n < n_valid) v[j] *= wsc * args.tscale[n];   // undo both FP8 scalings
-            if (n < n_valid) {
-              const size_t orow = (size_t)(KIND == TC_TANGENT_G ? b_row0 + n : n);
-              if (args.at_hi) put<X3>(args.at_hi, args.at_lo, orow * args.ldo + m, sm * v[j]);
-              if (args.zt_hi) put<X3>(args.zt_hi, args.zt_lo, orow * args.ldz + m, v[j]);
-              if (args.yt_hi) put<X3>(args.yt_hi, args.yt_lo, orow * args.ldz + m, cm * v[j]);
+            for (int j = 0; j < 16; ++j) {
+              const int n = n0 + c0 + j;
+              if (C::F8 && n < n_valid) v[j] *= wsc * args.tscale[n];   // undo both FP8 scalings
+              if (n < n_valid) {
+                const size_t orow = (size_t)(KIND == TC_TANGENT_G ? b_row0 + n : n);
+                if (args.at_hi) put<X3>(args.at_hi, args.at_lo, orow * args.ldo + m, sm * v[j]);
+                if (args.zt_hi) put<X3>(args.zt_hi, args.zt_lo, orow * args.ldz + m, v[j]);
+                if (args.yt_hi) put<X3>(args.yt_hi, args.yt_lo, orow * args.ldz + m, cm * v[j]);
+              }
             }
           }
         }
@@ -703,10 +814,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   } else {
     const int q = warp & 3;  // TMEM lanes 32q .. 32q+31 belong to this warp
     const int row = q * 32 + lane;
-    const bool ok = mbar_wait(smem_u32(accf), 0, args.err, 13, abort_flag);
+    const bool ok = epi_all(mbar_wait(smem_u32(accf), 0, args.err, 13, abort_flag));
     tc_fence_after();
     if (threadIdx.x == 64) griddep_launch();
-    if (ok) {
+    if (ok && args.vec_ok) {
+      static_assert(C::STAGES * C::STAGE_BYTES >= staged_epi_bytes<X3>(),
+                    "staged epilogue fits in the pipeline stages");
+      const int m = a_row0 + row;
+      tangent_epilogue_staged<MODE, TC_TANGENT>(args, smem, tmem + ((uint32_t)(q * 32) << 16), row,
+                                                a_row0, n0, n_eff, args.N, 0, (float)args.s1[m],
+                                                args.c[m], 1.f);
+    } else if (ok) {
       const int m = a_row0 + row;
       const float sm = (float)args.s1[m];
       const float cm = args.c[m];
@@ -1626,6 +1744,14 @@ cudaError_t launch_wait_selftest_tc(int* err, long long limit, int code, cudaStr
   return cudaGetLastError();
 }
 
+// The staged tangent epilogue stores 16-byte pieces: every output 16-byte aligned, row strides
+// multiples of 8 elements.
+int vec_outputs(const TcArgs& a) {
+  auto al = [](const void* q) { return ((uintptr_t)q & 15) == 0; };
+  return al(a.at_hi) && al(a.at_lo) && al(a.zt_hi) && al(a.zt_lo) && al(a.yt_hi) && al(a.yt_lo) &&
+         a.ldo % 8 == 0 && a.ldz % 8 == 0;
+}
+
 cudaError_t tc_tangent(const TcPlan& p, const double* s1, const float* c, void* at_hi, void* at_lo,
                        int ldo, void* zt_hi, void* zt_lo, void* yt_hi, void* yt_lo, int ldz,
                        int* err, cudaStream_t st, const float* wscale, const float* tscale) {
@@ -1651,6 +1777,7 @@ cudaError_t tc_tangent(const TcPlan& p, const double* s1, const float* c, void* 
   a.err = err;
   a.wscale = wscale;
   a.tscale = tscale;
+  a.vec_ok = vec_outputs(a);
   if (p.pair) return launch_pair(p, a, 2 * p.ntm * p.ntn, st);
   return launch_any<TC_TANGENT>(p, a, dim3(p.ntn * p.ntm, 1, 1), st);
 }
@@ -1822,6 +1949,7 @@ cudaError_t tc_tangent_grouped(const TcPlan& p, int groups, const int* g_n, cons
   a.g_n = g_n;
   a.g_boff = g_boff;
   a.a_group_rows = p.M;
+  a.vec_ok = vec_outputs(a);
   if (p.persistent) {
     const int grid = std::min(p.sm_count, groups * p.ntm);
     switch (p.bn) {
