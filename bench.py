@@ -35,13 +35,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "hessian_lag_evals_per_s"
 
-# DRAM bytes (read + write) of one tangent-GEMM launch per (M, N, K) shape, form and N tile: mean
-# of two launches of the ncu captures summarised in profiles/k_tc_gemm_tangent_784x4096x4096.md
-# (M = 4096, N = 784, K = 4096); an entry is valid only for the shape and kernel version it was
-# taken on, other shapes report null.
-TANGENT_TRAFFIC = {((4096, 784, 4096), "bf16x3", 208): 81.66e6,
-                   ((4096, 784, 4096), "bf16x3", -208): 81.57e6,
-                   ((4096, 784, 4096), "bf16", 208): 40.20e6}
+# DRAM bytes (read + write) of one tangent-GEMM launch per (M, N, K) shape, form and N tile, from
+# the ncu capture summarised in profiles/k_tc_gemm_tangent_bf16_784x4096x4096.md (M = 4096,
+# N = 784, K = 4096, the kernel with the shared-memory staged epilogue); an entry is valid only for
+# the shape and kernel version it was taken on, other shapes and forms report null.
+TANGENT_TRAFFIC = {((4096, 784, 4096), "bf16", 208): 40.16e6}
 UNIT = "evals/s"
 FP64_NOMINAL_TFLOPS = 1.25   # GB300's nominal dense FP64 rate
 

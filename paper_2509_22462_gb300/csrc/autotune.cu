@@ -126,13 +126,18 @@ extern "C" int nnc_autotune(nnc_net* net, const char* cache_path, int retune) {
         bool okp = true;
         for (size_t i = 0; i < ls.size() && okp; ++i) okp = make_plan(plans[i], ls[i], bn) == NNC_OK;
         if (!okp) continue;
+        // each layer writes its own operand block, as in an evaluation (the first layer's block,
+        // written once at load, must stay intact)
         const double us = time_us(st, 3, [&] {
           for (size_t i = 0; i < ls.size(); ++i) {
             LayerDev& Ly = net->layers[ls[i]];
             const int cur = (ls[i] - 1) % 2;
+            auto zo = [&](void* base) {
+              return (base && Ly.zy_off >= 0) ? (void*)((char*)base + (size_t)Ly.zy_off * 2) : nullptr;
+            };
             tc_tangent(plans[i], Ly.s1, Ly.c_f, net->At[1 - cur][0], net->At[1 - cur][1], Ly.mp,
-                       net->Zt[0], net->Zt[1], net->Yt[0], net->Yt[1], net->K_total, net->dev_err, st,
-                       Ly.w8s, net->tsc);
+                       zo(net->Zt[0]), zo(net->Zt[1]), zo(net->Yt[0]), zo(net->Yt[1]), net->K_total,
+                       net->dev_err, st, Ly.w8s, net->tsc);
           }
         }) / ls.size();
         if (us < best_us) {

@@ -455,6 +455,92 @@ __global__ void __launch_bounds__(256) k_first_tangent_v(const float* __restrict
   }
 }
 
+// BF16 forms, from the FP32 transpose W1T [n][ldt] of the first layer (made once at load): eight
+// consecutive rows m of one tangent n per thread, read as two 16-byte loads and written as one
+// 16-byte vector per output part.  Zdot_1 = W_1 does not depend on x, so its block of the
+// symmetric product's operand is written once at load; per evaluation only Adot_1 = sigma_1' W_1^T
+// (and c_1 W_1^T when Ydot is not deferred) is formed.
+template <bool X3>
+__global__ void __launch_bounds__(256) k_first_tangent_t(const float* __restrict__ W1T, int ldt,
+                                                         int m_pad, int n,
+                                                         const double* __restrict__ s1,
+                                                         const double* __restrict__ c, TanBuf At,
+                                                         int lda, TanBuf Yt, int ldz) {
+  const int per_row = m_pad / 8;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n * per_row) return;
+  const int nn = (int)(t / per_row), mb = 8 * (int)(t % per_row);
+  const float4 w0 = __ldg(reinterpret_cast<const float4*>(W1T + (size_t)nn * ldt + mb));
+  const float4 w1 = __ldg(reinterpret_cast<const float4*>(W1T + (size_t)nn * ldt + mb + 4));
+  const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+  auto pk = [](float v0, float v1, uint32_t& hi, uint32_t& lo) {
+    __nv_bfloat16 h0, l0, h1, l1;
+    split_bf16(v0, h0, l0);
+    split_bf16(v1, h1, l1);
+    hi = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+    lo = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+  };
+  auto st16 = [](void* base, size_t idx, const uint32_t (&v)[4]) {
+    *reinterpret_cast<uint4*>((__nv_bfloat16*)base + idx) = make_uint4(v[0], v[1], v[2], v[3]);
+  };
+  if (At.hi) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 8; e += 2)
+      pk((float)__ldg(s1 + mb + e) * w[e], (float)__ldg(s1 + mb + e + 1) * w[e + 1], h[e / 2],
+         l[e / 2]);
+    st16(At.hi, (size_t)nn * lda + mb, h);
+    if (X3) st16(At.lo, (size_t)nn * lda + mb, l);
+  }
+  if (Yt.hi) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 8; e += 2)
+      pk((float)__ldg(c + mb + e) * w[e], (float)__ldg(c + mb + e + 1) * w[e + 1], h[e / 2],
+         l[e / 2]);
+    st16(Yt.hi, (size_t)nn * ldz + mb, h);
+    if (X3) st16(Yt.lo, (size_t)nn * ldz + mb, l);
+  }
+}
+
+// W^T (FP32): T[j][i] = W[i][j] for i < rows, j < cols, through 32 x 32 shared tiles.
+__global__ void k_transpose_f32(const float* __restrict__ W, int ldw, int rows, int cols,
+                                float* __restrict__ T, int ldt) {
+  __shared__ float tile[32][33];
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = i0 + r, j = j0 + threadIdx.x;
+    tile[r][threadIdx.x] = (i < rows && j < cols) ? W[(size_t)i * ldw + j] : 0.f;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int j = j0 + r, i = i0 + threadIdx.x;
+    if (j < cols && i < rows) T[(size_t)j * ldt + i] = tile[threadIdx.x][r];
+  }
+}
+
+cudaError_t launch_transpose_f32(const float* W, int ldw, int rows, int cols, float* T, int ldt,
+                                 cudaStream_t st) {
+  dim3 g((cols + 31) / 32, (rows + 31) / 32), b(32, 8);
+  k_transpose_f32<<<g, b, 0, st>>>(W, ldw, rows, cols, T, ldt);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_first_tangent_t(bool x3, const float* W1T, int ldt, int m_pad, int n,
+                                   const double* s1, const double* c, TanBuf At, int lda,
+                                   TanBuf Yt, int ldz, cudaStream_t st) {
+  if (m_pad % 8 || ldt % 4 || lda % 8 || ldz % 8 || ((uintptr_t)W1T & 15)) return cudaErrorInvalidValue;
+  const long long threads = (long long)n * (m_pad / 8);
+  const int blocks = (int)((threads + 255) / 256);
+  if (x3)
+    k_first_tangent_t<true><<<blocks, 256, 0, st>>>(W1T, ldt, m_pad, n, s1, c, At, lda, Yt, ldz);
+  else
+    k_first_tangent_t<false><<<blocks, 256, 0, st>>>(W1T, ldt, m_pad, n, s1, c, At, lda, Yt, ldz);
+  note_launch();
+  return cudaGetLastError();
+}
+
 // Ydot = c * Zdot over the columns [k0, k1) of the n x ldz operand blocks of the symmetric
 // product, c[k] per column (the curvature weight c_l of the layer owning column k):
 // Y = split(c * (Z_hi + Z_lo)) in the split form, bf16(c * Z) otherwise.  Eight columns per
@@ -588,35 +674,46 @@ __global__ void k_h_finish(const TP* __restrict__ Hp, int splits, int n, int ldp
   }
 }
 
-// FP32 partials (tensor-core forms): one block per lower 32 x 32 tile (bi >= bj) sums the splits
-// in FP32 (GB300's FP64 rate is a small fraction of FP32's; the partials carry FP32 accuracy
-// anyway), then writes the tile and its mirror, each coalesced.  Only R >= C entries of the
-// partials are read (the upper triangle of a diagonal tile is not written by the product).
-__global__ void __launch_bounds__(1024) k_h_finish_f32(const float* __restrict__ Hp, int splits,
-                                                       int n, int ldp, double* __restrict__ H) {
+// FP32 partials (tensor-core forms): one block of 32 x 8 threads per lower 32 x 32 tile (bi >= bj)
+// sums the splits in FP32 (GB300's FP64 rate is a small fraction of FP32's; the partials carry
+// FP32 accuracy anyway), four rows per thread with every split's load issued before the adds,
+// then writes the tile and its mirror, each coalesced.  Only R >= C entries of the partials are
+// read (the upper triangle of a diagonal tile is not written by the product).
+__global__ void __launch_bounds__(256) k_h_finish_f32(const float* __restrict__ Hp, int splits,
+                                                      int n, int ldp, double* __restrict__ H) {
   __shared__ float t[32][33];
   int b = blockIdx.x, bi = 0;
   while (b > bi) b -= ++bi;          // lower-tile index -> (bi, bj), bj = b <= bi
   const int bj = b;
-  const int i0 = bi * 32, j0 = bj * 32, rr = threadIdx.y, x = threadIdx.x;
-  {
-    const int r = i0 + rr, c = j0 + x;
-    float v = 0.f;
-    if (r < n && c < n) {
-      const int R = r >= c ? r : c, C = r >= c ? c : r;
-      const float* p = Hp + (size_t)R * ldp + C;
-      const size_t plane = (size_t)n * ldp;
-#pragma unroll 8
-      for (int s = 0; s < splits; ++s) v += __ldg(p + s * plane);
-    }
-    t[rr][x] = v;
+  const int i0 = bi * 32, j0 = bj * 32, x = threadIdx.x, y = threadIdx.y;
+  const size_t plane = (size_t)n * ldp;
+  const float* p[4];
+  bool in[4];
+  float v[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int r = i0 + y + 8 * k, c = j0 + x;
+    in[k] = r < n && c < n;
+    const int R = r >= c ? r : c, C = r >= c ? c : r;
+    p[k] = Hp + (size_t)R * ldp + C;
+    v[k] = 0.f;
   }
+  for (int s = 0; s < splits; ++s)
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (in[k]) v[k] += __ldg(p[k] + s * plane);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) t[y + 8 * k][x] = v[k];
   __syncthreads();
-  const int i = i0 + rr, j = j0 + x;
-  if (i < n && j < n) H[(size_t)i * n + j] = (double)t[rr][x];
-  if (bi != bj) {
-    const int i2 = j0 + rr, j2 = i0 + x;   // mirror tile H[j0..][i0..]
-    if (i2 < n && j2 < n) H[(size_t)i2 * n + j2] = (double)t[x][rr];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int rr = y + 8 * k;
+    const int i = i0 + rr, j = j0 + x;
+    if (i < n && j < n) H[(size_t)i * n + j] = (double)t[rr][x];
+    if (bi != bj) {
+      const int i2 = j0 + rr, j2 = i0 + x;   // mirror tile H[j0..][i0..]
+      if (i2 < n && j2 < n) H[(size_t)i2 * n + j2] = (double)t[x][rr];
+    }
   }
 }
 
@@ -624,7 +721,7 @@ cudaError_t launch_h_finish(bool part_f32, const void* Hp, int splits, int n, in
                             cudaStream_t st) {
   const int T = (n + 31) / 32;
   if (part_f32) {
-    k_h_finish_f32<<<T * (T + 1) / 2, dim3(32, 32), 0, st>>>((const float*)Hp, splits, n, ldp, H);
+    k_h_finish_f32<<<T * (T + 1) / 2, dim3(32, 8), 0, st>>>((const float*)Hp, splits, n, ldp, H);
   } else {
     dim3 grid(T, T), block(32, 8);
     k_h_finish<double><<<grid, block, 0, st>>>((const double*)Hp, splits, n, ldp, H);

@@ -55,6 +55,15 @@ cudaError_t launch_scale_y(bool x3, const void* Zh, const void* Zl, void* Yh, vo
 cudaError_t launch_first_tangent(Elem e, const void* W1, int ldw, int m_pad, int n,
                                  const double* s1, const double* c, TanBuf At, int lda, TanBuf Zt,
                                  TanBuf Yt, int ldz, cudaStream_t st);
+// The same for the BF16 forms from the FP32 transpose W1T [n][ldt] of W_1 (launch_transpose_f32):
+// At[n][m] = s1[m] W1T[n][m] and, if Yt.hi, Yt[n][m] = c[m] W1T[n][m]; Zdot_1 is written once at
+// load by launch_first_tangent with At and Yt empty.  m_pad, lda, ldz multiples of 8.
+cudaError_t launch_first_tangent_t(bool x3, const float* W1T, int ldt, int m_pad, int n,
+                                   const double* s1, const double* c, TanBuf At, int lda,
+                                   TanBuf Yt, int ldz, cudaStream_t st);
+// T[j][i] = W[i][j] (FP32) for i < rows, j < cols.
+cudaError_t launch_transpose_f32(const float* W, int ldw, int rows, int cols, float* T, int ldt,
+                                 cudaStream_t st);
 // H[i][j] = sum_s Hp[s][max(i,j)][min(i,j)]  (exactly symmetric); Hp is double or float.
 cudaError_t launch_h_finish(bool part_f32, const void* Hp, int splits, int n, int ldp, double* H,
                             cudaStream_t st);

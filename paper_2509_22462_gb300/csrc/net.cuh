@@ -77,6 +77,7 @@ struct nnc_net {
   void* Zt[2] = {nullptr, nullptr};  // [hi, lo]: Zdot_l^T of all curved layers, n x K_total
   void* Yt[2] = {nullptr, nullptr};  // [hi, lo]: (c_l * Zdot_l)^T, n x K_total
   int K_total = 0;                   // sum of mp_l over layers with sigma'' != 0 (+ 128: softmax)
+  float* W1T = nullptr;              // tensor-core forms: FP32 W_1^T [n_in][mp_1] for Adot_1
   // persistent chain of tangent GEMMs (BF16 and split-BF16x3 forms; k_tc_chain): plans of layers
   // 1 .. chain_nl with one N tile, the chain's arrival counters, and whether evaluations use it
   // (chosen by the autotuner or nnc_tune_set)

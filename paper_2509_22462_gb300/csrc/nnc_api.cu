@@ -297,9 +297,13 @@ int run_hessian(nnc_net* net, const double* lam, double* H, cudaStream_t st, boo
     TanBuf Zt{zoff(net->Zt[0], L1.zy_off), zoff(net->Zt[1], L1.zy_off)};
     TanBuf Yt{deferred ? nullptr : zoff(net->Yt[0], L1.zy_off),
               deferred ? nullptr : zoff(net->Yt[1], L1.zy_off)};
-    CK(launch_first_tangent(e, prec == NNC_FP64 ? (const void*)L1.W64 : (const void*)L1.W32, L1.kp,
-                            L1.mp, n, L1.s1, L1.c, net->L > 1 ? At0 : TanBuf{}, L1.mp, Zt, Yt,
-                            net->K_total, st));
+    if (net->W1T)   // Zdot_1 was written at load
+      CK(launch_first_tangent_t(e == Elem::BF16X3, net->W1T, L1.mp, L1.mp, n, L1.s1, L1.c,
+                                net->L > 1 ? At0 : TanBuf{}, L1.mp, Yt, net->K_total, st));
+    else
+      CK(launch_first_tangent(e, prec == NNC_FP64 ? (const void*)L1.W64 : (const void*)L1.W32,
+                              L1.kp, L1.mp, n, L1.s1, L1.c, net->L > 1 ? At0 : TanBuf{}, L1.mp, Zt,
+                              Yt, net->K_total, st));
   }
   if (tc && net->use_chain && net->chain_nl > 0) {
     // every tangent GEMM in one persistent launch; its counters are cleared before the first
@@ -764,6 +768,19 @@ static int load_impl(nnc_net* net, int n_layers, const int* widths, const int* a
   if (prec == NNC_FP8) {
     AL(net->A8, tan_elems);
     AL(net->tsc, n);
+  }
+  if (tc) {
+    // Zdot_1 = W_1 does not depend on x: its block of the symmetric product's operand is written
+    // here once, and each evaluation forms Adot_1 = sigma_1' W_1^T from an FP32 copy of W_1^T
+    LayerDev& L1 = net->layers[0];
+    AL(net->W1T, (size_t)n * L1.mp);
+    CK(launch_transpose_f32(L1.W32, L1.kp, L1.mp, n, net->W1T, L1.mp, net->stream));
+    if (L1.zy_off >= 0) {
+      const size_t off = (size_t)L1.zy_off * es;
+      TanBuf Z1{(char*)net->Zt[0] + off, net->Zt[1] ? (char*)net->Zt[1] + off : nullptr};
+      CK(launch_first_tangent(tan_elem(prec), L1.W32, L1.kp, L1.mp, n, L1.s1, L1.c, TanBuf{}, L1.mp,
+                              Z1, TanBuf{}, net->K_total, net->stream));
+    }
   }
   // split-K partial sums of H
   if (tc) {
