@@ -219,6 +219,21 @@ int check_dev_err(nnc_batch* b) {
   return NNC_OK;
 }
 
+// Host calls: queue the error word's copy behind the outputs into its pinned slot (the last
+// element of h_stage), wait for the device once, then check it.
+int sync_check(nnc_batch* b, cudaStream_t st) {
+  int* herr = reinterpret_cast<int*>(b->h_stage + b->n_sum + 2 * (size_t)b->K * b->n_out);
+  BCK(cudaMemcpyAsync(herr, b->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  BCK(cudaStreamSynchronize(st));
+  if (*herr) {
+    const int e = *herr;
+    int z = 0;
+    cudaMemcpy(b->dev_err, &z, sizeof(int), cudaMemcpyHostToDevice);
+    return bfail(NNC_ERR_TIMEOUT, "a bounded device-side wait ran out (code " + std::to_string(e) + ")");
+  }
+  return NNC_OK;
+}
+
 int build(nnc_batch* b, nnc_net* const* nets, int K) {
   b->K = K;
   nnc_net* n0 = nets[0];
@@ -359,7 +374,7 @@ int build(nnc_batch* b, nnc_net* const* nets, int K) {
   BAL(b->J_out, (size_t)b->n_sum * b->n_out);
   BAL(b->g_out, b->n_sum);
   BAL(b->H_out, b->h_sum);
-  BCK(cudaMallocHost(&b->h_stage, sizeof(double) * (b->n_sum + 2 * (size_t)K * b->n_out)));
+  BCK(cudaMallocHost(&b->h_stage, sizeof(double) * (b->n_sum + 2 * (size_t)K * b->n_out + 1)));
   BCK(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
   BCK(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));
   BCK(cudaStreamSynchronize(b->stream));
@@ -666,8 +681,7 @@ int nnc_batch_eval(nnc_batch* b, const double* x, const double* lambda, double* 
   if (J) BCK(cudaMemcpyAsync(J, b->J_out, sizeof(double) * b->n_sum * b->n_out, cudaMemcpyDeviceToHost, st));
   if (H) BCK(cudaMemcpyAsync(H, b->H_out, sizeof(double) * b->h_sum, cudaMemcpyDeviceToHost, st));
   if (grad) BCK(cudaMemcpyAsync(grad, b->g_out, sizeof(double) * b->n_sum, cudaMemcpyDeviceToHost, st));
-  BCK(cudaStreamSynchronize(st));
-  return check_dev_err(b);
+  return sync_check(b, st);
 }
 
 int nnc_batch_eval_kkt(nnc_batch* b, const double* x, const double* y, const double* lambda, double* r,
@@ -698,8 +712,7 @@ int nnc_batch_eval_kkt(nnc_batch* b, const double* x, const double* y, const dou
   if (J) BCK(cudaMemcpyAsync(J, b->J_out, sizeof(double) * b->n_sum * b->n_out, cudaMemcpyDeviceToHost, st));
   if (H) BCK(cudaMemcpyAsync(H, b->H_out, sizeof(double) * b->h_sum, cudaMemcpyDeviceToHost, st));
   if (grad) BCK(cudaMemcpyAsync(grad, b->g_out, sizeof(double) * b->n_sum, cudaMemcpyDeviceToHost, st));
-  BCK(cudaStreamSynchronize(st));
-  return check_dev_err(b);
+  return sync_check(b, st);
 }
 
 int nnc_batch_residual(nnc_batch* b, const double* x, const double* y, double* r) {
@@ -714,8 +727,7 @@ int nnc_batch_residual(nnc_batch* b, const double* x, const double* y, double* r
   int rc = batch_residual(b, b->x_in, b->y_in, b->r_out, st);
   if (rc) return rc;
   BCK(cudaMemcpyAsync(r, b->r_out, sizeof(double) * nl, cudaMemcpyDeviceToHost, st));
-  BCK(cudaStreamSynchronize(st));
-  return NNC_OK;
+  return sync_check(b, st);   // the value pass's bounded waits too
 }
 
 }  // extern "C"

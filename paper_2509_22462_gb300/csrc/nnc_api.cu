@@ -83,16 +83,23 @@ int check_finite(const double* v, int n, const char* what) {
   return NNC_OK;
 }
 
-int check_dev_err(nnc_net* net) {
-  int e = 0;
-  CK(cudaMemcpyAsync(&e, net->dev_err, sizeof(int), cudaMemcpyDeviceToHost, net->stream));
-  CK(cudaStreamSynchronize(net->stream));
+// The error word e of the bounded waits, already read back: clear it and report a timeout.
+int dev_err_status(nnc_net* net, int e) {
   if (e != 0) {
     int z = 0;
     cudaMemcpy(net->dev_err, &z, sizeof(int), cudaMemcpyHostToDevice);
     return fail(NNC_ERR_TIMEOUT, "a bounded device-side wait ran out (code " + std::to_string(e) + ")");
   }
   return NNC_OK;
+}
+
+// Host calls: queue the error word's copy behind the outputs into its pinned slot (the last
+// element of h_stage), wait for the device once, then check it.
+int sync_check(nnc_net* net, cudaStream_t st) {
+  int* herr = reinterpret_cast<int*>(net->h_stage + net->h_stage_elems - 1);
+  CK(cudaMemcpyAsync(herr, net->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return dev_err_status(net, *herr);
 }
 
 cudaStream_t pick(nnc_net* net, void* st) { return st ? (cudaStream_t)st : net->stream; }
@@ -488,8 +495,7 @@ int host_call(nnc_net* net, const double* x, const double* lam, double* y, doubl
   if (H) CK(cudaMemcpyAsync(H, net->Hdev, sizeof(double) * net->n_in * net->n_in,
                             cudaMemcpyDeviceToHost, st));
   if (g) CK(cudaMemcpyAsync(g, net->gdev, sizeof(double) * net->n_in, cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  return check_dev_err(net);
+  return sync_check(net, st);   // the error word of the bounded waits comes back with the outputs
 }
 
 }  // namespace
@@ -876,8 +882,8 @@ static int load_impl(nnc_net* net, int n_layers, const int* widths, const int* a
     AL(hp, (size_t)splits * n * n);
     net->Hp = hp;
   }
-  // pinned staging of the host calls: x [n_in_pad] | lambda [n_out] | y [n_out]
-  net->h_stage_elems = (size_t)net->n_in_pad + 2 * (size_t)net->n_out;
+  // pinned staging of the host calls: x [n_in_pad] | lambda [n_out] | y [n_out] | error word
+  net->h_stage_elems = (size_t)net->n_in_pad + 2 * (size_t)net->n_out + 1;
   CK(cudaMallocHost(&net->h_stage, sizeof(double) * net->h_stage_elems));
   CK(cudaStreamSynchronize(net->stream));
   return NNC_OK;
@@ -982,8 +988,7 @@ int nnc_residual(nnc_net* net, const double* x, const double* y, double* rr) {
   r = nnc_residual_dev(net, net->xin, net->yres, net->rdev, st);
   if (r) return r;
   CK(cudaMemcpyAsync(rr, net->rdev, sizeof(double) * net->n_out, cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  return NNC_OK;
+  return sync_check(net, st);   // the value pass's bounded waits too
 }
 
 int nnc_jacobian(nnc_net* net, const double* x, double* J) {
