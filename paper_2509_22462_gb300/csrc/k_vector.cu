@@ -455,24 +455,41 @@ __global__ void __launch_bounds__(256) k_first_tangent_v(const float* __restrict
   }
 }
 
-// BF16 forms, from the FP32 transpose W1T [n][ldt] of the first layer (made once at load): eight
-// consecutive rows m of one tangent n per thread, read as two 16-byte loads and written as one
-// 16-byte vector per output part.  Zdot_1 = W_1 does not depend on x, so its block of the
-// symmetric product's operand is written once at load; per evaluation only Adot_1 = sigma_1' W_1^T
-// (and c_1 W_1^T when Ydot is not deferred) is formed.
+// BF16 forms, from the FP32 transpose W1T [n][ldt] of the first layer (made once at load): a
+// thread takes eight consecutive rows m and kFtN tangents n (blockIdx.y), reads sigma' and c of its
+// rows once for all of them, and per tangent reads W1T as two 16-byte loads and writes one 16-byte
+// vector per output part.  Zdot_1 = W_1 does not depend on x, so its block of the symmetric
+// product's operand is written once at load; per evaluation only Adot_1 = sigma_1' W_1^T (and
+// c_1 W_1^T when Ydot is not deferred) is formed.
+constexpr int kFtN = 4;
 template <bool X3>
 __global__ void __launch_bounds__(256) k_first_tangent_t(const float* __restrict__ W1T, int ldt,
                                                          int m_pad, int n,
                                                          const double* __restrict__ s1,
                                                          const double* __restrict__ c, TanBuf At,
                                                          int lda, TanBuf Yt, int ldz) {
-  const int per_row = m_pad / 8;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)n * per_row) return;
-  const int nn = (int)(t / per_row), mb = 8 * (int)(t % per_row);
-  const float4 w0 = __ldg(reinterpret_cast<const float4*>(W1T + (size_t)nn * ldt + mb));
-  const float4 w1 = __ldg(reinterpret_cast<const float4*>(W1T + (size_t)nn * ldt + mb + 4));
-  const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+  const int mb = 8 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (mb >= m_pad) return;
+  const int n0 = blockIdx.y * kFtN;
+  float sv[8], cv[8];
+#pragma unroll
+  for (int e = 0; e < 8; e += 2) {
+    const double2 sp = __ldg(reinterpret_cast<const double2*>(s1 + mb + e));
+    sv[e] = (float)sp.x;
+    sv[e + 1] = (float)sp.y;
+    if (Yt.hi) {
+      const double2 cp = __ldg(reinterpret_cast<const double2*>(c + mb + e));
+      cv[e] = (float)cp.x;
+      cv[e + 1] = (float)cp.y;
+    }
+  }
+  float4 w0[kFtN], w1[kFtN];
+#pragma unroll
+  for (int j = 0; j < kFtN; ++j)
+    if (n0 + j < n) {
+      w0[j] = __ldg(reinterpret_cast<const float4*>(W1T + (size_t)(n0 + j) * ldt + mb));
+      w1[j] = __ldg(reinterpret_cast<const float4*>(W1T + (size_t)(n0 + j) * ldt + mb + 4));
+    }
   auto pk = [](float v0, float v1, uint32_t& hi, uint32_t& lo) {
     __nv_bfloat16 h0, l0, h1, l1;
     split_bf16(v0, h0, l0);
@@ -483,23 +500,25 @@ __global__ void __launch_bounds__(256) k_first_tangent_t(const float* __restrict
   auto st16 = [](void* base, size_t idx, const uint32_t (&v)[4]) {
     *reinterpret_cast<uint4*>((__nv_bfloat16*)base + idx) = make_uint4(v[0], v[1], v[2], v[3]);
   };
-  if (At.hi) {
-    uint32_t h[4], l[4];
 #pragma unroll
-    for (int e = 0; e < 8; e += 2)
-      pk((float)__ldg(s1 + mb + e) * w[e], (float)__ldg(s1 + mb + e + 1) * w[e + 1], h[e / 2],
-         l[e / 2]);
-    st16(At.hi, (size_t)nn * lda + mb, h);
-    if (X3) st16(At.lo, (size_t)nn * lda + mb, l);
-  }
-  if (Yt.hi) {
-    uint32_t h[4], l[4];
+  for (int j = 0; j < kFtN; ++j) {
+    const int nn = n0 + j;
+    if (nn >= n) break;
+    const float w[8] = {w0[j].x, w0[j].y, w0[j].z, w0[j].w, w1[j].x, w1[j].y, w1[j].z, w1[j].w};
+    if (At.hi) {
+      uint32_t h[4], l[4];
 #pragma unroll
-    for (int e = 0; e < 8; e += 2)
-      pk((float)__ldg(c + mb + e) * w[e], (float)__ldg(c + mb + e + 1) * w[e + 1], h[e / 2],
-         l[e / 2]);
-    st16(Yt.hi, (size_t)nn * ldz + mb, h);
-    if (X3) st16(Yt.lo, (size_t)nn * ldz + mb, l);
+      for (int e = 0; e < 8; e += 2) pk(sv[e] * w[e], sv[e + 1] * w[e + 1], h[e / 2], l[e / 2]);
+      st16(At.hi, (size_t)nn * lda + mb, h);
+      if (X3) st16(At.lo, (size_t)nn * lda + mb, l);
+    }
+    if (Yt.hi) {
+      uint32_t h[4], l[4];
+#pragma unroll
+      for (int e = 0; e < 8; e += 2) pk(cv[e] * w[e], cv[e + 1] * w[e + 1], h[e / 2], l[e / 2]);
+      st16(Yt.hi, (size_t)nn * ldz + mb, h);
+      if (X3) st16(Yt.lo, (size_t)nn * ldz + mb, l);
+    }
   }
 }
 
@@ -531,12 +550,11 @@ cudaError_t launch_first_tangent_t(bool x3, const float* W1T, int ldt, int m_pad
                                    const double* s1, const double* c, TanBuf At, int lda,
                                    TanBuf Yt, int ldz, cudaStream_t st) {
   if (m_pad % 8 || ldt % 4 || lda % 8 || ldz % 8 || ((uintptr_t)W1T & 15)) return cudaErrorInvalidValue;
-  const long long threads = (long long)n * (m_pad / 8);
-  const int blocks = (int)((threads + 255) / 256);
+  const dim3 grid((m_pad / 8 + 255) / 256, (n + kFtN - 1) / kFtN);
   if (x3)
-    k_first_tangent_t<true><<<blocks, 256, 0, st>>>(W1T, ldt, m_pad, n, s1, c, At, lda, Yt, ldz);
+    k_first_tangent_t<true><<<grid, 256, 0, st>>>(W1T, ldt, m_pad, n, s1, c, At, lda, Yt, ldz);
   else
-    k_first_tangent_t<false><<<blocks, 256, 0, st>>>(W1T, ldt, m_pad, n, s1, c, At, lda, Yt, ldz);
+    k_first_tangent_t<false><<<grid, 256, 0, st>>>(W1T, ldt, m_pad, n, s1, c, At, lda, Yt, ldz);
   note_launch();
   return cudaGetLastError();
 }
