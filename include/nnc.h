@@ -257,6 +257,11 @@ int nnc_layer_weights(const nnc_net* net, int layer, double* W, double* b, int* 
  * of the tensor-core kernels (which = 1, abort flag included).  The wait must give up: returns
  * NNC_ERR_TIMEOUT with the recorded wait code in *code (may be NULL), and the device stays usable. */
 int nnc_selftest_bounded_wait(int which, long long cycles, int* code);
+/* The same wait queued on the net's stream, recording its code in the net's own error word, as a
+ * timed-out wait inside an evaluation would (no fault, nothing synchronised).  The net's next host
+ * call (nnc_eval, nnc_eval_kkt, nnc_residual, ...) then returns NNC_ERR_TIMEOUT and clears the
+ * word, and the call after it runs normally.  which and cycles as above; NNC_ERR_ARG otherwise. */
+int nnc_selftest_net_wait(nnc_net* net, int which, long long cycles);
 /* Number of kernel launches this library queued since load (all nets, this process). */
 long long nnc_launch_count(void);
 

@@ -575,6 +575,17 @@ int nnc_selftest_bounded_wait(int which, long long cycles, int* code) {
   return NNC_OK;
 }
 
+int nnc_selftest_net_wait(nnc_net* net, int which, long long cycles) {
+  int r = check_net(net);
+  if (r) return r;
+  if (which < 0 || which > 1 || cycles < 1 || cycles > 4000000000LL)
+    return fail(NNC_ERR_ARG, "which must be 0 or 1, cycles in [1, 4e9]");
+  CK(cudaSetDevice(net->device));
+  CK(which == 0 ? launch_wait_selftest_stream(net->dev_err, cycles, 91, net->stream)
+                : launch_wait_selftest_tc(net->dev_err, cycles, 93, net->stream));
+  return NNC_OK;
+}
+
 int nnc_layer_weights(const nnc_net* net, int layer, double* W, double* b, int* act, int* rows,
                       int* cols) {
   if (!net) return fail(NNC_ERR_ARG, "net is NULL");

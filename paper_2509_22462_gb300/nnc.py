@@ -26,7 +26,7 @@ EXPORTS = ["nnc_load_weights", "nnc_eval", "nnc_residual", "nnc_jacobian", "nnc_
            "nnc_hessian_lag_dev", "nnc_eval_all_dev", "nnc_eval_kkt_dev", "nnc_eval_kkt", "nnc_free", "nnc_last_error",
            "nnc_net_info", "nnc_launch_count", "nnc_profile", "nnc_profile_read",
            "nnc_ipm_default_options", "nnc_ipm_adversarial", "nnc_ipm_adversarial_l1",
-           "nnc_ipm_adversarial_l1_fullspace", "nnc_layer_weights", "nnc_selftest_bounded_wait",
+           "nnc_ipm_adversarial_l1_fullspace", "nnc_layer_weights", "nnc_selftest_bounded_wait", "nnc_selftest_net_wait",
            "nnc_kkt_solve", "nnc_stage_kkt_solve",
            "nnc_residual_noalloc", "nnc_batch_create", "nnc_batch_free", "nnc_batch_info",
            "nnc_batch_set_bias", "nnc_batch_use_graph", "nnc_batch_tune_set", "nnc_batch_tuning", "nnc_batch_autotune", "nnc_batch_eval_dev", "nnc_batch_residual_dev", "nnc_batch_eval_kkt_dev",
@@ -171,6 +171,7 @@ def load_library(path: str = LIB_PATH):
     lib.nnc_layer_weights.argtypes = [_P, ctypes.c_int, _DP, _DP, ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.nnc_selftest_bounded_wait.argtypes = [ctypes.c_int, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int)]
+    lib.nnc_selftest_net_wait.argtypes = [_P, ctypes.c_int, ctypes.c_longlong]
     lib.nnc_profile_read.argtypes = [_P, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
     for name in EXPORTS:
@@ -308,6 +309,10 @@ class Net:
     def tune_set(self, tangent_bn=0, syrk_splits=0):
         """nnc_tune_set: pin the tangent N tile and / or the symmetric-product splits."""
         _check(_lib.nnc_tune_set(self._h, int(tangent_bn), int(syrk_splits)))
+
+    def selftest_wait(self, which, cycles):
+        """nnc_selftest_net_wait: queue a bounded wait that runs out into this net's error word."""
+        _check(_lib.nnc_selftest_net_wait(self._h, int(which), int(cycles)))
 
     def tuning(self, layer):
         bn, sp = ctypes.c_int(), ctypes.c_int()
