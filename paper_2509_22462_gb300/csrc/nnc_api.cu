@@ -145,7 +145,9 @@ struct ProfScope {
 // FP64 form: FP64 GEMV layers.  Other forms: one double-float streaming pass (about 48
 // significant bits) whose sigma, sigma' and sigma'' feed the derivative sweeps; expects net->x and
 // its pairs net->x2 (launch_copy_pad).
-int run_forward(nnc_net* net, bool fp64, cudaStream_t st) {
+// Non-FP64 forms may run the layers [l0, l1) only (the output layer then goes to another stream).
+int run_forward(nnc_net* net, bool fp64, cudaStream_t st, int l0 = 0, int l1 = -1) {
+  if (l1 < 0) l1 = net->L;
   if (fp64) {
     const double* a_in = net->x;
     for (auto& Ly : net->layers) {
@@ -157,18 +159,19 @@ int run_forward(nnc_net* net, bool fp64, cudaStream_t st) {
     if (net->softmax) CK(launch_softmax_head(net->n_out, net->layers.back().a, st));
     return NNC_OK;
   }
-  const void* a_in2 = net->x2;
+  const void* a_in2 = l0 == 0 ? net->x2 : net->layers[l0 - 1].a2;
   {
-    ProfScope span(net, PK_FWD_SPAN, st);   // the whole value pass, counted as its layers
-    if (span.on) net->ev_weight.back() = (int)net->layers.size();
-    for (auto& Ly : net->layers) {
+    ProfScope span(net, PK_FWD_SPAN, st);   // the value pass's layers, counted as such
+    if (span.on) net->ev_weight.back() = l1 - l0;
+    for (int l = l0; l < l1; ++l) {
+      LayerDev& Ly = net->layers[l];
       PROF(PK_FWD);
       CK(launch_gemv_stream_df(Ly.W2, Ly.kp, Ly.m, Ly.b, a_in2, Ly.act, Ly.a, Ly.a2, Ly.s1, Ly.s2,
                                net->dev_err, net->sm_count, st));
       a_in2 = Ly.a2;
     }
   }
-  if (net->softmax) CK(launch_softmax_head(net->n_out, net->layers.back().a, st));
+  if (net->softmax && l1 == net->L) CK(launch_softmax_head(net->n_out, net->layers.back().a, st));
   return NNC_OK;
 }
 
@@ -422,19 +425,32 @@ int eval_all(nnc_net* net, const double* x, const double* lam, double* y, double
              double* g, cudaStream_t st, const double* yv = nullptr, double* rr = nullptr) {
   CK(launch_copy_pad(x, net->x, net->x2, net->n_in, net->n_in_pad, st));
   const bool fp64 = net->prec == NNC_FP64;
-  int r = run_forward(net, fp64, st);
-  if (r != NNC_OK) return r;
-  if (y)
-    CK(cudaMemcpyAsync(y, net->layers.back().a, sizeof(double) * net->n_out,
-                       cudaMemcpyDeviceToDevice, st));
-  if (rr) CK(launch_sub(yv, net->layers.back().a, rr, net->n_out, st));
-  const bool need_lam = (H != nullptr) || (g != nullptr);
   // tensor-core forms: the reverse sweep (streaming, or on the tensor cores for more than 15
   // outputs) on the side stream, next to the tangent chain
   const bool fork = H && is_tc(net->prec) && (net->rev_stream || net->tc_rev) && net->side_stream;
+  // With a linear output layer the tangent chain reads nothing of it, so that layer, y and the
+  // residual go to the side stream ahead of the reverse sweep and the chain starts after layer
+  // L - 1.  (Not while the value pass is timed as one span, nor with the persistent chain.)
+  const bool tail = fork && !fp64 && net->L > 1 && net->layers.back().act == NNC_IDENTITY &&
+                    !net->use_chain && !(net->prof_mask & (1u << PK_FWD_SPAN));
+  int r = run_forward(net, fp64, st, 0, tail ? net->L - 1 : net->L);
+  if (r != NNC_OK) return r;
+  cudaStream_t vs = st;   // the stream of the output layer and of what reads its values
   if (fork) {
     CK(cudaEventRecord(net->ev_fork, st));
     CK(cudaStreamWaitEvent(net->side_stream, net->ev_fork, 0));
+    if (tail) {
+      vs = net->side_stream;
+      r = run_forward(net, fp64, vs, net->L - 1, net->L);
+      if (r != NNC_OK) return r;
+    }
+  }
+  if (y)
+    CK(cudaMemcpyAsync(y, net->layers.back().a, sizeof(double) * net->n_out,
+                       cudaMemcpyDeviceToDevice, vs));
+  if (rr) CK(launch_sub(yv, net->layers.back().a, rr, net->n_out, vs));
+  const bool need_lam = (H != nullptr) || (g != nullptr);
+  if (fork) {
     r = run_reverse(net, fp64, J ? net->n_out : 0, true, lam, J, g, net->side_stream);
     if (r != NNC_OK) return r;
     CK(cudaEventRecord(net->ev_join, net->side_stream));
