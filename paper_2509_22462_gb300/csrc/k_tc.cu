@@ -10,7 +10,9 @@
 //                tcgen05.commit frees a stage when its MMAs have read it, and signals the
 //                epilogue after the last one.
 //   warps 2..5 : epilogue. Each warp reads its 32 TMEM lanes (= 32 rows of the tile) with
-//                tcgen05.ld and writes the fused outputs.
+//                tcgen05.ld and writes the fused outputs; the tangent outputs go through shared
+//                memory 16 columns at a time and leave as whole 256-byte row segments
+//                (tangent_epilogue_staged).
 // Every mbarrier wait is bounded: on expiry the CTA records an error code in *err, stops its
 // loops, waits (again bounded) for its own copies and MMAs in flight, frees its tensor memory
 // and returns.
