@@ -105,7 +105,8 @@ def load_library(path: str = LIB_PATH):
     lib.nnc_hessian_lag_dev.argtypes = [_P, _P, _P, _P, _P, _P]
     lib.nnc_eval_all_dev.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P]
     lib.nnc_eval_kkt_dev.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _P]
-    lib.nnc_eval_kkt.argtypes = [_P, _DP, _DP, _DP, _DP, _DP, _DP, _DP]
+    # host arrays passed as raw addresses (the per-call IPM path; data_as costs ~3 us a pointer)
+    lib.nnc_eval_kkt.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P]
     lib.nnc_free.argtypes = [_P]
     lib.nnc_free.restype = None
     lib.nnc_ipm_default_options.restype = None
@@ -130,7 +131,7 @@ def load_library(path: str = LIB_PATH):
     lib.nnc_batch_eval_kkt_dev.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _P]
     lib.nnc_batch_eval.argtypes = [_P, _DP, _DP, _DP, _DP, _DP, _DP]
     lib.nnc_batch_residual.argtypes = [_P, _DP, _DP, _DP]
-    lib.nnc_batch_eval_kkt.argtypes = [_P, _DP, _DP, _DP, _DP, _DP, _DP, _DP]
+    lib.nnc_batch_eval_kkt.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P]
     lib.nnc_ipm_scopf.argtypes = [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                   ctypes.POINTER(ctypes.c_int), _DP, ctypes.c_double, _DP,
                                   ctypes.POINTER(IpmOptions), _DP, _DP, ctypes.POINTER(IpmResult)]
@@ -193,6 +194,11 @@ def _dp(a):
 
 def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ad(a):
+    """Address of a C-contiguous numpy array, for c_void_p arguments."""
+    return a.ctypes.data
 
 
 def launch_count() -> int:
@@ -299,7 +305,7 @@ class Net:
             if a.dtype != np.float64 or a.shape != shape or not a.flags.c_contiguous:
                 raise ValueError("eval_kkt: out arrays must be C-contiguous float64 of shapes "
                                  "(n_out,), (n_out, n_in), (n_in, n_in), (n_in,)")
-        _check(_lib.nnc_eval_kkt(self._h, _dp(x), _dp(y), _dp(lam), _dp(r), _dp(J), _dp(H), _dp(g)))
+        _check(_lib.nnc_eval_kkt(self._h, _ad(x), _ad(y), _ad(lam), _ad(r), _ad(J), _ad(H), _ad(g)))
         return r, J, H, g
 
     def autotune(self, cache_path=None, retune=False):
@@ -600,7 +606,7 @@ class Batch:
             if a.dtype != np.float64 or a.size != k or not a.flags.c_contiguous:
                 raise ValueError("eval_kkt: out arrays must be C-contiguous float64 of the concatenated sizes")
         r, J, H, g = out
-        _check(_lib.nnc_batch_eval_kkt(self._h, _dp(x), _dp(y), _dp(lam), _dp(r), _dp(J), _dp(H), _dp(g)))
+        _check(_lib.nnc_batch_eval_kkt(self._h, _ad(x), _ad(y), _ad(lam), _ad(r), _ad(J), _ad(H), _ad(g)))
         return r, J, H, g
 
     def eval_dev(self, x, lam=None, y=None, J=None, H=None, g=None, stream=None):
