@@ -474,7 +474,20 @@ int check_net(const nnc_net* net) {
   return NNC_OK;
 }
 
-// Host-pointer wrapper: copy inputs in, run, copy outputs out, wait.
+// Device address of a host buffer in page-locked memory (cudaHostAlloc, cudaHostRegister), which
+// the device reads and writes directly through unified addressing; NULL for pageable memory.
+void* pinned_dev_ptr(void* host) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// Host-pointer wrapper: copy inputs in, run, copy outputs out, wait.  A Hessian output in
+// page-locked memory is written there by the kernel that forms it (no device copy, no transfer
+// after it).
 int host_call(nnc_net* net, const double* x, const double* lam, double* y, double* J, double* H,
               double* g, const double* yv = nullptr, double* rr = nullptr) {
   int r = check_net(net);
@@ -500,16 +513,18 @@ int host_call(nnc_net* net, const double* x, const double* lam, double* y, doubl
     std::memcpy(hy, yv, sizeof(double) * net->n_out);
     CK(cudaMemcpyAsync(net->yres, hy, sizeof(double) * net->n_out, cudaMemcpyHostToDevice, st));
   }
+  double* H_direct = H ? (double*)pinned_dev_ptr(H) : nullptr;
   r = eval_all(net, net->xin, lam ? net->lam : nullptr, y ? net->ydev : nullptr,
-               J ? net->Jdev : nullptr, H ? net->Hdev : nullptr, g ? net->gdev : nullptr, st,
-               rr ? net->yres : nullptr, rr ? net->rdev : nullptr);
+               J ? net->Jdev : nullptr, H_direct ? H_direct : H ? net->Hdev : nullptr,
+               g ? net->gdev : nullptr, st, rr ? net->yres : nullptr, rr ? net->rdev : nullptr);
   if (r) return r;
   if (rr) CK(cudaMemcpyAsync(rr, net->rdev, sizeof(double) * net->n_out, cudaMemcpyDeviceToHost, st));
   if (y) CK(cudaMemcpyAsync(y, net->ydev, sizeof(double) * net->n_out, cudaMemcpyDeviceToHost, st));
   if (J) CK(cudaMemcpyAsync(J, net->Jdev, sizeof(double) * net->n_out * net->n_in,
                             cudaMemcpyDeviceToHost, st));
-  if (H) CK(cudaMemcpyAsync(H, net->Hdev, sizeof(double) * net->n_in * net->n_in,
-                            cudaMemcpyDeviceToHost, st));
+  if (H && !H_direct)
+    CK(cudaMemcpyAsync(H, net->Hdev, sizeof(double) * net->n_in * net->n_in,
+                       cudaMemcpyDeviceToHost, st));
   if (g) CK(cudaMemcpyAsync(g, net->gdev, sizeof(double) * net->n_in, cudaMemcpyDeviceToHost, st));
   return sync_check(net, st);   // the error word of the bounded waits comes back with the outputs
 }
