@@ -445,9 +445,9 @@ int eval_all(nnc_net* net, const double* x, const double* lam, double* y, double
       if (r != NNC_OK) return r;
     }
   }
-  if (y)
-    CK(cudaMemcpyAsync(y, net->layers.back().a, sizeof(double) * net->n_out,
-                       cudaMemcpyDeviceToDevice, vs));
+  if (y)   // y may be the device address of page-locked host memory
+    CK(cudaMemcpyAsync(y, net->layers.back().a, sizeof(double) * net->n_out, cudaMemcpyDefault,
+                       vs));
   if (rr) CK(launch_sub(yv, net->layers.back().a, rr, net->n_out, vs));
   const bool need_lam = (H != nullptr) || (g != nullptr);
   if (fork) {
@@ -485,9 +485,8 @@ void* pinned_dev_ptr(void* host) {
   return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
-// Host-pointer wrapper: copy inputs in, run, copy outputs out, wait.  A Hessian output in
-// page-locked memory is written there by the kernel that forms it (no device copy, no transfer
-// after it).
+// Host-pointer wrapper: copy inputs in, run, copy outputs out, wait.  An output in page-locked
+// memory is written there by the kernel that forms it (no device buffer, no transfer after it).
 int host_call(nnc_net* net, const double* x, const double* lam, double* y, double* J, double* H,
               double* g, const double* yv = nullptr, double* rr = nullptr) {
   int r = check_net(net);
@@ -513,19 +512,23 @@ int host_call(nnc_net* net, const double* x, const double* lam, double* y, doubl
     std::memcpy(hy, yv, sizeof(double) * net->n_out);
     CK(cudaMemcpyAsync(net->yres, hy, sizeof(double) * net->n_out, cudaMemcpyHostToDevice, st));
   }
-  double* H_direct = H ? (double*)pinned_dev_ptr(H) : nullptr;
-  r = eval_all(net, net->xin, lam ? net->lam : nullptr, y ? net->ydev : nullptr,
-               J ? net->Jdev : nullptr, H_direct ? H_direct : H ? net->Hdev : nullptr,
-               g ? net->gdev : nullptr, st, rr ? net->yres : nullptr, rr ? net->rdev : nullptr);
+  // each output: written in place if pinned, else through its device buffer and a copy
+  auto direct = [](double* h) { return h ? (double*)pinned_dev_ptr(h) : nullptr; };
+  double *y_d = direct(y), *J_d = direct(J), *H_d = direct(H), *g_d = direct(g), *r_d = direct(rr);
+  r = eval_all(net, net->xin, lam ? net->lam : nullptr, y_d ? y_d : y ? net->ydev : nullptr,
+               J_d ? J_d : J ? net->Jdev : nullptr, H_d ? H_d : H ? net->Hdev : nullptr,
+               g_d ? g_d : g ? net->gdev : nullptr, st, rr ? net->yres : nullptr,
+               r_d ? r_d : rr ? net->rdev : nullptr);
   if (r) return r;
-  if (rr) CK(cudaMemcpyAsync(rr, net->rdev, sizeof(double) * net->n_out, cudaMemcpyDeviceToHost, st));
-  if (y) CK(cudaMemcpyAsync(y, net->ydev, sizeof(double) * net->n_out, cudaMemcpyDeviceToHost, st));
-  if (J) CK(cudaMemcpyAsync(J, net->Jdev, sizeof(double) * net->n_out * net->n_in,
-                            cudaMemcpyDeviceToHost, st));
-  if (H && !H_direct)
-    CK(cudaMemcpyAsync(H, net->Hdev, sizeof(double) * net->n_in * net->n_in,
-                       cudaMemcpyDeviceToHost, st));
-  if (g) CK(cudaMemcpyAsync(g, net->gdev, sizeof(double) * net->n_in, cudaMemcpyDeviceToHost, st));
+  auto back = [&](double* h, double* d_direct, const double* dev, size_t n) -> cudaError_t {
+    if (!h || d_direct) return cudaSuccess;
+    return cudaMemcpyAsync(h, dev, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
+  };
+  CK(back(rr, r_d, net->rdev, net->n_out));
+  CK(back(y, y_d, net->ydev, net->n_out));
+  CK(back(J, J_d, net->Jdev, (size_t)net->n_out * net->n_in));
+  CK(back(H, H_d, net->Hdev, (size_t)net->n_in * net->n_in));
+  CK(back(g, g_d, net->gdev, net->n_in));
   return sync_check(net, st);   // the error word of the bounded waits comes back with the outputs
 }
 
@@ -981,8 +984,7 @@ int nnc_eval(nnc_net* net, const double* x, double* y, int fp64_residual) {
   r = run_forward_fp64_values(net, net->xin, st);
   if (r) return r;
   CK(cudaMemcpyAsync(y, net->layers.back().ra, sizeof(double) * net->n_out, cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  return NNC_OK;
+  return sync_check(net, st);   // the value pass's bounded waits too
 }
 
 int nnc_eval_dev(nnc_net* net, const double* x, double* y, int fp64_residual, void* stream) {
