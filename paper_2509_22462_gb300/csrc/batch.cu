@@ -704,14 +704,20 @@ int nnc_batch_eval_kkt(nnc_batch* b, const double* x, const double* y, const dou
     std::memcpy(hl, lambda, sizeof(double) * nl);
     BCK(cudaMemcpyAsync(b->lam_in, hl, sizeof(double) * nl, cudaMemcpyHostToDevice, st));
   }
+  // outputs in page-locked memory are written in place by the kernels that form them
+  auto direct = [](double* h) { return h ? (double*)pinned_dev_ptr(h) : nullptr; };
+  double *r_d = direct(r), *J_d = direct(J), *H_d = direct(H), *g_d = direct(grad);
   int rc = nnc_batch_eval_kkt_dev(b, b->x_in, r ? b->y_in : nullptr, lambda ? b->lam_in : nullptr,
-                                  r ? b->r_out : nullptr, J ? b->J_out : nullptr,
-                                  H ? b->H_out : nullptr, grad ? b->g_out : nullptr, st);
+                                  r_d ? r_d : r ? b->r_out : nullptr, J_d ? J_d : J ? b->J_out : nullptr,
+                                  H_d ? H_d : H ? b->H_out : nullptr,
+                                  g_d ? g_d : grad ? b->g_out : nullptr, st);
   if (rc) return rc;
-  if (r) BCK(cudaMemcpyAsync(r, b->r_out, sizeof(double) * nl, cudaMemcpyDeviceToHost, st));
-  if (J) BCK(cudaMemcpyAsync(J, b->J_out, sizeof(double) * b->n_sum * b->n_out, cudaMemcpyDeviceToHost, st));
-  if (H) BCK(cudaMemcpyAsync(H, b->H_out, sizeof(double) * b->h_sum, cudaMemcpyDeviceToHost, st));
-  if (grad) BCK(cudaMemcpyAsync(grad, b->g_out, sizeof(double) * b->n_sum, cudaMemcpyDeviceToHost, st));
+  if (r && !r_d) BCK(cudaMemcpyAsync(r, b->r_out, sizeof(double) * nl, cudaMemcpyDeviceToHost, st));
+  if (J && !J_d)
+    BCK(cudaMemcpyAsync(J, b->J_out, sizeof(double) * b->n_sum * b->n_out, cudaMemcpyDeviceToHost, st));
+  if (H && !H_d) BCK(cudaMemcpyAsync(H, b->H_out, sizeof(double) * b->h_sum, cudaMemcpyDeviceToHost, st));
+  if (grad && !g_d)
+    BCK(cudaMemcpyAsync(grad, b->g_out, sizeof(double) * b->n_sum, cudaMemcpyDeviceToHost, st));
   return sync_check(b, st);
 }
 

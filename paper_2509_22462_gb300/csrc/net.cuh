@@ -10,6 +10,10 @@
 struct nnc_net;
 namespace nnc {
 void set_last_error(const std::string& msg);
+// Device address of a host buffer in page-locked memory (cudaHostAlloc, cudaHostRegister), which
+// kernels read and write directly through unified addressing; NULL for pageable memory.  Host
+// calls let the kernels that form an output write such a buffer in place.
+void* pinned_dev_ptr(void* host);
 void batch_cache_forget(const nnc_net* net);
 int eval_batched_grouped(nnc_net* const* nets, int K, const double* const* x,
                          const double* const* lambda, double* const* y, double* const* J,

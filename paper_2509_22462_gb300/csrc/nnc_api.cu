@@ -27,6 +27,14 @@ static int fail(int code, const std::string& msg) {
   return code;
 }
 void set_last_error(const std::string& msg) { g_err = msg; }
+void* pinned_dev_ptr(void* host) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
 }  // namespace nnc
 
 using namespace nnc;
@@ -472,17 +480,6 @@ int eval_all(nnc_net* net, const double* x, const double* lam, double* y, double
 int check_net(const nnc_net* net) {
   if (!net) return fail(NNC_ERR_ARG, "net is NULL");
   return NNC_OK;
-}
-
-// Device address of a host buffer in page-locked memory (cudaHostAlloc, cudaHostRegister), which
-// the device reads and writes directly through unified addressing; NULL for pageable memory.
-void* pinned_dev_ptr(void* host) {
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
-    cudaGetLastError();
-    return nullptr;
-  }
-  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
 // Host-pointer wrapper: copy inputs in, run, copy outputs out, wait.  An output in page-locked

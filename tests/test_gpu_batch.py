@@ -225,6 +225,35 @@ def test_host_eval_kkt_matches_separate_calls(nnc, small_batch):
     b.free()
 
 
+def test_host_eval_kkt_pinned_outputs(nnc, small_batch):
+    """nnc_batch_eval_kkt with outputs in page-locked memory (written in place by the kernels that
+    form them) equals the call with pageable outputs bit for bit, with and without the CUDA graph,
+    on repeated calls."""
+    import torch
+    data, raw, nets = small_batch
+    b = nnc.Batch(nets)
+    x = synth.uniform01(synth.derive_key(6, "bx"), data.G)
+    xs = [x[S] for S in data.subsets]
+    lams = [np.array([0.2 + 0.03 * k]) for k in range(len(raw))]
+    ys = [np.array([0.05 * k - 0.3]) for k in range(len(raw))]
+    ref = b.eval_kkt(xs, ys, lams)
+
+    def pin(k):
+        a = torch.empty(k, dtype=torch.float64, pin_memory=True).numpy()
+        a[...] = np.nan
+        return a
+
+    outs = tuple(pin(a.size) for a in ref)
+    for graph in (False, True, True):
+        b.use_graph(graph)
+        got = b.eval_kkt(xs, ys, lams, out=outs)
+        for a, c in zip(got, ref):
+            assert np.array_equal(a, c)
+        for a in outs:
+            a[...] = np.nan
+    b.free()
+
+
 def test_batch_bench_size_matches_oracle(nnc):
     """The batch the bench times: 256 surrogates n_k -> 1024 x 5 sigmoid -> 1 with n_k ~ U{20..200}
     (seed 0, loads d = 1), autotuned tiles, one fused evaluation per iterate replayed from the CUDA
