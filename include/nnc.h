@@ -17,7 +17,8 @@
  *     throws across this interface.  nnc_last_error() gives a message for the calling thread.
  *   - Host pointers ("const double* x"): owned by the caller, read or written during the call
  *     only; the call copies them to or from the device and returns after the device work and
- *     the copies have finished.
+ *     the copies have finished.  An output in page-locked memory (cudaHostAlloc,
+ *     cudaHostRegister) is written in place by the kernel that forms it, without a copy.
  *   - Device pointers (entry points ending in _dev): owned by the caller, must stay valid
  *     until the work queued on `stream` has finished; the call returns once the work is
  *     queued (asynchronous).  `stream` is a cudaStream_t; NULL means the net's own stream.
