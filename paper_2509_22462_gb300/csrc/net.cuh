@@ -64,12 +64,12 @@ struct nnc_net {
   std::vector<void*> allocs;
   double* x = nullptr;       // a_0 [n_in_pad]
   void* x2 = nullptr;        // double-float (hi, lo) pairs of a_0 [n_in_pad] (float2)
-  double* xin = nullptr;     // host-call staging of x [n_in_pad]
+  double* xin = nullptr;     // host-call inputs: x [n_in_pad] | lambda | y, one block
   double* xr = nullptr;      // input of the FP64 residual pass [n_in_pad] (its own copy, so that
                              // a residual may run on another stream next to an evaluation)
   void* xr2 = nullptr;       // its double-float pairs (float2)
-  double* yres = nullptr;    // host-call staging of y for the residual [n_out]
-  double* lam = nullptr;     // [n_out]
+  double* yres = nullptr;    // y for the residual [n_out] (in the xin block)
+  double* lam = nullptr;     // lambda [n_out] (in the xin block)
   double* ydev = nullptr;    // [n_out] staging
   double* rdev = nullptr;    // [n_out]
   double* Zbar[2] = {nullptr, nullptr};

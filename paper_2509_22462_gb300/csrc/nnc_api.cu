@@ -503,12 +503,11 @@ int host_call(nnc_net* net, const double* x, const double* lam, double* y, doubl
   double* hl = hs + net->n_in_pad;
   double* hy = hl + net->n_out;
   if (lam) std::memcpy(hl, lam, sizeof(double) * net->n_out);
-  CK(cudaMemcpyAsync(net->xin, hs, sizeof(double) * net->n_in, cudaMemcpyHostToDevice, st));
-  if (lam) CK(cudaMemcpyAsync(net->lam, hl, sizeof(double) * net->n_out, cudaMemcpyHostToDevice, st));
-  if (rr) {
-    std::memcpy(hy, yv, sizeof(double) * net->n_out);
-    CK(cudaMemcpyAsync(net->yres, hy, sizeof(double) * net->n_out, cudaMemcpyHostToDevice, st));
-  }
+  if (rr) std::memcpy(hy, yv, sizeof(double) * net->n_out);
+  // one copy of the staging block up to the last input used (the device block has its layout)
+  const size_t n_copy = rr ? (size_t)(hy - hs) + net->n_out
+                        : lam ? (size_t)(hl - hs) + net->n_out : (size_t)net->n_in;
+  CK(cudaMemcpyAsync(net->xin, hs, sizeof(double) * n_copy, cudaMemcpyHostToDevice, st));
   // each output: written in place if pinned, else through its device buffer and a copy
   auto direct = [](double* h) { return h ? (double*)pinned_dev_ptr(h) : nullptr; };
   double *y_d = direct(y), *J_d = direct(J), *H_d = direct(H), *g_d = direct(g), *r_d = direct(rr);
@@ -742,20 +741,22 @@ static int load_impl(nnc_net* net, int n_layers, const int* widths, const int* a
   }
   net->mp_max = mp_max;
   AL(net->x, net->n_in_pad);
-  AL(net->xin, net->n_in_pad);
+  // host-call inputs x | lambda | y in one block laid out as the pinned staging, so that one copy
+  // moves them
+  AL(net->xin, (size_t)net->n_in_pad + 2 * (size_t)net->n_out);
+  net->lam = net->xin + net->n_in_pad;
+  net->yres = net->lam + net->n_out;
   {
     float2* x2;
     AL(x2, net->n_in_pad);
     net->x2 = x2;
   }
   AL(net->xr, net->n_in_pad);
-  AL(net->yres, net->n_out);
   {
     float2* x2;
     AL(x2, net->n_in_pad);
     net->xr2 = x2;
   }
-  AL(net->lam, net->n_out);
   AL(net->ydev, net->n_out);
   AL(net->rdev, net->n_out);
   AL(net->Zbar[0], (size_t)mp_max * net->S_max);
